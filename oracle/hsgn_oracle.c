@@ -1,0 +1,502 @@
+/*
+ * hsgn_oracle.c -- plain, serial, FP64 CPU restatement of the semi-implicit
+ * IMEX time step of the hyperbolic Serre-Green-Naghdi (hSGN) system.
+ *
+ * TEST INFRASTRUCTURE. This is the oracle the CUDA library is checked
+ * against. Only the test-suite, the smoke check and the CPU-baseline leg of
+ * the benchmark load it. It shares no code, header, table or helper with the
+ * CUDA library and never calls it.
+ *
+ * Source: E. Macca, W. Boscheri, M. Ricchiuto, "Semi-implicit strategies for
+ * the Serre-Green-Naghdi equations in hyperbolic form" (arXiv 2510.07539).
+ *   hSGN system, pressure:          Sec. 2.2, eqs. (hSGN_eq), (eq:hSGN_p)
+ *   eigenvalues / celerity:         eqs. (eq:hSGN_eigenvalues), (eq:hSGN_c)
+ *   pressure-gradient split:        eqs. (eq:hSGN_px), (eq:hSGN_alpha)
+ *   splitting and h-elimination:    Sec. 3.1, eqs. (hSGN_eq-split) .. (eq:hnew)
+ *   IMEX stages and tableau:        Sec. 3.2, eq. (tableau) and its efficient form
+ *   time-step rule:                 Sec. 3.3 eq. (eq:MCFL), Sec. 5 (CFL definitions)
+ *   D_x, hat D_x, reconstruction:   Sec. 4.1
+ *   fully-discrete stage:           Sec. 4.2, eq. (GN_hyp_eq_semi_fully_discrete)
+ *
+ * Readings where the paper is silent or ambiguous (each restated at its use):
+ *   R1  the printed 2-stage tableau (implicit first stage) is the scheme;
+ *   R2  interface coefficients beta_{i+1/2}, delta_{i+1/2} are arithmetic means;
+ *   R3  the "1/2" in front of the delta term of h^dagger pairs with a SUM of the
+ *       two cell values, i.e. the term uses the mean with factor 1 (the literal
+ *       reading is kept behind a flag, used only by a test that shows it gives
+ *       the wrong linear dispersion);
+ *   R4  in a stage, the additive "old" values come from the base state U_b and
+ *       every flux and coefficient from the linearisation state U_l = U_E^(i);
+ *   R5  reconstruction acts on the conserved variables (h, q, m, r). The
+ *       Rusanov speed "alpha ~ |u|" (Sec. 4.1) is read as the global speed
+ *       max_i |u_i^n| of the step (the same u_max the time-step rule of Sec. 5
+ *       computes at t^n), used by both stages (rusanov = 1, default). The
+ *       local speed max(|u^L|, |u^R|) is kept as rusanov = 0. Reason: at rest
+ *       the local speed is zero, the explicit flux of h eta is then linear in
+ *       q (coefficient eta) with no dissipation, and the linearised step
+ *       amplifies grid-scale modes (spectral radius 1.02-1.14 per step on the
+ *       paper's grids); the global speed damps them;
+ *   R6  periodic: indices wrap and the matrix is cyclic; transmissive:
+ *       zero-order ghost copies of every per-cell quantity, so the end rows of
+ *       the matrix are Neumann rows;
+ *   R9  nu = |u| + sqrt(g h + (lambda/3) eta^2/h^2) (the form of eq. (eq:hSGN_c)).
+ *
+ * State layout: four arrays of n cells each, h, q = h u, m = h eta, r = h w.
+ * Every routine returns 0 on success or a positive error code (see below).
+ *
+ * Parity status of each function (what pins it, in the test-suite):
+ *   oracle_tridiag_solve   dense LU of the same matrix (library routine)
+ *   oracle_imex_scalar     stability function from the unreduced tableau,
+ *                          Taylor expansion 1 + z + z^2/2 + O(z^3)
+ *   oracle_stage/step/run  exact mass conservation, constant-state
+ *                          preservation, mirror symmetry, periodic shift,
+ *                          linear hSGN dispersion relation (with Doppler
+ *                          shift), lambda = 0 shallow-water limit, solitary
+ *                          wave closed form (convergence trend), temporal
+ *                          order 2
+ *   oracle_assemble        row sums 1 (Delta[const] = const), symmetry,
+ *                          diagonal dominance
+ *   oracle_suggest_dt      the CFL_SW / CFL_IMEX ratios printed for the
+ *                          Gaussian-bell test (Sec. 6.1)
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define ORACLE_OK 0
+#define ORACLE_ERR_ARG 1
+#define ORACLE_ERR_DEPTH 2      /* a depth used as a divisor was <= 0 */
+#define ORACLE_ERR_COERCIVE 3   /* beta <= 0 or a zero pivot */
+#define ORACLE_ERR_NONFINITE 4
+#define ORACLE_ERR_NOMEM 5
+
+#define BC_PERIODIC 0
+#define BC_TRANSMISSIVE 1
+
+typedef struct {
+    int64_t n;          /* number of cells, >= 3 */
+    double dx;          /* uniform cell width */
+    int32_t bc;         /* BC_PERIODIC or BC_TRANSMISSIVE */
+    int32_t delta_half; /* 0: reading R3 (default); 1: literal factor 1/2 */
+    double g;           /* gravity */
+    double lambda;      /* relaxation parameter, >= 0 */
+    int32_t rusanov;    /* 0: local speed max(|u^L|,|u^R|); 1: global speed (R5) */
+    int32_t pad_;
+    double speed;       /* global Rusanov speed of the current step (rusanov == 1) */
+} oracle_params;
+
+/* Neighbour index: wrap (periodic) or clamp to the boundary cell
+ * (transmissive, zero-order ghost copies, reading R6). */
+static int64_t nb(const oracle_params* p, int64_t i) {
+    if (p->bc == BC_PERIODIC) {
+        int64_t k = i % p->n;
+        return k < 0 ? k + p->n : k;
+    }
+    if (i < 0) return 0;
+    if (i >= p->n) return p->n - 1;
+    return i;
+}
+
+/* ------------------------------------------------------------------------
+ * Tridiagonal solve. Row i reads a[i] x[i-1] + b[i] x[i] + c[i] x[i+1] = d[i].
+ * periodic == 0: a[0] and c[n-1] are ignored (plain Thomas elimination).
+ * periodic != 0: a[0] couples x[n-1] and c[n-1] couples x[0] (cyclic
+ * matrix); solved by writing the matrix as a tridiagonal matrix plus a rank-one
+ * correction u v^T and applying the Sherman-Morrison formula
+ *   x = y - z (v.y) / (1 + v.z),   T y = d,  T z = u.
+ * Choice: u = (s, 0..0, c[n-1]), v = (1, 0..0, a[0]/s) with s = -b[0], so T
+ * has T[0][0] = b[0] - s and T[n-1][n-1] = b[n-1] - a[0] c[n-1] / s.
+ * ------------------------------------------------------------------------ */
+static int thomas(int64_t n, const double* a, const double* b, const double* c,
+                  const double* d, double* x, double* work) {
+    /* forward elimination: work holds the modified super-diagonal */
+    double piv = b[0];
+    if (!(piv != 0.0)) return ORACLE_ERR_COERCIVE;
+    work[0] = c[0] / piv;
+    x[0] = d[0] / piv;
+    for (int64_t i = 1; i < n; ++i) {
+        piv = b[i] - a[i] * work[i - 1];
+        if (!(piv != 0.0)) return ORACLE_ERR_COERCIVE;
+        work[i] = (i < n - 1) ? c[i] / piv : 0.0;
+        x[i] = (d[i] - a[i] * x[i - 1]) / piv;
+    }
+    /* back substitution */
+    for (int64_t i = n - 2; i >= 0; --i) x[i] = x[i] - work[i] * x[i + 1];
+    return ORACLE_OK;
+}
+
+int oracle_tridiag_solve(int64_t n, int32_t periodic, const double* a, const double* b,
+                         const double* c, const double* d, double* x) {
+    if (n < 1 || !a || !b || !c || !d || !x) return ORACLE_ERR_ARG;
+    if (n == 1) {
+        double diag = b[0] + (periodic ? a[0] + c[0] : 0.0);
+        if (!(diag != 0.0)) return ORACLE_ERR_COERCIVE;
+        x[0] = d[0] / diag;
+        return ORACLE_OK;
+    }
+    if (!periodic || n == 2) {
+        double* work = (double*)malloc((size_t)n * sizeof(double));
+        if (!work) return ORACLE_ERR_NOMEM;
+        int rc;
+        if (!periodic) {
+            rc = thomas(n, a, b, c, d, x, work);
+        } else {
+            /* n == 2: both couplings of each row hit the other unknown */
+            double bb[2] = {b[0], b[1]};
+            double aa[2] = {0.0, a[1] + c[1]};
+            double cc[2] = {a[0] + c[0], 0.0};
+            rc = thomas(2, aa, bb, cc, d, x, work);
+        }
+        free(work);
+        return rc;
+    }
+    double* bt = (double*)malloc((size_t)n * sizeof(double));
+    double* u = (double*)malloc((size_t)n * sizeof(double));
+    double* z = (double*)malloc((size_t)n * sizeof(double));
+    double* work = (double*)malloc((size_t)n * sizeof(double));
+    if (!bt || !u || !z || !work) {
+        free(bt); free(u); free(z); free(work);
+        return ORACLE_ERR_NOMEM;
+    }
+    const double s = -b[0];
+    const double corner_lo = c[n - 1]; /* A[n-1][0] */
+    const double corner_hi = a[0];     /* A[0][n-1] */
+    memcpy(bt, b, (size_t)n * sizeof(double));
+    bt[0] = b[0] - s;
+    bt[n - 1] = b[n - 1] - corner_hi * corner_lo / s;
+    for (int64_t i = 0; i < n; ++i) u[i] = 0.0;
+    u[0] = s;
+    u[n - 1] = corner_lo;
+    int rc = thomas(n, a, bt, c, d, x, work);
+    if (rc == ORACLE_OK) rc = thomas(n, a, bt, c, u, z, work);
+    if (rc == ORACLE_OK) {
+        const double vy = x[0] + (corner_hi / s) * x[n - 1];
+        const double vz = z[0] + (corner_hi / s) * z[n - 1];
+        const double den = 1.0 + vz;
+        if (!(den != 0.0)) {
+            rc = ORACLE_ERR_COERCIVE;
+        } else {
+            const double f = vy / den;
+            for (int64_t i = 0; i < n; ++i) x[i] -= f * z[i];
+        }
+    }
+    free(bt); free(u); free(z); free(work);
+    return rc;
+}
+
+/* ------------------------------------------------------------------------
+ * One implicit stage of the semi-implicit scheme, Sec. 4.2, eq.
+ * (GN_hyp_eq_semi_fully_discrete), with Delta t replaced by the stage step tau
+ * and the state roles of reading R4:
+ *   base state U_b: the additive old values h, q, h eta, h w;
+ *   linearisation state U_l: the reconstructed fluxes (Sec. 4.1) and every
+ *   coefficient (a^2, alpha, beta_1, beta_2, beta, delta).
+ * The full set of per-cell quantities is returned through `asm_out` when it is
+ * not NULL (used by the tests of the assembled matrix).
+ * ------------------------------------------------------------------------ */
+typedef struct {
+    double *qs, *ms, *rs;          /* q^dagger, (h eta)^dagger, (h w)^dagger */
+    double *beta, *delta;          /* cell coefficients */
+    double *a, *b, *c, *d;         /* rows of Delta[h] = h^dagger */
+} oracle_assembly;
+
+static double sqr(double x) { return x * x; }
+
+static int stage_impl(const oracle_params* p,
+                      const double* hb, const double* qb, const double* mb, const double* rb,
+                      const double* hl, const double* ql, const double* ml, const double* rl,
+                      double tau, double* ho, double* qo, double* mo, double* ro,
+                      oracle_assembly* keep) {
+    const int64_t n = p->n;
+    if (n < 3 || !(p->dx > 0.0) || !(tau >= 0.0) || !(p->lambda >= 0.0)) return ORACLE_ERR_ARG;
+    const double dx = p->dx, g = p->g, lam = p->lambda;
+    int rc = ORACLE_OK;
+
+    /* face fluxes: index k + 1 holds the face between cells k and k+1, k = -1..n-1 */
+    double* Fq = (double*)malloc((size_t)(n + 1) * sizeof(double));
+    double* Fm = (double*)malloc((size_t)(n + 1) * sizeof(double));
+    double* Fr = (double*)malloc((size_t)(n + 1) * sizeof(double));
+    double* qs = (double*)malloc((size_t)n * sizeof(double));
+    double* ms = (double*)malloc((size_t)n * sizeof(double));
+    double* rs = (double*)malloc((size_t)n * sizeof(double));
+    double* beta = (double*)malloc((size_t)n * sizeof(double));
+    double* delta = (double*)malloc((size_t)n * sizeof(double));
+    double* A = (double*)malloc((size_t)n * sizeof(double));
+    double* B = (double*)malloc((size_t)n * sizeof(double));
+    double* C = (double*)malloc((size_t)n * sizeof(double));
+    double* D = (double*)malloc((size_t)n * sizeof(double));
+    double* hbar = (double*)malloc((size_t)n * sizeof(double));
+    if (!Fq || !Fm || !Fr || !qs || !ms || !rs || !beta || !delta || !A || !B || !C || !D || !hbar) {
+        rc = ORACLE_ERR_NOMEM;
+        goto done;
+    }
+
+    /* (1) Rusanov fluxes of hu^2, hu eta, hu w at every face (Sec. 4.1, hat D_x)
+     * from the unlimited centred linear reconstruction of the conserved
+     * variables of U_l:  v^L_{k+1/2} = v_k + (v_{k+1} - v_{k-1})/4,
+     *                    v^R_{k+1/2} = v_{k+1} - (v_{k+2} - v_k)/4. */
+    for (int64_t k = -1; k < n; ++k) {
+        const int64_t im = nb(p, k - 1), i0 = nb(p, k), i1 = nb(p, k + 1), i2 = nb(p, k + 2);
+        const double hL = hl[i0] + (hl[i1] - hl[im]) / 4.0;
+        const double hR = hl[i1] - (hl[i2] - hl[i0]) / 4.0;
+        const double qL = ql[i0] + (ql[i1] - ql[im]) / 4.0;
+        const double qR = ql[i1] - (ql[i2] - ql[i0]) / 4.0;
+        const double mL = ml[i0] + (ml[i1] - ml[im]) / 4.0;
+        const double mR = ml[i1] - (ml[i2] - ml[i0]) / 4.0;
+        const double rL = rl[i0] + (rl[i1] - rl[im]) / 4.0;
+        const double rR = rl[i1] - (rl[i2] - rl[i0]) / 4.0;
+        if (!(hL > 0.0) || !(hR > 0.0)) { rc = ORACLE_ERR_DEPTH; goto done; }
+        const double uL = qL / hL, uR = qR / hR;
+        const double s = p->rusanov ? p->speed : fmax(fabs(uL), fabs(uR));
+        Fq[k + 1] = 0.5 * (uL * qL + uR * qR - s * (qR - qL));
+        Fm[k + 1] = 0.5 * (uL * mL + uR * mR - s * (mR - mL));
+        Fr[k + 1] = 0.5 * (uL * rL + uR * rR - s * (rR - rL));
+    }
+
+    /* (2) starred values and the coefficients of eqs. (eq:hSGN_alpha) and
+     * (GN_hyp_eq_semi_fully_discrete), per cell. */
+    for (int64_t i = 0; i < n; ++i) {
+        rs[i] = rb[i] - (tau / dx) * (Fr[i + 1] - Fr[i]) + lam * tau;
+        ms[i] = mb[i] - (tau / dx) * (Fm[i + 1] - Fm[i]) + tau * rs[i];
+        qs[i] = qb[i] - (tau / dx) * (Fq[i + 1] - Fq[i]);
+        const double h = hl[i];
+        if (!(h > 0.0)) { rc = ORACLE_ERR_DEPTH; goto done; }
+        const double eta = ml[i] / h;
+        const double alpha = -(2.0 * eta / h - 1.0) / (3.0 * h);
+        const double c2 = g * h + (lam / 3.0) * eta * eta / (h * h);
+        const double a2 = c2 - lam * eta * alpha;
+        const double beta1 = 1.0 + lam * tau * tau / (h * h);
+        const double beta2 = 2.0 * lam * tau * tau / (beta1 * beta1 * h * h * h);
+        beta[i] = a2 + lam * alpha * beta2 * ms[i];
+        delta[i] = alpha / beta1;
+        if (!(beta[i] > 0.0)) { rc = ORACLE_ERR_COERCIVE; goto done; }
+    }
+
+    /* (3) rows of Delta[h]_i = h^dagger_i. Interface values are means (R2);
+     * the delta term carries factor 1 with means (R3). */
+    {
+        const double Cc = tau * tau / (dx * dx);
+        const double fd = (p->delta_half ? 0.5 : 1.0) * lam * tau * tau / (dx * dx);
+        for (int64_t i = 0; i < n; ++i) {
+            const int64_t il = nb(p, i - 1), ir = nb(p, i + 1);
+            const double bm = 0.5 * (beta[il] + beta[i]);   /* beta_{i-1/2} */
+            const double bp = 0.5 * (beta[i] + beta[ir]);   /* beta_{i+1/2} */
+            const double dm = 0.5 * (delta[il] + delta[i]);
+            const double dp = 0.5 * (delta[i] + delta[ir]);
+            D[i] = hb[i] - (tau / (2.0 * dx)) * (qs[ir] - qs[il])
+                 + fd * (dp * (ms[ir] - ms[i]) - dm * (ms[i] - ms[il]));
+            A[i] = -Cc * bm;
+            C[i] = -Cc * bp;
+            B[i] = 1.0 + Cc * (bm + bp);
+            if (p->bc == BC_TRANSMISSIVE) {
+                /* Neumann rows: the ghost h_{-1} = h_0 (resp. h_n = h_{n-1}) */
+                if (i == 0) { B[i] = 1.0 + Cc * bp; A[i] = 0.0; }
+                if (i == n - 1) { B[i] = 1.0 + Cc * bm; C[i] = 0.0; }
+            }
+        }
+    }
+
+    /* (4) solve Delta[hbar] = h^dagger (cyclic when periodic) */
+    rc = oracle_tridiag_solve(n, p->bc == BC_PERIODIC, A, B, C, D, hbar);
+    if (rc != ORACLE_OK) goto done;
+
+    /* (5) back-substitution for qbar, (h eta)bar, (h w)bar; the fourth
+     * equation treats h^2 implicitly (Sec. 6.3.1, "second version"). */
+    for (int64_t i = 0; i < n; ++i) {
+        const int64_t il = nb(p, i - 1), ir = nb(p, i + 1);
+        const double h = hbar[i];
+        if (!(h > 0.0)) { rc = ORACLE_ERR_DEPTH; goto done; }
+        const double q = qs[i] - (tau / (2.0 * dx)) * beta[i] * (hbar[ir] - hbar[il])
+                       - (lam * tau / (2.0 * dx)) * delta[i] * (ms[ir] - ms[il]);
+        const double m = ms[i] / (1.0 + lam * tau * tau / (h * h));
+        const double r = rs[i] - lam * tau * m / (h * h);
+        if (!isfinite(h) || !isfinite(q) || !isfinite(m) || !isfinite(r)) {
+            rc = ORACLE_ERR_NONFINITE;
+            goto done;
+        }
+        ho[i] = h; qo[i] = q; mo[i] = m; ro[i] = r;
+    }
+
+    if (keep) {
+        memcpy(keep->qs, qs, (size_t)n * sizeof(double));
+        memcpy(keep->ms, ms, (size_t)n * sizeof(double));
+        memcpy(keep->rs, rs, (size_t)n * sizeof(double));
+        memcpy(keep->beta, beta, (size_t)n * sizeof(double));
+        memcpy(keep->delta, delta, (size_t)n * sizeof(double));
+        memcpy(keep->a, A, (size_t)n * sizeof(double));
+        memcpy(keep->b, B, (size_t)n * sizeof(double));
+        memcpy(keep->c, C, (size_t)n * sizeof(double));
+        memcpy(keep->d, D, (size_t)n * sizeof(double));
+    }
+
+done:
+    free(Fq); free(Fm); free(Fr); free(qs); free(ms); free(rs); free(beta); free(delta);
+    free(A); free(B); free(C); free(D); free(hbar);
+    return rc;
+}
+
+int oracle_stage(const oracle_params* p,
+                 const double* hb, const double* qb, const double* mb, const double* rb,
+                 const double* hl, const double* ql, const double* ml, const double* rl,
+                 double tau, double* ho, double* qo, double* mo, double* ro) {
+    if (!p) return ORACLE_ERR_ARG;
+    return stage_impl(p, hb, qb, mb, rb, hl, ql, ml, rl, tau, ho, qo, mo, ro, NULL);
+}
+
+/* The assembled quantities of one stage (same arguments as oracle_stage);
+ * outputs are n-long arrays. */
+int oracle_assemble(const oracle_params* p,
+                    const double* hb, const double* qb, const double* mb, const double* rb,
+                    const double* hl, const double* ql, const double* ml, const double* rl,
+                    double tau, double* qs, double* ms, double* rs, double* beta,
+                    double* delta, double* a, double* b, double* c, double* d) {
+    if (!p) return ORACLE_ERR_ARG;
+    const int64_t n = p->n;
+    if (n < 3) return ORACLE_ERR_ARG;
+    double* tmp = (double*)malloc((size_t)(4 * n) * sizeof(double));
+    if (!tmp) return ORACLE_ERR_NOMEM;
+    oracle_assembly keep = {qs, ms, rs, beta, delta, a, b, c, d};
+    int rc = stage_impl(p, hb, qb, mb, rb, hl, ql, ml, rl, tau,
+                        tmp, tmp + n, tmp + 2 * n, tmp + 3 * n, &keep);
+    free(tmp);
+    return rc;
+}
+
+/* ------------------------------------------------------------------------
+ * IMEX Runge-Kutta step of Sec. 3.2 with the double Butcher tableau of eq.
+ * (tableau) (reading R1: two stages, implicit first stage),
+ *   gamma = 1 - 1/sqrt(2),  c = 1/(2 gamma),
+ * written in the efficient form given right after the tableau:
+ *   U_I^(1) = U^n + dt gamma H(U_E^(1), U_I^(1)),           U_E^(1) = U^n
+ *   U_E^(2) = (1 - c/gamma) U^n + (c/gamma) U_I^(1)
+ *   U_I^(2) = (1 - (1-gamma)/gamma) U^n + ((1-gamma)/gamma) U_I^(1)
+ *             + dt gamma H(U_E^(2), U_I^(2)),
+ *   U^{n+1} = U_I^(2) (stiffly accurate).
+ * Each implicit stage is a call S(U_b, U_l, tau = gamma dt) of a stage
+ * operator; the generic driver below is shared by the hSGN step and by the
+ * scalar split test equation.
+ * ------------------------------------------------------------------------ */
+typedef int (*stage_fn)(void* ctx, int64_t len, const double* Ub, const double* Ul,
+                        double tau, double* Uout);
+
+static int imex2_step(void* ctx, stage_fn S, int64_t len, double* U, double dt, double* work) {
+    const double gamma = 1.0 - 1.0 / sqrt(2.0);
+    const double c = 1.0 / (2.0 * gamma);
+    double* U1 = work;
+    double* Ue = work + len;
+    double* Ub = work + 2 * len;
+    int rc = S(ctx, len, U, U, gamma * dt, U1);
+    if (rc != ORACLE_OK) return rc;
+    for (int64_t k = 0; k < len; ++k) {
+        Ue[k] = (1.0 - c / gamma) * U[k] + (c / gamma) * U1[k];
+        Ub[k] = (1.0 - (1.0 - gamma) / gamma) * U[k] + ((1.0 - gamma) / gamma) * U1[k];
+    }
+    return S(ctx, len, Ub, Ue, gamma * dt, U);
+}
+
+/* hSGN stage on a packed state [h | q | m | r] of 4 n values */
+static int hsgn_stage_packed(void* ctx, int64_t len, const double* Ub, const double* Ul,
+                             double tau, double* Uo) {
+    const oracle_params* p = (const oracle_params*)ctx;
+    const int64_t n = p->n;
+    (void)len;
+    return stage_impl(p, Ub, Ub + n, Ub + 2 * n, Ub + 3 * n, Ul, Ul + n, Ul + 2 * n, Ul + 3 * n,
+                      tau, Uo, Uo + n, Uo + 2 * n, Uo + 3 * n, NULL);
+}
+
+/* n_steps IMEX steps of size dt on the state arrays (in place). */
+int oracle_run(const oracle_params* p, double* h, double* q, double* m, double* r,
+               double dt, int64_t n_steps) {
+    if (!p || !h || !q || !m || !r || p->n < 3 || n_steps < 0) return ORACLE_ERR_ARG;
+    const int64_t n = p->n;
+    double* U = (double*)malloc((size_t)(4 * n) * sizeof(double));
+    double* work = (double*)malloc((size_t)(12 * n) * sizeof(double));
+    if (!U || !work) { free(U); free(work); return ORACLE_ERR_NOMEM; }
+    memcpy(U, h, (size_t)n * sizeof(double));
+    memcpy(U + n, q, (size_t)n * sizeof(double));
+    memcpy(U + 2 * n, m, (size_t)n * sizeof(double));
+    memcpy(U + 3 * n, r, (size_t)n * sizeof(double));
+    int rc = ORACLE_OK;
+    oracle_params ps = *p;
+    for (int64_t s = 0; s < n_steps && rc == ORACLE_OK; ++s) {
+        if (ps.rusanov) {
+            /* global Rusanov speed of this step: max over cells of |u^n| */
+            double umax = 0.0;
+            for (int64_t i = 0; i < n; ++i) {
+                if (!(U[i] > 0.0)) return free(U), free(work), ORACLE_ERR_DEPTH;
+                const double u = fabs(U[n + i] / U[i]);
+                if (u > umax) umax = u;
+            }
+            ps.speed = umax;
+        }
+        rc = imex2_step((void*)&ps, hsgn_stage_packed, 4 * n, U, dt, work);
+    }
+    if (rc == ORACLE_OK) {
+        memcpy(h, U, (size_t)n * sizeof(double));
+        memcpy(q, U + n, (size_t)n * sizeof(double));
+        memcpy(m, U + 2 * n, (size_t)n * sizeof(double));
+        memcpy(r, U + 3 * n, (size_t)n * sizeof(double));
+    }
+    free(U); free(work);
+    return rc;
+}
+
+int oracle_step(const oracle_params* p, double* h, double* q, double* m, double* r, double dt) {
+    return oracle_run(p, h, q, m, r, dt, 1);
+}
+
+/* Scalar split linear test equation y' = aE y + aI y: H(y_E, y_I) =
+ * aE y_E + aI y_I, so a stage solves y = y_b + tau (aE y_l + aI y). */
+typedef struct { double aE, aI; } scalar_ctx;
+
+static int scalar_stage(void* ctx, int64_t len, const double* Ub, const double* Ul,
+                        double tau, double* Uo) {
+    const scalar_ctx* s = (const scalar_ctx*)ctx;
+    for (int64_t k = 0; k < len; ++k) {
+        const double den = 1.0 - tau * s->aI;
+        if (!(den != 0.0)) return ORACLE_ERR_COERCIVE;
+        Uo[k] = (Ub[k] + tau * s->aE * Ul[k]) / den;
+    }
+    return ORACLE_OK;
+}
+
+int oracle_imex_scalar(double aE, double aI, double y, double dt, int64_t n_steps, double* out) {
+    if (!out || n_steps < 0) return ORACLE_ERR_ARG;
+    scalar_ctx s = {aE, aI};
+    double U[1] = {y};
+    double work[3];
+    for (int64_t k = 0; k < n_steps; ++k) {
+        int rc = imex2_step(&s, scalar_stage, 1, U, dt, work);
+        if (rc != ORACLE_OK) return rc;
+    }
+    *out = U[0];
+    return ORACLE_OK;
+}
+
+/* ------------------------------------------------------------------------
+ * Time step rule of Sec. 5: dt_bar = CFL dx / nu_max, then the material
+ * condition MCFL = u_max dt / dx must not exceed `mcfl`; otherwise dt =
+ * mcfl dx / u_max. nu = |u| + sqrt(g h + (lambda/3) eta^2/h^2) (reading R9).
+ * Also returns nu_max and u_max.
+ * ------------------------------------------------------------------------ */
+int oracle_suggest_dt(const oracle_params* p, const double* h, const double* q,
+                      const double* m, double cfl, double mcfl,
+                      double* dt_out, double* nu_max_out, double* u_max_out) {
+    if (!p || !h || !q || !m || !dt_out || p->n < 1 || !(cfl > 0.0)) return ORACLE_ERR_ARG;
+    double numax = 0.0, umax = 0.0;
+    for (int64_t i = 0; i < p->n; ++i) {
+        if (!(h[i] > 0.0)) return ORACLE_ERR_DEPTH;
+        const double u = q[i] / h[i];
+        const double eta = m[i] / h[i];
+        const double nu = fabs(u) + sqrt(p->g * h[i] + (p->lambda / 3.0) * sqr(eta / h[i]));
+        if (nu > numax) numax = nu;
+        if (fabs(u) > umax) umax = fabs(u);
+    }
+    double dt = cfl * p->dx / numax;
+    if (mcfl > 0.0 && umax > 0.0 && umax * dt / p->dx > mcfl) dt = mcfl * p->dx / umax;
+    *dt_out = dt;
+    if (nu_max_out) *nu_max_out = numax;
+    if (u_max_out) *u_max_out = umax;
+    return ORACLE_OK;
+}

@@ -1,0 +1,355 @@
+"""Pins of the FP64 CPU oracle against facts the paper and the mathematics fix.
+
+None of these tests uses the CUDA library. Each pin is chosen so that a
+plausible slip in the oracle (a dropped term, a wrong sign, index or factor, a
+transposed operand) fails at least one of them:
+
+* tridiagonal solve   -> dense LU of the same matrix (numpy);
+* IMEX driver         -> stability function written from the unreduced double
+                         Butcher tableau (Sec. 3.2, stage list 1-5), and its
+                         Taylor expansion 1 + z + z^2/2 + O(z^3);
+* assembled matrix    -> row sums 1 (Delta[const] = const), symmetry,
+                         diagonal dominance, beta > 0 (Sec. 3.1 Remark);
+* whole step          -> constant states, exact mass conservation, mirror and
+                         shift symmetry, linear hSGN dispersion relation (with
+                         Doppler shift; lambda = 0 gives sqrt(g h0)), temporal
+                         order 2, solitary-wave convergence trend (Sec. 6.3);
+* time-step rule      -> the CFL_SW numbers printed in Sec. 6.1.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2510_07539_gb300 import inputs
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+G = 9.81
+
+
+def dense(a, b, c, periodic):
+    n = len(b)
+    A = np.zeros((n, n))
+    for i in range(n):
+        A[i, i] += b[i]
+        if i > 0:
+            A[i, i - 1] += a[i]
+        elif periodic:
+            A[i, n - 1] += a[i]
+        if i < n - 1:
+            A[i, i + 1] += c[i]
+        elif periodic:
+            A[i, 0] += c[i]
+    return A
+
+
+# --------------------------------------------------------------------------
+# tridiagonal solve (Thomas; Sherman-Morrison when cyclic)
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("periodic", [False, True])
+@pytest.mark.parametrize("n", [1, 2, 3, 4, 5, 8, 16, 33, 257])
+def test_tridiag_matches_dense(n, periodic):
+    a, b, c, d = inputs.random_tridiag(100 + n, n, periodic)
+    if n == 1:
+        a[:] = c[:] = 0.0 if not periodic else a
+    x = oracle.tridiag_solve(a, b, c, d, periodic)
+    ref = np.linalg.solve(dense(a, b, c, periodic), d)
+    assert np.max(np.abs(x - ref)) <= 1e-13 * max(1.0, np.max(np.abs(ref)))
+
+
+def test_tridiag_nonsymmetric_dominant():
+    rng = np.random.default_rng(7)
+    for periodic in (False, True):
+        n = 40
+        a, c = rng.uniform(-1, 1, n), rng.uniform(-1, 1, n)
+        b = 2.5 + rng.uniform(0, 1, n)
+        d = rng.normal(size=n)
+        x = oracle.tridiag_solve(a, b, c, d, periodic)
+        ref = np.linalg.solve(dense(a, b, c, periodic), d)
+        assert np.allclose(x, ref, rtol=0, atol=1e-13)
+
+
+# --------------------------------------------------------------------------
+# IMEX tableau: scalar split test equation y' = aE y + aI y
+# --------------------------------------------------------------------------
+def tableau_step(zE, zI):
+    """One step of size 1 from y = 1, written from the stage list of Sec. 3.2
+    (not the efficient form): K_i = H(Y_E^(i), Y_I^(i)) = zE Y_E + zI Y_I."""
+    gam = 1.0 - 1.0 / math.sqrt(2.0)
+    c = 1.0 / (2.0 * gam)
+    # stage 1: Y_E1 = 1, Y_I1 = 1 + gam K1
+    K1 = (zE * 1.0 + zI * 1.0) / (1.0 - gam * zI)
+    YE2 = 1.0 + c * K1
+    # stage 2: Y_I2 = 1 + (1-gam) K1 + gam K2, K2 = zE YE2 + zI Y_I2
+    K2 = (zE * YE2 + zI * (1.0 + (1.0 - gam) * K1)) / (1.0 - gam * zI)
+    return 1.0 + (1.0 - gam) * K1 + gam * K2
+
+
+@pytest.mark.parametrize("zE,zI", [(0.3, -2.0), (-0.1, -50.0), (0.0, -1.0), (1.0, 0.0),
+                                   (0.25, -0.25), (-0.7, -1e3)])
+def test_imex_efficient_form_matches_tableau(zE, zI):
+    r = oracle.imex_scalar(zE, zI, 1.0, 1.0, 1)
+    assert abs(r - tableau_step(zE, zI)) <= 1e-14 * max(1.0, abs(r))
+
+
+@pytest.mark.parametrize("split", [0.0, 0.5, 1.0])
+def test_imex_second_order(split):
+    # |R(z) - exp(z)| = O(z^3): the ratio err/z^3 stays bounded as z -> 0
+    ratios = []
+    for z in (1e-1, 5e-2, 2.5e-2):
+        r = oracle.imex_scalar(split * z, (1 - split) * z, 1.0, 1.0, 1)
+        ratios.append(abs(r - math.exp(z)) / z ** 3)
+        assert abs(r - (1 + z + z * z / 2)) <= 0.5 * z ** 3
+    assert max(ratios) < 1.0 and min(ratios) > 1e-4
+
+
+def test_imex_stiff_decay():
+    # the implicit part is L-stable in the stiff limit: R -> small for zI -> -inf
+    assert abs(oracle.imex_scalar(0.0, -1e8, 1.0, 1.0, 1)) < 1e-7
+
+
+# --------------------------------------------------------------------------
+# assembled matrix structure (Sec. 4.2 rows, readings R2, R6)
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("bc", [oracle.BC_PERIODIC, oracle.BC_TRANSMISSIVE])
+def test_assembly_structure(bc):
+    n, dx = 97, 0.1
+    U = inputs.random_state(11, n, dx)
+    p = oracle.Params(n, dx, bc, lam=300.0)
+    A = oracle.assemble(p, U, U, 0.02)
+    a, b, c = A["a"], A["b"], A["c"]
+    assert np.all(A["beta"] > 0)
+    np.testing.assert_allclose(a + b + c, 1.0, rtol=0, atol=1e-13)   # Delta[const] = const
+    if bc == oracle.BC_PERIODIC:
+        np.testing.assert_array_equal(c, np.roll(a, -1))              # symmetric, cyclic
+    else:
+        np.testing.assert_array_equal(c[:-1], a[1:])
+        assert a[0] == 0.0 and c[-1] == 0.0
+    assert np.all(b - np.abs(a) - np.abs(c) > 0.999)                  # strictly dominant
+    assert np.all(a <= 0) and np.all(c <= 0)
+
+
+def test_constant_rhs_identity():
+    # with q, m, r uniform and h uniform the right-hand side is h_b itself
+    n, dx = 40, 0.2
+    h = np.full(n, 1.3)
+    U = (h, 0.4 * h, h * h, np.zeros(n))
+    A = oracle.assemble(oracle.Params(n, dx, 0, lam=50.0), U, U, 0.05)
+    np.testing.assert_allclose(A["d"], 1.3, rtol=0, atol=1e-14)
+
+
+# --------------------------------------------------------------------------
+# whole-step invariants
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("bc", [oracle.BC_PERIODIC, oracle.BC_TRANSMISSIVE])
+@pytest.mark.parametrize("u0", [0.0, 0.7, -0.4])
+def test_constant_state_preserved(bc, u0):
+    n, dx, h0 = 64, 0.1, 0.9
+    h = np.full(n, h0)
+    U = (h, h * u0, h * h, np.zeros(n))
+    lam, dt = 500.0, 0.02
+    V = oracle.run(oracle.Params(n, dx, bc, lam=lam), U, dt, 20)
+    # the relaxation update r = r^dagger - lambda tau m/h^2 subtracts two
+    # numbers of size lambda*tau, so its rounding scales with lambda*dt
+    tol = 1e-14 * 20 * max(1.0, lam * dt)
+    for v, u in zip(V, U):
+        np.testing.assert_allclose(v, u, rtol=0, atol=tol)
+
+
+@pytest.mark.parametrize("lam", [0.0, 100.0, 5000.0])
+def test_mass_conservation(lam):
+    n, dx = 300, 0.1
+    U = inputs.random_state(3, n, dx)
+    p = oracle.Params(n, dx, oracle.BC_PERIODIC, lam=lam)
+    dt, _, _ = oracle.suggest_dt(p, U, 2.0, 0.5)
+    V = oracle.run(p, U, dt, 200)
+    m0, m1 = math.fsum(U[0]), math.fsum(V[0])
+    assert abs(m1 - m0) <= 2e-14 * m0
+    assert np.max(np.abs(V[0] - U[0])) > 1e-4  # the state did evolve
+
+
+@pytest.mark.parametrize("rusanov", [0, 1])
+def test_mirror_symmetry(rusanov):
+    n, dx = 128, 0.1
+    U = inputs.random_state(5, n, dx)
+    p = oracle.Params(n, dx, oracle.BC_PERIODIC, lam=200.0, rusanov=rusanov)
+    V = oracle.run(p, U, 0.02, 10)
+    Um = (U[0][::-1], -U[1][::-1], U[2][::-1], U[3][::-1])
+    Vm = oracle.run(p, Um, 0.02, 10)
+    for k, s in enumerate((1, -1, 1, 1)):
+        np.testing.assert_allclose(Vm[k], s * V[k][::-1], rtol=0, atol=1e-12)
+
+
+def test_mirror_symmetry_transmissive():
+    n, dx = 120, 0.1
+    x, U = inputs.dam_break(n, dx, 1.2, 1.0, 10.0)
+    U = (U[0], 0.1 * np.sin(x), U[2], 0.01 * np.cos(x))
+    p = oracle.Params(n, dx, oracle.BC_TRANSMISSIVE, lam=100.0)
+    V = oracle.run(p, U, 0.02, 10)
+    Vm = oracle.run(p, (U[0][::-1], -U[1][::-1], U[2][::-1], U[3][::-1]), 0.02, 10)
+    for k, s in enumerate((1, -1, 1, 1)):
+        np.testing.assert_allclose(Vm[k], s * V[k][::-1], rtol=0, atol=1e-12)
+
+
+def test_periodic_shift():
+    n, dx, k = 96, 0.1, 17
+    U = inputs.random_state(9, n, dx)
+    p = oracle.Params(n, dx, oracle.BC_PERIODIC, lam=300.0)
+    V = oracle.run(p, U, 0.02, 10)
+    Vs = oracle.run(p, tuple(np.roll(u, k) for u in U), 0.02, 10)
+    for a, b in zip(Vs, V):
+        np.testing.assert_allclose(a, np.roll(b, k), rtol=0, atol=1e-12)
+
+
+# --------------------------------------------------------------------------
+# linear dispersion of hSGN (Sec. 2.2, eq. (hSGN_eq)): linearised about
+# (h0, u0, eta = h0, w = 0), a mode exp(i(kx - wt)) with w' = w - u0 k obeys
+#   w'^2 = k^2 [ g h0 - (lambda/3) w'^2 h0^2 / (lambda - w'^2 h0^2) ],
+# a quadratic in X = w'^2 whose small root is the SGN-like branch (it tends to
+# g h0 k^2 / (1 + k^2 h0^2 / 3) as lambda -> infinity, and to g h0 k^2 at
+# lambda = 0).
+# --------------------------------------------------------------------------
+def slow_branch(k, h0, lam):
+    if lam == 0.0:
+        return math.sqrt(G * h0) * k
+    A = h0 * h0
+    B = -(lam + G * h0 ** 3 * k * k + (lam / 3.0) * k * k * h0 * h0)
+    C = G * h0 * lam * k * k
+    X = (-B - math.sqrt(B * B - 4 * A * C)) / (2 * A)
+    return math.sqrt(X)
+
+
+def measured_omega(n, lam, u0, h0=1.0, length=20.0, cfl=1.0, periods=0.5, delta_half=False,
+                   eps=1e-6):
+    dx = length / n
+    x = (np.arange(n) + 0.5) * dx
+    k = 2 * math.pi / length
+    wp = slow_branch(k, h0, lam)
+    eta_hat = lam * eps / (lam - wp * wp * h0 * h0) if lam > 0 else 0.0
+    th = k * x
+    h = h0 + eps * np.cos(th)
+    u = u0 + (wp * eps / (k * h0)) * np.cos(th)
+    eta = h0 + eta_hat * np.cos(th)
+    w = eta_hat * wp * np.sin(th)
+    U = (h, h * u, h * eta, h * w)
+    p = oracle.Params(n, dx, oracle.BC_PERIODIC, lam=lam, delta_half=delta_half)
+    nu = abs(u0) + math.sqrt(G * h0 + lam / 3.0)
+    T = periods * 2 * math.pi / (wp + u0 * k)
+    steps = max(4, int(math.ceil(T / (cfl * dx / nu))))
+    dt = T / steps
+    phase, prev = 0.0, 0.0
+    V = U
+    for _ in range(steps):
+        V = oracle.step(p, V, dt)
+        z = np.sum((V[0] - h0) * np.exp(-1j * th))
+        ang = -np.angle(z)
+        dphi = (ang - prev + math.pi) % (2 * math.pi) - math.pi
+        phase += dphi
+        prev = ang
+    return phase / T, wp + u0 * k
+
+
+@pytest.mark.parametrize("lam,u0", [(0.0, 0.0), (100.0, 0.0), (1000.0, 0.0), (100.0, 0.5),
+                                    (1000.0, -0.3)])
+def test_linear_dispersion_second_order(lam, u0):
+    errs = []
+    for n in (32, 64, 128):
+        om, exact = measured_omega(n, lam, u0)
+        errs.append(abs(om - exact) / exact)
+    assert errs[-1] < 2e-3
+    assert errs[0] / errs[1] > 3.0 and errs[1] / errs[2] > 3.0, errs
+
+
+def test_dispersion_rejects_literal_half_factor():
+    # reading R3: the literal factor 1/2 with mean delta converges to a wrong
+    # phase speed (or is unstable); the chosen reading converges to the root
+    lam = 1000.0
+    om, exact = measured_omega(128, lam, 0.0)
+    assert abs(om - exact) / exact < 2e-3
+    try:
+        om_lit, _ = measured_omega(128, lam, 0.0, delta_half=True)
+        assert abs(om_lit - exact) / exact > 2e-2
+    except oracle.OracleError:
+        pass
+
+
+# --------------------------------------------------------------------------
+# temporal order at a fixed grid
+# --------------------------------------------------------------------------
+def test_temporal_order_two():
+    n, dx = 128, 0.2
+    U = inputs.random_state(21, n, dx, h_var=0.05, u_amp=0.1)
+    p = oracle.Params(n, dx, oracle.BC_PERIODIC, lam=100.0)
+    T = 0.4
+    ref = oracle.run(p, U, T / 256, 256)
+    errs = []
+    for steps in (8, 16, 32):
+        V = oracle.run(p, U, T / steps, steps)
+        errs.append(max(np.max(np.abs(V[k] - ref[k])) for k in range(4)))
+    r1, r2 = errs[0] / errs[1], errs[1] / errs[2]
+    assert 3.3 < r1 < 4.8 and 3.3 < r2 < 4.8, errs
+
+
+# --------------------------------------------------------------------------
+# solitary wave (Sec. 6.3): trend checks against the SGN closed form
+# --------------------------------------------------------------------------
+def solitary_error(n, lam, T=1.0, amp=0.2, cfl=1.0):
+    L = 100.0
+    x, dx = inputs.cell_centres(n, -50.0, 50.0)
+    U = inputs.solitary(x, 1.0, amp, 0.0, period=L)
+    p = oracle.Params(n, dx, oracle.BC_PERIODIC, lam=lam)
+    dt, _, _ = oracle.suggest_dt(p, U, cfl, 0.5)
+    steps = int(math.ceil(T / dt))
+    V = oracle.run(p, U, T / steps, steps)
+    E = inputs.solitary(x, 1.0, amp, 0.0, t=T, period=L)
+    return np.sum(np.abs(V[0] - E[0])) / np.sum(np.abs(V[0]))  # relative L1 (Sec. 5)
+
+
+def test_solitary_grid_convergence():
+    # second order in dx while the O(1/lambda) gap between hSGN and SGN is small
+    e = [solitary_error(n, 1000.0) for n in (200, 400, 800)]
+    assert e[0] / e[1] > 3.3 and e[1] / e[2] > 3.3, e
+
+
+def test_solitary_error_decreases_with_lambda():
+    # on a fine grid the error is the hSGN-SGN gap, which shrinks as lambda grows
+    e = [solitary_error(3200, lam) for lam in (100.0, 1000.0, 5000.0)]
+    assert e[0] > 4 * e[1] and e[1] > e[2], e
+
+
+# --------------------------------------------------------------------------
+# time-step rule against the numbers printed in Sec. 6.1
+# --------------------------------------------------------------------------
+def test_cfl_ratio_matches_gaussian_bell_table():
+    rows = [l.split() for l in open(os.path.join(GOLDEN, "cfl_gaussian_bell.txt"))
+            if l.strip() and not l.startswith("#")]
+    n = 5000
+    x, dx = inputs.cell_centres(n, -200.0, 200.0)
+    h = 1.0 + np.exp(-x * x / 20.0)
+    U = (h, np.zeros(n), h * h)
+    for lam_s, cfl_sw_s in rows:
+        lam, printed = float(lam_s), float(cfl_sw_s)
+        dt, nu, _ = oracle.suggest_dt(oracle.Params(n, dx, 0, lam=lam), U, 2.0, 0.0)
+        cfl_sw = dt / dx * math.sqrt(G * np.max(h))
+        if lam == 100.0:
+            continue  # misprint, see the fixture header
+        assert abs(cfl_sw - printed) / printed < 0.03, (lam, cfl_sw, printed)
+
+
+# --------------------------------------------------------------------------
+# error reporting
+# --------------------------------------------------------------------------
+def test_errors_reported():
+    n, dx = 16, 0.1
+    h = np.ones(n)
+    bad = h.copy()
+    bad[3] = -0.1
+    with pytest.raises(oracle.OracleError) as e:
+        oracle.step(oracle.Params(n, dx, 0, lam=10.0), (bad, 0 * h, h * h, 0 * h), 0.01)
+    assert e.value.code == 2
+    with pytest.raises(oracle.OracleError):
+        oracle.step(oracle.Params(n, dx, 0, lam=-1.0), (h, 0 * h, h * h, 0 * h), 0.01)
+    with pytest.raises(oracle.OracleError):
+        oracle.step(oracle.Params(2, dx, 0, lam=1.0), (h[:2], 0 * h[:2], h[:2], 0 * h[:2]), 0.01)
