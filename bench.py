@@ -1,0 +1,409 @@
+#!/usr/bin/env python3
+"""Throughput benchmark of the semi-implicit IMEX hSGN step on GB300.
+
+Workload (the dam-break / undular-bore configuration): N = 2^20 cells,
+dx = 0.05, transmissive ends, flat bottom, h = 1.2 on the left and 1.0 on the
+right joined by a tanh transition of width 5 h0 (h0 = 1), u = 0, eta = h,
+w = 0; one instance per relaxation parameter lambda in {10, 100, 1000}, each
+with its own dt = min(4 dx / nu_max, 0.5 dx / u_max) computed at t = 0
+(CFL_IMEX = 4, material CFL 0.5). One benchmark step advances all three
+instances by one IMEX step (two implicit stages each). Inputs are synthetic
+(seed-free closed forms); all arithmetic is FP64.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0). --impl reference times the FP64 CPU oracle on
+the host cores instead (the reference arm of this comparison).
+"""
+from __future__ import annotations
+
+import argparse
+import glob
+import hashlib
+import json
+import math
+import os
+import re
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "hSGN cell-stage updates/sec and % HBM roofline on 1 GB300 at stated L2 error vs FP64 oracle"
+UNIT = "cell-stage updates/s"
+L2_BYTES = 129 * 1024 * 1024
+FLUSH_BYTES = 512 * 1024 * 1024
+
+# Algorithmic traffic of one cell-stage in FP64 (flat bottom): stage 1 reads U^n
+# (32 B) and writes U_I^(1) (32 B); stage 2 reads U^n and U_I^(1) (64 B) and
+# writes U^{n+1} (32 B): 160 B per cell and step = 80 B per cell-stage.
+BYTES_PER_CELL_STAGE = 80.0
+# Algorithmic FP64 operations of the flux + assembly + block elimination kernel
+# per cell and launch (average of the two stages), counted from the kernel's
+# formulas: stage-state combination 12, face reconstruction and Rusanov fluxes
+# 47, starred values and coefficients 42, matrix row and right-hand side 23,
+# chunk Thomas sweep with three right-hand sides and recombination 25
+# (a fused multiply-add counts 2, a division 1).
+FLOPS_PER_CELL_ASSEMBLE = 149.0
+# FP64 peak of a GB300 (nominal, dense): 1.25 TFLOP/s.
+FP64_PEAK_TFLOPS = 1.25
+
+
+def parse_args():
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--log2n", type=int, default=20)
+    ap.add_argument("--lams", default="10,100,1000")
+    ap.add_argument("--cpu-steps", type=int, default=6,
+                    help="oracle steps per instance for the CPU baseline and the L2 check")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------------------
+# workload
+# ---------------------------------------------------------------------------
+def workload(log2n: int, lams):
+    from paper_2510_07539_gb300 import inputs
+    n = 1 << log2n
+    dx = 0.05
+    x, U = inputs.dam_break(n, dx, 1.2, 1.0, 5.0 / dx)
+    return n, dx, -0.5 * n * dx, 0.5 * n * dx, U, [float(l) for l in lams]
+
+
+def config_dict(n, lams, dts, extra=None):
+    d = {
+        "workload": "hSGN dam break / undular bore, 1D, flat bottom, transmissive",
+        "cells": n,
+        "instances": len(lams),
+        "lambda": lams,
+        "dt": dts,
+        "dx": 0.05,
+        "h_left": 1.2,
+        "h_right": 1.0,
+        "transition_width": "5 h0 (tanh)",
+        "cfl_imex": 4.0,
+        "mcfl": 0.5,
+        "scheme": "2-stage IMEX RK (printed tableau), FP64",
+        "rusanov_speed": "global max|u^n|",
+        "l2_between_steps": f"flushed ({FLUSH_BYTES >> 20} MiB write) before every timed step",
+    }
+    if extra:
+        d.update(extra)
+    return d
+
+
+def source_sha() -> str:
+    h = hashlib.sha256()
+    for f in sorted(glob.glob(os.path.join(ROOT, "paper_2510_07539_gb300", "csrc", "*"))):
+        with open(f, "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic_per_cell():
+    """DRAM bytes per cell of the dominant kernel from the committed ncu summary,
+    or None when the kernel sources changed since that capture."""
+    path = os.path.join(ROOT, "profiles", "ncu_stage_assemble.md")
+    if not os.path.exists(path):
+        return None
+    txt = open(path).read()
+    sha = re.search(r"source_sha:\s*([0-9a-f]+)", txt)
+    val = re.search(r"dram_bytes_per_cell_per_launch:\s*([0-9.eE+-]+)", txt)
+    if not sha or not val or sha.group(1) != source_sha():
+        return None
+    return float(val.group(1))
+
+
+# ---------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id: str):
+        self.proc = None
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", gpu_id, f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except Exception:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, mx, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for line in out.strip().splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[3:7]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle (baseline leg and reference arm)
+# ---------------------------------------------------------------------------
+def oracle_steps(n, dx, U, lams, dts, steps):
+    import oracle
+    oracle.build()
+    out, t0 = [], time.perf_counter()
+    for lam, dt in zip(lams, dts):
+        p = oracle.Params(n, dx, oracle.BC_TRANSMISSIVE, lam=lam)
+        out.append(oracle.run(p, U, dt, steps))
+    return out, time.perf_counter() - t0
+
+
+def cpu_dts(n, dx, U, lams):
+    import oracle
+    return [oracle.suggest_dt(oracle.Params(n, dx, oracle.BC_TRANSMISSIVE, lam=l), U, 4.0, 0.5)[0]
+            for l in lams]
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    lams = [float(x) for x in args.lams.split(",")]
+    n, dx, _, _, U, lams = workload(args.log2n, lams)
+    dts = cpu_dts(n, dx, U, lams)
+    import oracle
+    oracle.build()
+    params = [oracle.Params(n, dx, oracle.BC_TRANSMISSIVE, lam=l) for l in lams]
+    states = [U for _ in lams]
+    for _ in range(args.warmup):
+        states = [oracle.run(p, s, dt, 1) for p, s, dt in zip(params, states, dts)]
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        states = [oracle.run(p, s, dt, 1) for p, s, dt in zip(params, states, dts)]
+    el = time.perf_counter() - t0
+    units = 2.0 * n * len(lams) * args.steps
+    value = units / el
+    sample = (f"{args.steps} full IMEX steps of all {len(lams)} instances "
+              f"({n} cells each), single-threaded C oracle")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": config_dict(n, lams, dts),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA GPU (the CPU oracle arm is --impl reference)")
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+
+    from paper_2510_07539_gb300 import build
+    if rank == 0:
+        build.build()
+    if dist:
+        dist.barrier()
+    from paper_2510_07539_gb300 import solver as S
+
+    lams = [float(x) for x in args.lams.split(",")]
+    n, dx, xl, xr, U, lams = workload(args.log2n, lams)
+    Ud = [torch.tensor(u, device="cuda") for u in U]
+    sols = [S.Solver(n, xl, xr, S.BC_TRANSMISSIVE, lam=l) for l in lams]
+    for s in sols:
+        s.set_state(*Ud)
+    dts = [s.suggest_dt(4.0, 0.5) for s in sols]
+    flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def one_step():
+        for s, dt in zip(sols, dts):
+            s.step(dt)
+
+    for _ in range(args.warmup):
+        one_step()
+    for s in sols:
+        s.check()
+    torch.cuda.synchronize()
+
+    props = torch.cuda.get_device_properties(local)
+    gpu_id = str(getattr(props, "uuid", local))
+    if gpu_id and not gpu_id.startswith("GPU-") and len(gpu_id) >= 32:
+        gpu_id = "GPU-" + gpu_id
+    for s in sols:
+        s.profile(True)
+        s.profile_read(reset=True)
+    ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    sampler = ClockSampler(gpu_id)
+    time.sleep(0.3)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    for k in range(args.steps):
+        flush.fill_(float(k))
+        ev0[k].record(stream)
+        one_step()
+        ev1[k].record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clocks = sampler.stop()
+    for s in sols:
+        s.check()
+    ms = sum(a.elapsed_time(b) for a, b in zip(ev0, ev1))
+    prof = [s.profile_read(reset=True) for s in sols]
+    for s in sols:
+        s.profile(False)
+    if dist:
+        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+
+    units_rank = 2.0 * n * len(lams) * args.steps
+    value = units_rank * world / (ms / 1e3)
+    asm_ms = sum(p["assemble"][0] for p in prof)
+    asm_n = sum(p["assemble"][1] for p in prof)
+    red_ms = sum(p["reduced"][0] for p in prof)
+    bs_ms = sum(p["backsub"][0] for p in prof)
+    avg_asm = asm_ms / max(asm_n, 1)
+    achieved_tf = FLOPS_PER_CELL_ASSEMBLE * n / (avg_asm / 1e3) / 1e12
+    tpc = profiled_traffic_per_cell()
+    hbm_gbs = BYTES_PER_CELL_STAGE * units_rank / (ms / 1e3) / 1e9
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
+    roofline = {
+        "bound": "alu",
+        "kernel": "k_stage_assemble (fluxes + assembly + block elimination)",
+        "achieved": achieved_tf, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+        "frac": achieved_tf / FP64_PEAK_TFLOPS,
+        "peak_source": "nominal dense FP64 of GB300 (1.25 TFLOP/s)",
+        "traffic": tpc * n if tpc is not None else None,
+        "kernel_avg_ms": avg_asm,
+        "kernel_share": {"assemble": asm_ms / (asm_ms + red_ms + bs_ms),
+                         "reduced": red_ms / (asm_ms + red_ms + bs_ms),
+                         "backsub": bs_ms / (asm_ms + red_ms + bs_ms)},
+        "hbm_effective_gbs": hbm_gbs,
+        "hbm_frac_of_measured": hbm_gbs / hbm_peak,
+    }
+
+    # ---- end to end through the C ABI with host buffers
+    e2e = None
+    if not args.no_e2e:
+        host_in = [[torch.tensor(u).pin_memory() for u in U] for _ in lams]
+        host_out = [[torch.empty(n, dtype=torch.float64).pin_memory() for _ in range(4)]
+                    for _ in lams]
+        k_e2e = max(1, min(args.steps, 20))
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(k_e2e):
+            for s, dt, hi, ho in zip(sols, dts, host_in, host_out):
+                s.set_state(*hi)
+                s.step(dt)
+                s.get_state(out=ho)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ems = e0.elapsed_time(e1)
+        if dist:
+            t = torch.tensor([ems], device="cuda", dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ems = float(t.item())
+        nbytes = 4 * n * 8 * len(lams)
+        e2e = {"value": 2.0 * n * len(lams) * k_e2e * world / (ems / 1e3), "unit": UNIT,
+               "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes, "steps": k_e2e}
+
+    # ---- CPU oracle baseline and L2 error of the GPU path against it
+    cpu = None
+    l2err = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        ks = max(1, args.cpu_steps)
+        refs, el = oracle_steps(n, dx, U, lams, dts, ks)
+        cpu = {"value": 2.0 * n * len(lams) * ks / el, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"{ks} IMEX steps of each of the {len(lams)} instances ({n} cells), "
+                         f"single-threaded C oracle, {el:.1f} s"}
+        errs = []
+        for s, dt, ref in zip(sols, dts, refs):
+            s.set_state(*Ud)
+            s.run(dt, ks)
+            got = [t.cpu().numpy() for t in s.get_state()]
+            for k in range(4):
+                nr = np.linalg.norm(ref[k])
+                if nr > 0:
+                    errs.append(float(np.linalg.norm(got[k] - ref[k]) / nr))
+        l2err = max(errs)
+    for s in sols:
+        s.close()
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": config_dict(n, lams, dts, {"parallelism": f"{world} independent replicas"}),
+            "l2_rel_err_vs_oracle": l2err,
+            "l2_err_steps": args.cpu_steps if l2err is not None else None,
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
+            "gpu_launches": 6 * len(lams) * args.steps,
+        }
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

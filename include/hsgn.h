@@ -1,0 +1,169 @@
+/*
+ * hsgn.h -- C ABI of the GB300 (sm_103a) library for the semi-implicit IMEX
+ * time step of the hyperbolic Serre-Green-Naghdi (hSGN) equations in 1D.
+ *
+ * Method: E. Macca, W. Boscheri, M. Ricchiuto, "Semi-implicit strategies for
+ * the Serre-Green-Naghdi equations in hyperbolic form" (arXiv 2510.07539).
+ * The state of an instance is U = (h, q = h u, m = h eta, r = h w) on a
+ * uniform grid of n cells (Sec. 2.2, eq. (hSGN_eq)); one step is the two-stage
+ * IMEX Runge-Kutta scheme of Sec. 3.2 (eq. (tableau), efficient form), each
+ * stage being the fully-discrete semi-implicit update of Sec. 4.2 (eq.
+ * (GN_hyp_eq_semi_fully_discrete)): explicit Rusanov fluxes with linear
+ * reconstruction (Sec. 4.1), a symmetric tridiagonal system for the depth
+ * (cyclic when periodic), and the back-substitution for q, h eta, h w.
+ *
+ * Conventions shared by every entry point:
+ *  - Return value: HSGN_OK (0) or one of the HSGN_ERR_* codes below. No entry
+ *    point throws, aborts or prints.
+ *  - Arrays are contiguous FP64 with n elements, 8-byte aligned. Unless a
+ *    description says otherwise a pointer may address device memory, pinned
+ *    host memory or pageable host memory (copies use cudaMemcpyDefault).
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream). Work is enqueued on it; functions that say "synchronises"
+ *    wait for the stream before returning.
+ *  - Errors found on the device (non-positive depth, beta <= 0 or a
+ *    non-positive pivot, non-finite values) are accumulated in a device error
+ *    word and reported by the next synchronising call (hsgn_run, hsgn_check,
+ *    hsgn_get_state), which also clears the word. After such an error the
+ *    state is undefined until the next hsgn_set_state.
+ *  - No call is thread-safe on one handle; distinct handles are independent.
+ */
+#ifndef HSGN_H
+#define HSGN_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+    HSGN_OK = 0,
+    HSGN_ERR_INVALID_ARG = 1,       /* bad size, pointer, flag or parameter */
+    HSGN_ERR_CUDA = 2,              /* a CUDA runtime call failed */
+    HSGN_ERR_NONPOSITIVE_DEPTH = 3, /* a depth used as a divisor was <= 0 */
+    HSGN_ERR_NOT_COERCIVE = 4,      /* beta <= 0 or a non-positive pivot */
+    HSGN_ERR_NONFINITE = 5,         /* NaN or Inf produced */
+    HSGN_ERR_UNIMPLEMENTED = 6,     /* entry point or flag not built yet */
+    HSGN_ERR_OUT_OF_MEMORY = 7
+};
+
+/* boundary conditions (reading of the paper, which states none):
+ * periodic = indices wrap, cyclic matrix; transmissive = zero-order ghost
+ * copies of every per-cell quantity, Neumann end rows. */
+#define HSGN_BC_PERIODIC 0
+#define HSGN_BC_TRANSMISSIVE 1
+
+/* flags of hsgn_create */
+#define HSGN_FP64 0x0          /* every operation in FP64 */
+#define HSGN_RUSANOV_LOCAL 0x10 /* Rusanov speed max(|u^L|,|u^R|) per face instead
+                                 * of the global max |u^n| of the step */
+
+typedef struct {
+    int64_t n;       /* number of cells, n >= 3 */
+    double x_left;   /* domain [x_left, x_right], dx = (x_right - x_left)/n */
+    double x_right;
+    int32_t bc;      /* HSGN_BC_PERIODIC or HSGN_BC_TRANSMISSIVE */
+    int32_t reserved; /* must be 0 */
+} hsgn_grid_t;
+
+typedef struct hsgn_s* hsgn_handle_t;
+
+/* Create an instance: grid, gravity g > 0, relaxation parameter lambda >= 0
+ * (Sec. 2.2, eq. (hSGN_eq)). `bathymetry` must be NULL (flat bottom; the
+ * paper derives the semi-implicit scheme only for a flat bottom). Allocates
+ * the state and workspace on the current device (about 17 doubles per cell).
+ * On success *out owns them until hsgn_destroy. */
+int hsgn_create(const hsgn_grid_t* grid, double g, double lambda, const double* bathymetry,
+                int32_t flags, hsgn_handle_t* out);
+
+/* Copy a state in (U = (h, q, h eta, h w), n values each) and recompute the
+ * global Rusanov speed. The caller keeps ownership of the arrays. Does not
+ * synchronise; the arrays must stay valid until the stream reaches the copy. */
+int hsgn_set_state(hsgn_handle_t h, const double* depth, const double* q, const double* heta,
+                   const double* hw, void* stream);
+
+/* Copy the state out. Synchronises and reports pending device errors. */
+int hsgn_get_state(hsgn_handle_t h, double* depth, double* q, double* heta, double* hw,
+                   void* stream);
+
+/* One IMEX step of size dt > 0 (Sec. 3.2): two implicit stages with
+ * tau = gamma dt, gamma = 1 - 1/sqrt(2). Enqueues six kernels; does not
+ * synchronise. */
+int hsgn_step(hsgn_handle_t h, double dt, void* stream);
+
+/* n_steps >= 0 steps of size dt: one step is captured once per dt into a CUDA
+ * graph and replayed. Synchronises and reports pending device errors. */
+int hsgn_run(hsgn_handle_t h, double dt, int64_t n_steps, void* stream);
+
+/* Enqueue n_steps >= 0 steps as CUDA-graph replays (same graph as hsgn_run)
+ * without synchronising; errors surface at the next synchronising call. */
+int hsgn_enqueue(hsgn_handle_t h, double dt, int64_t n_steps, void* stream);
+
+/* Per-kernel timing. While enabled, hsgn_step and hsgn_stage record a CUDA
+ * event pair around each kernel launch on the launch stream (graph replays are
+ * not timed). hsgn_profile_read waits for the recorded events, adds their
+ * elapsed times to ms[kind] and their count to launches[kind] for the
+ * HSGN_PROF_KINDS kinds below (either pointer may be NULL), and clears the
+ * record when `reset` is non-zero. */
+#define HSGN_PROF_ASSEMBLE 0 /* flux + assembly + block elimination kernel */
+#define HSGN_PROF_REDUCED 1  /* separator-system solve */
+#define HSGN_PROF_BACKSUB 2  /* back-substitution kernel */
+#define HSGN_PROF_KINDS 3
+int hsgn_profile(hsgn_handle_t h, int32_t enable);
+int hsgn_profile_read(hsgn_handle_t h, double* ms, int64_t* launches, int32_t reset);
+
+/* Synchronise the stream and report (and clear) pending device errors. */
+int hsgn_check(hsgn_handle_t h, void* stream);
+
+/* Time-step rule of Sec. 5 on the current state: dt = cfl dx / nu_max with
+ * nu = |u| + sqrt(g h + (lambda/3) eta^2/h^2); if u_max dt / dx > mcfl then
+ * dt = mcfl dx / u_max (mcfl <= 0 disables that test). Synchronises. */
+int hsgn_suggest_dt(hsgn_handle_t h, double cfl, double mcfl, double* dt_out, void* stream);
+
+/* One implicit stage S(U_b, U_l, tau) of Sec. 4.2 on caller arrays: base
+ * state `base` (the additive old values), linearisation state `lin` (fluxes
+ * and coefficients), stage step tau > 0, and Rusanov speed `speed` (ignored
+ * with HSGN_RUSANOV_LOCAL). base, lin, out: 4 device pointers each (h, q, m, r),
+ * out must not alias base or lin. Uses the handle's grid, parameters and
+ * workspace; does not touch its state. Does not synchronise. */
+int hsgn_stage(hsgn_handle_t h, const double* const base[4], const double* const lin[4],
+               double tau, double speed, double* const out[4], void* stream);
+
+/* Discrete adjoint of hsgn_run (gradient of a gauge misfit with respect to
+ * the initial depth). Not built: returns HSGN_ERR_UNIMPLEMENTED. */
+int hsgn_adjoint(hsgn_handle_t h, double dt, int64_t n_steps, int64_t n_gauges,
+                 const int64_t* gauge_cells, const double* gauge_data, double* grad_h0,
+                 double* misfit, void* stream);
+
+/* Release everything owned by the handle (NULL is accepted). */
+void hsgn_destroy(hsgn_handle_t h);
+
+/* Static, NUL-terminated description of an error code. */
+const char* hsgn_error_string(int code);
+
+/* ---------------------------------------------------------------------------
+ * Tridiagonal component (the depth solve of Sec. 4.2, Delta[hbar] = h^dagger)
+ * ------------------------------------------------------------------------- */
+
+/* Bytes of device workspace hsgn_tridiag_solve needs for n rows. */
+int hsgn_tridiag_workspace_bytes(int64_t n, size_t* bytes);
+
+/* Solve a[i] x[i-1] + b[i] x[i] + c[i] x[i+1] = d[i], i = 0..n-1, n >= 1.
+ * periodic != 0: a[0] couples x[n-1] and c[n-1] couples x[0] (cyclic);
+ * periodic == 0: a[0] and c[n-1] are ignored. a, b, c, d, x: device pointers;
+ * x may alias d. The matrix must be an M-matrix-like, diagonally dominant
+ * system (the hSGN depth matrix is); no pivoting is done. A non-positive pivot
+ * is reported as HSGN_ERR_NOT_COERCIVE. `workspace` (device, 256-byte aligned,
+ * at least hsgn_tridiag_workspace_bytes) is caller-owned scratch.
+ * Synchronises and reports device errors. */
+int hsgn_tridiag_solve(int64_t n, int32_t periodic, const double* a, const double* b,
+                       const double* c, const double* d, double* x, void* workspace,
+                       size_t workspace_bytes, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HSGN_H */

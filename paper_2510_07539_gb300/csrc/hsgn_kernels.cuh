@@ -1,0 +1,518 @@
+// hsgn_kernels.cuh -- CUDA kernels of one semi-implicit IMEX stage (sm_103a).
+//
+// Paper: Macca, Boscheri, Ricchiuto, arXiv 2510.07539.
+//   stage update:  Sec. 4.2, eq. (GN_hyp_eq_semi_fully_discrete)
+//   fluxes:        Sec. 4.1 (Rusanov flux hat D_x, centred linear reconstruction)
+//   coefficients:  eqs. (eq:hSGN_alpha), (eq:b1), (eq:hnew)
+//   stage states:  Sec. 3.2, eq. (tableau) in its efficient form
+//
+// One stage is three launches:
+//   k_stage_assemble  one CTA per block of rows: loads the two stage inputs
+//                     with a 3-cell halo, forms U_l and U_b on load, computes
+//                     face fluxes, starred values, coefficients and matrix rows
+//                     in shared memory, and eliminates the block (separator
+//                     method, hsgn_tridiag.cuh). Stores per row (y, v, w) and
+//                     the back-substitution inputs; per block a summary row.
+//   k_reduced_cyclic  one CTA: the cyclic system of the block separators.
+//   k_backsub         one thread per cell: hbar = y - s_L v - s_R w, then
+//                     qbar, (h eta)bar, (h w)bar.
+#pragma once
+
+#include <cstdint>
+
+#include "hsgn_tridiag.cuh"
+
+namespace hsgn {
+
+constexpr int BC_PERIODIC = 0;
+constexpr int BC_TRANSMISSIVE = 1;
+
+// Number of doubles in a block summary: separator row (a, b, c, d), then the
+// triples of the first row (F) and of the last interior row (L).
+constexpr int BLK_STRIDE = 10;
+
+__device__ __forceinline__ int64_t wrap_index(int64_t i, int64_t n, int bc) {
+    if (bc == BC_PERIODIC) {
+        int64_t k = i % n;
+        return k < 0 ? k + n : k;
+    }
+    return i < 0 ? 0 : (i >= n ? n - 1 : i);
+}
+
+// Even split of n rows into P blocks: block b starts at b*base + min(b, rem)
+// and has base + (b < rem) rows.
+struct BlockSplit {
+    int64_t n, base;
+    int32_t P, rem;
+    __host__ __device__ int64_t start(int64_t b) const { return b * base + (b < rem ? b : rem); }
+    __host__ __device__ int64_t size(int64_t b) const { return base + (b < rem ? 1 : 0); }
+    __host__ __device__ int64_t block_of(int64_t i) const {
+        const int64_t big = (int64_t)rem * (base + 1);
+        return i < big ? i / (base + 1) : rem + (i - big) / base;
+    }
+};
+
+struct StageParams {
+    int64_t n;
+    int32_t bc;
+    int32_t local_speed;  // 1: Rusanov speed max(|u^L|,|u^R|); 0: global *speed
+    double dx, g, lam, tau;
+    const double* A[4];  // first input state (h, q, m, r)
+    const double* B[4];  // second input state, may be null when wl1 == wb1 == 0
+    double wl0, wl1;     // U_l = wl0 A + wl1 B   (linearisation state)
+    double wb0, wb1;     // U_b = wb0 A + wb1 B   (base state)
+    const double* speed; // device scalar: global Rusanov speed of the step
+    BlockSplit split;
+    // per-row outputs
+    double *y, *v, *w;
+    double *qs, *ms, *rs, *be, *de;
+    double* blk;          // P * BLK_STRIDE
+    unsigned* err;
+};
+
+// Shared memory of k_stage_assemble for blocks of at most S = T*M rows.
+template <int T, int M>
+struct AssembleShared {
+    static constexpr int S = T * M;
+    double hl[S + 6], ql[S + 6], ml[S + 6], rl[S + 6];  // U_l, cells -3 .. S+2
+    double hb[S + 6], qb[S + 6], mb[S + 6], rb[S + 6];  // U_b, same indexing
+    double Fq[S + 3], Fm[S + 3], Fr[S + 3];             // faces -2 .. S
+    double qs[S + 2], ms[S + 2], rs[S + 2], be[S + 2], de[S + 2];  // cells -1 .. S
+    SepShared<T> sep;
+    double lastrow[4];
+};
+
+template <int T, int M, int BC>
+__global__ void __launch_bounds__(T) k_stage_assemble(const StageParams p) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    auto& sm = *reinterpret_cast<AssembleShared<T, M>*>(smem_raw);
+    const int tid = threadIdx.x;
+    const int64_t b = blockIdx.x;
+    const int64_t r0 = p.split.start(b);
+    const int nb = (int)p.split.size(b);
+    const int64_t n = p.n;
+    const bool two = (p.B[0] != nullptr);
+
+    // ---- 0. stage inputs with a 3-cell halo; U_l and U_b formed on load
+    for (int j = tid; j < nb + 6; j += T) {
+        const int64_t gi = wrap_index(r0 + j - 3, n, BC);
+        const double ah = p.A[0][gi], aq = p.A[1][gi], am = p.A[2][gi], ar = p.A[3][gi];
+        if (two) {
+            const double bh = p.B[0][gi], bq = p.B[1][gi], bm = p.B[2][gi], br = p.B[3][gi];
+            sm.hl[j] = p.wl0 * ah + p.wl1 * bh;
+            sm.ql[j] = p.wl0 * aq + p.wl1 * bq;
+            sm.ml[j] = p.wl0 * am + p.wl1 * bm;
+            sm.rl[j] = p.wl0 * ar + p.wl1 * br;
+            sm.hb[j] = p.wb0 * ah + p.wb1 * bh;
+            sm.qb[j] = p.wb0 * aq + p.wb1 * bq;
+            sm.mb[j] = p.wb0 * am + p.wb1 * bm;
+            sm.rb[j] = p.wb0 * ar + p.wb1 * br;
+        } else {
+            sm.hl[j] = ah; sm.ql[j] = aq; sm.ml[j] = am; sm.rl[j] = ar;
+            sm.hb[j] = ah; sm.qb[j] = aq; sm.mb[j] = am; sm.rb[j] = ar;
+        }
+    }
+    __syncthreads();
+
+    const double dx = p.dx, tau = p.tau, lam = p.lam, g = p.g;
+    const double gspeed = p.local_speed ? 0.0 : *p.speed;
+    unsigned bad = 0;
+
+    // ---- 1. Rusanov fluxes at faces f = -2 .. nb (face f between cells f, f+1),
+    //         centred unlimited reconstruction of the conserved variables of U_l.
+    for (int j = tid; j < nb + 3; j += T) {
+        const int c = j;  // face f = j-2; its stencil cells f-1 .. f+2 sit at smem j .. j+3
+        const double hm = sm.hl[c], h0 = sm.hl[c + 1], h1 = sm.hl[c + 2], h2 = sm.hl[c + 3];
+        const double qm = sm.ql[c], q0 = sm.ql[c + 1], q1 = sm.ql[c + 2], q2 = sm.ql[c + 3];
+        const double mm = sm.ml[c], m0 = sm.ml[c + 1], m1 = sm.ml[c + 2], m2 = sm.ml[c + 3];
+        const double rm = sm.rl[c], r0_ = sm.rl[c + 1], r1 = sm.rl[c + 2], r2 = sm.rl[c + 3];
+        const double hL = fma(0.25, h1 - hm, h0), hR = fma(-0.25, h2 - h0, h1);
+        const double qL = fma(0.25, q1 - qm, q0), qR = fma(-0.25, q2 - q0, q1);
+        const double mL = fma(0.25, m1 - mm, m0), mR = fma(-0.25, m2 - m0, m1);
+        const double rL = fma(0.25, r1 - rm, r0_), rR = fma(-0.25, r2 - r0_, r1);
+        if (!(hL > 0.0) || !(hR > 0.0)) bad |= HSGN_DEV_ERR_DEPTH;
+        const double uL = qL / hL, uR = qR / hR;
+        const double s = p.local_speed ? fmax(fabs(uL), fabs(uR)) : gspeed;
+        sm.Fq[j] = 0.5 * (fma(uL, qL, uR * qR) - s * (qR - qL));
+        sm.Fm[j] = 0.5 * (fma(uL, mL, uR * mR) - s * (mR - mL));
+        sm.Fr[j] = 0.5 * (fma(uL, rL, uR * rR) - s * (rR - rL));
+    }
+    __syncthreads();
+
+    // ---- 2. starred values and coefficients at cells c = -1 .. nb
+    const double lt2 = lam * tau * tau;
+    const double tdx = tau / dx;
+    for (int j = tid; j < nb + 2; j += T) {
+        const int c3 = j + 2;  // smem index of cell c = j-1 in the U arrays
+        const double rsv = fma(-tdx, sm.Fr[j + 1] - sm.Fr[j], sm.rb[c3]) + lam * tau;
+        const double msv = fma(tau, rsv, fma(-tdx, sm.Fm[j + 1] - sm.Fm[j], sm.mb[c3]));
+        const double qsv = fma(-tdx, sm.Fq[j + 1] - sm.Fq[j], sm.qb[c3]);
+        const double h = sm.hl[c3];
+        if (!(h > 0.0)) bad |= HSGN_DEV_ERR_DEPTH;
+        const double ih = 1.0 / h;
+        const double eta = sm.ml[c3] * ih;
+        const double e = eta * ih;
+        const double alpha = -(2.0 * e - 1.0) * ih * (1.0 / 3.0);
+        const double c2 = fma(g, h, (lam * (1.0 / 3.0)) * e * e);
+        const double a2 = fma(-lam * eta, alpha, c2);
+        const double ih2 = ih * ih;
+        const double beta1 = fma(lt2, ih2, 1.0);
+        const double ib1 = 1.0 / beta1;
+        const double beta2 = 2.0 * lt2 * ib1 * ib1 * ih2 * ih;
+        const double beta = fma(lam * alpha * beta2, msv, a2);
+        if (!(beta > 0.0)) bad |= HSGN_DEV_ERR_COERCIVE;
+        sm.qs[j] = qsv;
+        sm.ms[j] = msv;
+        sm.rs[j] = rsv;
+        sm.be[j] = beta;
+        sm.de[j] = alpha * ib1;
+    }
+    __syncthreads();
+    if (BC == BC_TRANSMISSIVE && tid == 0) {
+        // zero-order ghost copies of the per-cell quantities at the domain ends
+        if (r0 == 0) {
+            sm.qs[0] = sm.qs[1]; sm.ms[0] = sm.ms[1]; sm.rs[0] = sm.rs[1];
+            sm.be[0] = sm.be[1]; sm.de[0] = sm.de[1];
+        }
+        if (r0 + nb == n) {
+            sm.qs[nb + 1] = sm.qs[nb]; sm.ms[nb + 1] = sm.ms[nb]; sm.rs[nb + 1] = sm.rs[nb];
+            sm.be[nb + 1] = sm.be[nb]; sm.de[nb + 1] = sm.de[nb];
+        }
+    }
+    __syncthreads();
+
+    // back-substitution inputs of the block's own rows
+    for (int i = tid; i < nb; i += T) {
+        const int64_t gi = r0 + i;
+        p.qs[gi] = sm.qs[i + 1];
+        p.ms[gi] = sm.ms[i + 1];
+        p.rs[gi] = sm.rs[i + 1];
+        p.be[gi] = sm.be[i + 1];
+        p.de[gi] = sm.de[i + 1];
+    }
+
+    // ---- 3. rows of Delta[hbar] = h^dagger and the block elimination
+    const double Cc = tau * tau / (dx * dx);
+    const double fq = tau / (2.0 * dx);
+    const double fd = lam * tau * tau / (dx * dx);
+    auto row = [&](int i, double& a, double& bb, double& c, double& d) {
+        const double bm = 0.5 * (sm.be[i] + sm.be[i + 1]);
+        const double bp = 0.5 * (sm.be[i + 1] + sm.be[i + 2]);
+        const double dm = 0.5 * (sm.de[i] + sm.de[i + 1]);
+        const double dp = 0.5 * (sm.de[i + 1] + sm.de[i + 2]);
+        const double msc = sm.ms[i + 1];
+        d = fma(-fq, sm.qs[i + 2] - sm.qs[i], sm.hb[i + 3]) +
+            fd * (dp * (sm.ms[i + 2] - msc) - dm * (msc - sm.ms[i]));
+        a = -Cc * bm;
+        c = -Cc * bp;
+        bb = fma(Cc, bm + bp, 1.0);
+        if (BC == BC_TRANSMISSIVE) {
+            const int64_t gi = r0 + i;
+            if (gi == 0) { bb = fma(Cc, bp, 1.0); a = 0.0; }
+            if (gi == n - 1) { bb = fma(Cc, bm, 1.0); c = 0.0; }
+        }
+    };
+    double y[M], v[M], w[M], last[4];
+    int cs, m;
+    cta_block_solve<T, M>(nb, row, sm.sep, y, v, w, cs, m, last, p.err);
+    if (bad) flag_error(p.err, bad);
+
+    // ---- 4. stage (y, v, w) through shared memory for coalesced stores
+    __syncthreads();  // the row function no longer reads the U_l arrays
+#pragma unroll
+    for (int k = 0; k < M; ++k) {
+        if (k < m) {
+            sm.hl[cs + k] = y[k];
+            sm.ql[cs + k] = v[k];
+            sm.ml[cs + k] = w[k];
+        }
+    }
+    if (m > 0 && cs + m == nb) {
+        sm.lastrow[0] = last[0]; sm.lastrow[1] = last[1];
+        sm.lastrow[2] = last[2]; sm.lastrow[3] = last[3];
+    }
+    __syncthreads();
+    for (int i = tid; i < nb; i += T) {
+        p.y[r0 + i] = sm.hl[i];
+        p.v[r0 + i] = sm.ql[i];
+        p.w[r0 + i] = sm.ml[i];
+    }
+    if (tid == 0) {
+        double* s = p.blk + b * BLK_STRIDE;
+        s[0] = sm.lastrow[0]; s[1] = sm.lastrow[1]; s[2] = sm.lastrow[2]; s[3] = sm.lastrow[3];
+        s[4] = sm.hl[0]; s[5] = sm.ql[0]; s[6] = sm.ml[0];
+        if (nb >= 2) {
+            s[7] = sm.hl[nb - 2]; s[8] = sm.ql[nb - 2]; s[9] = sm.ml[nb - 2];
+        } else {
+            s[7] = 0.0; s[8] = -1.0; s[9] = 0.0;
+        }
+    }
+}
+
+// Row source of the block-separator system: row b couples s_{b-1}, s_b, s_{b+1}
+// (cyclic in b). With x_{sep-1} = y_L - s_{b-1} v_L - s_b w_L (last interior
+// row of block b) and x_{sep+1} = y_F - s_b v_F - s_{b+1} w_F (first row of
+// block b+1), the separator row a x_{sep-1} + b x_sep + c x_{sep+1} = d gives
+//   (-a v_L) s_{b-1} + (b - a w_L - c v_F) s_b + (-c w_F) s_{b+1} = d - a y_L - c y_F.
+struct BlkRows {
+    const double* blk;
+    int P;
+    __device__ void operator()(int i, double& A, double& B, double& C, double& D) const {
+        const double* s = blk + (int64_t)i * BLK_STRIDE;
+        const double* f = blk + (int64_t)(i + 1 == P ? 0 : i + 1) * BLK_STRIDE;
+        const double a = s[0], bb = s[1], c = s[2], d = s[3];
+        A = -a * s[8];
+        B = bb - a * s[9] - c * f[5];
+        C = -c * f[6];
+        D = d - a * s[7] - c * f[4];
+    }
+};
+
+// Row source reading explicit arrays (cyclic: a[0] couples x[n-1], c[n-1] couples x[0]).
+struct ArrayRows {
+    const double *a, *b, *c, *d;
+    int64_t off;
+    int periodic;
+    int64_t n;  // total rows of the system
+    __device__ void operator()(int i, double& A, double& B, double& C, double& D) const {
+        const int64_t k = off + i;
+        A = a[k];
+        B = b[k];
+        C = c[k];
+        D = d[k];
+        if (!periodic) {
+            if (k == 0) A = 0.0;
+            if (k == n - 1) C = 0.0;
+        }
+    }
+};
+
+// Cyclic tridiagonal system of `nrows` rows in one CTA. The last row's unknown
+// x_{n-1} is the external unknown on BOTH sides of rows 0 .. n-2 (the cyclic
+// couplings a_0 and c_{n-2}), so x_i = y_i - x_{n-1} (v_i + w_i), and the last
+// row a x_{n-2} + b x_{n-1} + c x_0 = d closes it.
+template <int T, int M>
+struct CyclicShared {
+    SepShared<T> sep;
+    double y0, z0, yq, zq, last[4], xlast;
+};
+
+template <int T, int M, class RowSrc>
+__global__ void __launch_bounds__(T) k_cyclic_onecta(int nrows, RowSrc rows, double* x,
+                                                     double* speed_reset, unsigned* err) {
+    __shared__ CyclicShared<T, M> sh;
+    const int t = threadIdx.x;
+    if (speed_reset && t == 0) *speed_reset = 0.0;
+    if (nrows == 1) {
+        if (t == 0) {
+            double A, B, C, D;
+            rows(0, A, B, C, D);
+            const double den = A + B + C;
+            if (!(den > 0.0)) flag_error(err, HSGN_DEV_ERR_COERCIVE);
+            x[0] = D / den;
+        }
+        return;
+    }
+    double y[M], v[M], w[M], last[4];
+    int cs, m;
+    cta_block_solve<T, M>(nrows, rows, sh.sep, y, v, w, cs, m, last, err);
+#pragma unroll
+    for (int k = 0; k < M; ++k) {
+        if (k < m) {
+            const int i = cs + k;
+            if (i == 0) { sh.y0 = y[k]; sh.z0 = v[k] + w[k]; }
+            if (i == nrows - 2) { sh.yq = y[k]; sh.zq = v[k] + w[k]; }
+        }
+    }
+    if (m > 0 && cs + m == nrows) {
+        sh.last[0] = last[0]; sh.last[1] = last[1]; sh.last[2] = last[2]; sh.last[3] = last[3];
+    }
+    __syncthreads();
+    if (t == 0) {
+        const double a = sh.last[0], b = sh.last[1], c = sh.last[2], d = sh.last[3];
+        const double den = b - a * sh.zq - c * sh.z0;
+        if (!(den > 0.0)) flag_error(err, HSGN_DEV_ERR_COERCIVE);
+        sh.xlast = (d - a * sh.yq - c * sh.y0) / den;
+    }
+    __syncthreads();
+    const double xl = sh.xlast;
+#pragma unroll
+    for (int k = 0; k < M; ++k) {
+        if (k < m) {
+            const int i = cs + k;
+            x[i] = (i == nrows - 1) ? xl : y[k] - xl * (v[k] + w[k]);
+        }
+    }
+}
+
+// Generic multi-block elimination of explicit rows (used when the separator
+// system itself is too large for one CTA, and by the standalone solver).
+template <int T, int M>
+struct ReduceShared {
+    SepShared<T> sep;
+    double ys[T * M], vs[T * M], ws[T * M];
+    double lastrow[4];
+};
+
+template <int T, int M>
+__global__ void __launch_bounds__(T) k_block_reduce_rows(ArrayRows rows, BlockSplit split,
+                                                         double* yo, double* vo, double* wo,
+                                                         double* blk, unsigned* err) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    auto& sh = *reinterpret_cast<ReduceShared<T, M>*>(smem_raw);
+    const int64_t b = blockIdx.x;
+    const int64_t r0 = split.start(b);
+    const int nb = (int)split.size(b);
+    ArrayRows rb = rows;
+    rb.off = r0;
+    double y[M], v[M], w[M], last[4];
+    int cs, m;
+    cta_block_solve<T, M>(nb, rb, sh.sep, y, v, w, cs, m, last, err);
+#pragma unroll
+    for (int k = 0; k < M; ++k) {
+        if (k < m) {
+            sh.ys[cs + k] = y[k];
+            sh.vs[cs + k] = v[k];
+            sh.ws[cs + k] = w[k];
+        }
+    }
+    if (m > 0 && cs + m == nb) {
+        sh.lastrow[0] = last[0]; sh.lastrow[1] = last[1];
+        sh.lastrow[2] = last[2]; sh.lastrow[3] = last[3];
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < nb; i += T) {
+        yo[r0 + i] = sh.ys[i];
+        vo[r0 + i] = sh.vs[i];
+        wo[r0 + i] = sh.ws[i];
+    }
+    if (threadIdx.x == 0) {
+        double* s = blk + b * BLK_STRIDE;
+        s[0] = sh.lastrow[0]; s[1] = sh.lastrow[1]; s[2] = sh.lastrow[2]; s[3] = sh.lastrow[3];
+        s[4] = sh.ys[0]; s[5] = sh.vs[0]; s[6] = sh.ws[0];
+        if (nb >= 2) {
+            s[7] = sh.ys[nb - 2]; s[8] = sh.vs[nb - 2]; s[9] = sh.ws[nb - 2];
+        } else {
+            s[7] = 0.0; s[8] = -1.0; s[9] = 0.0;
+        }
+    }
+}
+
+// Separator rows of the next level as explicit arrays (cyclic).
+__global__ void k_form_reduced(int P, const double* blk, double* A, double* B, double* C,
+                               double* D) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= P) return;
+    BlkRows r{blk, P};
+    r(i, A[i], B[i], C[i], D[i]);
+}
+
+// x_i = y_i - s_{b-1} v_i - s_b w_i for every row of a multi-block solve.
+__global__ void k_block_backout(BlockSplit split, const double* y, const double* v,
+                                const double* w, const double* s, double* x) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= split.n) return;
+    const int64_t b = split.block_of(i);
+    const double sl = s[b == 0 ? split.P - 1 : b - 1];
+    const double sr = s[b];
+    x[i] = y[i] - sl * v[i] - sr * w[i];
+}
+
+struct BacksubParams {
+    int64_t n;
+    int32_t bc;
+    int32_t track_speed;  // 1: atomically fold max |u| of the result into *speed
+    double dx, lam, tau;
+    BlockSplit split;
+    const double *y, *v, *w, *s;
+    const double *qs, *ms, *rs, *be, *de;
+    double* out[4];
+    double* speed;
+    unsigned* err;
+};
+
+__device__ __forceinline__ double hbar_at(const BacksubParams& p, int64_t i) {
+    const int64_t b = p.split.block_of(i);
+    const double sl = p.s[b == 0 ? p.split.P - 1 : b - 1];
+    const double sr = p.s[b];
+    return p.y[i] - sl * p.v[i] - sr * p.w[i];
+}
+
+// Back-substitution of Sec. 4.2 (the fourth equation with h^2 implicit, the
+// "second version" of Sec. 6.3.1):
+//   qbar = q^dag - tau/(2dx) beta (hbar_{i+1} - hbar_{i-1})
+//                - lambda tau/(2dx) delta (m^dag_{i+1} - m^dag_{i-1}),
+//   mbar = m^dag / (1 + lambda tau^2 / hbar^2),  rbar = r^dag - lambda tau mbar / hbar^2.
+template <int BC>
+__global__ void k_backsub(const BacksubParams p) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    double umax = 0.0;
+    if (i < p.n) {
+        const int64_t il = wrap_index(i - 1, p.n, BC), ir = wrap_index(i + 1, p.n, BC);
+        const double h = hbar_at(p, i);
+        const double hl = hbar_at(p, il), hr = hbar_at(p, ir);
+        const double fq = p.tau / (2.0 * p.dx);
+        const double q = p.qs[i] - fq * p.be[i] * (hr - hl) -
+                         p.lam * fq * p.de[i] * (p.ms[ir] - p.ms[il]);
+        const double h2 = h * h;
+        const double lt2 = p.lam * p.tau * p.tau;
+        const double inv = 1.0 / (h2 + lt2);
+        const double msv = p.ms[i];
+        const double m = msv * h2 * inv;
+        const double r = p.rs[i] - p.lam * p.tau * msv * inv;
+        unsigned bad = 0;
+        if (!(h > 0.0)) bad |= HSGN_DEV_ERR_DEPTH;
+        if (!isfinite(h) || !isfinite(q) || !isfinite(m) || !isfinite(r)) bad |= HSGN_DEV_ERR_NONFINITE;
+        if (bad) flag_error(p.err, bad);
+        p.out[0][i] = h;
+        p.out[1][i] = q;
+        p.out[2][i] = m;
+        p.out[3][i] = r;
+        if (p.track_speed && h > 0.0) umax = fabs(q / h);
+    }
+    if (p.track_speed) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) umax = fmax(umax, __shfl_xor_sync(0xffffffffu, umax, o));
+        if ((threadIdx.x & 31) == 0 && umax > 0.0)
+            atomicMax(reinterpret_cast<unsigned long long*>(p.speed),
+                      (unsigned long long)__double_as_longlong(umax));
+    }
+}
+
+// max |u| and max nu = |u| + sqrt(g h + (lambda/3) eta^2/h^2) over the state
+// (Sec. 5 time-step rule); out[0] = max |u|, out[1] = max nu. Non-negative
+// doubles order like their bit patterns, so atomicMax on the bits is exact.
+__global__ void k_speeds(int64_t n, const double* h, const double* q, const double* m, double g,
+                         double lam, double* out, unsigned* err) {
+    double um = 0.0, nm = 0.0;
+    bool bad = false;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const double hh = h[i];
+        if (!(hh > 0.0)) {
+            bad = true;
+            continue;
+        }
+        const double u = fabs(q[i] / hh);
+        const double e = m[i] / (hh * hh);
+        const double nu = u + sqrt(g * hh + (lam / 3.0) * e * e);
+        um = fmax(um, u);
+        nm = fmax(nm, nu);
+    }
+    if (bad) flag_error(err, HSGN_DEV_ERR_DEPTH);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        um = fmax(um, __shfl_xor_sync(0xffffffffu, um, o));
+        nm = fmax(nm, __shfl_xor_sync(0xffffffffu, nm, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        if (um > 0.0)
+            atomicMax(reinterpret_cast<unsigned long long*>(out),
+                      (unsigned long long)__double_as_longlong(um));
+        if (nm > 0.0)
+            atomicMax(reinterpret_cast<unsigned long long*>(out + 1),
+                      (unsigned long long)__double_as_longlong(nm));
+    }
+}
+
+}  // namespace hsgn

@@ -1,0 +1,583 @@
+// hsgn_lib.cu -- host runtime and C ABI of the hSGN semi-implicit IMEX library.
+//
+// Declarations, argument meaning, ownership and error behaviour: include/hsgn.h.
+// Paper: Macca, Boscheri, Ricchiuto, arXiv 2510.07539 (Sec. 3.2 time stepping,
+// Sec. 4.2 fully-discrete stage, Sec. 5 time-step rule).
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdint>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "../../include/hsgn.h"
+#include "hsgn_kernels.cuh"
+
+using namespace hsgn;
+
+namespace {
+
+// Stage block: T threads x M rows per thread.
+constexpr int AT = 64, AM = 8, AS = AT * AM;
+// One-CTA cyclic solve of the block-separator system: up to RT*RM rows.
+constexpr int RT = 256, RM = 16, RMAX = RT * RM;
+// Generic multi-block elimination of explicit rows.
+constexpr int GT = 64, GM = 8, GS = GT * GM;
+
+constexpr size_t kAlign = 256;
+
+size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
+
+BlockSplit make_split(int64_t n, int64_t rows_per_block) {
+    BlockSplit s;
+    s.n = n;
+    s.P = (int32_t)((n + rows_per_block - 1) / rows_per_block);
+    s.base = n / s.P;
+    s.rem = (int32_t)(n % s.P);
+    return s;
+}
+
+// Workspace (in bytes, excluding the error word) of the recursive explicit-row
+// solve of n rows.
+size_t rows_ws_bytes(int64_t n) {
+    if (n <= RMAX) return 0;
+    const BlockSplit s = make_split(n, GS);
+    const int64_t P = s.P;
+    size_t b = align_up(3 * n * sizeof(double)) + align_up(BLK_STRIDE * P * sizeof(double)) +
+               align_up(4 * P * sizeof(double)) + align_up(P * sizeof(double));
+    return b + rows_ws_bytes(P);
+}
+
+template <class K>
+cudaError_t set_smem(K kernel, size_t bytes) {
+    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+// Recursive solve of explicit rows (device arrays) with workspace `ws`.
+cudaError_t solve_rows(int64_t n, int periodic, const double* a, const double* b, const double* c,
+                       const double* d, double* x, unsigned char* ws, unsigned* err,
+                       double* speed_reset, cudaStream_t st) {
+    ArrayRows rows{a, b, c, d, 0, periodic, n};
+    if (n <= RMAX) {
+        k_cyclic_onecta<RT, RM, ArrayRows><<<1, RT, 0, st>>>((int)n, rows, x, speed_reset, err);
+        return cudaGetLastError();
+    }
+    const BlockSplit s = make_split(n, GS);
+    const int64_t P = s.P;
+    double* y = reinterpret_cast<double*>(ws);
+    ws += align_up(3 * n * sizeof(double));
+    double* blk = reinterpret_cast<double*>(ws);
+    ws += align_up(BLK_STRIDE * P * sizeof(double));
+    double* R = reinterpret_cast<double*>(ws);
+    ws += align_up(4 * P * sizeof(double));
+    double* sv = reinterpret_cast<double*>(ws);
+    ws += align_up(P * sizeof(double));
+    const size_t smem = sizeof(ReduceShared<GT, GM>);  // below the 48 KB default limit
+    static_assert(sizeof(ReduceShared<GT, GM>) <= 48 * 1024, "needs an opt-in smem attribute");
+    k_block_reduce_rows<GT, GM><<<(unsigned)P, GT, smem, st>>>(rows, s, y, y + n, y + 2 * n, blk, err);
+    k_form_reduced<<<(unsigned)((P + 255) / 256), 256, 0, st>>>((int)P, blk, R, R + P, R + 2 * P,
+                                                              R + 3 * P);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    e = solve_rows(P, 1, R, R + P, R + 2 * P, R + 3 * P, sv, ws, err, speed_reset, st);
+    if (e != cudaSuccess) return e;
+    k_block_backout<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(s, y, y + n, y + 2 * n, sv, x);
+    return cudaGetLastError();
+}
+
+int map_error_bits(unsigned bits) {
+    // the root cause first: a bad depth or coefficient produces the non-finite values
+    if (bits & HSGN_DEV_ERR_DEPTH) return HSGN_ERR_NONPOSITIVE_DEPTH;
+    if (bits & HSGN_DEV_ERR_COERCIVE) return HSGN_ERR_NOT_COERCIVE;
+    if (bits & HSGN_DEV_ERR_NONFINITE) return HSGN_ERR_NONFINITE;
+    return HSGN_OK;
+}
+
+__global__ void k_set_scalar(double* p, double v) { *p = v; }
+
+}  // namespace
+
+struct hsgn_s {
+    int64_t n = 0;
+    int32_t bc = 0, flags = 0;
+    double dx = 0, g = 0, lam = 0;
+    int device = 0;
+    BlockSplit split{};
+    unsigned char* mem = nullptr;  // one allocation for state and workspace
+    double* U[4] = {};
+    double* U1[4] = {};
+    double *y = nullptr, *v = nullptr, *w = nullptr;
+    double *qs = nullptr, *ms = nullptr, *rs = nullptr, *be = nullptr, *de = nullptr;
+    double* blk = nullptr;
+    double* s = nullptr;
+    double* red = nullptr;           // reduced rows (4 P) when P > RMAX
+    unsigned char* rws = nullptr;    // recursive workspace
+    double* spd = nullptr;           // [0] global Rusanov speed, [1] stage speed, [2..3] scratch
+    unsigned* err = nullptr;
+    cudaStream_t cap = nullptr;      // private stream used for graph capture
+    cudaGraphExec_t gexec = nullptr;
+    double gdt = 0.0;
+    // event-pair profiler (hsgn_profile)
+    bool prof = false;
+    std::vector<cudaEvent_t> ev_pool;
+    struct Rec { int kind; cudaEvent_t a, b; };
+    std::vector<Rec> recs;
+    double prof_ms[HSGN_PROF_KINDS] = {};
+    int64_t prof_n[HSGN_PROF_KINDS] = {};
+};
+
+namespace {
+
+bool local_speed(const hsgn_s* H) { return (H->flags & HSGN_RUSANOV_LOCAL) != 0; }
+
+cudaEvent_t take_event(hsgn_s* H) {
+    if (!H->ev_pool.empty()) {
+        cudaEvent_t e = H->ev_pool.back();
+        H->ev_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+// Records an event pair around one kernel launch when profiling is on.
+struct ProfScope {
+    hsgn_s* H;
+    int kind;
+    cudaStream_t st;
+    cudaEvent_t a = nullptr;
+    ProfScope(hsgn_s* h, int k, cudaStream_t s) : H(h), kind(k), st(s) {
+        if (H->prof) {
+            a = take_event(H);
+            cudaEventRecord(a, st);
+        }
+    }
+    ~ProfScope() {
+        if (a) {
+            cudaEvent_t b = take_event(H);
+            cudaEventRecord(b, st);
+            H->recs.push_back({kind, a, b});
+        }
+    }
+};
+
+cudaError_t launch_stage(hsgn_s* H, const double* const A[4], const double* const B[4], double wl0,
+                         double wl1, double wb0, double wb1, double tau, const double* speed_ptr,
+                         double* const out[4], bool reset_and_track, cudaStream_t st) {
+    StageParams p;
+    p.n = H->n;
+    p.bc = H->bc;
+    p.local_speed = local_speed(H) ? 1 : 0;
+    p.dx = H->dx;
+    p.g = H->g;
+    p.lam = H->lam;
+    p.tau = tau;
+    for (int k = 0; k < 4; ++k) {
+        p.A[k] = A[k];
+        p.B[k] = B ? B[k] : nullptr;
+    }
+    p.wl0 = wl0;
+    p.wl1 = wl1;
+    p.wb0 = wb0;
+    p.wb1 = wb1;
+    p.speed = speed_ptr;
+    p.split = H->split;
+    p.y = H->y;
+    p.v = H->v;
+    p.w = H->w;
+    p.qs = H->qs;
+    p.ms = H->ms;
+    p.rs = H->rs;
+    p.be = H->be;
+    p.de = H->de;
+    p.blk = H->blk;
+    p.err = H->err;
+    const size_t smem = sizeof(AssembleShared<AT, AM>);
+    const unsigned P = (unsigned)H->split.P;
+    {
+        ProfScope ps(H, HSGN_PROF_ASSEMBLE, st);
+        if (H->bc == BC_PERIODIC)
+            k_stage_assemble<AT, AM, BC_PERIODIC><<<P, AT, smem, st>>>(p);
+        else
+            k_stage_assemble<AT, AM, BC_TRANSMISSIVE><<<P, AT, smem, st>>>(p);
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+
+    const bool track = reset_and_track && !local_speed(H);
+    double* reset = track ? H->spd : nullptr;
+    {
+    ProfScope ps(H, HSGN_PROF_REDUCED, st);
+    if (P <= (unsigned)RMAX) {
+        k_cyclic_onecta<RT, RM, BlkRows><<<1, RT, 0, st>>>((int)P, BlkRows{H->blk, (int)P}, H->s,
+                                                           reset, H->err);
+    } else {
+        double* R = H->red;
+        k_form_reduced<<<(P + 255) / 256, 256, 0, st>>>((int)P, H->blk, R, R + P, R + 2 * P,
+                                                        R + 3 * P);
+        e = solve_rows(P, 1, R, R + P, R + 2 * P, R + 3 * P, H->s, H->rws, H->err, reset, st);
+    }
+    }
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+
+    BacksubParams q;
+    q.n = H->n;
+    q.bc = H->bc;
+    q.track_speed = track ? 1 : 0;
+    q.dx = H->dx;
+    q.lam = H->lam;
+    q.tau = tau;
+    q.split = H->split;
+    q.y = H->y;
+    q.v = H->v;
+    q.w = H->w;
+    q.s = H->s;
+    q.qs = H->qs;
+    q.ms = H->ms;
+    q.rs = H->rs;
+    q.be = H->be;
+    q.de = H->de;
+    for (int k = 0; k < 4; ++k) q.out[k] = out[k];
+    q.speed = H->spd;
+    q.err = H->err;
+    const unsigned nb = (unsigned)((H->n + 255) / 256);
+    {
+        ProfScope ps(H, HSGN_PROF_BACKSUB, st);
+        if (H->bc == BC_PERIODIC)
+            k_backsub<BC_PERIODIC><<<nb, 256, 0, st>>>(q);
+        else
+            k_backsub<BC_TRANSMISSIVE><<<nb, 256, 0, st>>>(q);
+    }
+    return cudaGetLastError();
+}
+
+// IMEX step of Sec. 3.2 in efficient form:
+//   U1 = S(U, U, gamma dt);
+//   U  <- S(U_b, U_l, gamma dt), U_l = (1-c/gamma) U + (c/gamma) U1,
+//                                U_b = (1-(1-gamma)/gamma) U + ((1-gamma)/gamma) U1.
+cudaError_t enqueue_step(hsgn_s* H, double dt, cudaStream_t st) {
+    const double gam = 1.0 - 1.0 / std::sqrt(2.0);
+    const double c = 1.0 / (2.0 * gam);
+    const double tau = gam * dt;
+    const double* A[4] = {H->U[0], H->U[1], H->U[2], H->U[3]};
+    const double* B[4] = {H->U1[0], H->U1[1], H->U1[2], H->U1[3]};
+    cudaError_t e = launch_stage(H, A, nullptr, 1.0, 0.0, 1.0, 0.0, tau, H->spd, H->U1, false, st);
+    if (e != cudaSuccess) return e;
+    return launch_stage(H, A, B, 1.0 - c / gam, c / gam, 1.0 - (1.0 - gam) / gam,
+                        (1.0 - gam) / gam, tau, H->spd, H->U, true, st);
+}
+
+int read_error(hsgn_s* H, cudaStream_t st) {
+    unsigned bits = 0;
+    if (cudaMemcpyAsync(&bits, H->err, sizeof(unsigned), cudaMemcpyDeviceToHost, st) != cudaSuccess)
+        return HSGN_ERR_CUDA;
+    if (cudaStreamSynchronize(st) != cudaSuccess) return HSGN_ERR_CUDA;
+    if (bits) {
+        if (cudaMemsetAsync(H->err, 0, sizeof(unsigned), st) != cudaSuccess) return HSGN_ERR_CUDA;
+        if (cudaStreamSynchronize(st) != cudaSuccess) return HSGN_ERR_CUDA;
+    }
+    return map_error_bits(bits);
+}
+
+// Recompute the global Rusanov speed max |u| of the current state.
+cudaError_t refresh_speed(hsgn_s* H, cudaStream_t st) {
+    cudaError_t e = cudaMemsetAsync(H->spd, 0, 2 * sizeof(double), st);
+    if (e != cudaSuccess) return e;
+    k_speeds<<<304, 256, 0, st>>>(H->n, H->U[0], H->U[1], H->U[2], H->g, H->lam, H->spd, H->err);
+    return cudaGetLastError();
+}
+
+inline cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+
+}  // namespace
+
+extern "C" {
+
+const char* hsgn_error_string(int code) {
+    switch (code) {
+        case HSGN_OK: return "ok";
+        case HSGN_ERR_INVALID_ARG: return "invalid argument";
+        case HSGN_ERR_CUDA: return "CUDA runtime error";
+        case HSGN_ERR_NONPOSITIVE_DEPTH: return "non-positive depth";
+        case HSGN_ERR_NOT_COERCIVE: return "not coercive (beta <= 0 or non-positive pivot)";
+        case HSGN_ERR_NONFINITE: return "non-finite value";
+        case HSGN_ERR_UNIMPLEMENTED: return "not implemented";
+        case HSGN_ERR_OUT_OF_MEMORY: return "out of device memory";
+        default: return "unknown error code";
+    }
+}
+
+int hsgn_create(const hsgn_grid_t* grid, double g, double lambda, const double* bathymetry,
+                int32_t flags, hsgn_handle_t* out) {
+    if (!out) return HSGN_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (!grid || grid->n < 3 || grid->reserved != 0) return HSGN_ERR_INVALID_ARG;
+    if (grid->bc != HSGN_BC_PERIODIC && grid->bc != HSGN_BC_TRANSMISSIVE) return HSGN_ERR_INVALID_ARG;
+    if (!(grid->x_right > grid->x_left) || !std::isfinite(grid->x_left) ||
+        !std::isfinite(grid->x_right))
+        return HSGN_ERR_INVALID_ARG;
+    if (!(g > 0.0) || !std::isfinite(g) || !(lambda >= 0.0) || !std::isfinite(lambda))
+        return HSGN_ERR_INVALID_ARG;
+    if (flags & ~(int32_t)(HSGN_RUSANOV_LOCAL)) return HSGN_ERR_UNIMPLEMENTED;
+    if (bathymetry) return HSGN_ERR_UNIMPLEMENTED;
+    if (grid->n > ((int64_t)1 << 40)) return HSGN_ERR_INVALID_ARG;
+
+    hsgn_s* H = new (std::nothrow) hsgn_s;
+    if (!H) return HSGN_ERR_OUT_OF_MEMORY;
+    H->n = grid->n;
+    H->bc = grid->bc;
+    H->flags = flags;
+    H->dx = (grid->x_right - grid->x_left) / (double)grid->n;
+    H->g = g;
+    H->lam = lambda;
+    cudaGetDevice(&H->device);
+    H->split = make_split(H->n, AS);
+    const int64_t n = H->n, P = H->split.P;
+
+    const size_t vec = align_up(n * sizeof(double));
+    size_t total = 16 * vec;                                   // U, U1, y v w, 5 back-sub arrays
+    total += align_up(BLK_STRIDE * P * sizeof(double)) + align_up(P * sizeof(double));
+    const size_t red = P > RMAX ? align_up(4 * P * sizeof(double)) : 0;
+    const size_t rws = P > RMAX ? rows_ws_bytes(P) : 0;
+    total += red + rws + align_up(4 * sizeof(double)) + align_up(sizeof(unsigned));
+    if (cudaMalloc(&H->mem, total) != cudaSuccess) {
+        cudaGetLastError();
+        delete H;
+        return HSGN_ERR_OUT_OF_MEMORY;
+    }
+    unsigned char* p = H->mem;
+    auto take = [&](size_t bytes) {
+        unsigned char* r = p;
+        p += bytes;
+        return r;
+    };
+    for (int k = 0; k < 4; ++k) H->U[k] = reinterpret_cast<double*>(take(vec));
+    for (int k = 0; k < 4; ++k) H->U1[k] = reinterpret_cast<double*>(take(vec));
+    H->y = reinterpret_cast<double*>(take(vec));
+    H->v = reinterpret_cast<double*>(take(vec));
+    H->w = reinterpret_cast<double*>(take(vec));
+    H->qs = reinterpret_cast<double*>(take(vec));
+    H->ms = reinterpret_cast<double*>(take(vec));
+    H->rs = reinterpret_cast<double*>(take(vec));
+    H->be = reinterpret_cast<double*>(take(vec));
+    H->de = reinterpret_cast<double*>(take(vec));
+    H->blk = reinterpret_cast<double*>(take(align_up(BLK_STRIDE * P * sizeof(double))));
+    H->s = reinterpret_cast<double*>(take(align_up(P * sizeof(double))));
+    H->red = red ? reinterpret_cast<double*>(take(red)) : nullptr;
+    H->rws = rws ? take(rws) : nullptr;
+    H->spd = reinterpret_cast<double*>(take(align_up(4 * sizeof(double))));
+    H->err = reinterpret_cast<unsigned*>(take(align_up(sizeof(unsigned))));
+
+    cudaError_t e = cudaMemset(H->mem, 0, total);
+    if (e == cudaSuccess)
+        e = set_smem(k_stage_assemble<AT, AM, BC_PERIODIC>, sizeof(AssembleShared<AT, AM>));
+    if (e == cudaSuccess)
+        e = set_smem(k_stage_assemble<AT, AM, BC_TRANSMISSIVE>, sizeof(AssembleShared<AT, AM>));
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&H->cap, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        if (H->cap) cudaStreamDestroy(H->cap);
+        cudaFree(H->mem);
+        delete H;
+        return HSGN_ERR_CUDA;
+    }
+    *out = H;
+    return HSGN_OK;
+}
+
+void hsgn_destroy(hsgn_handle_t H) {
+    if (!H) return;
+    for (const auto& r : H->recs) {
+        cudaEventSynchronize(r.b);
+        cudaEventDestroy(r.a);
+        cudaEventDestroy(r.b);
+    }
+    for (cudaEvent_t e : H->ev_pool) cudaEventDestroy(e);
+    if (H->gexec) cudaGraphExecDestroy(H->gexec);
+    if (H->cap) cudaStreamDestroy(H->cap);
+    cudaFree(H->mem);
+    delete H;
+}
+
+int hsgn_set_state(hsgn_handle_t H, const double* depth, const double* q, const double* heta,
+                   const double* hw, void* stream) {
+    if (!H || !depth || !q || !heta || !hw) return HSGN_ERR_INVALID_ARG;
+    cudaStream_t st = as_stream(stream);
+    const double* src[4] = {depth, q, heta, hw};
+    for (int k = 0; k < 4; ++k)
+        if (cudaMemcpyAsync(H->U[k], src[k], H->n * sizeof(double), cudaMemcpyDefault, st) !=
+            cudaSuccess)
+            return HSGN_ERR_CUDA;
+    return refresh_speed(H, st) == cudaSuccess ? HSGN_OK : HSGN_ERR_CUDA;
+}
+
+int hsgn_get_state(hsgn_handle_t H, double* depth, double* q, double* heta, double* hw,
+                   void* stream) {
+    if (!H || !depth || !q || !heta || !hw) return HSGN_ERR_INVALID_ARG;
+    cudaStream_t st = as_stream(stream);
+    double* dst[4] = {depth, q, heta, hw};
+    for (int k = 0; k < 4; ++k)
+        if (cudaMemcpyAsync(dst[k], H->U[k], H->n * sizeof(double), cudaMemcpyDefault, st) !=
+            cudaSuccess)
+            return HSGN_ERR_CUDA;
+    return read_error(H, st);
+}
+
+int hsgn_step(hsgn_handle_t H, double dt, void* stream) {
+    if (!H || !(dt > 0.0) || !std::isfinite(dt)) return HSGN_ERR_INVALID_ARG;
+    return enqueue_step(H, dt, as_stream(stream)) == cudaSuccess ? HSGN_OK : HSGN_ERR_CUDA;
+}
+
+int hsgn_enqueue(hsgn_handle_t H, double dt, int64_t n_steps, void* stream) {
+    if (!H || !(dt > 0.0) || !std::isfinite(dt) || n_steps < 0) return HSGN_ERR_INVALID_ARG;
+    cudaStream_t st = as_stream(stream);
+    if (n_steps == 0) return HSGN_OK;
+    if (!H->gexec || H->gdt != dt) {
+        const bool prof = H->prof;
+        H->prof = false;  // events are not captured into the graph
+        if (H->gexec) {
+            cudaGraphExecDestroy(H->gexec);
+            H->gexec = nullptr;
+        }
+        cudaGraph_t graph = nullptr;
+        if (cudaStreamBeginCapture(H->cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+            return HSGN_ERR_CUDA;
+        const cudaError_t e1 = enqueue_step(H, dt, H->cap);
+        const cudaError_t e2 = cudaStreamEndCapture(H->cap, &graph);
+        H->prof = prof;
+        if (e1 != cudaSuccess || e2 != cudaSuccess) {
+            if (graph) cudaGraphDestroy(graph);
+            cudaGetLastError();
+            return HSGN_ERR_CUDA;
+        }
+        const cudaError_t e3 = cudaGraphInstantiate(&H->gexec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e3 != cudaSuccess) {
+            H->gexec = nullptr;
+            cudaGetLastError();
+            return HSGN_ERR_CUDA;
+        }
+        H->gdt = dt;
+    }
+    for (int64_t k = 0; k < n_steps; ++k)
+        if (cudaGraphLaunch(H->gexec, st) != cudaSuccess) return HSGN_ERR_CUDA;
+    return HSGN_OK;
+}
+
+int hsgn_run(hsgn_handle_t H, double dt, int64_t n_steps, void* stream) {
+    const int rc = hsgn_enqueue(H, dt, n_steps, stream);
+    if (rc != HSGN_OK) return rc;
+    return read_error(H, as_stream(stream));
+}
+
+int hsgn_profile(hsgn_handle_t H, int32_t enable) {
+    if (!H) return HSGN_ERR_INVALID_ARG;
+    H->prof = enable != 0;
+    return HSGN_OK;
+}
+
+int hsgn_profile_read(hsgn_handle_t H, double* ms, int64_t* launches, int32_t reset) {
+    if (!H) return HSGN_ERR_INVALID_ARG;
+    int rc = HSGN_OK;
+    for (const auto& r : H->recs) {
+        float t = 0.f;
+        if (cudaEventSynchronize(r.b) != cudaSuccess || cudaEventElapsedTime(&t, r.a, r.b) != cudaSuccess)
+            rc = HSGN_ERR_CUDA;
+        H->prof_ms[r.kind] += t;
+        H->prof_n[r.kind] += 1;
+        H->ev_pool.push_back(r.a);
+        H->ev_pool.push_back(r.b);
+    }
+    H->recs.clear();
+    for (int k = 0; k < HSGN_PROF_KINDS; ++k) {
+        if (ms) ms[k] = H->prof_ms[k];
+        if (launches) launches[k] = H->prof_n[k];
+    }
+    if (reset)
+        for (int k = 0; k < HSGN_PROF_KINDS; ++k) {
+            H->prof_ms[k] = 0.0;
+            H->prof_n[k] = 0;
+        }
+    return rc;
+}
+
+int hsgn_check(hsgn_handle_t H, void* stream) {
+    if (!H) return HSGN_ERR_INVALID_ARG;
+    return read_error(H, as_stream(stream));
+}
+
+int hsgn_suggest_dt(hsgn_handle_t H, double cfl, double mcfl, double* dt_out, void* stream) {
+    if (!H || !dt_out || !(cfl > 0.0)) return HSGN_ERR_INVALID_ARG;
+    cudaStream_t st = as_stream(stream);
+    double* tmp = H->spd + 2;
+    if (cudaMemsetAsync(tmp, 0, 2 * sizeof(double), st) != cudaSuccess) return HSGN_ERR_CUDA;
+    k_speeds<<<304, 256, 0, st>>>(H->n, H->U[0], H->U[1], H->U[2], H->g, H->lam, tmp, H->err);
+    if (cudaGetLastError() != cudaSuccess) return HSGN_ERR_CUDA;
+    double hv[2];
+    if (cudaMemcpyAsync(hv, tmp, sizeof(hv), cudaMemcpyDeviceToHost, st) != cudaSuccess)
+        return HSGN_ERR_CUDA;
+    const int rc = read_error(H, st);
+    if (rc != HSGN_OK) return rc;
+    const double umax = hv[0], numax = hv[1];
+    if (!(numax > 0.0)) return HSGN_ERR_INVALID_ARG;
+    double dt = cfl * H->dx / numax;
+    if (mcfl > 0.0 && umax > 0.0 && umax * dt / H->dx > mcfl) dt = mcfl * H->dx / umax;
+    *dt_out = dt;
+    return HSGN_OK;
+}
+
+int hsgn_stage(hsgn_handle_t H, const double* const base[4], const double* const lin[4],
+               double tau, double speed, double* const out[4], void* stream) {
+    if (!H || !base || !lin || !out || !(tau > 0.0) || !(speed >= 0.0)) return HSGN_ERR_INVALID_ARG;
+    for (int k = 0; k < 4; ++k)
+        if (!base[k] || !lin[k] || !out[k]) return HSGN_ERR_INVALID_ARG;
+    cudaStream_t st = as_stream(stream);
+    k_set_scalar<<<1, 1, 0, st>>>(H->spd + 1, speed);
+    if (cudaGetLastError() != cudaSuccess) return HSGN_ERR_CUDA;
+    // A = base, B = lin: U_l = lin, U_b = base
+    return launch_stage(H, base, lin, 0.0, 1.0, 1.0, 0.0, tau, H->spd + 1, out, false, st) ==
+                   cudaSuccess
+               ? HSGN_OK
+               : HSGN_ERR_CUDA;
+}
+
+int hsgn_adjoint(hsgn_handle_t H, double dt, int64_t n_steps, int64_t n_gauges,
+                 const int64_t* gauge_cells, const double* gauge_data, double* grad_h0,
+                 double* misfit, void* stream) {
+    (void)H; (void)dt; (void)n_steps; (void)n_gauges; (void)gauge_cells; (void)gauge_data;
+    (void)grad_h0; (void)misfit; (void)stream;
+    return HSGN_ERR_UNIMPLEMENTED;
+}
+
+int hsgn_tridiag_workspace_bytes(int64_t n, size_t* bytes) {
+    if (n < 1 || !bytes) return HSGN_ERR_INVALID_ARG;
+    *bytes = align_up(sizeof(unsigned)) + rows_ws_bytes(n);
+    return HSGN_OK;
+}
+
+int hsgn_tridiag_solve(int64_t n, int32_t periodic, const double* a, const double* b,
+                       const double* c, const double* d, double* x, void* workspace,
+                       size_t workspace_bytes, void* stream) {
+    if (n < 1 || !a || !b || !c || !d || !x || !workspace) return HSGN_ERR_INVALID_ARG;
+    size_t need = 0;
+    hsgn_tridiag_workspace_bytes(n, &need);
+    if (workspace_bytes < need || (reinterpret_cast<uintptr_t>(workspace) % kAlign) != 0)
+        return HSGN_ERR_INVALID_ARG;
+    cudaStream_t st = as_stream(stream);
+    unsigned* err = reinterpret_cast<unsigned*>(workspace);
+    unsigned char* ws = reinterpret_cast<unsigned char*>(workspace) + align_up(sizeof(unsigned));
+    if (cudaMemsetAsync(err, 0, sizeof(unsigned), st) != cudaSuccess) return HSGN_ERR_CUDA;
+    if (solve_rows(n, periodic ? 1 : 0, a, b, c, d, x, ws, err, nullptr, st) != cudaSuccess)
+        return HSGN_ERR_CUDA;
+    unsigned bits = 0;
+    if (cudaMemcpyAsync(&bits, err, sizeof(unsigned), cudaMemcpyDeviceToHost, st) != cudaSuccess)
+        return HSGN_ERR_CUDA;
+    if (cudaStreamSynchronize(st) != cudaSuccess) return HSGN_ERR_CUDA;
+    return map_error_bits(bits);
+}
+
+}  // extern "C"

@@ -1,0 +1,211 @@
+"""Python binding of the C ABI in include/hsgn.h (argument marshalling only).
+
+Every step of the numerical method runs in the CUDA library libhsgn.so; this
+module passes torch tensor pointers and the current CUDA stream through ctypes.
+Importing it loads the library and raises if it is missing: there is no CPU or
+eager fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libhsgn.so")
+
+HSGN_OK = 0
+BC_PERIODIC = 0
+BC_TRANSMISSIVE = 1
+FLAG_FP64 = 0x0
+FLAG_RUSANOV_LOCAL = 0x10
+
+ERROR_NAMES = {
+    1: "HSGN_ERR_INVALID_ARG", 2: "HSGN_ERR_CUDA", 3: "HSGN_ERR_NONPOSITIVE_DEPTH",
+    4: "HSGN_ERR_NOT_COERCIVE", 5: "HSGN_ERR_NONFINITE", 6: "HSGN_ERR_UNIMPLEMENTED",
+    7: "HSGN_ERR_OUT_OF_MEMORY",
+}
+
+
+class HsgnError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        msg = _lib.hsgn_error_string(code).decode() if _lib is not None else "?"
+        super().__init__(f"{where}: {ERROR_NAMES.get(code, code)} ({msg})")
+        self.code = code
+
+
+class Grid(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("x_left", ctypes.c_double), ("x_right", ctypes.c_double),
+                ("bc", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+_lib = None
+_P = ctypes.c_void_p
+_D = ctypes.c_double
+_I64 = ctypes.c_int64
+
+
+def load():
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"CUDA library {LIB_PATH} is missing: run "
+                           "`python -c 'import __graft_entry__ as g; g.build()'` first")
+    lib = ctypes.CDLL(LIB_PATH)
+    sig = {
+        "hsgn_create": [ctypes.POINTER(Grid), _D, _D, _P, ctypes.c_int32, ctypes.POINTER(_P)],
+        "hsgn_set_state": [_P, _P, _P, _P, _P, _P],
+        "hsgn_get_state": [_P, _P, _P, _P, _P, _P],
+        "hsgn_step": [_P, _D, _P],
+        "hsgn_run": [_P, _D, _I64, _P],
+        "hsgn_enqueue": [_P, _D, _I64, _P],
+        "hsgn_profile": [_P, ctypes.c_int32],
+        "hsgn_profile_read": [_P, _P, _P, ctypes.c_int32],
+        "hsgn_check": [_P, _P],
+        "hsgn_suggest_dt": [_P, _D, _D, ctypes.POINTER(_D), _P],
+        "hsgn_stage": [_P, ctypes.POINTER(_P), ctypes.POINTER(_P), _D, _D, ctypes.POINTER(_P), _P],
+        "hsgn_adjoint": [_P, _D, _I64, _I64, _P, _P, _P, _P, _P],
+        "hsgn_tridiag_workspace_bytes": [_I64, ctypes.POINTER(ctypes.c_size_t)],
+        "hsgn_tridiag_solve": [_I64, ctypes.c_int32, _P, _P, _P, _P, _P, _P, ctypes.c_size_t, _P],
+    }
+    for name, args in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = ctypes.c_int
+    lib.hsgn_destroy.argtypes = [_P]
+    lib.hsgn_destroy.restype = None
+    lib.hsgn_error_string.argtypes = [ctypes.c_int]
+    lib.hsgn_error_string.restype = ctypes.c_char_p
+    _lib = lib
+    return lib
+
+
+def _check(rc: int, where: str):
+    if rc != HSGN_OK:
+        raise HsgnError(rc, where)
+
+
+def _stream(stream=None):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _ptr(t: torch.Tensor):
+    if t.dtype != torch.float64 or not t.is_contiguous():
+        raise ValueError("arrays must be contiguous float64 tensors")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class Solver:
+    """One hSGN instance on the current CUDA device (owns its state on the device)."""
+
+    def __init__(self, n: int, x_left: float, x_right: float, bc: int = BC_PERIODIC,
+                 g: float = 9.81, lam: float = 100.0, flags: int = FLAG_FP64):
+        load()
+        self.n, self.bc, self.g, self.lam, self.flags = int(n), int(bc), float(g), float(lam), flags
+        self.dx = (x_right - x_left) / n
+        grid = Grid(int(n), float(x_left), float(x_right), int(bc), 0)
+        h = _P()
+        _check(_lib.hsgn_create(ctypes.byref(grid), float(g), float(lam), None, int(flags),
+                                ctypes.byref(h)), "hsgn_create")
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.hsgn_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def set_state(self, h, q, m, r, stream=None):
+        ts = [t if isinstance(t, torch.Tensor) else torch.as_tensor(t, dtype=torch.float64)
+              for t in (h, q, m, r)]
+        for t in ts:
+            if t.numel() != self.n:
+                raise ValueError(f"expected {self.n} values")
+        self._keep = ts  # the copy is asynchronous: keep the sources alive
+        _check(_lib.hsgn_set_state(self._h, *(_ptr(t) for t in ts), _stream(stream)),
+               "hsgn_set_state")
+
+    def get_state(self, out=None, device="cuda", stream=None):
+        if out is None:
+            out = [torch.empty(self.n, dtype=torch.float64, device=device) for _ in range(4)]
+        _check(_lib.hsgn_get_state(self._h, *(_ptr(t) for t in out), _stream(stream)),
+               "hsgn_get_state")
+        return tuple(out)
+
+    def step(self, dt: float, stream=None):
+        _check(_lib.hsgn_step(self._h, float(dt), _stream(stream)), "hsgn_step")
+
+    def run(self, dt: float, n_steps: int, stream=None):
+        _check(_lib.hsgn_run(self._h, float(dt), int(n_steps), _stream(stream)), "hsgn_run")
+
+    def enqueue(self, dt: float, n_steps: int, stream=None):
+        _check(_lib.hsgn_enqueue(self._h, float(dt), int(n_steps), _stream(stream)), "hsgn_enqueue")
+
+    def profile(self, enable: bool):
+        _check(_lib.hsgn_profile(self._h, int(bool(enable))), "hsgn_profile")
+
+    def profile_read(self, reset: bool = True):
+        """Returns {kind: (total_ms, launches)} for assemble / reduced / backsub."""
+        ms = (ctypes.c_double * 3)()
+        cnt = (ctypes.c_int64 * 3)()
+        _check(_lib.hsgn_profile_read(self._h, ctypes.cast(ms, _P), ctypes.cast(cnt, _P),
+                                      int(bool(reset))), "hsgn_profile_read")
+        return {k: (ms[i], cnt[i]) for i, k in enumerate(("assemble", "reduced", "backsub"))}
+
+    def check(self, stream=None):
+        _check(_lib.hsgn_check(self._h, _stream(stream)), "hsgn_check")
+
+    def suggest_dt(self, cfl: float, mcfl: float, stream=None) -> float:
+        dt = _D()
+        _check(_lib.hsgn_suggest_dt(self._h, float(cfl), float(mcfl), ctypes.byref(dt),
+                                    _stream(stream)), "hsgn_suggest_dt")
+        return dt.value
+
+    def stage(self, base, lin, tau: float, speed: float = 0.0, out=None, stream=None):
+        if out is None:
+            out = [torch.empty(self.n, dtype=torch.float64, device=base[0].device)
+                   for _ in range(4)]
+        arr = _P * 4
+        b = arr(*(_ptr(t) for t in base))
+        l_ = arr(*(_ptr(t) for t in lin))
+        o = arr(*(_ptr(t) for t in out))
+        _check(_lib.hsgn_stage(self._h, b, l_, float(tau), float(speed), o, _stream(stream)),
+               "hsgn_stage")
+        return tuple(out)
+
+
+def tridiag_workspace_bytes(n: int) -> int:
+    load()
+    nb = ctypes.c_size_t()
+    _check(_lib.hsgn_tridiag_workspace_bytes(int(n), ctypes.byref(nb)), "hsgn_tridiag_workspace_bytes")
+    return nb.value
+
+
+def tridiag_solve(a, b, c, d, periodic: bool, stream=None):
+    """Solve the (cyclic) tridiagonal system on the GPU; returns x as a new tensor."""
+    load()
+    n = b.numel()
+    x = torch.empty_like(d)
+    nbytes = tridiag_workspace_bytes(n)
+    ws = torch.empty(max(nbytes, 256) + 256, dtype=torch.uint8, device=d.device)
+    base = ws.data_ptr()
+    aligned = (base + 255) // 256 * 256
+    _check(_lib.hsgn_tridiag_solve(int(n), int(bool(periodic)), _ptr(a), _ptr(b), _ptr(c), _ptr(d),
+                                   _ptr(x), ctypes.c_void_p(aligned), ctypes.c_size_t(nbytes),
+                                   _stream(stream)), "hsgn_tridiag_solve")
+    return x

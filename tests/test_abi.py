@@ -1,0 +1,75 @@
+"""The C-ABI library loads and exports every entry point declared in include/hsgn.h.
+
+Runs on CPU: only host-side logic is exercised (symbol table, error strings,
+argument validation that happens before any CUDA call, workspace sizing).
+"""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "hsgn.h")
+
+
+def declared_functions():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(hsgn_[a-z_]+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2510_07539_gb300 import build, solver
+    build.build()
+    return solver.load()
+
+
+def test_header_declares_expected_entry_points():
+    names = declared_functions()
+    for required in ("hsgn_create", "hsgn_step", "hsgn_run", "hsgn_adjoint", "hsgn_destroy",
+                     "hsgn_set_state", "hsgn_get_state", "hsgn_tridiag_solve"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    missing = [f for f in declared_functions() if not hasattr(lib, f)]
+    assert not missing, missing
+
+
+def test_error_strings(lib):
+    for code in range(0, 8):
+        s = lib.hsgn_error_string(code)
+        assert s and len(s) > 1
+    assert b"unknown" in lib.hsgn_error_string(99)
+
+
+def test_create_rejects_bad_arguments_before_touching_the_device(lib):
+    from paper_2510_07539_gb300.solver import Grid
+    h = ctypes.c_void_p()
+    bad = [Grid(2, 0.0, 1.0, 0, 0), Grid(10, 1.0, 0.0, 0, 0), Grid(10, 0.0, 1.0, 7, 0),
+           Grid(10, 0.0, 1.0, 0, 1)]
+    for g in bad:
+        assert lib.hsgn_create(ctypes.byref(g), 9.81, 1.0, None, 0, ctypes.byref(h)) == 1
+    g = Grid(10, 0.0, 1.0, 0, 0)
+    assert lib.hsgn_create(ctypes.byref(g), -1.0, 1.0, None, 0, ctypes.byref(h)) == 1
+    assert lib.hsgn_create(ctypes.byref(g), 9.81, -1.0, None, 0, ctypes.byref(h)) == 1
+    assert lib.hsgn_create(ctypes.byref(g), 9.81, 1.0, None, 0x4000, ctypes.byref(h)) == 6
+    assert lib.hsgn_create(ctypes.byref(g), 9.81, 1.0, None, 0, None) == 1
+    lib.hsgn_destroy(None)
+
+
+def test_workspace_sizing(lib):
+    nb = ctypes.c_size_t()
+    assert lib.hsgn_tridiag_workspace_bytes(0, ctypes.byref(nb)) == 1
+    assert lib.hsgn_tridiag_workspace_bytes(1000, ctypes.byref(nb)) == 0
+    small = nb.value
+    assert lib.hsgn_tridiag_workspace_bytes(10_000_000, ctypes.byref(nb)) == 0
+    assert nb.value > 24 * 10_000_000 > small
+
+
+def test_null_handle_calls_are_rejected(lib):
+    assert lib.hsgn_step(None, 0.1, None) == 1
+    assert lib.hsgn_run(None, 0.1, 1, None) == 1
+    assert lib.hsgn_check(None, None) == 1

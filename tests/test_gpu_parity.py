@@ -1,0 +1,240 @@
+"""GPU parity: the CUDA library (through its C ABI) against the FP64 CPU oracle.
+
+Element-by-element comparison on identical seeded inputs. Tolerances:
+  * tridiagonal solve: 1e-13 relative to max |x| (different elimination order,
+    condition number of the hSGN depth matrix is below about 100);
+  * one stage / one step: 1e-12 relative L2 per variable;
+  * short trajectories: 1e-9 relative L2 per variable;
+  * exact invariants (mass): 1e-13 relative.
+Sizes span several blocks (512 rows per CTA) with ragged tails, the one-CTA
+and the recursive separator solves, and the full sizes of the benchmark
+workloads (2^20 and 2^24 cells).
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2510_07539_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_2510_07539_gb300 import build
+    build.build()
+    torch.cuda.set_device(0)
+
+
+def S():
+    from paper_2510_07539_gb300 import solver
+    return solver
+
+
+def dev(a):
+    return torch.as_tensor(np.ascontiguousarray(a, dtype=np.float64), device="cuda")
+
+
+def rel_l2(x, ref):
+    return float(np.linalg.norm(x - ref) / max(np.linalg.norm(ref), 1e-300))
+
+
+def summand_scales(n, dx, bc, lam, U, dt):
+    """Per-cell magnitudes of the summands of the back-substitution (Sec. 4.2):
+    qbar = q^dag - tau/(2dx) beta (hbar_{i+1} - hbar_{i-1}) - lambda tau/(2dx) delta (..),
+    rbar = r^dag - lambda tau mbar / hbar^2 with r^dag containing + lambda tau.
+    Rounding errors of q and h w are proportional to these magnitudes, not to
+    the result, which is roundoff-sized wherever the water is at rest."""
+    p = oracle.Params(n, dx, bc, lam=lam)
+    tau = (1.0 - 1.0 / math.sqrt(2.0)) * dt
+    A = oracle.assemble(p, U, U, tau)
+    h, q, m, r = (np.abs(u) for u in U)
+    Sq = q + tau / dx * A["beta"] * h + lam * tau / dx * np.abs(A["delta"]) * np.abs(A["ms"])
+    Sr = r + lam * tau * (1.0 + m / (h * h))
+    return (h, Sq, m, Sr)
+
+
+def scaled_err(x, ref, scale):
+    return float(np.linalg.norm(x - ref) / np.linalg.norm(scale))
+
+
+# --------------------------------------------------------------------------
+# tridiagonal component
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("periodic", [False, True])
+@pytest.mark.parametrize("n", [1, 2, 3, 5, 33, 255, 256, 4095, 4096, 4097, 20000, 300001])
+def test_tridiag_matches_oracle(n, periodic):
+    a, b, c, d = inputs.random_tridiag(500 + n, n, periodic, coupling=5.0)
+    x = S().tridiag_solve(dev(a), dev(b), dev(c), dev(d), periodic).cpu().numpy()
+    ref = oracle.tridiag_solve(a, b, c, d, periodic)
+    assert np.max(np.abs(x - ref)) <= 1e-13 * np.max(np.abs(ref))
+
+
+def test_tridiag_strong_coupling():
+    # large tau^2 beta / dx^2 (slow decay of the inverse): still exact
+    n = 100_000
+    for periodic in (False, True):
+        a, b, c, d = inputs.random_tridiag(77, n, periodic, coupling=1e4)
+        x = S().tridiag_solve(dev(a), dev(b), dev(c), dev(d), periodic).cpu().numpy()
+        ref = oracle.tridiag_solve(a, b, c, d, periodic)
+        assert np.max(np.abs(x - ref)) <= 1e-10 * np.max(np.abs(ref))
+
+
+# --------------------------------------------------------------------------
+# one stage (hsgn_stage) with U_b != U_l
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("bc", [0, 1])
+@pytest.mark.parametrize("n", [3, 4, 7, 64, 511, 512, 513, 1000, 5000, 70001])
+def test_stage_matches_oracle(n, bc):
+    dx, lam, tau, speed = 0.1, 300.0, 0.01, 0.37
+    Ub = inputs.random_state(1000 + n, n, dx)
+    Ul = inputs.random_state(2000 + n, n, dx, h_var=0.1)
+    for local in (0, 1):
+        flags = S().FLAG_RUSANOV_LOCAL if local else 0
+        with S().Solver(n, 0.0, n * dx, bc, lam=lam, flags=flags) as s:
+            out = s.stage([dev(u) for u in Ub], [dev(u) for u in Ul], tau, speed)
+            got = [t.cpu().numpy() for t in out]
+            s.check()
+        p = oracle.Params(n, dx, bc, lam=lam, rusanov=0 if local else 1, speed=speed)
+        ref = oracle.stage(p, Ub, Ul, tau)
+        for k in range(4):
+            assert rel_l2(got[k], ref[k]) < 1e-12, (k, local, rel_l2(got[k], ref[k]))
+
+
+# --------------------------------------------------------------------------
+# whole steps
+# --------------------------------------------------------------------------
+def gpu_run(n, x_left, x_right, bc, lam, U, dt, steps, flags=0, use_graph=True):
+    with S().Solver(n, x_left, x_right, bc, lam=lam, flags=flags) as s:
+        s.set_state(*(dev(u) for u in U))
+        if use_graph:
+            s.run(dt, steps)
+        else:
+            for _ in range(steps):
+                s.step(dt)
+            s.check()
+        return [t.cpu().numpy() for t in s.get_state()]
+
+
+@pytest.mark.parametrize("bc", [0, 1])
+@pytest.mark.parametrize("n", [5, 100, 1000, 1537])
+def test_one_step_matches_oracle(n, bc):
+    dx, lam = 0.1, 500.0
+    U = inputs.random_state(3000 + n, n, dx)
+    p = oracle.Params(n, dx, bc, lam=lam)
+    dt, _, _ = oracle.suggest_dt(p, U, 2.0, 0.5)
+    got = gpu_run(n, 0.0, n * dx, bc, lam, U, dt, 1)
+    ref = oracle.step(p, U, dt)
+    for k in range(4):
+        assert rel_l2(got[k], ref[k]) < 1e-12, (k, rel_l2(got[k], ref[k]))
+
+
+def test_solitary_trajectory_500_steps():
+    # workload 1: solitary wave, N = 1000 on [-50, 50], lambda = 100,
+    # dt from the material CFL 0.5 only, 500 steps
+    n, lam = 1000, 100.0
+    x, dx = inputs.cell_centres(n, -50.0, 50.0)
+    U = inputs.solitary(x, 1.0, 0.2, 0.0, period=100.0)
+    p = oracle.Params(n, dx, 0, lam=lam)
+    dt, _, _ = oracle.suggest_dt(p, U, 1e9, 0.5)
+    got = gpu_run(n, -50.0, 50.0, 0, lam, U, dt, 500)
+    ref = oracle.run(p, U, dt, 500)
+    for k in range(4):
+        assert rel_l2(got[k], ref[k]) < 1e-9, (k, rel_l2(got[k], ref[k]))
+    assert abs(math.fsum(got[0]) - math.fsum(U[0])) <= 1e-13 * math.fsum(U[0])
+
+
+def test_graph_replay_equals_step_loop():
+    n, lam = 3000, 1000.0
+    x, dx = inputs.cell_centres(n, -150.0, 150.0)
+    U = inputs.solitary(x, 1.0, 0.3, 0.0, period=300.0)
+    dt = 0.01
+    a = gpu_run(n, -150.0, 150.0, 0, lam, U, dt, 7, use_graph=True)
+    b = gpu_run(n, -150.0, 150.0, 0, lam, U, dt, 7, use_graph=False)
+    for k in range(4):
+        np.testing.assert_array_equal(a[k], b[k])
+
+
+@pytest.mark.parametrize("lam", [10.0, 100.0, 1000.0])
+def test_dam_break_full_size(lam):
+    # workload 2 at full size: N = 2^20, dx = 0.05, transmissive, tanh
+    # transition of width 5 h0 (h0 = 1), CFL_IMEX = 4; every cell compared
+    # after 10 steps. Most of the domain is at rest, where q and h w are
+    # roundoff-sized, so the error is measured against the summand scales.
+    n, dx, steps = 1 << 20, 0.05, 10
+    x, U = inputs.dam_break(n, dx, 1.2, 1.0, 5.0 / dx)
+    p = oracle.Params(n, dx, 1, lam=lam)
+    dt, _, _ = oracle.suggest_dt(p, U, 4.0, 0.5)
+    got = gpu_run(n, -0.5 * n * dx, 0.5 * n * dx, 1, lam, U, dt, steps)
+    ref = oracle.run(p, U, dt, steps)
+    sc = summand_scales(n, dx, 1, lam, U, dt)
+    for k in range(4):
+        assert scaled_err(got[k], ref[k], sc[k]) < 1e-12, (k, scaled_err(got[k], ref[k], sc[k]))
+    # the depth itself is compared plainly
+    assert rel_l2(got[0], ref[0]) < 1e-12
+
+
+def test_large_instance_2_24_one_step():
+    # workload 5 shape: N = 2^24 cells, lambda = 1000, transmissive, solitary
+    # wave towards the shallow end (flat bottom), one step compared everywhere
+    n, dx, lam = 1 << 24, 0.005, 1000.0
+    x = (np.arange(n) + 0.5) * dx
+    U = inputs.solitary(x, 1.0, 0.1, 0.5 * n * dx - 80.0)
+    p = oracle.Params(n, dx, 1, lam=lam)
+    dt, _, _ = oracle.suggest_dt(p, U, 4.0, 0.5)
+    got = gpu_run(n, 0.0, n * dx, 1, lam, U, dt, 1)
+    ref = oracle.step(p, U, dt)
+    sc = summand_scales(n, dx, 1, lam, U, dt)
+    for k in range(4):
+        assert scaled_err(got[k], ref[k], sc[k]) < 1e-12, (k, scaled_err(got[k], ref[k], sc[k]))
+    assert rel_l2(got[0], ref[0]) < 1e-12 and rel_l2(got[2], ref[2]) < 1e-12
+
+
+def test_mass_conservation_on_gpu():
+    n, dx = 4099, 0.1
+    U = inputs.random_state(42, n, dx)
+    got = gpu_run(n, 0.0, n * dx, 0, 500.0, U, 0.01, 300)
+    assert abs(math.fsum(got[0]) - math.fsum(U[0])) <= 1e-13 * math.fsum(U[0])
+
+
+def test_suggest_dt_matches_oracle():
+    n = 5000
+    x, dx = inputs.cell_centres(n, -50.0, 50.0)
+    U = inputs.solitary(x, 1.0, 0.2, 0.0, period=100.0)
+    for cfl, mcfl in ((2.0, 0.5), (1e9, 0.5), (4.0, 0.0)):
+        with S().Solver(n, -50.0, 50.0, 0, lam=700.0) as s:
+            s.set_state(*(dev(u) for u in U))
+            dt = s.suggest_dt(cfl, mcfl)
+        ref, _, _ = oracle.suggest_dt(oracle.Params(n, dx, 0, lam=700.0), U, cfl, mcfl)
+        assert abs(dt - ref) <= 1e-14 * ref
+
+
+def test_device_errors_are_reported():
+    n, dx = 600, 0.1
+    U = list(inputs.random_state(5, n, dx))
+    U[0] = U[0].copy()
+    U[0][100] = -0.5
+    with S().Solver(n, 0.0, n * dx, 0, lam=100.0) as s:
+        s.set_state(*(dev(u) for u in U))
+        with pytest.raises(S().HsgnError) as e:
+            s.run(0.01, 1)
+        assert e.value.code == 3
+        # the error word is cleared; a good state runs again
+        s.set_state(*(dev(u) for u in inputs.random_state(6, n, dx)))
+        s.run(0.01, 2)
+    with S().Solver(n, 0.0, n * dx, 0, lam=100.0) as s:
+        with pytest.raises(S().HsgnError):
+            s.step(-1.0)
+        with pytest.raises(S().HsgnError):
+            s.step(float("nan"))
+
+
+def test_adjoint_reports_unimplemented():
+    with S().Solver(16, 0.0, 1.6, 0, lam=1.0) as s:
+        rc = S().load().hsgn_adjoint(s._h, 0.1, 1, 0, None, None, None, None, None)
+        assert rc == 6
