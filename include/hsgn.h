@@ -162,6 +162,32 @@ int hsgn_tridiag_solve(int64_t n, int32_t periodic, const double* a, const doubl
                        const double* c, const double* d, double* x, void* workspace,
                        size_t workspace_bytes, void* stream);
 
+/* ---------------------------------------------------------------------------
+ * Tridiagonal solve without any allocation. The paper has no counterpart; this
+ * entry point exists for callers that cannot call cudaMalloc: host loops with a
+ * latency budget (cudaMalloc and cudaFree may block and synchronise the device)
+ * and programs whose device memory belongs to another allocator (for example
+ * PyTorch's caching allocator), which cannot hand raw cudaMalloc'd scratch to a
+ * library. It solves the same system as hsgn_tridiag_solve, with the same
+ * arguments minus the workspace, and gives the same result.
+ *
+ * Scratch: one file-scope device array of HSGN_TRIDIAG_NOALLOC_SCRATCH_BYTES
+ * (about 6 MiB) inside the library; every GPU that loads the library keeps it
+ * until the process exits. Sizes: 1 <= n <= HSGN_TRIDIAG_NOALLOC_MAX_N;
+ * larger n returns HSGN_ERR_INVALID_ARG before any device work.
+ * Set-up: the first call on each device, with that device current, looks up
+ * the device address of the array (cudaGetSymbolAddress); make that first call
+ * before any stream capture. All calls share the one array, which keeps the
+ * contents of the previous call; the call clears its error word itself, and
+ * every other scratch value is written before it is read. Calls that overlap
+ * on the GPU (other streams or threads) race on the array and must not be
+ * issued. No cudaMalloc, cudaFree or allocating library routine is called.
+ * Synchronises `stream` and reports device errors like hsgn_tridiag_solve.
+ * --------------------------------------------------------------------------- */
+#define HSGN_TRIDIAG_NOALLOC_MAX_N 262144
+int hsgn_tridiag_solve_noalloc(int64_t n, int32_t periodic, const double* a, const double* b,
+                               const double* c, const double* d, double* x, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -9,6 +9,7 @@
 #include <cstdint>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -581,3 +582,63 @@ int hsgn_tridiag_solve(int64_t n, int32_t periodic, const double* a, const doubl
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// No-allocation variant of the tridiagonal solve (declared in include/hsgn.h).
+// The scratch is a file-scope device array; host code looks up its device
+// address once per device (the array's name is only a host-side stand-in).
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr int64_t kNoAllocMaxN = HSGN_TRIDIAG_NOALLOC_MAX_N;
+constexpr int64_t kNoAllocBlocks = (kNoAllocMaxN + GS - 1) / GS;
+static_assert(kNoAllocBlocks <= RMAX, "the separator system must fit one CTA");
+// error word + the one-level workspace of the recursive solve (see rows_ws_bytes)
+constexpr size_t kNoAllocBytes =
+    kAlign + (3 * kNoAllocMaxN * sizeof(double) + kAlign - 1) / kAlign * kAlign +
+    (BLK_STRIDE * kNoAllocBlocks * sizeof(double) + kAlign - 1) / kAlign * kAlign +
+    (4 * kNoAllocBlocks * sizeof(double) + kAlign - 1) / kAlign * kAlign +
+    (kNoAllocBlocks * sizeof(double) + kAlign - 1) / kAlign * kAlign;
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mu;
+void* g_noalloc_ptr[kMaxDevices] = {};
+
+// Device address of the scratch array on the current device (looked up on
+// the first call per device).
+int noalloc_scratch(void** out) {
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
+        cudaGetLastError();
+        return HSGN_ERR_CUDA;
+    }
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+        void* p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) {
+            cudaGetLastError();
+            return HSGN_ERR_CUDA;
+        }
+        g_noalloc_ptr[dev] = p;
+    }
+    *out = g_noalloc_ptr[dev];
+    return HSGN_OK;
+}
+
+}  // namespace
+
+extern "C" int hsgn_tridiag_solve_noalloc(int64_t n, int32_t periodic, const double* a,
+                                          const double* b, const double* c, const double* d,
+                                          double* x, void* stream) {
+    if (n < 1 || n > kNoAllocMaxN || !a || !b || !c || !d || !x) return HSGN_ERR_INVALID_ARG;
+    size_t need = 0;
+    if (hsgn_tridiag_workspace_bytes(n, &need) != HSGN_OK || need > kNoAllocBytes)
+        return HSGN_ERR_INVALID_ARG;
+    void* ws = nullptr;
+    const int rc = noalloc_scratch(&ws);
+    if (rc != HSGN_OK) return rc;
+    // same launch sequence as hsgn_tridiag_solve; it clears the error word first
+    return hsgn_tridiag_solve(n, periodic, a, b, c, d, x, ws, kNoAllocBytes, stream);
+}

@@ -209,3 +209,19 @@ def tridiag_solve(a, b, c, d, periodic: bool, stream=None):
                                    _ptr(x), ctypes.c_void_p(aligned), ctypes.c_size_t(nbytes),
                                    _stream(stream)), "hsgn_tridiag_solve")
     return x
+
+
+NOALLOC_MAX_N = 262144
+
+
+def tridiag_solve_noalloc(a, b, c, d, periodic: bool, out=None, stream=None):
+    """Same solve as tridiag_solve through the entry point that allocates
+    nothing (fixed device scratch inside the library, n <= NOALLOC_MAX_N)."""
+    lib = load()
+    f = lib.hsgn_tridiag_solve_noalloc
+    f.argtypes = [_I64, ctypes.c_int32, _P, _P, _P, _P, _P, _P]
+    f.restype = ctypes.c_int
+    x = torch.empty_like(d) if out is None else out
+    _check(f(int(b.numel()), int(bool(periodic)), _ptr(a), _ptr(b), _ptr(c), _ptr(d), _ptr(x),
+             _stream(stream)), "hsgn_tridiag_solve_noalloc")
+    return x
