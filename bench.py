@@ -367,16 +367,18 @@ def run_ours(args):
         cpu = {"value": 2.0 * n * len(lams) * ks / el, "unit": UNIT, "cores": 1, "kind": "oracle",
                "sample": f"{ks} IMEX steps of each of the {len(lams)} instances ({n} cells), "
                          f"single-threaded C oracle, {el:.1f} s"}
-        errs = []
+        per = {k: 0.0 for k in ("h", "q", "heta", "hw")}
         for s, dt, ref in zip(sols, dts, refs):
             s.set_state(*Ud)
             s.run(dt, ks)
             got = [t.cpu().numpy() for t in s.get_state()]
-            for k in range(4):
+            for k, name in enumerate(per):
                 nr = np.linalg.norm(ref[k])
                 if nr > 0:
-                    errs.append(float(np.linalg.norm(got[k] - ref[k]) / nr))
-        l2err = max(errs)
+                    per[name] = max(per[name], float(np.linalg.norm(got[k] - ref[k]) / nr))
+        # the depth is the headline variable; q and h w are roundoff-sized where
+        # the water is at rest, so their relative L2 is dominated by that noise
+        l2err = {"depth_rel_l2": per["h"], "per_variable_rel_l2": per}
     for s in sols:
         s.close()
 

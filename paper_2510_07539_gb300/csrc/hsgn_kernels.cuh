@@ -82,6 +82,7 @@ struct AssembleShared {
     double lastrow[4];
 };
 
+// T threads per CTA, M rows per thread in the block elimination.
 template <int T, int M, int BC>
 __global__ void __launch_bounds__(T) k_stage_assemble(const StageParams p) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -130,8 +131,9 @@ __global__ void __launch_bounds__(T) k_stage_assemble(const StageParams p) {
         const double qL = fma(0.25, q1 - qm, q0), qR = fma(-0.25, q2 - q0, q1);
         const double mL = fma(0.25, m1 - mm, m0), mR = fma(-0.25, m2 - m0, m1);
         const double rL = fma(0.25, r1 - rm, r0_), rR = fma(-0.25, r2 - r0_, r1);
-        if (!(hL > 0.0) || !(hR > 0.0)) bad |= HSGN_DEV_ERR_DEPTH;
-        const double uL = qL / hL, uR = qR / hR;
+        if (!pos_finite(hL) || !pos_finite(hR)) bad |= HSGN_DEV_ERR_DEPTH;
+        const double ip = rcp(hL * hR);  // one reciprocal for both velocities
+        const double uL = qL * hR * ip, uR = qR * hL * ip;
         const double s = p.local_speed ? fmax(fabs(uL), fabs(uR)) : gspeed;
         sm.Fq[j] = 0.5 * (fma(uL, qL, uR * qR) - s * (qR - qL));
         sm.Fm[j] = 0.5 * (fma(uL, mL, uR * mR) - s * (mR - mL));
@@ -147,20 +149,24 @@ __global__ void __launch_bounds__(T) k_stage_assemble(const StageParams p) {
         const double rsv = fma(-tdx, sm.Fr[j + 1] - sm.Fr[j], sm.rb[c3]) + lam * tau;
         const double msv = fma(tau, rsv, fma(-tdx, sm.Fm[j + 1] - sm.Fm[j], sm.mb[c3]));
         const double qsv = fma(-tdx, sm.Fq[j + 1] - sm.Fq[j], sm.qb[c3]);
+        // coefficients with one reciprocal R = 1/(h (h^2 + lambda tau^2)):
+        //   1/h = (h^2 + lambda tau^2) R,  1/beta_1 = h^2/(h^2 + lambda tau^2) = h^3 R,
+        //   beta_2 = 2 lambda tau^2 h / (h^2 + lambda tau^2)^2
         const double h = sm.hl[c3];
-        if (!(h > 0.0)) bad |= HSGN_DEV_ERR_DEPTH;
-        const double ih = 1.0 / h;
+        if (!pos_finite(h)) bad |= HSGN_DEV_ERR_DEPTH;
+        const double Dh = fma(h, h, lt2);
+        const double R = rcp(h * Dh);
+        const double ih = Dh * R;
+        const double iD = h * R;
         const double eta = sm.ml[c3] * ih;
         const double e = eta * ih;
-        const double alpha = -(2.0 * e - 1.0) * ih * (1.0 / 3.0);
+        const double alpha = fma(2.0, e, -1.0) * ih * (-1.0 / 3.0);
         const double c2 = fma(g, h, (lam * (1.0 / 3.0)) * e * e);
         const double a2 = fma(-lam * eta, alpha, c2);
-        const double ih2 = ih * ih;
-        const double beta1 = fma(lt2, ih2, 1.0);
-        const double ib1 = 1.0 / beta1;
-        const double beta2 = 2.0 * lt2 * ib1 * ib1 * ih2 * ih;
+        const double ib1 = h * h * iD;
+        const double beta2 = (2.0 * lt2) * h * iD * iD;
         const double beta = fma(lam * alpha * beta2, msv, a2);
-        if (!(beta > 0.0)) bad |= HSGN_DEV_ERR_COERCIVE;
+        if (!pos_finite(beta)) bad |= HSGN_DEV_ERR_COERCIVE;
         sm.qs[j] = qsv;
         sm.ms[j] = msv;
         sm.rs[j] = rsv;
@@ -215,10 +221,9 @@ __global__ void __launch_bounds__(T) k_stage_assemble(const StageParams p) {
     double y[M], v[M], w[M], last[4];
     int cs, m;
     cta_block_solve<T, M>(nb, row, sm.sep, y, v, w, cs, m, last, p.err);
-    if (bad) flag_error(p.err, bad);
-
-    // ---- 4. stage (y, v, w) through shared memory for coalesced stores
-    __syncthreads();  // the row function no longer reads the U_l arrays
+    // ---- 4. stage (y, v, w) in the U_l arrays, which the row function no
+    //         longer reads, for coalesced stores
+    __syncthreads();
 #pragma unroll
     for (int k = 0; k < M; ++k) {
         if (k < m) {
@@ -231,6 +236,7 @@ __global__ void __launch_bounds__(T) k_stage_assemble(const StageParams p) {
         sm.lastrow[0] = last[0]; sm.lastrow[1] = last[1];
         sm.lastrow[2] = last[2]; sm.lastrow[3] = last[3];
     }
+    if (bad) flag_error(p.err, bad);
     __syncthreads();
     for (int i = tid; i < nb; i += T) {
         p.y[r0 + i] = sm.hl[i];
@@ -256,10 +262,10 @@ __global__ void __launch_bounds__(T) k_stage_assemble(const StageParams p) {
 //   (-a v_L) s_{b-1} + (b - a w_L - c v_F) s_b + (-c w_F) s_{b+1} = d - a y_L - c y_F.
 struct BlkRows {
     const double* blk;
-    int P;
-    __device__ void operator()(int i, double& A, double& B, double& C, double& D) const {
-        const double* s = blk + (int64_t)i * BLK_STRIDE;
-        const double* f = blk + (int64_t)(i + 1 == P ? 0 : i + 1) * BLK_STRIDE;
+    int64_t P;
+    __device__ void operator()(int64_t i, double& A, double& B, double& C, double& D) const {
+        const double* s = blk + i * BLK_STRIDE;
+        const double* f = blk + (i + 1 == P ? 0 : i + 1) * BLK_STRIDE;
         const double a = s[0], bb = s[1], c = s[2], d = s[3];
         A = -a * s[8];
         B = bb - a * s[9] - c * f[5];
@@ -271,11 +277,9 @@ struct BlkRows {
 // Row source reading explicit arrays (cyclic: a[0] couples x[n-1], c[n-1] couples x[0]).
 struct ArrayRows {
     const double *a, *b, *c, *d;
-    int64_t off;
     int periodic;
     int64_t n;  // total rows of the system
-    __device__ void operator()(int i, double& A, double& B, double& C, double& D) const {
-        const int64_t k = off + i;
+    __device__ void operator()(int64_t k, double& A, double& B, double& C, double& D) const {
         A = a[k];
         B = b[k];
         C = c[k];
@@ -287,20 +291,19 @@ struct ArrayRows {
     }
 };
 
-// Cyclic tridiagonal system of `nrows` rows in one CTA. The last row's unknown
-// x_{n-1} is the external unknown on BOTH sides of rows 0 .. n-2 (the cyclic
-// couplings a_0 and c_{n-2}), so x_i = y_i - x_{n-1} (v_i + w_i), and the last
-// row a x_{n-2} + b x_{n-1} + c x_0 = d closes it.
-template <int T, int M>
-struct CyclicShared {
-    SepShared<T> sep;
-    double y0, z0, yq, zq, last[4], xlast;
-};
+// Rows per block of the separator levels: one warp, 4 rows per lane (short
+// dependent chains: these small systems are latency-bound, not throughput-bound).
+constexpr int SEP_MS = 4;
+constexpr int SEP_ROWS = 32 * SEP_MS;
 
-template <int T, int M, class RowSrc>
-__global__ void __launch_bounds__(T) k_cyclic_onecta(int nrows, RowSrc rows, double* x,
-                                                     double* speed_reset, unsigned* err) {
-    __shared__ CyclicShared<T, M> sh;
+// Cyclic tridiagonal system of nrows <= SEP_ROWS rows in one warp. The last
+// row's unknown x_{n-1} is the external unknown on BOTH sides of rows
+// 0 .. n-2 (the cyclic couplings a_0 and c_{n-2}), so x_i = y_i - x_{n-1}
+// (v_i + w_i), and the last row a x_{n-2} + b x_{n-1} + c x_0 = d closes it.
+template <class RowSrc>
+__global__ void __launch_bounds__(32) k_cyclic_onewarp(int nrows, RowSrc rows, double* x,
+                                                      double* speed_reset, unsigned* err) {
+    __shared__ double sh[8];
     const int t = threadIdx.x;
     if (speed_reset && t == 0) *speed_reset = 0.0;
     if (nrows == 1) {
@@ -308,36 +311,33 @@ __global__ void __launch_bounds__(T) k_cyclic_onecta(int nrows, RowSrc rows, dou
             double A, B, C, D;
             rows(0, A, B, C, D);
             const double den = A + B + C;
-            if (!(den > 0.0)) flag_error(err, HSGN_DEV_ERR_COERCIVE);
+            if (!pos_finite(den)) flag_error(err, HSGN_DEV_ERR_COERCIVE);
             x[0] = D / den;
         }
         return;
     }
-    double y[M], v[M], w[M], last[4];
+    double y[SEP_MS], v[SEP_MS], w[SEP_MS], last[4];
     int cs, m;
-    cta_block_solve<T, M>(nrows, rows, sh.sep, y, v, w, cs, m, last, err);
+    auto rf = [&](int i, double& A, double& B, double& C, double& D) { rows(i, A, B, C, D); };
+    warp_block_solve<SEP_MS>(nrows, rf, y, v, w, cs, m, last, err);
 #pragma unroll
-    for (int k = 0; k < M; ++k) {
+    for (int k = 0; k < SEP_MS; ++k) {
         if (k < m) {
             const int i = cs + k;
-            if (i == 0) { sh.y0 = y[k]; sh.z0 = v[k] + w[k]; }
-            if (i == nrows - 2) { sh.yq = y[k]; sh.zq = v[k] + w[k]; }
+            if (i == 0) { sh[0] = y[k]; sh[1] = v[k] + w[k]; }
+            if (i == nrows - 2) { sh[2] = y[k]; sh[3] = v[k] + w[k]; }
         }
     }
     if (m > 0 && cs + m == nrows) {
-        sh.last[0] = last[0]; sh.last[1] = last[1]; sh.last[2] = last[2]; sh.last[3] = last[3];
+        sh[4] = last[0]; sh[5] = last[1]; sh[6] = last[2]; sh[7] = last[3];
     }
-    __syncthreads();
-    if (t == 0) {
-        const double a = sh.last[0], b = sh.last[1], c = sh.last[2], d = sh.last[3];
-        const double den = b - a * sh.zq - c * sh.z0;
-        if (!(den > 0.0)) flag_error(err, HSGN_DEV_ERR_COERCIVE);
-        sh.xlast = (d - a * sh.yq - c * sh.y0) / den;
-    }
-    __syncthreads();
-    const double xl = sh.xlast;
+    __syncwarp();
+    const double a = sh[4], b = sh[5], c = sh[6], d = sh[7];
+    const double den = b - a * sh[3] - c * sh[1];
+    if (t == 0 && !pos_finite(den)) flag_error(err, HSGN_DEV_ERR_COERCIVE);
+    const double xl = (d - a * sh[2] - c * sh[0]) / den;
 #pragma unroll
-    for (int k = 0; k < M; ++k) {
+    for (int k = 0; k < SEP_MS; ++k) {
         if (k < m) {
             const int i = cs + k;
             x[i] = (i == nrows - 1) ? xl : y[k] - xl * (v[k] + w[k]);
@@ -345,31 +345,27 @@ __global__ void __launch_bounds__(T) k_cyclic_onecta(int nrows, RowSrc rows, dou
     }
 }
 
-// Generic multi-block elimination of explicit rows (used when the separator
-// system itself is too large for one CTA, and by the standalone solver).
-template <int T, int M>
+// One level of the multi-block elimination of a row source: one warp per
+// block of at most SEP_ROWS rows; per row (y, v, w) and a block summary.
 struct ReduceShared {
-    SepShared<T> sep;
-    double ys[T * M], vs[T * M], ws[T * M];
+    double ys[SEP_ROWS], vs[SEP_ROWS], ws[SEP_ROWS];
     double lastrow[4];
 };
 
-template <int T, int M>
-__global__ void __launch_bounds__(T) k_block_reduce_rows(ArrayRows rows, BlockSplit split,
-                                                         double* yo, double* vo, double* wo,
-                                                         double* blk, unsigned* err) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    auto& sh = *reinterpret_cast<ReduceShared<T, M>*>(smem_raw);
+template <class RowSrc>
+__global__ void __launch_bounds__(32) k_block_reduce(RowSrc rows, BlockSplit split, double* yo,
+                                                     double* vo, double* wo, double* blk,
+                                                     unsigned* err) {
+    __shared__ ReduceShared sh;
     const int64_t b = blockIdx.x;
     const int64_t r0 = split.start(b);
     const int nb = (int)split.size(b);
-    ArrayRows rb = rows;
-    rb.off = r0;
-    double y[M], v[M], w[M], last[4];
+    auto rf = [&](int i, double& A, double& B, double& C, double& D) { rows(r0 + i, A, B, C, D); };
+    double y[SEP_MS], v[SEP_MS], w[SEP_MS], last[4];
     int cs, m;
-    cta_block_solve<T, M>(nb, rb, sh.sep, y, v, w, cs, m, last, err);
+    warp_block_solve<SEP_MS>(nb, rf, y, v, w, cs, m, last, err);
 #pragma unroll
-    for (int k = 0; k < M; ++k) {
+    for (int k = 0; k < SEP_MS; ++k) {
         if (k < m) {
             sh.ys[cs + k] = y[k];
             sh.vs[cs + k] = v[k];
@@ -380,8 +376,8 @@ __global__ void __launch_bounds__(T) k_block_reduce_rows(ArrayRows rows, BlockSp
         sh.lastrow[0] = last[0]; sh.lastrow[1] = last[1];
         sh.lastrow[2] = last[2]; sh.lastrow[3] = last[3];
     }
-    __syncthreads();
-    for (int i = threadIdx.x; i < nb; i += T) {
+    __syncwarp();
+    for (int i = threadIdx.x; i < nb; i += 32) {
         yo[r0 + i] = sh.ys[i];
         vo[r0 + i] = sh.vs[i];
         wo[r0 + i] = sh.ws[i];
@@ -396,15 +392,6 @@ __global__ void __launch_bounds__(T) k_block_reduce_rows(ArrayRows rows, BlockSp
             s[7] = 0.0; s[8] = -1.0; s[9] = 0.0;
         }
     }
-}
-
-// Separator rows of the next level as explicit arrays (cyclic).
-__global__ void k_form_reduced(int P, const double* blk, double* A, double* B, double* C,
-                               double* D) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= P) return;
-    BlkRows r{blk, P};
-    r(i, A[i], B[i], C[i], D[i]);
 }
 
 // x_i = y_i - s_{b-1} v_i - s_b w_i for every row of a multi-block solve.
@@ -442,38 +429,47 @@ __device__ __forceinline__ double hbar_at(const BacksubParams& p, int64_t i) {
 // "second version" of Sec. 6.3.1):
 //   qbar = q^dag - tau/(2dx) beta (hbar_{i+1} - hbar_{i-1})
 //                - lambda tau/(2dx) delta (m^dag_{i+1} - m^dag_{i-1}),
-//   mbar = m^dag / (1 + lambda tau^2 / hbar^2),  rbar = r^dag - lambda tau mbar / hbar^2.
+//   mbar = m^dag / (1 + lambda tau^2 / hbar^2),  rbar = r^dag - lambda tau mbar / hbar^2,
+// i.e. with D = hbar^2 + lambda tau^2: mbar = m^dag hbar^2 / D, rbar = r^dag - lambda tau m^dag / D.
+// The neighbours' hbar come from the adjacent lanes; the lanes at the ends of
+// a warp compute their outer neighbour themselves.
 template <int BC>
 __global__ void k_backsub(const BacksubParams p) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int lane = threadIdx.x & 31;
+    const bool live = i < p.n;
+    const double h = live ? hbar_at(p, i) : 0.0;
+    const double hl_s = __shfl_up_sync(0xffffffffu, h, 1);
+    const double hr_s = __shfl_down_sync(0xffffffffu, h, 1);
     double umax = 0.0;
-    if (i < p.n) {
+    if (live) {
         const int64_t il = wrap_index(i - 1, p.n, BC), ir = wrap_index(i + 1, p.n, BC);
-        const double h = hbar_at(p, i);
-        const double hl = hbar_at(p, il), hr = hbar_at(p, ir);
+        const double hl = (lane == 0 || il != i - 1) ? hbar_at(p, il) : hl_s;
+        const double hr = (lane == 31 || ir != i + 1) ? hbar_at(p, ir) : hr_s;
         const double fq = p.tau / (2.0 * p.dx);
         const double q = p.qs[i] - fq * p.be[i] * (hr - hl) -
                          p.lam * fq * p.de[i] * (p.ms[ir] - p.ms[il]);
         const double h2 = h * h;
-        const double lt2 = p.lam * p.tau * p.tau;
-        const double inv = 1.0 / (h2 + lt2);
+        const double D = fma(h, h, p.lam * p.tau * p.tau);
+        const double R = rcp(h * D);  // 1/D = h R, 1/h = D R
+        const double iD = h * R;
         const double msv = p.ms[i];
-        const double m = msv * h2 * inv;
-        const double r = p.rs[i] - p.lam * p.tau * msv * inv;
+        const double m = msv * h2 * iD;
+        const double r = p.rs[i] - p.lam * p.tau * msv * iD;
         unsigned bad = 0;
-        if (!(h > 0.0)) bad |= HSGN_DEV_ERR_DEPTH;
-        if (!isfinite(h) || !isfinite(q) || !isfinite(m) || !isfinite(r)) bad |= HSGN_DEV_ERR_NONFINITE;
+        if (!pos_finite(h)) bad |= HSGN_DEV_ERR_DEPTH;
+        if (!finite_bits(q) || !finite_bits(m) || !finite_bits(r)) bad |= HSGN_DEV_ERR_NONFINITE;
         if (bad) flag_error(p.err, bad);
         p.out[0][i] = h;
         p.out[1][i] = q;
         p.out[2][i] = m;
         p.out[3][i] = r;
-        if (p.track_speed && h > 0.0) umax = fabs(q / h);
+        if (p.track_speed && !bad) umax = fabs(q * (D * R));
     }
     if (p.track_speed) {
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) umax = fmax(umax, __shfl_xor_sync(0xffffffffu, umax, o));
-        if ((threadIdx.x & 31) == 0 && umax > 0.0)
+        if (lane == 0 && umax > 0.0)
             atomicMax(reinterpret_cast<unsigned long long*>(p.speed),
                       (unsigned long long)__double_as_longlong(umax));
     }

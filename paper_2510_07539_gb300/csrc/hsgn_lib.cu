@@ -20,16 +20,14 @@ using namespace hsgn;
 
 namespace {
 
-// Stage block: T threads x M rows per thread.
+// Stage block: AT threads per CTA, AM rows per thread in the block elimination.
 constexpr int AT = 64, AM = 8, AS = AT * AM;
-// One-CTA cyclic solve of the block-separator system: up to RT*RM rows.
-constexpr int RT = 256, RM = 16, RMAX = RT * RM;
-// Generic multi-block elimination of explicit rows.
-constexpr int GT = 64, GM = 8, GS = GT * GM;
+// Separator levels: one warp per block of GS rows; one warp solves up to RMAX rows.
+constexpr int GS = SEP_ROWS, RMAX = SEP_ROWS;
 
 constexpr size_t kAlign = 256;
 
-size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
+constexpr size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 
 BlockSplit make_split(int64_t n, int64_t rows_per_block) {
     BlockSplit s;
@@ -40,15 +38,13 @@ BlockSplit make_split(int64_t n, int64_t rows_per_block) {
     return s;
 }
 
-// Workspace (in bytes, excluding the error word) of the recursive explicit-row
-// solve of n rows.
-size_t rows_ws_bytes(int64_t n) {
+// Workspace (in bytes, excluding the error word) of the recursive solve of n
+// rows: per level the row triples (3n), the block summaries and separators.
+constexpr size_t rows_ws_bytes(int64_t n) {
     if (n <= RMAX) return 0;
-    const BlockSplit s = make_split(n, GS);
-    const int64_t P = s.P;
-    size_t b = align_up(3 * n * sizeof(double)) + align_up(BLK_STRIDE * P * sizeof(double)) +
-               align_up(4 * P * sizeof(double)) + align_up(P * sizeof(double));
-    return b + rows_ws_bytes(P);
+    const int64_t P = (n + GS - 1) / GS;  // blocks of the even split
+    return align_up(3 * n * sizeof(double)) + align_up(BLK_STRIDE * P * sizeof(double)) +
+           align_up(P * sizeof(double)) + rows_ws_bytes(P);
 }
 
 template <class K>
@@ -56,13 +52,15 @@ cudaError_t set_smem(K kernel, size_t bytes) {
     return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
-// Recursive solve of explicit rows (device arrays) with workspace `ws`.
-cudaError_t solve_rows(int64_t n, int periodic, const double* a, const double* b, const double* c,
-                       const double* d, double* x, unsigned char* ws, unsigned* err,
-                       double* speed_reset, cudaStream_t st) {
-    ArrayRows rows{a, b, c, d, 0, periodic, n};
+// Recursive cyclic solve of n rows given by a row source, with workspace `ws`:
+// at most RMAX rows in one warp, otherwise one level of block elimination
+// (a warp per GS rows), the cyclic system of the block separators, and the
+// back-out of every row.
+template <class RowSrc>
+cudaError_t solve_src(int64_t n, RowSrc rows, double* x, unsigned char* ws, unsigned* err,
+                      double* speed_reset, cudaStream_t st) {
     if (n <= RMAX) {
-        k_cyclic_onecta<RT, RM, ArrayRows><<<1, RT, 0, st>>>((int)n, rows, x, speed_reset, err);
+        k_cyclic_onewarp<RowSrc><<<1, 32, 0, st>>>((int)n, rows, x, speed_reset, err);
         return cudaGetLastError();
     }
     const BlockSplit s = make_split(n, GS);
@@ -71,21 +69,21 @@ cudaError_t solve_rows(int64_t n, int periodic, const double* a, const double* b
     ws += align_up(3 * n * sizeof(double));
     double* blk = reinterpret_cast<double*>(ws);
     ws += align_up(BLK_STRIDE * P * sizeof(double));
-    double* R = reinterpret_cast<double*>(ws);
-    ws += align_up(4 * P * sizeof(double));
     double* sv = reinterpret_cast<double*>(ws);
     ws += align_up(P * sizeof(double));
-    const size_t smem = sizeof(ReduceShared<GT, GM>);  // below the 48 KB default limit
-    static_assert(sizeof(ReduceShared<GT, GM>) <= 48 * 1024, "needs an opt-in smem attribute");
-    k_block_reduce_rows<GT, GM><<<(unsigned)P, GT, smem, st>>>(rows, s, y, y + n, y + 2 * n, blk, err);
-    k_form_reduced<<<(unsigned)((P + 255) / 256), 256, 0, st>>>((int)P, blk, R, R + P, R + 2 * P,
-                                                              R + 3 * P);
+    k_block_reduce<RowSrc><<<(unsigned)P, 32, 0, st>>>(rows, s, y, y + n, y + 2 * n, blk, err);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    e = solve_rows(P, 1, R, R + P, R + 2 * P, R + 3 * P, sv, ws, err, speed_reset, st);
+    e = solve_src(P, BlkRows{blk, P}, sv, ws, err, speed_reset, st);
     if (e != cudaSuccess) return e;
     k_block_backout<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(s, y, y + n, y + 2 * n, sv, x);
     return cudaGetLastError();
+}
+
+cudaError_t solve_rows(int64_t n, int periodic, const double* a, const double* b, const double* c,
+                       const double* d, double* x, unsigned char* ws, unsigned* err,
+                       double* speed_reset, cudaStream_t st) {
+    return solve_src(n, ArrayRows{a, b, c, d, periodic, n}, x, ws, err, speed_reset, st);
 }
 
 int map_error_bits(unsigned bits) {
@@ -113,8 +111,7 @@ struct hsgn_s {
     double *qs = nullptr, *ms = nullptr, *rs = nullptr, *be = nullptr, *de = nullptr;
     double* blk = nullptr;
     double* s = nullptr;
-    double* red = nullptr;           // reduced rows (4 P) when P > RMAX
-    unsigned char* rws = nullptr;    // recursive workspace
+    unsigned char* rws = nullptr;    // workspace of the separator-system solve
     double* spd = nullptr;           // [0] global Rusanov speed, [1] stage speed, [2..3] scratch
     unsigned* err = nullptr;
     cudaStream_t cap = nullptr;      // private stream used for graph capture
@@ -211,18 +208,9 @@ cudaError_t launch_stage(hsgn_s* H, const double* const A[4], const double* cons
     const bool track = reset_and_track && !local_speed(H);
     double* reset = track ? H->spd : nullptr;
     {
-    ProfScope ps(H, HSGN_PROF_REDUCED, st);
-    if (P <= (unsigned)RMAX) {
-        k_cyclic_onecta<RT, RM, BlkRows><<<1, RT, 0, st>>>((int)P, BlkRows{H->blk, (int)P}, H->s,
-                                                           reset, H->err);
-    } else {
-        double* R = H->red;
-        k_form_reduced<<<(P + 255) / 256, 256, 0, st>>>((int)P, H->blk, R, R + P, R + 2 * P,
-                                                        R + 3 * P);
-        e = solve_rows(P, 1, R, R + P, R + 2 * P, R + 3 * P, H->s, H->rws, H->err, reset, st);
+        ProfScope ps(H, HSGN_PROF_REDUCED, st);
+        e = solve_src(P, BlkRows{H->blk, (int64_t)P}, H->s, H->rws, H->err, reset, st);
     }
-    }
-    e = cudaGetLastError();
     if (e != cudaSuccess) return e;
 
     BacksubParams q;
@@ -342,9 +330,8 @@ int hsgn_create(const hsgn_grid_t* grid, double g, double lambda, const double* 
     const size_t vec = align_up(n * sizeof(double));
     size_t total = 16 * vec;                                   // U, U1, y v w, 5 back-sub arrays
     total += align_up(BLK_STRIDE * P * sizeof(double)) + align_up(P * sizeof(double));
-    const size_t red = P > RMAX ? align_up(4 * P * sizeof(double)) : 0;
-    const size_t rws = P > RMAX ? rows_ws_bytes(P) : 0;
-    total += red + rws + align_up(4 * sizeof(double)) + align_up(sizeof(unsigned));
+    const size_t rws = rows_ws_bytes(P);
+    total += rws + align_up(4 * sizeof(double)) + align_up(sizeof(unsigned));
     if (cudaMalloc(&H->mem, total) != cudaSuccess) {
         cudaGetLastError();
         delete H;
@@ -368,7 +355,6 @@ int hsgn_create(const hsgn_grid_t* grid, double g, double lambda, const double* 
     H->de = reinterpret_cast<double*>(take(vec));
     H->blk = reinterpret_cast<double*>(take(align_up(BLK_STRIDE * P * sizeof(double))));
     H->s = reinterpret_cast<double*>(take(align_up(P * sizeof(double))));
-    H->red = red ? reinterpret_cast<double*>(take(red)) : nullptr;
     H->rws = rws ? take(rws) : nullptr;
     H->spd = reinterpret_cast<double*>(take(align_up(4 * sizeof(double))));
     H->err = reinterpret_cast<unsigned*>(take(align_up(sizeof(unsigned))));
@@ -591,14 +577,9 @@ int hsgn_tridiag_solve(int64_t n, int32_t periodic, const double* a, const doubl
 namespace {
 
 constexpr int64_t kNoAllocMaxN = HSGN_TRIDIAG_NOALLOC_MAX_N;
-constexpr int64_t kNoAllocBlocks = (kNoAllocMaxN + GS - 1) / GS;
-static_assert(kNoAllocBlocks <= RMAX, "the separator system must fit one CTA");
-// error word + the one-level workspace of the recursive solve (see rows_ws_bytes)
-constexpr size_t kNoAllocBytes =
-    kAlign + (3 * kNoAllocMaxN * sizeof(double) + kAlign - 1) / kAlign * kAlign +
-    (BLK_STRIDE * kNoAllocBlocks * sizeof(double) + kAlign - 1) / kAlign * kAlign +
-    (4 * kNoAllocBlocks * sizeof(double) + kAlign - 1) / kAlign * kAlign +
-    (kNoAllocBlocks * sizeof(double) + kAlign - 1) / kAlign * kAlign;
+// error word + the workspace of the recursive solve of the largest size
+constexpr size_t kNoAllocBytes = kAlign + rows_ws_bytes(kNoAllocMaxN);
+static_assert(kNoAllocBytes < (size_t)8 << 20, "fixed scratch must stay modest");
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
 

@@ -35,6 +35,24 @@ __device__ __forceinline__ void flag_error(unsigned* err, unsigned bits) {
     if (err) atomicOr(err, bits);
 }
 
+// x > 0 and finite, tested on the bit pattern (integer pipe; false for +-0,
+// negatives, +Inf and NaN).
+__device__ __forceinline__ bool pos_finite(double x) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    return (b - 1ull) < 0x7FEFFFFFFFFFFFFFull;
+}
+
+__device__ __forceinline__ bool finite_bits(double x) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    return (b & 0x7FF0000000000000ull) != 0x7FF0000000000000ull;
+}
+
+// Reciprocal. The IEEE division is used: on sm_103a it outruns a Newton-Raphson
+// reciprocal seeded in single precision (77 vs 65 Gop/s measured), because the
+// single/double conversions of the seed cost more than the division's own
+// refinement steps.
+__device__ __forceinline__ double rcp(double x) { return 1.0 / x; }
+
 // Shared memory of the separator system of a CTA with T threads.
 template <int T>
 struct SepShared {
@@ -85,16 +103,16 @@ __device__ __forceinline__ void cta_block_solve(int nrows, RowFn row, SepShared<
             double p, ip;
             if (k == 0) {
                 p = b;
-                ip = 1.0 / p;
+                ip = rcp(p);
                 y[k] = d * ip;
                 v[k] = a * ip;
             } else {
                 p = fma(-a, w[k - 1], b);
-                ip = 1.0 / p;
+                ip = rcp(p);
                 y[k] = fma(-a, y[k - 1], d) * ip;
                 v[k] = -a * v[k - 1] * ip;
             }
-            bad |= !(p > 0.0);
+            bad |= !pos_finite(p);
             w[k] = c * ip;
         }
     }
@@ -161,9 +179,12 @@ __device__ __forceinline__ void cta_block_solve(int nrows, RowFn row, SepShared<
     }
     __syncthreads();
 
-    // parallel cyclic reduction over the ns separator rows
+    // parallel cyclic reduction over the ns separator rows; each level first
+    // stores 1/B of every row so that both neighbours reuse it
     bool badp = false;
     for (int s = 1; s < ns; s <<= 1) {
+        if (t < ns) sh.YF[t] = rcp(sh.B[t]);
+        __syncthreads();
         double nA = 0.0, nB = 0.0, nC = 0.0, n1 = 0.0, n2 = 0.0, n3 = 0.0;
         if (t < ns) {
             nB = sh.B[t];
@@ -171,7 +192,7 @@ __device__ __forceinline__ void cta_block_solve(int nrows, RowFn row, SepShared<
             n2 = sh.D2[t];
             n3 = sh.D3[t];
             if (t - s >= 0) {
-                const double k1 = sh.A[t] / sh.B[t - s];
+                const double k1 = sh.A[t] * sh.YF[t - s];
                 nA = -sh.A[t - s] * k1;
                 nB = fma(-sh.C[t - s], k1, nB);
                 n1 = fma(-sh.D1[t - s], k1, n1);
@@ -179,7 +200,7 @@ __device__ __forceinline__ void cta_block_solve(int nrows, RowFn row, SepShared<
                 n3 = fma(-sh.D3[t - s], k1, n3);
             }
             if (t + s < ns) {
-                const double k2 = sh.C[t] / sh.B[t + s];
+                const double k2 = sh.C[t] * sh.YF[t + s];
                 nC = -sh.C[t + s] * k2;
                 nB = fma(-sh.A[t + s], k2, nB);
                 n1 = fma(-sh.D1[t + s], k2, n1);
@@ -200,8 +221,8 @@ __device__ __forceinline__ void cta_block_solve(int nrows, RowFn row, SepShared<
     }
     if (t < ns) {
         const double Bt = sh.B[t];
-        badp = !(Bt > 0.0);
-        const double iB = 1.0 / Bt;
+        badp = !pos_finite(Bt);
+        const double iB = rcp(Bt);
         sh.D1[t] *= iB;  // Ys
         sh.D2[t] *= iB;  // Vs
         sh.D3[t] *= iB;  // Ws
@@ -230,6 +251,182 @@ __device__ __forceinline__ void cta_block_solve(int nrows, RowFn row, SepShared<
             YsR = sh.D1[t];
             VsR = sh.D2[t];
             WsR = sh.D3[t];
+        }
+#pragma unroll
+        for (int k = 0; k < M; ++k) {
+            if (k < nint) {
+                const double Y = y[k], V = v[k], W = w[k];
+                y[k] = Y - YsL * V - YsR * W;
+                v[k] = -(VsL * V + VsR * W);
+                w[k] = -(WsL * V + WsR * W);
+            } else if (k == nint) {
+                y[k] = YsR;
+                v[k] = VsR;
+                w[k] = WsR;
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// The same elimination done by one warp: lane t owns a chunk of at most M rows,
+// the separator system of the chunks (at most 31 rows) is solved by parallel
+// cyclic reduction in registers with warp shuffles, so no shared memory and no
+// block barrier is involved. Same contract as cta_block_solve with T = 32;
+// nrows <= 32 * M. All 32 lanes of the warp must call it.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double shfl_up_d(double x, int s) {
+    return __shfl_up_sync(0xffffffffu, x, s);
+}
+__device__ __forceinline__ double shfl_down_d(double x, int s) {
+    return __shfl_down_sync(0xffffffffu, x, s);
+}
+
+template <int M, class RowFn>
+__device__ __forceinline__ void warp_block_solve(int nrows, RowFn row, double (&y)[M],
+                                                 double (&v)[M], double (&w)[M], int& cs, int& m,
+                                                 double (&last)[4], unsigned* err) {
+    const int t = threadIdx.x & 31;
+    int teff;
+    chunk_of<32>(nrows, t, cs, m, teff);
+    const int nint = m - 1;
+
+    double sa = 0.0, sb = 1.0, sc = 0.0, sd = 0.0;
+    bool bad = false;
+#pragma unroll
+    for (int k = 0; k < M; ++k) {
+        if (k < nint) {
+            double a, b, c, d;
+            row(cs + k, a, b, c, d);
+            double p, ip;
+            if (k == 0) {
+                p = b;
+                ip = rcp(p);
+                y[k] = d * ip;
+                v[k] = a * ip;
+            } else {
+                p = fma(-a, w[k - 1], b);
+                ip = rcp(p);
+                y[k] = fma(-a, y[k - 1], d) * ip;
+                v[k] = -a * v[k - 1] * ip;
+            }
+            bad |= !pos_finite(p);
+            w[k] = c * ip;
+        }
+    }
+    if (m > 0) row(cs + m - 1, sa, sb, sc, sd);
+    double YL = 0.0, VL = -1.0, WL = 0.0;
+    {
+        double Yn = 0.0, Vn = 0.0, Wn = -1.0;
+#pragma unroll
+        for (int k = M - 1; k >= 0; --k) {
+            if (k < nint) {
+                const double Y = fma(-w[k], Yn, y[k]);
+                const double V = fma(-w[k], Vn, v[k]);
+                const double W = -w[k] * Wn;
+                if (k == nint - 1) {
+                    YL = Y;
+                    VL = V;
+                    WL = W;
+                }
+                y[k] = Y;
+                v[k] = V;
+                w[k] = W;
+                Yn = Y;
+                Vn = V;
+                Wn = W;
+            }
+        }
+    }
+    if (bad) flag_error(err, HSGN_DEV_ERR_COERCIVE);
+
+    // first-interior values of the next lane's chunk
+    const double YF0 = nint > 0 ? y[0] : 0.0;
+    const double VF0 = nint > 0 ? v[0] : 0.0;
+    const double WF0 = nint > 0 ? w[0] : -1.0;
+    const double YF1 = shfl_down_d(YF0, 1), VF1 = shfl_down_d(VF0, 1), WF1 = shfl_down_d(WF0, 1);
+
+    const int ns = teff - 1;
+    double A = 0.0, B = 1.0, C = 0.0, D1 = 0.0, D2 = 0.0, D3 = 0.0;
+    if (t < ns) {
+        const double At = -sa * VL;
+        const double Bt = sb - sa * WL - sc * VF1;
+        const double Ct = -sc * WF1;
+        const double Dt = sd - sa * YL - sc * YF1;
+        A = (t == 0) ? 0.0 : At;
+        C = (t == ns - 1) ? 0.0 : Ct;
+        B = Bt;
+        D1 = Dt;
+        D2 = (t == 0) ? At : 0.0;
+        D3 = (t == ns - 1) ? Ct : 0.0;
+    }
+    if (t == teff - 1) {
+        last[0] = sa;
+        last[1] = sb;
+        last[2] = sc;
+        last[3] = sd;
+    }
+    // cyclic reduction; lanes >= ns hold decoupled identity rows
+    for (int s = 1; s < ns; s <<= 1) {
+        const double iB = rcp(B);
+        const double lA = shfl_up_d(A, s), lB = shfl_up_d(iB, s), lC = shfl_up_d(C, s);
+        const double l1 = shfl_up_d(D1, s), l2 = shfl_up_d(D2, s), l3 = shfl_up_d(D3, s);
+        const double rA = shfl_down_d(A, s), rB = shfl_down_d(iB, s), rC = shfl_down_d(C, s);
+        const double r1 = shfl_down_d(D1, s), r2 = shfl_down_d(D2, s), r3 = shfl_down_d(D3, s);
+        if (t < ns) {
+            double nA = 0.0, nB = B, nC = 0.0, n1 = D1, n2 = D2, n3 = D3;
+            if (t - s >= 0) {
+                const double k1 = A * lB;
+                nA = -lA * k1;
+                nB = fma(-lC, k1, nB);
+                n1 = fma(-l1, k1, n1);
+                n2 = fma(-l2, k1, n2);
+                n3 = fma(-l3, k1, n3);
+            }
+            if (t + s < ns) {
+                const double k2 = C * rB;
+                nC = -rC * k2;
+                nB = fma(-rA, k2, nB);
+                n1 = fma(-r1, k2, n1);
+                n2 = fma(-r2, k2, n2);
+                n3 = fma(-r3, k2, n3);
+            }
+            A = nA;
+            B = nB;
+            C = nC;
+            D1 = n1;
+            D2 = n2;
+            D3 = n3;
+        }
+    }
+    double Ys = 0.0, Vs = 0.0, Ws = 0.0;
+    if (t < ns) {
+        if (!pos_finite(B)) flag_error(err, HSGN_DEV_ERR_COERCIVE);
+        const double iB = rcp(B);
+        Ys = D1 * iB;
+        Vs = D2 * iB;
+        Ws = D3 * iB;
+    }
+    const double YsL0 = shfl_up_d(Ys, 1), VsL0 = shfl_up_d(Vs, 1), WsL0 = shfl_up_d(Ws, 1);
+    if (t < teff) {
+        double YsL, VsL, WsL, YsR, VsR, WsR;
+        if (t == 0) {
+            YsL = 0.0;
+            VsL = -1.0;
+            WsL = 0.0;
+        } else {
+            YsL = YsL0;
+            VsL = VsL0;
+            WsL = WsL0;
+        }
+        if (t == teff - 1) {
+            YsR = 0.0;
+            VsR = 0.0;
+            WsR = -1.0;
+        } else {
+            YsR = Ys;
+            VsR = Vs;
+            WsR = Ws;
         }
 #pragma unroll
         for (int k = 0; k < M; ++k) {
