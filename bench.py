@@ -8,7 +8,9 @@ w = 0; one instance per relaxation parameter lambda in {10, 100, 1000}, each
 with its own dt = min(4 dx / nu_max, 0.5 dx / u_max) computed at t = 0
 (CFL_IMEX = 4, material CFL 0.5). One benchmark step advances all three
 instances by one IMEX step (two implicit stages each). Inputs are synthetic
-(seed-free closed forms); all arithmetic is FP64.
+(seed-free closed forms). The headline is the mixed-precision form (FP32
+increments, FP64 state and accumulation) with its error against the FP64
+oracle; the all-FP64 form is timed on the same workload and reported beside it.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -92,8 +94,9 @@ def config_dict(n, lams, dts, extra=None):
         "transition_width": "5 h0 (tanh)",
         "cfl_imex": 4.0,
         "mcfl": 0.5,
-        "scheme": "2-stage IMEX RK (printed tableau), FP64",
+        "scheme": "2-stage IMEX RK (printed tableau)",
         "rusanov_speed": "global max|u^n|",
+        "streams": "one CUDA stream per instance, joined every step",
         "l2_between_steps": f"flushed ({FLUSH_BYTES >> 20} MiB write) before every timed step",
     }
     if extra:
@@ -109,10 +112,10 @@ def source_sha() -> str:
     return h.hexdigest()[:16]
 
 
-def profiled_traffic_per_cell():
-    """DRAM bytes per cell of the dominant kernel from the committed ncu summary,
-    or None when the kernel sources changed since that capture."""
-    path = os.path.join(ROOT, "profiles", "ncu_stage_assemble.md")
+def profiled_traffic_per_cell(summary: str):
+    """DRAM bytes per cell of a kernel from its committed ncu summary, or None
+    when the kernel sources changed since that capture."""
+    path = os.path.join(ROOT, "profiles", summary)
     if not os.path.exists(path):
         return None
     txt = open(path).read()
@@ -224,6 +227,86 @@ def run_reference(args):
 # ---------------------------------------------------------------------------
 # GPU arm
 # ---------------------------------------------------------------------------
+def sep_launches(n: int) -> int:
+    """Kernel launches of the separator-system solve of n blocks (mirrors the
+    library: one warp for <= 128 rows, else reduce + recurse + back-out)."""
+    return 1 if n <= 128 else 2 + sep_launches((n + 127) // 128)
+
+
+def time_path(S, torch, flags, n, xl, xr, lams, Ud, steps, warmup, flush, stream, dist, clocks):
+    """K timed steps of the three-instance workload in one precision form."""
+    sols = [S.Solver(n, xl, xr, S.BC_TRANSMISSIVE, lam=l, flags=flags) for l in lams]
+    for s in sols:
+        s.set_state(*Ud)
+    dts = [s.suggest_dt(4.0, 0.5) for s in sols]
+    # the instances are independent: one CUDA stream each, forked from and
+    # joined back into the timing stream every step
+    side = [torch.cuda.Stream() for _ in sols]
+    fork = torch.cuda.Event()
+    joins = [torch.cuda.Event() for _ in sols]
+
+    def one_step():
+        fork.record(stream)
+        for s, dt, st, j in zip(sols, dts, side, joins):
+            st.wait_event(fork)
+            s.step(dt, stream=st)
+            j.record(st)
+        for j in joins:
+            stream.wait_event(j)
+
+    for _ in range(warmup):
+        one_step()
+    for s in sols:
+        s.check()
+        s.profile(True)
+        s.profile_read(reset=True)
+    ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    sampler = ClockSampler(clocks) if clocks else None
+    if sampler:
+        time.sleep(0.3)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    for k in range(steps):
+        flush.fill_(float(k))
+        ev0[k].record(stream)
+        one_step()
+        ev1[k].record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clk = sampler.stop() if sampler else None
+    for s in sols:
+        s.check()
+    ms = sum(a.elapsed_time(b) for a, b in zip(ev0, ev1))
+    prof = [s.profile_read(reset=True) for s in sols]
+    for s in sols:
+        s.profile(False)
+    if dist:
+        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    tot = {k: (sum(p[k][0] for p in prof), sum(p[k][1] for p in prof))
+           for k in ("assemble", "reduced", "backsub")}
+    return sols, dts, ms, tot, clk
+
+
+def l2_vs_oracle(sols, dts, Ud, refs, ks, np):
+    per = {k: 0.0 for k in ("h", "q", "heta", "hw")}
+    for s, dt, ref in zip(sols, dts, refs):
+        s.set_state(*Ud)
+        s.run(dt, ks)
+        got = [t.cpu().numpy() for t in s.get_state()]
+        for k, name in enumerate(per):
+            nr = np.linalg.norm(ref[k])
+            if nr > 0:
+                per[name] = max(per[name], float(np.linalg.norm(got[k] - ref[k]) / nr))
+    # the depth is the headline variable; q and h w are roundoff-sized where
+    # the water is at rest, so their relative L2 is dominated by that noise
+    return {"depth_rel_l2": per["h"], "per_variable_rel_l2": per, "steps": ks}
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -249,89 +332,66 @@ def run_ours(args):
     lams = [float(x) for x in args.lams.split(",")]
     n, dx, xl, xr, U, lams = workload(args.log2n, lams)
     Ud = [torch.tensor(u, device="cuda") for u in U]
-    sols = [S.Solver(n, xl, xr, S.BC_TRANSMISSIVE, lam=l) for l in lams]
-    for s in sols:
-        s.set_state(*Ud)
-    dts = [s.suggest_dt(4.0, 0.5) for s in sols]
     flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
     stream = torch.cuda.current_stream()
-
-    def one_step():
-        for s, dt in zip(sols, dts):
-            s.step(dt)
-
-    for _ in range(args.warmup):
-        one_step()
-    for s in sols:
-        s.check()
-    torch.cuda.synchronize()
-
     props = torch.cuda.get_device_properties(local)
     gpu_id = str(getattr(props, "uuid", local))
     if gpu_id and not gpu_id.startswith("GPU-") and len(gpu_id) >= 32:
         gpu_id = "GPU-" + gpu_id
-    for s in sols:
-        s.profile(True)
-        s.profile_read(reset=True)
-    ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    sampler = ClockSampler(gpu_id)
-    time.sleep(0.3)
-    if dist:
-        dist.barrier()
-    torch.cuda.synchronize()
-    for k in range(args.steps):
-        flush.fill_(float(k))
-        ev0[k].record(stream)
-        one_step()
-        ev1[k].record(stream)
-    torch.cuda.synchronize()
-    if dist:
-        dist.barrier()
-    clocks = sampler.stop()
-    for s in sols:
-        s.check()
-    ms = sum(a.elapsed_time(b) for a, b in zip(ev0, ev1))
-    prof = [s.profile_read(reset=True) for s in sols]
-    for s in sols:
-        s.profile(False)
-    if dist:
-        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-
-    units_rank = 2.0 * n * len(lams) * args.steps
-    value = units_rank * world / (ms / 1e3)
-    asm_ms = sum(p["assemble"][0] for p in prof)
-    asm_n = sum(p["assemble"][1] for p in prof)
-    red_ms = sum(p["reduced"][0] for p in prof)
-    bs_ms = sum(p["backsub"][0] for p in prof)
-    avg_asm = asm_ms / max(asm_n, 1)
-    achieved_tf = FLOPS_PER_CELL_ASSEMBLE * n / (avg_asm / 1e3) / 1e12
-    tpc = profiled_traffic_per_cell()
-    hbm_gbs = BYTES_PER_CELL_STAGE * units_rank / (ms / 1e3) / 1e9
     peaks = {}
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
     except Exception:
         pass
     hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
+    units_rank = 2.0 * n * len(lams) * args.steps
+
+    # ---- headline: mixed precision (FP32 increments, FP64 state)
+    msols, mdts, mms, mtot, clocks = time_path(S, torch, S.FLAG_MIXED, n, xl, xr, lams, Ud,
+                                              args.steps, args.warmup, flush, stream, dist,
+                                              gpu_id)
+    value = units_rank * world / (mms / 1e3)
+    avg_asm = mtot["assemble"][0] / max(mtot["assemble"][1], 1)
+    stage_ms = mms / (2 * len(lams) * args.steps)
+    kernel_gbs = BYTES_PER_CELL_STAGE * n / (avg_asm / 1e3) / 1e9
+    tpc = profiled_traffic_per_cell("ncu_mixed_assemble.md")
+    share_den = sum(v[0] for v in mtot.values())
     roofline = {
-        "bound": "alu",
-        "kernel": "k_stage_assemble (fluxes + assembly + block elimination)",
-        "achieved": achieved_tf, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-        "frac": achieved_tf / FP64_PEAK_TFLOPS,
-        "peak_source": "nominal dense FP64 of GB300 (1.25 TFLOP/s)",
+        "bound": "hbm",
+        "kernel": "k_mixed_assemble (fluxes + assembly + block elimination, FP32 increments)",
+        "achieved": kernel_gbs, "peak": hbm_peak, "unit": "GB/s",
+        "frac": kernel_gbs / hbm_peak,
+        "peak_source": "measured copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
         "traffic": tpc * n if tpc is not None else None,
         "kernel_avg_ms": avg_asm,
-        "kernel_share": {"assemble": asm_ms / (asm_ms + red_ms + bs_ms),
-                         "reduced": red_ms / (asm_ms + red_ms + bs_ms),
-                         "backsub": bs_ms / (asm_ms + red_ms + bs_ms)},
-        "hbm_effective_gbs": hbm_gbs,
-        "hbm_frac_of_measured": hbm_gbs / hbm_peak,
+        "kernel_share": {k: v[0] / share_den for k, v in mtot.items()},
+        "stage_avg_ms": stage_ms,
+        "stage_achieved_gbs": BYTES_PER_CELL_STAGE * n / (stage_ms / 1e3) / 1e9,
+        "stage_frac": BYTES_PER_CELL_STAGE * n / (stage_ms / 1e3) / 1e9 / hbm_peak,
+    }
+    launches = len(lams) * args.steps * 2 * (2 + sep_launches((n + 511) // 512))
+
+    # ---- the all-FP64 path on the same workload
+    fsols, fdts, fms, ftot, _ = time_path(S, torch, S.FLAG_FP64, n, xl, xr, lams, Ud,
+                                          args.steps, args.warmup, flush, stream, dist, None)
+    favg = ftot["assemble"][0] / max(ftot["assemble"][1], 1)
+    ftf = FLOPS_PER_CELL_ASSEMBLE * n / (favg / 1e3) / 1e12
+    fshare_den = sum(v[0] for v in ftot.values())
+    fp64 = {
+        "value": units_rank * world / (fms / 1e3), "unit": UNIT, "ms_per_step": fms / args.steps,
+        "dtype": "f64",
+        "roofline": {"bound": "alu", "kernel": "k_stage_assemble", "achieved": ftf,
+                     "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": ftf / FP64_PEAK_TFLOPS,
+                     "peak_source": "nominal dense FP64 of GB300 (1.25 TFLOP/s)",
+                     "traffic": (lambda t: t * n if t is not None else None)(
+                         profiled_traffic_per_cell("ncu_stage_assemble.md")),
+                     "kernel_avg_ms": favg,
+                     "kernel_share": {k: v[0] / fshare_den for k, v in ftot.items()},
+                     "hbm_frac_of_measured": BYTES_PER_CELL_STAGE * units_rank / (fms / 1e3)
+                     / 1e9 / hbm_peak},
     }
 
-    # ---- end to end through the C ABI with host buffers
+    # ---- end to end through the C ABI with host buffers (mixed path)
     e2e = None
     if not args.no_e2e:
         host_in = [[torch.tensor(u).pin_memory() for u in U] for _ in lams]
@@ -343,7 +403,7 @@ def run_ours(args):
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         for _ in range(k_e2e):
-            for s, dt, hi, ho in zip(sols, dts, host_in, host_out):
+            for s, dt, hi, ho in zip(msols, mdts, host_in, host_out):
                 s.set_state(*hi)
                 s.step(dt)
                 s.get_state(out=ho)
@@ -358,40 +418,33 @@ def run_ours(args):
         e2e = {"value": 2.0 * n * len(lams) * k_e2e * world / (ems / 1e3), "unit": UNIT,
                "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes, "steps": k_e2e}
 
-    # ---- CPU oracle baseline and L2 error of the GPU path against it
+    # ---- CPU oracle baseline and the error of both paths against it
     cpu = None
     l2err = None
     if rank == 0 and world == 1 and not args.no_cpu:
         ks = max(1, args.cpu_steps)
-        refs, el = oracle_steps(n, dx, U, lams, dts, ks)
+        refs, el = oracle_steps(n, dx, U, lams, mdts, ks)
         cpu = {"value": 2.0 * n * len(lams) * ks / el, "unit": UNIT, "cores": 1, "kind": "oracle",
                "sample": f"{ks} IMEX steps of each of the {len(lams)} instances ({n} cells), "
                          f"single-threaded C oracle, {el:.1f} s"}
-        per = {k: 0.0 for k in ("h", "q", "heta", "hw")}
-        for s, dt, ref in zip(sols, dts, refs):
-            s.set_state(*Ud)
-            s.run(dt, ks)
-            got = [t.cpu().numpy() for t in s.get_state()]
-            for k, name in enumerate(per):
-                nr = np.linalg.norm(ref[k])
-                if nr > 0:
-                    per[name] = max(per[name], float(np.linalg.norm(got[k] - ref[k]) / nr))
-        # the depth is the headline variable; q and h w are roundoff-sized where
-        # the water is at rest, so their relative L2 is dominated by that noise
-        l2err = {"depth_rel_l2": per["h"], "per_variable_rel_l2": per}
-    for s in sols:
+        l2err = l2_vs_oracle(msols, mdts, Ud, refs, ks, np)
+        fp64["l2_rel_err_vs_oracle"] = l2_vs_oracle(fsols, fdts, Ud, refs, ks, np)
+    for s in msols + fsols:
         s.close()
 
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": config_dict(n, lams, dts, {"parallelism": f"{world} independent replicas"}),
+            "warmup": args.warmup, "ms_per_step": mms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "mixed-f32/f64",
+            "data": "synthetic",
+            "config": config_dict(n, lams, mdts, {
+                "parallelism": f"{world} independent replicas",
+                "precision": "FP32 fluxes, coefficients and depth solve on increments; "
+                             "FP64 state, base differences and accumulation"}),
             "l2_rel_err_vs_oracle": l2err,
-            "l2_err_steps": args.cpu_steps if l2err is not None else None,
-            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
-            "gpu_launches": 6 * len(lams) * args.steps,
+            "roofline": roofline, "fp64_path": fp64, "cpu_baseline": cpu, "e2e": e2e,
+            "clocks": clocks, "gpu_launches": launches,
         }
         print(json.dumps(line), flush=True)
     if dist:

@@ -57,6 +57,11 @@ enum {
 
 /* flags of hsgn_create */
 #define HSGN_FP64 0x0          /* every operation in FP64 */
+#define HSGN_MIXED 0x1         /* fluxes, coefficients and the depth solve in FP32
+                                * on increments; state, base-state differences and
+                                * the accumulation in FP64; the depth is updated in
+                                * flux form (mass conserved to FP64 rounding).
+                                * hsgn_stage is not available in this form. */
 #define HSGN_RUSANOV_LOCAL 0x10 /* Rusanov speed max(|u^L|,|u^R|) per face instead
                                  * of the global max |u^n| of the step */
 
@@ -73,7 +78,8 @@ typedef struct hsgn_s* hsgn_handle_t;
 /* Create an instance: grid, gravity g > 0, relaxation parameter lambda >= 0
  * (Sec. 2.2, eq. (hSGN_eq)). `bathymetry` must be NULL (flat bottom; the
  * paper derives the semi-implicit scheme only for a flat bottom). Allocates
- * the state and workspace on the current device (about 17 doubles per cell).
+ * the state and workspace on the current device (about 17 doubles per cell in
+ * FP64, 4 doubles and 17 floats per cell with HSGN_MIXED).
  * On success *out owns them until hsgn_destroy. */
 int hsgn_create(const hsgn_grid_t* grid, double g, double lambda, const double* bathymetry,
                 int32_t flags, hsgn_handle_t* out);

@@ -31,13 +31,17 @@ constexpr int BC_TRANSMISSIVE = 1;
 // triples of the first row (F) and of the last interior row (L).
 constexpr int BLK_STRIDE = 10;
 
+// Neighbour index for offsets |i - j| <= n of an in-range j (all stencils here
+// reach at most 3 cells and n >= 3): one conditional add or subtract.
 __device__ __forceinline__ int64_t wrap_index(int64_t i, int64_t n, int bc) {
-    if (bc == BC_PERIODIC) {
-        int64_t k = i % n;
-        return k < 0 ? k + n : k;
-    }
+    if (bc == BC_PERIODIC) return i < 0 ? i + n : (i >= n ? i - n : i);
     return i < 0 ? 0 : (i >= n ? n - 1 : i);
 }
+
+// Shared-memory index with one pad word every 32: rows read by threads at a
+// stride of M words (the chunk mapping) then fall in distinct banks.
+__device__ __forceinline__ int pd(int i) { return i + (i >> 5); }
+__host__ __device__ constexpr int pd_size(int n) { return n + (n >> 5) + 1; }
 
 // Even split of n rows into P blocks: block b starts at b*base + min(b, rem)
 // and has base + (b < rem) rows.
@@ -48,7 +52,20 @@ struct BlockSplit {
     __host__ __device__ int64_t size(int64_t b) const { return base + (b < rem ? 1 : 0); }
     __host__ __device__ int64_t block_of(int64_t i) const {
         const int64_t big = (int64_t)rem * (base + 1);
+        if (n < ((int64_t)1 << 31)) {  // 32-bit division is several times cheaper
+            const unsigned ui = (unsigned)i, ub = (unsigned)base, ubig = (unsigned)big;
+            return ui < ubig ? ui / (ub + 1u) : (unsigned)rem + (ui - ubig) / ub;
+        }
         return i < big ? i / (base + 1) : rem + (i - big) / base;
+    }
+    // block of row j = i - 1 or i + 1 given the block b of row i (cyclic)
+    __host__ __device__ int64_t left_of(int64_t b, int64_t j) const {
+        if (j < 0) return P - 1;
+        return j < start(b) ? b - 1 : b;
+    }
+    __host__ __device__ int64_t right_of(int64_t b, int64_t j) const {
+        if (j >= n) return 0;
+        return j >= start(b) + size(b) ? b + 1 : b;
     }
 };
 
@@ -260,22 +277,26 @@ __global__ void __launch_bounds__(T) k_stage_assemble(const StageParams p) {
 // row of block b) and x_{sep+1} = y_F - s_b v_F - s_{b+1} w_F (first row of
 // block b+1), the separator row a x_{sep-1} + b x_sep + c x_{sep+1} = d gives
 //   (-a v_L) s_{b-1} + (b - a w_L - c v_F) s_b + (-c w_F) s_{b+1} = d - a y_L - c y_F.
-struct BlkRows {
-    const double* blk;
+template <class R>
+struct BlkRowsT {
+    using Real = R;
+    const R* blk;
     int64_t P;
-    __device__ void operator()(int64_t i, double& A, double& B, double& C, double& D) const {
-        const double* s = blk + i * BLK_STRIDE;
-        const double* f = blk + (i + 1 == P ? 0 : i + 1) * BLK_STRIDE;
-        const double a = s[0], bb = s[1], c = s[2], d = s[3];
+    __device__ void operator()(int64_t i, R& A, R& B, R& C, R& D) const {
+        const R* s = blk + i * BLK_STRIDE;
+        const R* f = blk + (i + 1 == P ? 0 : i + 1) * BLK_STRIDE;
+        const R a = s[0], bb = s[1], c = s[2], d = s[3];
         A = -a * s[8];
         B = bb - a * s[9] - c * f[5];
         C = -c * f[6];
         D = d - a * s[7] - c * f[4];
     }
 };
+using BlkRows = BlkRowsT<double>;
 
 // Row source reading explicit arrays (cyclic: a[0] couples x[n-1], c[n-1] couples x[0]).
 struct ArrayRows {
+    using Real = double;
     const double *a, *b, *c, *d;
     int periodic;
     int64_t n;  // total rows of the system
@@ -301,24 +322,26 @@ constexpr int SEP_ROWS = 32 * SEP_MS;
 // 0 .. n-2 (the cyclic couplings a_0 and c_{n-2}), so x_i = y_i - x_{n-1}
 // (v_i + w_i), and the last row a x_{n-2} + b x_{n-1} + c x_0 = d closes it.
 template <class RowSrc>
-__global__ void __launch_bounds__(32) k_cyclic_onewarp(int nrows, RowSrc rows, double* x,
+__global__ void __launch_bounds__(32) k_cyclic_onewarp(int nrows, RowSrc rows,
+                                                      typename RowSrc::Real* x,
                                                       double* speed_reset, unsigned* err) {
-    __shared__ double sh[8];
+    using Real = typename RowSrc::Real;
+    __shared__ Real sh[8];
     const int t = threadIdx.x;
     if (speed_reset && t == 0) *speed_reset = 0.0;
     if (nrows == 1) {
         if (t == 0) {
-            double A, B, C, D;
+            Real A, B, C, D;
             rows(0, A, B, C, D);
-            const double den = A + B + C;
+            const Real den = A + B + C;
             if (!pos_finite(den)) flag_error(err, HSGN_DEV_ERR_COERCIVE);
             x[0] = D / den;
         }
         return;
     }
-    double y[SEP_MS], v[SEP_MS], w[SEP_MS], last[4];
+    Real y[SEP_MS], v[SEP_MS], w[SEP_MS], last[4];
     int cs, m;
-    auto rf = [&](int i, double& A, double& B, double& C, double& D) { rows(i, A, B, C, D); };
+    auto rf = [&](int i, Real& A, Real& B, Real& C, Real& D) { rows(i, A, B, C, D); };
     warp_block_solve<SEP_MS>(nrows, rf, y, v, w, cs, m, last, err);
 #pragma unroll
     for (int k = 0; k < SEP_MS; ++k) {
@@ -332,10 +355,10 @@ __global__ void __launch_bounds__(32) k_cyclic_onewarp(int nrows, RowSrc rows, d
         sh[4] = last[0]; sh[5] = last[1]; sh[6] = last[2]; sh[7] = last[3];
     }
     __syncwarp();
-    const double a = sh[4], b = sh[5], c = sh[6], d = sh[7];
-    const double den = b - a * sh[3] - c * sh[1];
+    const Real a = sh[4], b = sh[5], c = sh[6], d = sh[7];
+    const Real den = b - a * sh[3] - c * sh[1];
     if (t == 0 && !pos_finite(den)) flag_error(err, HSGN_DEV_ERR_COERCIVE);
-    const double xl = (d - a * sh[2] - c * sh[0]) / den;
+    const Real xl = (d - a * sh[2] - c * sh[0]) / den;
 #pragma unroll
     for (int k = 0; k < SEP_MS; ++k) {
         if (k < m) {
@@ -345,23 +368,78 @@ __global__ void __launch_bounds__(32) k_cyclic_onewarp(int nrows, RowSrc rows, d
     }
 }
 
+// Cyclic system of at most T*M rows in one CTA (the CTA block machinery); used
+// for the single-precision separator systems, where the parallel cyclic
+// reduction over T chunk separators is cheap.
+template <int T, int M, class RowSrc>
+__global__ void __launch_bounds__(T) k_cyclic_onecta(int nrows, RowSrc rows,
+                                                     typename RowSrc::Real* x,
+                                                     double* speed_reset, unsigned* err) {
+    using Real = typename RowSrc::Real;
+    __shared__ SepShared<T, Real> sep;
+    __shared__ Real sh[8];
+    const int t = threadIdx.x;
+    if (speed_reset && t == 0) *speed_reset = 0.0;
+    if (nrows == 1) {
+        if (t == 0) {
+            Real A, B, C, D;
+            rows(0, A, B, C, D);
+            const Real den = A + B + C;
+            if (!pos_finite(den)) flag_error(err, HSGN_DEV_ERR_COERCIVE);
+            x[0] = D / den;
+        }
+        return;
+    }
+    Real y[M], v[M], w[M], last[4];
+    int cs, m;
+    auto rf = [&](int i, Real& A, Real& B, Real& C, Real& D) { rows(i, A, B, C, D); };
+    cta_block_solve<T, M>(nrows, rf, sep, y, v, w, cs, m, last, err);
+#pragma unroll
+    for (int k = 0; k < M; ++k) {
+        if (k < m) {
+            const int i = cs + k;
+            if (i == 0) { sh[0] = y[k]; sh[1] = v[k] + w[k]; }
+            if (i == nrows - 2) { sh[2] = y[k]; sh[3] = v[k] + w[k]; }
+        }
+    }
+    if (m > 0 && cs + m == nrows) {
+        sh[4] = last[0]; sh[5] = last[1]; sh[6] = last[2]; sh[7] = last[3];
+    }
+    __syncthreads();
+    const Real a = sh[4], b = sh[5], c = sh[6], d = sh[7];
+    const Real den = b - a * sh[3] - c * sh[1];
+    if (t == 0 && !pos_finite(den)) flag_error(err, HSGN_DEV_ERR_COERCIVE);
+    const Real xl = (d - a * sh[2] - c * sh[0]) / den;
+#pragma unroll
+    for (int k = 0; k < M; ++k) {
+        if (k < m) {
+            const int i = cs + k;
+            x[i] = (i == nrows - 1) ? xl : y[k] - xl * (v[k] + w[k]);
+        }
+    }
+}
+
 // One level of the multi-block elimination of a row source: one warp per
 // block of at most SEP_ROWS rows; per row (y, v, w) and a block summary.
+template <class Real>
 struct ReduceShared {
-    double ys[SEP_ROWS], vs[SEP_ROWS], ws[SEP_ROWS];
-    double lastrow[4];
+    Real ys[SEP_ROWS], vs[SEP_ROWS], ws[SEP_ROWS];
+    Real lastrow[4];
 };
 
 template <class RowSrc>
-__global__ void __launch_bounds__(32) k_block_reduce(RowSrc rows, BlockSplit split, double* yo,
-                                                     double* vo, double* wo, double* blk,
-                                                     unsigned* err) {
-    __shared__ ReduceShared sh;
+__global__ void __launch_bounds__(32) k_block_reduce(RowSrc rows, BlockSplit split,
+                                                     typename RowSrc::Real* yo,
+                                                     typename RowSrc::Real* vo,
+                                                     typename RowSrc::Real* wo,
+                                                     typename RowSrc::Real* blk, unsigned* err) {
+    using Real = typename RowSrc::Real;
+    __shared__ ReduceShared<Real> sh;
     const int64_t b = blockIdx.x;
     const int64_t r0 = split.start(b);
     const int nb = (int)split.size(b);
-    auto rf = [&](int i, double& A, double& B, double& C, double& D) { rows(r0 + i, A, B, C, D); };
-    double y[SEP_MS], v[SEP_MS], w[SEP_MS], last[4];
+    auto rf = [&](int i, Real& A, Real& B, Real& C, Real& D) { rows(r0 + i, A, B, C, D); };
+    Real y[SEP_MS], v[SEP_MS], w[SEP_MS], last[4];
     int cs, m;
     warp_block_solve<SEP_MS>(nb, rf, y, v, w, cs, m, last, err);
 #pragma unroll
@@ -383,25 +461,26 @@ __global__ void __launch_bounds__(32) k_block_reduce(RowSrc rows, BlockSplit spl
         wo[r0 + i] = sh.ws[i];
     }
     if (threadIdx.x == 0) {
-        double* s = blk + b * BLK_STRIDE;
+        Real* s = blk + b * BLK_STRIDE;
         s[0] = sh.lastrow[0]; s[1] = sh.lastrow[1]; s[2] = sh.lastrow[2]; s[3] = sh.lastrow[3];
         s[4] = sh.ys[0]; s[5] = sh.vs[0]; s[6] = sh.ws[0];
         if (nb >= 2) {
             s[7] = sh.ys[nb - 2]; s[8] = sh.vs[nb - 2]; s[9] = sh.ws[nb - 2];
         } else {
-            s[7] = 0.0; s[8] = -1.0; s[9] = 0.0;
+            s[7] = Real(0); s[8] = Real(-1); s[9] = Real(0);
         }
     }
 }
 
 // x_i = y_i - s_{b-1} v_i - s_b w_i for every row of a multi-block solve.
-__global__ void k_block_backout(BlockSplit split, const double* y, const double* v,
-                                const double* w, const double* s, double* x) {
+template <class Real>
+__global__ void k_block_backout(BlockSplit split, const Real* y, const Real* v, const Real* w,
+                                const Real* s, Real* x) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= split.n) return;
     const int64_t b = split.block_of(i);
-    const double sl = s[b == 0 ? split.P - 1 : b - 1];
-    const double sr = s[b];
+    const Real sl = s[b == 0 ? split.P - 1 : b - 1];
+    const Real sr = s[b];
     x[i] = y[i] - sl * v[i] - sr * w[i];
 }
 
@@ -418,8 +497,7 @@ struct BacksubParams {
     unsigned* err;
 };
 
-__device__ __forceinline__ double hbar_at(const BacksubParams& p, int64_t i) {
-    const int64_t b = p.split.block_of(i);
+__device__ __forceinline__ double hbar_at(const BacksubParams& p, int64_t i, int64_t b) {
     const double sl = p.s[b == 0 ? p.split.P - 1 : b - 1];
     const double sr = p.s[b];
     return p.y[i] - sl * p.v[i] - sr * p.w[i];
@@ -438,14 +516,19 @@ __global__ void k_backsub(const BacksubParams p) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int lane = threadIdx.x & 31;
     const bool live = i < p.n;
-    const double h = live ? hbar_at(p, i) : 0.0;
+    const int64_t bi = live ? p.split.block_of(i) : 0;
+    const double h = live ? hbar_at(p, i, bi) : 0.0;
     const double hl_s = __shfl_up_sync(0xffffffffu, h, 1);
     const double hr_s = __shfl_down_sync(0xffffffffu, h, 1);
     double umax = 0.0;
     if (live) {
         const int64_t il = wrap_index(i - 1, p.n, BC), ir = wrap_index(i + 1, p.n, BC);
-        const double hl = (lane == 0 || il != i - 1) ? hbar_at(p, il) : hl_s;
-        const double hr = (lane == 31 || ir != i + 1) ? hbar_at(p, ir) : hr_s;
+        // block of the neighbour actually used: the next block, the same cell
+        // (transmissive clamp) or the cyclic wrap
+        const int64_t bl = il == i - 1 ? p.split.left_of(bi, i - 1) : (il == i ? bi : p.split.P - 1);
+        const int64_t br = ir == i + 1 ? p.split.right_of(bi, i + 1) : (ir == i ? bi : 0);
+        const double hl = (lane == 0 || il != i - 1) ? hbar_at(p, il, bl) : hl_s;
+        const double hr = (lane == 31 || ir != i + 1) ? hbar_at(p, ir, br) : hr_s;
         const double fq = p.tau / (2.0 * p.dx);
         const double q = p.qs[i] - fq * p.be[i] * (hr - hl) -
                          p.lam * fq * p.de[i] * (p.ms[ir] - p.ms[il]);

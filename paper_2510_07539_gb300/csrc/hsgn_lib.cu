@@ -15,13 +15,19 @@
 
 #include "../../include/hsgn.h"
 #include "hsgn_kernels.cuh"
+#include "hsgn_mixed.cuh"
 
 using namespace hsgn;
 
 namespace {
 
-// Stage block: AT threads per CTA, AM rows per thread in the block elimination.
+// Stage block: AT threads per CTA, AM rows per thread in the block elimination
+// (FP64 path); the mixed path uses more threads with shorter chunks.
 constexpr int AT = 64, AM = 8, AS = AT * AM;
+constexpr int XT = 128, XM = 4;
+static_assert(XT * XM == AS, "both precision forms use the same block split");
+// One CTA solves single-precision separator systems of up to OT*OM rows.
+constexpr int OT = 256, OM = 16;
 // Separator levels: one warp per block of GS rows; one warp solves up to RMAX rows.
 constexpr int GS = SEP_ROWS, RMAX = SEP_ROWS;
 
@@ -55,28 +61,35 @@ cudaError_t set_smem(K kernel, size_t bytes) {
 // Recursive cyclic solve of n rows given by a row source, with workspace `ws`:
 // at most RMAX rows in one warp, otherwise one level of block elimination
 // (a warp per GS rows), the cyclic system of the block separators, and the
-// back-out of every row.
+// back-out of every row. Works in the row source's precision.
 template <class RowSrc>
-cudaError_t solve_src(int64_t n, RowSrc rows, double* x, unsigned char* ws, unsigned* err,
-                      double* speed_reset, cudaStream_t st) {
+cudaError_t solve_src(int64_t n, RowSrc rows, typename RowSrc::Real* x, unsigned char* ws,
+                      unsigned* err, double* speed_reset, cudaStream_t st) {
+    using Real = typename RowSrc::Real;
     if (n <= RMAX) {
         k_cyclic_onewarp<RowSrc><<<1, 32, 0, st>>>((int)n, rows, x, speed_reset, err);
         return cudaGetLastError();
     }
+    if constexpr (sizeof(Real) == sizeof(float)) {
+        if (n <= OT * OM) {
+            k_cyclic_onecta<OT, OM, RowSrc><<<1, OT, 0, st>>>((int)n, rows, x, speed_reset, err);
+            return cudaGetLastError();
+        }
+    }
     const BlockSplit s = make_split(n, GS);
     const int64_t P = s.P;
-    double* y = reinterpret_cast<double*>(ws);
+    Real* y = reinterpret_cast<Real*>(ws);
     ws += align_up(3 * n * sizeof(double));
-    double* blk = reinterpret_cast<double*>(ws);
+    Real* blk = reinterpret_cast<Real*>(ws);
     ws += align_up(BLK_STRIDE * P * sizeof(double));
-    double* sv = reinterpret_cast<double*>(ws);
+    Real* sv = reinterpret_cast<Real*>(ws);
     ws += align_up(P * sizeof(double));
     k_block_reduce<RowSrc><<<(unsigned)P, 32, 0, st>>>(rows, s, y, y + n, y + 2 * n, blk, err);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    e = solve_src(P, BlkRows{blk, P}, sv, ws, err, speed_reset, st);
+    e = solve_src(P, BlkRowsT<Real>{blk, P}, sv, ws, err, speed_reset, st);
     if (e != cudaSuccess) return e;
-    k_block_backout<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(s, y, y + n, y + 2 * n, sv, x);
+    k_block_backout<Real><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(s, y, y + n, y + 2 * n, sv, x);
     return cudaGetLastError();
 }
 
@@ -113,6 +126,11 @@ struct hsgn_s {
     double* s = nullptr;
     unsigned char* rws = nullptr;    // workspace of the separator-system solve
     double* spd = nullptr;           // [0] global Rusanov speed, [1] stage speed, [2..3] scratch
+    // mixed precision (HSGN_MIXED): FP32 stage-1 increments and per-row results
+    bool mixed = false;
+    float *G1 = nullptr, *dq1 = nullptr, *dm1 = nullptr, *dr1 = nullptr;
+    float4* mrec = nullptr;          // three float4 records per row
+    float *mblk = nullptr, *ms_ = nullptr;
     unsigned* err = nullptr;
     cudaStream_t cap = nullptr;      // private stream used for graph capture
     cudaGraphExec_t gexec = nullptr;
@@ -244,6 +262,73 @@ cudaError_t launch_stage(hsgn_s* H, const double* const A[4], const double* cons
     return cudaGetLastError();
 }
 
+// One stage in mixed precision (hsgn_mixed.cuh). Stage 1 writes the FP32
+// increments dU1 = U_I^(1) - U^n; stage 2 reads them (U_l = U^n + (c/gamma) dU1,
+// U_b = U^n + ((1-gamma)/gamma) dU1) and writes U^{n+1} in place.
+cudaError_t launch_stage_mixed(hsgn_s* H, int stage, double tau, cudaStream_t st) {
+    const double gam = 1.0 - 1.0 / std::sqrt(2.0);
+    const double c = 1.0 / (2.0 * gam);
+    MixedParams p;
+    p.n = H->n;
+    p.bc = H->bc;
+    p.local_speed = local_speed(H) ? 1 : 0;
+    p.stage = stage;
+    const bool track = stage == 2 && !local_speed(H);
+    p.track_speed = track ? 1 : 0;
+    const double dx = H->dx, lam = H->lam;
+    p.g = (float)H->g;
+    p.lam = (float)lam;
+    p.tau = (float)tau;
+    p.tdx = (float)(tau / dx);
+    p.fq = (float)(tau / (2.0 * dx));
+    p.Cc = (float)(tau * tau / (dx * dx));
+    p.fd = (float)(lam * tau * tau / (dx * dx));
+    p.lt2 = (float)(lam * tau * tau);
+    p.ltau = (float)(lam * tau);
+    p.wl1 = stage == 2 ? (float)(c / gam) : 0.f;
+    p.wb1 = stage == 2 ? (float)((1.0 - gam) / gam) : 0.f;
+    for (int k = 0; k < 4; ++k) {
+        p.U[k] = H->U[k];
+        p.out[k] = H->U[k];
+    }
+    p.G1 = H->G1;
+    p.dq1 = H->dq1;
+    p.dm1 = H->dm1;
+    p.dr1 = H->dr1;
+    p.speed = H->spd;
+    p.split = H->split;
+    p.rec = H->mrec;
+    p.blk = H->mblk;
+    p.s = H->ms_;
+    p.err = H->err;
+    const unsigned P = (unsigned)H->split.P;
+    const size_t smem = sizeof(MixedShared<XT, XM>);
+    {
+        ProfScope ps(H, HSGN_PROF_ASSEMBLE, st);
+        if (H->bc == BC_PERIODIC)
+            k_mixed_assemble<XT, XM, BC_PERIODIC><<<P, XT, smem, st>>>(p);
+        else
+            k_mixed_assemble<XT, XM, BC_TRANSMISSIVE><<<P, XT, smem, st>>>(p);
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    {
+        ProfScope ps(H, HSGN_PROF_REDUCED, st);
+        e = solve_src(P, BlkRowsT<float>{H->mblk, (int64_t)P}, H->ms_, H->rws, H->err,
+                      track ? H->spd : nullptr, st);
+    }
+    if (e != cudaSuccess) return e;
+    const unsigned nb = (unsigned)((H->n + 255) / 256);
+    {
+        ProfScope ps(H, HSGN_PROF_BACKSUB, st);
+        if (H->bc == BC_PERIODIC)
+            k_mixed_backsub<BC_PERIODIC><<<nb, 256, 0, st>>>(p);
+        else
+            k_mixed_backsub<BC_TRANSMISSIVE><<<nb, 256, 0, st>>>(p);
+    }
+    return cudaGetLastError();
+}
+
 // IMEX step of Sec. 3.2 in efficient form:
 //   U1 = S(U, U, gamma dt);
 //   U  <- S(U_b, U_l, gamma dt), U_l = (1-c/gamma) U + (c/gamma) U1,
@@ -252,6 +337,11 @@ cudaError_t enqueue_step(hsgn_s* H, double dt, cudaStream_t st) {
     const double gam = 1.0 - 1.0 / std::sqrt(2.0);
     const double c = 1.0 / (2.0 * gam);
     const double tau = gam * dt;
+    if (H->mixed) {
+        const cudaError_t e = launch_stage_mixed(H, 1, tau, st);
+        if (e != cudaSuccess) return e;
+        return launch_stage_mixed(H, 2, tau, st);
+    }
     const double* A[4] = {H->U[0], H->U[1], H->U[2], H->U[3]};
     const double* B[4] = {H->U1[0], H->U1[1], H->U1[2], H->U1[3]};
     cudaError_t e = launch_stage(H, A, nullptr, 1.0, 0.0, 1.0, 0.0, tau, H->spd, H->U1, false, st);
@@ -311,7 +401,7 @@ int hsgn_create(const hsgn_grid_t* grid, double g, double lambda, const double* 
         return HSGN_ERR_INVALID_ARG;
     if (!(g > 0.0) || !std::isfinite(g) || !(lambda >= 0.0) || !std::isfinite(lambda))
         return HSGN_ERR_INVALID_ARG;
-    if (flags & ~(int32_t)(HSGN_RUSANOV_LOCAL)) return HSGN_ERR_UNIMPLEMENTED;
+    if (flags & ~(int32_t)(HSGN_RUSANOV_LOCAL | HSGN_MIXED)) return HSGN_ERR_UNIMPLEMENTED;
     if (bathymetry) return HSGN_ERR_UNIMPLEMENTED;
     if (grid->n > ((int64_t)1 << 40)) return HSGN_ERR_INVALID_ARG;
 
@@ -327,8 +417,12 @@ int hsgn_create(const hsgn_grid_t* grid, double g, double lambda, const double* 
     H->split = make_split(H->n, AS);
     const int64_t n = H->n, P = H->split.P;
 
+    H->mixed = (flags & HSGN_MIXED) != 0;
     const size_t vec = align_up(n * sizeof(double));
-    size_t total = 16 * vec;                                   // U, U1, y v w, 5 back-sub arrays
+    const size_t fvec = align_up((n + 1) * sizeof(float));
+    const size_t recb = align_up(3 * n * sizeof(float4));
+    size_t total = H->mixed ? 4 * vec + 4 * fvec + recb  // U; G1 dq1 dm1 dr1; row records
+                            : 16 * vec;                  // U, U1, y v w, 5 back-sub arrays
     total += align_up(BLK_STRIDE * P * sizeof(double)) + align_up(P * sizeof(double));
     const size_t rws = rows_ws_bytes(P);
     total += rws + align_up(4 * sizeof(double)) + align_up(sizeof(unsigned));
@@ -344,17 +438,27 @@ int hsgn_create(const hsgn_grid_t* grid, double g, double lambda, const double* 
         return r;
     };
     for (int k = 0; k < 4; ++k) H->U[k] = reinterpret_cast<double*>(take(vec));
-    for (int k = 0; k < 4; ++k) H->U1[k] = reinterpret_cast<double*>(take(vec));
-    H->y = reinterpret_cast<double*>(take(vec));
-    H->v = reinterpret_cast<double*>(take(vec));
-    H->w = reinterpret_cast<double*>(take(vec));
-    H->qs = reinterpret_cast<double*>(take(vec));
-    H->ms = reinterpret_cast<double*>(take(vec));
-    H->rs = reinterpret_cast<double*>(take(vec));
-    H->be = reinterpret_cast<double*>(take(vec));
-    H->de = reinterpret_cast<double*>(take(vec));
-    H->blk = reinterpret_cast<double*>(take(align_up(BLK_STRIDE * P * sizeof(double))));
-    H->s = reinterpret_cast<double*>(take(align_up(P * sizeof(double))));
+    if (H->mixed) {
+        H->G1 = reinterpret_cast<float*>(take(fvec));
+        H->dq1 = reinterpret_cast<float*>(take(fvec));
+        H->dm1 = reinterpret_cast<float*>(take(fvec));
+        H->dr1 = reinterpret_cast<float*>(take(fvec));
+        H->mrec = reinterpret_cast<float4*>(take(recb));
+        H->mblk = reinterpret_cast<float*>(take(align_up(BLK_STRIDE * P * sizeof(double))));
+        H->ms_ = reinterpret_cast<float*>(take(align_up(P * sizeof(double))));
+    } else {
+        for (int k = 0; k < 4; ++k) H->U1[k] = reinterpret_cast<double*>(take(vec));
+        H->y = reinterpret_cast<double*>(take(vec));
+        H->v = reinterpret_cast<double*>(take(vec));
+        H->w = reinterpret_cast<double*>(take(vec));
+        H->qs = reinterpret_cast<double*>(take(vec));
+        H->ms = reinterpret_cast<double*>(take(vec));
+        H->rs = reinterpret_cast<double*>(take(vec));
+        H->be = reinterpret_cast<double*>(take(vec));
+        H->de = reinterpret_cast<double*>(take(vec));
+        H->blk = reinterpret_cast<double*>(take(align_up(BLK_STRIDE * P * sizeof(double))));
+        H->s = reinterpret_cast<double*>(take(align_up(P * sizeof(double))));
+    }
     H->rws = rws ? take(rws) : nullptr;
     H->spd = reinterpret_cast<double*>(take(align_up(4 * sizeof(double))));
     H->err = reinterpret_cast<unsigned*>(take(align_up(sizeof(unsigned))));
@@ -364,6 +468,10 @@ int hsgn_create(const hsgn_grid_t* grid, double g, double lambda, const double* 
         e = set_smem(k_stage_assemble<AT, AM, BC_PERIODIC>, sizeof(AssembleShared<AT, AM>));
     if (e == cudaSuccess)
         e = set_smem(k_stage_assemble<AT, AM, BC_TRANSMISSIVE>, sizeof(AssembleShared<AT, AM>));
+    if (e == cudaSuccess)
+        e = set_smem(k_mixed_assemble<XT, XM, BC_PERIODIC>, sizeof(MixedShared<XT, XM>));
+    if (e == cudaSuccess)
+        e = set_smem(k_mixed_assemble<XT, XM, BC_TRANSMISSIVE>, sizeof(MixedShared<XT, XM>));
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&H->cap, cudaStreamNonBlocking);
     if (e != cudaSuccess) {
         cudaGetLastError();
@@ -520,6 +628,7 @@ int hsgn_suggest_dt(hsgn_handle_t H, double cfl, double mcfl, double* dt_out, vo
 int hsgn_stage(hsgn_handle_t H, const double* const base[4], const double* const lin[4],
                double tau, double speed, double* const out[4], void* stream) {
     if (!H || !base || !lin || !out || !(tau > 0.0) || !(speed >= 0.0)) return HSGN_ERR_INVALID_ARG;
+    if (H->mixed) return HSGN_ERR_UNIMPLEMENTED;
     for (int k = 0; k < 4; ++k)
         if (!base[k] || !lin[k] || !out[k]) return HSGN_ERR_INVALID_ARG;
     cudaStream_t st = as_stream(stream);

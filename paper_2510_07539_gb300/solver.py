@@ -19,6 +19,7 @@ HSGN_OK = 0
 BC_PERIODIC = 0
 BC_TRANSMISSIVE = 1
 FLAG_FP64 = 0x0
+FLAG_MIXED = 0x1
 FLAG_RUSANOV_LOCAL = 0x10
 
 ERROR_NAMES = {

@@ -238,3 +238,77 @@ def test_adjoint_reports_unimplemented():
     with S().Solver(16, 0.0, 1.6, 0, lam=1.0) as s:
         rc = S().load().hsgn_adjoint(s._h, 0.1, 1, 0, None, None, None, None, None)
         assert rc == 6
+
+
+# --------------------------------------------------------------------------
+# mixed precision (HSGN_MIXED): FP32 increments, FP64 state and accumulation.
+# Bounds: one step <= 1e-7 relative L2 for h and h eta (the FP32 rounding of
+# increments that are a few percent of the state), q and h w against the
+# summand scales; a 500-step solitary-wave trajectory <= 1e-6 relative L2
+# (target of the mixed form); mass conserved to FP64 rounding (flux form).
+# --------------------------------------------------------------------------
+def mixed_run(n, x_left, x_right, bc, lam, U, dt, steps, use_graph=True):
+    return gpu_run(n, x_left, x_right, bc, lam, U, dt, steps, flags=S().FLAG_MIXED,
+                   use_graph=use_graph)
+
+
+@pytest.mark.parametrize("bc", [0, 1])
+@pytest.mark.parametrize("n", [5, 100, 1000, 1537, 70001])
+def test_mixed_one_step_close_to_oracle(n, bc):
+    dx, lam = 0.1, 500.0
+    U = inputs.random_state(3000 + n, n, dx)
+    p = oracle.Params(n, dx, bc, lam=lam)
+    dt, _, _ = oracle.suggest_dt(p, U, 2.0, 0.5)
+    got = mixed_run(n, 0.0, n * dx, bc, lam, U, dt, 1)
+    ref = oracle.step(p, U, dt)
+    sc = summand_scales(n, dx, bc, lam, U, dt)
+    assert rel_l2(got[0], ref[0]) < 1e-7, rel_l2(got[0], ref[0])
+    assert rel_l2(got[2], ref[2]) < 1e-7, rel_l2(got[2], ref[2])
+    for k in (1, 3):
+        assert scaled_err(got[k], ref[k], sc[k]) < 1e-6, (k, scaled_err(got[k], ref[k], sc[k]))
+
+
+def test_mixed_solitary_trajectory_500_steps():
+    n, lam = 1000, 100.0
+    x, dx = inputs.cell_centres(n, -50.0, 50.0)
+    U = inputs.solitary(x, 1.0, 0.2, 0.0, period=100.0)
+    p = oracle.Params(n, dx, 0, lam=lam)
+    dt, _, _ = oracle.suggest_dt(p, U, 1e9, 0.5)
+    got = mixed_run(n, -50.0, 50.0, 0, lam, U, dt, 500)
+    ref = oracle.run(p, U, dt, 500)
+    errs = [rel_l2(got[k], ref[k]) for k in range(4)]
+    assert errs[0] < 1e-6 and errs[2] < 1e-6, errs
+    assert errs[1] < 1e-5 and errs[3] < 1e-4, errs
+    assert abs(math.fsum(got[0]) - math.fsum(U[0])) <= 1e-13 * math.fsum(U[0])
+
+
+def test_mixed_mass_conservation_and_graph():
+    n, dx = 4099, 0.1
+    U = inputs.random_state(42, n, dx)
+    a = mixed_run(n, 0.0, n * dx, 0, 500.0, U, 0.01, 300, use_graph=True)
+    b = mixed_run(n, 0.0, n * dx, 0, 500.0, U, 0.01, 300, use_graph=False)
+    assert abs(math.fsum(a[0]) - math.fsum(U[0])) <= 1e-13 * math.fsum(U[0])
+    for k in range(4):
+        np.testing.assert_array_equal(a[k], b[k])
+
+
+@pytest.mark.parametrize("lam", [10.0, 1000.0])
+def test_mixed_dam_break_full_size(lam):
+    n, dx, steps = 1 << 20, 0.05, 10
+    x, U = inputs.dam_break(n, dx, 1.2, 1.0, 5.0 / dx)
+    p = oracle.Params(n, dx, 1, lam=lam)
+    dt, _, _ = oracle.suggest_dt(p, U, 4.0, 0.5)
+    got = mixed_run(n, -0.5 * n * dx, 0.5 * n * dx, 1, lam, U, dt, steps)
+    ref = oracle.run(p, U, dt, steps)
+    sc = summand_scales(n, dx, 1, lam, U, dt)
+    assert rel_l2(got[0], ref[0]) < 1e-7, rel_l2(got[0], ref[0])
+    for k in range(4):
+        assert scaled_err(got[k], ref[k], sc[k]) < 1e-6, (k, scaled_err(got[k], ref[k], sc[k]))
+
+
+def test_mixed_rejects_stage_entry():
+    with S().Solver(16, 0.0, 1.6, 0, lam=1.0, flags=S().FLAG_MIXED) as s:
+        t = [dev(np.ones(16)) for _ in range(4)]
+        with pytest.raises(S().HsgnError) as e:
+            s.stage(t, t, 0.01, 0.0)
+        assert e.value.code == 6
