@@ -143,6 +143,35 @@ int hsgn_adjoint(hsgn_handle_t h, double dt, int64_t n_steps, int64_t n_gauges,
                  const int64_t* gauge_cells, const double* gauge_data, double* grad_h0,
                  double* misfit, void* stream);
 
+/* ---------------------------------------------------------------------------
+ * Batches of independent instances (the batched workload of many 1D problems
+ * of uneven length, relaxation parameter and time step). All instances of a
+ * batch share g and the boundary condition and are advanced together by the
+ * mixed-precision kernels (HSGN_MIXED is implied): one launch per kernel for
+ * the whole batch, with the separator systems solved one warp per instance.
+ * The state of a batch is the concatenation of the instances' states (packed,
+ * instance k occupying cells offset_k .. offset_k + n_k - 1 of every array),
+ * exchanged with hsgn_set_state / hsgn_get_state as for a single instance.
+ * hsgn_step, hsgn_run and hsgn_enqueue take dt = 0 for a batch: each instance
+ * uses the step set by hsgn_batched_set_dt. hsgn_stage, hsgn_suggest_dt and
+ * hsgn_adjoint are not available for a batch.
+ * ------------------------------------------------------------------------- */
+
+/* count >= 1 instances; per instance: n[k] in [3, 65536] cells on
+ * [x_left[k], x_right[k]] and lambda[k] >= 0 (host arrays). */
+int hsgn_create_batched(int32_t count, const int64_t* n, const double* x_left,
+                        const double* x_right, const double* lambda, double g, int32_t bc,
+                        int32_t flags, hsgn_handle_t* out);
+
+/* Per-instance time steps dt[k] > 0 (host array of `count`). Takes effect for
+ * steps enqueued after the call; synchronises the device. */
+int hsgn_batched_set_dt(hsgn_handle_t h, const double* dt);
+
+/* Per-instance time-step rule of Sec. 5 (as hsgn_suggest_dt) on the current
+ * state; dt_out: host array of `count`. Synchronises. */
+int hsgn_batched_suggest_dt(hsgn_handle_t h, double cfl, double mcfl, double* dt_out,
+                            void* stream);
+
 /* Release everything owned by the handle (NULL is accepted). */
 void hsgn_destroy(hsgn_handle_t h);
 

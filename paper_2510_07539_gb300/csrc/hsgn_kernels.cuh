@@ -322,13 +322,11 @@ constexpr int SEP_ROWS = 32 * SEP_MS;
 // 0 .. n-2 (the cyclic couplings a_0 and c_{n-2}), so x_i = y_i - x_{n-1}
 // (v_i + w_i), and the last row a x_{n-2} + b x_{n-1} + c x_0 = d closes it.
 template <class RowSrc>
-__global__ void __launch_bounds__(32) k_cyclic_onewarp(int nrows, RowSrc rows,
-                                                      typename RowSrc::Real* x,
-                                                      double* speed_reset, unsigned* err) {
+__device__ __forceinline__ void warp_cyclic_solve(int nrows, RowSrc rows,
+                                                  typename RowSrc::Real* x, unsigned* err) {
     using Real = typename RowSrc::Real;
     __shared__ Real sh[8];
     const int t = threadIdx.x;
-    if (speed_reset && t == 0) *speed_reset = 0.0;
     if (nrows == 1) {
         if (t == 0) {
             Real A, B, C, D;
@@ -366,6 +364,14 @@ __global__ void __launch_bounds__(32) k_cyclic_onewarp(int nrows, RowSrc rows,
             x[i] = (i == nrows - 1) ? xl : y[k] - xl * (v[k] + w[k]);
         }
     }
+}
+
+template <class RowSrc>
+__global__ void __launch_bounds__(32) k_cyclic_onewarp(int nrows, RowSrc rows,
+                                                      typename RowSrc::Real* x,
+                                                      double* speed_reset, unsigned* err) {
+    if (speed_reset && threadIdx.x == 0) *speed_reset = 0.0;
+    warp_cyclic_solve(nrows, rows, x, err);
 }
 
 // Cyclic system of at most T*M rows in one CTA (the CTA block machinery); used

@@ -130,6 +130,15 @@ struct hsgn_s {
     bool mixed = false;
     float *G1 = nullptr, *dq1 = nullptr, *dm1 = nullptr, *dr1 = nullptr;
     float4* mrec = nullptr;          // three float4 records per row
+    // batch (hsgn_create_batched)
+    int32_t count = 1;
+    bool batched = false;
+    int64_t total_blocks = 0;
+    InstInfo* inst = nullptr;        // device table
+    int32_t* blk_inst = nullptr;     // device table
+    double* speeds = nullptr;        // per-instance Rusanov speed (device)
+    double* speeds_tmp = nullptr;    // 2 per instance (device), for suggest_dt
+    std::vector<InstInfo> inst_h;    // host copy
     float *mblk = nullptr, *ms_ = nullptr;
     unsigned* err = nullptr;
     cudaStream_t cap = nullptr;      // private stream used for graph capture
@@ -301,7 +310,11 @@ cudaError_t launch_stage_mixed(hsgn_s* H, int stage, double tau, cudaStream_t st
     p.blk = H->mblk;
     p.s = H->ms_;
     p.err = H->err;
-    const unsigned P = (unsigned)H->split.P;
+    p.batched = H->batched ? 1 : 0;
+    p.inst = H->inst;
+    p.blk_inst = H->blk_inst;
+    p.speeds = H->speeds;
+    const unsigned P = (unsigned)(H->batched ? H->total_blocks : H->split.P);
     const size_t smem = sizeof(MixedShared<XT, XM>);
     {
         ProfScope ps(H, HSGN_PROF_ASSEMBLE, st);
@@ -314,17 +327,21 @@ cudaError_t launch_stage_mixed(hsgn_s* H, int stage, double tau, cudaStream_t st
     if (e != cudaSuccess) return e;
     {
         ProfScope ps(H, HSGN_PROF_REDUCED, st);
-        e = solve_src(P, BlkRowsT<float>{H->mblk, (int64_t)P}, H->ms_, H->rws, H->err,
-                      track ? H->spd : nullptr, st);
+        if (H->batched) {
+            k_sep_batched<<<(unsigned)H->count, 32, 0, st>>>(p, track ? 1 : 0);
+            e = cudaGetLastError();
+        } else {
+            e = solve_src(P, BlkRowsT<float>{H->mblk, (int64_t)P}, H->ms_, H->rws, H->err,
+                          track ? H->spd : nullptr, st);
+        }
     }
     if (e != cudaSuccess) return e;
-    const unsigned nb = (unsigned)((H->n + 255) / 256);
     {
         ProfScope ps(H, HSGN_PROF_BACKSUB, st);
         if (H->bc == BC_PERIODIC)
-            k_mixed_backsub<BC_PERIODIC><<<nb, 256, 0, st>>>(p);
+            k_mixed_backsub<BC_PERIODIC><<<P, 256, 0, st>>>(p);
         else
-            k_mixed_backsub<BC_TRANSMISSIVE><<<nb, 256, 0, st>>>(p);
+            k_mixed_backsub<BC_TRANSMISSIVE><<<P, 256, 0, st>>>(p);
     }
     return cudaGetLastError();
 }
@@ -364,6 +381,11 @@ int read_error(hsgn_s* H, cudaStream_t st) {
 
 // Recompute the global Rusanov speed max |u| of the current state.
 cudaError_t refresh_speed(hsgn_s* H, cudaStream_t st) {
+    if (H->batched) {
+        k_speeds_batched<<<(unsigned)H->count, 256, 0, st>>>(H->inst, H->U[0], H->U[1], H->U[2],
+                                                             H->g, H->speeds, nullptr, H->err);
+        return cudaGetLastError();
+    }
     cudaError_t e = cudaMemsetAsync(H->spd, 0, 2 * sizeof(double), st);
     if (e != cudaSuccess) return e;
     k_speeds<<<304, 256, 0, st>>>(H->n, H->U[0], H->U[1], H->U[2], H->g, H->lam, H->spd, H->err);
@@ -522,13 +544,19 @@ int hsgn_get_state(hsgn_handle_t H, double* depth, double* q, double* heta, doub
     return read_error(H, st);
 }
 
+// dt of a step: positive and finite for one instance, 0 for a batch (which
+// takes each instance's step from its table).
+bool valid_dt(const hsgn_s* H, double dt) {
+    return H->batched ? dt == 0.0 : (dt > 0.0 && std::isfinite(dt));
+}
+
 int hsgn_step(hsgn_handle_t H, double dt, void* stream) {
-    if (!H || !(dt > 0.0) || !std::isfinite(dt)) return HSGN_ERR_INVALID_ARG;
+    if (!H || !valid_dt(H, dt)) return HSGN_ERR_INVALID_ARG;
     return enqueue_step(H, dt, as_stream(stream)) == cudaSuccess ? HSGN_OK : HSGN_ERR_CUDA;
 }
 
 int hsgn_enqueue(hsgn_handle_t H, double dt, int64_t n_steps, void* stream) {
-    if (!H || !(dt > 0.0) || !std::isfinite(dt) || n_steps < 0) return HSGN_ERR_INVALID_ARG;
+    if (!H || !valid_dt(H, dt) || n_steps < 0) return HSGN_ERR_INVALID_ARG;
     cudaStream_t st = as_stream(stream);
     if (n_steps == 0) return HSGN_OK;
     if (!H->gexec || H->gdt != dt) {
@@ -564,6 +592,7 @@ int hsgn_enqueue(hsgn_handle_t H, double dt, int64_t n_steps, void* stream) {
 }
 
 int hsgn_run(hsgn_handle_t H, double dt, int64_t n_steps, void* stream) {
+    if (!H || !valid_dt(H, dt) || n_steps < 0) return HSGN_ERR_INVALID_ARG;
     const int rc = hsgn_enqueue(H, dt, n_steps, stream);
     if (rc != HSGN_OK) return rc;
     return read_error(H, as_stream(stream));
@@ -607,6 +636,7 @@ int hsgn_check(hsgn_handle_t H, void* stream) {
 
 int hsgn_suggest_dt(hsgn_handle_t H, double cfl, double mcfl, double* dt_out, void* stream) {
     if (!H || !dt_out || !(cfl > 0.0)) return HSGN_ERR_INVALID_ARG;
+    if (H->batched) return HSGN_ERR_UNIMPLEMENTED;
     cudaStream_t st = as_stream(stream);
     double* tmp = H->spd + 2;
     if (cudaMemsetAsync(tmp, 0, 2 * sizeof(double), st) != cudaSuccess) return HSGN_ERR_CUDA;
@@ -628,7 +658,7 @@ int hsgn_suggest_dt(hsgn_handle_t H, double cfl, double mcfl, double* dt_out, vo
 int hsgn_stage(hsgn_handle_t H, const double* const base[4], const double* const lin[4],
                double tau, double speed, double* const out[4], void* stream) {
     if (!H || !base || !lin || !out || !(tau > 0.0) || !(speed >= 0.0)) return HSGN_ERR_INVALID_ARG;
-    if (H->mixed) return HSGN_ERR_UNIMPLEMENTED;
+    if (H->mixed || H->batched) return HSGN_ERR_UNIMPLEMENTED;
     for (int k = 0; k < 4; ++k)
         if (!base[k] || !lin[k] || !out[k]) return HSGN_ERR_INVALID_ARG;
     cudaStream_t st = as_stream(stream);
@@ -647,6 +677,148 @@ int hsgn_adjoint(hsgn_handle_t H, double dt, int64_t n_steps, int64_t n_gauges,
     (void)H; (void)dt; (void)n_steps; (void)n_gauges; (void)gauge_cells; (void)gauge_data;
     (void)grad_h0; (void)misfit; (void)stream;
     return HSGN_ERR_UNIMPLEMENTED;
+}
+
+int hsgn_create_batched(int32_t count, const int64_t* n, const double* x_left,
+                        const double* x_right, const double* lambda, double g, int32_t bc,
+                        int32_t flags, hsgn_handle_t* out) {
+    if (!out) return HSGN_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (count < 1 || !n || !x_left || !x_right || !lambda) return HSGN_ERR_INVALID_ARG;
+    if (bc != HSGN_BC_PERIODIC && bc != HSGN_BC_TRANSMISSIVE) return HSGN_ERR_INVALID_ARG;
+    if (!(g > 0.0) || !std::isfinite(g)) return HSGN_ERR_INVALID_ARG;
+    if (flags & ~(int32_t)(HSGN_RUSANOV_LOCAL | HSGN_MIXED)) return HSGN_ERR_UNIMPLEMENTED;
+    std::vector<InstInfo> info((size_t)count);
+    std::vector<int32_t> binst;
+    int64_t cells = 0;
+    int64_t blocks = 0;
+    for (int32_t k = 0; k < count; ++k) {
+        const int64_t nk = n[k];
+        if (nk < 3 || nk > (int64_t)SEP_ROWS * AS) return HSGN_ERR_INVALID_ARG;
+        if (!(x_right[k] > x_left[k]) || !std::isfinite(x_left[k]) || !std::isfinite(x_right[k]))
+            return HSGN_ERR_INVALID_ARG;
+        if (!(lambda[k] >= 0.0) || !std::isfinite(lambda[k])) return HSGN_ERR_INVALID_ARG;
+        const BlockSplit s = make_split(nk, AS);
+        InstInfo& I = info[(size_t)k];
+        I.cell0 = cells;
+        I.n = nk;
+        I.base = s.base;
+        I.P = s.P;
+        I.rem = s.rem;
+        I.blk0 = (int32_t)blocks;
+        I.pad = 0;
+        I.dx = (x_right[k] - x_left[k]) / (double)nk;
+        I.lam = lambda[k];
+        I.dt = 0.0;
+        for (int32_t b = 0; b < s.P; ++b) binst.push_back(k);
+        cells += nk;
+        blocks += s.P;
+    }
+    hsgn_s* H = new (std::nothrow) hsgn_s;
+    if (!H) return HSGN_ERR_OUT_OF_MEMORY;
+    H->n = cells;
+    H->bc = bc;
+    H->flags = flags | HSGN_MIXED;
+    H->mixed = true;
+    H->batched = true;
+    H->count = count;
+    H->total_blocks = blocks;
+    H->g = g;
+    H->lam = 0.0;
+    H->dx = 0.0;
+    H->inst_h = info;
+    cudaGetDevice(&H->device);
+    const size_t vec = align_up(cells * sizeof(double));
+    const size_t fvec = align_up((cells + count) * sizeof(float));
+    const size_t recb = align_up(3 * cells * sizeof(float4));
+    size_t total = 4 * vec + 4 * fvec + recb;
+    total += align_up(BLK_STRIDE * blocks * sizeof(float)) + align_up(blocks * sizeof(float));
+    total += align_up(count * sizeof(InstInfo)) + align_up(blocks * sizeof(int32_t));
+    total += 3 * align_up(count * sizeof(double));
+    total += align_up(4 * sizeof(double)) + align_up(sizeof(unsigned));
+    if (cudaMalloc(&H->mem, total) != cudaSuccess) {
+        cudaGetLastError();
+        delete H;
+        return HSGN_ERR_OUT_OF_MEMORY;
+    }
+    unsigned char* p = H->mem;
+    auto take = [&](size_t bytes) {
+        unsigned char* r = p;
+        p += bytes;
+        return r;
+    };
+    for (int k = 0; k < 4; ++k) H->U[k] = reinterpret_cast<double*>(take(vec));
+    H->G1 = reinterpret_cast<float*>(take(fvec));
+    H->dq1 = reinterpret_cast<float*>(take(fvec));
+    H->dm1 = reinterpret_cast<float*>(take(fvec));
+    H->dr1 = reinterpret_cast<float*>(take(fvec));
+    H->mrec = reinterpret_cast<float4*>(take(recb));
+    H->mblk = reinterpret_cast<float*>(take(align_up(BLK_STRIDE * blocks * sizeof(float))));
+    H->ms_ = reinterpret_cast<float*>(take(align_up(blocks * sizeof(float))));
+    H->inst = reinterpret_cast<InstInfo*>(take(align_up(count * sizeof(InstInfo))));
+    H->blk_inst = reinterpret_cast<int32_t*>(take(align_up(blocks * sizeof(int32_t))));
+    H->speeds = reinterpret_cast<double*>(take(align_up(count * sizeof(double))));
+    H->speeds_tmp = reinterpret_cast<double*>(take(2 * align_up(count * sizeof(double))));
+    H->spd = reinterpret_cast<double*>(take(align_up(4 * sizeof(double))));
+    H->err = reinterpret_cast<unsigned*>(take(align_up(sizeof(unsigned))));
+    cudaError_t e = cudaMemset(H->mem, 0, total);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(H->inst, info.data(), count * sizeof(InstInfo), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(H->blk_inst, binst.data(), blocks * sizeof(int32_t), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = set_smem(k_mixed_assemble<XT, XM, BC_PERIODIC>, sizeof(MixedShared<XT, XM>));
+    if (e == cudaSuccess)
+        e = set_smem(k_mixed_assemble<XT, XM, BC_TRANSMISSIVE>, sizeof(MixedShared<XT, XM>));
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&H->cap, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        if (H->cap) cudaStreamDestroy(H->cap);
+        cudaFree(H->mem);
+        delete H;
+        return HSGN_ERR_CUDA;
+    }
+    *out = H;
+    return HSGN_OK;
+}
+
+int hsgn_batched_set_dt(hsgn_handle_t H, const double* dt) {
+    if (!H || !H->batched || !dt) return HSGN_ERR_INVALID_ARG;
+    for (int32_t k = 0; k < H->count; ++k)
+        if (!(dt[k] > 0.0) || !std::isfinite(dt[k])) return HSGN_ERR_INVALID_ARG;
+    for (int32_t k = 0; k < H->count; ++k) H->inst_h[(size_t)k].dt = dt[k];
+    if (cudaDeviceSynchronize() != cudaSuccess) return HSGN_ERR_CUDA;
+    if (cudaMemcpy(H->inst, H->inst_h.data(), H->count * sizeof(InstInfo), cudaMemcpyHostToDevice) !=
+        cudaSuccess)
+        return HSGN_ERR_CUDA;
+    return HSGN_OK;
+}
+
+int hsgn_batched_suggest_dt(hsgn_handle_t H, double cfl, double mcfl, double* dt_out,
+                            void* stream) {
+    if (!H || !H->batched || !dt_out || !(cfl > 0.0)) return HSGN_ERR_INVALID_ARG;
+    cudaStream_t st = as_stream(stream);
+    const int32_t c = H->count;
+    double* um = H->speeds_tmp;
+    double* nm = H->speeds_tmp + align_up(c * sizeof(double)) / sizeof(double);
+    k_speeds_batched<<<(unsigned)c, 256, 0, st>>>(H->inst, H->U[0], H->U[1], H->U[2], H->g, um, nm,
+                                                  H->err);
+    if (cudaGetLastError() != cudaSuccess) return HSGN_ERR_CUDA;
+    std::vector<double> hu((size_t)c), hn((size_t)c);
+    if (cudaMemcpyAsync(hu.data(), um, c * sizeof(double), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaMemcpyAsync(hn.data(), nm, c * sizeof(double), cudaMemcpyDeviceToHost, st) != cudaSuccess)
+        return HSGN_ERR_CUDA;
+    const int rc = read_error(H, st);
+    if (rc != HSGN_OK) return rc;
+    for (int32_t k = 0; k < c; ++k) {
+        const double dx = H->inst_h[(size_t)k].dx;
+        if (!(hn[(size_t)k] > 0.0)) return HSGN_ERR_INVALID_ARG;
+        double dt = cfl * dx / hn[(size_t)k];
+        if (mcfl > 0.0 && hu[(size_t)k] > 0.0 && hu[(size_t)k] * dt / dx > mcfl)
+            dt = mcfl * dx / hu[(size_t)k];
+        dt_out[k] = dt;
+    }
+    return HSGN_OK;
 }
 
 int hsgn_tridiag_workspace_bytes(int64_t n, size_t* bytes) {

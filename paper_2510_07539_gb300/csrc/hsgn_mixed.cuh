@@ -94,7 +94,78 @@ struct MixedParams {
     float* s;                            // block separators (after the separator solve)
     double* out[4];                      // U^{n+1} (stage 2)
     unsigned* err;
+    // batch of independent instances (batched != 0): the fields n, split, the
+    // dt-dependent constants and speed above are replaced per block by the
+    // instance's entries
+    int32_t batched;
+    const struct InstInfo* inst;         // per instance
+    const int32_t* blk_inst;             // instance of every global block
+    double* speeds;                      // per-instance Rusanov speed
 };
+
+// One instance of a batch: packed cell offset, size, block split, first global
+// block, grid spacing, relaxation parameter and time step.
+struct InstInfo {
+    int64_t cell0;
+    int64_t n;
+    int64_t base;
+    int32_t P, rem;
+    int32_t blk0, pad;
+    double dx, lam, dt;
+};
+
+// Geometry and constants of the instance that owns a block.
+struct BlockCtx {
+    int64_t cell0, face0;  // packed offsets of the instance's cell 0 and face -1/2
+    int64_t n;             // cells of the instance
+    BlockSplit split;      // the instance's blocks
+    int64_t lb, blk0;      // local block index, global index of block 0
+    int64_t r0;            // first local row of the block
+    int nb;                // rows of the block
+    float tau, tdx, fq, Cc, fd, lt2, ltau, lam;
+    double* speed;
+};
+
+__device__ __forceinline__ BlockCtx make_ctx(const MixedParams& p, int64_t b) {
+    BlockCtx c;
+    if (!p.batched) {
+        c.cell0 = 0;
+        c.face0 = 0;
+        c.n = p.n;
+        c.split = p.split;
+        c.lb = b;
+        c.blk0 = 0;
+        c.tau = p.tau; c.tdx = p.tdx; c.fq = p.fq; c.Cc = p.Cc; c.fd = p.fd;
+        c.lt2 = p.lt2; c.ltau = p.ltau; c.lam = p.lam;
+        c.speed = p.speed;
+    } else {
+        const int k = p.blk_inst[b];
+        const InstInfo I = p.inst[k];
+        c.cell0 = I.cell0;
+        c.face0 = I.cell0 + k;  // instance k's n+1 faces follow those of instances < k
+        c.n = I.n;
+        c.split.n = I.n;
+        c.split.base = I.base;
+        c.split.P = I.P;
+        c.split.rem = I.rem;
+        c.lb = b - I.blk0;
+        c.blk0 = I.blk0;
+        // tau = gamma dt with gamma = 1 - 1/sqrt(2) (Sec. 3.2)
+        const double tau = (1.0 - 1.0 / sqrt(2.0)) * I.dt;
+        c.tau = (float)tau;
+        c.tdx = (float)(tau / I.dx);
+        c.fq = (float)(tau / (2.0 * I.dx));
+        c.Cc = (float)(tau * tau / (I.dx * I.dx));
+        c.fd = (float)(I.lam * tau * tau / (I.dx * I.dx));
+        c.lt2 = (float)(I.lam * tau * tau);
+        c.ltau = (float)(I.lam * tau);
+        c.lam = (float)I.lam;
+        c.speed = p.speeds + k;
+    }
+    c.r0 = c.split.start(c.lb);
+    c.nb = (int)c.split.size(c.lb);
+    return c;
+}
 
 // Face index of G1: face i+1/2 is stored at i+1 (i = -1 .. n-1).
 // Shared memory of the mixed assembly for blocks of at most S = T*M rows; the
@@ -119,11 +190,21 @@ __global__ void __launch_bounds__(T) k_mixed_assemble(const MixedParams p) {
     auto& sm = *reinterpret_cast<MixedShared<T, M>*>(smem_raw);
     const int tid = threadIdx.x;
     const int64_t b = blockIdx.x;
-    const int64_t r0 = p.split.start(b);
-    const int nb = (int)p.split.size(b);
-    const int64_t n = p.n;
+    const BlockCtx X = make_ctx(p, b);
+    const int64_t r0 = X.r0;
+    const int nb = X.nb;
+    const int64_t n = X.n;
     const bool two = p.stage == 2;
     const float wl1 = p.wl1, wb1 = p.wb1;
+    const double* __restrict__ U0 = p.U[0] + X.cell0;
+    const double* __restrict__ U1 = p.U[1] + X.cell0;
+    const double* __restrict__ U2 = p.U[2] + X.cell0;
+    const double* __restrict__ U3 = p.U[3] + X.cell0;
+    const float* __restrict__ G1 = p.G1 + X.face0;
+    const float* __restrict__ dq1p = p.dq1 + X.cell0;
+    const float* __restrict__ dm1p = p.dm1 + X.cell0;
+    const float* __restrict__ dr1p = p.dr1 + X.cell0;
+    float4* __restrict__ rec = p.rec + 3 * X.cell0;
 
     // ---- 0. stage inputs with a 3-cell halo; FP64 differences of U^n. At most
     //         ceil((S+6)/T) cells per thread; all loads of a cell are issued
@@ -135,18 +216,18 @@ __global__ void __launch_bounds__(T) k_mixed_assemble(const MixedParams p) {
         if (j < nb + 6) {
             const int64_t gi = wrap_index(r0 + j - 3, n, BC);
             const int64_t gn = wrap_index(r0 + j - 2, n, BC);
-            const double h0 = __ldg(p.U[0] + gi), q0 = __ldg(p.U[1] + gi);
-            const double m0 = __ldg(p.U[2] + gi), rr0 = __ldg(p.U[3] + gi);
-            const double h1 = __ldg(p.U[0] + gn), q1 = __ldg(p.U[1] + gn), m1 = __ldg(p.U[2] + gn);
+            const double h0 = __ldg(U0 + gi), q0 = __ldg(U1 + gi);
+            const double m0 = __ldg(U2 + gi), rr0 = __ldg(U3 + gi);
+            const double h1 = __ldg(U0 + gn), q1 = __ldg(U1 + gn), m1 = __ldg(U2 + gn);
             float dh1 = 0.f, dq1 = 0.f, dm1 = 0.f, dr1 = 0.f, dh1n = 0.f, dq1n = 0.f, dm1n = 0.f;
             if (two) {
-                const float g0 = __ldg(p.G1 + gi), g1 = __ldg(p.G1 + gi + 1);
-                const float g2 = __ldg(p.G1 + gn), g3 = __ldg(p.G1 + gn + 1);
-                dq1 = __ldg(p.dq1 + gi);
-                dm1 = __ldg(p.dm1 + gi);
-                dr1 = __ldg(p.dr1 + gi);
-                dq1n = __ldg(p.dq1 + gn);
-                dm1n = __ldg(p.dm1 + gn);
+                const float g0 = __ldg(G1 + gi), g1 = __ldg(G1 + gi + 1);
+                const float g2 = __ldg(G1 + gn), g3 = __ldg(G1 + gn + 1);
+                dq1 = __ldg(dq1p + gi);
+                dm1 = __ldg(dm1p + gi);
+                dr1 = __ldg(dr1p + gi);
+                dq1n = __ldg(dq1p + gn);
+                dm1n = __ldg(dm1p + gn);
                 dh1 = g0 - g1;
                 dh1n = g2 - g3;
             }
@@ -169,8 +250,8 @@ __global__ void __launch_bounds__(T) k_mixed_assemble(const MixedParams p) {
     }
     __syncthreads();
 
-    const float tau = p.tau, lam = p.lam, g = p.g;
-    const float gspeed = p.local_speed ? 0.f : (float)(*p.speed);
+    const float tau = X.tau, lam = X.lam, g = p.g;
+    const float gspeed = p.local_speed ? 0.f : (float)(*X.speed);
     unsigned bad = 0;
 
     // ---- 1. Rusanov fluxes of U_l at faces f = -2 .. nb (Sec. 4.1)
@@ -196,7 +277,7 @@ __global__ void __launch_bounds__(T) k_mixed_assemble(const MixedParams p) {
 
     // ---- 2. increments and coefficients at cells c = -1 .. nb:
     //         r^dag = r_b + dr' + lambda tau, m^dag = m_b + dm' + lambda tau^2, q^dag = q_b + dq
-    const float lt2 = p.lt2, tdx = p.tdx;
+    const float lt2 = X.lt2, tdx = X.tdx;
     for (int j = tid; j < nb + 2; j += T) {
         const int c3 = pd(j + 2);
         const float drv = -tdx * (sm.Fr[j + 1] - sm.Fr[j]);
@@ -243,12 +324,12 @@ __global__ void __launch_bounds__(T) k_mixed_assemble(const MixedParams p) {
     for (int i = tid; i < nb; i += T) {
         const int64_t gi = r0 + i;
         const int c1 = pd(i + 1), f3 = pd(i + 3);
-        p.rec[3 * gi + 1] = make_float4(sm.dq[c1], sm.dm[c1], sm.dr[c1], sm.be[c1]);
-        p.rec[3 * gi + 2] = make_float4(sm.de[c1], sm.Dh[f3], sm.Dm[f3], sm.P0[f3]);
+        rec[3 * gi + 1] = make_float4(sm.dq[c1], sm.dm[c1], sm.dr[c1], sm.be[c1]);
+        rec[3 * gi + 2] = make_float4(sm.de[c1], sm.Dh[f3], sm.Dm[f3], sm.P0[f3]);
     }
 
     // ---- 3. rows of A dh = d - A h_b (face i+1/2 of cell i is index i+3)
-    const float Cc = p.Cc, fq = p.fq, fd = p.fd;
+    const float Cc = X.Cc, fq = X.fq, fd = X.fd;
     auto row = [&](int i, float& a, float& bb, float& c, float& d) {
         const int c0 = pd(i), c1 = pd(i + 1), c2 = pd(i + 2), f2 = pd(i + 2), f3 = pd(i + 3);
         const float bm = 0.5f * (sm.be[c0] + sm.be[c1]);
@@ -289,10 +370,10 @@ __global__ void __launch_bounds__(T) k_mixed_assemble(const MixedParams p) {
     __syncthreads();
     for (int i = tid; i < nb; i += T) {
         const int a = pd(i);
-        p.rec[3 * (r0 + i)] = make_float4(sm.hl[a], sm.ql[a], sm.ml[a], sm.qb[pd(i + 3)]);
+        rec[3 * (r0 + i)] = make_float4(sm.hl[a], sm.ql[a], sm.ml[a], sm.qb[pd(i + 3)]);
     }
     if (tid == 0) {
-        float* s = p.blk + b * BLK_STRIDE;
+        float* s = p.blk + (X.blk0 + X.lb) * BLK_STRIDE;
         s[0] = sm.lastrow[0]; s[1] = sm.lastrow[1]; s[2] = sm.lastrow[2]; s[3] = sm.lastrow[3];
         s[4] = sm.hl[0]; s[5] = sm.ql[0]; s[6] = sm.ml[0];
         if (nb >= 2) {
@@ -313,12 +394,10 @@ struct MixedCell {
     float Dh, Dm;      // base differences at the face to the right
 };
 
-__device__ __forceinline__ MixedCell mixed_cell(const MixedParams& p, int64_t j, int64_t b,
-                                                bool ghost, float& P0) {
+__device__ __forceinline__ MixedCell mixed_cell(const float4* __restrict__ rec, int64_t j,
+                                                float sl, float sr, bool ghost, float& P0) {
     MixedCell c;
-    const float sl = p.s[b == 0 ? p.split.P - 1 : b - 1];
-    const float sr = p.s[b];
-    const float4 r0 = p.rec[3 * j], r1 = p.rec[3 * j + 1], r2 = p.rec[3 * j + 2];
+    const float4 r0 = rec[3 * j], r1 = rec[3 * j + 1], r2 = rec[3 * j + 2];
     c.dh = r0.x - sl * r0.y - sr * r0.z;
     c.qb = r0.w;
     c.dq = r1.x;
@@ -335,47 +414,61 @@ __device__ __forceinline__ MixedCell mixed_cell(const MixedParams& p, int64_t j,
 
 // Face mass flux (divided by dx) between cells L and R; the face differences
 // are those stored with L. Both neighbours evaluate it identically.
-__device__ __forceinline__ float face_flux(const MixedParams& p, const MixedCell& L,
+__device__ __forceinline__ float face_flux(const BlockCtx& X, const MixedCell& L,
                                            const MixedCell& R) {
     const float qsum = (L.qb + R.qb) + (L.dq + R.dq);
     const float dmf = L.Dm + (R.dm - L.dm);
     const float dhf = L.Dh + (R.dh - L.dh);
-    return p.fq * qsum - p.fd * (0.5f * (L.de + R.de)) * dmf - p.Cc * (0.5f * (L.be + R.be)) * dhf;
+    return X.fq * qsum - X.fd * (0.5f * (L.de + R.de)) * dmf - X.Cc * (0.5f * (L.be + R.be)) * dhf;
 }
 
+// One CTA per block; each thread handles rows of the block.
 template <int BC>
-__global__ void k_mixed_backsub(const MixedParams p) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int lane = threadIdx.x & 31;
+__global__ void __launch_bounds__(256) k_mixed_backsub(const MixedParams p) {
+    __shared__ float red[8];
+    const BlockCtx X = make_ctx(p, blockIdx.x);
+    const int64_t n = X.n;
+    const BlockSplit& sp = X.split;
+    const float* __restrict__ s = p.s + X.blk0;
+    const float4* __restrict__ rec = p.rec + 3 * X.cell0;
+    const float* __restrict__ G1 = p.G1 + X.face0;
+    const int64_t lb = X.lb;
+    const int64_t lbl = lb == 0 ? sp.P - 1 : lb - 1, lbr = lb + 1 == sp.P ? 0 : lb + 1;
+    const float s_ll = s[lbl == 0 ? sp.P - 1 : lbl - 1];  // separators around the block
+    const float s_l = s[lbl], s_c = s[lb], s_r = s[lbr];
     float umax = 0.f;
-    if (i < p.n) {
-        const int64_t il = wrap_index(i - 1, p.n, BC), ir = wrap_index(i + 1, p.n, BC);
+    for (int t = threadIdx.x; t < X.nb; t += blockDim.x) {
+        const int64_t i = X.r0 + t;  // local row
+        const int64_t il = wrap_index(i - 1, n, BC), ir = wrap_index(i + 1, n, BC);
         const bool gl = (BC == BC_TRANSMISSIVE) && i == 0;
-        const bool gr = (BC == BC_TRANSMISSIVE) && i == p.n - 1;
-        const int64_t bi = p.split.block_of(i);
-        const int64_t bl = il == i - 1 ? p.split.left_of(bi, i - 1) : (il == i ? bi : p.split.P - 1);
-        const int64_t br = ir == i + 1 ? p.split.right_of(bi, i + 1) : (ir == i ? bi : 0);
+        const bool gr = (BC == BC_TRANSMISSIVE) && i == n - 1;
+        // separators (s_{B-1}, s_B) of the block B of each of the three cells
+        const bool lin = (il == i - 1 && t > 0) || il == i;          // left cell in this block
+        const bool rin = (ir == i + 1 && t + 1 < X.nb) || ir == i;   // right cell in this block
         float P0, P0l, P0r;
-        const MixedCell C = mixed_cell(p, i, bi, gr, P0);
-        const MixedCell Lc = mixed_cell(p, il, bl, gl, P0l);
-        const MixedCell Rc = mixed_cell(p, ir, br, gr, P0r);
+        const MixedCell C = mixed_cell(rec, i, s_l, s_c, gr, P0);
+        const MixedCell Lc = lin ? mixed_cell(rec, il, s_l, s_c, gl, P0l)
+                                 : mixed_cell(rec, il, s_ll, s_l, gl, P0l);
+        const MixedCell Rc = rin ? mixed_cell(rec, ir, s_l, s_c, gr, P0r)
+                                 : mixed_cell(rec, ir, s_c, s_r, gr, P0r);
         // own base depth (rounded): U^n of this cell is read here, before this
         // thread overwrites it
-        float hbf = f32_of(p.U[0][i]);
-        if (p.stage == 2) hbf = fmaf(p.wb1, p.G1[i] - p.G1[i + 1], hbf);
-        const float Gp = face_flux(p, C, Rc);   // face i+1/2
-        const float Gm = face_flux(p, Lc, C);   // face i-1/2
+        const int64_t pi = X.cell0 + i;
+        float hbf = f32_of(p.U[0][pi]);
+        if (p.stage == 2) hbf = fmaf(p.wb1, G1[i] - G1[i + 1], hbf);
+        const float Gp = face_flux(X, C, Rc);  // face i+1/2
+        const float Gm = face_flux(X, Lc, C);  // face i-1/2
         // q: tau/(2dx) beta (hbar_{i+1} - hbar_{i-1}), lambda tau/(2dx) delta (m^dag_{i+1} - m^dag_{i-1})
         const float dhc = (Lc.Dh + C.Dh) + (Rc.dh - Lc.dh);
         const float dmc = (Lc.Dm + C.Dm) + (Rc.dm - Lc.dm);
-        const float dQ = C.dq - p.fq * C.be * dhc - p.lam * p.fq * C.de * dmc;
+        const float dQ = C.dq - X.fq * C.be * dhc - X.lam * X.fq * C.de * dmc;
         // relaxation pair
         const float hbar = hbf + C.dh;
         const float P = fmaf(C.dh, 2.f * hbf + C.dh, P0);  // hbar^2 - m_b
-        const float E = P - C.dm;                                // hbar^2 - m^
+        const float E = P - C.dm;                           // hbar^2 - m^
         const float h2 = hbar * hbar;
-        const float iDen = __frcp_rn(h2 + p.lt2);
-        const float dR = fmaf(p.ltau * E, iDen, C.dr);
+        const float iDen = __frcp_rn(h2 + X.lt2);
+        const float dR = fmaf(X.ltau * E, iDen, C.dr);
         const float dM = P - E * h2 * iDen;
         unsigned bad = 0;
         if (!pos_finite(hbar)) bad |= HSGN_DEV_ERR_DEPTH;
@@ -383,33 +476,92 @@ __global__ void k_mixed_backsub(const MixedParams p) {
             bad |= HSGN_DEV_ERR_NONFINITE;
         if (bad) flag_error(p.err, bad);
         if (p.stage == 1) {
-            p.G1[i + 1] = Gp;
-            if (i == 0) p.G1[0] = Gm;
-            p.dq1[i] = dQ;
-            p.dm1[i] = dM;
-            p.dr1[i] = dR;
+            p.G1[X.face0 + i + 1] = Gp;
+            if (i == 0) p.G1[X.face0] = Gm;
+            p.dq1[pi] = dQ;
+            p.dm1[pi] = dM;
+            p.dr1[pi] = dR;
         } else {
             const float wb1 = p.wb1;
-            const float Tp = fmaf(wb1, p.G1[i + 1], Gp);
-            const float Tm = fmaf(wb1, p.G1[i], Gm);
-            const double h = p.U[0][i] - (f64_of(Tp) - f64_of(Tm));
-            const double q = p.U[1][i] + f64_of(fmaf(wb1, p.dq1[i], dQ));
-            const double m = p.U[2][i] + f64_of(fmaf(wb1, p.dm1[i], dM));
-            const double r = p.U[3][i] + f64_of(fmaf(wb1, p.dr1[i], dR));
-            p.out[0][i] = h;
-            p.out[1][i] = q;
-            p.out[2][i] = m;
-            p.out[3][i] = r;
-            if (p.track_speed && !bad) umax = fabsf((C.qb + dQ) / hbar);
+            const float Tp = fmaf(wb1, G1[i + 1], Gp);
+            const float Tm = fmaf(wb1, G1[i], Gm);
+            const double h = p.U[0][pi] - (f64_of(Tp) - f64_of(Tm));
+            const double q = p.U[1][pi] + f64_of(fmaf(wb1, p.dq1[pi], dQ));
+            const double m = p.U[2][pi] + f64_of(fmaf(wb1, p.dm1[pi], dM));
+            const double r = p.U[3][pi] + f64_of(fmaf(wb1, p.dr1[pi], dR));
+            p.out[0][pi] = h;
+            p.out[1][pi] = q;
+            p.out[2][pi] = m;
+            p.out[3][pi] = r;
+            if (p.track_speed && !bad) umax = fmaxf(umax, fabsf((C.qb + dQ) / hbar));
         }
     }
     if (p.track_speed) {
+        const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) umax = fmaxf(umax, __shfl_xor_sync(0xffffffffu, umax, o));
-        if (lane == 0 && umax > 0.f)
-            atomicMax(reinterpret_cast<unsigned long long*>(p.speed),
-                      (unsigned long long)__double_as_longlong(f64_of(umax)));
+        if (lane == 0) red[wid] = umax;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            float v = 0.f;
+            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) v = fmaxf(v, red[w]);
+            if (v > 0.f)
+                atomicMax(reinterpret_cast<unsigned long long*>(X.speed),
+                          (unsigned long long)__double_as_longlong(f64_of(v)));
+        }
     }
+}
+
+// Per-instance max |u| and max nu = |u| + sqrt(g h + (lambda/3) eta^2/h^2) of a
+// batch (Sec. 5 time-step rule): one CTA per instance.
+__global__ void __launch_bounds__(256) k_speeds_batched(const InstInfo* inst, const double* h,
+                                                        const double* q, const double* m,
+                                                        double g, double* out_u, double* out_nu,
+                                                        unsigned* err) {
+    __shared__ double ru[8], rn[8];
+    const InstInfo I = inst[blockIdx.x];
+    double um = 0.0, nm = 0.0;
+    bool bad = false;
+    for (int64_t i = I.cell0 + threadIdx.x; i < I.cell0 + I.n; i += blockDim.x) {
+        const double hh = h[i];
+        if (!pos_finite(hh)) {
+            bad = true;
+            continue;
+        }
+        const double u = fabs(q[i] / hh);
+        const double e = m[i] / (hh * hh);
+        um = fmax(um, u);
+        nm = fmax(nm, u + sqrt(g * hh + (I.lam / 3.0) * e * e));
+    }
+    if (bad) flag_error(err, HSGN_DEV_ERR_DEPTH);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        um = fmax(um, __shfl_xor_sync(0xffffffffu, um, o));
+        nm = fmax(nm, __shfl_xor_sync(0xffffffffu, nm, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        ru[threadIdx.x >> 5] = um;
+        rn[threadIdx.x >> 5] = nm;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) {
+            um = fmax(um, ru[w]);
+            nm = fmax(nm, rn[w]);
+        }
+        out_u[blockIdx.x] = um;
+        if (out_nu) out_nu[blockIdx.x] = nm;
+    }
+}
+
+// Separator systems of a batch: one warp per instance, cyclic system of the
+// instance's blocks (at most SEP_ROWS of them).
+__global__ void __launch_bounds__(32) k_sep_batched(const MixedParams p, int reset_speed) {
+    const int k = blockIdx.x;
+    const InstInfo I = p.inst[k];
+    if (reset_speed && threadIdx.x == 0) p.speeds[k] = 0.0;
+    warp_cyclic_solve((int)I.P, BlkRowsT<float>{p.blk + (int64_t)I.blk0 * BLK_STRIDE, I.P},
+                      p.s + I.blk0, p.err);
 }
 
 }  // namespace hsgn

@@ -69,6 +69,10 @@ def load():
         "hsgn_stage": [_P, ctypes.POINTER(_P), ctypes.POINTER(_P), _D, _D, ctypes.POINTER(_P), _P],
         "hsgn_adjoint": [_P, _D, _I64, _I64, _P, _P, _P, _P, _P],
         "hsgn_tridiag_workspace_bytes": [_I64, ctypes.POINTER(ctypes.c_size_t)],
+        "hsgn_create_batched": [ctypes.c_int32, _P, _P, _P, _P, _D, ctypes.c_int32, ctypes.c_int32,
+                                ctypes.POINTER(_P)],
+        "hsgn_batched_set_dt": [_P, _P],
+        "hsgn_batched_suggest_dt": [_P, _D, _D, _P, _P],
         "hsgn_tridiag_solve": [_I64, ctypes.c_int32, _P, _P, _P, _P, _P, _P, ctypes.c_size_t, _P],
     }
     for name, args in sig.items():
@@ -226,3 +230,53 @@ def tridiag_solve_noalloc(a, b, c, d, periodic: bool, out=None, stream=None):
     _check(f(int(b.numel()), int(bool(periodic)), _ptr(a), _ptr(b), _ptr(c), _ptr(d), _ptr(x),
              _stream(stream)), "hsgn_tridiag_solve_noalloc")
     return x
+
+
+class BatchedSolver(Solver):
+    """A batch of independent instances (packed state, mixed precision).
+
+    ns, x_left, x_right, lams: one entry per instance. The state arrays passed
+    to set_state / returned by get_state are the instances' arrays
+    concatenated in order; `offsets` gives each instance's first cell."""
+
+    def __init__(self, ns, x_left, x_right, lams, bc: int = BC_PERIODIC, g: float = 9.81,
+                 flags: int = FLAG_MIXED):
+        import numpy as np
+        load()
+        ns = np.ascontiguousarray(ns, dtype=np.int64)
+        xl = np.ascontiguousarray(x_left, dtype=np.float64)
+        xr = np.ascontiguousarray(x_right, dtype=np.float64)
+        lm = np.ascontiguousarray(lams, dtype=np.float64)
+        self.count = int(len(ns))
+        self.ns = ns
+        self.offsets = np.concatenate([[0], np.cumsum(ns)]).astype(np.int64)
+        self.n = int(self.offsets[-1])
+        self.bc, self.g, self.flags = int(bc), float(g), flags
+        h = _P()
+        _check(_lib.hsgn_create_batched(self.count, ns.ctypes.data, xl.ctypes.data, xr.ctypes.data,
+                                        lm.ctypes.data, float(g), int(bc), int(flags),
+                                        ctypes.byref(h)), "hsgn_create_batched")
+        self._h = h
+
+    def set_dt(self, dts):
+        import numpy as np
+        d = np.ascontiguousarray(dts, dtype=np.float64)
+        if d.shape != (self.count,):
+            raise ValueError(f"expected {self.count} time steps")
+        _check(_lib.hsgn_batched_set_dt(self._h, d.ctypes.data), "hsgn_batched_set_dt")
+
+    def suggest_dt(self, cfl: float, mcfl: float, stream=None):
+        import numpy as np
+        out = np.empty(self.count)
+        _check(_lib.hsgn_batched_suggest_dt(self._h, float(cfl), float(mcfl), out.ctypes.data,
+                                            _stream(stream)), "hsgn_batched_suggest_dt")
+        return out
+
+    def step(self, dt: float = 0.0, stream=None):
+        super().step(0.0, stream)
+
+    def run(self, dt: float = 0.0, n_steps: int = 1, stream=None):
+        super().run(0.0, n_steps, stream)
+
+    def enqueue(self, dt: float = 0.0, n_steps: int = 1, stream=None):
+        super().enqueue(0.0, n_steps, stream)

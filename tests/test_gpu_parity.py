@@ -312,3 +312,67 @@ def test_mixed_rejects_stage_entry():
         with pytest.raises(S().HsgnError) as e:
             s.stage(t, t, 0.01, 0.0)
         assert e.value.code == 6
+
+
+# --------------------------------------------------------------------------
+# batches of independent instances (mixed precision, one launch per kernel)
+# --------------------------------------------------------------------------
+def batch_case(seed, count, n_min=64, n_max=3000):
+    insts = inputs.batched_instances(seed, count, n_min=n_min, n_max=n_max)
+    ns = [it.n for it in insts]
+    xl = [-0.5 * it.n * it.dx for it in insts]
+    xr = [0.5 * it.n * it.dx for it in insts]
+    lams = [it.lam for it in insts]
+    return insts, ns, xl, xr, lams
+
+
+def test_batched_equals_single_instance_mixed_bitwise():
+    insts, ns, xl, xr, lams = batch_case(11, 6)
+    with S().BatchedSolver(ns, xl, xr, lams) as B:
+        packed = [np.concatenate([it.state[k] for it in insts]) for k in range(4)]
+        B.set_state(*(dev(a) for a in packed))
+        dts = B.suggest_dt(2.0, 0.5)
+        B.set_dt(dts)
+        B.run(0.0, 5)
+        got = [t.cpu().numpy() for t in B.get_state()]
+    for k_inst, it in enumerate(insts):
+        o0, o1 = int(B.offsets[k_inst]), int(B.offsets[k_inst + 1])
+        single = mixed_run(it.n, xl[k_inst], xr[k_inst], 0, it.lam, it.state, dts[k_inst], 5)
+        for k in range(4):
+            np.testing.assert_array_equal(got[k][o0:o1], single[k])
+
+
+def test_batched_matches_oracle_per_instance():
+    insts, ns, xl, xr, lams = batch_case(12, 12, n_min=256, n_max=8192)
+    with S().BatchedSolver(ns, xl, xr, lams) as B:
+        packed = [np.concatenate([it.state[k] for it in insts]) for k in range(4)]
+        B.set_state(*(dev(a) for a in packed))
+        dts = B.suggest_dt(4.0, 0.5)
+        B.set_dt(dts)
+        B.run(0.0, 30)
+        got = [t.cpu().numpy() for t in B.get_state()]
+    for k_inst, it in enumerate(insts):
+        o0, o1 = int(B.offsets[k_inst]), int(B.offsets[k_inst + 1])
+        p = oracle.Params(it.n, it.dx, 0, lam=it.lam)
+        ref = oracle.run(p, it.state, dts[k_inst], 30)
+        # 30 steps at CFL_IMEX = 4: the lambda = 1000, a = 0.35 instances lose
+        # most (the relaxation update scales FP32 rounding by lambda tau)
+        assert rel_l2(got[0][o0:o1], ref[0]) < 5e-6, (k_inst, rel_l2(got[0][o0:o1], ref[0]))
+        assert rel_l2(got[2][o0:o1], ref[2]) < 5e-6
+        assert abs(math.fsum(got[0][o0:o1]) - math.fsum(it.state[0])) <= 1e-13 * math.fsum(it.state[0])
+
+
+def test_batched_suggest_dt_matches_oracle_and_rejects_bad_use():
+    insts, ns, xl, xr, lams = batch_case(13, 5)
+    with S().BatchedSolver(ns, xl, xr, lams) as B:
+        packed = [np.concatenate([it.state[k] for it in insts]) for k in range(4)]
+        B.set_state(*(dev(a) for a in packed))
+        dts = B.suggest_dt(2.5, 0.5)
+        for k_inst, it in enumerate(insts):
+            ref, _, _ = oracle.suggest_dt(oracle.Params(it.n, it.dx, 0, lam=it.lam), it.state,
+                                          2.5, 0.5)
+            assert abs(dts[k_inst] - ref) <= 1e-14 * ref
+        with pytest.raises(S().HsgnError):
+            S().Solver.step(B, 0.1)  # a batch takes dt = 0
+        with pytest.raises(S().HsgnError):
+            B.set_dt(np.zeros(len(ns)))
