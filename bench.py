@@ -227,6 +227,23 @@ def run_reference(args):
 
 
 # ---------------------------------------------------------------------------
+# replicas: whole-job value from per-rank timings
+# ---------------------------------------------------------------------------
+def combine_ranks(dist, local_ms: float, local_units: float, device="cpu"):
+    """Max over ranks of the timed region and sum over ranks of the work done.
+    The job value is (sum of units) / (slowest rank's time): each rank runs
+    an independent replica of the workload (no data exchange)."""
+    import torch
+    if dist is None:
+        return local_ms, local_units
+    t = torch.tensor([local_ms], dtype=torch.float64, device=device)
+    u = torch.tensor([local_units], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(u.item())
+
+
+# ---------------------------------------------------------------------------
 # GPU arm
 # ---------------------------------------------------------------------------
 def sep_launches(n: int) -> int:
@@ -285,10 +302,7 @@ def time_path(S, torch, flags, n, xl, xr, lams, Ud, steps, warmup, flush, stream
     prof = [s.profile_read(reset=True) for s in sols]
     for s in sols:
         s.profile(False)
-    if dist:
-        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms, _ = combine_ranks(dist, ms, 0.0, device="cuda")
     tot = {k: (sum(p[k][0] for p in prof), sum(p[k][1] for p in prof))
            for k in ("assemble", "reduced", "backsub")}
     return sols, dts, ms, tot, clk
@@ -467,13 +481,10 @@ def run_ours(args):
                 s.get_state(out=ho)
         e1.record(stream)
         torch.cuda.synchronize()
-        ems = e0.elapsed_time(e1)
-        if dist:
-            t = torch.tensor([ems], device="cuda", dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ems = float(t.item())
+        ems, units = combine_ranks(dist, e0.elapsed_time(e1), 2.0 * n * len(lams) * k_e2e,
+                                   device="cuda")
         nbytes = 4 * n * 8 * len(lams)
-        e2e = {"value": 2.0 * n * len(lams) * k_e2e * world / (ems / 1e3), "unit": UNIT,
+        e2e = {"value": units / (ems / 1e3), "unit": UNIT,
                "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes, "steps": k_e2e}
 
     # ---- CPU oracle baseline and the error of both paths against it

@@ -54,8 +54,9 @@ class _Params(ctypes.Structure):
         ("g", ctypes.c_double),
         ("lam", ctypes.c_double),
         ("rusanov", ctypes.c_int32),
-        ("pad_", ctypes.c_int32),
+        ("form", ctypes.c_int32),
         ("speed", ctypes.c_double),
+        ("bathy", ctypes.POINTER(ctypes.c_double)),
     ]
 
 
@@ -115,14 +116,17 @@ class Params:
     """Grid and physics of one hSGN instance (uniform 1D grid of n cells)."""
 
     def __init__(self, n, dx, bc=BC_PERIODIC, g=9.81, lam=100.0, delta_half=False,
-                 rusanov=1, speed=0.0):
+                 rusanov=1, speed=0.0, form=0, bathy=None):
         self.n, self.dx, self.bc, self.g, self.lam = int(n), float(dx), int(bc), float(g), float(lam)
         self.delta_half = bool(delta_half)
         self.rusanov, self.speed = int(rusanov), float(speed)
+        self.form = int(form)
+        self.bathy = None if bathy is None else _f64(bathy, self.n)
 
     def _c(self) -> _Params:
+        bp = _ptr(self.bathy) if self.bathy is not None else None
         return _Params(self.n, self.dx, self.bc, int(self.delta_half), self.g, self.lam,
-                       self.rusanov, 0, self.speed)
+                       self.rusanov, self.form, self.speed, bp)
 
 
 def tridiag_solve(a, b, c, d, periodic: bool) -> np.ndarray:

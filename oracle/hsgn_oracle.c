@@ -39,6 +39,22 @@
  *   R6  periodic: indices wrap and the matrix is cyclic; transmissive:
  *       zero-order ghost copies of every per-cell quantity, so the end rows of
  *       the matrix are Neumann rows;
+ *   R7  bathymetry (form 1): the paper writes the model with a bottom (Sec.
+ *       2.3, eq. (hSGNb_eq)) but derives the semi-implicit scheme only for a
+ *       flat one. Form 1 keeps the splitting and the tridiagonal structure and
+ *       is well balanced. With b_t = 0 the third equation of (hSGNb_eq) is
+ *       (h eta)_t + (h u eta)_x = h w - (3/2) h u b_x (explicit source), the
+ *       pressure p = g h^2/2 + eta p~ is the flat one, and the momentum gets the
+ *       source -(g h + (3/2) p~) b_x. The implicit pressure is linearised about
+ *       the linearisation state: p^ + beta (hbar - h_l) with
+ *       p^ = p(h_l, m_l) + lambda alpha_l (m^dag b_1(h_l) - m_l); face forces
+ *       F_{i+1/2} = p^_{i+1} - p^_i + (g h + (3/2) p~)_{i+1/2} (b_{i+1} - b_i)
+ *                 + beta_{i+1/2} ((hbar_{i+1} - hbar_i) - (h_l,i+1 - h_l,i))
+ *       drive both the depth rows, Delta[hbar]_i = h_b,i - tau/(2dx)
+ *       (q^dag_{i+1} - q^dag_{i-1}) + tau^2/dx^2 (Phi_{i+1/2} - Phi_{i-1/2})
+ *       with Phi = F - beta (hbar_{i+1} - hbar_i), and the momentum,
+ *       qbar_i = q^dag_i - tau/(2dx) (F_{i+1/2} + F_{i-1/2}). At a lake at rest
+ *       (u = 0, eta = h, w = 0, h + b = const) every term cancels exactly;
  *   R9  nu = |u| + sqrt(g h + (lambda/3) eta^2/h^2) (the form of eq. (eq:hSGN_c)).
  *
  * State layout: four arrays of n cells each, h, q = h u, m = h eta, r = h w.
@@ -82,8 +98,9 @@ typedef struct {
     double g;           /* gravity */
     double lambda;      /* relaxation parameter, >= 0 */
     int32_t rusanov;    /* 0: local speed max(|u^L|,|u^R|); 1: global speed (R5) */
-    int32_t pad_;
+    int32_t form;       /* 0: the printed flat-bottom scheme; 1: well-balanced form (R7) */
     double speed;       /* global Rusanov speed of the current step (rusanov == 1) */
+    const double* bathy; /* bottom b per cell (form 1; NULL = flat) */
 } oracle_params;
 
 /* Neighbour index: wrap (periodic) or clamp to the boundary cell
@@ -256,9 +273,13 @@ static int stage_impl(const oracle_params* p,
 
     /* (2) starred values and the coefficients of eqs. (eq:hSGN_alpha) and
      * (GN_hyp_eq_semi_fully_discrete), per cell. */
+    const int wb = p->form == 1;
+    const double* bb = p->bathy;
     for (int64_t i = 0; i < n; ++i) {
         rs[i] = rb[i] - (tau / dx) * (Fr[i + 1] - Fr[i]) + lam * tau;
         ms[i] = mb[i] - (tau / dx) * (Fm[i + 1] - Fm[i]) + tau * rs[i];
+        if (wb && bb) /* -(3/2) h u b_x of the (h eta) equation, from U_l */
+            ms[i] -= tau * 1.5 * ql[i] * (bb[nb(p, i + 1)] - bb[nb(p, i - 1)]) / (2.0 * dx);
         qs[i] = qb[i] - (tau / dx) * (Fq[i + 1] - Fq[i]);
         const double h = hl[i];
         if (!(h > 0.0)) { rc = ORACLE_ERR_DEPTH; goto done; }
@@ -274,7 +295,31 @@ static int stage_impl(const oracle_params* p,
     }
 
     /* (3) rows of Delta[h]_i = h^dagger_i. Interface values are means (R2);
-     * the delta term carries factor 1 with means (R3). */
+     * the delta term carries factor 1 with means (R3). Form 1 (R7) replaces
+     * the delta term by the explicit face forces Phi. */
+    double* Phi = NULL;
+    if (wb) {
+        Phi = (double*)malloc((size_t)(n + 1) * sizeof(double)); /* face k+1/2 at k+1 */
+        double* ph = (double*)malloc((size_t)n * sizeof(double));
+        double* pt = (double*)malloc((size_t)n * sizeof(double));
+        if (!Phi || !ph || !pt) { free(ph); free(pt); rc = ORACLE_ERR_NOMEM; goto done; }
+        for (int64_t i = 0; i < n; ++i) {
+            const double h = hl[i], eta = ml[i] / h;
+            const double ptil = (lam / 3.0) * (1.0 - eta / h);
+            const double alpha = -(2.0 * eta / h - 1.0) / (3.0 * h);
+            const double b1 = h * h / (h * h + lam * tau * tau);
+            ph[i] = g * h * h / 2.0 + eta * ptil + lam * alpha * (ms[i] * b1 - ml[i]);
+            pt[i] = ptil;
+        }
+        for (int64_t k = -1; k < n; ++k) {
+            const int64_t i0 = nb(p, k), i1 = nb(p, k + 1);
+            const double db = bb ? bb[i1] - bb[i0] : 0.0;
+            const double bbar = 0.5 * (beta[i0] + beta[i1]);
+            Phi[k + 1] = (ph[i1] - ph[i0]) + (g * 0.5 * (hl[i0] + hl[i1]) + 1.5 * 0.5 * (pt[i0] + pt[i1])) * db
+                       - bbar * (hl[i1] - hl[i0]);
+        }
+        free(ph); free(pt);
+    }
     {
         const double Cc = tau * tau / (dx * dx);
         const double fd = (p->delta_half ? 0.5 : 1.0) * lam * tau * tau / (dx * dx);
@@ -284,8 +329,11 @@ static int stage_impl(const oracle_params* p,
             const double bp = 0.5 * (beta[i] + beta[ir]);   /* beta_{i+1/2} */
             const double dm = 0.5 * (delta[il] + delta[i]);
             const double dp = 0.5 * (delta[i] + delta[ir]);
-            D[i] = hb[i] - (tau / (2.0 * dx)) * (qs[ir] - qs[il])
-                 + fd * (dp * (ms[ir] - ms[i]) - dm * (ms[i] - ms[il]));
+            if (wb)
+                D[i] = hb[i] - (tau / (2.0 * dx)) * (qs[ir] - qs[il]) + Cc * (Phi[i + 1] - Phi[i]);
+            else
+                D[i] = hb[i] - (tau / (2.0 * dx)) * (qs[ir] - qs[il])
+                     + fd * (dp * (ms[ir] - ms[i]) - dm * (ms[i] - ms[il]));
             A[i] = -Cc * bm;
             C[i] = -Cc * bp;
             B[i] = 1.0 + Cc * (bm + bp);
@@ -307,8 +355,16 @@ static int stage_impl(const oracle_params* p,
         const int64_t il = nb(p, i - 1), ir = nb(p, i + 1);
         const double h = hbar[i];
         if (!(h > 0.0)) { rc = ORACLE_ERR_DEPTH; goto done; }
-        const double q = qs[i] - (tau / (2.0 * dx)) * beta[i] * (hbar[ir] - hbar[il])
-                       - (lam * tau / (2.0 * dx)) * delta[i] * (ms[ir] - ms[il]);
+        double q;
+        if (wb) {
+            /* face forces F = Phi + beta_{face} (hbar jump) on both sides */
+            const double Fp = Phi[i + 1] + 0.5 * (beta[i] + beta[ir]) * (hbar[ir] - hbar[i]);
+            const double Fm_ = Phi[i] + 0.5 * (beta[il] + beta[i]) * (hbar[i] - hbar[il]);
+            q = qs[i] - (tau / (2.0 * dx)) * (Fp + Fm_);
+        } else {
+            q = qs[i] - (tau / (2.0 * dx)) * beta[i] * (hbar[ir] - hbar[il])
+              - (lam * tau / (2.0 * dx)) * delta[i] * (ms[ir] - ms[il]);
+        }
         const double m = ms[i] / (1.0 + lam * tau * tau / (h * h));
         const double r = rs[i] - lam * tau * m / (h * h);
         if (!isfinite(h) || !isfinite(q) || !isfinite(m) || !isfinite(r)) {
@@ -331,6 +387,7 @@ static int stage_impl(const oracle_params* p,
     }
 
 done:
+    free(Phi);
     free(Fq); free(Fm); free(Fr); free(qs); free(ms); free(rs); free(beta); free(delta);
     free(A); free(B); free(C); free(D); free(hbar);
     return rc;

@@ -353,3 +353,112 @@ def test_errors_reported():
         oracle.step(oracle.Params(n, dx, 0, lam=-1.0), (h, 0 * h, h * h, 0 * h), 0.01)
     with pytest.raises(oracle.OracleError):
         oracle.step(oracle.Params(2, dx, 0, lam=1.0), (h[:2], 0 * h[:2], h[:2], 0 * h[:2]), 0.01)
+
+
+# --------------------------------------------------------------------------
+# well-balanced bathymetry form (reading R7)
+# --------------------------------------------------------------------------
+def _bottom(n, length, seed=5):
+    x, dx = inputs.cell_centres(n, 0.0, length)
+    b = inputs.gaussian_bathymetry(seed, x)
+    return x, dx, b - b.min()
+
+
+@pytest.mark.parametrize("bc", [oracle.BC_PERIODIC, oracle.BC_TRANSMISSIVE])
+@pytest.mark.parametrize("lam", [0.0, 500.0])
+def test_lake_at_rest_is_preserved(bc, lam):
+    # u = 0, eta = h, w = 0, h + b = const: every term of the stage cancels
+    # (one stage is exact to rounding). Per step the face forces carry rounding
+    # of size beta * eps (beta ~ lambda) into q; at exact rest the Rusanov
+    # speed max|u| is zero, so nothing damps it either. After 40 steps the
+    # state stays at rest to 1e-12, while ignoring the bottom source gives
+    # O(1e-2) within 5 steps (next test).
+    n = 400
+    x, dx, b = _bottom(n, 80.0)
+    h = 1.0 - b
+    U = (h, 0 * h, h * h, 0 * h)
+    p = oracle.Params(n, dx, bc, lam=lam, form=1, bathy=b)
+    one = oracle.step(p, U, 0.05)
+    assert np.max(np.abs(one[1])) < 1e-13 and np.max(np.abs(one[0] - h)) < 1e-14
+    V = oracle.run(p, U, 0.05, 40)
+    assert np.max(np.abs(V[0] - h)) < 1e-12
+    assert np.max(np.abs(V[1])) < 1e-12
+    assert np.max(np.abs(V[2] - h * h)) < 1e-12
+    assert np.max(np.abs(V[3])) < 1e-11
+
+
+def test_lake_at_rest_breaks_without_the_bottom_source():
+    # the same state with the bottom ignored (printed flat scheme) is not at rest
+    n = 400
+    x, dx, b = _bottom(n, 80.0)
+    h = 1.0 - b
+    U = (h, 0 * h, h * h, 0 * h)
+    V = oracle.run(oracle.Params(n, dx, 0, lam=500.0), U, 0.05, 5)
+    assert np.max(np.abs(V[1])) > 1e-3
+
+
+@pytest.mark.parametrize("lam,u0", [(0.0, 0.0), (100.0, 0.0), (1000.0, 0.3)])
+def test_wb_form_linear_dispersion(lam, u0):
+    # over a flat bottom the well-balanced form converges to the same hSGN
+    # dispersion relation at second order
+    errs = []
+    for n in (32, 64, 128):
+        om, exact = measured_omega_form(n, lam, u0, form=1)
+        errs.append(abs(om - exact) / exact)
+    assert errs[-1] < 2e-3
+    assert errs[0] / errs[1] > 3.0 and errs[1] / errs[2] > 3.0, errs
+
+
+def measured_omega_form(n, lam, u0, form, h0=1.0, length=20.0, cfl=1.0, periods=0.5, eps=1e-6):
+    dx = length / n
+    x = (np.arange(n) + 0.5) * dx
+    k = 2 * math.pi / length
+    wp = slow_branch(k, h0, lam)
+    eta_hat = lam * eps / (lam - wp * wp * h0 * h0) if lam > 0 else 0.0
+    th = k * x
+    h = h0 + eps * np.cos(th)
+    u = u0 + (wp * eps / (k * h0)) * np.cos(th)
+    eta = h0 + eta_hat * np.cos(th)
+    w = eta_hat * wp * np.sin(th)
+    U = (h, h * u, h * eta, h * w)
+    p = oracle.Params(n, dx, oracle.BC_PERIODIC, lam=lam, form=form, bathy=np.zeros(n))
+    nu = abs(u0) + math.sqrt(G * h0 + lam / 3.0)
+    T = periods * 2 * math.pi / (wp + u0 * k)
+    steps = max(4, int(math.ceil(T / (cfl * dx / nu))))
+    dt = T / steps
+    phase, prev, V = 0.0, 0.0, U
+    for _ in range(steps):
+        V = oracle.step(p, V, dt)
+        z = np.sum((V[0] - h0) * np.exp(-1j * th))
+        ang = -np.angle(z)
+        phase += (ang - prev + math.pi) % (2 * math.pi) - math.pi
+        prev = ang
+    return phase / T, wp + u0 * k
+
+
+def test_wb_form_solitary_convergence_flat():
+    errs = []
+    for n in (200, 400, 800):
+        x, dx = inputs.cell_centres(n, -50.0, 50.0)
+        U = inputs.solitary(x, 1.0, 0.2, 0.0, period=100.0)
+        p = oracle.Params(n, dx, 0, lam=1000.0, form=1, bathy=np.zeros(n))
+        dt, _, _ = oracle.suggest_dt(p, U, 1.0, 0.5)
+        steps = int(math.ceil(1.0 / dt))
+        V = oracle.run(p, U, 1.0 / steps, steps)
+        E = inputs.solitary(x, 1.0, 0.2, 0.0, t=1.0, period=100.0)
+        errs.append(np.sum(np.abs(V[0] - E[0])) / np.sum(np.abs(V[0])))
+    assert errs[0] / errs[1] > 3.0 and errs[1] / errs[2] > 1.8, errs
+
+
+def test_wb_form_mass_and_mirror_over_bathymetry():
+    n = 300
+    x, dx, b = _bottom(n, 60.0, seed=9)
+    h = 1.0 - b + 0.05 * np.exp(-((x - 30.0) ** 2) / 4.0)
+    U = (h, 0.05 * np.sin(2 * np.pi * x / 60.0) * h, h * h, 0 * h)
+    p = oracle.Params(n, dx, oracle.BC_PERIODIC, lam=300.0, form=1, bathy=b)
+    V = oracle.run(p, U, 0.02, 100)
+    assert abs(math.fsum(V[0]) - math.fsum(U[0])) <= 1e-13 * math.fsum(U[0])
+    pm = oracle.Params(n, dx, oracle.BC_PERIODIC, lam=300.0, form=1, bathy=b[::-1])
+    Vm = oracle.run(pm, (U[0][::-1], -U[1][::-1], U[2][::-1], U[3][::-1]), 0.02, 100)
+    for k, s in enumerate((1, -1, 1, 1)):
+        np.testing.assert_allclose(Vm[k], s * V[k][::-1], rtol=0, atol=1e-11)
