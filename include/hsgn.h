@@ -64,6 +64,17 @@ enum {
                                 * hsgn_stage is not available in this form. */
 #define HSGN_RUSANOV_LOCAL 0x10 /* Rusanov speed max(|u^L|,|u^R|) per face instead
                                  * of the global max |u^n| of the step */
+#define HSGN_WELL_BALANCED 0x2  /* variable bottom b(x) (Sec. 2.3, eq. (hSGNb_eq))
+                                 * in a well-balanced extension of the flat-bottom
+                                 * scheme, which the paper does not derive: the
+                                 * (h eta) equation gets the explicit source
+                                 * -(3/2) h u b_x, and the pressure jump plus the
+                                 * bottom force -(g h + (3/2) p~) b_x enter the
+                                 * depth rows and the momentum as face forces
+                                 * linearised about U_l, so that a lake at rest
+                                 * (u = 0, eta = h, w = 0, h + b constant) stays at
+                                 * rest. FP64 only (not with HSGN_MIXED), single
+                                 * instances only. */
 
 typedef struct {
     int64_t n;       /* number of cells, n >= 3 */
@@ -76,10 +87,13 @@ typedef struct {
 typedef struct hsgn_s* hsgn_handle_t;
 
 /* Create an instance: grid, gravity g > 0, relaxation parameter lambda >= 0
- * (Sec. 2.2, eq. (hSGN_eq)). `bathymetry` must be NULL (flat bottom; the
- * paper derives the semi-implicit scheme only for a flat bottom). Allocates
- * the state and workspace on the current device (about 17 doubles per cell in
- * FP64, 4 doubles and 17 floats per cell with HSGN_MIXED).
+ * (Sec. 2.2, eq. (hSGN_eq)). `bathymetry`: NULL for a flat bottom, else n
+ * bottom elevations b_i at the cell centres (host or device memory, copied
+ * during the call; the caller keeps ownership), which requires
+ * HSGN_WELL_BALANCED (INVALID_ARG otherwise). HSGN_WELL_BALANCED with NULL
+ * runs the well-balanced form over a flat bottom. Allocates the state and
+ * workspace on the current device (about 17 doubles per cell in FP64, 19 with
+ * a bottom, 4 doubles and 17 floats per cell with HSGN_MIXED).
  * On success *out owns them until hsgn_destroy. */
 int hsgn_create(const hsgn_grid_t* grid, double g, double lambda, const double* bathymetry,
                 int32_t flags, hsgn_handle_t* out);

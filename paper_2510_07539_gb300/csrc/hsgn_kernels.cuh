@@ -85,10 +85,24 @@ struct StageParams {
     double *qs, *ms, *rs, *be, *de;
     double* blk;          // P * BLK_STRIDE
     unsigned* err;
+    // well-balanced bathymetry form: bottom per cell, face forces Phi_{i+1/2}
+    const double* bathy;
+    double* phi;
 };
 
+// Arrays of the well-balanced form only; empty for the flat-bottom kernel so
+// that its shared memory (and occupancy) is unchanged.
+template <int S, bool WB>
+struct WbShared {
+    double bb[S + 6];             // bottom, cells -3 .. S+2
+    double ph[S + 2], pt[S + 2];  // p^ and p~, cells -1 .. S
+    double Phi[S + 1];            // faces -1/2 .. S-1/2
+};
+template <int S>
+struct WbShared<S, false> {};
+
 // Shared memory of k_stage_assemble for blocks of at most S = T*M rows.
-template <int T, int M>
+template <int T, int M, bool WB = false>
 struct AssembleShared {
     static constexpr int S = T * M;
     double hl[S + 6], ql[S + 6], ml[S + 6], rl[S + 6];  // U_l, cells -3 .. S+2
@@ -97,13 +111,15 @@ struct AssembleShared {
     double qs[S + 2], ms[S + 2], rs[S + 2], be[S + 2], de[S + 2];  // cells -1 .. S
     SepShared<T> sep;
     double lastrow[4];
+    WbShared<S, WB> wb;
 };
 
-// T threads per CTA, M rows per thread in the block elimination.
-template <int T, int M, int BC>
+// T threads per CTA, M rows per thread in the block elimination. WB selects
+// the well-balanced bathymetry form (the printed flat scheme otherwise).
+template <int T, int M, int BC, bool WB>
 __global__ void __launch_bounds__(T) k_stage_assemble(const StageParams p) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    auto& sm = *reinterpret_cast<AssembleShared<T, M>*>(smem_raw);
+    auto& sm = *reinterpret_cast<AssembleShared<T, M, WB>*>(smem_raw);
     const int tid = threadIdx.x;
     const int64_t b = blockIdx.x;
     const int64_t r0 = p.split.start(b);
@@ -129,6 +145,7 @@ __global__ void __launch_bounds__(T) k_stage_assemble(const StageParams p) {
             sm.hl[j] = ah; sm.ql[j] = aq; sm.ml[j] = am; sm.rl[j] = ar;
             sm.hb[j] = ah; sm.qb[j] = aq; sm.mb[j] = am; sm.rb[j] = ar;
         }
+        if constexpr (WB) sm.wb.bb[j] = p.bathy ? p.bathy[gi] : 0.0;
     }
     __syncthreads();
 
@@ -164,7 +181,9 @@ __global__ void __launch_bounds__(T) k_stage_assemble(const StageParams p) {
     for (int j = tid; j < nb + 2; j += T) {
         const int c3 = j + 2;  // smem index of cell c = j-1 in the U arrays
         const double rsv = fma(-tdx, sm.Fr[j + 1] - sm.Fr[j], sm.rb[c3]) + lam * tau;
-        const double msv = fma(tau, rsv, fma(-tdx, sm.Fm[j + 1] - sm.Fm[j], sm.mb[c3]));
+        double msv = fma(tau, rsv, fma(-tdx, sm.Fm[j + 1] - sm.Fm[j], sm.mb[c3]));
+        if constexpr (WB)  // -(3/2) h u b_x of the (h eta) equation (Sec. 2.3, eq. (hSGNb_eq)), from U_l
+            msv -= tau * 1.5 * sm.ql[c3] * (sm.wb.bb[c3 + 1] - sm.wb.bb[c3 - 1]) / (2.0 * dx);
         const double qsv = fma(-tdx, sm.Fq[j + 1] - sm.Fq[j], sm.qb[c3]);
         // coefficients with one reciprocal R = 1/(h (h^2 + lambda tau^2)):
         //   1/h = (h^2 + lambda tau^2) R,  1/beta_1 = h^2/(h^2 + lambda tau^2) = h^3 R,
@@ -189,6 +208,13 @@ __global__ void __launch_bounds__(T) k_stage_assemble(const StageParams p) {
         sm.rs[j] = rsv;
         sm.be[j] = beta;
         sm.de[j] = alpha * ib1;
+        if constexpr (WB) {
+            // p^ = p(h_l, m_l) + lambda alpha (m^dag b_1(h_l) - m_l), p = g h^2/2 + eta p~,
+            // p~ = (lambda/3)(1 - eta/h) (e = eta/h), b_1 = h^2 / (h^2 + lambda tau^2)
+            const double ptil = (lam * (1.0 / 3.0)) * (1.0 - e);
+            sm.wb.pt[j] = ptil;
+            sm.wb.ph[j] = fma(0.5 * g * h, h, eta * ptil) + lam * alpha * fma(msv, h * h * iD, -sm.ml[c3]);
+        }
     }
     __syncthreads();
     if (BC == BC_TRANSMISSIVE && tid == 0) {
@@ -203,6 +229,30 @@ __global__ void __launch_bounds__(T) k_stage_assemble(const StageParams p) {
         }
     }
     __syncthreads();
+
+    if constexpr (WB) {
+        // explicit face forces Phi_{f+1/2}, f = -1 .. nb-1 (smem index f+1):
+        //   p^ jump + (g h + (3/2) p~)_{face} (b jump) - beta_{face} (h_l jump).
+        // Transmissive: both cells of an end face are the same ghost copy, so
+        // every jump and Phi vanish there.
+        for (int f1 = tid; f1 < nb + 1; f1 += T) {
+            const int c0 = f1, c1 = f1 + 1;        // cells f, f+1 in the -1 .. nb arrays
+            const int u0 = f1 + 2, u1 = f1 + 3;    // the same cells in the U_l arrays
+            const double db = sm.wb.bb[u1] - sm.wb.bb[u0];
+            const double dhl = sm.hl[u1] - sm.hl[u0];
+            const double hbar_f = 0.5 * (sm.hl[u0] + sm.hl[u1]);
+            const double ptf = 0.5 * (sm.wb.pt[c0] + sm.wb.pt[c1]);
+            const double bf = 0.5 * (sm.be[c0] + sm.be[c1]);
+            double phi = (sm.wb.ph[c1] - sm.wb.ph[c0]) + fma(g, hbar_f, 1.5 * ptf) * db - bf * dhl;
+            if (BC == BC_TRANSMISSIVE) {
+                const int64_t gf = r0 + f1 - 1;    // face between global cells gf, gf+1
+                if (gf < 0 || gf + 1 > n - 1) phi = 0.0;
+            }
+            sm.wb.Phi[f1] = phi;
+        }
+        __syncthreads();
+        for (int i = tid; i < nb; i += T) p.phi[r0 + i] = sm.wb.Phi[i + 1];
+    }
 
     // back-substitution inputs of the block's own rows
     for (int i = tid; i < nb; i += T) {
@@ -224,8 +274,11 @@ __global__ void __launch_bounds__(T) k_stage_assemble(const StageParams p) {
         const double dm = 0.5 * (sm.de[i] + sm.de[i + 1]);
         const double dp = 0.5 * (sm.de[i + 1] + sm.de[i + 2]);
         const double msc = sm.ms[i + 1];
-        d = fma(-fq, sm.qs[i + 2] - sm.qs[i], sm.hb[i + 3]) +
-            fd * (dp * (sm.ms[i + 2] - msc) - dm * (msc - sm.ms[i]));
+        if constexpr (WB)
+            d = fma(-fq, sm.qs[i + 2] - sm.qs[i], sm.hb[i + 3]) + Cc * (sm.wb.Phi[i + 1] - sm.wb.Phi[i]);
+        else
+            d = fma(-fq, sm.qs[i + 2] - sm.qs[i], sm.hb[i + 3]) +
+                fd * (dp * (sm.ms[i + 2] - msc) - dm * (msc - sm.ms[i]));
         a = -Cc * bm;
         c = -Cc * bp;
         bb = fma(Cc, bm + bp, 1.0);
@@ -498,6 +551,7 @@ struct BacksubParams {
     BlockSplit split;
     const double *y, *v, *w, *s;
     const double *qs, *ms, *rs, *be, *de;
+    const double* phi;    // face forces Phi_{i+1/2} (well-balanced form)
     double* out[4];
     double* speed;
     unsigned* err;
@@ -517,7 +571,7 @@ __device__ __forceinline__ double hbar_at(const BacksubParams& p, int64_t i, int
 // i.e. with D = hbar^2 + lambda tau^2: mbar = m^dag hbar^2 / D, rbar = r^dag - lambda tau m^dag / D.
 // The neighbours' hbar come from the adjacent lanes; the lanes at the ends of
 // a warp compute their outer neighbour themselves.
-template <int BC>
+template <int BC, bool WB>
 __global__ void k_backsub(const BacksubParams p) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int lane = threadIdx.x & 31;
@@ -536,8 +590,17 @@ __global__ void k_backsub(const BacksubParams p) {
         const double hl = (lane == 0 || il != i - 1) ? hbar_at(p, il, bl) : hl_s;
         const double hr = (lane == 31 || ir != i + 1) ? hbar_at(p, ir, br) : hr_s;
         const double fq = p.tau / (2.0 * p.dx);
-        const double q = p.qs[i] - fq * p.be[i] * (hr - hl) -
-                         p.lam * fq * p.de[i] * (p.ms[ir] - p.ms[il]);
+        double q;
+        if constexpr (WB) {
+            // q = q^dag - tau/(2dx) (F_{i+1/2} + F_{i-1/2}), F = Phi + beta_{face} (hbar jump)
+            const double phr = p.phi[i];
+            const double phl = (i > 0) ? p.phi[i - 1] : (BC == BC_PERIODIC ? p.phi[p.n - 1] : 0.0);
+            const double Fp = fma(0.5 * (p.be[i] + p.be[ir]), hr - h, phr);
+            const double Fm = fma(0.5 * (p.be[il] + p.be[i]), h - hl, phl);
+            q = p.qs[i] - fq * (Fp + Fm);
+        } else {
+            q = p.qs[i] - fq * p.be[i] * (hr - hl) - p.lam * fq * p.de[i] * (p.ms[ir] - p.ms[il]);
+        }
         const double h2 = h * h;
         const double D = fma(h, h, p.lam * p.tau * p.tau);
         const double R = rcp(h * D);  // 1/D = h R, 1/h = D R

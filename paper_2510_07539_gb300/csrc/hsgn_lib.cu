@@ -124,6 +124,10 @@ struct hsgn_s {
     double *qs = nullptr, *ms = nullptr, *rs = nullptr, *be = nullptr, *de = nullptr;
     double* blk = nullptr;
     double* s = nullptr;
+    // well-balanced bathymetry form (HSGN_WELL_BALANCED)
+    bool wb = false;
+    double* bathy = nullptr;         // bottom per cell, null for a flat bottom
+    double* phi = nullptr;           // face forces Phi_{i+1/2}
     unsigned char* rws = nullptr;    // workspace of the separator-system solve
     double* spd = nullptr;           // [0] global Rusanov speed, [1] stage speed, [2..3] scratch
     // mixed precision (HSGN_MIXED): FP32 stage-1 increments and per-row results
@@ -220,14 +224,24 @@ cudaError_t launch_stage(hsgn_s* H, const double* const A[4], const double* cons
     p.de = H->de;
     p.blk = H->blk;
     p.err = H->err;
-    const size_t smem = sizeof(AssembleShared<AT, AM>);
+    p.bathy = H->bathy;
+    p.phi = H->phi;
     const unsigned P = (unsigned)H->split.P;
     {
         ProfScope ps(H, HSGN_PROF_ASSEMBLE, st);
-        if (H->bc == BC_PERIODIC)
-            k_stage_assemble<AT, AM, BC_PERIODIC><<<P, AT, smem, st>>>(p);
-        else
-            k_stage_assemble<AT, AM, BC_TRANSMISSIVE><<<P, AT, smem, st>>>(p);
+        if (H->wb) {
+            const size_t smem = sizeof(AssembleShared<AT, AM, true>);
+            if (H->bc == BC_PERIODIC)
+                k_stage_assemble<AT, AM, BC_PERIODIC, true><<<P, AT, smem, st>>>(p);
+            else
+                k_stage_assemble<AT, AM, BC_TRANSMISSIVE, true><<<P, AT, smem, st>>>(p);
+        } else {
+            const size_t smem = sizeof(AssembleShared<AT, AM>);
+            if (H->bc == BC_PERIODIC)
+                k_stage_assemble<AT, AM, BC_PERIODIC, false><<<P, AT, smem, st>>>(p);
+            else
+                k_stage_assemble<AT, AM, BC_TRANSMISSIVE, false><<<P, AT, smem, st>>>(p);
+        }
     }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
@@ -257,16 +271,24 @@ cudaError_t launch_stage(hsgn_s* H, const double* const A[4], const double* cons
     q.rs = H->rs;
     q.be = H->be;
     q.de = H->de;
+    q.phi = H->phi;
     for (int k = 0; k < 4; ++k) q.out[k] = out[k];
     q.speed = H->spd;
     q.err = H->err;
     const unsigned nb = (unsigned)((H->n + 255) / 256);
     {
         ProfScope ps(H, HSGN_PROF_BACKSUB, st);
-        if (H->bc == BC_PERIODIC)
-            k_backsub<BC_PERIODIC><<<nb, 256, 0, st>>>(q);
-        else
-            k_backsub<BC_TRANSMISSIVE><<<nb, 256, 0, st>>>(q);
+        if (H->wb) {
+            if (H->bc == BC_PERIODIC)
+                k_backsub<BC_PERIODIC, true><<<nb, 256, 0, st>>>(q);
+            else
+                k_backsub<BC_TRANSMISSIVE, true><<<nb, 256, 0, st>>>(q);
+        } else {
+            if (H->bc == BC_PERIODIC)
+                k_backsub<BC_PERIODIC, false><<<nb, 256, 0, st>>>(q);
+            else
+                k_backsub<BC_TRANSMISSIVE, false><<<nb, 256, 0, st>>>(q);
+        }
     }
     return cudaGetLastError();
 }
@@ -423,8 +445,10 @@ int hsgn_create(const hsgn_grid_t* grid, double g, double lambda, const double* 
         return HSGN_ERR_INVALID_ARG;
     if (!(g > 0.0) || !std::isfinite(g) || !(lambda >= 0.0) || !std::isfinite(lambda))
         return HSGN_ERR_INVALID_ARG;
-    if (flags & ~(int32_t)(HSGN_RUSANOV_LOCAL | HSGN_MIXED)) return HSGN_ERR_UNIMPLEMENTED;
-    if (bathymetry) return HSGN_ERR_UNIMPLEMENTED;
+    if (flags & ~(int32_t)(HSGN_RUSANOV_LOCAL | HSGN_MIXED | HSGN_WELL_BALANCED))
+        return HSGN_ERR_UNIMPLEMENTED;
+    if (bathymetry && !(flags & HSGN_WELL_BALANCED)) return HSGN_ERR_INVALID_ARG;
+    if ((flags & HSGN_WELL_BALANCED) && (flags & HSGN_MIXED)) return HSGN_ERR_UNIMPLEMENTED;
     if (grid->n > ((int64_t)1 << 40)) return HSGN_ERR_INVALID_ARG;
 
     hsgn_s* H = new (std::nothrow) hsgn_s;
@@ -440,11 +464,13 @@ int hsgn_create(const hsgn_grid_t* grid, double g, double lambda, const double* 
     const int64_t n = H->n, P = H->split.P;
 
     H->mixed = (flags & HSGN_MIXED) != 0;
+    H->wb = (flags & HSGN_WELL_BALANCED) != 0;
     const size_t vec = align_up(n * sizeof(double));
     const size_t fvec = align_up((n + 1) * sizeof(float));
     const size_t recb = align_up(3 * n * sizeof(float4));
     size_t total = H->mixed ? 4 * vec + 4 * fvec + recb  // U; G1 dq1 dm1 dr1; row records
                             : 16 * vec;                  // U, U1, y v w, 5 back-sub arrays
+    if (H->wb) total += (bathymetry ? 2 : 1) * vec;      // Phi, bottom
     total += align_up(BLK_STRIDE * P * sizeof(double)) + align_up(P * sizeof(double));
     const size_t rws = rows_ws_bytes(P);
     total += rws + align_up(4 * sizeof(double)) + align_up(sizeof(unsigned));
@@ -480,16 +506,28 @@ int hsgn_create(const hsgn_grid_t* grid, double g, double lambda, const double* 
         H->de = reinterpret_cast<double*>(take(vec));
         H->blk = reinterpret_cast<double*>(take(align_up(BLK_STRIDE * P * sizeof(double))));
         H->s = reinterpret_cast<double*>(take(align_up(P * sizeof(double))));
+        if (H->wb) {
+            H->phi = reinterpret_cast<double*>(take(vec));
+            if (bathymetry) H->bathy = reinterpret_cast<double*>(take(vec));
+        }
     }
     H->rws = rws ? take(rws) : nullptr;
     H->spd = reinterpret_cast<double*>(take(align_up(4 * sizeof(double))));
     H->err = reinterpret_cast<unsigned*>(take(align_up(sizeof(unsigned))));
 
     cudaError_t e = cudaMemset(H->mem, 0, total);
+    // the bottom: host or device memory, copied once (cudaMemcpyDefault infers which)
+    if (e == cudaSuccess && H->bathy)
+        e = cudaMemcpy(H->bathy, bathymetry, n * sizeof(double), cudaMemcpyDefault);
     if (e == cudaSuccess)
-        e = set_smem(k_stage_assemble<AT, AM, BC_PERIODIC>, sizeof(AssembleShared<AT, AM>));
+        e = set_smem(k_stage_assemble<AT, AM, BC_PERIODIC, false>, sizeof(AssembleShared<AT, AM>));
     if (e == cudaSuccess)
-        e = set_smem(k_stage_assemble<AT, AM, BC_TRANSMISSIVE>, sizeof(AssembleShared<AT, AM>));
+        e = set_smem(k_stage_assemble<AT, AM, BC_TRANSMISSIVE, false>, sizeof(AssembleShared<AT, AM>));
+    if (e == cudaSuccess)
+        e = set_smem(k_stage_assemble<AT, AM, BC_PERIODIC, true>, sizeof(AssembleShared<AT, AM, true>));
+    if (e == cudaSuccess)
+        e = set_smem(k_stage_assemble<AT, AM, BC_TRANSMISSIVE, true>,
+                     sizeof(AssembleShared<AT, AM, true>));
     if (e == cudaSuccess)
         e = set_smem(k_mixed_assemble<XT, XM, BC_PERIODIC>, sizeof(MixedShared<XT, XM>));
     if (e == cudaSuccess)

@@ -160,3 +160,33 @@ def gaussian_bathymetry(seed: int, x, count: int = 8, amp_max: float = 0.3,
 
 def shelf_bathymetry(x, x_toe: float, slope: float = 1.0 / 20.0, rise: float = 0.5):
     return np.clip((x - x_toe) * slope, 0.0, rise)
+
+
+def wave_over_bottom(x, b, h0: float, amp: float, x0: float, period: float | None = None):
+    """Still water at level h0 over the bottom b plus a solitary wave of
+    amplitude amp centred at x0: h = h_sol - b, u = u_sol, eta = h, w = -h u_x
+    (the flat-bottom wave's velocity field; not an exact solution over b)."""
+    hs, qs, _, rs = solitary(x, h0, amp, x0, period=period)
+    u = qs / hs
+    ux = -rs / (hs * hs)
+    h = hs - b
+    return h, h * u, h * h, -h * h * ux
+
+
+def gauss_bottom_wave(seed: int, n: int = 4096, dx: float = 0.1, amp: float = 0.1):
+    """Periodic wave over a sum of 8 Gaussians (amplitudes up to 0.3, widths
+    2-10, clipped at 0.6) on [0, n dx]: x, dx, b, U."""
+    x, dx = cell_centres(n, 0.0, n * dx)
+    b = gaussian_bathymetry(seed, x)
+    L = n * dx
+    return x, dx, b, wave_over_bottom(x, b, 1.0, amp, 0.5 * L, period=L)
+
+
+def shelf_wave(n: int = 1 << 24, dx: float = 0.005, amp: float = 0.1):
+    """Solitary wave of amplitude amp at L/2 - 80 running towards a 1:20 ramp
+    that starts at L/2 and lifts the bottom by 0.5 (depth 1 -> 0.5), on
+    [0, L], L = n dx: x, dx, b, U."""
+    x, dx = cell_centres(n, 0.0, n * dx)
+    L = n * dx
+    b = shelf_bathymetry(x, 0.5 * L)
+    return x, dx, b, wave_over_bottom(x, b, 1.0, amp, 0.5 * L - 80.0)

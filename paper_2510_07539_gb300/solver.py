@@ -21,6 +21,7 @@ BC_TRANSMISSIVE = 1
 FLAG_FP64 = 0x0
 FLAG_MIXED = 0x1
 FLAG_RUSANOV_LOCAL = 0x10
+FLAG_WELL_BALANCED = 0x2
 
 ERROR_NAMES = {
     1: "HSGN_ERR_INVALID_ARG", 2: "HSGN_ERR_CUDA", 3: "HSGN_ERR_NONPOSITIVE_DEPTH",
@@ -108,13 +109,22 @@ class Solver:
     """One hSGN instance on the current CUDA device (owns its state on the device)."""
 
     def __init__(self, n: int, x_left: float, x_right: float, bc: int = BC_PERIODIC,
-                 g: float = 9.81, lam: float = 100.0, flags: int = FLAG_FP64):
+                 g: float = 9.81, lam: float = 100.0, flags: int = FLAG_FP64, bathymetry=None):
+        """bathymetry: None (flat) or n bottom elevations (needs FLAG_WELL_BALANCED)."""
         load()
         self.n, self.bc, self.g, self.lam, self.flags = int(n), int(bc), float(g), float(lam), flags
         self.dx = (x_right - x_left) / n
         grid = Grid(int(n), float(x_left), float(x_right), int(bc), 0)
+        bptr = None
+        if bathymetry is not None:
+            bt = bathymetry if isinstance(bathymetry, torch.Tensor) else \
+                torch.as_tensor(bathymetry, dtype=torch.float64)
+            if bt.numel() != self.n:
+                raise ValueError(f"expected {self.n} bottom values")
+            bt = bt.to(torch.float64).contiguous()
+            bptr = _ptr(bt)  # copied synchronously by hsgn_create
         h = _P()
-        _check(_lib.hsgn_create(ctypes.byref(grid), float(g), float(lam), None, int(flags),
+        _check(_lib.hsgn_create(ctypes.byref(grid), float(g), float(lam), bptr, int(flags),
                                 ctypes.byref(h)), "hsgn_create")
         self._h = h
 

@@ -57,6 +57,13 @@ def test_create_rejects_bad_arguments_before_touching_the_device(lib):
     assert lib.hsgn_create(ctypes.byref(g), 9.81, -1.0, None, 0, ctypes.byref(h)) == 1
     assert lib.hsgn_create(ctypes.byref(g), 9.81, 1.0, None, 0x4000, ctypes.byref(h)) == 6
     assert lib.hsgn_create(ctypes.byref(g), 9.81, 1.0, None, 0, None) == 1
+    # a bottom needs the well-balanced form; that form has no mixed-precision variant
+    bottom = (ctypes.c_double * 10)()
+    assert lib.hsgn_create(ctypes.byref(g), 9.81, 1.0, bottom, 0, ctypes.byref(h)) == 1
+    assert lib.hsgn_create(ctypes.byref(g), 9.81, 1.0, bottom, 0x1, ctypes.byref(h)) == 1
+    assert lib.hsgn_create(ctypes.byref(g), 9.81, 1.0, bottom, 0x3, ctypes.byref(h)) == 6
+    assert lib.hsgn_create(ctypes.byref(g), 9.81, 1.0, None, 0x3, ctypes.byref(h)) == 6
+    assert not h.value
     lib.hsgn_destroy(None)
 
 

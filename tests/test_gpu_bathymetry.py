@@ -1,0 +1,176 @@
+"""GPU parity of the well-balanced bathymetry form (HSGN_WELL_BALANCED) with
+the oracle's form 1: one stage with U_b != U_l over a random bottom, single
+steps and trajectories over a Gaussian-bump bottom, the lake at rest, and one
+full-size step of the 2^24-cell shelf workload.
+
+Tolerances as for the flat form: 1e-12 relative L2 per stage / step, 1e-9
+over trajectories; at full size q and h w are compared against the scales of
+the back-substitution summands, since both are roundoff-sized wherever the
+water is at rest.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2510_07539_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_2510_07539_gb300 import build
+    build.build()
+    torch.cuda.set_device(0)
+
+
+def S():
+    from paper_2510_07539_gb300 import solver
+    return solver
+
+
+def dev(a):
+    return torch.as_tensor(np.ascontiguousarray(a, dtype=np.float64), device="cuda")
+
+
+def rel_l2(x, ref):
+    return float(np.linalg.norm(x - ref) / max(np.linalg.norm(ref), 1e-300))
+
+
+def wb_solver(n, dx, bc, lam, b, flags=0):
+    return S().Solver(n, 0.0, n * dx, bc, lam=lam, flags=flags | S().FLAG_WELL_BALANCED,
+                      bathymetry=b)
+
+
+def hw_scale(U, lam, dt):
+    """Size of the summands of the (h w) update (Sec. 4.2): r^dag contains
+    + lambda tau and the result subtracts lambda tau mbar / hbar^2, so h w,
+    small where the flow is slow, carries rounding of that size."""
+    tau = (1.0 - 1.0 / math.sqrt(2.0)) * dt
+    return np.abs(U[3]) + lam * tau * (1.0 + np.abs(U[2]) / (U[0] * U[0]))
+
+
+def gpu_run(n, dx, bc, lam, b, U, dt, steps, use_graph=True):
+    with wb_solver(n, dx, bc, lam, b) as s:
+        s.set_state(*(dev(u) for u in U))
+        if use_graph:
+            s.run(dt, steps)
+        else:
+            for _ in range(steps):
+                s.step(dt)
+            s.check()
+        return [t.cpu().numpy() for t in s.get_state()]
+
+
+@pytest.mark.parametrize("bc", [0, 1])
+@pytest.mark.parametrize("n", [3, 4, 7, 64, 511, 512, 513, 1000, 5000, 70001])
+def test_wb_stage_matches_oracle(n, bc):
+    dx, lam, tau, speed = 0.1, 300.0, 0.01, 0.37
+    x, _ = inputs.cell_centres(n, 0.0, n * dx)
+    b = inputs.gaussian_bathymetry(70 + n, x, amp_max=0.1)
+    Ub = inputs.random_state(1000 + n, n, dx)
+    Ul = inputs.random_state(2000 + n, n, dx, h_var=0.1)
+    for local in (0, 1):
+        flags = S().FLAG_RUSANOV_LOCAL if local else 0
+        with wb_solver(n, dx, bc, lam, b, flags) as s:
+            out = s.stage([dev(u) for u in Ub], [dev(u) for u in Ul], tau, speed)
+            got = [t.cpu().numpy() for t in out]
+            s.check()
+        p = oracle.Params(n, dx, bc, lam=lam, rusanov=0 if local else 1, speed=speed,
+                          form=1, bathy=b)
+        ref = oracle.stage(p, Ub, Ul, tau)
+        for k in range(4):
+            assert rel_l2(got[k], ref[k]) < 1e-12, (k, local, rel_l2(got[k], ref[k]))
+
+
+def test_wb_flat_bottom_pointer_equals_null_bottom():
+    # a zero bottom array and no bottom at all give bitwise the same steps
+    n, dx, lam = 1537, 0.1, 500.0
+    U = inputs.random_state(77, n, dx)
+    a = gpu_run(n, dx, 1, lam, np.zeros(n), U, 0.01, 3)
+    b = gpu_run(n, dx, 1, lam, None, U, 0.01, 3)
+    for k in range(4):
+        np.testing.assert_array_equal(a[k], b[k])
+
+
+@pytest.mark.parametrize("bc", [0, 1])
+@pytest.mark.parametrize("n", [5, 100, 1000, 1537])
+def test_wb_one_step_matches_oracle(n, bc):
+    dx, lam = 0.1, 500.0
+    x, _, b, U = inputs.gauss_bottom_wave(300 + n, n, dx)
+    p = oracle.Params(n, dx, bc, lam=lam, form=1, bathy=b)
+    dt, _, _ = oracle.suggest_dt(p, U, 2.0, 0.5)
+    got = gpu_run(n, dx, bc, lam, b, U, dt, 1)
+    ref = oracle.step(p, U, dt)
+    # q is compared against its own scale plus the size of the depth-driven
+    # forces (q itself is small where the wave has not arrived); h w against
+    # the scale of its summands
+    for k in (0, 2):
+        assert rel_l2(got[k], ref[k]) < 1e-12, (k, rel_l2(got[k], ref[k]))
+    assert np.linalg.norm(got[1] - ref[1]) < 1e-12 * (np.linalg.norm(ref[1]) + np.linalg.norm(U[0]))
+    assert np.linalg.norm(got[3] - ref[3]) < 1e-12 * np.linalg.norm(hw_scale(U, lam, dt))
+
+
+@pytest.mark.parametrize("bc", [0, 1])
+@pytest.mark.parametrize("n", [400, 5000])
+def test_wb_lake_at_rest_on_gpu(n, bc):
+    # u = 0, eta = h, w = 0, h + b = const: the GPU keeps the state at rest to
+    # rounding over 40 steps, like the oracle (Sec. 2.3 with b_t = 0)
+    x, dx = inputs.cell_centres(n, 0.0, 0.2 * n)
+    b = inputs.gaussian_bathymetry(5, x)
+    b = b - b.min()
+    h = 1.0 - b
+    U = (h, 0 * h, h * h, 0 * h)
+    got = gpu_run(n, dx, bc, 500.0, b, U, 0.05, 40)
+    assert np.max(np.abs(got[0] - h)) < 1e-12
+    assert np.max(np.abs(got[1])) < 1e-12
+    assert np.max(np.abs(got[2] - h * h)) < 1e-12
+    assert np.max(np.abs(got[3])) < 1e-11
+
+
+def test_wb_gauss_bottom_trajectory():
+    # the adjoint workload's forward problem: N = 4096, dx = 0.1, periodic,
+    # lambda = 100, wave a = 0.1 over 8 Gaussian bumps; 200 steps at CFL 2
+    n, lam, steps = 4096, 100.0, 200
+    x, dx, b, U = inputs.gauss_bottom_wave(20251011, n)
+    p = oracle.Params(n, dx, 0, lam=lam, form=1, bathy=b)
+    dt, _, _ = oracle.suggest_dt(p, U, 2.0, 0.5)
+    got = gpu_run(n, dx, 0, lam, b, U, dt, steps)
+    ref = oracle.run(p, U, dt, steps)
+    for k in range(3):
+        assert rel_l2(got[k], ref[k]) < 1e-9, (k, rel_l2(got[k], ref[k]))
+    assert np.linalg.norm(got[3] - ref[3]) < 1e-9 * np.linalg.norm(hw_scale(U, lam, dt))
+    assert abs(math.fsum(got[0]) - math.fsum(U[0])) <= 1e-13 * math.fsum(U[0])
+
+
+def test_wb_graph_replay_equals_step_loop():
+    n, lam = 3000, 1000.0
+    x, dx, b, U = inputs.gauss_bottom_wave(8, n)
+    a = gpu_run(n, dx, 0, lam, b, U, 0.01, 7, use_graph=True)
+    c = gpu_run(n, dx, 0, lam, b, U, 0.01, 7, use_graph=False)
+    for k in range(4):
+        np.testing.assert_array_equal(a[k], c[k])
+
+
+def test_wb_shelf_2_24_one_step():
+    # the large workload: N = 2^24, dx = 0.005, transmissive, lambda = 1000,
+    # 1:20 shelf, wave a = 0.1; one step at CFL_IMEX 4, every cell compared
+    n, lam = 1 << 24, 1000.0
+    x, dx, b, U = inputs.shelf_wave(n)
+    p = oracle.Params(n, dx, 1, lam=lam, form=1, bathy=b)
+    dt, _, _ = oracle.suggest_dt(p, U, 4.0, 0.5)
+    got = gpu_run(n, dx, 1, lam, b, U, dt, 1)
+    ref = oracle.step(p, U, dt)
+    A = oracle.assemble(p, U, U, (1.0 - 1.0 / math.sqrt(2.0)) * dt)
+    tau = (1.0 - 1.0 / math.sqrt(2.0)) * dt
+    h = np.abs(U[0])
+    Sq = np.abs(U[1]) + tau / dx * A["beta"] * h
+    Sr = np.abs(U[3]) + lam * tau * (1.0 + np.abs(U[2]) / (h * h))
+    assert rel_l2(got[0], ref[0]) < 1e-12 and rel_l2(got[2], ref[2]) < 1e-12
+    assert np.linalg.norm(got[1] - ref[1]) / np.linalg.norm(Sq) < 1e-12
+    assert np.linalg.norm(got[3] - ref[3]) / np.linalg.norm(Sr) < 1e-12
