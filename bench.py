@@ -68,6 +68,7 @@ def parse_args():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true", help="skip the all-FP64 path")
     ap.add_argument("--batch", type=int, default=4096, help="instances of the batched workload")
     return ap.parse_args()
 
@@ -323,6 +324,30 @@ def l2_vs_oracle(sols, dts, Ud, refs, ks, np):
     return {"depth_rel_l2": per["h"], "per_variable_rel_l2": per, "steps": ks}
 
 
+def time_fp64(S, torch, n, xl, xr, lams, Ud, args, flush, stream, dist, units_rank, world,
+              hbm_peak):
+    """The all-FP64 path (exact separator solve) on the same workload."""
+    fsols, fdts, fms, ftot, _ = time_path(S, torch, S.FLAG_FP64, n, xl, xr, lams, Ud,
+                                          args.steps, args.warmup, flush, stream, dist, None)
+    favg = ftot["assemble"][0] / max(ftot["assemble"][1], 1)
+    ftf = FLOPS_PER_CELL_ASSEMBLE * n / (favg / 1e3) / 1e12
+    fshare_den = sum(v[0] for v in ftot.values())
+    fp64 = {
+        "value": units_rank * world / (fms / 1e3), "unit": UNIT, "ms_per_step": fms / args.steps,
+        "dtype": "f64",
+        "roofline": {"bound": "alu", "kernel": "k_stage_assemble", "achieved": ftf,
+                     "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": ftf / FP64_PEAK_TFLOPS,
+                     "peak_source": "nominal dense FP64 of GB300 (1.25 TFLOP/s)",
+                     "traffic": (lambda t: t * n if t is not None else None)(
+                         profiled_traffic_per_cell("ncu_stage_assemble.md")),
+                     "kernel_avg_ms": favg,
+                     "kernel_share": {k: v[0] / fshare_den for k, v in ftot.items()},
+                     "hbm_frac_of_measured": BYTES_PER_CELL_STAGE * units_rank / (fms / 1e3)
+                     / 1e9 / hbm_peak},
+    }
+    return fp64, fsols, fdts
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -388,24 +413,10 @@ def run_ours(args):
     launches = len(lams) * args.steps * 2 * (2 + sep_launches((n + 511) // 512))
 
     # ---- the all-FP64 path on the same workload
-    fsols, fdts, fms, ftot, _ = time_path(S, torch, S.FLAG_FP64, n, xl, xr, lams, Ud,
-                                          args.steps, args.warmup, flush, stream, dist, None)
-    favg = ftot["assemble"][0] / max(ftot["assemble"][1], 1)
-    ftf = FLOPS_PER_CELL_ASSEMBLE * n / (favg / 1e3) / 1e12
-    fshare_den = sum(v[0] for v in ftot.values())
-    fp64 = {
-        "value": units_rank * world / (fms / 1e3), "unit": UNIT, "ms_per_step": fms / args.steps,
-        "dtype": "f64",
-        "roofline": {"bound": "alu", "kernel": "k_stage_assemble", "achieved": ftf,
-                     "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": ftf / FP64_PEAK_TFLOPS,
-                     "peak_source": "nominal dense FP64 of GB300 (1.25 TFLOP/s)",
-                     "traffic": (lambda t: t * n if t is not None else None)(
-                         profiled_traffic_per_cell("ncu_stage_assemble.md")),
-                     "kernel_avg_ms": favg,
-                     "kernel_share": {k: v[0] / fshare_den for k, v in ftot.items()},
-                     "hbm_frac_of_measured": BYTES_PER_CELL_STAGE * units_rank / (fms / 1e3)
-                     / 1e9 / hbm_peak},
-    }
+    fp64, fsols, fdts = None, [], []
+    if not args.no_fp64:
+        fp64, fsols, fdts = time_fp64(S, torch, n, xl, xr, lams, Ud, args, flush, stream, dist,
+                                units_rank, world, hbm_peak)
 
     # ---- batched workload: 4096 independent periodic solitary waves of uneven
     #      length in one launch per kernel (mixed precision)
@@ -497,7 +508,8 @@ def run_ours(args):
                "sample": f"{ks} IMEX steps of each of the {len(lams)} instances ({n} cells), "
                          f"single-threaded C oracle, {el:.1f} s"}
         l2err = l2_vs_oracle(msols, mdts, Ud, refs, ks, np)
-        fp64["l2_rel_err_vs_oracle"] = l2_vs_oracle(fsols, fdts, Ud, refs, ks, np)
+        if fp64 is not None:
+            fp64["l2_rel_err_vs_oracle"] = l2_vs_oracle(fsols, fdts, Ud, refs, ks, np)
     for s in msols + fsols:
         s.close()
 

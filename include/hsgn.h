@@ -46,7 +46,11 @@ enum {
     HSGN_ERR_NOT_COERCIVE = 4,      /* beta <= 0 or a non-positive pivot */
     HSGN_ERR_NONFINITE = 5,         /* NaN or Inf produced */
     HSGN_ERR_UNIMPLEMENTED = 6,     /* entry point or flag not built yet */
-    HSGN_ERR_OUT_OF_MEMORY = 7
+    HSGN_ERR_OUT_OF_MEMORY = 7,
+    HSGN_ERR_TRUNCATION = 8         /* windowed depth solve: the coupling of the depth
+                                     * system decays too slowly for the window overlap
+                                     * (time step too large); HSGN_EXACT_SOLVE solves
+                                     * it without truncation */
 };
 
 /* boundary conditions (reading of the paper, which states none):
@@ -61,7 +65,19 @@ enum {
                                 * on increments; state, base-state differences and
                                 * the accumulation in FP64; the depth is updated in
                                 * flux form (mass conserved to FP64 rounding).
+                                * One launch per stage: each CTA solves the depth
+                                * system of its tile on a window that overlaps the
+                                * neighbouring tiles by 64 rows and drops the
+                                * coupling beyond it (the depth matrix is strictly
+                                * diagonally dominant, so that coupling decays
+                                * geometrically; each CTA checks the decay bound and
+                                * reports HSGN_ERR_TRUNCATION when the dropped part
+                                * could exceed 2^-30 of the increment). The state
+                                * alternates between two device buffers.
                                 * hsgn_stage is not available in this form. */
+#define HSGN_EXACT_SOLVE 0x4   /* with HSGN_MIXED: solve the depth system exactly
+                                * through the global separator system (three
+                                * launches per stage, state updated in place) */
 #define HSGN_RUSANOV_LOCAL 0x10 /* Rusanov speed max(|u^L|,|u^R|) per face instead
                                  * of the global max |u^n| of the step */
 #define HSGN_WELL_BALANCED 0x2  /* variable bottom b(x) (Sec. 2.3, eq. (hSGNb_eq))

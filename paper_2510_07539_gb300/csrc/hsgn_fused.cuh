@@ -1,0 +1,512 @@
+// hsgn_fused.cuh -- the mixed-precision stage in one launch (sm_103a).
+//
+// Same arithmetic as hsgn_mixed.cuh (Sec. 4.2, eq. (GN_hyp_eq_semi_fully_discrete),
+// increment form; Sec. 3.2, efficient form of the tableau), but the depth
+// system A dh = d - A h_b is solved on overlapping windows instead of through
+// a global separator system, so that fluxes, rows, solve and back-substitution
+// of a tile run in one CTA and nothing per row goes through HBM except the
+// stage inputs and outputs:
+//  * CTA p owns the tile of rows [t0, t0 + sp) and solves the rows of the
+//    window [t0 - HW, t0 + sp + HW) with the coupling to the rows outside the
+//    window dropped. Periodic: indices are taken modulo n, so a window longer
+//    than the grid is the periodic system unrolled, whose solution is the
+//    periodic one. Transmissive: the window is clipped at the domain ends,
+//    where the Neumann rows are the exact ones.
+//  * A has diagonal 1 + l_i + r_i and off-diagonals -l_i, -r_i with
+//    l_i = tau^2/dx^2 beta_{i-1/2}, r_i = tau^2/dx^2 beta_{i+1/2} > 0. The
+//    error e caused by the dropped value x beyond the left edge solves the
+//    window system with one forcing term at row 0, so e_i = rho_i e_{i-1} with
+//    rho_i = l_i / (1 + l_i + r_i (1 - rho_{i+1})), starting from the right
+//    edge. With kappa <= l_i, r_i <= K over the window every rho_i stays below
+//    the smaller root rho* = 2K / (B + sqrt(B^2 - 4 kappa K)), B = 1 + K + kappa,
+//    of rho = K / (1 + K + kappa (1 - rho)) (the iteration from the edge rises
+//    monotonically towards it), hence |e_i| <= rho*^(i+1) |x|; the same holds
+//    from the right. The tile rows and the rows of a tile-face mini window lie
+//    HB = HW - 1 rows or more inside their window. Each CTA evaluates rho* from
+//    the min and max of tau^2 beta / dx^2 over its cells and raises
+//    HSGN_DEV_ERR_TRUNCATION when rho*^HB > 2^-30 (the single-precision
+//    increments themselves carry 2^-24). For a uniform state rho* is the decay
+//    rate of the inverse, about 0.55 at CFL_IMEX = 4.
+//  * Mass: the face flux at a tile boundary is used by the two CTAs on either
+//    side. Both solve the same mini-window of 2 HB rows centred on that face
+//    with the same code path and evaluate the face flux from it, so the two
+//    values are bitwise equal and the flux-form depth update stays
+//    conservative to FP64 rounding.
+//  * Stage 2 cannot update U in place (the windows of neighbouring tiles still
+//    read U^n), so it writes U^{n+1} to a second state buffer.
+#pragma once
+
+#include "hsgn_mixed.cuh"
+
+namespace hsgn {
+
+struct FusedParams {
+    int64_t n;
+    int32_t stage;        // 1: writes G1, dq1, dm1, dr1; 2: writes U^{n+1} to out
+    int32_t local_speed;
+    int32_t track_speed;  // stage 1 clears *speed_next, stage 2 folds max |u| into it
+    int32_t S;            // tile rows (<= the kernel's capacity)
+    float g, lam, tau, tdx, fq, Cc, fd, lt2, ltau, wl1, wb1;
+    const double* U[4];             // U^n (FP64)
+    float *G1, *dq1, *dm1, *dr1;    // stage-1 increments; G1 has n+1 faces (face i+1/2 at i+1)
+    double* out[4];                 // U^{n+1} (stage 2; not aliased with U)
+    const double* speed;            // global Rusanov speed of the step
+    double* speed_next;             // max |u^{n+1}|
+    unsigned* err;
+};
+
+// Window of tile p: tile rows [t0, t0 + sp); window rows [wl, wl + W) (global,
+// periodic ones not yet reduced modulo n); the tile starts at window row lo.
+// lend / rend: the window ends at the domain end (transmissive only).
+struct Window {
+    int64_t t0, wl;
+    int sp, W, lo;
+    bool lend, rend;
+};
+
+template <int BC>
+__host__ __device__ inline Window window_of(int64_t p, int64_t n, int S, int HW) {
+    Window w;
+    w.t0 = p * (int64_t)S;
+    const int64_t rest = n - w.t0;
+    w.sp = (int)(rest < S ? rest : S);
+    if (BC == BC_PERIODIC) {
+        w.wl = w.t0 - HW;
+        w.W = w.sp + 2 * HW;
+        w.lend = w.rend = false;
+    } else {
+        w.wl = w.t0 - HW < 0 ? 0 : w.t0 - HW;
+        const int64_t wr = w.t0 + w.sp + HW > n ? n : w.t0 + w.sp + HW;
+        w.W = (int)(wr - w.wl);
+        w.lend = w.wl == 0;
+        w.rend = wr == n;
+    }
+    w.lo = (int)(w.t0 - w.wl);
+    return w;
+}
+
+// Mini-window of the face between global rows t-1 and t: rows [ml, ml + mw)
+// (global, unreduced), clipped at transmissive domain ends; the face's right
+// row is mini row t - ml.
+struct MiniWindow {
+    int64_t ml;
+    int mw;
+    bool lend, rend;
+};
+
+template <int BC>
+__host__ __device__ inline MiniWindow mini_of(int64_t t, int64_t n, int HB) {
+    MiniWindow m;
+    if (BC == BC_PERIODIC) {
+        m.ml = t - HB;
+        m.mw = 2 * HB;
+        m.lend = m.rend = false;
+    } else {
+        m.ml = t - HB < 0 ? 0 : t - HB;
+        const int64_t mr = t + HB > n ? n : t + HB;
+        m.mw = (int)(mr - m.ml);
+        m.lend = m.ml == 0;
+        m.rend = mr == n;
+    }
+    return m;
+}
+
+// Cell of global index x: modulo n (periodic, any x) or clamped (transmissive).
+template <int BC>
+__host__ __device__ __forceinline__ int64_t cell_at(int64_t x, int64_t n) {
+    if (BC == BC_PERIODIC) {
+        if (x >= 0 && x < n) return x;
+        if (x < 0 && x >= -n) return x + n;
+        if (x >= n && x < 2 * n) return x - n;
+        const int64_t r = x % n;
+        return r < 0 ? r + n : r;
+    }
+    return x < 0 ? 0 : (x >= n ? n - 1 : x);
+}
+
+// Capacity of the fused kernel: T threads, M rows per thread, overlap HW.
+template <int T, int M, int HW>
+struct FusedGeom {
+    static constexpr int R = T * M - 1;      // window rows (+1 identity row in the elimination)
+    static constexpr int S = R - 2 * HW;     // largest tile
+    static constexpr int HB = HW - 1;        // half-width of a tile-boundary mini-window
+    static constexpr int NC = pd_size(R + 6);
+    static constexpr int MB = (2 * HB + 1 + 31) / 32;  // rows per lane of the mini solve
+    static_assert(S > 0, "overlap too wide for the window");
+};
+
+// Shared memory. Arrays are reused once their phase is over:
+//   phase 0 writes hl, ql, ml, rl (U_l), qb, mb, rb (U_b), Dh, Dq, Dm (FP64
+//   differences of U_b at the face to the right of a cell, rounded);
+//   phase 1 writes the fluxes into ql (Fq), X0 (Fm), rl (Fr);
+//   phase 2 writes dq -> ql, dm -> X0, dr -> rl, beta -> hl, delta -> ml;
+//   the solve writes dh -> mb.
+template <int T, int M, int HW>
+struct FusedShared {
+    static constexpr int NC = FusedGeom<T, M, HW>::NC;
+    float hl[NC], ql[NC], ml[NC], rl[NC];
+    float qb[NC], mb[NC], rb[NC];
+    float Dh[NC], Dq[NC], Dm[NC];
+    float X0[NC];
+    SepShared<T, float> sep;
+    float bnd[2][2];       // dh of the two rows at the left / right tile face (mini solves)
+    unsigned kmax, kmin;   // bits of max / min tau^2 beta / dx^2 (positive floats order as integers)
+};
+
+template <int T, int M, int HW, int BC>
+__global__ void __launch_bounds__(T, 4) k_mixed_fused(const FusedParams p) {
+    using Gm = FusedGeom<T, M, HW>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    auto& sm = *reinterpret_cast<FusedShared<T, M, HW>*>(smem_raw);
+    const int tid = threadIdx.x;
+    const int64_t n = p.n;
+    const Window win = window_of<BC>(blockIdx.x, n, p.S, HW);
+    const int W = win.W;
+    const int64_t wl = win.wl;
+    const bool two = p.stage == 2;
+    const float wl1 = p.wl1, wb1 = p.wb1;
+    const double* __restrict__ U0 = p.U[0];
+    const double* __restrict__ U1 = p.U[1];
+    const double* __restrict__ U2 = p.U[2];
+    const double* __restrict__ U3 = p.U[3];
+    const float* __restrict__ G1 = p.G1;
+    if (tid == 0) {
+        sm.kmax = 0u;
+        sm.kmin = 0x7F7FFFFFu;
+    }
+    if (p.track_speed && p.stage == 1 && blockIdx.x == 0 && tid == 0) *p.speed_next = 0.0;
+
+    // ---- 0. window cells -3 .. W+2 (smem index j = cell + 3); FP64 differences of U^n
+    constexpr int NL = (Gm::R + 6 + T - 1) / T;
+    // windows away from the domain ends read cells wl-3 .. wl+W+3 directly
+    const bool inner = wl - 3 >= 0 && wl + W + 3 <= n;
+#pragma unroll
+    for (int it = 0; it < NL; ++it) {
+        const int j = tid + it * T;
+        if (j < W + 6) {
+            const int64_t gi = inner ? wl - 3 + j : cell_at<BC>(wl - 3 + j, n);
+            const int64_t gn = inner ? gi + 1 : cell_at<BC>(wl - 2 + j, n);
+            const double h0 = __ldg(U0 + gi), q0 = __ldg(U1 + gi);
+            const double m0 = __ldg(U2 + gi), rr0 = __ldg(U3 + gi);
+            const double h1 = __ldg(U0 + gn), q1 = __ldg(U1 + gn), m1 = __ldg(U2 + gn);
+            float dh1 = 0.f, dq1 = 0.f, dm1 = 0.f, dr1 = 0.f, dh1n = 0.f, dq1n = 0.f, dm1n = 0.f;
+            if (two) {
+                const float g0 = __ldg(G1 + gi), g1 = __ldg(G1 + gi + 1);
+                const float g2 = __ldg(G1 + gn), g3 = __ldg(G1 + gn + 1);
+                dq1 = __ldg(p.dq1 + gi);
+                dm1 = __ldg(p.dm1 + gi);
+                dr1 = __ldg(p.dr1 + gi);
+                dq1n = __ldg(p.dq1 + gn);
+                dm1n = __ldg(p.dm1 + gn);
+                dh1 = g0 - g1;
+                dh1n = g2 - g3;
+            }
+            const float hf = f32_of(h0), qf = f32_of(q0), mf = f32_of(m0), rf = f32_of(rr0);
+            const int jp = pd(j);
+            sm.hl[jp] = fmaf(wl1, dh1, hf);
+            sm.ql[jp] = fmaf(wl1, dq1, qf);
+            sm.ml[jp] = fmaf(wl1, dm1, mf);
+            sm.rl[jp] = fmaf(wl1, dr1, rf);
+            sm.qb[jp] = fmaf(wb1, dq1, qf);
+            sm.mb[jp] = fmaf(wb1, dm1, mf);
+            sm.rb[jp] = fmaf(wb1, dr1, rf);
+            sm.Dh[jp] = fmaf(wb1, dh1n - dh1, f32_of(h1 - h0));
+            sm.Dq[jp] = fmaf(wb1, dq1n - dq1, f32_of(q1 - q0));
+            sm.Dm[jp] = fmaf(wb1, dm1n - dm1, f32_of(m1 - m0));
+        }
+    }
+    __syncthreads();
+
+    const float tau = p.tau, lam = p.lam, g = p.g;
+    const float gspeed = p.local_speed ? 0.f : (float)(*p.speed);
+    unsigned bad = 0;
+
+    // ---- 1. Rusanov fluxes of U_l at faces f = -2 .. W (index j = f + 2), Sec. 4.1.
+    //         All reads of phase 0's ql / rl happen before the barrier, the
+    //         flux stores (which reuse ql, rl) after it.
+    constexpr int NF = (Gm::R + 3 + T - 1) / T;
+    float fq_[NF], fm_[NF], fr_[NF];
+#pragma unroll
+    for (int it = 0; it < NF; ++it) {
+        const int j = tid + it * T;
+        fq_[it] = fm_[it] = fr_[it] = 0.f;
+        if (j < W + 3) {
+            const int a0 = pd(j), a1 = pd(j + 1), a2 = pd(j + 2), a3 = pd(j + 3);
+            const float hm = sm.hl[a0], h0 = sm.hl[a1], h1 = sm.hl[a2], h2 = sm.hl[a3];
+            const float qm = sm.ql[a0], q0 = sm.ql[a1], q1 = sm.ql[a2], q2 = sm.ql[a3];
+            const float mm = sm.ml[a0], m0 = sm.ml[a1], m1 = sm.ml[a2], m2 = sm.ml[a3];
+            const float rm = sm.rl[a0], r0_ = sm.rl[a1], r1 = sm.rl[a2], r2 = sm.rl[a3];
+            const float hL = fmaf(0.25f, h1 - hm, h0), hR = fmaf(-0.25f, h2 - h0, h1);
+            const float qL = fmaf(0.25f, q1 - qm, q0), qR = fmaf(-0.25f, q2 - q0, q1);
+            const float mL = fmaf(0.25f, m1 - mm, m0), mR = fmaf(-0.25f, m2 - m0, m1);
+            const float rL = fmaf(0.25f, r1 - rm, r0_), rR = fmaf(-0.25f, r2 - r0_, r1);
+            if (!pos_finite(hL) || !pos_finite(hR)) bad |= HSGN_DEV_ERR_DEPTH;
+            const float ip = __frcp_rn(hL * hR);
+            const float uL = qL * hR * ip, uR = qR * hL * ip;
+            const float s = p.local_speed ? fmaxf(fabsf(uL), fabsf(uR)) : gspeed;
+            fq_[it] = 0.5f * (fmaf(uL, qL, uR * qR) - s * (qR - qL));
+            fm_[it] = 0.5f * (fmaf(uL, mL, uR * mR) - s * (mR - mL));
+            fr_[it] = 0.5f * (fmaf(uL, rL, uR * rR) - s * (rR - rL));
+        }
+    }
+    __syncthreads();
+    float* const Fq = sm.ql;
+    float* const Fm = sm.X0;
+    float* const Fr = sm.rl;
+#pragma unroll
+    for (int it = 0; it < NF; ++it) {
+        const int j = tid + it * T;
+        if (j < W + 3) {
+            Fq[j] = fq_[it];
+            Fm[j] = fm_[it];
+            Fr[j] = fr_[it];
+        }
+    }
+    __syncthreads();
+
+    // ---- 2. increments and coefficients at cells c = -1 .. W (index j = c + 1):
+    //         r^dag = r_b + dr' + lambda tau, m^dag = m_b + dm' + lambda tau^2, q^dag = q_b + dq
+    constexpr int NCL = (Gm::R + 2 + T - 1) / T;
+    const float lt2 = p.lt2, tdx = p.tdx, Cc = p.Cc;
+    float dq_[NCL], dm_[NCL], dr_[NCL], be_[NCL], de_[NCL];
+    float kloc = 0.f, kmin = 3.0e38f;
+#pragma unroll
+    for (int it = 0; it < NCL; ++it) {
+        const int j = tid + it * T;
+        dq_[it] = dm_[it] = dr_[it] = be_[it] = de_[it] = 0.f;
+        if (j < W + 2) {
+            const int c3 = pd(j + 2);
+            const float drv = -tdx * (Fr[j + 1] - Fr[j]);
+            const float dmv = fmaf(tau, sm.rb[c3] + drv, -tdx * (Fm[j + 1] - Fm[j]));
+            const float dqv = -tdx * (Fq[j + 1] - Fq[j]);
+            const float msv = sm.mb[c3] + dmv + lt2;
+            const float h = sm.hl[c3];
+            if (!pos_finite(h)) bad |= HSGN_DEV_ERR_DEPTH;
+            const float Dh_ = fmaf(h, h, lt2);
+            const float Rr = __frcp_rn(h * Dh_);
+            const float ih = Dh_ * Rr;
+            const float iD = h * Rr;
+            const float eta = sm.ml[c3] * ih;
+            const float e = eta * ih;
+            const float alpha = fmaf(2.f, e, -1.f) * ih * (-1.f / 3.f);
+            const float c2 = fmaf(g, h, (lam * (1.f / 3.f)) * e * e);
+            const float a2 = fmaf(-lam * eta, alpha, c2);
+            const float ib1 = h * h * iD;
+            const float beta2 = (2.f * lt2) * h * iD * iD;
+            const float beta = fmaf(lam * alpha * beta2, msv, a2);
+            if (!pos_finite(beta)) bad |= HSGN_DEV_ERR_COERCIVE;
+            dq_[it] = dqv;
+            dm_[it] = dmv;
+            dr_[it] = drv;
+            be_[it] = beta;
+            de_[it] = alpha * ib1;
+            kloc = fmaxf(kloc, Cc * beta);
+            kmin = fminf(kmin, Cc * beta);
+        }
+    }
+    __syncthreads();
+    float* const dqa = sm.ql;
+    float* const dma = sm.X0;
+    float* const dra = sm.rl;
+    float* const bea = sm.hl;
+    float* const dea = sm.ml;
+#pragma unroll
+    for (int it = 0; it < NCL; ++it) {
+        const int j = tid + it * T;
+        if (j < W + 2) {
+            const int jp = pd(j);
+            dqa[jp] = dq_[it];
+            dma[jp] = dm_[it];
+            dra[jp] = dr_[it];
+            bea[jp] = be_[it];
+            dea[jp] = de_[it];
+        }
+    }
+    if (pos_finite(kloc)) atomicMax(&sm.kmax, __float_as_uint(kloc));
+    if (pos_finite(kmin)) atomicMin(&sm.kmin, __float_as_uint(kmin));
+    __syncthreads();
+    if (BC == BC_TRANSMISSIVE && tid == 0) {
+        // zero-order ghost copies at the domain ends
+        if (win.lend) {
+            const int a = pd(0), c = pd(1);
+            dqa[a] = dqa[c]; dma[a] = dma[c]; dra[a] = dra[c]; bea[a] = bea[c]; dea[a] = dea[c];
+        }
+        if (win.rend) {
+            const int a = pd(W + 1), c = pd(W);
+            dqa[a] = dqa[c]; dma[a] = dma[c]; dra[a] = dra[c]; bea[a] = bea[c]; dea[a] = dea[c];
+        }
+    }
+    __syncthreads();
+
+    // ---- 3. rows of A dh = d - A h_b (window row i; face i+1/2 at index i+3),
+    //         with the coupling across a truncated edge dropped
+    const float fq = p.fq, fd = p.fd;
+    auto row_at = [&](int i, bool cutL, bool cutR, float& a, float& bb, float& c, float& d) {
+        const int c0 = pd(i), c1 = pd(i + 1), c2 = pd(i + 2), f2 = pd(i + 2), f3 = pd(i + 3);
+        const float bm = 0.5f * (bea[c0] + bea[c1]);
+        const float bp = 0.5f * (bea[c1] + bea[c2]);
+        const float dmn = 0.5f * (dea[c0] + dea[c1]);
+        const float dpl = 0.5f * (dea[c1] + dea[c2]);
+        const float dqc = sm.Dq[f2] + sm.Dq[f3] + (dqa[c2] - dqa[c0]);
+        const float dmp = sm.Dm[f3] + (dma[c2] - dma[c1]);
+        const float dmm = sm.Dm[f2] + (dma[c1] - dma[c0]);
+        d = -fq * dqc + fd * (dpl * dmp - dmn * dmm) - Cc * (bm * sm.Dh[f2] - bp * sm.Dh[f3]);
+        a = -Cc * bm;
+        c = -Cc * bp;
+        bb = fmaf(Cc, bm + bp, 1.f);
+        if (BC == BC_TRANSMISSIVE) {
+            const int64_t gi = wl + i;
+            if (gi == 0) { bb = fmaf(Cc, bp, 1.f); a = 0.f; }
+            if (gi == n - 1) { bb = fmaf(Cc, bm, 1.f); c = 0.f; }
+        }
+        if (cutL) a = 0.f;
+        if (cutR) c = 0.f;
+    };
+    // tile-boundary mini solves (warps 1 and 2, while warp 0 solves the
+    // separator system of the window)
+    const bool lface = !(BC == BC_TRANSMISSIVE && win.t0 == 0);
+    const bool rface = !(BC == BC_TRANSMISSIVE && win.t0 + win.sp == n);
+    auto mini = [&](int wid) {
+        const int side = wid - 1;
+        if (side < 0 || side > 1 || !(side == 0 ? lface : rface)) return;
+        const int64_t tf = side == 0 ? win.t0 : win.t0 + win.sp;  // right row of the face
+        const MiniWindow mwn = mini_of<BC>(tf, n, Gm::HB);
+        const int ms = (int)(mwn.ml - wl);                         // first mini row in the window
+        const int mw = mwn.mw;
+        auto rowm = [&](int k, float& a, float& bb, float& c, float& d) {
+            if (k >= mw) {
+                a = 0.f; bb = 1.f; c = 0.f; d = 0.f;
+                return;
+            }
+            row_at(ms + k, k == 0 && !mwn.lend, k == mw - 1 && !mwn.rend, a, bb, c, d);
+        };
+        float y[Gm::MB], v[Gm::MB], w[Gm::MB], last[4];
+        int cs, m;
+        warp_block_solve<Gm::MB>(mw + 1, rowm, y, v, w, cs, m, last, p.err);
+        const int kr = (int)(tf - mwn.ml);  // mini row of the face's right row
+#pragma unroll
+        for (int k = 0; k < Gm::MB; ++k) {
+            if (k < m) {
+                if (cs + k == kr - 1) sm.bnd[side][0] = y[k];
+                if (cs + k == kr) sm.bnd[side][1] = y[k];
+            }
+        }
+    };
+    {
+        auto roww = [&](int i, float& a, float& bb, float& c, float& d) {
+            if (i >= W) {  // identity row closing the window
+                a = 0.f; bb = 1.f; c = 0.f; d = 0.f;
+                return;
+            }
+            row_at(i, i == 0 && !win.lend, i == W - 1 && !win.rend, a, bb, c, d);
+        };
+        float y[M], v[M], w[M], last[4];
+        int cs, m;
+        cta_block_solve<T, M>(W + 1, roww, sm.sep, y, v, w, cs, m, last, p.err, mini);
+        // dh = y: the values outside the window (and the closing row) are taken as 0
+#pragma unroll
+        for (int k = 0; k < M; ++k)
+            if (k < m && cs + k < W) sm.mb[pd(cs + k + 1)] = y[k];
+    }
+    __syncthreads();
+    float* const dha = sm.mb;  // dh of window row r at pd(r + 1), r = -1 .. W
+    if (BC == BC_TRANSMISSIVE && tid == 0) {
+        if (win.lend) dha[pd(0)] = dha[pd(1)];
+        if (win.rend) dha[pd(W + 1)] = dha[pd(W)];
+    }
+    __syncthreads();
+
+    // truncation bound of this window: rho*^HB <= 2^-30
+    if (tid == 0) {
+        const bool cut = BC == BC_PERIODIC || !(win.lend && win.rend);
+        const float K = __uint_as_float(sm.kmax), kap = fminf(__uint_as_float(sm.kmin), K);
+        if (cut && K > 0.f) {
+            const float B = 1.f + K + kap;
+            const float rho = 2.f * K / (B + sqrtf(fmaxf(B * B - 4.f * kap * K, 0.f)));
+            if ((float)Gm::HB * __log2f(rho) > -30.f) bad |= HSGN_DEV_ERR_TRUNCATION;
+        }
+    }
+
+    // ---- 4. back-substitution of the tile rows
+    const float fqv = fq, fdv = fd, lamv = lam;
+    auto face_G = [&](float qbL, float qbR, float dqL, float dqR, float dmL, float dmR, float dhL,
+                      float dhR, float deL, float deR, float beL, float beR, float DmL, float DhL) {
+        const float qsum = (qbL + qbR) + (dqL + dqR);
+        const float dmf = DmL + (dmR - dmL);
+        const float dhf = DhL + (dhR - dhL);
+        return fqv * qsum - fdv * (0.5f * (deL + deR)) * dmf - Cc * (0.5f * (beL + beR)) * dhf;
+    };
+    float umax = 0.f;
+    for (int t = tid; t < win.sp; t += T) {
+        const int r = win.lo + t;       // window row
+        const int64_t i = win.t0 + t;   // global row (in range)
+        const int cL = pd(r), cC = pd(r + 1), cR = pd(r + 2);   // cell arrays (cell c at c+1)
+        const int uL = pd(r + 2), uC = pd(r + 3), uR = pd(r + 4);  // U arrays (cell c at c+3)
+        const float dhC = dha[cC];
+        float dhL = dha[cL], dhR = dha[cR];
+        const float qbC = sm.qb[uC], qbL = sm.qb[uL], qbR = sm.qb[uR];
+        const float dqC = dqa[cC], dqL = dqa[cL], dqR = dqa[cR];
+        const float dmC = dma[cC], dmL = dma[cL], dmR = dma[cR];
+        const float beC = bea[cC], beL = bea[cL], beR = bea[cR];
+        const float deC = dea[cC], deL = dea[cL], deR = dea[cR];
+        const float DhL = sm.Dh[uL], DhC = sm.Dh[uC];  // faces r-1/2, r+1/2
+        const float DmL = sm.Dm[uL], DmC = sm.Dm[uC];
+        // face fluxes; at a tile face both rows come from the shared mini solve
+        float aL = dhL, aC = dhC;
+        if (t == 0 && lface) { aL = sm.bnd[0][0]; aC = sm.bnd[0][1]; }
+        const float Gm_ = face_G(qbL, qbC, dqL, dqC, dmL, dmC, aL, aC, deL, deC, beL, beC, DmL, DhL);
+        float bC = dhC, bR = dhR;
+        if (t == win.sp - 1 && rface) { bC = sm.bnd[1][0]; bR = sm.bnd[1][1]; }
+        const float Gp = face_G(qbC, qbR, dqC, dqR, dmC, dmR, bC, bR, deC, deR, beC, beR, DmC, DhC);
+        // q: tau/(2dx) beta (hbar_{i+1} - hbar_{i-1}), lambda tau/(2dx) delta (m^dag_{i+1} - m^dag_{i-1})
+        const float dhc = (DhL + DhC) + (dhR - dhL);
+        const float dmc = (DmL + DmC) + (dmR - dmL);
+        const float dQ = dqC - fqv * beC * dhc - lamv * fqv * deC * dmc;
+        // base depth (rounded) and P0 = h_b^2 - m_b of this cell
+        const double h0 = U0[i], m0 = U2[i];
+        const float hf = f32_of(h0);
+        float hbf = hf, P0 = f32_of(fma(h0, h0, -m0));
+        if (two) {
+            const float dh1 = G1[i] - G1[i + 1], dm1 = p.dm1[i];
+            hbf = fmaf(wb1, dh1, hf);
+            P0 = fmaf(wb1, fmaf(dh1, fmaf(wb1, dh1, 2.f * hf), -dm1), P0);
+        }
+        const float hbar = hbf + dhC;
+        const float P = fmaf(dhC, 2.f * hbf + dhC, P0);  // hbar^2 - m_b
+        const float E = P - dmC;                                  // hbar^2 - m^
+        const float h2 = hbar * hbar;
+        const float iDen = __frcp_rn(h2 + p.lt2);
+        const float dR = fmaf(p.ltau * E, iDen, dra[cC]);
+        const float dM = P - E * h2 * iDen;
+        unsigned b2 = 0;
+        if (!pos_finite(hbar)) b2 |= HSGN_DEV_ERR_DEPTH;
+        if (!isfinite(Gp) || !isfinite(Gm_) || !isfinite(dQ) || !isfinite(dM) || !isfinite(dR))
+            b2 |= HSGN_DEV_ERR_NONFINITE;
+        bad |= b2;
+        if (!two) {
+            p.G1[i + 1] = Gp;
+            if (i == 0) p.G1[0] = Gm_;
+            p.dq1[i] = dQ;
+            p.dm1[i] = dM;
+            p.dr1[i] = dR;
+        } else {
+            const float Tp = fmaf(wb1, G1[i + 1], Gp);
+            const float Tm = fmaf(wb1, G1[i], Gm_);
+            p.out[0][i] = h0 - (f64_of(Tp) - f64_of(Tm));
+            p.out[1][i] = U1[i] + f64_of(fmaf(wb1, p.dq1[i], dQ));
+            p.out[2][i] = m0 + f64_of(fmaf(wb1, p.dm1[i], dM));
+            p.out[3][i] = U3[i] + f64_of(fmaf(wb1, p.dr1[i], dR));
+            if (p.track_speed && !b2) umax = fmaxf(umax, fabsf((qbC + dQ) / hbar));
+        }
+    }
+    if (bad) flag_error(p.err, bad);
+    if (p.track_speed && two) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) umax = fmaxf(umax, __shfl_xor_sync(0xffffffffu, umax, o));
+        if ((tid & 31) == 0 && umax > 0.f)
+            atomicMax(reinterpret_cast<unsigned long long*>(p.speed_next),
+                      (unsigned long long)__double_as_longlong(f64_of(umax)));
+    }
+}
+
+}  // namespace hsgn

@@ -38,10 +38,6 @@ __device__ __forceinline__ int64_t wrap_index(int64_t i, int64_t n, int bc) {
     return i < 0 ? 0 : (i >= n ? n - 1 : i);
 }
 
-// Shared-memory index with one pad word every 32: rows read by threads at a
-// stride of M words (the chunk mapping) then fall in distinct banks.
-__device__ __forceinline__ int pd(int i) { return i + (i >> 5); }
-__host__ __device__ constexpr int pd_size(int n) { return n + (n >> 5) + 1; }
 
 // Even split of n rows into P blocks: block b starts at b*base + min(b, rem)
 // and has base + (b < rem) rows.

@@ -15,7 +15,7 @@
 
 #include "../../include/hsgn.h"
 #include "hsgn_kernels.cuh"
-#include "hsgn_mixed.cuh"
+#include "hsgn_fused.cuh"
 
 using namespace hsgn;
 
@@ -28,10 +28,24 @@ constexpr int XT = 128, XM = 4;
 static_assert(XT * XM == AS, "both precision forms use the same block split");
 // One CTA solves single-precision separator systems of up to OT*OM rows.
 constexpr int OT = 256, OM = 16;
+// Windowed mixed stage: FT threads, FM rows per thread, FHW overlap rows.
+constexpr int FT = 256, FM = 4, FHW = 64;
 // Separator levels: one warp per block of GS rows; one warp solves up to RMAX rows.
 constexpr int GS = SEP_ROWS, RMAX = SEP_ROWS;
 
 constexpr size_t kAlign = 256;
+
+// Tile rows of the windowed path: as few tiles of at most smax rows as
+// possible, evened out so that a grid larger than one wave of `slots`
+// resident CTAs ends in full waves.
+int64_t fused_tile_rows(int64_t n, int64_t smax, int64_t slots) {
+    const int64_t pmin = (n + smax - 1) / smax;
+    if (pmin >= slots) {
+        const int64_t waves = (pmin + slots - 1) / slots;
+        return (n + waves * slots - 1) / (waves * slots);
+    }
+    return (n + pmin - 1) / pmin;
+}
 
 constexpr size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 
@@ -104,6 +118,7 @@ int map_error_bits(unsigned bits) {
     if (bits & HSGN_DEV_ERR_DEPTH) return HSGN_ERR_NONPOSITIVE_DEPTH;
     if (bits & HSGN_DEV_ERR_COERCIVE) return HSGN_ERR_NOT_COERCIVE;
     if (bits & HSGN_DEV_ERR_NONFINITE) return HSGN_ERR_NONFINITE;
+    if (bits & HSGN_DEV_ERR_TRUNCATION) return HSGN_ERR_TRUNCATION;
     return HSGN_OK;
 }
 
@@ -129,7 +144,14 @@ struct hsgn_s {
     double* bathy = nullptr;         // bottom per cell, null for a flat bottom
     double* phi = nullptr;           // face forces Phi_{i+1/2}
     unsigned char* rws = nullptr;    // workspace of the separator-system solve
-    double* spd = nullptr;           // [0] global Rusanov speed, [1] stage speed, [2..3] scratch
+    double* spd = nullptr;           // [0] global Rusanov speed, [1] stage speed, [2..3] scratch,
+                                     // [4] global Rusanov speed while the state is in V
+    // windowed mixed stage (HSGN_MIXED without HSGN_EXACT_SOLVE): one launch per
+    // stage; U^{n+1} goes to the other of the two state buffers U, V
+    bool windowed = false;
+    int32_t tileS = 0;               // tile rows per CTA
+    double* V[4] = {};
+    int cur = 0;                     // 1: the state is in V
     // mixed precision (HSGN_MIXED): FP32 stage-1 increments and per-row results
     bool mixed = false;
     float *G1 = nullptr, *dq1 = nullptr, *dm1 = nullptr, *dr1 = nullptr;
@@ -146,8 +168,8 @@ struct hsgn_s {
     float *mblk = nullptr, *ms_ = nullptr;
     unsigned* err = nullptr;
     cudaStream_t cap = nullptr;      // private stream used for graph capture
-    cudaGraphExec_t gexec = nullptr;
-    double gdt = 0.0;
+    cudaGraphExec_t gexec[2] = {};   // one step, per state buffer
+    double gdt[2] = {};
     // event-pair profiler (hsgn_profile)
     bool prof = false;
     std::vector<cudaEvent_t> ev_pool;
@@ -160,6 +182,11 @@ struct hsgn_s {
 namespace {
 
 bool local_speed(const hsgn_s* H) { return (H->flags & HSGN_RUSANOV_LOCAL) != 0; }
+
+// The buffer holding the current state, and the global Rusanov speed of the
+// state in buffer `which` (0: U, 1: V).
+double* const* state(const hsgn_s* H) { return H->cur ? H->V : H->U; }
+double* speed_of(const hsgn_s* H, int which) { return H->spd + (which ? 4 : 0); }
 
 cudaEvent_t take_event(hsgn_s* H) {
     if (!H->ev_pool.empty()) {
@@ -368,6 +395,54 @@ cudaError_t launch_stage_mixed(hsgn_s* H, int stage, double tau, cudaStream_t st
     return cudaGetLastError();
 }
 
+// One stage of the windowed mixed path (hsgn_fused.cuh): one launch. Stage 1
+// writes the FP32 increments, stage 2 writes U^{n+1} into the other buffer.
+cudaError_t launch_stage_fused(hsgn_s* H, int stage, double tau, cudaStream_t st) {
+    const double gam = 1.0 - 1.0 / std::sqrt(2.0);
+    const double c = 1.0 / (2.0 * gam);
+    FusedParams p;
+    p.n = H->n;
+    p.stage = stage;
+    p.local_speed = local_speed(H) ? 1 : 0;
+    p.track_speed = local_speed(H) ? 0 : 1;
+    p.S = H->tileS;
+    const double dx = H->dx, lam = H->lam;
+    p.g = (float)H->g;
+    p.lam = (float)lam;
+    p.tau = (float)tau;
+    p.tdx = (float)(tau / dx);
+    p.fq = (float)(tau / (2.0 * dx));
+    p.Cc = (float)(tau * tau / (dx * dx));
+    p.fd = (float)(lam * tau * tau / (dx * dx));
+    p.lt2 = (float)(lam * tau * tau);
+    p.ltau = (float)(lam * tau);
+    p.wl1 = stage == 2 ? (float)(c / gam) : 0.f;
+    p.wb1 = stage == 2 ? (float)((1.0 - gam) / gam) : 0.f;
+    double* const* Uc = state(H);
+    double* const* Un = H->cur ? H->U : H->V;
+    for (int k = 0; k < 4; ++k) {
+        p.U[k] = Uc[k];
+        p.out[k] = stage == 2 ? Un[k] : nullptr;
+    }
+    p.G1 = H->G1;
+    p.dq1 = H->dq1;
+    p.dm1 = H->dm1;
+    p.dr1 = H->dr1;
+    p.speed = speed_of(H, H->cur);
+    p.speed_next = speed_of(H, 1 - H->cur);
+    p.err = H->err;
+    const unsigned P = (unsigned)((H->n + H->tileS - 1) / H->tileS);
+    const size_t smem = sizeof(FusedShared<FT, FM, FHW>);
+    {
+        ProfScope ps(H, HSGN_PROF_ASSEMBLE, st);
+        if (H->bc == BC_PERIODIC)
+            k_mixed_fused<FT, FM, FHW, BC_PERIODIC><<<P, FT, smem, st>>>(p);
+        else
+            k_mixed_fused<FT, FM, FHW, BC_TRANSMISSIVE><<<P, FT, smem, st>>>(p);
+    }
+    return cudaGetLastError();
+}
+
 // IMEX step of Sec. 3.2 in efficient form:
 //   U1 = S(U, U, gamma dt);
 //   U  <- S(U_b, U_l, gamma dt), U_l = (1-c/gamma) U + (c/gamma) U1,
@@ -376,6 +451,12 @@ cudaError_t enqueue_step(hsgn_s* H, double dt, cudaStream_t st) {
     const double gam = 1.0 - 1.0 / std::sqrt(2.0);
     const double c = 1.0 / (2.0 * gam);
     const double tau = gam * dt;
+    if (H->windowed) {
+        cudaError_t e = launch_stage_fused(H, 1, tau, st);
+        if (e == cudaSuccess) e = launch_stage_fused(H, 2, tau, st);
+        if (e == cudaSuccess) H->cur ^= 1;
+        return e;
+    }
     if (H->mixed) {
         const cudaError_t e = launch_stage_mixed(H, 1, tau, st);
         if (e != cudaSuccess) return e;
@@ -408,9 +489,11 @@ cudaError_t refresh_speed(hsgn_s* H, cudaStream_t st) {
                                                              H->g, H->speeds, nullptr, H->err);
         return cudaGetLastError();
     }
-    cudaError_t e = cudaMemsetAsync(H->spd, 0, 2 * sizeof(double), st);
+    double* out = speed_of(H, H->cur);
+    cudaError_t e = cudaMemsetAsync(out, 0, 2 * sizeof(double), st);
     if (e != cudaSuccess) return e;
-    k_speeds<<<304, 256, 0, st>>>(H->n, H->U[0], H->U[1], H->U[2], H->g, H->lam, H->spd, H->err);
+    double* const* U = state(H);
+    k_speeds<<<304, 256, 0, st>>>(H->n, U[0], U[1], U[2], H->g, H->lam, out, H->err);
     return cudaGetLastError();
 }
 
@@ -430,6 +513,9 @@ const char* hsgn_error_string(int code) {
         case HSGN_ERR_NONFINITE: return "non-finite value";
         case HSGN_ERR_UNIMPLEMENTED: return "not implemented";
         case HSGN_ERR_OUT_OF_MEMORY: return "out of device memory";
+        case HSGN_ERR_TRUNCATION:
+            return "windowed depth solve: coupling decays too slowly for the overlap (reduce dt "
+                   "or use HSGN_EXACT_SOLVE)";
         default: return "unknown error code";
     }
 }
@@ -445,7 +531,7 @@ int hsgn_create(const hsgn_grid_t* grid, double g, double lambda, const double* 
         return HSGN_ERR_INVALID_ARG;
     if (!(g > 0.0) || !std::isfinite(g) || !(lambda >= 0.0) || !std::isfinite(lambda))
         return HSGN_ERR_INVALID_ARG;
-    if (flags & ~(int32_t)(HSGN_RUSANOV_LOCAL | HSGN_MIXED | HSGN_WELL_BALANCED))
+    if (flags & ~(int32_t)(HSGN_RUSANOV_LOCAL | HSGN_MIXED | HSGN_WELL_BALANCED | HSGN_EXACT_SOLVE))
         return HSGN_ERR_UNIMPLEMENTED;
     if (bathymetry && !(flags & HSGN_WELL_BALANCED)) return HSGN_ERR_INVALID_ARG;
     if ((flags & HSGN_WELL_BALANCED) && (flags & HSGN_MIXED)) return HSGN_ERR_UNIMPLEMENTED;
@@ -464,16 +550,18 @@ int hsgn_create(const hsgn_grid_t* grid, double g, double lambda, const double* 
     const int64_t n = H->n, P = H->split.P;
 
     H->mixed = (flags & HSGN_MIXED) != 0;
+    H->windowed = H->mixed && !(flags & HSGN_EXACT_SOLVE);
     H->wb = (flags & HSGN_WELL_BALANCED) != 0;
     const size_t vec = align_up(n * sizeof(double));
     const size_t fvec = align_up((n + 1) * sizeof(float));
     const size_t recb = align_up(3 * n * sizeof(float4));
-    size_t total = H->mixed ? 4 * vec + 4 * fvec + recb  // U; G1 dq1 dm1 dr1; row records
-                            : 16 * vec;                  // U, U1, y v w, 5 back-sub arrays
+    size_t total = H->windowed ? 8 * vec + 4 * fvec            // U, V; G1 dq1 dm1 dr1
+                   : H->mixed  ? 4 * vec + 4 * fvec + recb     // U; G1 dq1 dm1 dr1; row records
+                               : 16 * vec;                     // U, U1, y v w, 5 back-sub arrays
     if (H->wb) total += (bathymetry ? 2 : 1) * vec;      // Phi, bottom
     total += align_up(BLK_STRIDE * P * sizeof(double)) + align_up(P * sizeof(double));
     const size_t rws = rows_ws_bytes(P);
-    total += rws + align_up(4 * sizeof(double)) + align_up(sizeof(unsigned));
+    total += rws + align_up(8 * sizeof(double)) + align_up(sizeof(unsigned));
     if (cudaMalloc(&H->mem, total) != cudaSuccess) {
         cudaGetLastError();
         delete H;
@@ -486,7 +574,13 @@ int hsgn_create(const hsgn_grid_t* grid, double g, double lambda, const double* 
         return r;
     };
     for (int k = 0; k < 4; ++k) H->U[k] = reinterpret_cast<double*>(take(vec));
-    if (H->mixed) {
+    if (H->windowed) {
+        for (int k = 0; k < 4; ++k) H->V[k] = reinterpret_cast<double*>(take(vec));
+        H->G1 = reinterpret_cast<float*>(take(fvec));
+        H->dq1 = reinterpret_cast<float*>(take(fvec));
+        H->dm1 = reinterpret_cast<float*>(take(fvec));
+        H->dr1 = reinterpret_cast<float*>(take(fvec));
+    } else if (H->mixed) {
         H->G1 = reinterpret_cast<float*>(take(fvec));
         H->dq1 = reinterpret_cast<float*>(take(fvec));
         H->dm1 = reinterpret_cast<float*>(take(fvec));
@@ -512,10 +606,25 @@ int hsgn_create(const hsgn_grid_t* grid, double g, double lambda, const double* 
         }
     }
     H->rws = rws ? take(rws) : nullptr;
-    H->spd = reinterpret_cast<double*>(take(align_up(4 * sizeof(double))));
+    H->spd = reinterpret_cast<double*>(take(align_up(8 * sizeof(double))));
     H->err = reinterpret_cast<unsigned*>(take(align_up(sizeof(unsigned))));
 
     cudaError_t e = cudaMemset(H->mem, 0, total);
+    if (e == cudaSuccess && H->windowed) {
+        e = set_smem(k_mixed_fused<FT, FM, FHW, BC_PERIODIC>, sizeof(FusedShared<FT, FM, FHW>));
+        if (e == cudaSuccess)
+            e = set_smem(k_mixed_fused<FT, FM, FHW, BC_TRANSMISSIVE>,
+                         sizeof(FusedShared<FT, FM, FHW>));
+        int sms = 0, per_sm = 0;
+        if (e == cudaSuccess)
+            e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, H->device);
+        if (e == cudaSuccess)
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                &per_sm, k_mixed_fused<FT, FM, FHW, BC_PERIODIC>, FT,
+                sizeof(FusedShared<FT, FM, FHW>));
+        const int64_t slots = (int64_t)(sms > 0 ? sms : 1) * (per_sm > 0 ? per_sm : 1);
+        H->tileS = (int32_t)fused_tile_rows(n, FusedGeom<FT, FM, FHW>::S, slots);
+    }
     // the bottom: host or device memory, copied once (cudaMemcpyDefault infers which)
     if (e == cudaSuccess && H->bathy)
         e = cudaMemcpy(H->bathy, bathymetry, n * sizeof(double), cudaMemcpyDefault);
@@ -552,7 +661,8 @@ void hsgn_destroy(hsgn_handle_t H) {
         cudaEventDestroy(r.b);
     }
     for (cudaEvent_t e : H->ev_pool) cudaEventDestroy(e);
-    if (H->gexec) cudaGraphExecDestroy(H->gexec);
+    for (int c = 0; c < 2; ++c)
+        if (H->gexec[c]) cudaGraphExecDestroy(H->gexec[c]);
     if (H->cap) cudaStreamDestroy(H->cap);
     cudaFree(H->mem);
     delete H;
@@ -564,7 +674,7 @@ int hsgn_set_state(hsgn_handle_t H, const double* depth, const double* q, const 
     cudaStream_t st = as_stream(stream);
     const double* src[4] = {depth, q, heta, hw};
     for (int k = 0; k < 4; ++k)
-        if (cudaMemcpyAsync(H->U[k], src[k], H->n * sizeof(double), cudaMemcpyDefault, st) !=
+        if (cudaMemcpyAsync(state(H)[k], src[k], H->n * sizeof(double), cudaMemcpyDefault, st) !=
             cudaSuccess)
             return HSGN_ERR_CUDA;
     return refresh_speed(H, st) == cudaSuccess ? HSGN_OK : HSGN_ERR_CUDA;
@@ -576,7 +686,7 @@ int hsgn_get_state(hsgn_handle_t H, double* depth, double* q, double* heta, doub
     cudaStream_t st = as_stream(stream);
     double* dst[4] = {depth, q, heta, hw};
     for (int k = 0; k < 4; ++k)
-        if (cudaMemcpyAsync(dst[k], H->U[k], H->n * sizeof(double), cudaMemcpyDefault, st) !=
+        if (cudaMemcpyAsync(dst[k], state(H)[k], H->n * sizeof(double), cudaMemcpyDefault, st) !=
             cudaSuccess)
             return HSGN_ERR_CUDA;
     return read_error(H, st);
@@ -596,36 +706,42 @@ int hsgn_step(hsgn_handle_t H, double dt, void* stream) {
 int hsgn_enqueue(hsgn_handle_t H, double dt, int64_t n_steps, void* stream) {
     if (!H || !valid_dt(H, dt) || n_steps < 0) return HSGN_ERR_INVALID_ARG;
     cudaStream_t st = as_stream(stream);
-    if (n_steps == 0) return HSGN_OK;
-    if (!H->gexec || H->gdt != dt) {
-        const bool prof = H->prof;
-        H->prof = false;  // events are not captured into the graph
-        if (H->gexec) {
-            cudaGraphExecDestroy(H->gexec);
-            H->gexec = nullptr;
+    // one captured step per state buffer (the windowed path alternates them)
+    for (int64_t k = 0; k < n_steps; ++k) {
+        const int c = H->cur;
+        if (!H->gexec[c] || H->gdt[c] != dt) {
+            const bool prof = H->prof;
+            H->prof = false;  // events are not captured into the graph
+            if (H->gexec[c]) {
+                cudaGraphExecDestroy(H->gexec[c]);
+                H->gexec[c] = nullptr;
+            }
+            cudaGraph_t graph = nullptr;
+            if (cudaStreamBeginCapture(H->cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+                H->prof = prof;
+                return HSGN_ERR_CUDA;
+            }
+            const cudaError_t e1 = enqueue_step(H, dt, H->cap);
+            const cudaError_t e2 = cudaStreamEndCapture(H->cap, &graph);
+            H->prof = prof;
+            H->cur = c;  // capturing does not advance the state
+            if (e1 != cudaSuccess || e2 != cudaSuccess) {
+                if (graph) cudaGraphDestroy(graph);
+                cudaGetLastError();
+                return HSGN_ERR_CUDA;
+            }
+            const cudaError_t e3 = cudaGraphInstantiate(&H->gexec[c], graph, 0);
+            cudaGraphDestroy(graph);
+            if (e3 != cudaSuccess) {
+                H->gexec[c] = nullptr;
+                cudaGetLastError();
+                return HSGN_ERR_CUDA;
+            }
+            H->gdt[c] = dt;
         }
-        cudaGraph_t graph = nullptr;
-        if (cudaStreamBeginCapture(H->cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
-            return HSGN_ERR_CUDA;
-        const cudaError_t e1 = enqueue_step(H, dt, H->cap);
-        const cudaError_t e2 = cudaStreamEndCapture(H->cap, &graph);
-        H->prof = prof;
-        if (e1 != cudaSuccess || e2 != cudaSuccess) {
-            if (graph) cudaGraphDestroy(graph);
-            cudaGetLastError();
-            return HSGN_ERR_CUDA;
-        }
-        const cudaError_t e3 = cudaGraphInstantiate(&H->gexec, graph, 0);
-        cudaGraphDestroy(graph);
-        if (e3 != cudaSuccess) {
-            H->gexec = nullptr;
-            cudaGetLastError();
-            return HSGN_ERR_CUDA;
-        }
-        H->gdt = dt;
+        if (cudaGraphLaunch(H->gexec[c], st) != cudaSuccess) return HSGN_ERR_CUDA;
+        if (H->windowed) H->cur ^= 1;
     }
-    for (int64_t k = 0; k < n_steps; ++k)
-        if (cudaGraphLaunch(H->gexec, st) != cudaSuccess) return HSGN_ERR_CUDA;
     return HSGN_OK;
 }
 
@@ -678,7 +794,8 @@ int hsgn_suggest_dt(hsgn_handle_t H, double cfl, double mcfl, double* dt_out, vo
     cudaStream_t st = as_stream(stream);
     double* tmp = H->spd + 2;
     if (cudaMemsetAsync(tmp, 0, 2 * sizeof(double), st) != cudaSuccess) return HSGN_ERR_CUDA;
-    k_speeds<<<304, 256, 0, st>>>(H->n, H->U[0], H->U[1], H->U[2], H->g, H->lam, tmp, H->err);
+    double* const* U = state(H);
+    k_speeds<<<304, 256, 0, st>>>(H->n, U[0], U[1], U[2], H->g, H->lam, tmp, H->err);
     if (cudaGetLastError() != cudaSuccess) return HSGN_ERR_CUDA;
     double hv[2];
     if (cudaMemcpyAsync(hv, tmp, sizeof(hv), cudaMemcpyDeviceToHost, st) != cudaSuccess)
@@ -773,7 +890,7 @@ int hsgn_create_batched(int32_t count, const int64_t* n, const double* x_left,
     total += align_up(BLK_STRIDE * blocks * sizeof(float)) + align_up(blocks * sizeof(float));
     total += align_up(count * sizeof(InstInfo)) + align_up(blocks * sizeof(int32_t));
     total += 3 * align_up(count * sizeof(double));
-    total += align_up(4 * sizeof(double)) + align_up(sizeof(unsigned));
+    total += align_up(8 * sizeof(double)) + align_up(sizeof(unsigned));
     if (cudaMalloc(&H->mem, total) != cudaSuccess) {
         cudaGetLastError();
         delete H;
@@ -797,7 +914,7 @@ int hsgn_create_batched(int32_t count, const int64_t* n, const double* x_left,
     H->blk_inst = reinterpret_cast<int32_t*>(take(align_up(blocks * sizeof(int32_t))));
     H->speeds = reinterpret_cast<double*>(take(align_up(count * sizeof(double))));
     H->speeds_tmp = reinterpret_cast<double*>(take(2 * align_up(count * sizeof(double))));
-    H->spd = reinterpret_cast<double*>(take(align_up(4 * sizeof(double))));
+    H->spd = reinterpret_cast<double*>(take(align_up(8 * sizeof(double))));
     H->err = reinterpret_cast<unsigned*>(take(align_up(sizeof(unsigned))));
     cudaError_t e = cudaMemset(H->mem, 0, total);
     if (e == cudaSuccess)

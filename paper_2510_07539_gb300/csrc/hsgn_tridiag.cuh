@@ -28,8 +28,19 @@
 #define HSGN_DEV_ERR_DEPTH 1u
 #define HSGN_DEV_ERR_COERCIVE 2u
 #define HSGN_DEV_ERR_NONFINITE 4u
+#define HSGN_DEV_ERR_TRUNCATION 8u  // windowed solve: coupling decays too slowly
 
 namespace hsgn {
+
+// Shared-memory index with one pad word every 32: rows read by threads at a
+// stride of 4 or 8 words (the chunk mapping) then fall in distinct banks.
+__host__ __device__ __forceinline__ int pd(int i) { return i + (i >> 5); }
+__host__ __device__ constexpr int pd_size(int n) { return n + (n >> 5) + 1; }
+
+// No extra work for the warps that wait while warp 0 solves a separator system.
+struct NoSide {
+    __device__ void operator()(int) const {}
+};
 
 __device__ __forceinline__ void flag_error(unsigned* err, unsigned bits) {
     if (err) atomicOr(err, bits);
@@ -60,10 +71,12 @@ __device__ __forceinline__ double rcp(double x) { return 1.0 / x; }
 __device__ __forceinline__ float rcp(float x) { return __frcp_rn(x); }
 
 // Shared memory of the separator system of a CTA with T threads.
+// Indexed with pd(): warp 0 reads the rows at a stride of T/32.
 template <int T, class Real = double>
 struct SepShared {
-    Real A[T], B[T], C[T], D1[T];
-    Real YF[T], VF[T], WF[T];  // first-interior values, then the separator triples
+    static constexpr int NP = pd_size(T);
+    Real A[NP], B[NP], C[NP], D1[NP];
+    Real YF[NP], VF[NP], WF[NP];  // first-interior values, then the separator triples
 };
 
 // Chunk of rows [cs, cs + m) owned by thread t when `nrows` rows are split as
@@ -265,11 +278,12 @@ __device__ __forceinline__ void warp_block_solve(int nrows, RowFn row, Real (&y)
 // On return thread t holds, for k < m, the triple (y, v, w) of row cs + k; the
 // block separator (row nrows - 1) gets (0, 0, -1). The thread that owns the
 // last row also returns its coefficients in last[0..3].
-template <int T, int M, class RowFn, class Real>
+// While warp 0 solves the separator system, every other warp w calls side(w).
+template <int T, int M, class RowFn, class Real, class Side = NoSide>
 __device__ __forceinline__ void cta_block_solve(int nrows, RowFn row, SepShared<T, Real>& sh,
                                                 Real (&y)[M], Real (&v)[M], Real (&w)[M],
                                                 int& cs, int& m, Real (&last)[4],
-                                                unsigned* err) {
+                                                unsigned* err, Side side = Side()) {
     const int t = threadIdx.x;
     int teff;
     chunk_of<T>(nrows, t, cs, m, teff);
@@ -334,9 +348,9 @@ __device__ __forceinline__ void cta_block_solve(int nrows, RowFn row, SepShared<
     // first-interior values of the chunk; an empty interior means the row
     // after the previous separator is this chunk's separator: (0, 0, -1)
     if (t < teff) {
-        sh.YF[t] = nint > 0 ? y[0] : Real(0);
-        sh.VF[t] = nint > 0 ? v[0] : Real(0);
-        sh.WF[t] = nint > 0 ? w[0] : -Real(1);
+        sh.YF[pd(t)] = nint > 0 ? y[0] : Real(0);
+        sh.VF[pd(t)] = nint > 0 ? v[0] : Real(0);
+        sh.WF[pd(t)] = nint > 0 ? w[0] : -Real(1);
     }
     __syncthreads();
 
@@ -347,10 +361,10 @@ __device__ __forceinline__ void cta_block_solve(int nrows, RowFn row, SepShared<
     //         is (Ys, Vs, Ws) with sigma_t = Ys - x_L Vs - x_R Ws.
     const int ns = teff - 1;
     if (t < ns) {
-        sh.A[t] = -sa * VL;
-        sh.B[t] = sb - sa * WL - sc * sh.VF[t + 1];
-        sh.C[t] = -sc * sh.WF[t + 1];
-        sh.D1[t] = sd - sa * YL - sc * sh.YF[t + 1];
+        sh.A[pd(t)] = -sa * VL;
+        sh.B[pd(t)] = sb - sa * WL - sc * sh.VF[pd(t + 1)];
+        sh.C[pd(t)] = -sc * sh.WF[pd(t + 1)];
+        sh.D1[pd(t)] = sd - sa * YL - sc * sh.YF[pd(t + 1)];
     }
     if (t == teff - 1) {
         last[0] = sa;
@@ -359,14 +373,15 @@ __device__ __forceinline__ void cta_block_solve(int nrows, RowFn row, SepShared<
         last[3] = sd;
     }
     __syncthreads();
+    if (t >= 32) side(t >> 5);
     if (ns > 0 && t < 32) {
         constexpr int MW = (T + 31) / 32;
         auto srow = [&](int r, Real& a, Real& b, Real& c, Real& d) {
             if (r < ns) {
-                a = sh.A[r];
-                b = sh.B[r];
-                c = sh.C[r];
-                d = sh.D1[r];
+                a = sh.A[pd(r)];
+                b = sh.B[pd(r)];
+                c = sh.C[pd(r)];
+                d = sh.D1[pd(r)];
             } else {  // the external x_R: never eliminated
                 a = Real(0);
                 b = Real(1);
@@ -380,9 +395,9 @@ __device__ __forceinline__ void cta_block_solve(int nrows, RowFn row, SepShared<
 #pragma unroll
         for (int k = 0; k < MW; ++k) {
             if (k < m2 && c2 + k < ns) {
-                sh.YF[c2 + k] = ys[k];
-                sh.VF[c2 + k] = vs[k];
-                sh.WF[c2 + k] = ws[k];
+                sh.YF[pd(c2 + k)] = ys[k];
+                sh.VF[pd(c2 + k)] = vs[k];
+                sh.WF[pd(c2 + k)] = ws[k];
             }
         }
     }
@@ -397,18 +412,18 @@ __device__ __forceinline__ void cta_block_solve(int nrows, RowFn row, SepShared<
             VsL = -Real(1);
             WsL = Real(0);
         } else {
-            YsL = sh.YF[t - 1];
-            VsL = sh.VF[t - 1];
-            WsL = sh.WF[t - 1];
+            YsL = sh.YF[pd(t - 1)];
+            VsL = sh.VF[pd(t - 1)];
+            WsL = sh.WF[pd(t - 1)];
         }
         if (t == teff - 1) {
             YsR = Real(0);
             VsR = Real(0);
             WsR = -Real(1);
         } else {
-            YsR = sh.YF[t];
-            VsR = sh.VF[t];
-            WsR = sh.WF[t];
+            YsR = sh.YF[pd(t)];
+            VsR = sh.VF[pd(t)];
+            WsR = sh.WF[pd(t)];
         }
 #pragma unroll
         for (int k = 0; k < M; ++k) {

@@ -22,11 +22,12 @@ FLAG_FP64 = 0x0
 FLAG_MIXED = 0x1
 FLAG_RUSANOV_LOCAL = 0x10
 FLAG_WELL_BALANCED = 0x2
+FLAG_EXACT_SOLVE = 0x4
 
 ERROR_NAMES = {
     1: "HSGN_ERR_INVALID_ARG", 2: "HSGN_ERR_CUDA", 3: "HSGN_ERR_NONPOSITIVE_DEPTH",
     4: "HSGN_ERR_NOT_COERCIVE", 5: "HSGN_ERR_NONFINITE", 6: "HSGN_ERR_UNIMPLEMENTED",
-    7: "HSGN_ERR_OUT_OF_MEMORY",
+    7: "HSGN_ERR_OUT_OF_MEMORY", 8: "HSGN_ERR_TRUNCATION",
 }
 
 

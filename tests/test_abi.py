@@ -39,7 +39,7 @@ def test_library_exports_every_declared_symbol(lib):
 
 
 def test_error_strings(lib):
-    for code in range(0, 8):
+    for code in range(0, 9):
         s = lib.hsgn_error_string(code)
         assert s and len(s) > 1
     assert b"unknown" in lib.hsgn_error_string(99)

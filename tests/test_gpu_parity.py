@@ -247,19 +247,20 @@ def test_adjoint_reports_unimplemented():
 # summand scales; a 500-step solitary-wave trajectory <= 1e-6 relative L2
 # (target of the mixed form); mass conserved to FP64 rounding (flux form).
 # --------------------------------------------------------------------------
-def mixed_run(n, x_left, x_right, bc, lam, U, dt, steps, use_graph=True):
-    return gpu_run(n, x_left, x_right, bc, lam, U, dt, steps, flags=S().FLAG_MIXED,
-                   use_graph=use_graph)
+def mixed_run(n, x_left, x_right, bc, lam, U, dt, steps, use_graph=True, exact=False):
+    flags = S().FLAG_MIXED | (S().FLAG_EXACT_SOLVE if exact else 0)
+    return gpu_run(n, x_left, x_right, bc, lam, U, dt, steps, flags=flags, use_graph=use_graph)
 
 
+@pytest.mark.parametrize("exact", [False, True])
 @pytest.mark.parametrize("bc", [0, 1])
 @pytest.mark.parametrize("n", [5, 100, 1000, 1537, 70001])
-def test_mixed_one_step_close_to_oracle(n, bc):
+def test_mixed_one_step_close_to_oracle(n, bc, exact):
     dx, lam = 0.1, 500.0
     U = inputs.random_state(3000 + n, n, dx)
     p = oracle.Params(n, dx, bc, lam=lam)
     dt, _, _ = oracle.suggest_dt(p, U, 2.0, 0.5)
-    got = mixed_run(n, 0.0, n * dx, bc, lam, U, dt, 1)
+    got = mixed_run(n, 0.0, n * dx, bc, lam, U, dt, 1, exact=exact)
     ref = oracle.step(p, U, dt)
     sc = summand_scales(n, dx, bc, lam, U, dt)
     assert rel_l2(got[0], ref[0]) < 1e-7, rel_l2(got[0], ref[0])
@@ -268,13 +269,14 @@ def test_mixed_one_step_close_to_oracle(n, bc):
         assert scaled_err(got[k], ref[k], sc[k]) < 1e-6, (k, scaled_err(got[k], ref[k], sc[k]))
 
 
-def test_mixed_solitary_trajectory_500_steps():
+@pytest.mark.parametrize("exact", [False, True])
+def test_mixed_solitary_trajectory_500_steps(exact):
     n, lam = 1000, 100.0
     x, dx = inputs.cell_centres(n, -50.0, 50.0)
     U = inputs.solitary(x, 1.0, 0.2, 0.0, period=100.0)
     p = oracle.Params(n, dx, 0, lam=lam)
     dt, _, _ = oracle.suggest_dt(p, U, 1e9, 0.5)
-    got = mixed_run(n, -50.0, 50.0, 0, lam, U, dt, 500)
+    got = mixed_run(n, -50.0, 50.0, 0, lam, U, dt, 500, exact=exact)
     ref = oracle.run(p, U, dt, 500)
     errs = [rel_l2(got[k], ref[k]) for k in range(4)]
     assert errs[0] < 1e-6 and errs[2] < 1e-6, errs
@@ -282,28 +284,90 @@ def test_mixed_solitary_trajectory_500_steps():
     assert abs(math.fsum(got[0]) - math.fsum(U[0])) <= 1e-13 * math.fsum(U[0])
 
 
-def test_mixed_mass_conservation_and_graph():
+@pytest.mark.parametrize("exact", [False, True])
+def test_mixed_mass_conservation_and_graph(exact):
+    # 4099 cells: the windowed path splits them into 4 tiles, so the face
+    # fluxes at 4 tile faces are shared by two CTAs each
     n, dx = 4099, 0.1
     U = inputs.random_state(42, n, dx)
-    a = mixed_run(n, 0.0, n * dx, 0, 500.0, U, 0.01, 300, use_graph=True)
-    b = mixed_run(n, 0.0, n * dx, 0, 500.0, U, 0.01, 300, use_graph=False)
+    a = mixed_run(n, 0.0, n * dx, 0, 500.0, U, 0.01, 300, use_graph=True, exact=exact)
+    b = mixed_run(n, 0.0, n * dx, 0, 500.0, U, 0.01, 300, use_graph=False, exact=exact)
     assert abs(math.fsum(a[0]) - math.fsum(U[0])) <= 1e-13 * math.fsum(U[0])
     for k in range(4):
         np.testing.assert_array_equal(a[k], b[k])
 
 
+@pytest.mark.parametrize("exact", [False, True])
 @pytest.mark.parametrize("lam", [10.0, 1000.0])
-def test_mixed_dam_break_full_size(lam):
+def test_mixed_dam_break_full_size(lam, exact):
     n, dx, steps = 1 << 20, 0.05, 10
     x, U = inputs.dam_break(n, dx, 1.2, 1.0, 5.0 / dx)
     p = oracle.Params(n, dx, 1, lam=lam)
     dt, _, _ = oracle.suggest_dt(p, U, 4.0, 0.5)
-    got = mixed_run(n, -0.5 * n * dx, 0.5 * n * dx, 1, lam, U, dt, steps)
+    got = mixed_run(n, -0.5 * n * dx, 0.5 * n * dx, 1, lam, U, dt, steps, exact=exact)
     ref = oracle.run(p, U, dt, steps)
     sc = summand_scales(n, dx, 1, lam, U, dt)
     assert rel_l2(got[0], ref[0]) < 1e-7, rel_l2(got[0], ref[0])
     for k in range(4):
         assert scaled_err(got[k], ref[k], sc[k]) < 1e-6, (k, scaled_err(got[k], ref[k], sc[k]))
+
+
+@pytest.mark.parametrize("bc", [0, 1])
+def test_windowed_close_to_exact_mixed(bc):
+    # the two mixed solves differ only by FP32 rounding (and the dropped
+    # coupling, below 2^-30 of the increment); 70001 cells = 55 tiles
+    n, dx, lam = 70001, 0.05, 1000.0
+    if bc == 1:
+        x, U = inputs.dam_break(n, dx, 1.2, 1.0, 5.0 / dx)
+    else:  # a dam break has an unsmoothed jump across a periodic seam
+        U = inputs.random_state(70001, n, dx)
+    p = oracle.Params(n, dx, bc, lam=lam)
+    dt, _, _ = oracle.suggest_dt(p, U, 4.0, 0.5)
+    a = mixed_run(n, 0.0, n * dx, bc, lam, U, dt, 5)
+    b = mixed_run(n, 0.0, n * dx, bc, lam, U, dt, 5, exact=True)
+    assert rel_l2(a[0], b[0]) < 1e-7 and rel_l2(a[2], b[2]) < 1e-7
+    assert abs(math.fsum(a[0]) - math.fsum(b[0])) <= 1e-12 * math.fsum(b[0]) or bc == 1
+
+
+def test_windowed_alternates_buffers_consistently():
+    # odd step counts, graph replays and single steps interleaved: the state
+    # must follow the buffer that holds it
+    n, dx = 3001, 0.1
+    U = inputs.random_state(7, n, dx)
+    with S().Solver(n, 0.0, n * dx, 0, lam=300.0, flags=S().FLAG_MIXED) as s:
+        s.set_state(*(dev(u) for u in U))
+        s.run(0.01, 2)
+        s.step(0.01)
+        s.run(0.01, 3)
+        a = [t.cpu().numpy() for t in s.get_state()]
+        s.set_state(*(dev(u) for u in U))
+        for _ in range(6):
+            s.step(0.01)
+        s.check()
+        b = [t.cpu().numpy() for t in s.get_state()]
+    for k in range(4):
+        np.testing.assert_array_equal(a[k], b[k])
+
+
+def test_windowed_reports_truncation_and_exact_path_does_not():
+    # CFL_IMEX 16: tau^2 beta/dx^2 ~ 21, the coupling decays by 0.95 per row,
+    # too slowly for a 128-row overlap; the exact separator solve has no limit
+    n, dx, lam = 20000, 0.1, 100.0
+    x, _ = inputs.cell_centres(n, 0.0, n * dx)
+    U = inputs.solitary(x, 1.0, 0.05, 0.5 * n * dx, period=n * dx)
+    p = oracle.Params(n, dx, 0, lam=lam)
+    dt, _, _ = oracle.suggest_dt(p, U, 16.0, 1e9)
+    with S().Solver(n, 0.0, n * dx, 0, lam=lam, flags=S().FLAG_MIXED) as s:
+        s.set_state(*(dev(u) for u in U))
+        s.step(dt)
+        with pytest.raises(S().HsgnError) as e:
+            s.check()
+        assert e.value.code == 8
+    with S().Solver(n, 0.0, n * dx, 0, lam=lam,
+                    flags=S().FLAG_MIXED | S().FLAG_EXACT_SOLVE) as s:
+        s.set_state(*(dev(u) for u in U))
+        s.step(dt)
+        s.check()
 
 
 def test_mixed_rejects_stage_entry():
@@ -337,7 +401,8 @@ def test_batched_equals_single_instance_mixed_bitwise():
         got = [t.cpu().numpy() for t in B.get_state()]
     for k_inst, it in enumerate(insts):
         o0, o1 = int(B.offsets[k_inst]), int(B.offsets[k_inst + 1])
-        single = mixed_run(it.n, xl[k_inst], xr[k_inst], 0, it.lam, it.state, dts[k_inst], 5)
+        single = mixed_run(it.n, xl[k_inst], xr[k_inst], 0, it.lam, it.state, dts[k_inst], 5,
+                           exact=True)
         for k in range(4):
             np.testing.assert_array_equal(got[k][o0:o1], single[k])
 
