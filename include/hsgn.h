@@ -73,7 +73,10 @@ enum {
                                 * geometrically; each CTA checks the decay bound and
                                 * reports HSGN_ERR_TRUNCATION when the dropped part
                                 * could exceed 2^-30 of the increment). The state
-                                * alternates between two device buffers.
+                                * alternates between two device buffers and is held
+                                * as double-float pairs (hi + lo, 48-bit significand;
+                                * set/get_state convert from and to doubles), so the
+                                * stage runs without double-precision instructions.
                                 * hsgn_stage is not available in this form. */
 #define HSGN_EXACT_SOLVE 0x4   /* with HSGN_MIXED: solve the depth system exactly
                                 * through the global separator system (three

@@ -34,11 +34,46 @@
 //    conservative to FP64 rounding.
 //  * Stage 2 cannot update U in place (the windows of neighbouring tiles still
 //    read U^n), so it writes U^{n+1} to a second state buffer.
+//  * The state is held as double-float pairs x = hi + lo (hi = x rounded to
+//    single precision, |lo| <= half an ulp of hi: a 48-bit significand), so
+//    that no step of the stage needs the double-precision datapath, which on
+//    sm_103a runs at 1/58 of the single-precision rate:
+//      - hi is the single-precision value the stage works with;
+//      - differences of neighbouring values are (hi1 - hi0) + (lo1 - lo0),
+//        where hi1 - hi0 is exact for values within a factor 2 (Sterbenz);
+//      - h^2 - m uses the exact product hi*hi = p + e (one fma);
+//      - the accumulation U + dU is TwoSum (Knuth) followed by a renormalising
+//        TwoSum, and the depth subtracts the exact difference of the two face
+//        fluxes (TwoSum again), so the depth update stays conservative up to
+//        the 2^-49 rounding of the pair.
 #pragma once
 
 #include "hsgn_mixed.cuh"
 
 namespace hsgn {
+
+// s + e = a + b exactly (Knuth's TwoSum, no ordering assumption).
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+// (hi, lo) + (x + y) with x + y given exactly as two floats; renormalised.
+__device__ __forceinline__ float2 df_add(float2 a, float x, float y) {
+    float s, e;
+    two_sum(a.x, x, s, e);
+    e = __fadd_rn(e, __fadd_rn(a.y, y));
+    float h, l;
+    two_sum(s, e, h, l);
+    return make_float2(h, l);
+}
+
+// Pair of a double (state conversion, off the stepping path).
+__device__ __forceinline__ float2 df_of(double x) {
+    const float hi = __double2float_rn(x);
+    return make_float2(hi, __double2float_rn(x - (double)hi));
+}
 
 struct FusedParams {
     int64_t n;
@@ -47,9 +82,9 @@ struct FusedParams {
     int32_t track_speed;  // stage 1 clears *speed_next, stage 2 folds max |u| into it
     int32_t S;            // tile rows (<= the kernel's capacity)
     float g, lam, tau, tdx, fq, Cc, fd, lt2, ltau, wl1, wb1;
-    const double* U[4];             // U^n (FP64)
+    const float2* U[4];             // U^n (double-float pairs)
     float *G1, *dq1, *dm1, *dr1;    // stage-1 increments; G1 has n+1 faces (face i+1/2 at i+1)
-    double* out[4];                 // U^{n+1} (stage 2; not aliased with U)
+    float2* out[4];                 // U^{n+1} (stage 2; not aliased with U)
     const double* speed;            // global Rusanov speed of the step
     double* speed_next;             // max |u^{n+1}|
     unsigned* err;
@@ -165,10 +200,10 @@ __global__ void __launch_bounds__(T, 4) k_mixed_fused(const FusedParams p) {
     const int64_t wl = win.wl;
     const bool two = p.stage == 2;
     const float wl1 = p.wl1, wb1 = p.wb1;
-    const double* __restrict__ U0 = p.U[0];
-    const double* __restrict__ U1 = p.U[1];
-    const double* __restrict__ U2 = p.U[2];
-    const double* __restrict__ U3 = p.U[3];
+    const float2* __restrict__ U0 = p.U[0];
+    const float2* __restrict__ U1 = p.U[1];
+    const float2* __restrict__ U2 = p.U[2];
+    const float2* __restrict__ U3 = p.U[3];
     const float* __restrict__ G1 = p.G1;
     if (tid == 0) {
         sm.kmax = 0u;
@@ -186,9 +221,9 @@ __global__ void __launch_bounds__(T, 4) k_mixed_fused(const FusedParams p) {
         if (j < W + 6) {
             const int64_t gi = inner ? wl - 3 + j : cell_at<BC>(wl - 3 + j, n);
             const int64_t gn = inner ? gi + 1 : cell_at<BC>(wl - 2 + j, n);
-            const double h0 = __ldg(U0 + gi), q0 = __ldg(U1 + gi);
-            const double m0 = __ldg(U2 + gi), rr0 = __ldg(U3 + gi);
-            const double h1 = __ldg(U0 + gn), q1 = __ldg(U1 + gn), m1 = __ldg(U2 + gn);
+            const float2 h0 = __ldg(U0 + gi), q0 = __ldg(U1 + gi);
+            const float2 m0 = __ldg(U2 + gi), rr0 = __ldg(U3 + gi);
+            const float2 h1 = __ldg(U0 + gn), q1 = __ldg(U1 + gn), m1 = __ldg(U2 + gn);
             float dh1 = 0.f, dq1 = 0.f, dm1 = 0.f, dr1 = 0.f, dh1n = 0.f, dq1n = 0.f, dm1n = 0.f;
             if (two) {
                 const float g0 = __ldg(G1 + gi), g1 = __ldg(G1 + gi + 1);
@@ -201,7 +236,7 @@ __global__ void __launch_bounds__(T, 4) k_mixed_fused(const FusedParams p) {
                 dh1 = g0 - g1;
                 dh1n = g2 - g3;
             }
-            const float hf = f32_of(h0), qf = f32_of(q0), mf = f32_of(m0), rf = f32_of(rr0);
+            const float hf = h0.x, qf = q0.x, mf = m0.x, rf = rr0.x;
             const int jp = pd(j);
             sm.hl[jp] = fmaf(wl1, dh1, hf);
             sm.ql[jp] = fmaf(wl1, dq1, qf);
@@ -210,9 +245,13 @@ __global__ void __launch_bounds__(T, 4) k_mixed_fused(const FusedParams p) {
             sm.qb[jp] = fmaf(wb1, dq1, qf);
             sm.mb[jp] = fmaf(wb1, dm1, mf);
             sm.rb[jp] = fmaf(wb1, dr1, rf);
-            sm.Dh[jp] = fmaf(wb1, dh1n - dh1, f32_of(h1 - h0));
-            sm.Dq[jp] = fmaf(wb1, dq1n - dq1, f32_of(q1 - q0));
-            sm.Dm[jp] = fmaf(wb1, dm1n - dm1, f32_of(m1 - m0));
+            // differences of U^n at the face to the right: (hi1 - hi0) + (lo1 - lo0)
+            const float Dhn = __fadd_rn(__fsub_rn(h1.x, h0.x), __fsub_rn(h1.y, h0.y));
+            const float Dqn = __fadd_rn(__fsub_rn(q1.x, q0.x), __fsub_rn(q1.y, q0.y));
+            const float Dmn = __fadd_rn(__fsub_rn(m1.x, m0.x), __fsub_rn(m1.y, m0.y));
+            sm.Dh[jp] = fmaf(wb1, dh1n - dh1, Dhn);
+            sm.Dq[jp] = fmaf(wb1, dq1n - dq1, Dqn);
+            sm.Dm[jp] = fmaf(wb1, dm1n - dm1, Dmn);
         }
     }
     __syncthreads();
@@ -463,9 +502,13 @@ __global__ void __launch_bounds__(T, 4) k_mixed_fused(const FusedParams p) {
         const float dmc = (DmL + DmC) + (dmR - dmL);
         const float dQ = dqC - fqv * beC * dhc - lamv * fqv * deC * dmc;
         // base depth (rounded) and P0 = h_b^2 - m_b of this cell
-        const double h0 = U0[i], m0 = U2[i];
-        const float hf = f32_of(h0);
-        float hbf = hf, P0 = f32_of(fma(h0, h0, -m0));
+        const float2 h0 = U0[i], m0 = U2[i];
+        const float hf = h0.x;
+        // (h^2 - m)^n: hi^2 = p + e exactly; p - m.hi is exact for m close to h^2
+        const float pp = __fmul_rn(hf, hf);
+        const float pe = fmaf(hf, hf, -pp);
+        float hbf = hf;
+        float P0 = __fadd_rn(__fsub_rn(pp, m0.x), fmaf(2.f * hf, h0.y, __fsub_rn(pe, m0.y)));
         if (two) {
             const float dh1 = G1[i] - G1[i + 1], dm1 = p.dm1[i];
             hbf = fmaf(wb1, dh1, hf);
@@ -492,10 +535,12 @@ __global__ void __launch_bounds__(T, 4) k_mixed_fused(const FusedParams p) {
         } else {
             const float Tp = fmaf(wb1, G1[i + 1], Gp);
             const float Tm = fmaf(wb1, G1[i], Gm_);
-            p.out[0][i] = h0 - (f64_of(Tp) - f64_of(Tm));
-            p.out[1][i] = U1[i] + f64_of(fmaf(wb1, p.dq1[i], dQ));
-            p.out[2][i] = m0 + f64_of(fmaf(wb1, p.dm1[i], dM));
-            p.out[3][i] = U3[i] + f64_of(fmaf(wb1, p.dr1[i], dR));
+            float d, de;
+            two_sum(Tm, -Tp, d, de);  // exact Tm - Tp
+            p.out[0][i] = df_add(h0, d, de);
+            p.out[1][i] = df_add(U1[i], fmaf(wb1, p.dq1[i], dQ), 0.f);
+            p.out[2][i] = df_add(m0, fmaf(wb1, p.dm1[i], dM), 0.f);
+            p.out[3][i] = df_add(U3[i], fmaf(wb1, p.dr1[i], dR), 0.f);
             if (p.track_speed && !b2) umax = fmaxf(umax, fabsf((qbC + dQ) / hbar));
         }
     }
@@ -506,6 +551,56 @@ __global__ void __launch_bounds__(T, 4) k_mixed_fused(const FusedParams p) {
         if ((tid & 31) == 0 && umax > 0.f)
             atomicMax(reinterpret_cast<unsigned long long*>(p.speed_next),
                       (unsigned long long)__double_as_longlong(f64_of(umax)));
+    }
+}
+
+// State conversions of the windowed path (off the stepping path).
+__global__ void k_df_from_f64(int64_t n, const double* __restrict__ src, float2* __restrict__ dst) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        dst[i] = df_of(src[i]);
+}
+
+__global__ void k_f64_from_df(int64_t n, const float2* __restrict__ src, double* __restrict__ dst) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const float2 v = src[i];
+        dst[i] = (double)v.x + (double)v.y;  // exact: the pair has 48 significant bits
+    }
+}
+
+// k_speeds (hsgn_kernels.cuh) for a double-float state.
+__global__ void k_speeds_df(int64_t n, const float2* h, const float2* q, const float2* m, double g,
+                            double lam, double* out, unsigned* err) {
+    double um = 0.0, nm = 0.0;
+    bool bad = false;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const float2 hv = h[i], qv = q[i], mv = m[i];
+        const double hh = (double)hv.x + (double)hv.y;
+        if (!(hh > 0.0)) {
+            bad = true;
+            continue;
+        }
+        const double u = fabs(((double)qv.x + (double)qv.y) / hh);
+        const double e = ((double)mv.x + (double)mv.y) / (hh * hh);
+        const double nu = u + sqrt(g * hh + (lam / 3.0) * e * e);
+        um = fmax(um, u);
+        nm = fmax(nm, nu);
+    }
+    if (bad) flag_error(err, HSGN_DEV_ERR_DEPTH);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        um = fmax(um, __shfl_xor_sync(0xffffffffu, um, o));
+        nm = fmax(nm, __shfl_xor_sync(0xffffffffu, nm, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        if (um > 0.0)
+            atomicMax(reinterpret_cast<unsigned long long*>(out),
+                      (unsigned long long)__double_as_longlong(um));
+        if (nm > 0.0)
+            atomicMax(reinterpret_cast<unsigned long long*>(out + 1),
+                      (unsigned long long)__double_as_longlong(nm));
     }
 }
 

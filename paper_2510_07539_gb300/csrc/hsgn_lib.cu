@@ -421,8 +421,8 @@ cudaError_t launch_stage_fused(hsgn_s* H, int stage, double tau, cudaStream_t st
     double* const* Uc = state(H);
     double* const* Un = H->cur ? H->U : H->V;
     for (int k = 0; k < 4; ++k) {
-        p.U[k] = Uc[k];
-        p.out[k] = stage == 2 ? Un[k] : nullptr;
+        p.U[k] = reinterpret_cast<const float2*>(Uc[k]);
+        p.out[k] = stage == 2 ? reinterpret_cast<float2*>(Un[k]) : nullptr;
     }
     p.G1 = H->G1;
     p.dq1 = H->dq1;
@@ -482,6 +482,18 @@ int read_error(hsgn_s* H, cudaStream_t st) {
     return map_error_bits(bits);
 }
 
+// max |u| and max nu of the current state into out[0..1] (which must be zero).
+void launch_speeds(hsgn_s* H, double* out, cudaStream_t st) {
+    double* const* U = state(H);
+    if (H->windowed)
+        k_speeds_df<<<304, 256, 0, st>>>(H->n, reinterpret_cast<const float2*>(U[0]),
+                                         reinterpret_cast<const float2*>(U[1]),
+                                         reinterpret_cast<const float2*>(U[2]), H->g, H->lam, out,
+                                         H->err);
+    else
+        k_speeds<<<304, 256, 0, st>>>(H->n, U[0], U[1], U[2], H->g, H->lam, out, H->err);
+}
+
 // Recompute the global Rusanov speed max |u| of the current state.
 cudaError_t refresh_speed(hsgn_s* H, cudaStream_t st) {
     if (H->batched) {
@@ -492,8 +504,7 @@ cudaError_t refresh_speed(hsgn_s* H, cudaStream_t st) {
     double* out = speed_of(H, H->cur);
     cudaError_t e = cudaMemsetAsync(out, 0, 2 * sizeof(double), st);
     if (e != cudaSuccess) return e;
-    double* const* U = state(H);
-    k_speeds<<<304, 256, 0, st>>>(H->n, U[0], U[1], U[2], H->g, H->lam, out, H->err);
+    launch_speeds(H, out, st);
     return cudaGetLastError();
 }
 
@@ -673,10 +684,17 @@ int hsgn_set_state(hsgn_handle_t H, const double* depth, const double* q, const 
     if (!H || !depth || !q || !heta || !hw) return HSGN_ERR_INVALID_ARG;
     cudaStream_t st = as_stream(stream);
     const double* src[4] = {depth, q, heta, hw};
+    // the windowed path holds double-float pairs: stage through the idle buffer
+    double* const* dst = H->windowed ? (H->cur ? H->U : H->V) : state(H);
     for (int k = 0; k < 4; ++k)
-        if (cudaMemcpyAsync(state(H)[k], src[k], H->n * sizeof(double), cudaMemcpyDefault, st) !=
+        if (cudaMemcpyAsync(dst[k], src[k], H->n * sizeof(double), cudaMemcpyDefault, st) !=
             cudaSuccess)
             return HSGN_ERR_CUDA;
+    if (H->windowed) {
+        for (int k = 0; k < 4; ++k)
+            k_df_from_f64<<<1216, 256, 0, st>>>(H->n, dst[k], reinterpret_cast<float2*>(state(H)[k]));
+        if (cudaGetLastError() != cudaSuccess) return HSGN_ERR_CUDA;
+    }
     return refresh_speed(H, st) == cudaSuccess ? HSGN_OK : HSGN_ERR_CUDA;
 }
 
@@ -685,8 +703,16 @@ int hsgn_get_state(hsgn_handle_t H, double* depth, double* q, double* heta, doub
     if (!H || !depth || !q || !heta || !hw) return HSGN_ERR_INVALID_ARG;
     cudaStream_t st = as_stream(stream);
     double* dst[4] = {depth, q, heta, hw};
+    double* const* src = state(H);
+    if (H->windowed) {  // pairs to doubles in the idle buffer
+        double* const* tmp = H->cur ? H->U : H->V;
+        for (int k = 0; k < 4; ++k)
+            k_f64_from_df<<<1216, 256, 0, st>>>(H->n, reinterpret_cast<const float2*>(src[k]), tmp[k]);
+        if (cudaGetLastError() != cudaSuccess) return HSGN_ERR_CUDA;
+        src = tmp;
+    }
     for (int k = 0; k < 4; ++k)
-        if (cudaMemcpyAsync(dst[k], state(H)[k], H->n * sizeof(double), cudaMemcpyDefault, st) !=
+        if (cudaMemcpyAsync(dst[k], src[k], H->n * sizeof(double), cudaMemcpyDefault, st) !=
             cudaSuccess)
             return HSGN_ERR_CUDA;
     return read_error(H, st);
@@ -794,8 +820,7 @@ int hsgn_suggest_dt(hsgn_handle_t H, double cfl, double mcfl, double* dt_out, vo
     cudaStream_t st = as_stream(stream);
     double* tmp = H->spd + 2;
     if (cudaMemsetAsync(tmp, 0, 2 * sizeof(double), st) != cudaSuccess) return HSGN_ERR_CUDA;
-    double* const* U = state(H);
-    k_speeds<<<304, 256, 0, st>>>(H->n, U[0], U[1], U[2], H->g, H->lam, tmp, H->err);
+    launch_speeds(H, tmp, st);
     if (cudaGetLastError() != cudaSuccess) return HSGN_ERR_CUDA;
     double hv[2];
     if (cudaMemcpyAsync(hv, tmp, sizeof(hv), cudaMemcpyDeviceToHost, st) != cudaSuccess)
