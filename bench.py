@@ -69,6 +69,8 @@ def parse_args():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-fp64", action="store_true", help="skip the all-FP64 path")
+    ap.add_argument("--concurrent", action="store_true",
+                    help="run the instances of a step on one CUDA stream each")
     ap.add_argument("--batch", type=int, default=4096, help="instances of the batched workload")
     return ap.parse_args()
 
@@ -253,19 +255,25 @@ def sep_launches(n: int) -> int:
     return 1 if n <= 128 else 2 + sep_launches((n + 127) // 128)
 
 
-def time_path(S, torch, flags, n, xl, xr, lams, Ud, steps, warmup, flush, stream, dist, clocks):
+def time_path(S, torch, flags, n, xl, xr, lams, Ud, steps, warmup, flush, stream, dist, clocks,
+              concurrent=False):
     """K timed steps of the three-instance workload in one precision form."""
     sols = [S.Solver(n, xl, xr, S.BC_TRANSMISSIVE, lam=l, flags=flags) for l in lams]
     for s in sols:
         s.set_state(*Ud)
     dts = [s.suggest_dt(4.0, 0.5) for s in sols]
-    # the instances are independent: one CUDA stream each, forked from and
-    # joined back into the timing stream every step
+    # the instances are independent. Default: one after the other on the
+    # timing stream (each kernel's event pair then times that kernel alone);
+    # concurrent: one CUDA stream each, forked and joined every step
     side = [torch.cuda.Stream() for _ in sols]
     fork = torch.cuda.Event()
     joins = [torch.cuda.Event() for _ in sols]
 
     def one_step():
+        if not concurrent:
+            for s, dt in zip(sols, dts):
+                s.step(dt, stream=stream)
+            return
         fork.record(stream)
         for s, dt, st, j in zip(sols, dts, side, joins):
             st.wait_event(fork)
@@ -328,7 +336,8 @@ def time_fp64(S, torch, n, xl, xr, lams, Ud, args, flush, stream, dist, units_ra
               hbm_peak):
     """The all-FP64 path (exact separator solve) on the same workload."""
     fsols, fdts, fms, ftot, _ = time_path(S, torch, S.FLAG_FP64, n, xl, xr, lams, Ud,
-                                          args.steps, args.warmup, flush, stream, dist, None)
+                                          args.steps, args.warmup, flush, stream, dist, None,
+                                          args.concurrent)
     favg = ftot["assemble"][0] / max(ftot["assemble"][1], 1)
     ftf = FLOPS_PER_CELL_ASSEMBLE * n / (favg / 1e3) / 1e12
     fshare_den = sum(v[0] for v in ftot.values())
@@ -390,7 +399,7 @@ def run_ours(args):
     # ---- headline: mixed precision (FP32 increments, FP64 state)
     msols, mdts, mms, mtot, clocks = time_path(S, torch, S.FLAG_MIXED, n, xl, xr, lams, Ud,
                                               args.steps, args.warmup, flush, stream, dist,
-                                              gpu_id)
+                                              gpu_id, args.concurrent)
     value = units_rank * world / (mms / 1e3)
     avg_asm = mtot["assemble"][0] / max(mtot["assemble"][1], 1)
     stage_ms = mms / (2 * len(lams) * args.steps)

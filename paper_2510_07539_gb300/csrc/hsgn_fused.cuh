@@ -170,12 +170,18 @@ struct FusedGeom {
     static_assert(S > 0, "overlap too wide for the window");
 };
 
-// Shared memory. Arrays are reused once their phase is over:
-//   phase 0 writes hl, ql, ml, rl (U_l), qb, mb, rb (U_b), Dh, Dq, Dm (FP64
-//   differences of U_b at the face to the right of a cell, rounded);
-//   phase 1 writes the fluxes into ql (Fq), X0 (Fm), rl (Fr);
-//   phase 2 writes dq -> ql, dm -> X0, dr -> rl, beta -> hl, delta -> ml;
-//   the solve writes dh -> mb.
+// Single-precision reciprocal: the hardware approximation (hsgn_tridiag.cuh).
+__device__ __forceinline__ float rcpa(float x) { return rcp(x); }
+
+// Shared memory. Arrays are reused once their phase is over (cell c of the
+// window at index c+3 in the U arrays, c+1 in the per-cell arrays):
+//   phase 0: hl, ql, ml, rl (U_l), qb, mb, rb (U_b), Dh, Dq, Dm (differences
+//            of U_b at the face to the right of a cell);
+//   phase 1: fluxes Fq -> ql, Fm -> X0, Fr -> rl (face f at f+2);
+//   phase 2: dq -> ql, dm -> X0, dr -> rl, beta -> hl, delta -> ml;
+//   phase 3: rows: face couplings tau^2 beta_{f+1/2}/dx^2 -> rb, right-hand
+//            sides -> mb (both padded, read in the chunk mapping);
+//   phase 4: dh -> Dq (padded); face mass fluxes of the tile -> rb.
 template <int T, int M, int HW>
 struct FusedShared {
     static constexpr int NC = FusedGeom<T, M, HW>::NC;
@@ -211,7 +217,7 @@ __global__ void __launch_bounds__(T, 4) k_mixed_fused(const FusedParams p) {
     }
     if (p.track_speed && p.stage == 1 && blockIdx.x == 0 && tid == 0) *p.speed_next = 0.0;
 
-    // ---- 0. window cells -3 .. W+2 (smem index j = cell + 3); FP64 differences of U^n
+    // ---- 0. window cells -3 .. W+2 (index c + 3)
     constexpr int NL = (Gm::R + 6 + T - 1) / T;
     // windows away from the domain ends read cells wl-3 .. wl+W+3 directly
     const bool inner = wl - 3 >= 0 && wl + W + 3 <= n;
@@ -237,21 +243,20 @@ __global__ void __launch_bounds__(T, 4) k_mixed_fused(const FusedParams p) {
                 dh1n = g2 - g3;
             }
             const float hf = h0.x, qf = q0.x, mf = m0.x, rf = rr0.x;
-            const int jp = pd(j);
-            sm.hl[jp] = fmaf(wl1, dh1, hf);
-            sm.ql[jp] = fmaf(wl1, dq1, qf);
-            sm.ml[jp] = fmaf(wl1, dm1, mf);
-            sm.rl[jp] = fmaf(wl1, dr1, rf);
-            sm.qb[jp] = fmaf(wb1, dq1, qf);
-            sm.mb[jp] = fmaf(wb1, dm1, mf);
-            sm.rb[jp] = fmaf(wb1, dr1, rf);
+            sm.hl[j] = fmaf(wl1, dh1, hf);
+            sm.ql[j] = fmaf(wl1, dq1, qf);
+            sm.ml[j] = fmaf(wl1, dm1, mf);
+            sm.rl[j] = fmaf(wl1, dr1, rf);
+            sm.qb[j] = fmaf(wb1, dq1, qf);
+            sm.mb[j] = fmaf(wb1, dm1, mf);
+            sm.rb[j] = fmaf(wb1, dr1, rf);
             // differences of U^n at the face to the right: (hi1 - hi0) + (lo1 - lo0)
             const float Dhn = __fadd_rn(__fsub_rn(h1.x, h0.x), __fsub_rn(h1.y, h0.y));
             const float Dqn = __fadd_rn(__fsub_rn(q1.x, q0.x), __fsub_rn(q1.y, q0.y));
             const float Dmn = __fadd_rn(__fsub_rn(m1.x, m0.x), __fsub_rn(m1.y, m0.y));
-            sm.Dh[jp] = fmaf(wb1, dh1n - dh1, Dhn);
-            sm.Dq[jp] = fmaf(wb1, dq1n - dq1, Dqn);
-            sm.Dm[jp] = fmaf(wb1, dm1n - dm1, Dmn);
+            sm.Dh[j] = fmaf(wb1, dh1n - dh1, Dhn);
+            sm.Dq[j] = fmaf(wb1, dq1n - dq1, Dqn);
+            sm.Dm[j] = fmaf(wb1, dm1n - dm1, Dmn);
         }
     }
     __syncthreads();
@@ -260,7 +265,7 @@ __global__ void __launch_bounds__(T, 4) k_mixed_fused(const FusedParams p) {
     const float gspeed = p.local_speed ? 0.f : (float)(*p.speed);
     unsigned bad = 0;
 
-    // ---- 1. Rusanov fluxes of U_l at faces f = -2 .. W (index j = f + 2), Sec. 4.1.
+    // ---- 1. Rusanov fluxes of U_l at faces f = -2 .. W (index f + 2), Sec. 4.1.
     //         All reads of phase 0's ql / rl happen before the barrier, the
     //         flux stores (which reuse ql, rl) after it.
     constexpr int NF = (Gm::R + 3 + T - 1) / T;
@@ -270,17 +275,16 @@ __global__ void __launch_bounds__(T, 4) k_mixed_fused(const FusedParams p) {
         const int j = tid + it * T;
         fq_[it] = fm_[it] = fr_[it] = 0.f;
         if (j < W + 3) {
-            const int a0 = pd(j), a1 = pd(j + 1), a2 = pd(j + 2), a3 = pd(j + 3);
-            const float hm = sm.hl[a0], h0 = sm.hl[a1], h1 = sm.hl[a2], h2 = sm.hl[a3];
-            const float qm = sm.ql[a0], q0 = sm.ql[a1], q1 = sm.ql[a2], q2 = sm.ql[a3];
-            const float mm = sm.ml[a0], m0 = sm.ml[a1], m1 = sm.ml[a2], m2 = sm.ml[a3];
-            const float rm = sm.rl[a0], r0_ = sm.rl[a1], r1 = sm.rl[a2], r2 = sm.rl[a3];
+            const float hm = sm.hl[j], h0 = sm.hl[j + 1], h1 = sm.hl[j + 2], h2 = sm.hl[j + 3];
+            const float qm = sm.ql[j], q0 = sm.ql[j + 1], q1 = sm.ql[j + 2], q2 = sm.ql[j + 3];
+            const float mm = sm.ml[j], m0 = sm.ml[j + 1], m1 = sm.ml[j + 2], m2 = sm.ml[j + 3];
+            const float rm = sm.rl[j], r0_ = sm.rl[j + 1], r1 = sm.rl[j + 2], r2 = sm.rl[j + 3];
             const float hL = fmaf(0.25f, h1 - hm, h0), hR = fmaf(-0.25f, h2 - h0, h1);
             const float qL = fmaf(0.25f, q1 - qm, q0), qR = fmaf(-0.25f, q2 - q0, q1);
             const float mL = fmaf(0.25f, m1 - mm, m0), mR = fmaf(-0.25f, m2 - m0, m1);
             const float rL = fmaf(0.25f, r1 - rm, r0_), rR = fmaf(-0.25f, r2 - r0_, r1);
-            if (!pos_finite(hL) || !pos_finite(hR)) bad |= HSGN_DEV_ERR_DEPTH;
-            const float ip = __frcp_rn(hL * hR);
+            if (!pos_finite(fminf(hL, hR))) bad |= HSGN_DEV_ERR_DEPTH;
+            const float ip = rcpa(hL * hR);
             const float uL = qL * hR * ip, uR = qR * hL * ip;
             const float s = p.local_speed ? fmaxf(fabsf(uL), fabsf(uR)) : gspeed;
             fq_[it] = 0.5f * (fmaf(uL, qL, uR * qR) - s * (qR - qL));
@@ -303,7 +307,7 @@ __global__ void __launch_bounds__(T, 4) k_mixed_fused(const FusedParams p) {
     }
     __syncthreads();
 
-    // ---- 2. increments and coefficients at cells c = -1 .. W (index j = c + 1):
+    // ---- 2. increments and coefficients at cells c = -1 .. W (index c + 1):
     //         r^dag = r_b + dr' + lambda tau, m^dag = m_b + dm' + lambda tau^2, q^dag = q_b + dq
     constexpr int NCL = (Gm::R + 2 + T - 1) / T;
     const float lt2 = p.lt2, tdx = p.tdx, Cc = p.Cc;
@@ -314,7 +318,7 @@ __global__ void __launch_bounds__(T, 4) k_mixed_fused(const FusedParams p) {
         const int j = tid + it * T;
         dq_[it] = dm_[it] = dr_[it] = be_[it] = de_[it] = 0.f;
         if (j < W + 2) {
-            const int c3 = pd(j + 2);
+            const int c3 = j + 2;
             const float drv = -tdx * (Fr[j + 1] - Fr[j]);
             const float dmv = fmaf(tau, sm.rb[c3] + drv, -tdx * (Fm[j + 1] - Fm[j]));
             const float dqv = -tdx * (Fq[j + 1] - Fq[j]);
@@ -322,7 +326,7 @@ __global__ void __launch_bounds__(T, 4) k_mixed_fused(const FusedParams p) {
             const float h = sm.hl[c3];
             if (!pos_finite(h)) bad |= HSGN_DEV_ERR_DEPTH;
             const float Dh_ = fmaf(h, h, lt2);
-            const float Rr = __frcp_rn(h * Dh_);
+            const float Rr = rcpa(h * Dh_);
             const float ih = Dh_ * Rr;
             const float iD = h * Rr;
             const float eta = sm.ml[c3] * ih;
@@ -353,53 +357,69 @@ __global__ void __launch_bounds__(T, 4) k_mixed_fused(const FusedParams p) {
     for (int it = 0; it < NCL; ++it) {
         const int j = tid + it * T;
         if (j < W + 2) {
-            const int jp = pd(j);
-            dqa[jp] = dq_[it];
-            dma[jp] = dm_[it];
-            dra[jp] = dr_[it];
-            bea[jp] = be_[it];
-            dea[jp] = de_[it];
+            dqa[j] = dq_[it];
+            dma[j] = dm_[it];
+            dra[j] = dr_[it];
+            bea[j] = be_[it];
+            dea[j] = de_[it];
         }
     }
-    if (pos_finite(kloc)) atomicMax(&sm.kmax, __float_as_uint(kloc));
-    if (pos_finite(kmin)) atomicMin(&sm.kmin, __float_as_uint(kmin));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        kloc = fmaxf(kloc, __shfl_xor_sync(0xffffffffu, kloc, o));
+        kmin = fminf(kmin, __shfl_xor_sync(0xffffffffu, kmin, o));
+    }
+    if ((tid & 31) == 0) {
+        if (pos_finite(kloc)) atomicMax(&sm.kmax, __float_as_uint(kloc));
+        if (pos_finite(kmin)) atomicMin(&sm.kmin, __float_as_uint(kmin));
+    }
     __syncthreads();
     if (BC == BC_TRANSMISSIVE && tid == 0) {
         // zero-order ghost copies at the domain ends
         if (win.lend) {
-            const int a = pd(0), c = pd(1);
-            dqa[a] = dqa[c]; dma[a] = dma[c]; dra[a] = dra[c]; bea[a] = bea[c]; dea[a] = dea[c];
+            dqa[0] = dqa[1]; dma[0] = dma[1]; dra[0] = dra[1]; bea[0] = bea[1]; dea[0] = dea[1];
         }
         if (win.rend) {
-            const int a = pd(W + 1), c = pd(W);
+            const int a = W + 1, c = W;
             dqa[a] = dqa[c]; dma[a] = dma[c]; dra[a] = dra[c]; bea[a] = bea[c]; dea[a] = dea[c];
         }
     }
     __syncthreads();
 
-    // ---- 3. rows of A dh = d - A h_b (window row i; face i+1/2 at index i+3),
-    //         with the coupling across a truncated edge dropped
+    // ---- 3. rows of A dh = d - A h_b: face couplings k_f = tau^2/dx^2 beta_{f+1/2}
+    //         (f = -1 .. W-1, at pd(f+1); zero across a transmissive domain end,
+    //         which makes the end rows the Neumann rows) and right-hand sides d_i
+    //         (i = 0 .. W-1, at pd(i)); cell c of the per-cell arrays at c+1,
+    //         the face right of cell c of the difference arrays at c+3
     const float fq = p.fq, fd = p.fd;
-    auto row_at = [&](int i, bool cutL, bool cutR, float& a, float& bb, float& c, float& d) {
-        const int c0 = pd(i), c1 = pd(i + 1), c2 = pd(i + 2), f2 = pd(i + 2), f3 = pd(i + 3);
-        const float bm = 0.5f * (bea[c0] + bea[c1]);
-        const float bp = 0.5f * (bea[c1] + bea[c2]);
-        const float dmn = 0.5f * (dea[c0] + dea[c1]);
-        const float dpl = 0.5f * (dea[c1] + dea[c2]);
-        const float dqc = sm.Dq[f2] + sm.Dq[f3] + (dqa[c2] - dqa[c0]);
-        const float dmp = sm.Dm[f3] + (dma[c2] - dma[c1]);
-        const float dmm = sm.Dm[f2] + (dma[c1] - dma[c0]);
-        d = -fq * dqc + fd * (dpl * dmp - dmn * dmm) - Cc * (bm * sm.Dh[f2] - bp * sm.Dh[f3]);
-        a = -Cc * bm;
-        c = -Cc * bp;
-        bb = fmaf(Cc, bm + bp, 1.f);
-        if (BC == BC_TRANSMISSIVE) {
-            const int64_t gi = wl + i;
-            if (gi == 0) { bb = fmaf(Cc, bp, 1.f); a = 0.f; }
-            if (gi == n - 1) { bb = fmaf(Cc, bm, 1.f); c = 0.f; }
+    float* const BF = sm.rb;
+    float* const RD = sm.mb;
+    for (int j = tid; j < W + 1; j += T) {
+        const int f = j - 1;  // face between window rows f and f+1
+        float kf = Cc * (0.5f * (bea[f + 1] + bea[f + 2]));
+        if (BC == BC_TRANSMISSIVE && ((f < 0 && win.lend) || (f == W - 1 && win.rend))) kf = 0.f;
+        BF[pd(j)] = kf;
+        if (j < W) {
+            const int i = j;
+            const float bm = 0.5f * (bea[i] + bea[i + 1]);
+            const float bp = 0.5f * (bea[i + 1] + bea[i + 2]);
+            const float dmn = 0.5f * (dea[i] + dea[i + 1]);
+            const float dpl = 0.5f * (dea[i + 1] + dea[i + 2]);
+            const float dqc = sm.Dq[i + 2] + sm.Dq[i + 3] + (dqa[i + 2] - dqa[i]);
+            const float dmp = sm.Dm[i + 3] + (dma[i + 2] - dma[i + 1]);
+            const float dmm = sm.Dm[i + 2] + (dma[i + 1] - dma[i]);
+            RD[pd(i)] = -fq * dqc + fd * (dpl * dmp - dmn * dmm) -
+                        Cc * (bm * sm.Dh[i + 2] - bp * sm.Dh[i + 3]);
         }
-        if (cutL) a = 0.f;
-        if (cutR) c = 0.f;
+    }
+    __syncthreads();
+    // row i of a window whose first / last row drops its outer coupling
+    auto row_at = [&](int i, bool cutL, bool cutR, float& a, float& bb, float& c, float& d) {
+        const float kl = BF[pd(i)], kr = BF[pd(i + 1)];
+        a = cutL ? 0.f : -kl;
+        c = cutR ? 0.f : -kr;
+        bb = 1.f + kl + kr;
+        d = RD[pd(i)];
     };
     // tile-boundary mini solves (warps 1 and 2, while warp 0 solves the
     // separator system of the window)
@@ -431,6 +451,7 @@ __global__ void __launch_bounds__(T, 4) k_mixed_fused(const FusedParams p) {
             }
         }
     };
+    float* const dha = sm.Dq;  // dh of window row r at pd(r + 1), r = -1 .. W
     {
         auto roww = [&](int i, float& a, float& bb, float& c, float& d) {
             if (i >= W) {  // identity row closing the window
@@ -445,15 +466,13 @@ __global__ void __launch_bounds__(T, 4) k_mixed_fused(const FusedParams p) {
         // dh = y: the values outside the window (and the closing row) are taken as 0
 #pragma unroll
         for (int k = 0; k < M; ++k)
-            if (k < m && cs + k < W) sm.mb[pd(cs + k + 1)] = y[k];
+            if (k < m && cs + k < W) dha[pd(cs + k + 1)] = y[k];
     }
     __syncthreads();
-    float* const dha = sm.mb;  // dh of window row r at pd(r + 1), r = -1 .. W
     if (BC == BC_TRANSMISSIVE && tid == 0) {
         if (win.lend) dha[pd(0)] = dha[pd(1)];
         if (win.rend) dha[pd(W + 1)] = dha[pd(W)];
     }
-    __syncthreads();
 
     // truncation bound of this window: rho*^HB <= 2^-30
     if (tid == 0) {
@@ -465,42 +484,49 @@ __global__ void __launch_bounds__(T, 4) k_mixed_fused(const FusedParams p) {
             if ((float)Gm::HB * __log2f(rho) > -30.f) bad |= HSGN_DEV_ERR_TRUNCATION;
         }
     }
+    __syncthreads();
 
-    // ---- 4. back-substitution of the tile rows
-    const float fqv = fq, fdv = fd, lamv = lam;
-    auto face_G = [&](float qbL, float qbR, float dqL, float dqR, float dmL, float dmR, float dhL,
-                      float dhR, float deL, float deR, float beL, float beR, float DmL, float DhL) {
-        const float qsum = (qbL + qbR) + (dqL + dqR);
-        const float dmf = DmL + (dmR - dmL);
-        const float dhf = DhL + (dhR - dhL);
-        return fqv * qsum - fdv * (0.5f * (deL + deR)) * dmf - Cc * (0.5f * (beL + beR)) * dhf;
-    };
+    // ---- 4a. face mass fluxes (divided by dx) of the tile's faces f = lo-1 .. lo+sp-1,
+    //          each evaluated once; at a tile face both rows come from the shared
+    //          mini solve
+    //   G = tau/(2dx) (q^dag_L + q^dag_R) - lambda tau^2/dx^2 delta_face (m^dag_R - m^dag_L)
+    //       - tau^2/dx^2 beta_face (hbar_R - hbar_L)
+    const int lo = win.lo, sp = win.sp;
+    float* const Gt = sm.rb;  // face f at f - lo + 1
+    for (int j = tid; j < sp + 1; j += T) {
+        const int f = lo - 1 + j;  // face between window cells f and f+1
+        float dL = dha[pd(f + 1)], dR = dha[pd(f + 2)];
+        if (j == 0 && lface) { dL = sm.bnd[0][0]; dR = sm.bnd[0][1]; }
+        if (j == sp && rface) { dL = sm.bnd[1][0]; dR = sm.bnd[1][1]; }
+        const float qsum = (sm.qb[f + 3] + sm.qb[f + 4]) + (dqa[f + 1] + dqa[f + 2]);
+        const float dmf = sm.Dm[f + 3] + (dma[f + 2] - dma[f + 1]);
+        const float dhf = sm.Dh[f + 3] + (dR - dL);
+        const float G = fq * qsum - fd * (0.5f * (dea[f + 1] + dea[f + 2])) * dmf -
+                        Cc * (0.5f * (bea[f + 1] + bea[f + 2])) * dhf;
+        if (!isfinite(G)) bad |= HSGN_DEV_ERR_NONFINITE;
+        Gt[j] = G;
+        if (!two) {
+            const int64_t gf = win.t0 + j;  // G1 index of this face (face i+1/2 at i+1)
+            if (j > 0 || win.t0 == 0) p.G1[gf] = G;
+        }
+    }
+    __syncthreads();
+
+    // ---- 4b. back-substitution of the tile rows
+    const float lamv = lam;
     float umax = 0.f;
-    for (int t = tid; t < win.sp; t += T) {
-        const int r = win.lo + t;       // window row
-        const int64_t i = win.t0 + t;   // global row (in range)
-        const int cL = pd(r), cC = pd(r + 1), cR = pd(r + 2);   // cell arrays (cell c at c+1)
-        const int uL = pd(r + 2), uC = pd(r + 3), uR = pd(r + 4);  // U arrays (cell c at c+3)
-        const float dhC = dha[cC];
-        float dhL = dha[cL], dhR = dha[cR];
-        const float qbC = sm.qb[uC], qbL = sm.qb[uL], qbR = sm.qb[uR];
-        const float dqC = dqa[cC], dqL = dqa[cL], dqR = dqa[cR];
-        const float dmC = dma[cC], dmL = dma[cL], dmR = dma[cR];
-        const float beC = bea[cC], beL = bea[cL], beR = bea[cR];
-        const float deC = dea[cC], deL = dea[cL], deR = dea[cR];
-        const float DhL = sm.Dh[uL], DhC = sm.Dh[uC];  // faces r-1/2, r+1/2
-        const float DmL = sm.Dm[uL], DmC = sm.Dm[uC];
-        // face fluxes; at a tile face both rows come from the shared mini solve
-        float aL = dhL, aC = dhC;
-        if (t == 0 && lface) { aL = sm.bnd[0][0]; aC = sm.bnd[0][1]; }
-        const float Gm_ = face_G(qbL, qbC, dqL, dqC, dmL, dmC, aL, aC, deL, deC, beL, beC, DmL, DhL);
-        float bC = dhC, bR = dhR;
-        if (t == win.sp - 1 && rface) { bC = sm.bnd[1][0]; bR = sm.bnd[1][1]; }
-        const float Gp = face_G(qbC, qbR, dqC, dqR, dmC, dmR, bC, bR, deC, deR, beC, beR, DmC, DhC);
+    for (int t = tid; t < sp; t += T) {
+        const int r = lo + t;            // window row
+        const int64_t i = win.t0 + t;    // global row (in range)
+        const float dhL = dha[pd(r)], dhC = dha[pd(r + 1)], dhR = dha[pd(r + 2)];
+        const float dqC = dqa[r + 1], dmL = dma[r], dmC = dma[r + 1], dmR = dma[r + 2];
+        const float beC = bea[r + 1], deC = dea[r + 1];
+        const float DhL = sm.Dh[r + 2], DhC = sm.Dh[r + 3];  // faces r-1/2, r+1/2
+        const float DmL = sm.Dm[r + 2], DmC = sm.Dm[r + 3];
         // q: tau/(2dx) beta (hbar_{i+1} - hbar_{i-1}), lambda tau/(2dx) delta (m^dag_{i+1} - m^dag_{i-1})
         const float dhc = (DhL + DhC) + (dhR - dhL);
         const float dmc = (DmL + DmC) + (dmR - dmL);
-        const float dQ = dqC - fqv * beC * dhc - lamv * fqv * deC * dmc;
+        const float dQ = dqC - fq * beC * dhc - lamv * fq * deC * dmc;
         // base depth (rounded) and P0 = h_b^2 - m_b of this cell
         const float2 h0 = U0[i], m0 = U2[i];
         const float hf = h0.x;
@@ -509,39 +535,39 @@ __global__ void __launch_bounds__(T, 4) k_mixed_fused(const FusedParams p) {
         const float pe = fmaf(hf, hf, -pp);
         float hbf = hf;
         float P0 = __fadd_rn(__fsub_rn(pp, m0.x), fmaf(2.f * hf, h0.y, __fsub_rn(pe, m0.y)));
+        float g1l = 0.f, g1r = 0.f;
         if (two) {
-            const float dh1 = G1[i] - G1[i + 1], dm1 = p.dm1[i];
+            g1l = G1[i];
+            g1r = G1[i + 1];
+            const float dh1 = g1l - g1r, dm1 = p.dm1[i];
             hbf = fmaf(wb1, dh1, hf);
             P0 = fmaf(wb1, fmaf(dh1, fmaf(wb1, dh1, 2.f * hf), -dm1), P0);
         }
         const float hbar = hbf + dhC;
         const float P = fmaf(dhC, 2.f * hbf + dhC, P0);  // hbar^2 - m_b
-        const float E = P - dmC;                                  // hbar^2 - m^
+        const float E = P - dmC;                          // hbar^2 - m^
         const float h2 = hbar * hbar;
-        const float iDen = __frcp_rn(h2 + p.lt2);
-        const float dR = fmaf(p.ltau * E, iDen, dra[cC]);
+        const float iDen = rcpa(h2 + p.lt2);
+        const float dR = fmaf(p.ltau * E, iDen, dra[r + 1]);
         const float dM = P - E * h2 * iDen;
         unsigned b2 = 0;
         if (!pos_finite(hbar)) b2 |= HSGN_DEV_ERR_DEPTH;
-        if (!isfinite(Gp) || !isfinite(Gm_) || !isfinite(dQ) || !isfinite(dM) || !isfinite(dR))
-            b2 |= HSGN_DEV_ERR_NONFINITE;
+        if (!isfinite(dQ) || !isfinite(dM) || !isfinite(dR)) b2 |= HSGN_DEV_ERR_NONFINITE;
         bad |= b2;
         if (!two) {
-            p.G1[i + 1] = Gp;
-            if (i == 0) p.G1[0] = Gm_;
             p.dq1[i] = dQ;
             p.dm1[i] = dM;
             p.dr1[i] = dR;
         } else {
-            const float Tp = fmaf(wb1, G1[i + 1], Gp);
-            const float Tm = fmaf(wb1, G1[i], Gm_);
+            const float Tp = fmaf(wb1, g1r, Gt[t + 1]);
+            const float Tm = fmaf(wb1, g1l, Gt[t]);
             float d, de;
             two_sum(Tm, -Tp, d, de);  // exact Tm - Tp
             p.out[0][i] = df_add(h0, d, de);
             p.out[1][i] = df_add(U1[i], fmaf(wb1, p.dq1[i], dQ), 0.f);
             p.out[2][i] = df_add(m0, fmaf(wb1, p.dm1[i], dM), 0.f);
             p.out[3][i] = df_add(U3[i], fmaf(wb1, p.dr1[i], dR), 0.f);
-            if (p.track_speed && !b2) umax = fmaxf(umax, fabsf((qbC + dQ) / hbar));
+            if (p.track_speed && !b2) umax = fmaxf(umax, fabsf((sm.qb[r + 3] + dQ) / hbar));
         }
     }
     if (bad) flag_error(p.err, bad);
