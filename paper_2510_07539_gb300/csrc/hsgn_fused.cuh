@@ -27,11 +27,12 @@
 //    HSGN_DEV_ERR_TRUNCATION when rho*^HB > 2^-30 (the single-precision
 //    increments themselves carry 2^-24). For a uniform state rho* is the decay
 //    rate of the inverse, about 0.55 at CFL_IMEX = 4.
-//  * Mass: the face flux at a tile boundary is used by the two CTAs on either
-//    side. Both solve the same mini-window of 2 HB rows centred on that face
-//    with the same code path and evaluate the face flux from it, so the two
-//    values are bitwise equal and the flux-form depth update stays
-//    conservative to FP64 rounding.
+//  * Mass: in stage 2 the face flux at a tile boundary is used by the two CTAs
+//    on either side. Both solve the same mini-window of 2 HB rows centred on
+//    that face with the same code path and evaluate the face flux from it, so
+//    the two values are bitwise equal and the flux-form depth update stays
+//    conservative. Stage 1 updates no depth: each face of G1 is written once,
+//    by the tile on its left (periodic face -1/2 is read as face n-1/2).
 //  * Stage 2 cannot update U in place (the windows of neighbouring tiles still
 //    read U^n), so it writes U^{n+1} to a second state buffer.
 //  * The state is held as double-float pairs x = hi + lo (hi = x rounded to
@@ -59,14 +60,15 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
     e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
 }
 
-// (hi, lo) + (x + y) with x + y given exactly as two floats; renormalised.
+// (hi, lo) + (x + y) with x + y given exactly as two floats; renormalised by
+// Dekker's FastTwoSum (hi' = s + e rounded is exact to rounding whatever the
+// ordering; lo' loses accuracy only where the pair's lowest bits do not matter).
 __device__ __forceinline__ float2 df_add(float2 a, float x, float y) {
     float s, e;
     two_sum(a.x, x, s, e);
     e = __fadd_rn(e, __fadd_rn(a.y, y));
-    float h, l;
-    two_sum(s, e, h, l);
-    return make_float2(h, l);
+    const float h = __fadd_rn(s, e);
+    return make_float2(h, __fsub_rn(e, __fsub_rn(h, s)));
 }
 
 // Pair of a double (state conversion, off the stepping path).
@@ -211,6 +213,9 @@ __global__ void __launch_bounds__(T, 4) k_mixed_fused(const FusedParams p) {
     const float2* __restrict__ U2 = p.U[2];
     const float2* __restrict__ U3 = p.U[3];
     const float* __restrict__ G1 = p.G1;
+    // G1 index of the face left of cell i: periodic face -1/2 is face n-1/2,
+    // which only the last tile writes
+    auto lf = [&](int64_t i) { return (BC == BC_PERIODIC && i == 0) ? n : i; };
     if (tid == 0) {
         sm.kmax = 0u;
         sm.kmin = 0x7F7FFFFFu;
@@ -232,8 +237,8 @@ __global__ void __launch_bounds__(T, 4) k_mixed_fused(const FusedParams p) {
             const float2 h1 = __ldg(U0 + gn), q1 = __ldg(U1 + gn), m1 = __ldg(U2 + gn);
             float dh1 = 0.f, dq1 = 0.f, dm1 = 0.f, dr1 = 0.f, dh1n = 0.f, dq1n = 0.f, dm1n = 0.f;
             if (two) {
-                const float g0 = __ldg(G1 + gi), g1 = __ldg(G1 + gi + 1);
-                const float g2 = __ldg(G1 + gn), g3 = __ldg(G1 + gn + 1);
+                const float g0 = __ldg(G1 + lf(gi)), g1 = __ldg(G1 + gi + 1);
+                const float g2 = __ldg(G1 + lf(gn)), g3 = __ldg(G1 + gn + 1);
                 dq1 = __ldg(p.dq1 + gi);
                 dm1 = __ldg(p.dm1 + gi);
                 dr1 = __ldg(p.dr1 + gi);
@@ -423,8 +428,10 @@ __global__ void __launch_bounds__(T, 4) k_mixed_fused(const FusedParams p) {
     };
     // tile-boundary mini solves (warps 1 and 2, while warp 0 solves the
     // separator system of the window)
-    const bool lface = !(BC == BC_TRANSMISSIVE && win.t0 == 0);
-    const bool rface = !(BC == BC_TRANSMISSIVE && win.t0 + win.sp == n);
+    // (stage 2 only: stage 1 writes every face of G1 once, from the tile on
+    // its left, and updates no depth)
+    const bool lface = two && !(BC == BC_TRANSMISSIVE && win.t0 == 0);
+    const bool rface = two && !(BC == BC_TRANSMISSIVE && win.t0 + win.sp == n);
     auto mini = [&](int wid) {
         const int side = wid - 1;
         if (side < 0 || side > 1 || !(side == 0 ? lface : rface)) return;
@@ -507,7 +514,7 @@ __global__ void __launch_bounds__(T, 4) k_mixed_fused(const FusedParams p) {
         Gt[j] = G;
         if (!two) {
             const int64_t gf = win.t0 + j;  // G1 index of this face (face i+1/2 at i+1)
-            if (j > 0 || win.t0 == 0) p.G1[gf] = G;
+            if (j > 0 || (BC == BC_TRANSMISSIVE && win.t0 == 0)) p.G1[gf] = G;
         }
     }
     __syncthreads();
@@ -537,7 +544,7 @@ __global__ void __launch_bounds__(T, 4) k_mixed_fused(const FusedParams p) {
         float P0 = __fadd_rn(__fsub_rn(pp, m0.x), fmaf(2.f * hf, h0.y, __fsub_rn(pe, m0.y)));
         float g1l = 0.f, g1r = 0.f;
         if (two) {
-            g1l = G1[i];
+            g1l = G1[lf(i)];
             g1r = G1[i + 1];
             const float dh1 = g1l - g1r, dm1 = p.dm1[i];
             hbf = fmaf(wb1, dh1, hf);
