@@ -29,6 +29,9 @@ _lib = None
 BC_PERIODIC = 0
 BC_TRANSMISSIVE = 1
 
+# time-stepping schemes of run/step (see hsgn_oracle.c)
+SCHEME_PRINTED, SCHEME_ARS222, SCHEME_SI1, SCHEME_EX_HEUN, SCHEME_EX_EULER = 0, 1, 2, 3, 4
+
 ERRORS = {
     0: "ok",
     1: "invalid argument",
@@ -57,6 +60,8 @@ class _Params(ctypes.Structure):
         ("form", ctypes.c_int32),
         ("speed", ctypes.c_double),
         ("bathy", ctypes.POINTER(ctypes.c_double)),
+        ("recon", ctypes.c_int32),
+        ("scheme", ctypes.c_int32),
     ]
 
 
@@ -87,10 +92,14 @@ def _load():
         lib.oracle_run.argtypes = [ctypes.POINTER(_Params)] + [P] * 4 + [ctypes.c_double,
                                                                          ctypes.c_int64]
         lib.oracle_imex_scalar.argtypes = [ctypes.c_double] * 4 + [ctypes.c_int64, P]
+        lib.oracle_imex_scalar_scheme.argtypes = ([ctypes.c_int32] + [ctypes.c_double] * 4
+                                                  + [ctypes.c_int64, P])
+        lib.oracle_explicit_rhs.argtypes = [ctypes.POINTER(_Params)] + [P] * 8
         lib.oracle_suggest_dt.argtypes = ([ctypes.POINTER(_Params)] + [P] * 3
                                           + [ctypes.c_double] * 2 + [P] * 3)
         for f in ("oracle_tridiag_solve", "oracle_stage", "oracle_assemble", "oracle_run",
-                  "oracle_imex_scalar", "oracle_suggest_dt"):
+                  "oracle_imex_scalar", "oracle_imex_scalar_scheme", "oracle_explicit_rhs",
+                  "oracle_suggest_dt"):
             getattr(lib, f).restype = ctypes.c_int
         _lib = lib
     return _lib
@@ -116,17 +125,18 @@ class Params:
     """Grid and physics of one hSGN instance (uniform 1D grid of n cells)."""
 
     def __init__(self, n, dx, bc=BC_PERIODIC, g=9.81, lam=100.0, delta_half=False,
-                 rusanov=1, speed=0.0, form=0, bathy=None):
+                 rusanov=1, speed=0.0, form=0, bathy=None, recon=1, scheme=0):
         self.n, self.dx, self.bc, self.g, self.lam = int(n), float(dx), int(bc), float(g), float(lam)
         self.delta_half = bool(delta_half)
         self.rusanov, self.speed = int(rusanov), float(speed)
         self.form = int(form)
         self.bathy = None if bathy is None else _f64(bathy, self.n)
+        self.recon, self.scheme = int(recon), int(scheme)
 
     def _c(self) -> _Params:
         bp = _ptr(self.bathy) if self.bathy is not None else None
         return _Params(self.n, self.dx, self.bc, int(self.delta_half), self.g, self.lam,
-                       self.rusanov, self.form, self.speed, bp)
+                       self.rusanov, self.form, self.speed, bp, self.recon, self.scheme)
 
 
 def tridiag_solve(a, b, c, d, periodic: bool) -> np.ndarray:
@@ -177,11 +187,25 @@ def step(p: Params, U, dt: float):
     return run(p, U, dt, 1)
 
 
-def imex_scalar(aE: float, aI: float, y: float, dt: float, n_steps: int = 1) -> float:
+def imex_scalar(aE: float, aI: float, y: float, dt: float, n_steps: int = 1,
+                scheme: int = 0) -> float:
+    """Steps of y' = aE y + aI y (aE explicit, aI implicit) with scheme `scheme`."""
     out = ctypes.c_double()
-    _check(_load().oracle_imex_scalar(float(aE), float(aI), float(y), float(dt), int(n_steps),
-                                      ctypes.byref(out)), "imex_scalar")
+    _check(_load().oracle_imex_scalar_scheme(int(scheme), float(aE), float(aI), float(y),
+                                             float(dt), int(n_steps), ctypes.byref(out)),
+           "imex_scalar")
     return out.value
+
+
+def explicit_rhs(p: Params, U):
+    """Right-hand side L(U) of the explicit hSGN scheme (Sec. 4.4), 4 arrays."""
+    n = p.n
+    u = [_f64(v, n) for v in U]
+    out = [np.empty(n) for _ in range(4)]
+    pc = p._c()
+    _check(_load().oracle_explicit_rhs(ctypes.byref(pc), *map(_ptr, u), *map(_ptr, out)),
+           "explicit_rhs")
+    return out
 
 
 def suggest_dt(p: Params, U, cfl: float, mcfl: float):

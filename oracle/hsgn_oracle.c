@@ -74,6 +74,15 @@
  *                          diagonal dominance
  *   oracle_suggest_dt      the CFL_SW / CFL_IMEX ratios printed for the
  *                          Gaussian-bell test (Sec. 6.1)
+ *   oracle_explicit_rhs    the continuous hSGN right-hand side differentiated
+ *                          spectrally (second-order consistency, first order
+ *                          without reconstruction), zero at rest, mass
+ *   oracle_run schemes     ARS(2,2,2) against its double tableau on the
+ *                          scalar split equation; SI1 / Euler / Heun against
+ *                          their one-line definitions; temporal orders 2, 1,
+ *                          2, 1 on hSGN; dispersion relation and solitary
+ *                          wave at second order (ARS(2,2,2), Heun); mass and
+ *                          constant states for every scheme
  */
 #include <math.h>
 #include <stdint.h>
@@ -101,7 +110,24 @@ typedef struct {
     int32_t form;       /* 0: the printed flat-bottom scheme; 1: well-balanced form (R7) */
     double speed;       /* global Rusanov speed of the current step (rusanov == 1) */
     const double* bathy; /* bottom b per cell (form 1; NULL = flat) */
+    int32_t recon;      /* 1: centred linear reconstruction (Sec. 4.1); 0: none (first order) */
+    int32_t scheme;     /* time stepping of oracle_run, see ORACLE_SCHEME_* */
 } oracle_params;
+
+/* Time-stepping schemes of oracle_run (the first is the method of the paper;
+ * the others are the comparisons it reports or names):
+ *   PRINTED  the two-stage IMEX tableau of Sec. 3.2, eq. (tableau) (R1)
+ *   ARS222   the three-stage Ascher-Ruuth-Spiteri ARS(2,2,2) double tableau
+ *            (explicit first stage), in the generic stage form of Sec. 3.2
+ *   SI1      first-order semi-implicit: one stage with tau = dt
+ *            (eq. (GN_hyp_eq_semi_fully_discrete) as printed)
+ *   EX_HEUN  explicit hSGN, eq. (GN_hyp_eq_explicit), with Heun's method
+ *   EX_EULER explicit hSGN, eq. (GN_hyp_eq_explicit), forward Euler */
+#define ORACLE_SCHEME_PRINTED 0
+#define ORACLE_SCHEME_ARS222 1
+#define ORACLE_SCHEME_SI1 2
+#define ORACLE_SCHEME_EX_HEUN 3
+#define ORACLE_SCHEME_EX_EULER 4
 
 /* Neighbour index: wrap (periodic) or clamp to the boundary cell
  * (transmissive, zero-order ghost copies, reading R6). */
@@ -220,6 +246,43 @@ typedef struct {
 
 static double sqr(double x) { return x * x; }
 
+/* ------------------------------------------------------------------------
+ * Rusanov fluxes of hu^2, hu eta, hu w at every face (Sec. 4.1, hat D_x),
+ * shared by the semi-implicit stage and the explicit scheme. Index k + 1
+ * holds the face between cells k and k+1, k = -1 .. n-1. With p->recon the
+ * conserved variables are reconstructed by the unlimited centred slope,
+ *   v^L_{k+1/2} = v_k + (v_{k+1} - v_{k-1})/4,
+ *   v^R_{k+1/2} = v_{k+1} - (v_{k+2} - v_k)/4,
+ * without it the face values are the cell values (first order).
+ * ------------------------------------------------------------------------ */
+static int rusanov_fluxes(const oracle_params* p, const double* hl, const double* ql,
+                          const double* ml, const double* rl, double* Fq, double* Fm,
+                          double* Fr) {
+    const int64_t n = p->n;
+    for (int64_t k = -1; k < n; ++k) {
+        const int64_t im = nb(p, k - 1), i0 = nb(p, k), i1 = nb(p, k + 1), i2 = nb(p, k + 2);
+        double hL = hl[i0], hR = hl[i1], qL = ql[i0], qR = ql[i1];
+        double mL = ml[i0], mR = ml[i1], rL = rl[i0], rR = rl[i1];
+        if (p->recon) {
+            hL = hl[i0] + (hl[i1] - hl[im]) / 4.0;
+            hR = hl[i1] - (hl[i2] - hl[i0]) / 4.0;
+            qL = ql[i0] + (ql[i1] - ql[im]) / 4.0;
+            qR = ql[i1] - (ql[i2] - ql[i0]) / 4.0;
+            mL = ml[i0] + (ml[i1] - ml[im]) / 4.0;
+            mR = ml[i1] - (ml[i2] - ml[i0]) / 4.0;
+            rL = rl[i0] + (rl[i1] - rl[im]) / 4.0;
+            rR = rl[i1] - (rl[i2] - rl[i0]) / 4.0;
+        }
+        if (!(hL > 0.0) || !(hR > 0.0)) return ORACLE_ERR_DEPTH;
+        const double uL = qL / hL, uR = qR / hR;
+        const double s = p->rusanov ? p->speed : fmax(fabs(uL), fabs(uR));
+        Fq[k + 1] = 0.5 * (uL * qL + uR * qR - s * (qR - qL));
+        Fm[k + 1] = 0.5 * (uL * mL + uR * mR - s * (mR - mL));
+        Fr[k + 1] = 0.5 * (uL * rL + uR * rR - s * (rR - rL));
+    }
+    return ORACLE_OK;
+}
+
 static int stage_impl(const oracle_params* p,
                       const double* hb, const double* qb, const double* mb, const double* rb,
                       const double* hl, const double* ql, const double* ml, const double* rl,
@@ -229,6 +292,7 @@ static int stage_impl(const oracle_params* p,
     if (n < 3 || !(p->dx > 0.0) || !(tau >= 0.0) || !(p->lambda >= 0.0)) return ORACLE_ERR_ARG;
     const double dx = p->dx, g = p->g, lam = p->lambda;
     int rc = ORACLE_OK;
+    double* Phi = NULL; /* face forces of form 1 (freed on every exit path) */
 
     /* face fluxes: index k + 1 holds the face between cells k and k+1, k = -1..n-1 */
     double* Fq = (double*)malloc((size_t)(n + 1) * sizeof(double));
@@ -249,27 +313,9 @@ static int stage_impl(const oracle_params* p,
         goto done;
     }
 
-    /* (1) Rusanov fluxes of hu^2, hu eta, hu w at every face (Sec. 4.1, hat D_x)
-     * from the unlimited centred linear reconstruction of the conserved
-     * variables of U_l:  v^L_{k+1/2} = v_k + (v_{k+1} - v_{k-1})/4,
-     *                    v^R_{k+1/2} = v_{k+1} - (v_{k+2} - v_k)/4. */
-    for (int64_t k = -1; k < n; ++k) {
-        const int64_t im = nb(p, k - 1), i0 = nb(p, k), i1 = nb(p, k + 1), i2 = nb(p, k + 2);
-        const double hL = hl[i0] + (hl[i1] - hl[im]) / 4.0;
-        const double hR = hl[i1] - (hl[i2] - hl[i0]) / 4.0;
-        const double qL = ql[i0] + (ql[i1] - ql[im]) / 4.0;
-        const double qR = ql[i1] - (ql[i2] - ql[i0]) / 4.0;
-        const double mL = ml[i0] + (ml[i1] - ml[im]) / 4.0;
-        const double mR = ml[i1] - (ml[i2] - ml[i0]) / 4.0;
-        const double rL = rl[i0] + (rl[i1] - rl[im]) / 4.0;
-        const double rR = rl[i1] - (rl[i2] - rl[i0]) / 4.0;
-        if (!(hL > 0.0) || !(hR > 0.0)) { rc = ORACLE_ERR_DEPTH; goto done; }
-        const double uL = qL / hL, uR = qR / hR;
-        const double s = p->rusanov ? p->speed : fmax(fabs(uL), fabs(uR));
-        Fq[k + 1] = 0.5 * (uL * qL + uR * qR - s * (qR - qL));
-        Fm[k + 1] = 0.5 * (uL * mL + uR * mR - s * (mR - mL));
-        Fr[k + 1] = 0.5 * (uL * rL + uR * rR - s * (rR - rL));
-    }
+    /* (1) Rusanov fluxes of hu^2, hu eta, hu w at every face (Sec. 4.1, hat D_x) */
+    rc = rusanov_fluxes(p, hl, ql, ml, rl, Fq, Fm, Fr);
+    if (rc != ORACLE_OK) goto done;
 
     /* (2) starred values and the coefficients of eqs. (eq:hSGN_alpha) and
      * (GN_hyp_eq_semi_fully_discrete), per cell. */
@@ -297,7 +343,6 @@ static int stage_impl(const oracle_params* p,
     /* (3) rows of Delta[h]_i = h^dagger_i. Interface values are means (R2);
      * the delta term carries factor 1 with means (R3). Form 1 (R7) replaces
      * the delta term by the explicit face forces Phi. */
-    double* Phi = NULL;
     if (wb) {
         Phi = (double*)malloc((size_t)(n + 1) * sizeof(double)); /* face k+1/2 at k+1 */
         double* ph = (double*)malloc((size_t)n * sizeof(double));
@@ -421,6 +466,54 @@ int oracle_assemble(const oracle_params* p,
 }
 
 /* ------------------------------------------------------------------------
+ * Right-hand side of the explicit hSGN scheme, eq. (GN_hyp_eq_explicit)
+ * (Sec. 4.4), with every term evaluated at the given state U:
+ *   L_h = -D_x(q)
+ *   L_q = -hat D_x(q u) - a^2 D_x(h) - lambda alpha D_x(h eta)
+ *   L_m = -hat D_x(h u eta) + h w
+ *   L_r = -hat D_x(h u w) - lambda ((h eta)/h^2 - 1)
+ * D_x(F)_i = (F_{i+1} - F_{i-1})/(2 dx) (the mean face values of Sec. 4.4),
+ * hat D_x the Rusanov flux difference, a^2 and alpha of eq. (eq:hSGN_alpha)
+ * at the cell. The forward Euler step U + dt L(U) is the scheme as printed;
+ * L(U) is also the explicit evaluation H(U, U) of the IMEX right-hand side.
+ * Flat bottom only.
+ * ------------------------------------------------------------------------ */
+int oracle_explicit_rhs(const oracle_params* p, const double* h, const double* q,
+                        const double* m, const double* r, double* Lh, double* Lq, double* Lm,
+                        double* Lr) {
+    if (!p || p->n < 3 || !(p->dx > 0.0) || p->form != 0) return ORACLE_ERR_ARG;
+    const int64_t n = p->n;
+    const double dx = p->dx, g = p->g, lam = p->lambda;
+    double* Fq = (double*)malloc((size_t)(n + 1) * sizeof(double));
+    double* Fm = (double*)malloc((size_t)(n + 1) * sizeof(double));
+    double* Fr = (double*)malloc((size_t)(n + 1) * sizeof(double));
+    int rc = ORACLE_OK;
+    if (!Fq || !Fm || !Fr) { rc = ORACLE_ERR_NOMEM; goto done; }
+    rc = rusanov_fluxes(p, h, q, m, r, Fq, Fm, Fr);
+    if (rc != ORACLE_OK) goto done;
+    for (int64_t i = 0; i < n; ++i) {
+        const int64_t il = nb(p, i - 1), ir = nb(p, i + 1);
+        if (!(h[i] > 0.0)) { rc = ORACLE_ERR_DEPTH; goto done; }
+        const double eta = m[i] / h[i];
+        const double alpha = -(2.0 * eta / h[i] - 1.0) / (3.0 * h[i]);
+        const double c2 = g * h[i] + (lam / 3.0) * eta * eta / (h[i] * h[i]);
+        const double a2 = c2 - lam * eta * alpha;
+        Lh[i] = -(q[ir] - q[il]) / (2.0 * dx);
+        Lq[i] = -(Fq[i + 1] - Fq[i]) / dx - a2 * (h[ir] - h[il]) / (2.0 * dx)
+              - lam * alpha * (m[ir] - m[il]) / (2.0 * dx);
+        Lm[i] = -(Fm[i + 1] - Fm[i]) / dx + r[i];
+        Lr[i] = -(Fr[i + 1] - Fr[i]) / dx - lam * (m[i] / (h[i] * h[i]) - 1.0);
+        if (!isfinite(Lh[i]) || !isfinite(Lq[i]) || !isfinite(Lm[i]) || !isfinite(Lr[i])) {
+            rc = ORACLE_ERR_NONFINITE;
+            goto done;
+        }
+    }
+done:
+    free(Fq); free(Fm); free(Fr);
+    return rc;
+}
+
+/* ------------------------------------------------------------------------
  * IMEX Runge-Kutta step of Sec. 3.2 with the double Butcher tableau of eq.
  * (tableau) (reading R1: two stages, implicit first stage),
  *   gamma = 1 - 1/sqrt(2),  c = 1/(2 gamma),
@@ -452,6 +545,85 @@ static int imex2_step(void* ctx, stage_fn S, int64_t len, double* U, double dt, 
     return S(ctx, len, Ub, Ue, gamma * dt, U);
 }
 
+/* Explicit evaluation F(U) = H(U, U) of the full right-hand side. */
+typedef int (*rhs_fn)(void* ctx, int64_t len, const double* U, double* L);
+
+/* ARS(2,2,2) (Ascher, Ruuth, Spiteri 1997) in the generic stage form of
+ * Sec. 3.2 (U_E^(i) = U^n + dt sum_{j<i} aE_ij H_j, U_I^(i) = U^n +
+ * dt (sum_{j<i} aI_ij H_j + aI_ii H(U_E^(i), U_I^(i))), H_j = H(U_E^(j),
+ * U_I^(j))), with the double tableau
+ *   explicit: aE_21 = gamma, aE_31 = delta, aE_32 = 1 - delta
+ *   implicit: aI_22 = gamma, aI_32 = 1 - gamma, aI_33 = gamma,
+ * gamma = 1 - 1/sqrt(2), delta = 1 - 1/(2 gamma), U^{n+1} = U_I^(3).
+ * Stage 1 is explicit (U_E^(1) = U_I^(1) = U^n, H_1 = F(U^n)); an implicit
+ * stage is the stage operator with base U^n + dt sum_{j<i} aI_ij H_j,
+ * linearisation state U_E^(i) and tau = gamma dt, and H_i is recovered from
+ * its result as (U_I^(i) - base)/(gamma dt). */
+static int ars222_step(void* ctx, stage_fn S, rhs_fn F, int64_t len, double* U, double dt,
+                       double* work) {
+    const double gamma = 1.0 - 1.0 / sqrt(2.0);
+    const double delta = 1.0 - 1.0 / (2.0 * gamma);
+    double* H1 = work;
+    double* H2 = work + len;
+    double* Ue = work + 2 * len;
+    double* Ub = work + 3 * len;
+    double* Ui = work + 4 * len;
+    int rc = F(ctx, len, U, H1);
+    if (rc != ORACLE_OK) return rc;
+    for (int64_t k = 0; k < len; ++k) Ue[k] = U[k] + dt * gamma * H1[k];
+    rc = S(ctx, len, U, Ue, gamma * dt, Ui); /* stage 2: base U^n */
+    if (rc != ORACLE_OK) return rc;
+    for (int64_t k = 0; k < len; ++k) {
+        H2[k] = (Ui[k] - U[k]) / (gamma * dt);
+        Ue[k] = U[k] + dt * (delta * H1[k] + (1.0 - delta) * H2[k]);
+        Ub[k] = U[k] + dt * (1.0 - gamma) * H2[k];
+    }
+    return S(ctx, len, Ub, Ue, gamma * dt, U); /* stage 3 */
+}
+
+/* First-order semi-implicit step: one stage with tau = dt. */
+static int si1_step(void* ctx, stage_fn S, int64_t len, double* U, double dt, double* work) {
+    double* Ui = work;
+    const int rc = S(ctx, len, U, U, dt, Ui);
+    if (rc == ORACLE_OK) memcpy(U, Ui, (size_t)len * sizeof(double));
+    return rc;
+}
+
+/* Explicit steps: forward Euler U + dt F(U), and Heun's method
+ * U* = U + dt F(U), U^{n+1} = (U + U* + dt F(U*))/2. */
+static int euler_step(void* ctx, rhs_fn F, int64_t len, double* U, double dt, double* work) {
+    double* L = work;
+    const int rc = F(ctx, len, U, L);
+    if (rc != ORACLE_OK) return rc;
+    for (int64_t k = 0; k < len; ++k) U[k] = U[k] + dt * L[k];
+    return ORACLE_OK;
+}
+
+static int heun_step(void* ctx, rhs_fn F, int64_t len, double* U, double dt, double* work) {
+    double* L = work;
+    double* Us = work + len;
+    int rc = F(ctx, len, U, L);
+    if (rc != ORACLE_OK) return rc;
+    for (int64_t k = 0; k < len; ++k) Us[k] = U[k] + dt * L[k];
+    rc = F(ctx, len, Us, L);
+    if (rc != ORACLE_OK) return rc;
+    for (int64_t k = 0; k < len; ++k) U[k] = 0.5 * (U[k] + Us[k] + dt * L[k]);
+    return ORACLE_OK;
+}
+
+/* One step of the selected scheme (work holds 5 len values). */
+static int scheme_step(int32_t scheme, void* ctx, stage_fn S, rhs_fn F, int64_t len, double* U,
+                       double dt, double* work) {
+    switch (scheme) {
+        case ORACLE_SCHEME_PRINTED: return imex2_step(ctx, S, len, U, dt, work);
+        case ORACLE_SCHEME_ARS222: return ars222_step(ctx, S, F, len, U, dt, work);
+        case ORACLE_SCHEME_SI1: return si1_step(ctx, S, len, U, dt, work);
+        case ORACLE_SCHEME_EX_HEUN: return heun_step(ctx, F, len, U, dt, work);
+        case ORACLE_SCHEME_EX_EULER: return euler_step(ctx, F, len, U, dt, work);
+        default: return ORACLE_ERR_ARG;
+    }
+}
+
 /* hSGN stage on a packed state [h | q | m | r] of 4 n values */
 static int hsgn_stage_packed(void* ctx, int64_t len, const double* Ub, const double* Ul,
                              double tau, double* Uo) {
@@ -462,13 +634,21 @@ static int hsgn_stage_packed(void* ctx, int64_t len, const double* Ub, const dou
                       tau, Uo, Uo + n, Uo + 2 * n, Uo + 3 * n, NULL);
 }
 
-/* n_steps IMEX steps of size dt on the state arrays (in place). */
+/* explicit right-hand side on a packed state */
+static int hsgn_rhs_packed(void* ctx, int64_t len, const double* U, double* L) {
+    const oracle_params* p = (const oracle_params*)ctx;
+    const int64_t n = p->n;
+    (void)len;
+    return oracle_explicit_rhs(p, U, U + n, U + 2 * n, U + 3 * n, L, L + n, L + 2 * n, L + 3 * n);
+}
+
+/* n_steps steps of size dt (scheme p->scheme) on the state arrays (in place). */
 int oracle_run(const oracle_params* p, double* h, double* q, double* m, double* r,
                double dt, int64_t n_steps) {
     if (!p || !h || !q || !m || !r || p->n < 3 || n_steps < 0) return ORACLE_ERR_ARG;
     const int64_t n = p->n;
     double* U = (double*)malloc((size_t)(4 * n) * sizeof(double));
-    double* work = (double*)malloc((size_t)(12 * n) * sizeof(double));
+    double* work = (double*)malloc((size_t)(20 * n) * sizeof(double));
     if (!U || !work) { free(U); free(work); return ORACLE_ERR_NOMEM; }
     memcpy(U, h, (size_t)n * sizeof(double));
     memcpy(U + n, q, (size_t)n * sizeof(double));
@@ -487,7 +667,8 @@ int oracle_run(const oracle_params* p, double* h, double* q, double* m, double* 
             }
             ps.speed = umax;
         }
-        rc = imex2_step((void*)&ps, hsgn_stage_packed, 4 * n, U, dt, work);
+        rc = scheme_step(ps.scheme, (void*)&ps, hsgn_stage_packed, hsgn_rhs_packed, 4 * n, U, dt,
+                         work);
     }
     if (rc == ORACLE_OK) {
         memcpy(h, U, (size_t)n * sizeof(double));
@@ -518,17 +699,28 @@ static int scalar_stage(void* ctx, int64_t len, const double* Ub, const double* 
     return ORACLE_OK;
 }
 
-int oracle_imex_scalar(double aE, double aI, double y, double dt, int64_t n_steps, double* out) {
+static int scalar_rhs(void* ctx, int64_t len, const double* U, double* L) {
+    const scalar_ctx* s = (const scalar_ctx*)ctx;
+    for (int64_t k = 0; k < len; ++k) L[k] = (s->aE + s->aI) * U[k];
+    return ORACLE_OK;
+}
+
+int oracle_imex_scalar_scheme(int32_t scheme, double aE, double aI, double y, double dt,
+                              int64_t n_steps, double* out) {
     if (!out || n_steps < 0) return ORACLE_ERR_ARG;
     scalar_ctx s = {aE, aI};
     double U[1] = {y};
-    double work[3];
+    double work[5];
     for (int64_t k = 0; k < n_steps; ++k) {
-        int rc = imex2_step(&s, scalar_stage, 1, U, dt, work);
+        int rc = scheme_step(scheme, &s, scalar_stage, scalar_rhs, 1, U, dt, work);
         if (rc != ORACLE_OK) return rc;
     }
     *out = U[0];
     return ORACLE_OK;
+}
+
+int oracle_imex_scalar(double aE, double aI, double y, double dt, int64_t n_steps, double* out) {
+    return oracle_imex_scalar_scheme(ORACLE_SCHEME_PRINTED, aE, aI, y, dt, n_steps, out);
 }
 
 /* ------------------------------------------------------------------------
