@@ -63,8 +63,10 @@ enum {
 #define HSGN_FP64 0x0          /* every operation in FP64 */
 #define HSGN_MIXED 0x1         /* fluxes, coefficients and the depth solve in FP32
                                 * on increments; state, base-state differences and
-                                * the accumulation in FP64; the depth is updated in
-                                * flux form (mass conserved to FP64 rounding).
+                                * the accumulation in FP64 (with HSGN_EXACT_SOLVE)
+                                * or double-float pairs (below); the depth is
+                                * updated in flux form (mass conserved to the
+                                * rounding of the state).
                                 * One launch per stage: each CTA solves the depth
                                 * system of its tile on a window that overlaps the
                                 * neighbouring tiles by 64 rows and drops the
@@ -81,6 +83,26 @@ enum {
 #define HSGN_EXACT_SOLVE 0x4   /* with HSGN_MIXED: solve the depth system exactly
                                 * through the global separator system (three
                                 * launches per stage, state updated in place) */
+
+/* Time-stepping scheme (flags & HSGN_SCHEME_MASK). The default is the paper's
+ * method; the others are the comparisons it reports or names, FP64 flat bottom
+ * only (HSGN_ERR_UNIMPLEMENTED with HSGN_MIXED or HSGN_WELL_BALANCED):
+ *   PRINTED  the two-stage IMEX tableau of Sec. 3.2, eq. (tableau)
+ *   ARS222   the three-stage ARS(2,2,2) double tableau (explicit first stage)
+ *            in the generic stage form of Sec. 3.2
+ *   SI1      first-order semi-implicit: one stage of eq.
+ *            (GN_hyp_eq_semi_fully_discrete) with tau = dt, no reconstruction
+ *   EX_HEUN  explicit hSGN (Sec. 4.4, eq. (GN_hyp_eq_explicit)), Heun's method,
+ *            centred linear reconstruction; needs dt <= CFL dx / nu_max with
+ *            CFL about 0.4 (hsgn_suggest_dt with that CFL)
+ *   EX_EULER explicit hSGN, forward Euler, no reconstruction */
+#define HSGN_SCHEME_PRINTED 0x000
+#define HSGN_SCHEME_ARS222 0x100
+#define HSGN_SCHEME_SI1 0x200
+#define HSGN_SCHEME_EX_HEUN 0x300
+#define HSGN_SCHEME_EX_EULER 0x400
+#define HSGN_SCHEME_MASK 0x700
+
 #define HSGN_RUSANOV_LOCAL 0x10 /* Rusanov speed max(|u^L|,|u^R|) per face instead
                                  * of the global max |u^n| of the step */
 #define HSGN_WELL_BALANCED 0x2  /* variable bottom b(x) (Sec. 2.3, eq. (hSGNb_eq))

@@ -74,6 +74,9 @@ struct StageParams {
     const double* B[4];  // second input state, may be null when wl1 == wb1 == 0
     double wl0, wl1;     // U_l = wl0 A + wl1 B   (linearisation state)
     double wb0, wb1;     // U_b = wb0 A + wb1 B   (base state)
+    const double* C[4];  // optional third state (null: none): U_l += wl2 C
+    double wl2;
+    int32_t recon;       // 1: centred linear reconstruction; 0: none (first order)
     const double* speed; // device scalar: global Rusanov speed of the step
     BlockSplit split;
     // per-row outputs
@@ -122,6 +125,7 @@ __global__ void __launch_bounds__(T) k_stage_assemble(const StageParams p) {
     const int nb = (int)p.split.size(b);
     const int64_t n = p.n;
     const bool two = (p.B[0] != nullptr);
+    const bool three = (p.C[0] != nullptr);
 
     // ---- 0. stage inputs with a 3-cell halo; U_l and U_b formed on load
     for (int j = tid; j < nb + 6; j += T) {
@@ -141,6 +145,12 @@ __global__ void __launch_bounds__(T) k_stage_assemble(const StageParams p) {
             sm.hl[j] = ah; sm.ql[j] = aq; sm.ml[j] = am; sm.rl[j] = ar;
             sm.hb[j] = ah; sm.qb[j] = aq; sm.mb[j] = am; sm.rb[j] = ar;
         }
+        if (three) {
+            sm.hl[j] = fma(p.wl2, p.C[0][gi], sm.hl[j]);
+            sm.ql[j] = fma(p.wl2, p.C[1][gi], sm.ql[j]);
+            sm.ml[j] = fma(p.wl2, p.C[2][gi], sm.ml[j]);
+            sm.rl[j] = fma(p.wl2, p.C[3][gi], sm.rl[j]);
+        }
         if constexpr (WB) sm.wb.bb[j] = p.bathy ? p.bathy[gi] : 0.0;
     }
     __syncthreads();
@@ -157,10 +167,11 @@ __global__ void __launch_bounds__(T) k_stage_assemble(const StageParams p) {
         const double qm = sm.ql[c], q0 = sm.ql[c + 1], q1 = sm.ql[c + 2], q2 = sm.ql[c + 3];
         const double mm = sm.ml[c], m0 = sm.ml[c + 1], m1 = sm.ml[c + 2], m2 = sm.ml[c + 3];
         const double rm = sm.rl[c], r0_ = sm.rl[c + 1], r1 = sm.rl[c + 2], r2 = sm.rl[c + 3];
-        const double hL = fma(0.25, h1 - hm, h0), hR = fma(-0.25, h2 - h0, h1);
-        const double qL = fma(0.25, q1 - qm, q0), qR = fma(-0.25, q2 - q0, q1);
-        const double mL = fma(0.25, m1 - mm, m0), mR = fma(-0.25, m2 - m0, m1);
-        const double rL = fma(0.25, r1 - rm, r0_), rR = fma(-0.25, r2 - r0_, r1);
+        const double sl = p.recon ? 0.25 : 0.0;  // reconstruction slope factor
+        const double hL = fma(sl, h1 - hm, h0), hR = fma(-sl, h2 - h0, h1);
+        const double qL = fma(sl, q1 - qm, q0), qR = fma(-sl, q2 - q0, q1);
+        const double mL = fma(sl, m1 - mm, m0), mR = fma(-sl, m2 - m0, m1);
+        const double rL = fma(sl, r1 - rm, r0_), rR = fma(-sl, r2 - r0_, r1);
         if (!pos_finite(hL) || !pos_finite(hR)) bad |= HSGN_DEV_ERR_DEPTH;
         const double ip = rcp(hL * hR);  // one reciprocal for both velocities
         const double uL = qL * hR * ip, uR = qR * hL * ip;
@@ -619,6 +630,113 @@ __global__ void k_backsub(const BacksubParams p) {
         for (int o = 16; o > 0; o >>= 1) umax = fmax(umax, __shfl_xor_sync(0xffffffffu, umax, o));
         if (lane == 0 && umax > 0.0)
             atomicMax(reinterpret_cast<unsigned long long*>(p.speed),
+                      (unsigned long long)__double_as_longlong(umax));
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Explicit hSGN operator (Sec. 4.4, eq. (GN_hyp_eq_explicit)) at the state Us,
+//   L_h = -D_x(q),  L_q = -hat D_x(q u) - a^2 D_x(h) - lambda alpha D_x(h eta),
+//   L_m = -hat D_x(h u eta) + h w,  L_r = -hat D_x(h u w) - lambda ((h eta)/h^2 - 1),
+// D_x central over 2 dx, hat D_x the Rusanov difference of the (reconstructed)
+// face fluxes. One thread per cell; each face flux is evaluated by both of its
+// cells. Writes out1 = a1 U0 + b1 Us + c1 L(Us) and, if out2 is set, out2 =
+// a2 U0 + b2 Us + c2 L(Us) (U0 is read at the own cell only, so out1 may
+// alias U0); Euler, Heun and the explicit stage of ARS(2,2,2) are
+// combinations of this form.
+// ---------------------------------------------------------------------------
+struct ExplicitParams {
+    int64_t n;
+    int32_t recon;        // 1: centred linear reconstruction; 0: none
+    int32_t local_speed;  // 1: Rusanov speed max(|u^L|,|u^R|); 0: global *speed
+    int32_t track_speed;  // 1: fold max |u| of out1 into *speed_next
+    double dx, g, lam;
+    const double* Us[4];
+    const double* U0[4];  // may be null when a1 == a2 == 0
+    double a1, b1, c1, a2, b2, c2;
+    double* out1[4];
+    double* out2[4];      // may be null
+    const double* speed;
+    double* speed_next;
+    unsigned* err;
+};
+
+// Rusanov fluxes of q u, h u eta, h u w at the face between cells 0 and 1
+// from cells -1 .. 2 (Sec. 4.1).
+__device__ __forceinline__ void explicit_face(const double* h, const double* q, const double* m,
+                                              const double* r, double sl, bool local,
+                                              double gspeed, double& Fq, double& Fm, double& Fr,
+                                              unsigned& bad) {
+    const double hL = fma(sl, h[2] - h[0], h[1]), hR = fma(-sl, h[3] - h[1], h[2]);
+    const double qL = fma(sl, q[2] - q[0], q[1]), qR = fma(-sl, q[3] - q[1], q[2]);
+    const double mL = fma(sl, m[2] - m[0], m[1]), mR = fma(-sl, m[3] - m[1], m[2]);
+    const double rL = fma(sl, r[2] - r[0], r[1]), rR = fma(-sl, r[3] - r[1], r[2]);
+    if (!pos_finite(hL) || !pos_finite(hR)) bad |= HSGN_DEV_ERR_DEPTH;
+    const double ip = rcp(hL * hR);
+    const double uL = qL * hR * ip, uR = qR * hL * ip;
+    const double s = local ? fmax(fabs(uL), fabs(uR)) : gspeed;
+    Fq = 0.5 * (fma(uL, qL, uR * qR) - s * (qR - qL));
+    Fm = 0.5 * (fma(uL, mL, uR * mR) - s * (mR - mL));
+    Fr = 0.5 * (fma(uL, rL, uR * rR) - s * (rR - rL));
+}
+
+template <int BC>
+__global__ void __launch_bounds__(256) k_explicit(const ExplicitParams p) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int lane = threadIdx.x & 31;
+    double umax = 0.0;
+    if (i < p.n) {
+        double h[5], q[5], m[5], r[5];  // cells i-2 .. i+2
+#pragma unroll
+        for (int k = 0; k < 5; ++k) {
+            const int64_t c = wrap_index(i + k - 2, p.n, BC);
+            h[k] = p.Us[0][c];
+            q[k] = p.Us[1][c];
+            m[k] = p.Us[2][c];
+            r[k] = p.Us[3][c];
+        }
+        unsigned bad = 0;
+        const double sl = p.recon ? 0.25 : 0.0;
+        const bool local = p.local_speed != 0;
+        const double gspeed = local ? 0.0 : *p.speed;
+        double Fqm, Fmm, Frm, Fqp, Fmp, Frp;
+        explicit_face(h, q, m, r, sl, local, gspeed, Fqm, Fmm, Frm, bad);          // face i-1/2
+        explicit_face(h + 1, q + 1, m + 1, r + 1, sl, local, gspeed, Fqp, Fmp, Frp, bad);  // i+1/2
+        const double hc = h[2];
+        if (!pos_finite(hc)) bad |= HSGN_DEV_ERR_DEPTH;
+        const double ih = rcp(hc);
+        const double eta = m[2] * ih;
+        const double e = eta * ih;
+        const double alpha = fma(2.0, e, -1.0) * ih * (-1.0 / 3.0);
+        const double c2 = fma(p.g, hc, (p.lam * (1.0 / 3.0)) * e * e);
+        const double a2 = fma(-p.lam * eta, alpha, c2);
+        const double idx = 1.0 / p.dx, i2dx = 0.5 / p.dx;
+        double L[4];
+        L[0] = -(q[3] - q[1]) * i2dx;
+        L[1] = -(Fqp - Fqm) * idx - a2 * (h[3] - h[1]) * i2dx - p.lam * alpha * (m[3] - m[1]) * i2dx;
+        L[2] = -(Fmp - Fmm) * idx + r[2];
+        L[3] = -(Frp - Frm) * idx - p.lam * (e - 1.0);
+        const double cur[4] = {h[2], q[2], m[2], r[2]};
+        double o1[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const double u0 = p.U0[0] ? p.U0[k][i] : 0.0;
+            o1[k] = fma(p.c1, L[k], fma(p.b1, cur[k], p.a1 * u0));
+            if (p.out2[0]) p.out2[k][i] = fma(p.c2, L[k], fma(p.b2, cur[k], p.a2 * u0));
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) p.out1[k][i] = o1[k];
+        if (!finite_bits(o1[0]) || !finite_bits(o1[1]) || !finite_bits(o1[2]) ||
+            !finite_bits(o1[3]))
+            bad |= HSGN_DEV_ERR_NONFINITE;
+        if (bad) flag_error(p.err, bad);
+        if (p.track_speed && !bad) umax = fabs(o1[1] / o1[0]);
+    }
+    if (p.track_speed) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) umax = fmax(umax, __shfl_xor_sync(0xffffffffu, umax, o));
+        if (lane == 0 && umax > 0.0)
+            atomicMax(reinterpret_cast<unsigned long long*>(p.speed_next),
                       (unsigned long long)__double_as_longlong(umax));
     }
 }

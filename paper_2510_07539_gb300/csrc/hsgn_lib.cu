@@ -139,6 +139,10 @@ struct hsgn_s {
     double *qs = nullptr, *ms = nullptr, *rs = nullptr, *be = nullptr, *de = nullptr;
     double* blk = nullptr;
     double* s = nullptr;
+    // time-stepping scheme (HSGN_SCHEME_*) and its extra state buffers
+    int32_t scheme = HSGN_SCHEME_PRINTED;
+    double* E2[4] = {};              // ARS(2,2,2): U^n + gamma dt L(U^n)
+    double* Wd[4] = {};              // ARS(2,2,2): U^n + delta dt L(U^n)
     // well-balanced bathymetry form (HSGN_WELL_BALANCED)
     bool wb = false;
     double* bathy = nullptr;         // bottom per cell, null for a flat bottom
@@ -222,8 +226,12 @@ struct ProfScope {
 
 cudaError_t launch_stage(hsgn_s* H, const double* const A[4], const double* const B[4], double wl0,
                          double wl1, double wb0, double wb1, double tau, const double* speed_ptr,
-                         double* const out[4], bool reset_and_track, cudaStream_t st) {
+                         double* const out[4], bool reset_and_track, cudaStream_t st,
+                         const double* const C[4] = nullptr, double wl2 = 0.0) {
     StageParams p;
+    for (int k = 0; k < 4; ++k) p.C[k] = C ? C[k] : nullptr;
+    p.wl2 = wl2;
+    p.recon = H->scheme == HSGN_SCHEME_SI1 ? 0 : 1;
     p.n = H->n;
     p.bc = H->bc;
     p.local_speed = local_speed(H) ? 1 : 0;
@@ -443,6 +451,94 @@ cudaError_t launch_stage_fused(hsgn_s* H, int stage, double tau, cudaStream_t st
     return cudaGetLastError();
 }
 
+// Explicit operator (k_explicit): out1 = a1 U0 + b1 Us + c1 L(Us), optional out2.
+cudaError_t launch_explicit(hsgn_s* H, const double* const Us[4], const double* const U0[4],
+                            double a1, double b1, double c1, double* const out1[4],
+                            double a2, double b2, double c2, double* const out2[4],
+                            bool track, cudaStream_t st) {
+    ExplicitParams p;
+    p.n = H->n;
+    p.recon = H->scheme == HSGN_SCHEME_EX_EULER ? 0 : 1;
+    p.local_speed = local_speed(H) ? 1 : 0;
+    p.track_speed = track && !local_speed(H) ? 1 : 0;
+    p.dx = H->dx;
+    p.g = H->g;
+    p.lam = H->lam;
+    for (int k = 0; k < 4; ++k) {
+        p.Us[k] = Us[k];
+        p.U0[k] = U0 ? U0[k] : nullptr;
+        p.out1[k] = out1[k];
+        p.out2[k] = out2 ? out2[k] : nullptr;
+    }
+    p.a1 = a1; p.b1 = b1; p.c1 = c1;
+    p.a2 = a2; p.b2 = b2; p.c2 = c2;
+    p.speed = H->spd;
+    p.speed_next = H->spd + 4;
+    p.err = H->err;
+    const unsigned nb = (unsigned)((H->n + 255) / 256);
+    ProfScope ps(H, HSGN_PROF_ASSEMBLE, st);
+    if (H->bc == BC_PERIODIC)
+        k_explicit<BC_PERIODIC><<<nb, 256, 0, st>>>(p);
+    else
+        k_explicit<BC_TRANSMISSIVE><<<nb, 256, 0, st>>>(p);
+    return cudaGetLastError();
+}
+
+// The comparison schemes of the FP64 form (HSGN_SCHEME_*, see hsgn.h).
+cudaError_t enqueue_step_scheme(hsgn_s* H, double dt, cudaStream_t st) {
+    const double gam = 1.0 - 1.0 / std::sqrt(2.0);
+    const double del = 1.0 - 1.0 / (2.0 * gam);
+    const double* U[4] = {H->U[0], H->U[1], H->U[2], H->U[3]};
+    const double* U1c[4] = {H->U1[0], H->U1[1], H->U1[2], H->U1[3]};
+    cudaError_t e = cudaSuccess;
+    switch (H->scheme) {
+        case HSGN_SCHEME_SI1:  // one stage with tau = dt, no reconstruction
+            return launch_stage(H, U, nullptr, 1.0, 0.0, 1.0, 0.0, dt, H->spd, H->U, true, st);
+        case HSGN_SCHEME_ARS222: {
+            // explicit stage: E2 = U + gamma dt L(U), W = U + delta dt L(U)
+            e = launch_explicit(H, U, nullptr, 0.0, 1.0, gam * dt, H->E2, 0.0, 1.0, del * dt, H->Wd,
+                                false, st);
+            if (e != cudaSuccess) return e;
+            // stage 2: base U^n, linearisation E2
+            const double* E2c[4] = {H->E2[0], H->E2[1], H->E2[2], H->E2[3]};
+            e = launch_stage(H, U, E2c, 0.0, 1.0, 1.0, 0.0, gam * dt, H->spd, H->U1, false, st);
+            if (e != cudaSuccess) return e;
+            // stage 3: base U + ((1-gamma)/gamma)(U_I2 - U), linearisation
+            // W + ((1-delta)/gamma)(U_I2 - U)
+            const double* Wc[4] = {H->Wd[0], H->Wd[1], H->Wd[2], H->Wd[3]};
+            const double k3 = (1.0 - del) / gam, kb = (1.0 - gam) / gam;
+            return launch_stage(H, U, U1c, -k3, k3, 1.0 - kb, kb, gam * dt, H->spd, H->U, true, st,
+                                Wc, 1.0);
+        }
+        case HSGN_SCHEME_EX_HEUN:
+        case HSGN_SCHEME_EX_EULER: {
+            const bool heun = H->scheme == HSGN_SCHEME_EX_HEUN;
+            e = cudaMemsetAsync(H->spd + 4, 0, sizeof(double), st);
+            if (e != cudaSuccess) return e;
+            // U* = U + dt L(U)
+            e = launch_explicit(H, U, nullptr, 0.0, 1.0, dt, H->U1, 0.0, 0.0, 0.0, nullptr, !heun,
+                                st);
+            if (e != cudaSuccess) return e;
+            if (heun) {  // U^{n+1} = (U + U* + dt L(U*))/2
+                e = launch_explicit(H, U1c, U, 0.5, 0.5, 0.5 * dt, H->U, 0.0, 0.0, 0.0, nullptr,
+                                    true, st);
+            } else {
+                for (int k = 0; k < 4 && e == cudaSuccess; ++k)
+                    e = cudaMemcpyAsync(H->U[k], H->U1[k], H->n * sizeof(double),
+                                        cudaMemcpyDeviceToDevice, st);
+            }
+            if (e != cudaSuccess) return e;
+            // the next step's Rusanov speed
+            if (!local_speed(H))
+                e = cudaMemcpyAsync(H->spd, H->spd + 4, sizeof(double), cudaMemcpyDeviceToDevice,
+                                    st);
+            return e;
+        }
+        default:
+            return cudaErrorInvalidValue;
+    }
+}
+
 // IMEX step of Sec. 3.2 in efficient form:
 //   U1 = S(U, U, gamma dt);
 //   U  <- S(U_b, U_l, gamma dt), U_l = (1-c/gamma) U + (c/gamma) U1,
@@ -462,6 +558,7 @@ cudaError_t enqueue_step(hsgn_s* H, double dt, cudaStream_t st) {
         if (e != cudaSuccess) return e;
         return launch_stage_mixed(H, 2, tau, st);
     }
+    if (H->scheme != HSGN_SCHEME_PRINTED) return enqueue_step_scheme(H, dt, st);
     const double* A[4] = {H->U[0], H->U[1], H->U[2], H->U[3]};
     const double* B[4] = {H->U1[0], H->U1[1], H->U1[2], H->U1[3]};
     cudaError_t e = launch_stage(H, A, nullptr, 1.0, 0.0, 1.0, 0.0, tau, H->spd, H->U1, false, st);
@@ -542,7 +639,13 @@ int hsgn_create(const hsgn_grid_t* grid, double g, double lambda, const double* 
         return HSGN_ERR_INVALID_ARG;
     if (!(g > 0.0) || !std::isfinite(g) || !(lambda >= 0.0) || !std::isfinite(lambda))
         return HSGN_ERR_INVALID_ARG;
-    if (flags & ~(int32_t)(HSGN_RUSANOV_LOCAL | HSGN_MIXED | HSGN_WELL_BALANCED | HSGN_EXACT_SOLVE))
+    if (flags & ~(int32_t)(HSGN_RUSANOV_LOCAL | HSGN_MIXED | HSGN_WELL_BALANCED | HSGN_EXACT_SOLVE |
+                           HSGN_SCHEME_MASK))
+        return HSGN_ERR_UNIMPLEMENTED;
+    const int32_t scheme = flags & HSGN_SCHEME_MASK;
+    if (scheme > HSGN_SCHEME_EX_EULER) return HSGN_ERR_INVALID_ARG;
+    // the comparison schemes exist in the flat FP64 form only
+    if (scheme != HSGN_SCHEME_PRINTED && (flags & (HSGN_MIXED | HSGN_WELL_BALANCED)))
         return HSGN_ERR_UNIMPLEMENTED;
     if (bathymetry && !(flags & HSGN_WELL_BALANCED)) return HSGN_ERR_INVALID_ARG;
     if ((flags & HSGN_WELL_BALANCED) && (flags & HSGN_MIXED)) return HSGN_ERR_UNIMPLEMENTED;
@@ -563,6 +666,7 @@ int hsgn_create(const hsgn_grid_t* grid, double g, double lambda, const double* 
     H->mixed = (flags & HSGN_MIXED) != 0;
     H->windowed = H->mixed && !(flags & HSGN_EXACT_SOLVE);
     H->wb = (flags & HSGN_WELL_BALANCED) != 0;
+    H->scheme = scheme;
     const size_t vec = align_up(n * sizeof(double));
     const size_t fvec = align_up((n + 1) * sizeof(float));
     const size_t recb = align_up(3 * n * sizeof(float4));
@@ -570,6 +674,7 @@ int hsgn_create(const hsgn_grid_t* grid, double g, double lambda, const double* 
                    : H->mixed  ? 4 * vec + 4 * fvec + recb     // U; G1 dq1 dm1 dr1; row records
                                : 16 * vec;                     // U, U1, y v w, 5 back-sub arrays
     if (H->wb) total += (bathymetry ? 2 : 1) * vec;      // Phi, bottom
+    if (scheme == HSGN_SCHEME_ARS222) total += 8 * vec;    // E2, W
     total += align_up(BLK_STRIDE * P * sizeof(double)) + align_up(P * sizeof(double));
     const size_t rws = rows_ws_bytes(P);
     total += rws + align_up(8 * sizeof(double)) + align_up(sizeof(unsigned));
@@ -615,6 +720,11 @@ int hsgn_create(const hsgn_grid_t* grid, double g, double lambda, const double* 
             H->phi = reinterpret_cast<double*>(take(vec));
             if (bathymetry) H->bathy = reinterpret_cast<double*>(take(vec));
         }
+        if (scheme == HSGN_SCHEME_ARS222)
+            for (int k = 0; k < 4; ++k) {
+                H->E2[k] = reinterpret_cast<double*>(take(vec));
+                H->Wd[k] = reinterpret_cast<double*>(take(vec));
+            }
     }
     H->rws = rws ? take(rws) : nullptr;
     H->spd = reinterpret_cast<double*>(take(align_up(8 * sizeof(double))));

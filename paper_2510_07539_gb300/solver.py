@@ -23,6 +23,10 @@ FLAG_MIXED = 0x1
 FLAG_RUSANOV_LOCAL = 0x10
 FLAG_WELL_BALANCED = 0x2
 FLAG_EXACT_SOLVE = 0x4
+# time-stepping schemes (flags & SCHEME_MASK)
+SCHEME_PRINTED, SCHEME_ARS222, SCHEME_SI1, SCHEME_EX_HEUN, SCHEME_EX_EULER = (
+    0x000, 0x100, 0x200, 0x300, 0x400)
+SCHEME_MASK = 0x700
 
 ERROR_NAMES = {
     1: "HSGN_ERR_INVALID_ARG", 2: "HSGN_ERR_CUDA", 3: "HSGN_ERR_NONPOSITIVE_DEPTH",

@@ -64,6 +64,11 @@ def test_create_rejects_bad_arguments_before_touching_the_device(lib):
     assert lib.hsgn_create(ctypes.byref(g), 9.81, 1.0, bottom, 0x3, ctypes.byref(h)) == 6
     assert lib.hsgn_create(ctypes.byref(g), 9.81, 1.0, None, 0x3, ctypes.byref(h)) == 6
     assert not h.value
+    # comparison schemes: FP64 flat bottom only; an unknown scheme is invalid
+    assert lib.hsgn_create(ctypes.byref(g), 9.81, 1.0, None, 0x300 | 0x1, ctypes.byref(h)) == 6
+    assert lib.hsgn_create(ctypes.byref(g), 9.81, 1.0, None, 0x100 | 0x2, ctypes.byref(h)) == 6
+    assert lib.hsgn_create(ctypes.byref(g), 9.81, 1.0, None, 0x500, ctypes.byref(h)) == 1
+    assert not h.value
     lib.hsgn_destroy(None)
 
 
