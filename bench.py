@@ -73,6 +73,8 @@ def parse_args():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-fp64", action="store_true", help="skip the all-FP64 path")
+    ap.add_argument("--no-comparators", action="store_true",
+                    help="skip the scheme comparison (time to solution)")
     ap.add_argument("--sequential", action="store_true",
                     help="run the instances of a step back to back on one stream "
                          "(default: one CUDA stream each)")
@@ -337,6 +339,48 @@ def l2_vs_oracle(sols, dts, Ud, refs, ks, np):
     return {"depth_rel_l2": per["h"], "per_variable_rel_l2": per, "steps": ks}
 
 
+def time_to_solution(S, torch, n, xl, xr, Ud, stream):
+    """GPU time to advance the dam break (lambda = 1000, one instance of n
+    cells) by the physical time of 20 steps of the paper's scheme at
+    CFL_IMEX 4, with each scheme at its own stability limit: the semi-implicit
+    schemes at CFL_IMEX 4, the explicit ones at CFL 0.4 (Heun) and 0.2 (Euler),
+    as in the paper's cost tables (Sec. 6)."""
+    lam = 1000.0
+    runs = [("si_printed_fp64", S.FLAG_FP64, 4.0), ("si_ars222_fp64", S.SCHEME_ARS222, 4.0),
+            ("si_first_order_fp64", S.SCHEME_SI1, 4.0), ("ex_heun_fp64", S.SCHEME_EX_HEUN, 0.4),
+            ("ex_euler_fp64", S.SCHEME_EX_EULER, 0.2), ("si_printed_mixed", S.FLAG_MIXED, 4.0)]
+    out, T = {}, None
+    for name, flags, cfl in runs:
+        s = S.Solver(n, xl, xr, S.BC_TRANSMISSIVE, lam=lam, flags=flags)
+        s.set_state(*Ud)
+        dt = s.suggest_dt(cfl, 0.5)
+        if T is None:
+            T = 20 * dt
+        steps = max(1, int(math.ceil(T / dt - 1e-9)))
+        dt = T / steps
+        s.run(dt, 2)          # warm-up (graph capture)
+        s.set_state(*Ud)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        s.enqueue(dt, steps, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        s.check()
+        out[name] = {"steps": steps, "dt": dt, "ms": e0.elapsed_time(e1)}
+        s.close()
+    si = out["si_printed_fp64"]["ms"]
+    return {
+        "workload": f"dam break, lambda = 1000, {n} cells, physical time T = {T:.6g} "
+                    "(20 steps of the paper's scheme at CFL_IMEX 4)",
+        "runs": out,
+        "ex_heun_over_si_fp64": out["ex_heun_fp64"]["ms"] / si,
+        "ex_heun_fp64_over_si_mixed": out["ex_heun_fp64"]["ms"] / out["si_printed_mixed"]["ms"],
+        "paper_cpu_ratio_ex_over_si": "2.5-3.0 (Gaussian bell, lambda 100-1000, Sec. 6.1 table)",
+    }
+
+
 def time_fp64(S, torch, n, xl, xr, lams, Ud, args, flush, stream, dist, units_rank, world,
               hbm_peak):
     """The all-FP64 path (exact separator solve) on the same workload."""
@@ -445,6 +489,11 @@ def run_ours(args):
     if not args.no_fp64:
         fp64, fsols, fdts = time_fp64(S, torch, n, xl, xr, lams, Ud, args, flush, stream, dist,
                                       units_rank, world, hbm_peak)
+
+    # ---- the paper's comparison: the same physical time with each scheme
+    comparators = None
+    if not args.no_comparators:
+        comparators = time_to_solution(S, torch, n, xl, xr, Ud, stream)
 
     # ---- batched workload: 4096 independent periodic solitary waves of uneven
     #      length in one launch per kernel (mixed precision)
@@ -558,7 +607,9 @@ def run_ours(args):
                                "in-kernel by rho*^63 <= 2^-30"}),
             "l2_rel_err_vs_oracle": l2err,
             "roofline": roofline, "fp64_path": fp64, "batched": batched,
-            "batched_vs_fp64_single": (batched["value"] / fp64["value"]) if batched else None,
+            "batched_vs_fp64_single": (batched["value"] / fp64["value"])
+            if (batched and fp64) else None,
+            "comparators": comparators,
             "cpu_baseline": cpu, "e2e": e2e,
             "clocks": clocks, "gpu_launches": launches,
         }

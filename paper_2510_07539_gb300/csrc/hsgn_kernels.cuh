@@ -651,6 +651,7 @@ struct ExplicitParams {
     int32_t local_speed;  // 1: Rusanov speed max(|u^L|,|u^R|); 0: global *speed
     int32_t track_speed;  // 1: fold max |u| of out1 into *speed_next
     double dx, g, lam;
+    double idx, i2dx;     // 1/dx, 1/(2 dx)
     const double* Us[4];
     const double* U0[4];  // may be null when a1 == a2 == 0
     double a1, b1, c1, a2, b2, c2;
@@ -680,43 +681,62 @@ __device__ __forceinline__ void explicit_face(const double* h, const double* q, 
     Fr = 0.5 * (fma(uL, rL, uR * rR) - s * (rR - rL));
 }
 
+// One CTA of ET threads per ET consecutive cells: cells -2 .. ET+1 of the
+// block are staged in shared memory, each of the ET+1 faces is evaluated once.
+constexpr int ET = 256;
+
 template <int BC>
-__global__ void __launch_bounds__(256) k_explicit(const ExplicitParams p) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int lane = threadIdx.x & 31;
+__global__ void __launch_bounds__(ET) k_explicit(const ExplicitParams p) {
+    __shared__ double sh[4][ET + 4];      // cells c0-2 .. c0+ET+1
+    __shared__ double sf[3][ET + 1];      // faces c0-1/2 .. c0+ET-1/2
+    const int tid = threadIdx.x;
+    const int lane = tid & 31;
+    const int64_t c0 = (int64_t)blockIdx.x * ET;
+    const int64_t n = p.n;
+    for (int j = tid; j < ET + 4; j += ET) {
+        const int64_t c = wrap_index(c0 + j - 2 < 2 * n ? c0 + j - 2 : n - 1, n, BC);
+        sh[0][j] = p.Us[0][c];
+        sh[1][j] = p.Us[1][c];
+        sh[2][j] = p.Us[2][c];
+        sh[3][j] = p.Us[3][c];
+    }
+    __syncthreads();
+    unsigned bad = 0;
+    const double sl = p.recon ? 0.25 : 0.0;
+    const bool local = p.local_speed != 0;
+    const double gspeed = local ? 0.0 : *p.speed;
+    for (int f = tid; f < ET + 1; f += ET) {  // face f - 1/2 of the block: cells f-2 .. f+1
+        double Fq, Fm, Fr;
+        explicit_face(&sh[0][f], &sh[1][f], &sh[2][f], &sh[3][f], sl, local, gspeed, Fq, Fm, Fr,
+                      bad);
+        sf[0][f] = Fq;
+        sf[1][f] = Fm;
+        sf[2][f] = Fr;
+    }
+    __syncthreads();
+    const int64_t i = c0 + tid;
     double umax = 0.0;
-    if (i < p.n) {
-        double h[5], q[5], m[5], r[5];  // cells i-2 .. i+2
-#pragma unroll
-        for (int k = 0; k < 5; ++k) {
-            const int64_t c = wrap_index(i + k - 2, p.n, BC);
-            h[k] = p.Us[0][c];
-            q[k] = p.Us[1][c];
-            m[k] = p.Us[2][c];
-            r[k] = p.Us[3][c];
-        }
-        unsigned bad = 0;
-        const double sl = p.recon ? 0.25 : 0.0;
-        const bool local = p.local_speed != 0;
-        const double gspeed = local ? 0.0 : *p.speed;
-        double Fqm, Fmm, Frm, Fqp, Fmp, Frp;
-        explicit_face(h, q, m, r, sl, local, gspeed, Fqm, Fmm, Frm, bad);          // face i-1/2
-        explicit_face(h + 1, q + 1, m + 1, r + 1, sl, local, gspeed, Fqp, Fmp, Frp, bad);  // i+1/2
-        const double hc = h[2];
+    if (i < n) {
+        const int j = tid + 2;  // own cell in sh
+        const double hc = sh[0][j], hlft = sh[0][j - 1], hrgt = sh[0][j + 1];
+        const double qlft = sh[1][j - 1], qrgt = sh[1][j + 1];
+        const double mc = sh[2][j], mlft = sh[2][j - 1], mrgt = sh[2][j + 1];
+        const double rc = sh[3][j];
         if (!pos_finite(hc)) bad |= HSGN_DEV_ERR_DEPTH;
         const double ih = rcp(hc);
-        const double eta = m[2] * ih;
+        const double eta = mc * ih;
         const double e = eta * ih;
         const double alpha = fma(2.0, e, -1.0) * ih * (-1.0 / 3.0);
         const double c2 = fma(p.g, hc, (p.lam * (1.0 / 3.0)) * e * e);
         const double a2 = fma(-p.lam * eta, alpha, c2);
-        const double idx = 1.0 / p.dx, i2dx = 0.5 / p.dx;
+        const double idx = p.idx, i2dx = p.i2dx;
         double L[4];
-        L[0] = -(q[3] - q[1]) * i2dx;
-        L[1] = -(Fqp - Fqm) * idx - a2 * (h[3] - h[1]) * i2dx - p.lam * alpha * (m[3] - m[1]) * i2dx;
-        L[2] = -(Fmp - Fmm) * idx + r[2];
-        L[3] = -(Frp - Frm) * idx - p.lam * (e - 1.0);
-        const double cur[4] = {h[2], q[2], m[2], r[2]};
+        L[0] = -(qrgt - qlft) * i2dx;
+        L[1] = -(sf[0][tid + 1] - sf[0][tid]) * idx - a2 * (hrgt - hlft) * i2dx -
+               p.lam * alpha * (mrgt - mlft) * i2dx;
+        L[2] = -(sf[1][tid + 1] - sf[1][tid]) * idx + rc;
+        L[3] = -(sf[2][tid + 1] - sf[2][tid]) * idx - p.lam * (e - 1.0);
+        const double cur[4] = {hc, sh[1][j], mc, rc};
         double o1[4];
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
@@ -729,9 +749,9 @@ __global__ void __launch_bounds__(256) k_explicit(const ExplicitParams p) {
         if (!finite_bits(o1[0]) || !finite_bits(o1[1]) || !finite_bits(o1[2]) ||
             !finite_bits(o1[3]))
             bad |= HSGN_DEV_ERR_NONFINITE;
-        if (bad) flag_error(p.err, bad);
         if (p.track_speed && !bad) umax = fabs(o1[1] / o1[0]);
     }
+    if (bad) flag_error(p.err, bad);
     if (p.track_speed) {
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) umax = fmax(umax, __shfl_xor_sync(0xffffffffu, umax, o));

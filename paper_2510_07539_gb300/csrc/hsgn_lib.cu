@@ -464,6 +464,8 @@ cudaError_t launch_explicit(hsgn_s* H, const double* const Us[4], const double* 
     p.dx = H->dx;
     p.g = H->g;
     p.lam = H->lam;
+    p.idx = 1.0 / H->dx;
+    p.i2dx = 0.5 / H->dx;
     for (int k = 0; k < 4; ++k) {
         p.Us[k] = Us[k];
         p.U0[k] = U0 ? U0[k] : nullptr;
