@@ -95,10 +95,17 @@ def _load():
         lib.oracle_imex_scalar_scheme.argtypes = ([ctypes.c_int32] + [ctypes.c_double] * 4
                                                   + [ctypes.c_int64, P])
         lib.oracle_explicit_rhs.argtypes = [ctypes.POINTER(_Params)] + [P] * 8
+        lib.oracle_stage_adjoint.argtypes = ([ctypes.POINTER(_Params)] + [P] * 8 + [ctypes.c_double]
+                                             + [P] * 14)
+        I64P = ctypes.POINTER(ctypes.c_int64)
+        lib.oracle_adjoint.argtypes = ([ctypes.POINTER(_Params)] + [P] * 4
+                                       + [ctypes.c_double, ctypes.c_int64, ctypes.c_int64, I64P, P,
+                                          P] + [P] * 5)
         lib.oracle_suggest_dt.argtypes = ([ctypes.POINTER(_Params)] + [P] * 3
                                           + [ctypes.c_double] * 2 + [P] * 3)
         for f in ("oracle_tridiag_solve", "oracle_stage", "oracle_assemble", "oracle_run",
                   "oracle_imex_scalar", "oracle_imex_scalar_scheme", "oracle_explicit_rhs",
+                  "oracle_stage_adjoint", "oracle_adjoint",
                   "oracle_suggest_dt"):
             getattr(lib, f).restype = ctypes.c_int
         _lib = lib
@@ -218,3 +225,44 @@ def suggest_dt(p: Params, U, cfl: float, mcfl: float):
                                      float(mcfl), ctypes.byref(dt), ctypes.byref(nu),
                                      ctypes.byref(um)), "suggest_dt")
     return dt.value, nu.value, um.value
+
+
+def stage_adjoint(p: Params, Ub, Ul, tau: float, Ao):
+    """Adjoint of one stage (form 1, global speed): given dJ/dU_out (4 arrays)
+    returns (dJ/dU_b, dJ/dU_l, dJ/db, dJ/ds)."""
+    n = p.n
+    ub = [_f64(v, n) for v in Ub]
+    ul = [_f64(v, n) for v in Ul]
+    ao = [_f64(v, n) for v in Ao]
+    ab = [np.zeros(n) for _ in range(4)]
+    al = [np.zeros(n) for _ in range(4)]
+    gb = np.zeros(n)
+    sa = np.zeros(1)
+    pc = p._c()
+    _check(_load().oracle_stage_adjoint(ctypes.byref(pc), *map(_ptr, ub), *map(_ptr, ul),
+                                        float(tau), *map(_ptr, ao), *map(_ptr, ab),
+                                        *map(_ptr, al), _ptr(gb), _ptr(sa)), "stage_adjoint")
+    return ab, al, gb, float(sa[0])
+
+
+def misfit(states_h, gauge_cells, gauge_data, dt):
+    """J = 1/2 sum_s sum_g (h_g^s - d_{s,g})^2 dt for the depths after each step."""
+    e = np.asarray(states_h)[:, np.asarray(gauge_cells)] - np.asarray(gauge_data)
+    return 0.5 * float(np.sum(e * e)) * dt
+
+
+def adjoint(p: Params, U, dt: float, n_steps: int, gauge_cells, gauge_data):
+    """(J, [dJ/dh0, dJ/dq0, dJ/dm0, dJ/dr0], dJ/db, final state) of the gauge
+    misfit over n_steps steps of the paper's scheme (form 1, global speed)."""
+    n = p.n
+    u = [_f64(v, n).copy() for v in U]
+    cells = np.ascontiguousarray(gauge_cells, dtype=np.int64)
+    data = np.ascontiguousarray(gauge_data, dtype=np.float64).reshape(n_steps, len(cells))
+    g = [np.zeros(n) for _ in range(4)]
+    gb = np.zeros(n)
+    J = np.zeros(1)
+    pc = p._c()
+    _check(_load().oracle_adjoint(ctypes.byref(pc), *map(_ptr, u), float(dt), int(n_steps),
+                                  len(cells), cells.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+                                  _ptr(data), _ptr(J), *map(_ptr, g), _ptr(gb)), "adjoint")
+    return float(J[0]), g, gb, u

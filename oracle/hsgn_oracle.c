@@ -83,6 +83,12 @@
  *                          2, 1 on hSGN; dispersion relation and solitary
  *                          wave at second order (ARS(2,2,2), Heun); mass and
  *                          constant states for every scheme
+ *   oracle_stage_adjoint   central finite differences of oracle_stage along
+ *                          random smooth directions in U_b, U_l, b and the
+ *                          speed (both BCs)
+ *   oracle_adjoint         central finite differences of the gauge misfit of
+ *                          a run (initial state and bottom); zero gradient for
+ *                          a lake at rest with matching data
  */
 #include <math.h>
 #include <stdint.h>
@@ -748,4 +754,467 @@ int oracle_suggest_dt(const oracle_params* p, const double* h, const double* q,
     if (nu_max_out) *nu_max_out = numax;
     if (u_max_out) *u_max_out = umax;
     return ORACLE_OK;
+}
+
+/* ========================================================================
+ * Discrete adjoint of the step (well-balanced form 1, global Rusanov speed).
+ *
+ * For a misfit J(U_out), the adjoint of a stage maps dJ/dU_out to dJ/dU_b,
+ * dJ/dU_l, dJ/db and dJ/ds (s the Rusanov speed) by running the stage's
+ * operations backwards: every forward formula of stage_impl (form 1) is
+ * differentiated by the chain rule, each operation in reverse order of the
+ * forward one:
+ *   back-substitution  (q, m, r outputs; face forces Phi + beta_face dhbar)
+ *   solve              dJ/dD = M^{-T} dJ/dhbar,  dJ/dM_ij = -(dJ/dD)_i hbar_j
+ *   rows, right-hand side
+ *   face forces Phi    (p^ jumps, bottom force, beta_face dh_l)
+ *   p^, p~ per cell    (functions of h_l, m_l, m^dag)
+ *   beta per cell      (functions of h_l, m_l, m^dag, eq. (eq:hSGN_alpha))
+ *   starred values     (r^dag, m^dag with the bottom source, q^dag)
+ *   Rusanov fluxes     (reconstruction of U_l, the speed s)
+ * The adjoints of inputs are ADDED to the given arrays (callers zero them).
+ * Requires form 1 (a zero bottom gives the flat-bottom variant of the form),
+ * rusanov = 1 and recon = 1.
+ * ======================================================================== */
+static int stage_adjoint(const oracle_params* p, const double* const Ub[4],
+                         const double* const Ul[4], double tau, const double* const Ao[4],
+                         double* const Ab[4], double* const Al[4], double* Abathy,
+                         double* Aspeed) {
+    const int64_t n = p->n;
+    if (p->form != 1 || !p->rusanov || !p->recon || n < 3) return ORACLE_ERR_ARG;
+    const double dx = p->dx, g = p->g, lam = p->lambda, s = p->speed;
+    const double* hl = Ul[0]; const double* ql = Ul[1];
+    const double* ml = Ul[2]; const double* rl = Ul[3];
+    const double* hb = Ub[0];
+    const double* bb = p->bathy;
+    const double Cc = tau * tau / (dx * dx), f2 = tau / (2.0 * dx), fd = tau / dx;
+    const double lt2 = lam * tau * tau;
+    int rc = ORACLE_OK;
+    const int nn = 34;  /* work arrays below */
+    double* w = (double*)calloc((size_t)nn * (size_t)(n + 1), sizeof(double));
+    if (!w) return ORACLE_ERR_NOMEM;
+    double* Fq = w;             double* Fm = w + (n + 1);   double* Fr = w + 2 * (n + 1);
+    double* qs = w + 3 * (n + 1); double* ms = w + 4 * (n + 1); double* rs = w + 5 * (n + 1);
+    double* be = w + 6 * (n + 1); double* ph = w + 7 * (n + 1); double* pt = w + 8 * (n + 1);
+    double* Phi = w + 9 * (n + 1); double* A = w + 10 * (n + 1); double* B = w + 11 * (n + 1);
+    double* C = w + 12 * (n + 1); double* D = w + 13 * (n + 1); double* hbar = w + 14 * (n + 1);
+    double* mbar = w + 15 * (n + 1);
+    double* Fq_a = w + 16 * (n + 1); double* Fm_a = w + 17 * (n + 1); double* Fr_a = w + 18 * (n + 1);
+    double* qs_a = w + 19 * (n + 1); double* ms_a = w + 20 * (n + 1); double* rs_a = w + 21 * (n + 1);
+    double* be_a = w + 22 * (n + 1); double* ph_a = w + 23 * (n + 1); double* pt_a = w + 24 * (n + 1);
+    double* Phi_a = w + 25 * (n + 1); double* hbar_a = w + 26 * (n + 1); double* D_a = w + 27 * (n + 1);
+    double* aT = w + 28 * (n + 1); double* cT = w + 29 * (n + 1);
+    const int periodic = p->bc == BC_PERIODIC;
+    double bsum = 0.0;
+    (void)bsum;
+
+    /* ---- forward recomputation (the operations of stage_impl, form 1) */
+    rc = rusanov_fluxes(p, hl, ql, ml, rl, Fq, Fm, Fr);
+    if (rc != ORACLE_OK) goto done;
+    for (int64_t i = 0; i < n; ++i) {
+        const int64_t il = nb(p, i - 1), ir = nb(p, i + 1);
+        rs[i] = Ub[3][i] - (tau / dx) * (Fr[i + 1] - Fr[i]) + lam * tau;
+        ms[i] = Ub[2][i] - (tau / dx) * (Fm[i + 1] - Fm[i]) + tau * rs[i];
+        if (bb) ms[i] -= tau * 1.5 * ql[i] * (bb[ir] - bb[il]) / (2.0 * dx);
+        qs[i] = Ub[1][i] - (tau / dx) * (Fq[i + 1] - Fq[i]);
+        const double h = hl[i];
+        if (!(h > 0.0)) { rc = ORACLE_ERR_DEPTH; goto done; }
+        const double eta = ml[i] / h;
+        const double alpha = -(2.0 * eta / h - 1.0) / (3.0 * h);
+        const double c2 = g * h + (lam / 3.0) * eta * eta / (h * h);
+        const double a2 = c2 - lam * eta * alpha;
+        const double beta1 = 1.0 + lam * tau * tau / (h * h);
+        const double beta2 = 2.0 * lam * tau * tau / (beta1 * beta1 * h * h * h);
+        be[i] = a2 + lam * alpha * beta2 * ms[i];
+        const double ptil = (lam / 3.0) * (1.0 - eta / h);
+        const double b1 = h * h / (h * h + lt2);
+        pt[i] = ptil;
+        ph[i] = g * h * h / 2.0 + eta * ptil + lam * alpha * (ms[i] * b1 - ml[i]);
+    }
+    for (int64_t k = -1; k < n; ++k) {
+        const int64_t i0 = nb(p, k), i1 = nb(p, k + 1);
+        const double db = bb ? bb[i1] - bb[i0] : 0.0;
+        const double bbar = 0.5 * (be[i0] + be[i1]);
+        Phi[k + 1] = (ph[i1] - ph[i0]) + (g * 0.5 * (hl[i0] + hl[i1]) + 1.5 * 0.5 * (pt[i0] + pt[i1])) * db
+                   - bbar * (hl[i1] - hl[i0]);
+    }
+    for (int64_t i = 0; i < n; ++i) {
+        const int64_t il = nb(p, i - 1), ir = nb(p, i + 1);
+        const double bm = 0.5 * (be[il] + be[i]), bp = 0.5 * (be[i] + be[ir]);
+        D[i] = hb[i] - f2 * (qs[ir] - qs[il]) + Cc * (Phi[i + 1] - Phi[i]);
+        A[i] = -Cc * bm;
+        C[i] = -Cc * bp;
+        B[i] = 1.0 + Cc * (bm + bp);
+        if (!periodic) {
+            if (i == 0) { B[i] = 1.0 + Cc * bp; A[i] = 0.0; }
+            if (i == n - 1) { B[i] = 1.0 + Cc * bm; C[i] = 0.0; }
+        }
+    }
+    rc = oracle_tridiag_solve(n, periodic, A, B, C, D, hbar);
+    if (rc != ORACLE_OK) goto done;
+    for (int64_t i = 0; i < n; ++i) mbar[i] = ms[i] / (1.0 + lt2 / (hbar[i] * hbar[i]));
+
+    /* ---- back-substitution */
+    for (int64_t i = 0; i < n; ++i) {
+        const int64_t il = nb(p, i - 1), ir = nb(p, i + 1);
+        const double h = hbar[i], den = h * h + lt2;
+        const double ho_a = Ao[0][i], qo_a = Ao[1][i], mo_a = Ao[2][i], ro_a = Ao[3][i];
+        /* r = r^dag - lambda tau m / h^2 */
+        rs_a[i] += ro_a;
+        const double m_a = mo_a - ro_a * lam * tau / (h * h);
+        hbar_a[i] += ho_a + ro_a * 2.0 * lam * tau * mbar[i] / (h * h * h);
+        /* m = m^dag h^2 / (h^2 + lambda tau^2) */
+        ms_a[i] += m_a * h * h / den;
+        hbar_a[i] += m_a * ms[i] * 2.0 * h * lt2 / (den * den);
+        /* q = q^dag - tau/(2dx) (F_{i+1/2} + F_{i-1/2}), F = Phi + beta_face (hbar jump) */
+        qs_a[i] += qo_a;
+        const double a = -f2 * qo_a;
+        const double bp = 0.5 * (be[i] + be[ir]), bm = 0.5 * (be[il] + be[i]);
+        const double jp = hbar[ir] - hbar[i], jm = hbar[i] - hbar[il];
+        Phi_a[i + 1] += a;
+        be_a[i] += 0.5 * a * jp;
+        be_a[ir] += 0.5 * a * jp;
+        hbar_a[ir] += a * bp;
+        hbar_a[i] -= a * bp;
+        Phi_a[i] += a;
+        be_a[il] += 0.5 * a * jm;
+        be_a[i] += 0.5 * a * jm;
+        hbar_a[i] += a * bm;
+        hbar_a[il] -= a * bm;
+    }
+
+    /* ---- solve: dJ/dD = M^{-T} dJ/dhbar (rows of the transposed matrix) */
+    for (int64_t i = 0; i < n; ++i) {
+        aT[i] = i > 0 ? C[i - 1] : (periodic ? C[n - 1] : 0.0);
+        cT[i] = i < n - 1 ? A[i + 1] : (periodic ? A[0] : 0.0);
+    }
+    rc = oracle_tridiag_solve(n, periodic, aT, B, cT, hbar_a, D_a);
+    if (rc != ORACLE_OK) goto done;
+
+    /* ---- rows and right-hand side */
+    for (int64_t i = 0; i < n; ++i) {
+        const int64_t il = nb(p, i - 1), ir = nb(p, i + 1);
+        const double A_a = -D_a[i] * hbar[il], B_a = -D_a[i] * hbar[i], C_a = -D_a[i] * hbar[ir];
+        double bm_a = -Cc * A_a + Cc * B_a, bp_a = -Cc * C_a + Cc * B_a;
+        if (!periodic && i == 0) bm_a = 0.0;
+        if (!periodic && i == n - 1) bp_a = 0.0;
+        be_a[il] += 0.5 * bm_a;
+        be_a[i] += 0.5 * bm_a + 0.5 * bp_a;
+        be_a[ir] += 0.5 * bp_a;
+        Ab[0][i] += D_a[i];
+        qs_a[ir] -= f2 * D_a[i];
+        qs_a[il] += f2 * D_a[i];
+        Phi_a[i + 1] += Cc * D_a[i];
+        Phi_a[i] -= Cc * D_a[i];
+    }
+
+    /* ---- face forces Phi_{k+1/2}, k = -1 .. n-1 */
+    for (int64_t k = -1; k < n; ++k) {
+        const int64_t i0 = nb(p, k), i1 = nb(p, k + 1);
+        const double a = Phi_a[k + 1];
+        const double db = bb ? bb[i1] - bb[i0] : 0.0;
+        const double G = g * 0.5 * (hl[i0] + hl[i1]) + 1.5 * 0.5 * (pt[i0] + pt[i1]);
+        const double bbar = 0.5 * (be[i0] + be[i1]), dhl = hl[i1] - hl[i0];
+        ph_a[i1] += a;
+        ph_a[i0] -= a;
+        const double G_a = a * db;
+        Al[0][i0] += 0.5 * g * G_a;
+        Al[0][i1] += 0.5 * g * G_a;
+        pt_a[i0] += 0.75 * G_a;
+        pt_a[i1] += 0.75 * G_a;
+        if (bb && Abathy) {
+            Abathy[i1] += a * G;
+            Abathy[i0] -= a * G;
+        }
+        be_a[i0] += 0.5 * (-a * dhl);
+        be_a[i1] += 0.5 * (-a * dhl);
+        Al[0][i1] -= a * bbar;
+        Al[0][i0] += a * bbar;
+    }
+
+    /* ---- p^ and p~ per cell:
+     *   e = m_l/h^2, eta = m_l/h, p~ = (lambda/3)(1 - e), alpha = -(2e - 1)/(3h),
+     *   b_1 = h^2/(h^2 + lambda tau^2), w = m^dag b_1 - m_l,
+     *   p^ = g h^2/2 + eta p~ + lambda alpha w */
+    for (int64_t i = 0; i < n; ++i) {
+        const double h = hl[i], m = ml[i];
+        const double e = m / (h * h), eta = m / h;
+        const double alpha = -(2.0 * e - 1.0) / (3.0 * h);
+        const double den = h * h + lt2, b1 = h * h / den;
+        const double wv = ms[i] * b1 - m;
+        const double a = ph_a[i];
+        const double ptot_a = pt_a[i] + a * eta;
+        const double eta_a = a * pt[i];
+        const double alpha_a = a * lam * wv;
+        const double w_a = a * lam * alpha;
+        double h_a = a * g * h, m_a = -w_a, e_a = 0.0;
+        ms_a[i] += w_a * b1;
+        const double b1_a = w_a * ms[i];
+        h_a += b1_a * 2.0 * h * lt2 / (den * den);
+        e_a += alpha_a * (-2.0 / (3.0 * h));
+        h_a += alpha_a * (2.0 * e - 1.0) / (3.0 * h * h);
+        e_a += -(lam / 3.0) * ptot_a;
+        m_a += eta_a / h;
+        h_a += -eta_a * m / (h * h);
+        m_a += e_a / (h * h);
+        h_a += -2.0 * e_a * m / (h * h * h);
+        Al[0][i] += h_a;
+        Al[2][i] += m_a;
+    }
+
+    /* ---- beta per cell (eq. (eq:hSGN_alpha) and the semi-discrete beta):
+     *   eta = m_l/h, alpha = -(2 eta/h - 1)/(3h), c^2 = g h + (lambda/3) eta^2/h^2,
+     *   a^2 = c^2 - lambda eta alpha, beta_1 = 1 + lambda tau^2/h^2,
+     *   beta_2 = 2 lambda tau^2/(beta_1^2 h^3), beta = a^2 + lambda alpha beta_2 m^dag */
+    for (int64_t i = 0; i < n; ++i) {
+        const double h = hl[i], m = ml[i];
+        const double eta = m / h;
+        const double alpha = -(2.0 * eta / h - 1.0) / (3.0 * h);
+        const double beta1 = 1.0 + lt2 / (h * h);
+        const double beta2 = 2.0 * lt2 / (beta1 * beta1 * h * h * h);
+        const double a = be_a[i];
+        const double a2_a = a;
+        double alpha_a = a * lam * beta2 * ms[i];
+        const double beta2_a = a * lam * alpha * ms[i];
+        ms_a[i] += a * lam * alpha * beta2;
+        const double beta1_a = beta2_a * (-2.0 * beta2 / beta1);
+        double h_a = beta2_a * (-3.0 * beta2 / h);
+        h_a += beta1_a * (-2.0 * lt2 / (h * h * h));
+        const double c2_a = a2_a;
+        double eta_a = -a2_a * lam * alpha;
+        alpha_a += -a2_a * lam * eta;
+        h_a += c2_a * (g - (2.0 * lam / 3.0) * eta * eta / (h * h * h));
+        eta_a += c2_a * (2.0 * lam / 3.0) * eta / (h * h);
+        eta_a += alpha_a * (-2.0 / (3.0 * h * h));
+        h_a += alpha_a * (4.0 * eta / (3.0 * h * h * h) - 1.0 / (3.0 * h * h));
+        Al[2][i] += eta_a / h;
+        h_a += -eta_a * m / (h * h);
+        Al[0][i] += h_a;
+    }
+
+    /* ---- starred values: m^dag first (it feeds r^dag), then r^dag, q^dag */
+    for (int64_t i = 0; i < n; ++i) {
+        const int64_t il = nb(p, i - 1), ir = nb(p, i + 1);
+        const double a = ms_a[i];
+        Ab[2][i] += a;
+        Fm_a[i + 1] -= fd * a;
+        Fm_a[i] += fd * a;
+        rs_a[i] += tau * a;
+        if (bb) {
+            const double k = -tau * 1.5 / (2.0 * dx);
+            Al[1][i] += k * (bb[ir] - bb[il]) * a;
+            if (Abathy) {
+                Abathy[ir] += k * ql[i] * a;
+                Abathy[il] -= k * ql[i] * a;
+            }
+        }
+    }
+    for (int64_t i = 0; i < n; ++i) {
+        Ab[3][i] += rs_a[i];
+        Fr_a[i + 1] -= fd * rs_a[i];
+        Fr_a[i] += fd * rs_a[i];
+        Ab[1][i] += qs_a[i];
+        Fq_a[i + 1] -= fd * qs_a[i];
+        Fq_a[i] += fd * qs_a[i];
+    }
+
+    /* ---- Rusanov fluxes and the reconstruction of U_l (face k+1/2 at k+1) */
+    for (int64_t k = -1; k < n; ++k) {
+        const int64_t im = nb(p, k - 1), i0 = nb(p, k), i1 = nb(p, k + 1), i2 = nb(p, k + 2);
+        const double hL = hl[i0] + (hl[i1] - hl[im]) / 4.0, hR = hl[i1] - (hl[i2] - hl[i0]) / 4.0;
+        const double qL = ql[i0] + (ql[i1] - ql[im]) / 4.0, qR = ql[i1] - (ql[i2] - ql[i0]) / 4.0;
+        const double mL = ml[i0] + (ml[i1] - ml[im]) / 4.0, mR = ml[i1] - (ml[i2] - ml[i0]) / 4.0;
+        const double rL = rl[i0] + (rl[i1] - rl[im]) / 4.0, rR = rl[i1] - (rl[i2] - rl[i0]) / 4.0;
+        const double uL = qL / hL, uR = qR / hR;
+        const double aq = Fq_a[k + 1], am = Fm_a[k + 1], ar = Fr_a[k + 1];
+        const double uL_a = 0.5 * (aq * qL + am * mL + ar * rL);
+        const double uR_a = 0.5 * (aq * qR + am * mR + ar * rR);
+        double qL_a = 0.5 * aq * (uL + s), qR_a = 0.5 * aq * (uR - s);
+        const double mL_a = 0.5 * am * (uL + s), mR_a = 0.5 * am * (uR - s);
+        const double rL_a = 0.5 * ar * (uL + s), rR_a = 0.5 * ar * (uR - s);
+        if (Aspeed) *Aspeed += -0.5 * (aq * (qR - qL) + am * (mR - mL) + ar * (rR - rL));
+        qL_a += uL_a / hL;
+        qR_a += uR_a / hR;
+        const double hL_a = -uL_a * uL / hL, hR_a = -uR_a * uR / hR;
+        const double vL_a[4] = {hL_a, qL_a, mL_a, rL_a}, vR_a[4] = {hR_a, qR_a, mR_a, rR_a};
+        for (int v = 0; v < 4; ++v) {
+            Al[v][i0] += vL_a[v] + 0.25 * vR_a[v];
+            Al[v][i1] += 0.25 * vL_a[v] + vR_a[v];
+            Al[v][im] -= 0.25 * vL_a[v];
+            Al[v][i2] -= 0.25 * vR_a[v];
+        }
+    }
+done:
+    free(w);
+    return rc;
+}
+
+/* Adjoint of a stage on caller arrays (test entry point): the adjoints are
+ * added to Ab (4 arrays), Al (4 arrays), *Abathy (n, may be NULL) and
+ * *Aspeed (may be NULL). */
+int oracle_stage_adjoint(const oracle_params* p, const double* hb, const double* qb,
+                         const double* mb, const double* rb, const double* hl, const double* ql,
+                         const double* ml, const double* rl, double tau, const double* ho_a,
+                         const double* qo_a, const double* mo_a, const double* ro_a,
+                         double* hb_a, double* qb_a, double* mb_a, double* rb_a, double* hl_a,
+                         double* ql_a, double* ml_a, double* rl_a, double* bathy_a,
+                         double* speed_a) {
+    if (!p) return ORACLE_ERR_ARG;
+    const double* Ub[4] = {hb, qb, mb, rb};
+    const double* Ul[4] = {hl, ql, ml, rl};
+    const double* Ao[4] = {ho_a, qo_a, mo_a, ro_a};
+    double* Ab[4] = {hb_a, qb_a, mb_a, rb_a};
+    double* Al[4] = {hl_a, ql_a, ml_a, rl_a};
+    return stage_adjoint(p, Ub, Ul, tau, Ao, Ab, Al, bathy_a, speed_a);
+}
+
+/* ------------------------------------------------------------------------
+ * Gradient of the gauge misfit
+ *   J = 1/2 sum_{s=1..n_steps} sum_g (h_{c_g}^s - d_{s,g})^2 dt
+ * (h^s the depth after step s, c_g the gauge cells, d the data, n_steps x
+ * n_gauges row-major) with respect to the initial state and the bottom, for
+ * the paper's two-stage step (efficient form) in form 1 with the global
+ * Rusanov speed s^n = max_i |q_i/h_i| of each step (its subgradient goes to
+ * the first cell attaining the maximum). All states of the run are kept (the
+ * oracle serves small cases). On return U holds the final state, *misfit J
+ * and gU (4 arrays) / gb (n, may be NULL) the gradient.
+ * ------------------------------------------------------------------------ */
+int oracle_adjoint(const oracle_params* p, double* h, double* q, double* m, double* r, double dt,
+                   int64_t n_steps, int64_t n_gauges, const int64_t* gauge_cells,
+                   const double* gauge_data, double* misfit, double* gh, double* gq, double* gm,
+                   double* gr, double* gb) {
+    if (!p || !h || !q || !m || !r || !misfit || !gh || !gq || !gm || !gr || n_steps < 0 ||
+        n_gauges < 0 || (n_gauges > 0 && (!gauge_cells || !gauge_data)) || p->form != 1 ||
+        !p->rusanov || !p->recon || p->scheme != ORACLE_SCHEME_PRINTED)
+        return ORACLE_ERR_ARG;
+    const int64_t n = p->n;
+    for (int64_t k = 0; k < n_gauges; ++k)
+        if (gauge_cells[k] < 0 || gauge_cells[k] >= n) return ORACLE_ERR_ARG;
+    const double gam = 1.0 - 1.0 / sqrt(2.0), c = 1.0 / (2.0 * gam);
+    const double wl0 = 1.0 - c / gam, wl1 = c / gam;
+    const double wb0 = 1.0 - (1.0 - gam) / gam, wb1 = (1.0 - gam) / gam;
+    const double tau = gam * dt;
+    const size_t st = (size_t)(4 * n);
+    double* S = (double*)malloc((size_t)(n_steps + 1) * st * sizeof(double)); /* states */
+    double* sp = (double*)malloc((size_t)(n_steps + 1) * sizeof(double));
+    int64_t* am = (int64_t*)malloc((size_t)(n_steps + 1) * sizeof(int64_t));
+    double* wk = (double*)calloc(24 * (size_t)n, sizeof(double));
+    if (!S || !sp || !am || !wk) { free(S); free(sp); free(am); free(wk); return ORACLE_ERR_NOMEM; }
+    int rc = ORACLE_OK;
+    memcpy(S, h, (size_t)n * sizeof(double));
+    memcpy(S + n, q, (size_t)n * sizeof(double));
+    memcpy(S + 2 * n, m, (size_t)n * sizeof(double));
+    memcpy(S + 3 * n, r, (size_t)n * sizeof(double));
+    oracle_params ps = *p;
+    double J = 0.0;
+    /* forward, keeping every state, its speed and its argmax cell */
+    for (int64_t s = 0; s < n_steps; ++s) {
+        double* U = S + (size_t)s * st;
+        double umax = 0.0;
+        int64_t imax = 0;
+        for (int64_t i = 0; i < n; ++i) {
+            if (!(U[i] > 0.0)) { rc = ORACLE_ERR_DEPTH; goto done; }
+            const double u = fabs(U[n + i] / U[i]);
+            if (u > umax) { umax = u; imax = i; }
+        }
+        sp[s] = umax;
+        am[s] = imax;
+        ps.speed = umax;
+        memcpy(U + st, U, st * sizeof(double));
+        double work[1];
+        (void)work;
+        double* W = (double*)malloc(12 * (size_t)n * sizeof(double));
+        if (!W) { rc = ORACLE_ERR_NOMEM; goto done; }
+        rc = imex2_step((void*)&ps, hsgn_stage_packed, 4 * n, U + st, dt, W);
+        free(W);
+        if (rc != ORACLE_OK) goto done;
+        for (int64_t k = 0; k < n_gauges; ++k) {
+            const double e = U[st + gauge_cells[k]] - gauge_data[s * n_gauges + k];
+            J += 0.5 * e * e * dt;
+        }
+    }
+    /* reverse */
+    {
+        double* Ua = wk;                 /* dJ/dU^s (4n) */
+        double* Ua1 = wk + 4 * n;        /* dJ/dU_I^(1) */
+        double* Ab = wk + 8 * n;         /* stage base adjoint */
+        double* Al = wk + 12 * n;        /* stage linearisation adjoint */
+        double* U1 = wk + 16 * n;        /* U_I^(1) */
+        double* Ue = wk + 20 * n;        /* stage-2 linearisation state */
+        double* Ubs = (double*)malloc(st * sizeof(double));
+        double* Ab2 = (double*)malloc(st * sizeof(double));
+        if (!Ubs || !Ab2) { free(Ubs); free(Ab2); rc = ORACLE_ERR_NOMEM; goto done; }
+        memset(Ua, 0, st * sizeof(double));
+        if (gb) memset(gb, 0, (size_t)n * sizeof(double));
+        for (int64_t s = n_steps - 1; s >= 0 && rc == ORACLE_OK; --s) {
+            const double* U = S + (size_t)s * st;
+            const double* Un = S + (size_t)(s + 1) * st;
+            for (int64_t k = 0; k < n_gauges; ++k)
+                Ua[gauge_cells[k]] += (Un[gauge_cells[k]] - gauge_data[s * n_gauges + k]) * dt;
+            ps.speed = sp[s];
+            /* recompute the stage-1 result and the stage-2 states */
+            const double* Uv[4] = {U, U + n, U + 2 * n, U + 3 * n};
+            double* U1v[4] = {U1, U1 + n, U1 + 2 * n, U1 + 3 * n};
+            rc = stage_impl(&ps, Uv[0], Uv[1], Uv[2], Uv[3], Uv[0], Uv[1], Uv[2], Uv[3], tau,
+                            U1v[0], U1v[1], U1v[2], U1v[3], NULL);
+            if (rc != ORACLE_OK) break;
+            for (size_t k = 0; k < st; ++k) {
+                Ue[k] = wl0 * U[k] + wl1 * U1[k];
+                Ubs[k] = wb0 * U[k] + wb1 * U1[k];
+            }
+            double speed_a = 0.0;
+            /* stage 2 */
+            memset(Ab, 0, st * sizeof(double));
+            memset(Al, 0, st * sizeof(double));
+            {
+                const double* Ubv[4] = {Ubs, Ubs + n, Ubs + 2 * n, Ubs + 3 * n};
+                const double* Ulv[4] = {Ue, Ue + n, Ue + 2 * n, Ue + 3 * n};
+                const double* Aov[4] = {Ua, Ua + n, Ua + 2 * n, Ua + 3 * n};
+                double* Abv[4] = {Ab, Ab + n, Ab + 2 * n, Ab + 3 * n};
+                double* Alv[4] = {Al, Al + n, Al + 2 * n, Al + 3 * n};
+                rc = stage_adjoint(&ps, Ubv, Ulv, tau, Aov, Abv, Alv, gb, &speed_a);
+                if (rc != ORACLE_OK) break;
+            }
+            for (size_t k = 0; k < st; ++k) {
+                Ua1[k] = wl1 * Al[k] + wb1 * Ab[k];
+                Ua[k] = wl0 * Al[k] + wb0 * Ab[k];
+            }
+            /* stage 1: U_b = U_l = U^s */
+            memset(Ab2, 0, st * sizeof(double));
+            memset(Al, 0, st * sizeof(double));
+            {
+                const double* Aov[4] = {Ua1, Ua1 + n, Ua1 + 2 * n, Ua1 + 3 * n};
+                double* Abv[4] = {Ab2, Ab2 + n, Ab2 + 2 * n, Ab2 + 3 * n};
+                double* Alv[4] = {Al, Al + n, Al + 2 * n, Al + 3 * n};
+                rc = stage_adjoint(&ps, Uv, Uv, tau, Aov, Abv, Alv, gb, &speed_a);
+                if (rc != ORACLE_OK) break;
+            }
+            for (size_t k = 0; k < st; ++k) Ua[k] += Ab2[k] + Al[k];
+            /* the step's speed s = |q/h| at its argmax cell */
+            {
+                const int64_t i = am[s];
+                const double hh = U[i], qq = U[n + i];
+                const double sg = qq > 0.0 ? 1.0 : (qq < 0.0 ? -1.0 : 0.0);
+                Ua[n + i] += speed_a * sg / hh;
+                Ua[i] += -speed_a * fabs(qq) / (hh * hh);
+            }
+        }
+        free(Ubs);
+        free(Ab2);
+        if (rc == ORACLE_OK) {
+            memcpy(gh, Ua, (size_t)n * sizeof(double));
+            memcpy(gq, Ua + n, (size_t)n * sizeof(double));
+            memcpy(gm, Ua + 2 * n, (size_t)n * sizeof(double));
+            memcpy(gr, Ua + 3 * n, (size_t)n * sizeof(double));
+            const double* Uf = S + (size_t)n_steps * st;
+            memcpy(h, Uf, (size_t)n * sizeof(double));
+            memcpy(q, Uf + n, (size_t)n * sizeof(double));
+            memcpy(m, Uf + 2 * n, (size_t)n * sizeof(double));
+            memcpy(r, Uf + 3 * n, (size_t)n * sizeof(double));
+            *misfit = J;
+        }
+    }
+done:
+    free(S); free(sp); free(am); free(wk);
+    return rc;
 }
