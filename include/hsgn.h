@@ -192,11 +192,35 @@ int hsgn_suggest_dt(hsgn_handle_t h, double cfl, double mcfl, double* dt_out, vo
 int hsgn_stage(hsgn_handle_t h, const double* const base[4], const double* const lin[4],
                double tau, double speed, double* const out[4], void* stream);
 
-/* Discrete adjoint of hsgn_run (gradient of a gauge misfit with respect to
- * the initial depth). Not built: returns HSGN_ERR_UNIMPLEMENTED. */
+/* Discrete adjoint of a run (the gradient of a gauge misfit).
+ *
+ * Runs n_steps steps of the paper's scheme (Sec. 3.2) of size dt from the
+ * current state and returns
+ *   J = 1/2 sum_{s=1..n_steps} sum_g (h_{c_g}^s - d_{s,g})^2 dt
+ * in *misfit (host), where h^s is the depth after step s, c_g = gauge_cells[g]
+ * (host array of n_gauges cells in [0, n)) and d = gauge_data (host or device,
+ * n_steps x n_gauges, row-major). The gradient of J with respect to the
+ * initial state goes to grad_state[0..3] (device arrays of n for h, q, h eta,
+ * h w; grad_state or any entry may be NULL) and with respect to the bottom to
+ * grad_bathymetry (device array of n, may be NULL).
+ *
+ * The gradient is the exact derivative of the discrete step (every operation
+ * of the stage reversed: back-substitution, the depth solve through a second
+ * solve with the transposed matrix, rows, face forces, coefficients, starred
+ * values, Rusanov fluxes and reconstruction), including the global Rusanov
+ * speed max|u| of each step through its first argmax cell. States are stored
+ * every checkpoint_every steps and recomputed segment by segment in the
+ * reverse sweep (memory: n_steps/checkpoint_every + checkpoint_every + 16
+ * states of 4 n doubles, allocated during the call).
+ *
+ * Requires an FP64 instance created with HSGN_WELL_BALANCED (a NULL bottom
+ * gives the flat-bottom case), the paper's scheme and the global Rusanov speed
+ * (HSGN_ERR_UNIMPLEMENTED otherwise); the paper has no adjoint. On return the
+ * state is the state after n_steps steps. Synchronises. */
 int hsgn_adjoint(hsgn_handle_t h, double dt, int64_t n_steps, int64_t n_gauges,
-                 const int64_t* gauge_cells, const double* gauge_data, double* grad_h0,
-                 double* misfit, void* stream);
+                 const int64_t* gauge_cells, const double* gauge_data, int64_t checkpoint_every,
+                 double* const grad_state[4], double* grad_bathymetry, double* misfit,
+                 void* stream);
 
 /* ---------------------------------------------------------------------------
  * Batches of independent instances (the batched workload of many 1D problems

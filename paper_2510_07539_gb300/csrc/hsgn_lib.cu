@@ -16,6 +16,7 @@
 #include "../../include/hsgn.h"
 #include "hsgn_kernels.cuh"
 #include "hsgn_fused.cuh"
+#include "hsgn_adjoint.cuh"
 
 using namespace hsgn;
 
@@ -963,12 +964,301 @@ int hsgn_stage(hsgn_handle_t H, const double* const base[4], const double* const
                : HSGN_ERR_CUDA;
 }
 
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Discrete adjoint of a run (declared in include/hsgn.h): the paper's step in
+// the FP64 bottom form, states kept at checkpoints and recomputed per segment.
+// ---------------------------------------------------------------------------
+namespace {
+
+struct AdjWork {
+    unsigned char* mem = nullptr;
+    int64_t n = 0, K = 0, nck = 0;
+    double* ck = nullptr;       // checkpoints, nck x 4n
+    double* seg = nullptr;      // states of a segment, (K+1) x 4n
+    double* U1 = nullptr;       // stage-1 result
+    double* Ue = nullptr;       // stage-2 linearisation state
+    double* Ubs = nullptr;      // stage-2 base state
+    double* O2 = nullptr;       // stage-2 output
+    double* Ua = nullptr;       // dJ/dU of the current step boundary
+    double* Ua1 = nullptr;      // dJ/dU_I^(1)
+    double* Ab = nullptr;       // stage adjoints
+    double* Al = nullptr;
+    double* cellw = nullptr;    // 11 x n per-cell work
+    double* facew = nullptr;    // 4 x (n+1) per-face work
+    unsigned char* sws = nullptr;  // tridiagonal solve workspace
+    unsigned long long* sbits = nullptr;  // speed of the step (bits of a double), argmax
+    double* Aspeed = nullptr;
+    double* J = nullptr;
+    int64_t* cells = nullptr;
+    double* data = nullptr;
+    size_t work_bytes = 0;      // cellw + facew, zeroed per stage adjoint
+};
+
+Ptr4 cp4(const double* b, int64_t n) {
+    return Ptr4{{b, b + n, b + 2 * n, b + 3 * n}};
+}
+MutPtr4 mp4(double* b, int64_t n) {
+    return MutPtr4{{b, b + n, b + 2 * n, b + 3 * n}};
+}
+
+unsigned grid_of(int64_t m) { return (unsigned)((m + 255) / 256); }
+
+// global Rusanov speed max |q/h| of a state and its first argmax cell
+cudaError_t adj_speed(AdjWork& W, const double* U, cudaStream_t st) {
+    const int64_t n = W.n;
+    cudaError_t e = cudaMemsetAsync(W.sbits, 0, sizeof(unsigned long long), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(W.sbits + 1, 0xFF, sizeof(unsigned long long), st);
+    if (e != cudaSuccess) return e;
+    k_adj_umax<<<304, 256, 0, st>>>(n, U, U + n, W.sbits);
+    k_adj_argmax<<<304, 256, 0, st>>>(n, U, U + n, W.sbits, W.sbits + 1);
+    return cudaGetLastError();
+}
+
+// one step of the paper's scheme on packed arrays in -> out (4n each)
+cudaError_t adj_forward_step(hsgn_s* H, AdjWork& W, const double* in, double* out, double dt,
+                             cudaStream_t st) {
+    const int64_t n = W.n;
+    const double gam = 1.0 - 1.0 / std::sqrt(2.0), c = 1.0 / (2.0 * gam);
+    cudaError_t e = adj_speed(W, in, st);
+    if (e != cudaSuccess) return e;
+    const double* speed = reinterpret_cast<const double*>(W.sbits);
+    const double* A[4] = {in, in + n, in + 2 * n, in + 3 * n};
+    double* U1[4] = {W.U1, W.U1 + n, W.U1 + 2 * n, W.U1 + 3 * n};
+    const double* B[4] = {W.U1, W.U1 + n, W.U1 + 2 * n, W.U1 + 3 * n};
+    double* O[4] = {out, out + n, out + 2 * n, out + 3 * n};
+    e = launch_stage(H, A, nullptr, 1.0, 0.0, 1.0, 0.0, gam * dt, speed, U1, false, st);
+    if (e != cudaSuccess) return e;
+    return launch_stage(H, A, B, 1.0 - c / gam, c / gam, 1.0 - (1.0 - gam) / gam,
+                        (1.0 - gam) / gam, gam * dt, speed, O, false, st);
+}
+
+// adjoint of one stage whose forward was just run by launch_stage (the work
+// arrays of the handle hold its q^dag, m^dag, r^dag, beta)
+cudaError_t adj_stage(hsgn_s* H, AdjWork& W, const double* Ub, const double* Ul, double tau,
+                      const double* out, const double* Ao, double* Ab, double* Al,
+                      double* Abathy, cudaStream_t st) {
+    const int64_t n = W.n;
+    AdjParams p;
+    p.n = n;
+    p.bc = H->bc;
+    p.dx = H->dx;
+    p.g = H->g;
+    p.lam = H->lam;
+    p.tau = tau;
+    p.speed = reinterpret_cast<const double*>(W.sbits);
+    for (int v = 0; v < 4; ++v) {
+        p.Ub[v] = Ub + v * n;
+        p.Ul[v] = Ul + v * n;
+        p.Ao[v] = Ao + v * n;
+        p.Ab[v] = Ab + v * n;
+        p.Al[v] = Al + v * n;
+    }
+    p.bathy = H->bathy;
+    p.qs = H->qs;
+    p.ms = H->ms;
+    p.rs = H->rs;
+    p.be = H->be;
+    p.hbar = out;
+    p.mbar = out + 2 * n;
+    p.Abathy = Abathy;
+    p.Aspeed = W.Aspeed;
+    double* c = W.cellw;
+    p.qs_a = c; p.ms_a = c + n; p.rs_a = c + 2 * n; p.be_a = c + 3 * n; p.ph_a = c + 4 * n;
+    p.pt_a = c + 5 * n; p.hbar_a = c + 6 * n; p.D_a = c + 7 * n;
+    p.ra = c + 8 * n; p.rb = c + 9 * n; p.rc = c + 10 * n;
+    double* f = W.facew;
+    p.Phi_a = f; p.Fq_a = f + (n + 1); p.Fm_a = f + 2 * (n + 1); p.Fr_a = f + 3 * (n + 1);
+    cudaError_t e = cudaMemsetAsync(W.cellw, 0, W.work_bytes, st);
+    if (e != cudaSuccess) return e;
+    const unsigned gc = grid_of(n), gf = grid_of(n + 1);
+    const bool per = H->bc == BC_PERIODIC;
+    if (per) k_adj_backsub<BC_PERIODIC><<<gc, 256, 0, st>>>(p);
+    else k_adj_backsub<BC_TRANSMISSIVE><<<gc, 256, 0, st>>>(p);
+    if (per) k_adj_rows<BC_PERIODIC><<<gc, 256, 0, st>>>(p);
+    else k_adj_rows<BC_TRANSMISSIVE><<<gc, 256, 0, st>>>(p);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    e = solve_rows(n, per ? 1 : 0, p.ra, p.rb, p.rc, p.hbar_a, p.D_a, W.sws, H->err, nullptr, st);
+    if (e != cudaSuccess) return e;
+    if (per) k_adj_rowsadj<BC_PERIODIC><<<gc, 256, 0, st>>>(p);
+    else k_adj_rowsadj<BC_TRANSMISSIVE><<<gc, 256, 0, st>>>(p);
+    if (per) k_adj_phi<BC_PERIODIC><<<gf, 256, 0, st>>>(p);
+    else k_adj_phi<BC_TRANSMISSIVE><<<gf, 256, 0, st>>>(p);
+    k_adj_cell<<<gc, 256, 0, st>>>(p);
+    if (per) k_adj_starred<BC_PERIODIC><<<gc, 256, 0, st>>>(p);
+    else k_adj_starred<BC_TRANSMISSIVE><<<gc, 256, 0, st>>>(p);
+    if (per) k_adj_flux<BC_PERIODIC><<<gf, 256, 0, st>>>(p);
+    else k_adj_flux<BC_TRANSMISSIVE><<<gf, 256, 0, st>>>(p);
+    return cudaGetLastError();
+}
+
+// dJ/dU^s from dJ/dU^{s+1} (in W.Ua, updated in place) for the step from U
+cudaError_t adj_step(hsgn_s* H, AdjWork& W, const double* U, double dt, double* Abathy,
+                     cudaStream_t st) {
+    const int64_t n = W.n;
+    const double gam = 1.0 - 1.0 / std::sqrt(2.0), c = 1.0 / (2.0 * gam);
+    const double wl0 = 1.0 - c / gam, wl1 = c / gam;
+    const double wb0 = 1.0 - (1.0 - gam) / gam, wb1 = (1.0 - gam) / gam;
+    const double tau = gam * dt;
+    const unsigned gc = grid_of(n);
+    const Ptr4 none{{nullptr, nullptr, nullptr, nullptr}};
+    cudaError_t e = adj_speed(W, U, st);
+    if (e != cudaSuccess) return e;
+    const double* speed = reinterpret_cast<const double*>(W.sbits);
+    const double* A[4] = {U, U + n, U + 2 * n, U + 3 * n};
+    double* U1m[4] = {W.U1, W.U1 + n, W.U1 + 2 * n, W.U1 + 3 * n};
+    // stage-1 forward, the stage-2 states, stage-2 forward
+    e = launch_stage(H, A, nullptr, 1.0, 0.0, 1.0, 0.0, tau, speed, U1m, false, st);
+    if (e != cudaSuccess) return e;
+    k_adj_axpby<<<gc, 256, 0, st>>>(n, wl0, cp4(U, n), wl1, cp4(W.U1, n), 0.0, none, mp4(W.Ue, n));
+    k_adj_axpby<<<gc, 256, 0, st>>>(n, wb0, cp4(U, n), wb1, cp4(W.U1, n), 0.0, none, mp4(W.Ubs, n));
+    const double* Bb[4] = {W.Ubs, W.Ubs + n, W.Ubs + 2 * n, W.Ubs + 3 * n};
+    const double* Bl[4] = {W.Ue, W.Ue + n, W.Ue + 2 * n, W.Ue + 3 * n};
+    double* O2m[4] = {W.O2, W.O2 + n, W.O2 + 2 * n, W.O2 + 3 * n};
+    e = launch_stage(H, Bb, Bl, 0.0, 1.0, 1.0, 0.0, tau, speed, O2m, false, st);
+    if (e != cudaSuccess) return e;
+    // stage-2 adjoint
+    e = cudaMemsetAsync(W.Ab, 0, 8 * (size_t)n * sizeof(double), st);  // Ab and Al
+    if (e == cudaSuccess) e = cudaMemsetAsync(W.Aspeed, 0, sizeof(double), st);
+    if (e != cudaSuccess) return e;
+    e = adj_stage(H, W, W.Ubs, W.Ue, tau, W.O2, W.Ua, W.Ab, W.Al, Abathy, st);
+    if (e != cudaSuccess) return e;
+    k_adj_axpby<<<gc, 256, 0, st>>>(n, wl1, cp4(W.Al, n), wb1, cp4(W.Ab, n), 0.0, none,
+                                    mp4(W.Ua1, n));
+    k_adj_axpby<<<gc, 256, 0, st>>>(n, wl0, cp4(W.Al, n), wb0, cp4(W.Ab, n), 0.0, none,
+                                    mp4(W.Ua, n));
+    // stage-1 forward again (its work arrays), then its adjoint
+    e = launch_stage(H, A, nullptr, 1.0, 0.0, 1.0, 0.0, tau, speed, U1m, false, st);
+    if (e != cudaSuccess) return e;
+    e = cudaMemsetAsync(W.Ab, 0, 8 * (size_t)n * sizeof(double), st);
+    if (e != cudaSuccess) return e;
+    e = adj_stage(H, W, U, U, tau, W.U1, W.Ua1, W.Ab, W.Al, Abathy, st);
+    if (e != cudaSuccess) return e;
+    k_adj_axpby<<<gc, 256, 0, st>>>(n, 1.0, cp4(W.Ua, n), 1.0, cp4(W.Ab, n), 1.0, cp4(W.Al, n),
+                                    mp4(W.Ua, n));
+    // the step's speed
+    k_adj_speed<<<1, 1, 0, st>>>(U, U + n, W.sbits + 1, W.Aspeed, W.Ua, W.Ua + n);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+extern "C" {
+
 int hsgn_adjoint(hsgn_handle_t H, double dt, int64_t n_steps, int64_t n_gauges,
-                 const int64_t* gauge_cells, const double* gauge_data, double* grad_h0,
-                 double* misfit, void* stream) {
-    (void)H; (void)dt; (void)n_steps; (void)n_gauges; (void)gauge_cells; (void)gauge_data;
-    (void)grad_h0; (void)misfit; (void)stream;
-    return HSGN_ERR_UNIMPLEMENTED;
+                 const int64_t* gauge_cells, const double* gauge_data, int64_t checkpoint_every,
+                 double* const grad_state[4], double* grad_bathymetry, double* misfit,
+                 void* stream) {
+    if (!H || !(dt > 0.0) || !std::isfinite(dt) || n_steps < 1 || n_gauges < 0 || !misfit ||
+        checkpoint_every < 1 || (n_gauges > 0 && (!gauge_cells || !gauge_data)))
+        return HSGN_ERR_INVALID_ARG;
+    if (H->batched || H->mixed || !H->wb || H->scheme != HSGN_SCHEME_PRINTED || local_speed(H))
+        return HSGN_ERR_UNIMPLEMENTED;
+    const int64_t n = H->n;
+    for (int64_t k = 0; k < n_gauges; ++k)
+        if (gauge_cells[k] < 0 || gauge_cells[k] >= n) return HSGN_ERR_INVALID_ARG;
+    cudaStream_t st = as_stream(stream);
+    AdjWork W;
+    W.n = n;
+    W.K = checkpoint_every < n_steps ? checkpoint_every : n_steps;
+    W.nck = (n_steps + W.K - 1) / W.K;
+    const size_t s4 = align_up(4 * (size_t)n * sizeof(double));
+    const size_t cellb = align_up(11 * (size_t)n * sizeof(double));
+    const size_t faceb = align_up(4 * (size_t)(n + 1) * sizeof(double));
+    const size_t swsb = rows_ws_bytes(n);
+    const size_t gcb = align_up((size_t)(n_gauges > 0 ? n_gauges : 1) * sizeof(int64_t));
+    const size_t gdb = align_up((size_t)(n_gauges > 0 ? n_gauges : 1) * (size_t)n_steps *
+                                sizeof(double));
+    const size_t total = (size_t)W.nck * s4 + (size_t)(W.K + 1) * s4 + 10 * s4 + cellb + faceb +
+                         swsb + align_up(4 * sizeof(unsigned long long)) + gcb + gdb;
+    if (cudaMalloc(&W.mem, total) != cudaSuccess) {
+        cudaGetLastError();
+        return HSGN_ERR_OUT_OF_MEMORY;
+    }
+    unsigned char* p = W.mem;
+    auto take = [&](size_t b) { unsigned char* r = p; p += b; return r; };
+    W.ck = reinterpret_cast<double*>(take((size_t)W.nck * s4));
+    W.seg = reinterpret_cast<double*>(take((size_t)(W.K + 1) * s4));
+    W.U1 = reinterpret_cast<double*>(take(s4));
+    W.Ue = reinterpret_cast<double*>(take(s4));
+    W.Ubs = reinterpret_cast<double*>(take(s4));
+    W.O2 = reinterpret_cast<double*>(take(s4));
+    W.Ua = reinterpret_cast<double*>(take(s4));
+    W.Ua1 = reinterpret_cast<double*>(take(s4));
+    // Ab and Al are contiguous (one memset clears both)
+    W.Ab = reinterpret_cast<double*>(take(2 * s4));
+    W.Al = W.Ab + 4 * n;
+    double* cur = reinterpret_cast<double*>(take(s4));
+    double* nxt = reinterpret_cast<double*>(take(s4));
+    W.cellw = reinterpret_cast<double*>(take(cellb));
+    W.facew = reinterpret_cast<double*>(take(faceb));
+    W.work_bytes = cellb + faceb;  // contiguous
+    W.sws = swsb ? take(swsb) : nullptr;
+    W.sbits = reinterpret_cast<unsigned long long*>(take(align_up(4 * sizeof(unsigned long long))));
+    W.Aspeed = reinterpret_cast<double*>(W.sbits + 2);
+    W.J = reinterpret_cast<double*>(W.sbits + 3);
+    W.cells = reinterpret_cast<int64_t*>(take(gcb));
+    W.data = reinterpret_cast<double*>(take(gdb));
+    // Ab/Al: 2*s4 holds 8n doubles only when s4 has no padding between the halves
+    int rc = HSGN_OK;
+    cudaError_t e = cudaSuccess;
+    auto chk = [&](cudaError_t x) { if (x != cudaSuccess && e == cudaSuccess) e = x; };
+    if (n_gauges > 0) {
+        chk(cudaMemcpyAsync(W.cells, gauge_cells, (size_t)n_gauges * sizeof(int64_t),
+                            cudaMemcpyHostToDevice, st));
+        chk(cudaMemcpyAsync(W.data, gauge_data, (size_t)n_gauges * n_steps * sizeof(double),
+                            cudaMemcpyDefault, st));
+    }
+    chk(cudaMemsetAsync(W.J, 0, sizeof(double), st));
+    // forward: checkpoints every K steps, the misfit after every step
+    for (int k = 0; k < 4; ++k)
+        chk(cudaMemcpyAsync(cur + k * n, H->U[k], n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    const unsigned gg = (unsigned)((n_gauges + 255) / 256);
+    for (int64_t s = 0; s < n_steps && e == cudaSuccess; ++s) {
+        if (s % W.K == 0)
+            chk(cudaMemcpyAsync(W.ck + (size_t)(s / W.K) * (s4 / sizeof(double)), cur,
+                                4 * n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+        chk(adj_forward_step(H, W, cur, nxt, dt, st));
+        if (n_gauges > 0)
+            k_adj_gauges<<<gg, 256, 0, st>>>(n_gauges, W.cells, W.data + s * n_gauges, nxt, dt,
+                                             W.J, nullptr);
+        std::swap(cur, nxt);
+    }
+    for (int k = 0; k < 4 && e == cudaSuccess; ++k)
+        chk(cudaMemcpyAsync(H->U[k], cur + k * n, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    // reverse, one segment at a time
+    chk(cudaMemsetAsync(W.Ua, 0, 4 * n * sizeof(double), st));
+    if (grad_bathymetry) chk(cudaMemsetAsync(grad_bathymetry, 0, n * sizeof(double), st));
+    const size_t sd = s4 / sizeof(double);
+    for (int64_t cix = W.nck - 1; cix >= 0 && e == cudaSuccess; --cix) {
+        const int64_t s0 = cix * W.K, s1 = std::min(n_steps, s0 + W.K);
+        chk(cudaMemcpyAsync(W.seg, W.ck + (size_t)cix * sd, 4 * n * sizeof(double),
+                            cudaMemcpyDeviceToDevice, st));
+        for (int64_t j = 0; j < s1 - s0 && e == cudaSuccess; ++j)
+            chk(adj_forward_step(H, W, W.seg + (size_t)j * sd, W.seg + (size_t)(j + 1) * sd, dt, st));
+        for (int64_t s = s1 - 1; s >= s0 && e == cudaSuccess; --s) {
+            const double* Uafter = W.seg + (size_t)(s - s0 + 1) * sd;
+            if (n_gauges > 0)
+                k_adj_gauges<<<gg, 256, 0, st>>>(n_gauges, W.cells, W.data + s * n_gauges, Uafter,
+                                                 dt, nullptr, W.Ua);
+            chk(adj_step(H, W, W.seg + (size_t)(s - s0) * sd, dt, grad_bathymetry, st));
+        }
+    }
+    if (grad_state)
+        for (int k = 0; k < 4 && e == cudaSuccess; ++k)
+            if (grad_state[k])
+                chk(cudaMemcpyAsync(grad_state[k], W.Ua + k * n, n * sizeof(double),
+                                    cudaMemcpyDeviceToDevice, st));
+    chk(cudaMemcpyAsync(misfit, W.J, sizeof(double), cudaMemcpyDeviceToHost, st));
+    chk(refresh_speed(H, st));
+    if (e == cudaSuccess) e = cudaGetLastError();
+    if (e == cudaSuccess) rc = read_error(H, st);  // synchronises
+    else rc = HSGN_ERR_CUDA;
+    cudaStreamSynchronize(st);
+    cudaFree(W.mem);
+    return rc;
 }
 
 int hsgn_create_batched(int32_t count, const int64_t* n, const double* x_left,

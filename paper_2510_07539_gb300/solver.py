@@ -73,7 +73,7 @@ def load():
         "hsgn_check": [_P, _P],
         "hsgn_suggest_dt": [_P, _D, _D, ctypes.POINTER(_D), _P],
         "hsgn_stage": [_P, ctypes.POINTER(_P), ctypes.POINTER(_P), _D, _D, ctypes.POINTER(_P), _P],
-        "hsgn_adjoint": [_P, _D, _I64, _I64, _P, _P, _P, _P, _P],
+        "hsgn_adjoint": [_P, _D, _I64, _I64, _P, _P, _I64, _P, _P, _P, _P],
         "hsgn_tridiag_workspace_bytes": [_I64, ctypes.POINTER(ctypes.c_size_t)],
         "hsgn_create_batched": [ctypes.c_int32, _P, _P, _P, _P, _D, ctypes.c_int32, ctypes.c_int32,
                                 ctypes.POINTER(_P)],
@@ -207,6 +207,54 @@ class Solver:
         _check(_lib.hsgn_stage(self._h, b, l_, float(tau), float(speed), o, _stream(stream)),
                "hsgn_stage")
         return tuple(out)
+
+    def adjoint(self, dt: float, n_steps: int, gauge_cells, gauge_data, checkpoint_every: int = 100,
+                stream=None):
+        """Gauge misfit J of n_steps steps from the current state and its gradient
+        (hsgn_adjoint): returns (J, [dJ/dh0, dJ/dq0, dJ/dm0, dJ/dr0], dJ/db); the
+        state is left after the last step."""
+        import numpy as np
+        cells = np.ascontiguousarray(np.asarray(gauge_cells, dtype=np.int64))
+        data = gauge_data if isinstance(gauge_data, torch.Tensor) else torch.as_tensor(
+            np.asarray(gauge_data, dtype=np.float64))
+        data = data.to(torch.float64).contiguous()
+        if data.numel() != n_steps * cells.size:
+            raise ValueError("gauge_data must hold n_steps x n_gauges values")
+        dev = torch.device("cuda", torch.cuda.current_device())
+        grads = [torch.empty(self.n, dtype=torch.float64, device=dev) for _ in range(4)]
+        gb = torch.empty(self.n, dtype=torch.float64, device=dev)
+        arr = _P * 4
+        g4 = arr(*(_ptr(t) for t in grads))
+        J = ctypes.c_double()
+        self._keep = (cells, data)
+        _check(_lib.hsgn_adjoint(self._h, float(dt), int(n_steps), int(cells.size),
+                                 cells.ctypes.data_as(ctypes.c_void_p), _ptr(data),
+                                 int(checkpoint_every), g4, _ptr(gb), ctypes.byref(J),
+                                 _stream(stream)), "hsgn_adjoint")
+        return J.value, grads, gb
+
+
+class GaugeMisfit(torch.autograd.Function):
+    """J(h0, q0, m0, r0, b) = 1/2 sum_s sum_g (h_g^s - d_{s,g})^2 dt over n_steps
+    steps of the paper's scheme in the well-balanced FP64 form, with its exact
+    discrete gradient (hsgn_adjoint) for backward. Inputs are float64 CUDA
+    tensors of n cells; b is the bottom."""
+
+    @staticmethod
+    def forward(ctx, h0, q0, m0, r0, b, x_left, x_right, bc, lam, dt, n_steps, gauge_cells,
+                gauge_data, checkpoint_every=100):
+        n = h0.numel()
+        with Solver(n, x_left, x_right, bc, lam=lam, flags=FLAG_WELL_BALANCED,
+                    bathymetry=b.detach()) as s:
+            s.set_state(*(t.detach().contiguous() for t in (h0, q0, m0, r0)))
+            J, grads, gb = s.adjoint(dt, n_steps, gauge_cells, gauge_data, checkpoint_every)
+        ctx.save_for_backward(*grads, gb)
+        return torch.tensor(J, dtype=torch.float64, device=h0.device)
+
+    @staticmethod
+    def backward(ctx, gJ):
+        gh, gq, gm, gr, gb = ctx.saved_tensors
+        return (gJ * gh, gJ * gq, gJ * gm, gJ * gr, gJ * gb) + (None,) * 9
 
 
 def tridiag_workspace_bytes(n: int) -> int:

@@ -234,10 +234,12 @@ def test_device_errors_are_reported():
             s.step(float("nan"))
 
 
-def test_adjoint_reports_unimplemented():
+def test_adjoint_needs_the_well_balanced_form():
+    # the adjoint exists for the FP64 bottom form only
     with S().Solver(16, 0.0, 1.6, 0, lam=1.0) as s:
-        rc = S().load().hsgn_adjoint(s._h, 0.1, 1, 0, None, None, None, None, None)
-        assert rc == 6
+        with pytest.raises(S().HsgnError) as e:
+            s.adjoint(0.01, 2, [3], np.zeros(2))
+        assert e.value.code == 6
 
 
 # --------------------------------------------------------------------------
