@@ -90,6 +90,14 @@ struct FusedParams {
     const double* speed;            // global Rusanov speed of the step
     double* speed_next;             // max |u^{n+1}|
     unsigned* err;
+    // a batch of independent instances (batched != 0): tile b belongs to instance
+    // tile_inst[b]; for that instance inst[] gives the packed cell offset, n, dx,
+    // lambda, dt, its tile rows (`base`), tile count (`P`) and first tile (`blk0`);
+    // speed / speed_next are then per-instance arrays. The fields n, S, tau and
+    // the constants derived from it above are used for a single instance only.
+    int32_t batched;
+    const InstInfo* inst;
+    const int32_t* tile_inst;
 };
 
 // Window of tile p: tile rows [t0, t0 + sp); window rows [wl, wl + W) (global,
@@ -202,17 +210,48 @@ __global__ void __launch_bounds__(T, 4) k_mixed_fused(const FusedParams p) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     auto& sm = *reinterpret_cast<FusedShared<T, M, HW>*>(smem_raw);
     const int tid = threadIdx.x;
-    const int64_t n = p.n;
-    const Window win = window_of<BC>(blockIdx.x, n, p.S, HW);
+    // the instance of this tile: its size, offsets, constants and speeds
+    int64_t n = p.n, cell0 = 0, face0 = 0, tile = blockIdx.x;
+    int S = p.S;
+    float c_tau = p.tau, c_lam = p.lam, c_tdx = p.tdx, c_fq = p.fq, c_Cc = p.Cc, c_fd = p.fd;
+    float c_lt2 = p.lt2, c_ltau = p.ltau;
+    const double* spd_in = p.speed;
+    double* spd_out = p.speed_next;
+    if (p.batched) {
+        const int k = p.tile_inst[blockIdx.x];
+        const InstInfo I = p.inst[k];
+        n = I.n;
+        S = (int)I.base;
+        tile = blockIdx.x - I.blk0;
+        cell0 = I.cell0;
+        face0 = I.cell0 + k;  // instance k's n+1 faces follow those of instances < k
+        // tau = gamma dt, gamma = 1 - 1/sqrt(2) (Sec. 3.2), rounded as for one instance
+        const double tau = (1.0 - 1.0 / sqrt(2.0)) * I.dt;
+        c_tau = (float)tau;
+        c_lam = (float)I.lam;
+        c_tdx = (float)(tau / I.dx);
+        c_fq = (float)(tau / (2.0 * I.dx));
+        c_Cc = (float)(tau * tau / (I.dx * I.dx));
+        c_fd = (float)(I.lam * tau * tau / (I.dx * I.dx));
+        c_lt2 = (float)(I.lam * tau * tau);
+        c_ltau = (float)(I.lam * tau);
+        spd_in = p.speed + k;
+        spd_out = p.speed_next + k;
+    }
+    const Window win = window_of<BC>(tile, n, S, HW);
     const int W = win.W;
     const int64_t wl = win.wl;
     const bool two = p.stage == 2;
     const float wl1 = p.wl1, wb1 = p.wb1;
-    const float2* __restrict__ U0 = p.U[0];
-    const float2* __restrict__ U1 = p.U[1];
-    const float2* __restrict__ U2 = p.U[2];
-    const float2* __restrict__ U3 = p.U[3];
-    const float* __restrict__ G1 = p.G1;
+    const float2* __restrict__ U0 = p.U[0] + cell0;
+    const float2* __restrict__ U1 = p.U[1] + cell0;
+    const float2* __restrict__ U2 = p.U[2] + cell0;
+    const float2* __restrict__ U3 = p.U[3] + cell0;
+    const float* __restrict__ G1 = p.G1 + face0;
+    float* const G1w = p.G1 + face0;
+    float* const dq1p = p.dq1 + cell0;
+    float* const dm1p = p.dm1 + cell0;
+    float* const dr1p = p.dr1 + cell0;
     // G1 index of the face left of cell i: periodic face -1/2 is face n-1/2,
     // which only the last tile writes
     auto lf = [&](int64_t i) { return (BC == BC_PERIODIC && i == 0) ? n : i; };
@@ -220,7 +259,7 @@ __global__ void __launch_bounds__(T, 4) k_mixed_fused(const FusedParams p) {
         sm.kmax = 0u;
         sm.kmin = 0x7F7FFFFFu;
     }
-    if (p.track_speed && p.stage == 1 && blockIdx.x == 0 && tid == 0) *p.speed_next = 0.0;
+    if (p.track_speed && p.stage == 1 && tile == 0 && tid == 0) *spd_out = 0.0;
 
     // ---- 0. window cells -3 .. W+2 (index c + 3)
     constexpr int NL = (Gm::R + 6 + T - 1) / T;
@@ -239,11 +278,11 @@ __global__ void __launch_bounds__(T, 4) k_mixed_fused(const FusedParams p) {
             if (two) {
                 const float g0 = __ldg(G1 + lf(gi)), g1 = __ldg(G1 + gi + 1);
                 const float g2 = __ldg(G1 + lf(gn)), g3 = __ldg(G1 + gn + 1);
-                dq1 = __ldg(p.dq1 + gi);
-                dm1 = __ldg(p.dm1 + gi);
-                dr1 = __ldg(p.dr1 + gi);
-                dq1n = __ldg(p.dq1 + gn);
-                dm1n = __ldg(p.dm1 + gn);
+                dq1 = __ldg(dq1p + gi);
+                dm1 = __ldg(dm1p + gi);
+                dr1 = __ldg(dr1p + gi);
+                dq1n = __ldg(dq1p + gn);
+                dm1n = __ldg(dm1p + gn);
                 dh1 = g0 - g1;
                 dh1n = g2 - g3;
             }
@@ -266,8 +305,8 @@ __global__ void __launch_bounds__(T, 4) k_mixed_fused(const FusedParams p) {
     }
     __syncthreads();
 
-    const float tau = p.tau, lam = p.lam, g = p.g;
-    const float gspeed = p.local_speed ? 0.f : (float)(*p.speed);
+    const float tau = c_tau, lam = c_lam, g = p.g;
+    const float gspeed = p.local_speed ? 0.f : (float)(*spd_in);
     unsigned bad = 0;
 
     // ---- 1. Rusanov fluxes of U_l at faces f = -2 .. W (index f + 2), Sec. 4.1.
@@ -315,7 +354,7 @@ __global__ void __launch_bounds__(T, 4) k_mixed_fused(const FusedParams p) {
     // ---- 2. increments and coefficients at cells c = -1 .. W (index c + 1):
     //         r^dag = r_b + dr' + lambda tau, m^dag = m_b + dm' + lambda tau^2, q^dag = q_b + dq
     constexpr int NCL = (Gm::R + 2 + T - 1) / T;
-    const float lt2 = p.lt2, tdx = p.tdx, Cc = p.Cc;
+    const float lt2 = c_lt2, tdx = c_tdx, Cc = c_Cc;
     float dq_[NCL], dm_[NCL], dr_[NCL], be_[NCL], de_[NCL];
     float kloc = 0.f, kmin = 3.0e38f;
 #pragma unroll
@@ -396,7 +435,7 @@ __global__ void __launch_bounds__(T, 4) k_mixed_fused(const FusedParams p) {
     //         which makes the end rows the Neumann rows) and right-hand sides d_i
     //         (i = 0 .. W-1, at pd(i)); cell c of the per-cell arrays at c+1,
     //         the face right of cell c of the difference arrays at c+3
-    const float fq = p.fq, fd = p.fd;
+    const float fq = c_fq, fd = c_fd;
     float* const BF = sm.rb;
     float* const RD = sm.mb;
     for (int j = tid; j < W + 1; j += T) {
@@ -514,7 +553,7 @@ __global__ void __launch_bounds__(T, 4) k_mixed_fused(const FusedParams p) {
         Gt[j] = G;
         if (!two) {
             const int64_t gf = win.t0 + j;  // G1 index of this face (face i+1/2 at i+1)
-            if (j > 0 || (BC == BC_TRANSMISSIVE && win.t0 == 0)) p.G1[gf] = G;
+            if (j > 0 || (BC == BC_TRANSMISSIVE && win.t0 == 0)) G1w[gf] = G;
         }
     }
     __syncthreads();
@@ -546,7 +585,7 @@ __global__ void __launch_bounds__(T, 4) k_mixed_fused(const FusedParams p) {
         if (two) {
             g1l = G1[lf(i)];
             g1r = G1[i + 1];
-            const float dh1 = g1l - g1r, dm1 = p.dm1[i];
+            const float dh1 = g1l - g1r, dm1 = dm1p[i];
             hbf = fmaf(wb1, dh1, hf);
             P0 = fmaf(wb1, fmaf(dh1, fmaf(wb1, dh1, 2.f * hf), -dm1), P0);
         }
@@ -554,26 +593,26 @@ __global__ void __launch_bounds__(T, 4) k_mixed_fused(const FusedParams p) {
         const float P = fmaf(dhC, 2.f * hbf + dhC, P0);  // hbar^2 - m_b
         const float E = P - dmC;                          // hbar^2 - m^
         const float h2 = hbar * hbar;
-        const float iDen = rcpa(h2 + p.lt2);
-        const float dR = fmaf(p.ltau * E, iDen, dra[r + 1]);
+        const float iDen = rcpa(h2 + c_lt2);
+        const float dR = fmaf(c_ltau * E, iDen, dra[r + 1]);
         const float dM = P - E * h2 * iDen;
         unsigned b2 = 0;
         if (!pos_finite(hbar)) b2 |= HSGN_DEV_ERR_DEPTH;
         if (!isfinite(dQ) || !isfinite(dM) || !isfinite(dR)) b2 |= HSGN_DEV_ERR_NONFINITE;
         bad |= b2;
         if (!two) {
-            p.dq1[i] = dQ;
-            p.dm1[i] = dM;
-            p.dr1[i] = dR;
+            dq1p[i] = dQ;
+            dm1p[i] = dM;
+            dr1p[i] = dR;
         } else {
             const float Tp = fmaf(wb1, g1r, Gt[t + 1]);
             const float Tm = fmaf(wb1, g1l, Gt[t]);
             float d, de;
             two_sum(Tm, -Tp, d, de);  // exact Tm - Tp
-            p.out[0][i] = df_add(h0, d, de);
-            p.out[1][i] = df_add(U1[i], fmaf(wb1, p.dq1[i], dQ), 0.f);
-            p.out[2][i] = df_add(m0, fmaf(wb1, p.dm1[i], dM), 0.f);
-            p.out[3][i] = df_add(U3[i], fmaf(wb1, p.dr1[i], dR), 0.f);
+            p.out[0][cell0 + i] = df_add(h0, d, de);
+            p.out[1][cell0 + i] = df_add(U1[i], fmaf(wb1, dq1p[i], dQ), 0.f);
+            p.out[2][cell0 + i] = df_add(m0, fmaf(wb1, dm1p[i], dM), 0.f);
+            p.out[3][cell0 + i] = df_add(U3[i], fmaf(wb1, dr1p[i], dR), 0.f);
             if (p.track_speed && !b2) umax = fmaxf(umax, fabsf((sm.qb[r + 3] + dQ) / hbar));
         }
     }
@@ -582,7 +621,7 @@ __global__ void __launch_bounds__(T, 4) k_mixed_fused(const FusedParams p) {
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) umax = fmaxf(umax, __shfl_xor_sync(0xffffffffu, umax, o));
         if ((tid & 31) == 0 && umax > 0.f)
-            atomicMax(reinterpret_cast<unsigned long long*>(p.speed_next),
+            atomicMax(reinterpret_cast<unsigned long long*>(spd_out),
                       (unsigned long long)__double_as_longlong(f64_of(umax)));
     }
 }
@@ -634,6 +673,49 @@ __global__ void k_speeds_df(int64_t n, const float2* h, const float2* q, const f
         if (nm > 0.0)
             atomicMax(reinterpret_cast<unsigned long long*>(out + 1),
                       (unsigned long long)__double_as_longlong(nm));
+    }
+}
+
+// k_speeds_batched (hsgn_mixed.cuh) for a batch held as double-float pairs:
+// per-instance max |u| and max nu, one CTA per instance.
+__global__ void __launch_bounds__(256) k_speeds_batched_df(const InstInfo* inst, const float2* h,
+                                                           const float2* q, const float2* m,
+                                                           double g, double* out_u, double* out_nu,
+                                                           unsigned* err) {
+    __shared__ double ru[8], rn[8];
+    const InstInfo I = inst[blockIdx.x];
+    double um = 0.0, nm = 0.0;
+    bool bad = false;
+    for (int64_t i = I.cell0 + threadIdx.x; i < I.cell0 + I.n; i += blockDim.x) {
+        const float2 hv = h[i], qv = q[i], mv = m[i];
+        const double hh = (double)hv.x + (double)hv.y;
+        if (!pos_finite(hh)) {
+            bad = true;
+            continue;
+        }
+        const double u = fabs(((double)qv.x + (double)qv.y) / hh);
+        const double e = ((double)mv.x + (double)mv.y) / (hh * hh);
+        um = fmax(um, u);
+        nm = fmax(nm, u + sqrt(g * hh + (I.lam / 3.0) * e * e));
+    }
+    if (bad) flag_error(err, HSGN_DEV_ERR_DEPTH);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        um = fmax(um, __shfl_xor_sync(0xffffffffu, um, o));
+        nm = fmax(nm, __shfl_xor_sync(0xffffffffu, nm, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        ru[threadIdx.x >> 5] = um;
+        rn[threadIdx.x >> 5] = nm;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) {
+            um = fmax(um, ru[w]);
+            nm = fmax(nm, rn[w]);
+        }
+        out_u[blockIdx.x] = um;
+        if (out_nu) out_nu[blockIdx.x] = nm;
     }
 }
 

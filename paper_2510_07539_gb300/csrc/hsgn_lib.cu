@@ -169,6 +169,9 @@ struct hsgn_s {
     int32_t* blk_inst = nullptr;     // device table
     double* speeds = nullptr;        // per-instance Rusanov speed (device)
     double* speeds_tmp = nullptr;    // 2 per instance (device), for suggest_dt
+    double* speeds_next = nullptr;   // windowed batch: per-instance speed while the state is in V
+    int32_t* tile_inst = nullptr;    // windowed batch: instance of every tile (device)
+    int64_t total_tiles = 0;
     std::vector<InstInfo> inst_h;    // host copy
     float *mblk = nullptr, *ms_ = nullptr;
     unsigned* err = nullptr;
@@ -191,7 +194,10 @@ bool local_speed(const hsgn_s* H) { return (H->flags & HSGN_RUSANOV_LOCAL) != 0;
 // The buffer holding the current state, and the global Rusanov speed of the
 // state in buffer `which` (0: U, 1: V).
 double* const* state(const hsgn_s* H) { return H->cur ? H->V : H->U; }
-double* speed_of(const hsgn_s* H, int which) { return H->spd + (which ? 4 : 0); }
+double* speed_of(const hsgn_s* H, int which) {
+    if (H->batched) return which ? H->speeds_next : H->speeds;  // per instance
+    return H->spd + (which ? 4 : 0);
+}
 
 cudaEvent_t take_event(hsgn_s* H) {
     if (!H->ev_pool.empty()) {
@@ -440,7 +446,11 @@ cudaError_t launch_stage_fused(hsgn_s* H, int stage, double tau, cudaStream_t st
     p.speed = speed_of(H, H->cur);
     p.speed_next = speed_of(H, 1 - H->cur);
     p.err = H->err;
-    const unsigned P = (unsigned)((H->n + H->tileS - 1) / H->tileS);
+    p.batched = H->batched ? 1 : 0;
+    p.inst = H->inst;
+    p.tile_inst = H->tile_inst;
+    const unsigned P = H->batched ? (unsigned)H->total_tiles
+                                  : (unsigned)((H->n + H->tileS - 1) / H->tileS);
     const size_t smem = sizeof(FusedShared<FT, FM, FHW>);
     {
         ProfScope ps(H, HSGN_PROF_ASSEMBLE, st);
@@ -597,8 +607,16 @@ void launch_speeds(hsgn_s* H, double* out, cudaStream_t st) {
 // Recompute the global Rusanov speed max |u| of the current state.
 cudaError_t refresh_speed(hsgn_s* H, cudaStream_t st) {
     if (H->batched) {
-        k_speeds_batched<<<(unsigned)H->count, 256, 0, st>>>(H->inst, H->U[0], H->U[1], H->U[2],
-                                                             H->g, H->speeds, nullptr, H->err);
+        if (H->windowed) {
+            double* const* U = state(H);
+            k_speeds_batched_df<<<(unsigned)H->count, 256, 0, st>>>(
+                H->inst, reinterpret_cast<const float2*>(U[0]), reinterpret_cast<const float2*>(U[1]),
+                reinterpret_cast<const float2*>(U[2]), H->g, speed_of(H, H->cur), nullptr, H->err);
+        } else {
+            k_speeds_batched<<<(unsigned)H->count, 256, 0, st>>>(H->inst, H->U[0], H->U[1],
+                                                                 H->U[2], H->g, H->speeds, nullptr,
+                                                                 H->err);
+        }
         return cudaGetLastError();
     }
     double* out = speed_of(H, H->cur);
@@ -1269,32 +1287,44 @@ int hsgn_create_batched(int32_t count, const int64_t* n, const double* x_left,
     if (count < 1 || !n || !x_left || !x_right || !lambda) return HSGN_ERR_INVALID_ARG;
     if (bc != HSGN_BC_PERIODIC && bc != HSGN_BC_TRANSMISSIVE) return HSGN_ERR_INVALID_ARG;
     if (!(g > 0.0) || !std::isfinite(g)) return HSGN_ERR_INVALID_ARG;
-    if (flags & ~(int32_t)(HSGN_RUSANOV_LOCAL | HSGN_MIXED)) return HSGN_ERR_UNIMPLEMENTED;
+    if (flags & ~(int32_t)(HSGN_RUSANOV_LOCAL | HSGN_MIXED | HSGN_EXACT_SOLVE))
+        return HSGN_ERR_UNIMPLEMENTED;
+    const bool windowed = !(flags & HSGN_EXACT_SOLVE);
     std::vector<InstInfo> info((size_t)count);
     std::vector<int32_t> binst;
     int64_t cells = 0;
     int64_t blocks = 0;
     for (int32_t k = 0; k < count; ++k) {
         const int64_t nk = n[k];
-        if (nk < 3 || nk > (int64_t)SEP_ROWS * AS) return HSGN_ERR_INVALID_ARG;
+        if (nk < 3 || (!windowed && nk > (int64_t)SEP_ROWS * AS) || nk > ((int64_t)1 << 31))
+            return HSGN_ERR_INVALID_ARG;
         if (!(x_right[k] > x_left[k]) || !std::isfinite(x_left[k]) || !std::isfinite(x_right[k]))
             return HSGN_ERR_INVALID_ARG;
         if (!(lambda[k] >= 0.0) || !std::isfinite(lambda[k])) return HSGN_ERR_INVALID_ARG;
-        const BlockSplit s = make_split(nk, AS);
         InstInfo& I = info[(size_t)k];
         I.cell0 = cells;
         I.n = nk;
-        I.base = s.base;
-        I.P = s.P;
-        I.rem = s.rem;
         I.blk0 = (int32_t)blocks;
         I.pad = 0;
         I.dx = (x_right[k] - x_left[k]) / (double)nk;
         I.lam = lambda[k];
         I.dt = 0.0;
-        for (int32_t b = 0; b < s.P; ++b) binst.push_back(k);
+        if (windowed) {
+            // tiles of the windowed stage: base = tile rows, P = tiles, blk0 = first tile
+            const int64_t smax = FusedGeom<FT, FM, FHW>::S;
+            const int64_t tiles = (nk + smax - 1) / smax;
+            I.base = (nk + tiles - 1) / tiles;
+            I.P = (int32_t)tiles;
+            I.rem = 0;
+        } else {
+            const BlockSplit s = make_split(nk, AS);
+            I.base = s.base;
+            I.P = s.P;
+            I.rem = s.rem;
+        }
+        for (int32_t b = 0; b < I.P; ++b) binst.push_back(k);
         cells += nk;
-        blocks += s.P;
+        blocks += I.P;
     }
     hsgn_s* H = new (std::nothrow) hsgn_s;
     if (!H) return HSGN_ERR_OUT_OF_MEMORY;
@@ -1303,8 +1333,10 @@ int hsgn_create_batched(int32_t count, const int64_t* n, const double* x_left,
     H->flags = flags | HSGN_MIXED;
     H->mixed = true;
     H->batched = true;
+    H->windowed = windowed;
     H->count = count;
-    H->total_blocks = blocks;
+    H->total_blocks = windowed ? 0 : blocks;
+    H->total_tiles = windowed ? blocks : 0;
     H->g = g;
     H->lam = 0.0;
     H->dx = 0.0;
@@ -1312,11 +1344,12 @@ int hsgn_create_batched(int32_t count, const int64_t* n, const double* x_left,
     cudaGetDevice(&H->device);
     const size_t vec = align_up(cells * sizeof(double));
     const size_t fvec = align_up((cells + count) * sizeof(float));
-    const size_t recb = align_up(3 * cells * sizeof(float4));
-    size_t total = 4 * vec + 4 * fvec + recb;
-    total += align_up(BLK_STRIDE * blocks * sizeof(float)) + align_up(blocks * sizeof(float));
+    const size_t recb = windowed ? 0 : align_up(3 * cells * sizeof(float4));
+    size_t total = (windowed ? 8 : 4) * vec + 4 * fvec + recb;
+    if (!windowed)
+        total += align_up(BLK_STRIDE * blocks * sizeof(float)) + align_up(blocks * sizeof(float));
     total += align_up(count * sizeof(InstInfo)) + align_up(blocks * sizeof(int32_t));
-    total += 3 * align_up(count * sizeof(double));
+    total += 4 * align_up(count * sizeof(double));
     total += align_up(8 * sizeof(double)) + align_up(sizeof(unsigned));
     if (cudaMalloc(&H->mem, total) != cudaSuccess) {
         cudaGetLastError();
@@ -1330,17 +1363,23 @@ int hsgn_create_batched(int32_t count, const int64_t* n, const double* x_left,
         return r;
     };
     for (int k = 0; k < 4; ++k) H->U[k] = reinterpret_cast<double*>(take(vec));
+    if (windowed)
+        for (int k = 0; k < 4; ++k) H->V[k] = reinterpret_cast<double*>(take(vec));
     H->G1 = reinterpret_cast<float*>(take(fvec));
     H->dq1 = reinterpret_cast<float*>(take(fvec));
     H->dm1 = reinterpret_cast<float*>(take(fvec));
     H->dr1 = reinterpret_cast<float*>(take(fvec));
-    H->mrec = reinterpret_cast<float4*>(take(recb));
-    H->mblk = reinterpret_cast<float*>(take(align_up(BLK_STRIDE * blocks * sizeof(float))));
-    H->ms_ = reinterpret_cast<float*>(take(align_up(blocks * sizeof(float))));
+    if (!windowed) {
+        H->mrec = reinterpret_cast<float4*>(take(recb));
+        H->mblk = reinterpret_cast<float*>(take(align_up(BLK_STRIDE * blocks * sizeof(float))));
+        H->ms_ = reinterpret_cast<float*>(take(align_up(blocks * sizeof(float))));
+    }
     H->inst = reinterpret_cast<InstInfo*>(take(align_up(count * sizeof(InstInfo))));
     H->blk_inst = reinterpret_cast<int32_t*>(take(align_up(blocks * sizeof(int32_t))));
+    if (windowed) H->tile_inst = H->blk_inst;
     H->speeds = reinterpret_cast<double*>(take(align_up(count * sizeof(double))));
     H->speeds_tmp = reinterpret_cast<double*>(take(2 * align_up(count * sizeof(double))));
+    H->speeds_next = reinterpret_cast<double*>(take(align_up(count * sizeof(double))));
     H->spd = reinterpret_cast<double*>(take(align_up(8 * sizeof(double))));
     H->err = reinterpret_cast<unsigned*>(take(align_up(sizeof(unsigned))));
     cudaError_t e = cudaMemset(H->mem, 0, total);
@@ -1352,6 +1391,10 @@ int hsgn_create_batched(int32_t count, const int64_t* n, const double* x_left,
         e = set_smem(k_mixed_assemble<XT, XM, BC_PERIODIC>, sizeof(MixedShared<XT, XM>));
     if (e == cudaSuccess)
         e = set_smem(k_mixed_assemble<XT, XM, BC_TRANSMISSIVE>, sizeof(MixedShared<XT, XM>));
+    if (e == cudaSuccess)
+        e = set_smem(k_mixed_fused<FT, FM, FHW, BC_PERIODIC>, sizeof(FusedShared<FT, FM, FHW>));
+    if (e == cudaSuccess)
+        e = set_smem(k_mixed_fused<FT, FM, FHW, BC_TRANSMISSIVE>, sizeof(FusedShared<FT, FM, FHW>));
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&H->cap, cudaStreamNonBlocking);
     if (e != cudaSuccess) {
         cudaGetLastError();
@@ -1383,8 +1426,15 @@ int hsgn_batched_suggest_dt(hsgn_handle_t H, double cfl, double mcfl, double* dt
     const int32_t c = H->count;
     double* um = H->speeds_tmp;
     double* nm = H->speeds_tmp + align_up(c * sizeof(double)) / sizeof(double);
-    k_speeds_batched<<<(unsigned)c, 256, 0, st>>>(H->inst, H->U[0], H->U[1], H->U[2], H->g, um, nm,
-                                                  H->err);
+    if (H->windowed) {
+        double* const* U = state(H);
+        k_speeds_batched_df<<<(unsigned)c, 256, 0, st>>>(
+            H->inst, reinterpret_cast<const float2*>(U[0]), reinterpret_cast<const float2*>(U[1]),
+            reinterpret_cast<const float2*>(U[2]), H->g, um, nm, H->err);
+    } else {
+        k_speeds_batched<<<(unsigned)c, 256, 0, st>>>(H->inst, H->U[0], H->U[1], H->U[2], H->g, um,
+                                                      nm, H->err);
+    }
     if (cudaGetLastError() != cudaSuccess) return HSGN_ERR_CUDA;
     std::vector<double> hu((size_t)c), hn((size_t)c);
     if (cudaMemcpyAsync(hu.data(), um, c * sizeof(double), cudaMemcpyDeviceToHost, st) != cudaSuccess ||

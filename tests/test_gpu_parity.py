@@ -392,9 +392,15 @@ def batch_case(seed, count, n_min=64, n_max=3000):
     return insts, ns, xl, xr, lams
 
 
-def test_batched_equals_single_instance_mixed_bitwise():
-    insts, ns, xl, xr, lams = batch_case(11, 6)
-    with S().BatchedSolver(ns, xl, xr, lams) as B:
+@pytest.mark.parametrize("exact", [False, True])
+def test_batched_equals_single_instance_mixed_bitwise(exact):
+    # the batch runs the same kernels as single instances (windowed: one tile
+    # table for all instances; exact: one block table), so every instance
+    # evolves bitwise as it would alone; an odd step count checks that the
+    # windowed batch follows its two state buffers
+    insts, ns, xl, xr, lams = batch_case(11, 6, n_max=5000)
+    flags = S().FLAG_MIXED | (S().FLAG_EXACT_SOLVE if exact else 0)
+    with S().BatchedSolver(ns, xl, xr, lams, flags=flags) as B:
         packed = [np.concatenate([it.state[k] for it in insts]) for k in range(4)]
         B.set_state(*(dev(a) for a in packed))
         dts = B.suggest_dt(2.0, 0.5)
@@ -404,14 +410,16 @@ def test_batched_equals_single_instance_mixed_bitwise():
     for k_inst, it in enumerate(insts):
         o0, o1 = int(B.offsets[k_inst]), int(B.offsets[k_inst + 1])
         single = mixed_run(it.n, xl[k_inst], xr[k_inst], 0, it.lam, it.state, dts[k_inst], 5,
-                           exact=True)
+                           exact=exact)
         for k in range(4):
             np.testing.assert_array_equal(got[k][o0:o1], single[k])
 
 
-def test_batched_matches_oracle_per_instance():
+@pytest.mark.parametrize("exact", [False, True])
+def test_batched_matches_oracle_per_instance(exact):
     insts, ns, xl, xr, lams = batch_case(12, 12, n_min=256, n_max=8192)
-    with S().BatchedSolver(ns, xl, xr, lams) as B:
+    flags = S().FLAG_MIXED | (S().FLAG_EXACT_SOLVE if exact else 0)
+    with S().BatchedSolver(ns, xl, xr, lams, flags=flags) as B:
         packed = [np.concatenate([it.state[k] for it in insts]) for k in range(4)]
         B.set_state(*(dev(a) for a in packed))
         dts = B.suggest_dt(4.0, 0.5)
