@@ -169,6 +169,31 @@ __host__ __device__ __forceinline__ int64_t cell_at(int64_t x, int64_t n) {
     return x < 0 ? 0 : (x >= n ? n - 1 : x);
 }
 
+// Cells read by the load phase for window cell index j (window cell j - 3):
+// the cell itself (gi) and its right neighbour (gn), j = 0 .. W + 5. A window
+// whose cells -3 .. W + 3 all lie in [0, n) (`inner`) indexes them directly.
+__host__ __device__ inline bool inner_window(int64_t wl, int W, int64_t n) {
+    return wl - 3 >= 0 && wl + W + 3 < n;
+}
+
+template <int BC>
+__host__ __device__ __forceinline__ void load_cells(bool inner, int64_t wl, int j, int64_t n,
+                                                    int64_t& gi, int64_t& gn) {
+    gi = inner ? wl - 3 + j : cell_at<BC>(wl - 3 + j, n);
+    gn = inner ? gi + 1 : cell_at<BC>(wl - 2 + j, n);
+}
+
+// Tile rows of an n-row grid for a kernel of tiles of at most smax rows:
+// equal tiles, as many as fill `slots` co-resident CTAs in whole waves.
+__host__ inline int64_t fused_tile_rows(int64_t n, int64_t smax, int64_t slots) {
+    const int64_t pmin = (n + smax - 1) / smax;
+    if (pmin >= slots) {
+        const int64_t waves = (pmin + slots - 1) / slots;
+        return (n + waves * slots - 1) / (waves * slots);
+    }
+    return (n + pmin - 1) / pmin;
+}
+
 // Capacity of the fused kernel: T threads, M rows per thread, overlap HW.
 template <int T, int M, int HW>
 struct FusedGeom {
@@ -264,13 +289,13 @@ __global__ void __launch_bounds__(T, 4) k_mixed_fused(const FusedParams p) {
     // ---- 0. window cells -3 .. W+2 (index c + 3)
     constexpr int NL = (Gm::R + 6 + T - 1) / T;
     // windows away from the domain ends read cells wl-3 .. wl+W+3 directly
-    const bool inner = wl - 3 >= 0 && wl + W + 3 <= n;
+    const bool inner = inner_window(wl, W, n);
 #pragma unroll
     for (int it = 0; it < NL; ++it) {
         const int j = tid + it * T;
         if (j < W + 6) {
-            const int64_t gi = inner ? wl - 3 + j : cell_at<BC>(wl - 3 + j, n);
-            const int64_t gn = inner ? gi + 1 : cell_at<BC>(wl - 2 + j, n);
+            int64_t gi, gn;
+            load_cells<BC>(inner, wl, j, n, gi, gn);
             const float2 h0 = __ldg(U0 + gi), q0 = __ldg(U1 + gi);
             const float2 m0 = __ldg(U2 + gi), rr0 = __ldg(U3 + gi);
             const float2 h1 = __ldg(U0 + gn), q1 = __ldg(U1 + gn), m1 = __ldg(U2 + gn);

@@ -39,15 +39,6 @@ constexpr size_t kAlign = 256;
 // Tile rows of the windowed path: as few tiles of at most smax rows as
 // possible, evened out so that a grid larger than one wave of `slots`
 // resident CTAs ends in full waves.
-int64_t fused_tile_rows(int64_t n, int64_t smax, int64_t slots) {
-    const int64_t pmin = (n + smax - 1) / smax;
-    if (pmin >= slots) {
-        const int64_t waves = (pmin + slots - 1) / slots;
-        return (n + waves * slots - 1) / (waves * slots);
-    }
-    return (n + pmin - 1) / pmin;
-}
-
 constexpr size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 
 BlockSplit make_split(int64_t n, int64_t rows_per_block) {
@@ -1311,10 +1302,8 @@ int hsgn_create_batched(int32_t count, const int64_t* n, const double* x_left,
         I.dt = 0.0;
         if (windowed) {
             // tiles of the windowed stage: base = tile rows, P = tiles, blk0 = first tile
-            const int64_t smax = FusedGeom<FT, FM, FHW>::S;
-            const int64_t tiles = (nk + smax - 1) / smax;
-            I.base = (nk + tiles - 1) / tiles;
-            I.P = (int32_t)tiles;
+            I.base = fused_tile_rows(nk, FusedGeom<FT, FM, FHW>::S, 1);
+            I.P = (int32_t)((nk + I.base - 1) / I.base);
             I.rem = 0;
         } else {
             const BlockSplit s = make_split(nk, AS);

@@ -1,0 +1,121 @@
+// Host-side check of the windowed stage kernel's index arithmetic
+// (k_mixed_fused in hsgn_fused.cuh): every tile geometry the library launches,
+// single grids (tile rows for several co-resident CTA counts) and batch
+// instances (one CTA slot), both boundary conditions. It evaluates the same
+// __host__ __device__ helpers the kernel calls and checks that every global
+// cell index lies in [0, n), every shared-memory index within the arrays, that
+// tiles cover the grid once, that the rows kept from a window lie HW - 1 rows
+// or more inside it, and that the two tiles beside a face build the same
+// mini-window. Exit status 0 when every check passes.
+#include <cstdio>
+#include <cstdlib>
+#include "../paper_2510_07539_gb300/csrc/hsgn_fused.cuh"
+
+using namespace hsgn;
+constexpr int T = 256, M = 4, HW = 64;
+using G = FusedGeom<T, M, HW>;
+
+#define CHECK(c)                                                                               \
+    do {                                                                                       \
+        if (!(c)) {                                                                            \
+            printf("FAIL %s n=%lld S=%d p=%lld bc=%d line %d\n", #c, (long long)n, S,          \
+                   (long long)p, BC, __LINE__);                                                \
+            exit(1);                                                                           \
+        }                                                                                      \
+    } while (0)
+
+static long long checked_windows = 0;
+
+template <int BC>
+void check(int64_t n, int S) {
+    int64_t p = -1;
+    CHECK(S >= 1 && S <= G::S);
+    const int64_t P = (n + S - 1) / S;
+    int64_t covered = 0;
+    for (p = 0; p < P; ++p) {
+        ++checked_windows;
+        const Window w = window_of<BC>(p, n, S, HW);
+        CHECK(w.sp >= 1 && w.sp <= S);
+        CHECK(w.t0 == covered);
+        covered += w.sp;
+        CHECK(w.W >= 1 && w.W + 1 <= T * M);  // rows of the block solve, closing row included
+        CHECK(w.lo >= 0 && w.lo + w.sp <= w.W);
+        // load phase: j < W + 6, both cells in range on either path
+        CHECK(w.W + 6 <= G::NC);
+        const bool inner = inner_window(w.wl, w.W, n);
+        for (int j = 0; j < w.W + 6; ++j) {
+            int64_t gi, gn, ci, cn;
+            load_cells<BC>(inner, w.wl, j, n, gi, gn);
+            load_cells<BC>(false, w.wl, j, n, ci, cn);
+            CHECK(gi >= 0 && gi < n && gn >= 0 && gn < n);
+            CHECK(gi == ci && gn == cn);  // the direct path reads the cells the general one does
+            if (BC == BC_PERIODIC) CHECK(((w.wl - 3 + j) % n + n) % n == gi);
+        }
+        // padded stores: face couplings pd(j), j <= W; dh at pd(r + 1), r <= W
+        CHECK(pd(w.W + 1) < G::NC);
+        // back-substitution reads rows r - 1 .. r + 1 of the tile rows r
+        if (!(BC == BC_TRANSMISSIVE && w.lend)) CHECK(w.lo >= HW);
+        if (!(BC == BC_TRANSMISSIVE && w.rend)) CHECK(w.W - (w.lo + w.sp) >= HW);
+        CHECK(pd(w.lo + w.sp + 1) < G::NC && w.lo + w.sp + 3 < G::NC);
+        CHECK(w.t0 + w.sp <= n);
+        // mini-windows of the tile faces
+        const bool lface = !(BC == BC_TRANSMISSIVE && w.t0 == 0);
+        const bool rface = !(BC == BC_TRANSMISSIVE && w.t0 + w.sp == n);
+        for (int side = 0; side < 2; ++side) {
+            if (!(side == 0 ? lface : rface)) continue;
+            const int64_t tf = side == 0 ? w.t0 : w.t0 + w.sp;
+            const MiniWindow m = mini_of<BC>(tf, n, G::HB);
+            const int ms = (int)(m.ml - w.wl);
+            CHECK(ms >= 0 && ms + m.mw <= w.W);
+            CHECK(m.mw + 1 <= 32 * G::MB);
+            const int kr = (int)(tf - m.ml);
+            CHECK(kr - 1 >= 0 && kr < m.mw);
+            if (BC == BC_TRANSMISSIVE) {
+                if (m.lend) CHECK(m.ml == 0);
+                if (m.rend) CHECK(m.ml + m.mw == n);
+            }
+            // the tile on the other side of the face builds the same mini-window
+            const int64_t q = side == 0 ? (p == 0 ? P - 1 : p - 1) : (p + 1 == P ? 0 : p + 1);
+            const Window wq = window_of<BC>(q, n, S, HW);
+            const int64_t tq = side == 0 ? wq.t0 + wq.sp : wq.t0;
+            if (BC == BC_PERIODIC)
+                CHECK(((tq - tf) % n + n) % n == 0);
+            else
+                CHECK(tq == tf);
+            const MiniWindow mq = mini_of<BC>(tq, n, G::HB);
+            CHECK(mq.mw == m.mw && mq.lend == m.lend && mq.rend == m.rend);
+            if (BC == BC_PERIODIC) CHECK(((mq.ml - m.ml) % n + n) % n == 0);
+            const int msq = (int)(mq.ml - wq.wl);
+            CHECK(msq >= 0 && msq + mq.mw <= wq.W);
+        }
+    }
+    CHECK(covered == n);
+}
+
+template <int BC>
+void check_grid(int64_t n) {
+    for (int64_t slots : {1, 2, 152, 304, 456, 608}) check<BC>(n, (int)fused_tile_rows(n, G::S, slots));
+}
+
+int main() {
+    const int64_t big[] = {1000, 1278, 1279, 1280, 1281, 2557, 2558, 2559, 70001, 388800,
+                           388801, 1048576, 3000000, 16777216, 16777217};
+    for (int64_t n = 3; n <= 9000; ++n) {
+        check_grid<BC_PERIODIC>(n);
+        check_grid<BC_TRANSMISSIVE>(n);
+    }
+    for (int64_t n : big) {
+        check_grid<BC_PERIODIC>(n);
+        check_grid<BC_TRANSMISSIVE>(n);
+    }
+    // windows ending 3 or 4 cells before the domain end (the edge of the direct path)
+    for (int64_t k = 1; k <= 40; ++k)
+        for (int64_t e = 60; e <= 72; ++e) {
+            const int64_t n = k * G::S + e;
+            check<BC_PERIODIC>(n, G::S);
+            check<BC_TRANSMISSIVE>(n, G::S);
+        }
+    printf("R=%d S=%d HB=%d NC=%d windows=%lld\nall index checks passed\n", G::R, G::S, G::HB,
+           G::NC, checked_windows);
+    return 0;
+}
