@@ -114,8 +114,11 @@ enum {
                                  * depth rows and the momentum as face forces
                                  * linearised about U_l, so that a lake at rest
                                  * (u = 0, eta = h, w = 0, h + b constant) stays at
-                                 * rest. FP64 only (not with HSGN_MIXED), single
-                                 * instances only. */
+                                 * rest. FP64, or HSGN_MIXED on the windowed
+                                 * kernel (the bottom held as double-float pairs,
+                                 * the free-surface jumps taken from the pairs;
+                                 * HSGN_ERR_UNIMPLEMENTED with HSGN_EXACT_SOLVE);
+                                 * single instances only. */
 
 typedef struct {
     int64_t n;       /* number of cells, n >= 3 */

@@ -98,6 +98,7 @@ struct FusedParams {
     int32_t batched;
     const InstInfo* inst;
     const int32_t* tile_inst;
+    const float2* bathy;  // bottom b per cell as double-float pairs (bottom form only)
 };
 
 // Window of tile p: tile rows [t0, t0 + sp); window rows [wl, wl + W) (global,
@@ -217,23 +218,47 @@ __device__ __forceinline__ float rcpa(float x) { return rcp(x); }
 //   phase 3: rows: face couplings tau^2 beta_{f+1/2}/dx^2 -> rb, right-hand
 //            sides -> mb (both padded, read in the chunk mapping);
 //   phase 4: dh -> Dq (padded); face mass fluxes of the tile -> rb.
-template <int T, int M, int HW>
+// The bottom form (WB) reuses Dh for the jump of h_l - h_b at the face, Dm for
+// P_l = h_l^2 - m_l and then beta (hl keeps h_l), ml for the non-gravity part
+// of the pressure, mb for p~, and adds the free-surface jump Z (which becomes
+// the face force Psi in phase 3), the bottom jump Db, the bottom source Sb
+// and m_b - m_l = (w_b - w_l) dm1 taken from the increment (the single-
+// precision m_b and m_l round it away, and lambda alpha amplifies it).
+template <int NC, bool WB>
+struct FusedWb {
+    float Z[NC], Db[NC], Sb[NC], Mbl[NC];
+};
+template <int NC>
+struct FusedWb<NC, false> {};
+
+template <int T, int M, int HW, bool WB = false>
 struct FusedShared {
     static constexpr int NC = FusedGeom<T, M, HW>::NC;
     float hl[NC], ql[NC], ml[NC], rl[NC];
     float qb[NC], mb[NC], rb[NC];
     float Dh[NC], Dq[NC], Dm[NC];
     float X0[NC];
+    FusedWb<NC, WB> wb;
     SepShared<T, float> sep;
     float bnd[2][2];       // dh of the two rows at the left / right tile face (mini solves)
     unsigned kmax, kmin;   // bits of max / min tau^2 beta / dx^2 (positive floats order as integers)
 };
 
-template <int T, int M, int HW, int BC>
-__global__ void __launch_bounds__(T, 4) k_mixed_fused(const FusedParams p) {
+// WB selects the well-balanced bottom form (the flat printed scheme otherwise):
+// the m^dag bottom source -(3/2) tau q_l b_x, and in place of the delta terms
+// the face forces Phi_{f+1/2} of the bottom form, used in the increment form
+//   Psi_f = Phi_f + beta_f (h_b jump) = g hbar_f (h_l + b jump) + (pi jump)
+//           + (3/2) p~_f (b jump) - beta_f (h_l - h_b jump),
+// with pi = eta p~ + lambda alpha (m^dag b_1 - m_l) the non-gravity part of
+// p^ (g/2 (h_l^2 jump) + g hbar_f (b jump) = g hbar_f (h_l + b jump) exactly).
+// The free-surface jump comes from the double-float h and b, and p~ and
+// m^dag b_1 - m_l from P_l = h_l^2 - m_l of the pairs, so that a lake at rest
+// stays at rest to the pairs' precision rather than to single precision.
+template <int T, int M, int HW, int BC, bool WB = false>
+__global__ void __launch_bounds__(T, WB ? 3 : 4) k_mixed_fused(const FusedParams p) {
     using Gm = FusedGeom<T, M, HW>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    auto& sm = *reinterpret_cast<FusedShared<T, M, HW>*>(smem_raw);
+    auto& sm = *reinterpret_cast<FusedShared<T, M, HW, WB>*>(smem_raw);
     const int tid = threadIdx.x;
     // the instance of this tile: its size, offsets, constants and speeds
     int64_t n = p.n, cell0 = 0, face0 = 0, tile = blockIdx.x;
@@ -322,10 +347,37 @@ __global__ void __launch_bounds__(T, 4) k_mixed_fused(const FusedParams p) {
             // differences of U^n at the face to the right: (hi1 - hi0) + (lo1 - lo0)
             const float Dhn = __fadd_rn(__fsub_rn(h1.x, h0.x), __fsub_rn(h1.y, h0.y));
             const float Dqn = __fadd_rn(__fsub_rn(q1.x, q0.x), __fsub_rn(q1.y, q0.y));
-            const float Dmn = __fadd_rn(__fsub_rn(m1.x, m0.x), __fsub_rn(m1.y, m0.y));
-            sm.Dh[j] = fmaf(wb1, dh1n - dh1, Dhn);
             sm.Dq[j] = fmaf(wb1, dq1n - dq1, Dqn);
-            sm.Dm[j] = fmaf(wb1, dm1n - dm1, Dmn);
+            if constexpr (!WB) {
+                const float Dmn = __fadd_rn(__fsub_rn(m1.x, m0.x), __fsub_rn(m1.y, m0.y));
+                sm.Dh[j] = fmaf(wb1, dh1n - dh1, Dhn);
+                sm.Dm[j] = fmaf(wb1, dm1n - dm1, Dmn);
+            } else {
+                const float2* __restrict__ Bp = p.bathy + cell0;
+                const float2 b0 = __ldg(Bp + gi), b1 = __ldg(Bp + gn);
+                // free-surface jump (h_l + b) at the face right of the cell:
+                // hi1 - hi0 of h is exact, that of b is taken exactly by TwoSum
+                float sb, eb;
+                two_sum(b1.x, -b0.x, sb, eb);
+                const float lo = __fadd_rn(__fadd_rn(__fsub_rn(h1.y, h0.y), __fsub_rn(b1.y, b0.y)), eb);
+                const float hz = __fadd_rn(__fsub_rn(h1.x, h0.x), sb);
+                sm.wb.Z[j] = fmaf(wl1, dh1n - dh1, __fadd_rn(hz, lo));
+                sm.wb.Db[j] = __fadd_rn(sb, __fadd_rn(__fsub_rn(b1.y, b0.y), eb));
+                sm.Dh[j] = (wl1 - wb1) * (dh1n - dh1);  // (h_l - h_b) jump
+                // P_l = h_l^2 - m_l: hi^2 = pp + pe exactly, pp - m.hi exact for m close to h^2
+                const float pp = __fmul_rn(hf, hf);
+                const float pe = fmaf(hf, hf, -pp);
+                const float P0 = __fadd_rn(__fsub_rn(pp, m0.x), fmaf(2.f * hf, h0.y, __fsub_rn(pe, m0.y)));
+                sm.Dm[j] = fmaf(wl1, fmaf(dh1, fmaf(wl1, dh1, 2.f * hf), -dm1), P0);
+                // (3/2) q_l (b_{c+1} - b_{c-1}) of the cells c = -1 .. W whose m^dag is formed
+                float src = 0.f;
+                if (j >= 2 && j <= W + 3) {
+                    const int64_t gp = inner ? gi - 1 : cell_at<BC>(wl - 4 + j, n);
+                    src = 1.5f * fmaf(wl1, dq1, qf) * (b1.x - __ldg(Bp + gp).x);
+                }
+                sm.wb.Sb[j] = src;
+                sm.wb.Mbl[j] = (wb1 - wl1) * dm1;
+            }
         }
     }
     __syncthreads();
@@ -381,15 +433,19 @@ __global__ void __launch_bounds__(T, 4) k_mixed_fused(const FusedParams p) {
     constexpr int NCL = (Gm::R + 2 + T - 1) / T;
     const float lt2 = c_lt2, tdx = c_tdx, Cc = c_Cc;
     float dq_[NCL], dm_[NCL], dr_[NCL], be_[NCL], de_[NCL];
+    float pt_[WB ? NCL : 1];
     float kloc = 0.f, kmin = 3.0e38f;
 #pragma unroll
     for (int it = 0; it < NCL; ++it) {
         const int j = tid + it * T;
         dq_[it] = dm_[it] = dr_[it] = be_[it] = de_[it] = 0.f;
+        if constexpr (WB) pt_[it] = 0.f;
         if (j < W + 2) {
             const int c3 = j + 2;
             const float drv = -tdx * (Fr[j + 1] - Fr[j]);
-            const float dmv = fmaf(tau, sm.rb[c3] + drv, -tdx * (Fm[j + 1] - Fm[j]));
+            float dmv = fmaf(tau, sm.rb[c3] + drv, -tdx * (Fm[j + 1] - Fm[j]));
+            // bottom source of the (h eta) equation, -(3/2) h u b_x (Sec. 2.3, eq. (hSGNb_eq)), from U_l
+            if constexpr (WB) dmv = fmaf(-c_fq, sm.wb.Sb[c3], dmv);
             const float dqv = -tdx * (Fq[j + 1] - Fq[j]);
             const float msv = sm.mb[c3] + dmv + lt2;
             const float h = sm.hl[c3];
@@ -411,7 +467,17 @@ __global__ void __launch_bounds__(T, 4) k_mixed_fused(const FusedParams p) {
             dm_[it] = dmv;
             dr_[it] = drv;
             be_[it] = beta;
-            de_[it] = alpha * ib1;
+            if constexpr (!WB) {
+                de_[it] = alpha * ib1;
+            } else {
+                // p~ = (lambda/3)(1 - m_l/h_l^2) = (lambda/3) P_l / h_l^2;
+                // m^dag b_1 - m_l = (h^2 (m_b - m_l + dm) + lambda tau^2 P_l) / (h^2 + lambda tau^2)
+                const float Pl = sm.Dm[c3];
+                const float ptil = (lam * (1.f / 3.f)) * Pl * ih * ih;
+                const float X = fmaf(h * h, sm.wb.Mbl[c3] + dmv, lt2 * Pl) * iD;
+                de_[it] = fmaf(eta, ptil, lam * alpha * X);  // pi = eta p~ + lambda alpha X
+                pt_[it] = ptil;
+            }
             kloc = fmaxf(kloc, Cc * beta);
             kmin = fminf(kmin, Cc * beta);
         }
@@ -420,8 +486,9 @@ __global__ void __launch_bounds__(T, 4) k_mixed_fused(const FusedParams p) {
     float* const dqa = sm.ql;
     float* const dma = sm.X0;
     float* const dra = sm.rl;
-    float* const bea = sm.hl;
-    float* const dea = sm.ml;
+    float* const bea = WB ? sm.Dm : sm.hl;
+    float* const dea = sm.ml;  // delta (flat) or pi (bottom form)
+    float* const pta = sm.mb;  // p~ (bottom form)
 #pragma unroll
     for (int it = 0; it < NCL; ++it) {
         const int j = tid + it * T;
@@ -431,6 +498,7 @@ __global__ void __launch_bounds__(T, 4) k_mixed_fused(const FusedParams p) {
             dra[j] = dr_[it];
             bea[j] = be_[it];
             dea[j] = de_[it];
+            if constexpr (WB) pta[j] = pt_[it];
         }
     }
 #pragma unroll
@@ -447,10 +515,12 @@ __global__ void __launch_bounds__(T, 4) k_mixed_fused(const FusedParams p) {
         // zero-order ghost copies at the domain ends
         if (win.lend) {
             dqa[0] = dqa[1]; dma[0] = dma[1]; dra[0] = dra[1]; bea[0] = bea[1]; dea[0] = dea[1];
+            if constexpr (WB) pta[0] = pta[1];
         }
         if (win.rend) {
             const int a = W + 1, c = W;
             dqa[a] = dqa[c]; dma[a] = dma[c]; dra[a] = dra[c]; bea[a] = bea[c]; dea[a] = dea[c];
+            if constexpr (WB) pta[a] = pta[c];
         }
     }
     __syncthreads();
@@ -463,7 +533,33 @@ __global__ void __launch_bounds__(T, 4) k_mixed_fused(const FusedParams p) {
     const float fq = c_fq, fd = c_fd;
     float* const BF = sm.rb;
     float* const RD = sm.mb;
-    for (int j = tid; j < W + 1; j += T) {
+    float* Psi = nullptr;  // face forces of the bottom form, face f at f + 3
+    if constexpr (WB) Psi = sm.wb.Z;
+    if constexpr (WB) {
+        // face couplings and forces Psi_f, f = -1 .. W-1; zero across a transmissive domain end
+        for (int j = tid; j < W + 1; j += T) {
+            const int f = j - 1;
+            const float bf = 0.5f * (bea[f + 1] + bea[f + 2]);
+            const float hbar = 0.5f * (sm.hl[f + 3] + sm.hl[f + 4]);
+            const float ptf = 0.5f * (pta[f + 1] + pta[f + 2]);
+            float psi = fmaf(g * hbar, sm.wb.Z[f + 3], dea[f + 2] - dea[f + 1]);
+            psi = fmaf(1.5f * ptf, sm.wb.Db[f + 3], psi);
+            psi = fmaf(-bf, sm.Dh[f + 3], psi);
+            float kf = Cc * bf;
+            if (BC == BC_TRANSMISSIVE && ((f < 0 && win.lend) || (f == W - 1 && win.rend))) {
+                kf = 0.f;
+                psi = 0.f;
+            }
+            BF[pd(j)] = kf;
+            Psi[f + 3] = psi;
+        }
+        __syncthreads();
+        // d_i - (A h_b)_i = -tau/(2dx) (q^dag_{i+1} - q^dag_{i-1}) + tau^2/dx^2 (Psi_{i+1/2} - Psi_{i-1/2})
+        for (int i = tid; i < W; i += T) {
+            const float dqc = sm.Dq[i + 2] + sm.Dq[i + 3] + (dqa[i + 2] - dqa[i]);
+            RD[pd(i)] = fmaf(-fq, dqc, Cc * (Psi[i + 3] - Psi[i + 2]));
+        }
+    } else for (int j = tid; j < W + 1; j += T) {
         const int f = j - 1;  // face between window rows f and f+1
         float kf = Cc * (0.5f * (bea[f + 1] + bea[f + 2]));
         if (BC == BC_TRANSMISSIVE && ((f < 0 && win.lend) || (f == W - 1 && win.rend))) kf = 0.f;
@@ -570,10 +666,16 @@ __global__ void __launch_bounds__(T, 4) k_mixed_fused(const FusedParams p) {
         if (j == 0 && lface) { dL = sm.bnd[0][0]; dR = sm.bnd[0][1]; }
         if (j == sp && rface) { dL = sm.bnd[1][0]; dR = sm.bnd[1][1]; }
         const float qsum = (sm.qb[f + 3] + sm.qb[f + 4]) + (dqa[f + 1] + dqa[f + 2]);
-        const float dmf = sm.Dm[f + 3] + (dma[f + 2] - dma[f + 1]);
-        const float dhf = sm.Dh[f + 3] + (dR - dL);
-        const float G = fq * qsum - fd * (0.5f * (dea[f + 1] + dea[f + 2])) * dmf -
-                        Cc * (0.5f * (bea[f + 1] + bea[f + 2])) * dhf;
+        float G;
+        if constexpr (WB) {
+            // G = tau/(2dx) (q^dag_L + q^dag_R) - tau^2/dx^2 (Psi_f + beta_face (dh_R - dh_L))
+            G = fq * qsum - Cc * fmaf(0.5f * (bea[f + 1] + bea[f + 2]), dR - dL, Psi[f + 3]);
+        } else {
+            const float dmf = sm.Dm[f + 3] + (dma[f + 2] - dma[f + 1]);
+            const float dhf = sm.Dh[f + 3] + (dR - dL);
+            G = fq * qsum - fd * (0.5f * (dea[f + 1] + dea[f + 2])) * dmf -
+                Cc * (0.5f * (bea[f + 1] + bea[f + 2])) * dhf;
+        }
         if (!isfinite(G)) bad |= HSGN_DEV_ERR_NONFINITE;
         Gt[j] = G;
         if (!two) {
@@ -590,14 +692,23 @@ __global__ void __launch_bounds__(T, 4) k_mixed_fused(const FusedParams p) {
         const int r = lo + t;            // window row
         const int64_t i = win.t0 + t;    // global row (in range)
         const float dhL = dha[pd(r)], dhC = dha[pd(r + 1)], dhR = dha[pd(r + 2)];
-        const float dqC = dqa[r + 1], dmL = dma[r], dmC = dma[r + 1], dmR = dma[r + 2];
-        const float beC = bea[r + 1], deC = dea[r + 1];
-        const float DhL = sm.Dh[r + 2], DhC = sm.Dh[r + 3];  // faces r-1/2, r+1/2
-        const float DmL = sm.Dm[r + 2], DmC = sm.Dm[r + 3];
-        // q: tau/(2dx) beta (hbar_{i+1} - hbar_{i-1}), lambda tau/(2dx) delta (m^dag_{i+1} - m^dag_{i-1})
-        const float dhc = (DhL + DhC) + (dhR - dhL);
-        const float dmc = (DmL + DmC) + (dmR - dmL);
-        const float dQ = dqC - fq * beC * dhc - lamv * fq * deC * dmc;
+        const float dqC = dqa[r + 1], dmC = dma[r + 1];
+        float dQ;
+        if constexpr (WB) {
+            // q = q^dag - tau/(2dx) (F_{i+1/2} + F_{i-1/2}), F = Psi + beta_face (dh jump)
+            const float Fp = fmaf(0.5f * (bea[r + 1] + bea[r + 2]), dhR - dhC, Psi[r + 3]);
+            const float Fl = fmaf(0.5f * (bea[r] + bea[r + 1]), dhC - dhL, Psi[r + 2]);
+            dQ = dqC - fq * (Fp + Fl);
+        } else {
+            const float dmL = dma[r], dmR = dma[r + 2];
+            const float beC = bea[r + 1], deC = dea[r + 1];
+            const float DhL = sm.Dh[r + 2], DhC = sm.Dh[r + 3];  // faces r-1/2, r+1/2
+            const float DmL = sm.Dm[r + 2], DmC = sm.Dm[r + 3];
+            // q: tau/(2dx) beta (hbar_{i+1} - hbar_{i-1}), lambda tau/(2dx) delta (m^dag_{i+1} - m^dag_{i-1})
+            const float dhc = (DhL + DhC) + (dhR - dhL);
+            const float dmc = (DmL + DmC) + (dmR - dmL);
+            dQ = dqC - fq * beC * dhc - lamv * fq * deC * dmc;
+        }
         // base depth (rounded) and P0 = h_b^2 - m_b of this cell
         const float2 h0 = U0[i], m0 = U2[i];
         const float hf = h0.x;

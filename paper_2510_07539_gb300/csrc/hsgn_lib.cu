@@ -138,6 +138,7 @@ struct hsgn_s {
     // well-balanced bathymetry form (HSGN_WELL_BALANCED)
     bool wb = false;
     double* bathy = nullptr;         // bottom per cell, null for a flat bottom
+    float2* bathy_df = nullptr;      // the bottom as double-float pairs (windowed bottom form)
     double* phi = nullptr;           // face forces Phi_{i+1/2}
     unsigned char* rws = nullptr;    // workspace of the separator-system solve
     double* spd = nullptr;           // [0] global Rusanov speed, [1] stage speed, [2..3] scratch,
@@ -440,15 +441,24 @@ cudaError_t launch_stage_fused(hsgn_s* H, int stage, double tau, cudaStream_t st
     p.batched = H->batched ? 1 : 0;
     p.inst = H->inst;
     p.tile_inst = H->tile_inst;
+    p.bathy = H->bathy_df;
     const unsigned P = H->batched ? (unsigned)H->total_tiles
                                   : (unsigned)((H->n + H->tileS - 1) / H->tileS);
-    const size_t smem = sizeof(FusedShared<FT, FM, FHW>);
     {
         ProfScope ps(H, HSGN_PROF_ASSEMBLE, st);
-        if (H->bc == BC_PERIODIC)
-            k_mixed_fused<FT, FM, FHW, BC_PERIODIC><<<P, FT, smem, st>>>(p);
-        else
-            k_mixed_fused<FT, FM, FHW, BC_TRANSMISSIVE><<<P, FT, smem, st>>>(p);
+        if (H->wb) {
+            const size_t smem = sizeof(FusedShared<FT, FM, FHW, true>);
+            if (H->bc == BC_PERIODIC)
+                k_mixed_fused<FT, FM, FHW, BC_PERIODIC, true><<<P, FT, smem, st>>>(p);
+            else
+                k_mixed_fused<FT, FM, FHW, BC_TRANSMISSIVE, true><<<P, FT, smem, st>>>(p);
+        } else {
+            const size_t smem = sizeof(FusedShared<FT, FM, FHW>);
+            if (H->bc == BC_PERIODIC)
+                k_mixed_fused<FT, FM, FHW, BC_PERIODIC><<<P, FT, smem, st>>>(p);
+            else
+                k_mixed_fused<FT, FM, FHW, BC_TRANSMISSIVE><<<P, FT, smem, st>>>(p);
+        }
     }
     return cudaGetLastError();
 }
@@ -660,7 +670,9 @@ int hsgn_create(const hsgn_grid_t* grid, double g, double lambda, const double* 
     if (scheme != HSGN_SCHEME_PRINTED && (flags & (HSGN_MIXED | HSGN_WELL_BALANCED)))
         return HSGN_ERR_UNIMPLEMENTED;
     if (bathymetry && !(flags & HSGN_WELL_BALANCED)) return HSGN_ERR_INVALID_ARG;
-    if ((flags & HSGN_WELL_BALANCED) && (flags & HSGN_MIXED)) return HSGN_ERR_UNIMPLEMENTED;
+    // the bottom form in mixed precision exists on the windowed kernel only
+    if ((flags & HSGN_WELL_BALANCED) && (flags & HSGN_MIXED) && (flags & HSGN_EXACT_SOLVE))
+        return HSGN_ERR_UNIMPLEMENTED;
     if (grid->n > ((int64_t)1 << 40)) return HSGN_ERR_INVALID_ARG;
 
     hsgn_s* H = new (std::nothrow) hsgn_s;
@@ -685,7 +697,7 @@ int hsgn_create(const hsgn_grid_t* grid, double g, double lambda, const double* 
     size_t total = H->windowed ? 8 * vec + 4 * fvec            // U, V; G1 dq1 dm1 dr1
                    : H->mixed  ? 4 * vec + 4 * fvec + recb     // U; G1 dq1 dm1 dr1; row records
                                : 16 * vec;                     // U, U1, y v w, 5 back-sub arrays
-    if (H->wb) total += (bathymetry ? 2 : 1) * vec;      // Phi, bottom
+    if (H->wb) total += H->windowed ? vec : (bathymetry ? 2 : 1) * vec;  // pairs; Phi, bottom
     if (scheme == HSGN_SCHEME_ARS222) total += 8 * vec;    // E2, W
     total += align_up(BLK_STRIDE * P * sizeof(double)) + align_up(P * sizeof(double));
     const size_t rws = rows_ws_bytes(P);
@@ -708,6 +720,7 @@ int hsgn_create(const hsgn_grid_t* grid, double g, double lambda, const double* 
         H->dq1 = reinterpret_cast<float*>(take(fvec));
         H->dm1 = reinterpret_cast<float*>(take(fvec));
         H->dr1 = reinterpret_cast<float*>(take(fvec));
+        if (H->wb) H->bathy_df = reinterpret_cast<float2*>(take(vec));
     } else if (H->mixed) {
         H->G1 = reinterpret_cast<float*>(take(fvec));
         H->dq1 = reinterpret_cast<float*>(take(fvec));
@@ -748,19 +761,37 @@ int hsgn_create(const hsgn_grid_t* grid, double g, double lambda, const double* 
         if (e == cudaSuccess)
             e = set_smem(k_mixed_fused<FT, FM, FHW, BC_TRANSMISSIVE>,
                          sizeof(FusedShared<FT, FM, FHW>));
+        if (e == cudaSuccess)
+            e = set_smem(k_mixed_fused<FT, FM, FHW, BC_PERIODIC, true>,
+                         sizeof(FusedShared<FT, FM, FHW, true>));
+        if (e == cudaSuccess)
+            e = set_smem(k_mixed_fused<FT, FM, FHW, BC_TRANSMISSIVE, true>,
+                         sizeof(FusedShared<FT, FM, FHW, true>));
         int sms = 0, per_sm = 0;
         if (e == cudaSuccess)
             e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, H->device);
         if (e == cudaSuccess)
-            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-                &per_sm, k_mixed_fused<FT, FM, FHW, BC_PERIODIC>, FT,
-                sizeof(FusedShared<FT, FM, FHW>));
+            e = H->wb ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                            &per_sm, k_mixed_fused<FT, FM, FHW, BC_PERIODIC, true>, FT,
+                            sizeof(FusedShared<FT, FM, FHW, true>))
+                      : cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                            &per_sm, k_mixed_fused<FT, FM, FHW, BC_PERIODIC>, FT,
+                            sizeof(FusedShared<FT, FM, FHW>));
         const int64_t slots = (int64_t)(sms > 0 ? sms : 1) * (per_sm > 0 ? per_sm : 1);
         H->tileS = (int32_t)fused_tile_rows(n, FusedGeom<FT, FM, FHW>::S, slots);
     }
-    // the bottom: host or device memory, copied once (cudaMemcpyDefault infers which)
+    // the bottom: host or device memory, copied once (cudaMemcpyDefault infers which);
+    // the windowed form keeps it as double-float pairs, converted through V[0]
     if (e == cudaSuccess && H->bathy)
         e = cudaMemcpy(H->bathy, bathymetry, n * sizeof(double), cudaMemcpyDefault);
+    if (e == cudaSuccess && H->bathy_df && bathymetry) {
+        e = cudaMemcpy(H->V[0], bathymetry, n * sizeof(double), cudaMemcpyDefault);
+        if (e == cudaSuccess) {
+            k_df_from_f64<<<1216, 256>>>(n, H->V[0], H->bathy_df);
+            e = cudaGetLastError();
+        }
+        if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    }
     if (e == cudaSuccess)
         e = set_smem(k_stage_assemble<AT, AM, BC_PERIODIC, false>, sizeof(AssembleShared<AT, AM>));
     if (e == cudaSuccess)

@@ -57,12 +57,13 @@ def test_create_rejects_bad_arguments_before_touching_the_device(lib):
     assert lib.hsgn_create(ctypes.byref(g), 9.81, -1.0, None, 0, ctypes.byref(h)) == 1
     assert lib.hsgn_create(ctypes.byref(g), 9.81, 1.0, None, 0x4000, ctypes.byref(h)) == 6
     assert lib.hsgn_create(ctypes.byref(g), 9.81, 1.0, None, 0, None) == 1
-    # a bottom needs the well-balanced form; that form has no mixed-precision variant
+    # a bottom needs the well-balanced form; in mixed precision that form runs
+    # on the windowed kernel only (not with the exact separator solve)
     bottom = (ctypes.c_double * 10)()
     assert lib.hsgn_create(ctypes.byref(g), 9.81, 1.0, bottom, 0, ctypes.byref(h)) == 1
     assert lib.hsgn_create(ctypes.byref(g), 9.81, 1.0, bottom, 0x1, ctypes.byref(h)) == 1
-    assert lib.hsgn_create(ctypes.byref(g), 9.81, 1.0, bottom, 0x3, ctypes.byref(h)) == 6
-    assert lib.hsgn_create(ctypes.byref(g), 9.81, 1.0, None, 0x3, ctypes.byref(h)) == 6
+    assert lib.hsgn_create(ctypes.byref(g), 9.81, 1.0, bottom, 0x7, ctypes.byref(h)) == 6
+    assert lib.hsgn_create(ctypes.byref(g), 9.81, 1.0, None, 0x7, ctypes.byref(h)) == 6
     assert not h.value
     # comparison schemes: FP64 flat bottom only; an unknown scheme is invalid
     assert lib.hsgn_create(ctypes.byref(g), 9.81, 1.0, None, 0x300 | 0x1, ctypes.byref(h)) == 6

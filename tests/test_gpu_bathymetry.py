@@ -174,3 +174,116 @@ def test_wb_shelf_2_24_one_step():
     assert rel_l2(got[0], ref[0]) < 1e-12 and rel_l2(got[2], ref[2]) < 1e-12
     assert np.linalg.norm(got[1] - ref[1]) / np.linalg.norm(Sq) < 1e-12
     assert np.linalg.norm(got[3] - ref[3]) / np.linalg.norm(Sr) < 1e-12
+
+
+# --------------------------------------------------------------------------
+# the bottom form in mixed precision (HSGN_MIXED | HSGN_WELL_BALANCED, the
+# windowed kernel): bounds as for the flat mixed form (one step <= 1e-7
+# relative L2 for h and h eta, q and h w against their summand scales), the
+# lake at rest kept to the double-float pairs' precision, mass to FP64 rounding
+# --------------------------------------------------------------------------
+def wb_scales(p, U, dt):
+    """Summand magnitudes of the bottom form's back-substitution (Sec. 4.2 with
+    the face forces of the bottom form): q^dag and tau/dx beta h; r^dag with its
+    + lambda tau and the subtracted lambda tau mbar/hbar^2."""
+    tau = (1.0 - 1.0 / math.sqrt(2.0)) * dt
+    A = oracle.assemble(p, U, U, tau)
+    h, q, m, r = (np.abs(u) for u in U)
+    Sq = q + tau / p.dx * A["beta"] * h
+    Sr = r + p.lam * tau * (1.0 + m / (h * h))
+    return Sq, Sr
+
+
+def wb_mixed_run(n, dx, bc, lam, b, U, dt, steps, use_graph=True):
+    with wb_solver(n, dx, bc, lam, b, S().FLAG_MIXED) as s:
+        s.set_state(*(dev(u) for u in U))
+        if use_graph:
+            s.run(dt, steps)
+        else:
+            for _ in range(steps):
+                s.step(dt)
+        s.check()
+        return [t.cpu().numpy() for t in s.get_state()]
+
+
+@pytest.mark.parametrize("bc", [0, 1])
+@pytest.mark.parametrize("n", [5, 100, 1000, 1537, 70001])
+def test_wb_mixed_one_step_close_to_oracle(n, bc):
+    dx, lam = 0.1, 500.0
+    x, _, b, U = inputs.gauss_bottom_wave(300 + n, n, dx)
+    p = oracle.Params(n, dx, bc, lam=lam, form=1, bathy=b)
+    dt, _, _ = oracle.suggest_dt(p, U, 2.0, 0.5)
+    got = wb_mixed_run(n, dx, bc, lam, b, U, dt, 1)
+    ref = oracle.step(p, U, dt)
+    Sq, Sr = wb_scales(p, U, dt)
+    assert rel_l2(got[0], ref[0]) < 1e-7, rel_l2(got[0], ref[0])
+    assert rel_l2(got[2], ref[2]) < 1e-7, rel_l2(got[2], ref[2])
+    assert np.linalg.norm(got[1] - ref[1]) / np.linalg.norm(Sq) < 1e-6
+    assert np.linalg.norm(got[3] - ref[3]) / np.linalg.norm(Sr) < 1e-6
+
+
+@pytest.mark.parametrize("bc", [0, 1])
+@pytest.mark.parametrize("n", [400, 5000])
+def test_wb_mixed_lake_at_rest(n, bc):
+    # h + b = const, u = 0, eta = h, w = 0: every jump the stage forms from
+    # the pairs vanishes to their 2^-48 precision, so the state stays at rest
+    # far below single-precision rounding (which would be ~1e-7 per step)
+    x, dx = inputs.cell_centres(n, 0.0, 0.2 * n)
+    b = inputs.gaussian_bathymetry(5, x)
+    b = b - b.min()
+    h = 1.0 - b
+    U = (h, 0 * h, h * h, 0 * h)
+    got = wb_mixed_run(n, dx, bc, 500.0, b, U, 0.05, 40)
+    err = [np.max(np.abs(got[0] - h)), np.max(np.abs(got[1])), np.max(np.abs(got[2] - h * h)),
+           np.max(np.abs(got[3]))]
+    assert err[0] < 1e-12 and err[1] < 1e-12 and err[2] < 1e-12 and err[3] < 1e-10, err
+
+
+def test_wb_mixed_gauss_bottom_trajectory():
+    # the adjoint workload's forward problem, 200 steps at CFL 2: mixed within
+    # 1e-6 of the FP64 oracle, mass exact to FP64 rounding
+    n, lam, steps = 4096, 100.0, 200
+    x, dx, b, U = inputs.gauss_bottom_wave(20251011, n)
+    p = oracle.Params(n, dx, 0, lam=lam, form=1, bathy=b)
+    dt, _, _ = oracle.suggest_dt(p, U, 2.0, 0.5)
+    got = wb_mixed_run(n, dx, 0, lam, b, U, dt, steps)
+    ref = oracle.run(p, U, dt, steps)
+    assert rel_l2(got[0], ref[0]) < 1e-6 and rel_l2(got[2], ref[2]) < 1e-6
+    Sq, Sr = wb_scales(p, U, dt)
+    assert np.linalg.norm(got[1] - ref[1]) / np.linalg.norm(Sq) < 1e-5
+    assert np.linalg.norm(got[3] - ref[3]) / np.linalg.norm(Sr) < 1e-5
+    assert abs(math.fsum(got[0]) - math.fsum(U[0])) <= 1e-13 * math.fsum(U[0])
+
+
+def test_wb_mixed_graph_replay_equals_step_loop_and_null_bottom():
+    n, lam = 3000, 1000.0
+    x, dx, b, U = inputs.gauss_bottom_wave(8, n)
+    a = wb_mixed_run(n, dx, 0, lam, b, U, 0.01, 7, use_graph=True)
+    c = wb_mixed_run(n, dx, 0, lam, b, U, 0.01, 7, use_graph=False)
+    for k in range(4):
+        np.testing.assert_array_equal(a[k], c[k])
+    z = wb_mixed_run(n, dx, 1, lam, np.zeros(n), U, 0.01, 3)
+    o = wb_mixed_run(n, dx, 1, lam, None, U, 0.01, 3)
+    for k in range(4):
+        np.testing.assert_array_equal(z[k], o[k])
+
+
+def test_wb_mixed_needs_the_windowed_kernel():
+    with pytest.raises(S().HsgnError) as e:
+        wb_solver(16, 0.1, 0, 1.0, None, S().FLAG_MIXED | S().FLAG_EXACT_SOLVE)
+    assert e.value.code == 6
+
+
+def test_wb_mixed_shelf_2_24_steps():
+    # the large workload in mixed precision: 5 steps at CFL_IMEX 4 against
+    # the FP64 oracle, every cell
+    n, lam, steps = 1 << 24, 1000.0, 5
+    x, dx, b, U = inputs.shelf_wave(n)
+    p = oracle.Params(n, dx, 1, lam=lam, form=1, bathy=b)
+    dt, _, _ = oracle.suggest_dt(p, U, 4.0, 0.5)
+    got = wb_mixed_run(n, dx, 1, lam, b, U, dt, steps)
+    ref = oracle.run(p, U, dt, steps)
+    Sq, Sr = wb_scales(p, U, dt)
+    assert rel_l2(got[0], ref[0]) < 1e-7 and rel_l2(got[2], ref[2]) < 1e-7
+    assert np.linalg.norm(got[1] - ref[1]) / np.linalg.norm(Sq) < 1e-6
+    assert np.linalg.norm(got[3] - ref[3]) / np.linalg.norm(Sr) < 1e-6
