@@ -76,6 +76,7 @@ def parse_args():
     ap.add_argument("--no-comparators", action="store_true",
                     help="skip the scheme comparison (time to solution)")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint workload")
+    ap.add_argument("--no-shelf", action="store_true", help="skip the 2^24-cell shelf workload")
     ap.add_argument("--sequential", action="store_true",
                     help="run the instances of a step back to back on one stream "
                          "(default: one CUDA stream each)")
@@ -426,6 +427,52 @@ def time_adjoint(S, torch, stream):
             "grad_bottom_l2": float(np.linalg.norm(gb.cpu().numpy()))}
 
 
+def time_shelf(S, torch, stream, steps=50, warmup=3):
+    """The large workload: N = 2^24, dx = 0.005, transmissive, lambda = 1000, a
+    wave a = 0.1 running towards a 1:20 shelf (depth 1 -> 0.5), bottom form,
+    dt = min(4 dx/nu, 0.5 dx/u_max) at t = 0. FP64 and mixed precision
+    advance the same initial state by `steps` steps (each state is 537 MB,
+    far above L2); the mixed result is compared with the FP64 one, which
+    matches the FP64 oracle to 1e-12 per step."""
+    import numpy as np
+    from paper_2510_07539_gb300 import inputs as inp
+    n, lam = 1 << 24, 1000.0
+    x, dx, b, U = inp.shelf_wave(n)
+    Ud = [torch.tensor(u, device="cuda") for u in U]
+    del U
+    out, dt = {}, None
+    for name, flags in (("fp64", S.FLAG_WELL_BALANCED),
+                        ("mixed", S.FLAG_WELL_BALANCED | S.FLAG_MIXED)):
+        with S.Solver(n, 0.0, n * dx, S.BC_TRANSMISSIVE, lam=lam, flags=flags,
+                      bathymetry=b) as s:
+            s.set_state(*Ud)
+            if dt is None:
+                dt = s.suggest_dt(4.0, 0.5)
+            s.run(dt, warmup)
+            s.set_state(*Ud)
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            s.enqueue(dt, steps, stream=stream)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            s.check()
+            ms = e0.elapsed_time(e1)
+            out[name] = {"value": 2.0 * n * steps / (ms / 1e3), "unit": UNIT,
+                         "ms_per_step": ms / steps,
+                         "state": [t.cpu().numpy() for t in s.get_state()]}
+    ref, got = out["fp64"].pop("state"), out["mixed"].pop("state")
+    rel = [float(np.linalg.norm(got[k] - ref[k]) / np.linalg.norm(ref[k])) for k in range(4)]
+    return {"workload": f"wave a = 0.1 towards a 1:20 shelf, N = 2^24, dx = 0.005, "
+                        f"transmissive, lambda = 1000, bottom form, dt = {dt:.6g} "
+                        f"(CFL_IMEX 4), {steps} timed steps (of the 5000-step run)",
+            "fp64": out["fp64"], "mixed": out["mixed"],
+            "mixed_over_fp64": out["mixed"]["value"] / out["fp64"]["value"],
+            "mixed_vs_fp64_rel_l2_after_steps": {"h": rel[0], "q": rel[1], "h_eta": rel[2],
+                                                 "h_w": rel[3]}}
+
+
 def time_fp64(S, torch, n, xl, xr, lams, Ud, args, flush, stream, dist, units_rank, world,
               hbm_peak):
     """The all-FP64 path (exact separator solve) on the same workload."""
@@ -542,6 +589,9 @@ def run_ours(args):
     adjoint = None
     if not args.no_adjoint and rank == 0:
         adjoint = time_adjoint(S, torch, stream)
+    shelf = None
+    if not args.no_shelf and rank == 0:
+        shelf = time_shelf(S, torch, stream)
 
     # ---- batched workload: 4096 independent periodic solitary waves of uneven
     #      length, the windowed mixed stage over all of them: one launch per stage
@@ -658,7 +708,7 @@ def run_ours(args):
             "roofline": roofline, "fp64_path": fp64, "batched": batched,
             "batched_vs_fp64_single": (batched["value"] / fp64["value"])
             if (batched and fp64) else None,
-            "comparators": comparators, "adjoint": adjoint,
+            "comparators": comparators, "adjoint": adjoint, "shelf": shelf,
             "cpu_baseline": cpu, "e2e": e2e,
             "clocks": clocks, "gpu_launches": launches,
         }
