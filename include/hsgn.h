@@ -254,6 +254,29 @@ int hsgn_batched_set_dt(hsgn_handle_t h, const double* dt);
 int hsgn_batched_suggest_dt(hsgn_handle_t h, double cfl, double mcfl, double* dt_out,
                             void* stream);
 
+/* Tiles of a batch (the windowed kernel; HSGN_ERR_UNIMPLEMENTED for a batch
+ * created with HSGN_EXACT_SOLVE). variant[k] (host array of `count`) selects
+ * for instance k the large windowed kernel (0: 256 threads, tiles of up to 895
+ * rows, the default) or the small one (1: 128 threads, tiles of up to 383
+ * rows, less padding for short instances); each kernel then runs as one launch
+ * per stage over its instances' tiles. Values other than 0 and 1 give
+ * INVALID_ARG. Synchronises the device; the results of both variants agree to
+ * the rounding of the single-precision increments. */
+int hsgn_batched_set_tiles(hsgn_handle_t h, const int32_t* variant);
+
+/* Autotuner of the tiles: from the current state (restored exactly after every
+ * trial), times `steps` >= 1 steps with every instance on the large variant,
+ * then on the small one; from these a cost per tile of each variant gives
+ * each instance the variant of smaller predicted cost, and that assignment is
+ * timed when it mixes the two. The fastest timed assignment is kept.
+ * ms_out (host, 3 doubles, may be NULL): ms per step of all-large, all-small
+ * and the mixed assignment (NaN when not timed); choice_out (may be NULL): 0,
+ * 1 or 2 for the assignment kept. Needs hsgn_batched_set_dt first
+ * (INVALID_ARG otherwise); allocates 32 bytes per cell for the duration of the
+ * call; synchronises. */
+int hsgn_batched_autotune(hsgn_handle_t h, int32_t steps, double* ms_out, int32_t* choice_out,
+                          void* stream);
+
 /* Release everything owned by the handle (NULL is accepted). */
 void hsgn_destroy(hsgn_handle_t h);
 

@@ -255,7 +255,7 @@ struct FusedShared {
 // m^dag b_1 - m_l from P_l = h_l^2 - m_l of the pairs, so that a lake at rest
 // stays at rest to the pairs' precision rather than to single precision.
 template <int T, int M, int HW, int BC, bool WB = false>
-__global__ void __launch_bounds__(T, WB ? 3 : 4) k_mixed_fused(const FusedParams p) {
+__global__ void __launch_bounds__(T, (WB ? 768 : 1024) / T) k_mixed_fused(const FusedParams p) {
     using Gm = FusedGeom<T, M, HW>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     auto& sm = *reinterpret_cast<FusedShared<T, M, HW, WB>*>(smem_raw);

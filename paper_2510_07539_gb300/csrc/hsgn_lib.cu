@@ -31,6 +31,9 @@ static_assert(XT * XM == AS, "both precision forms use the same block split");
 constexpr int OT = 256, OM = 16;
 // Windowed mixed stage: FT threads, FM rows per thread, FHW overlap rows.
 constexpr int FT = 256, FM = 4, FHW = 64;
+// Small variant of the windowed stage for batches (tiles of 383 rows instead of
+// 895), chosen per instance by hsgn_batched_set_tiles / hsgn_batched_autotune.
+constexpr int FTS = 128;
 // Separator levels: one warp per block of GS rows; one warp solves up to RMAX rows.
 constexpr int GS = SEP_ROWS, RMAX = SEP_ROWS;
 
@@ -162,8 +165,11 @@ struct hsgn_s {
     double* speeds = nullptr;        // per-instance Rusanov speed (device)
     double* speeds_tmp = nullptr;    // 2 per instance (device), for suggest_dt
     double* speeds_next = nullptr;   // windowed batch: per-instance speed while the state is in V
-    int32_t* tile_inst = nullptr;    // windowed batch: instance of every tile (device)
+    int32_t* tile_inst = nullptr;    // windowed batch: instance of every large tile (device)
     int64_t total_tiles = 0;
+    int32_t* tile_inst_small = nullptr;  // ... of every tile of the small variant
+    int64_t tiles_small = 0;
+    std::vector<int8_t> variant;     // per instance: 0 large, 1 small windowed variant
     std::vector<InstInfo> inst_h;    // host copy
     float *mblk = nullptr, *ms_ = nullptr;
     unsigned* err = nullptr;
@@ -446,7 +452,20 @@ cudaError_t launch_stage_fused(hsgn_s* H, int stage, double tau, cudaStream_t st
                                   : (unsigned)((H->n + H->tileS - 1) / H->tileS);
     {
         ProfScope ps(H, HSGN_PROF_ASSEMBLE, st);
-        if (H->wb) {
+        if (H->batched && H->tiles_small > 0) {
+            // instances on the small variant: a launch of their own over their tiles
+            FusedParams ps_ = p;
+            ps_.tile_inst = H->tile_inst_small;
+            const size_t smem = sizeof(FusedShared<FTS, FM, FHW>);
+            const unsigned Ps = (unsigned)H->tiles_small;
+            if (H->bc == BC_PERIODIC)
+                k_mixed_fused<FTS, FM, FHW, BC_PERIODIC><<<Ps, FTS, smem, st>>>(ps_);
+            else
+                k_mixed_fused<FTS, FM, FHW, BC_TRANSMISSIVE><<<Ps, FTS, smem, st>>>(ps_);
+        }
+        if (P == 0) {
+            // every instance of the batch runs on the small variant
+        } else if (H->wb) {
             const size_t smem = sizeof(FusedShared<FT, FM, FHW, true>);
             if (H->bc == BC_PERIODIC)
                 k_mixed_fused<FT, FM, FHW, BC_PERIODIC, true><<<P, FT, smem, st>>>(p);
@@ -628,6 +647,47 @@ cudaError_t refresh_speed(hsgn_s* H, cudaStream_t st) {
 }
 
 inline cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+
+
+// Tiles of a windowed batch: instance k runs on the large (var[k] = 0) or the
+// small (var[k] = 1) windowed kernel with equal tiles of at most that kernel's
+// rows; instance info and both tile tables are rewritten (the device must be
+// idle) and the captured step graphs dropped, since the launches change.
+template <int T>
+int64_t tiles_of(int64_t n) {
+    const int64_t s = fused_tile_rows(n, FusedGeom<T, FM, FHW>::S, 1);
+    return (n + s - 1) / s;
+}
+
+cudaError_t assign_tiles(hsgn_s* H, const std::vector<int8_t>& var) {
+    std::vector<int32_t> t0, t1;
+    for (int32_t k = 0; k < H->count; ++k) {
+        InstInfo& I = H->inst_h[(size_t)k];
+        const int64_t smax = var[(size_t)k] ? FusedGeom<FTS, FM, FHW>::S : FusedGeom<FT, FM, FHW>::S;
+        std::vector<int32_t>& t = var[(size_t)k] ? t1 : t0;
+        I.base = fused_tile_rows(I.n, smax, 1);
+        I.P = (int32_t)((I.n + I.base - 1) / I.base);
+        I.blk0 = (int32_t)t.size();
+        for (int32_t b = 0; b < I.P; ++b) t.push_back(k);
+    }
+    cudaError_t e = cudaMemcpy(H->inst, H->inst_h.data(), H->count * sizeof(InstInfo),
+                               cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && !t0.empty())
+        e = cudaMemcpy(H->tile_inst, t0.data(), t0.size() * sizeof(int32_t), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && !t1.empty())
+        e = cudaMemcpy(H->tile_inst_small, t1.data(), t1.size() * sizeof(int32_t),
+                       cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return e;
+    H->variant = var;
+    H->total_tiles = (int64_t)t0.size();
+    H->tiles_small = (int64_t)t1.size();
+    for (int c = 0; c < 2; ++c)
+        if (H->gexec[c]) {
+            cudaGraphExecDestroy(H->gexec[c]);
+            H->gexec[c] = nullptr;
+        }
+    return cudaSuccess;
+}
 
 }  // namespace
 
@@ -1315,7 +1375,7 @@ int hsgn_create_batched(int32_t count, const int64_t* n, const double* x_left,
     std::vector<InstInfo> info((size_t)count);
     std::vector<int32_t> binst;
     int64_t cells = 0;
-    int64_t blocks = 0;
+    int64_t blocks = 0, small_cap = 0;
     for (int32_t k = 0; k < count; ++k) {
         const int64_t nk = n[k];
         if (nk < 3 || (!windowed && nk > (int64_t)SEP_ROWS * AS) || nk > ((int64_t)1 << 31))
@@ -1332,10 +1392,12 @@ int hsgn_create_batched(int32_t count, const int64_t* n, const double* x_left,
         I.lam = lambda[k];
         I.dt = 0.0;
         if (windowed) {
-            // tiles of the windowed stage: base = tile rows, P = tiles, blk0 = first tile
+            // tiles of the windowed stage (set by assign_tiles below); the tile
+            // tables hold every instance on either variant
             I.base = fused_tile_rows(nk, FusedGeom<FT, FM, FHW>::S, 1);
             I.P = (int32_t)((nk + I.base - 1) / I.base);
             I.rem = 0;
+            small_cap += tiles_of<FTS>(nk);
         } else {
             const BlockSplit s = make_split(nk, AS);
             I.base = s.base;
@@ -1369,6 +1431,7 @@ int hsgn_create_batched(int32_t count, const int64_t* n, const double* x_left,
     if (!windowed)
         total += align_up(BLK_STRIDE * blocks * sizeof(float)) + align_up(blocks * sizeof(float));
     total += align_up(count * sizeof(InstInfo)) + align_up(blocks * sizeof(int32_t));
+    if (windowed) total += align_up(small_cap * sizeof(int32_t));
     total += 4 * align_up(count * sizeof(double));
     total += align_up(8 * sizeof(double)) + align_up(sizeof(unsigned));
     if (cudaMalloc(&H->mem, total) != cudaSuccess) {
@@ -1396,7 +1459,10 @@ int hsgn_create_batched(int32_t count, const int64_t* n, const double* x_left,
     }
     H->inst = reinterpret_cast<InstInfo*>(take(align_up(count * sizeof(InstInfo))));
     H->blk_inst = reinterpret_cast<int32_t*>(take(align_up(blocks * sizeof(int32_t))));
-    if (windowed) H->tile_inst = H->blk_inst;
+    if (windowed) {
+        H->tile_inst = H->blk_inst;
+        H->tile_inst_small = reinterpret_cast<int32_t*>(take(align_up(small_cap * sizeof(int32_t))));
+    }
     H->speeds = reinterpret_cast<double*>(take(align_up(count * sizeof(double))));
     H->speeds_tmp = reinterpret_cast<double*>(take(2 * align_up(count * sizeof(double))));
     H->speeds_next = reinterpret_cast<double*>(take(align_up(count * sizeof(double))));
@@ -1415,6 +1481,11 @@ int hsgn_create_batched(int32_t count, const int64_t* n, const double* x_left,
         e = set_smem(k_mixed_fused<FT, FM, FHW, BC_PERIODIC>, sizeof(FusedShared<FT, FM, FHW>));
     if (e == cudaSuccess)
         e = set_smem(k_mixed_fused<FT, FM, FHW, BC_TRANSMISSIVE>, sizeof(FusedShared<FT, FM, FHW>));
+    if (e == cudaSuccess)
+        e = set_smem(k_mixed_fused<FTS, FM, FHW, BC_PERIODIC>, sizeof(FusedShared<FTS, FM, FHW>));
+    if (e == cudaSuccess)
+        e = set_smem(k_mixed_fused<FTS, FM, FHW, BC_TRANSMISSIVE>, sizeof(FusedShared<FTS, FM, FHW>));
+    if (e == cudaSuccess && windowed) e = assign_tiles(H, std::vector<int8_t>((size_t)count, 0));
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&H->cap, cudaStreamNonBlocking);
     if (e != cudaSuccess) {
         cudaGetLastError();
@@ -1471,6 +1542,110 @@ int hsgn_batched_suggest_dt(hsgn_handle_t H, double cfl, double mcfl, double* dt
         dt_out[k] = dt;
     }
     return HSGN_OK;
+}
+
+int hsgn_batched_set_tiles(hsgn_handle_t H, const int32_t* variant) {
+    if (!H || !H->batched || !variant) return HSGN_ERR_INVALID_ARG;
+    if (!H->windowed) return HSGN_ERR_UNIMPLEMENTED;
+    std::vector<int8_t> var((size_t)H->count);
+    for (int32_t k = 0; k < H->count; ++k) {
+        if (variant[k] != 0 && variant[k] != 1) return HSGN_ERR_INVALID_ARG;
+        var[(size_t)k] = (int8_t)variant[k];
+    }
+    if (cudaDeviceSynchronize() != cudaSuccess) return HSGN_ERR_CUDA;
+    return assign_tiles(H, var) == cudaSuccess ? HSGN_OK : HSGN_ERR_CUDA;
+}
+
+// Autotuner of the batch's tiles: times `steps` steps from the current state
+// (restored after every trial) with every instance on the large variant, then
+// on the small one; from the two times a cost per tile of each variant
+// (ms / tiles launched), which assigns each instance the variant with the
+// smaller predicted cost (tiles x cost per tile); that assignment is timed as
+// well when it mixes the variants. The fastest of the timed assignments stays.
+int hsgn_batched_autotune(hsgn_handle_t H, int32_t steps, double* ms_out, int32_t* choice_out,
+                          void* stream) {
+    if (!H || !H->batched || steps < 1) return HSGN_ERR_INVALID_ARG;
+    if (!H->windowed) return HSGN_ERR_UNIMPLEMENTED;
+    for (int32_t k = 0; k < H->count; ++k)
+        if (!(H->inst_h[(size_t)k].dt > 0.0)) return HSGN_ERR_INVALID_ARG;  // set_dt first
+    cudaStream_t st = as_stream(stream);
+    const int64_t n = H->n;
+    // the state, kept as doubles (exact: the pairs carry 48 bits)
+    double* keep = nullptr;
+    if (cudaMalloc(&keep, 4 * n * sizeof(double)) != cudaSuccess) {
+        cudaGetLastError();
+        return HSGN_ERR_OUT_OF_MEMORY;
+    }
+    double* kp[4] = {keep, keep + n, keep + 2 * n, keep + 3 * n};
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    int rc = HSGN_OK;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) rc = HSGN_ERR_CUDA;
+    if (rc == HSGN_OK) rc = hsgn_get_state(H, kp[0], kp[1], kp[2], kp[3], stream);
+    const std::vector<int8_t> start = H->variant;
+    auto trial = [&](const std::vector<int8_t>& var, double& ms) -> int {
+        if (cudaDeviceSynchronize() != cudaSuccess || assign_tiles(H, var) != cudaSuccess)
+            return HSGN_ERR_CUDA;
+        // two warm-up steps capture the graphs of both state buffers
+        int r = hsgn_run(H, 0.0, 2, stream);
+        if (r == HSGN_OK) r = hsgn_set_state(H, kp[0], kp[1], kp[2], kp[3], stream);
+        if (r != HSGN_OK) return r;
+        if (cudaEventRecord(e0, st) != cudaSuccess) return HSGN_ERR_CUDA;
+        r = hsgn_enqueue(H, 0.0, steps, stream);
+        if (r != HSGN_OK) return r;
+        float t = 0.f;
+        if (cudaEventRecord(e1, st) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+            cudaEventElapsedTime(&t, e0, e1) != cudaSuccess)
+            return HSGN_ERR_CUDA;
+        ms = (double)t / steps;
+        r = read_error(H, st);
+        if (r == HSGN_OK) r = hsgn_set_state(H, kp[0], kp[1], kp[2], kp[3], stream);
+        return r;
+    };
+    const size_t c = (size_t)H->count;
+    std::vector<int8_t> v0(c, 0), v1(c, 1), vm(c, 0);
+    double t0 = 0.0, t1 = 0.0, tm = std::nan("");
+    if (rc == HSGN_OK) rc = trial(v0, t0);
+    if (rc == HSGN_OK) rc = trial(v1, t1);
+    int32_t choice = t1 < t0 ? 1 : 0;
+    if (rc == HSGN_OK) {
+        int64_t n0 = 0, n1 = 0;
+        for (size_t k = 0; k < c; ++k) {
+            n0 += tiles_of<FT>(H->inst_h[k].n);
+            n1 += tiles_of<FTS>(H->inst_h[k].n);
+        }
+        const double c0 = t0 / (double)n0, c1 = t1 / (double)n1;
+        bool mixed = false, any0 = false;
+        for (size_t k = 0; k < c; ++k) {
+            const int64_t nk = H->inst_h[k].n;
+            vm[k] = (double)tiles_of<FTS>(nk) * c1 < (double)tiles_of<FT>(nk) * c0 ? 1 : 0;
+            any0 |= vm[k] == 0;
+            mixed |= vm[k] == 1;
+        }
+        mixed = mixed && any0;
+        if (mixed) {
+            rc = trial(vm, tm);
+            if (rc == HSGN_OK && tm < (choice ? t1 : t0)) choice = 2;
+        }
+    }
+    if (rc == HSGN_OK) {
+        if (cudaDeviceSynchronize() != cudaSuccess ||
+            assign_tiles(H, choice == 2 ? vm : (choice == 1 ? v1 : v0)) != cudaSuccess)
+            rc = HSGN_ERR_CUDA;
+    } else {
+        cudaDeviceSynchronize();
+        cudaGetLastError();
+        assign_tiles(H, start);
+    }
+    if (ms_out) {
+        ms_out[0] = t0;
+        ms_out[1] = t1;
+        ms_out[2] = tm;
+    }
+    if (choice_out) *choice_out = choice;
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaFree(keep);
+    return rc;
 }
 
 int hsgn_tridiag_workspace_bytes(int64_t n, size_t* bytes) {

@@ -79,6 +79,8 @@ def load():
                                 ctypes.POINTER(_P)],
         "hsgn_batched_set_dt": [_P, _P],
         "hsgn_batched_suggest_dt": [_P, _D, _D, _P, _P],
+        "hsgn_batched_set_tiles": [_P, _P],
+        "hsgn_batched_autotune": [_P, ctypes.c_int32, _P, _P, _P],
         "hsgn_tridiag_solve": [_I64, ctypes.c_int32, _P, _P, _P, _P, _P, _P, ctypes.c_size_t, _P],
     }
     for name, args in sig.items():
@@ -334,6 +336,25 @@ class BatchedSolver(Solver):
         _check(_lib.hsgn_batched_suggest_dt(self._h, float(cfl), float(mcfl), out.ctypes.data,
                                             _stream(stream)), "hsgn_batched_suggest_dt")
         return out
+
+    def set_tiles(self, variant):
+        """Per instance 0 (large windowed kernel) or 1 (small one)."""
+        import numpy as np
+        v = np.ascontiguousarray(variant, dtype=np.int32)
+        if v.shape != (self.count,):
+            raise ValueError(f"expected {self.count} variants")
+        _check(_lib.hsgn_batched_set_tiles(self._h, v.ctypes.data), "hsgn_batched_set_tiles")
+
+    def autotune(self, steps: int = 4, stream=None):
+        """Pick the tiles of the batch by timing (the state is kept); returns
+        the ms per step of all-large, all-small and the cost-model assignment
+        (NaN if not timed) and the choice kept (0, 1, 2)."""
+        import numpy as np
+        ms = np.empty(3)
+        ch = ctypes.c_int32(-1)
+        _check(_lib.hsgn_batched_autotune(self._h, int(steps), ms.ctypes.data, ctypes.byref(ch),
+                                          _stream(stream)), "hsgn_batched_autotune")
+        return {"ms_per_step": [float(x) for x in ms], "choice": int(ch.value)}
 
     def step(self, dt: float = 0.0, stream=None):
         super().step(0.0, stream)

@@ -451,3 +451,98 @@ def test_batched_suggest_dt_matches_oracle_and_rejects_bad_use():
             S().Solver.step(B, 0.1)  # a batch takes dt = 0
         with pytest.raises(S().HsgnError):
             B.set_dt(np.zeros(len(ns)))
+
+
+# --------------------------------------------------------------------------
+# tiles of a windowed batch: the small windowed variant and the autotuner
+# --------------------------------------------------------------------------
+def packed_state(insts):
+    return [np.concatenate([it.state[k] for it in insts]) for k in range(4)]
+
+
+@pytest.mark.parametrize("assign", ["small", "alternate"])
+def test_batched_tile_variants_match_oracle(assign):
+    # every instance on the small kernel, or the two kernels alternating (two
+    # launches per stage over disjoint tile tables); instances of 64 .. 5000
+    # cells span 1 .. 14 small tiles
+    insts, ns, xl, xr, lams = batch_case(14, 9, n_min=64, n_max=5000)
+    var = [1] * len(ns) if assign == "small" else [k % 2 for k in range(len(ns))]
+    with S().BatchedSolver(ns, xl, xr, lams) as B:
+        B.set_state(*(dev(a) for a in packed_state(insts)))
+        dts = B.suggest_dt(4.0, 0.5)
+        B.set_dt(dts)
+        B.set_tiles(var)
+        B.run(0.0, 30)
+        got = [t.cpu().numpy() for t in B.get_state()]
+        # a graph replay and a step loop of the same assignment agree bitwise
+        B.set_state(*(dev(a) for a in packed_state(insts)))
+        for _ in range(30):
+            B.step()
+        B.check()
+        loop = [t.cpu().numpy() for t in B.get_state()]
+    for k in range(4):
+        np.testing.assert_array_equal(got[k], loop[k])
+    for k_inst, it in enumerate(insts):
+        o0, o1 = int(B.offsets[k_inst]), int(B.offsets[k_inst + 1])
+        ref = oracle.run(oracle.Params(it.n, it.dx, 0, lam=it.lam), it.state, dts[k_inst], 30)
+        assert rel_l2(got[0][o0:o1], ref[0]) < 5e-6, (k_inst, rel_l2(got[0][o0:o1], ref[0]))
+        assert rel_l2(got[2][o0:o1], ref[2]) < 5e-6
+        assert abs(math.fsum(got[0][o0:o1]) - math.fsum(it.state[0])) <= 1e-13 * math.fsum(it.state[0])
+
+
+def test_batched_small_and_large_variant_agree_on_short_instances():
+    # instances short enough for one tile of either kernel solve the same
+    # window (the unrolled periodic ring) with different thread counts: the
+    # results agree to the single-precision rounding of the increments
+    insts, ns, xl, xr, lams = batch_case(15, 6, n_min=64, n_max=380)
+    with S().BatchedSolver(ns, xl, xr, lams) as B:
+        B.set_state(*(dev(a) for a in packed_state(insts)))
+        B.set_dt(B.suggest_dt(3.0, 0.5))
+        B.run(0.0, 10)
+        a = [t.cpu().numpy() for t in B.get_state()]
+        B.set_state(*(dev(a) for a in packed_state(insts)))
+        B.set_tiles([1] * len(ns))
+        B.run(0.0, 10)
+        b = [t.cpu().numpy() for t in B.get_state()]
+    assert rel_l2(b[0], a[0]) < 1e-7 and rel_l2(b[2], a[2]) < 1e-7
+
+
+def test_batched_autotune_keeps_the_state_and_a_valid_assignment():
+    insts, ns, xl, xr, lams = batch_case(16, 40, n_min=256, n_max=8192)
+    with S().BatchedSolver(ns, xl, xr, lams) as B:
+        with pytest.raises(S().HsgnError):
+            B.autotune(2)  # no time steps set yet
+        B.set_state(*(dev(a) for a in packed_state(insts)))
+        before = [t.cpu().numpy() for t in B.get_state()]
+        dts = B.suggest_dt(2.0, 0.5)
+        B.set_dt(dts)
+        r = B.autotune(3)
+        assert r["choice"] in (0, 1, 2)
+        t = r["ms_per_step"]
+        assert t[0] > 0 and t[1] > 0 and (math.isnan(t[2]) or t[2] > 0)
+        kept = t[r["choice"]]
+        assert kept == min(x for x in t if not math.isnan(x))
+        after = [t_.cpu().numpy() for t_ in B.get_state()]
+        for k in range(4):
+            np.testing.assert_array_equal(before[k], after[k])
+        B.run(0.0, 10)
+        got = [t_.cpu().numpy() for t_ in B.get_state()]
+    for k_inst in (0, 17, 39):
+        it = insts[k_inst]
+        o0, o1 = int(B.offsets[k_inst]), int(B.offsets[k_inst + 1])
+        ref = oracle.run(oracle.Params(it.n, it.dx, 0, lam=it.lam), it.state, dts[k_inst], 10)
+        assert rel_l2(got[0][o0:o1], ref[0]) < 5e-6
+
+
+def test_batched_set_tiles_rejects_bad_input():
+    insts, ns, xl, xr, lams = batch_case(17, 3)
+    with S().BatchedSolver(ns, xl, xr, lams) as B:
+        with pytest.raises(S().HsgnError) as e:
+            B.set_tiles([0, 2, 1])
+        assert e.value.code == 1
+        with pytest.raises(ValueError):
+            B.set_tiles([0, 1])
+    with S().BatchedSolver(ns, xl, xr, lams, flags=S().FLAG_MIXED | S().FLAG_EXACT_SOLVE) as B:
+        with pytest.raises(S().HsgnError) as e:
+            B.set_tiles([0, 0, 0])
+        assert e.value.code == 6

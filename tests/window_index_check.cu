@@ -1,7 +1,8 @@
 // Host-side check of the windowed stage kernel's index arithmetic
 // (k_mixed_fused in hsgn_fused.cuh): every tile geometry the library launches,
 // single grids (tile rows for several co-resident CTA counts) and batch
-// instances (one CTA slot), both boundary conditions. It evaluates the same
+// instances (one CTA slot) on both the large (256 threads) and the small (128
+// threads) windowed kernel, both boundary conditions. It evaluates the same
 // __host__ __device__ helpers the kernel calls and checks that every global
 // cell index lies in [0, n), every shared-memory index within the arrays, that
 // tiles cover the grid once, that the rows kept from a window lie HW - 1 rows
@@ -12,8 +13,7 @@
 #include "../paper_2510_07539_gb300/csrc/hsgn_fused.cuh"
 
 using namespace hsgn;
-constexpr int T = 256, M = 4, HW = 64;
-using G = FusedGeom<T, M, HW>;
+constexpr int M = 4, HW = 64;
 
 #define CHECK(c)                                                                               \
     do {                                                                                       \
@@ -26,8 +26,9 @@ using G = FusedGeom<T, M, HW>;
 
 static long long checked_windows = 0;
 
-template <int BC>
+template <int T, int BC>
 void check(int64_t n, int S) {
+    using G = FusedGeom<T, M, HW>;
     int64_t p = -1;
     CHECK(S >= 1 && S <= G::S);
     const int64_t P = (n + S - 1) / S;
@@ -94,7 +95,11 @@ void check(int64_t n, int S) {
 
 template <int BC>
 void check_grid(int64_t n) {
-    for (int64_t slots : {1, 2, 152, 304, 456, 608}) check<BC>(n, (int)fused_tile_rows(n, G::S, slots));
+    using G = FusedGeom<256, M, HW>;
+    using Gs = FusedGeom<128, M, HW>;
+    for (int64_t slots : {1, 2, 152, 304, 456, 608})
+        check<256, BC>(n, (int)fused_tile_rows(n, G::S, slots));
+    check<128, BC>(n, (int)fused_tile_rows(n, Gs::S, 1));
 }
 
 int main() {
@@ -109,13 +114,16 @@ int main() {
         check_grid<BC_TRANSMISSIVE>(n);
     }
     // windows ending 3 or 4 cells before the domain end (the edge of the direct path)
+    using G = FusedGeom<256, M, HW>;
+    using Gs = FusedGeom<128, M, HW>;
     for (int64_t k = 1; k <= 40; ++k)
         for (int64_t e = 60; e <= 72; ++e) {
-            const int64_t n = k * G::S + e;
-            check<BC_PERIODIC>(n, G::S);
-            check<BC_TRANSMISSIVE>(n, G::S);
+            check<256, BC_PERIODIC>(k * G::S + e, G::S);
+            check<256, BC_TRANSMISSIVE>(k * G::S + e, G::S);
+            check<128, BC_PERIODIC>(k * Gs::S + e, Gs::S);
+            check<128, BC_TRANSMISSIVE>(k * Gs::S + e, Gs::S);
         }
-    printf("R=%d S=%d HB=%d NC=%d windows=%lld\nall index checks passed\n", G::R, G::S, G::HB,
-           G::NC, checked_windows);
+    printf("large: R=%d S=%d NC=%d; small: R=%d S=%d NC=%d; windows=%lld\n"
+           "all index checks passed\n", G::R, G::S, G::NC, Gs::R, Gs::S, Gs::NC, checked_windows);
     return 0;
 }
