@@ -77,6 +77,8 @@ def parse_args():
                     help="skip the scheme comparison (time to solution)")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint workload")
     ap.add_argument("--no-shelf", action="store_true", help="skip the 2^24-cell shelf workload")
+    ap.add_argument("--shelf-log2n", type=int, default=24, help="cells of the shelf workload (log2)")
+    ap.add_argument("--shelf-steps", type=int, default=50, help="timed steps of the shelf workload")
     ap.add_argument("--sequential", action="store_true",
                     help="run the instances of a step back to back on one stream "
                          "(default: one CUDA stream each)")
@@ -427,7 +429,7 @@ def time_adjoint(S, torch, stream):
             "grad_bottom_l2": float(np.linalg.norm(gb.cpu().numpy()))}
 
 
-def time_shelf(S, torch, stream, steps=50, warmup=3):
+def time_shelf(S, torch, stream, log2n=24, steps=50, warmup=3):
     """The large workload: N = 2^24, dx = 0.005, transmissive, lambda = 1000, a
     wave a = 0.1 running towards a 1:20 shelf (depth 1 -> 0.5), bottom form,
     dt = min(4 dx/nu, 0.5 dx/u_max) at t = 0. FP64 and mixed precision
@@ -436,8 +438,8 @@ def time_shelf(S, torch, stream, steps=50, warmup=3):
     matches the FP64 oracle to 1e-12 per step."""
     import numpy as np
     from paper_2510_07539_gb300 import inputs as inp
-    n, lam = 1 << 24, 1000.0
-    x, dx, b, U = inp.shelf_wave(n)
+    n, lam = 1 << log2n, 1000.0
+    x, dx, b, U = inp.shelf_wave(n, dx=0.005 * (1 << 24) / n)
     Ud = [torch.tensor(u, device="cuda") for u in U]
     del U
     out, dt = {}, None
@@ -464,7 +466,15 @@ def time_shelf(S, torch, stream, steps=50, warmup=3):
                          "state": [t.cpu().numpy() for t in s.get_state()]}
     ref, got = out["fp64"].pop("state"), out["mixed"].pop("state")
     rel = [float(np.linalg.norm(got[k] - ref[k]) / np.linalg.norm(ref[k])) for k in range(4)]
-    return {"workload": f"wave a = 0.1 towards a 1:20 shelf, N = 2^24, dx = 0.005, "
+    # the mixed bottom form must move 72 B per cell and stage (state and bottom
+    # pairs read, increments written and read back, new state written)
+    gbs = 72.0 * 2.0 * n * steps / (out["mixed"]["ms_per_step"] * steps / 1e3) / 1e9
+    tpc = profiled_traffic_per_cell("ncu_mixed_fused_bottom.md")
+    out["mixed"]["roofline"] = {"bound": "hbm", "kernel": "k_mixed_fused (bottom form)",
+                                "achieved": gbs, "unit": "GB/s",
+                                "algorithmic_bytes_per_cell_stage": 72,
+                                "traffic_per_launch": tpc * n if tpc is not None else None}
+    return {"workload": f"wave a = 0.1 towards a 1:20 shelf, N = 2^{log2n}, dx = {dx:g}, "
                         f"transmissive, lambda = 1000, bottom form, dt = {dt:.6g} "
                         f"(CFL_IMEX 4), {steps} timed steps (of the 5000-step run)",
             "fp64": out["fp64"], "mixed": out["mixed"],
@@ -591,7 +601,7 @@ def run_ours(args):
         adjoint = time_adjoint(S, torch, stream)
     shelf = None
     if not args.no_shelf and rank == 0:
-        shelf = time_shelf(S, torch, stream)
+        shelf = time_shelf(S, torch, stream, args.shelf_log2n, args.shelf_steps)
 
     # ---- batched workload: 4096 independent periodic solitary waves of uneven
     #      length, the windowed mixed stage over all of them: one launch per stage
