@@ -144,13 +144,28 @@ int hsgn_create(const hsgn_grid_t* grid, double g, double lambda, const double* 
 
 /* Copy a state in (U = (h, q, h eta, h w), n values each) and recompute the
  * global Rusanov speed. The caller keeps ownership of the arrays. Does not
- * synchronise; the arrays must stay valid until the stream reaches the copy. */
+ * synchronise; the arrays must stay valid until the stream reaches the copy.
+ * With HSGN_MIXED (windowed) the state is held as double-float pairs: arrays
+ * in this device's memory are converted directly, host arrays are copied by
+ * the copy engines into a device buffer and converted there (pageable host
+ * memory makes the copy synchronous with respect to the host). */
 int hsgn_set_state(hsgn_handle_t h, const double* depth, const double* q, const double* heta,
                    const double* hw, void* stream);
 
-/* Copy the state out. Synchronises and reports pending device errors. */
+/* Copy the state out (the pairs of the windowed form are summed exactly into
+ * doubles). Synchronises `stream` only and reports pending device errors. */
 int hsgn_get_state(hsgn_handle_t h, double* depth, double* q, double* heta, double* hw,
                    void* stream);
+
+/* hsgn_get_state without the synchronisation: the copy out is enqueued on
+ * `stream` and the arrays hold the state once the stream reaches it; pending
+ * device errors are reported by the next synchronising call. The windowed form
+ * stages the pairs through its idle state buffer, which the next step
+ * overwrites: enqueue further steps on the same stream (or synchronise first).
+ * Lets a host loop pipeline state in, steps and state out over several
+ * handles and streams. */
+int hsgn_copy_state_out(hsgn_handle_t h, double* depth, double* q, double* heta, double* hw,
+                        void* stream);
 
 /* One IMEX step of size dt > 0 (Sec. 3.2): two implicit stages with
  * tau = gamma dt, gamma = 1 - 1/sqrt(2). Enqueues six kernels; does not

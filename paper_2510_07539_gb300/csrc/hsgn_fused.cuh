@@ -812,6 +812,59 @@ __global__ void k_speeds_df(int64_t n, const float2* h, const float2* q, const f
     }
 }
 
+// Global Rusanov speed max |u| of a double-float state in single precision,
+// u = |q.hi| / h.hi rounded once: the stage kernels use the speed in single
+// precision. Cheaper than k_speeds_df, whose double-precision divisions and
+// square root run on the slow FP64 pipe; that kernel stays for the time-step
+// rule. out must be zero on entry.
+__global__ void k_umax_df(int64_t n, const float2* __restrict__ h, const float2* __restrict__ q,
+                          double* out, unsigned* err) {
+    float um = 0.f;
+    bool bad = false;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const float hv = h[i].x;
+        if (!pos_finite(hv)) {
+            bad = true;
+            continue;
+        }
+        um = fmaxf(um, __fdiv_rn(fabsf(q[i].x), hv));
+    }
+    if (bad) flag_error(err, HSGN_DEV_ERR_DEPTH);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) um = fmaxf(um, __shfl_xor_sync(0xffffffffu, um, o));
+    if ((threadIdx.x & 31) == 0 && um > 0.f)
+        atomicMax(reinterpret_cast<unsigned long long*>(out),
+                  (unsigned long long)__double_as_longlong(f64_of(um)));
+}
+
+// k_umax_df per instance of a batch: one CTA per instance, out[k] = max |u|.
+__global__ void __launch_bounds__(256) k_umax_batched_df(const InstInfo* inst, const float2* h,
+                                                         const float2* q, double* out,
+                                                         unsigned* err) {
+    __shared__ float ru[8];
+    const InstInfo I = inst[blockIdx.x];
+    float um = 0.f;
+    bool bad = false;
+    for (int64_t i = I.cell0 + threadIdx.x; i < I.cell0 + I.n; i += blockDim.x) {
+        const float hv = h[i].x;
+        if (!pos_finite(hv)) {
+            bad = true;
+            continue;
+        }
+        um = fmaxf(um, __fdiv_rn(fabsf(q[i].x), hv));
+    }
+    if (bad) flag_error(err, HSGN_DEV_ERR_DEPTH);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) um = fmaxf(um, __shfl_xor_sync(0xffffffffu, um, o));
+    if ((threadIdx.x & 31) == 0) ru[threadIdx.x >> 5] = um;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) um = fmaxf(um, ru[w]);
+        out[blockIdx.x] = f64_of(um);
+    }
+}
+
 // k_speeds_batched (hsgn_mixed.cuh) for a batch held as double-float pairs:
 // per-instance max |u| and max nu, one CTA per instance.
 __global__ void __launch_bounds__(256) k_speeds_batched_df(const InstInfo* inst, const float2* h,

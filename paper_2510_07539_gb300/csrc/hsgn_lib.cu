@@ -625,13 +625,34 @@ void launch_speeds(hsgn_s* H, double* out, cudaStream_t st) {
 }
 
 // Recompute the global Rusanov speed max |u| of the current state.
+// A caller buffer the state conversions can address directly: memory of
+// this handle's device. Host memory (page-locked or not) goes through
+// cudaMemcpyAsync and the idle state buffer: the copy engines move it as fast
+// as kernels reading the host link would, and leave the SMs free for the work
+// of other streams.
+const void* device_view(const hsgn_s* H, const void* p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    if (a.type == cudaMemoryTypeDevice && a.device == H->device) return p;
+    return nullptr;
+}
+
+// Grid of the state conversions and of the speed refresh.
+unsigned convert_blocks(const hsgn_s* H) {
+    const int64_t want = (H->n + 255) / 256;
+    return (unsigned)(want < 4864 ? (want > 0 ? want : 1) : 4864);
+}
+
 cudaError_t refresh_speed(hsgn_s* H, cudaStream_t st) {
     if (H->batched) {
         if (H->windowed) {
             double* const* U = state(H);
-            k_speeds_batched_df<<<(unsigned)H->count, 256, 0, st>>>(
+            k_umax_batched_df<<<(unsigned)H->count, 256, 0, st>>>(
                 H->inst, reinterpret_cast<const float2*>(U[0]), reinterpret_cast<const float2*>(U[1]),
-                reinterpret_cast<const float2*>(U[2]), H->g, speed_of(H, H->cur), nullptr, H->err);
+                speed_of(H, H->cur), H->err);
         } else {
             k_speeds_batched<<<(unsigned)H->count, 256, 0, st>>>(H->inst, H->U[0], H->U[1],
                                                                  H->U[2], H->g, H->speeds, nullptr,
@@ -642,7 +663,14 @@ cudaError_t refresh_speed(hsgn_s* H, cudaStream_t st) {
     double* out = speed_of(H, H->cur);
     cudaError_t e = cudaMemsetAsync(out, 0, 2 * sizeof(double), st);
     if (e != cudaSuccess) return e;
-    launch_speeds(H, out, st);
+    if (H->windowed) {
+        double* const* U = state(H);
+        k_umax_df<<<convert_blocks(H), 256, 0, st>>>(H->n, reinterpret_cast<const float2*>(U[0]),
+                                                     reinterpret_cast<const float2*>(U[1]), out,
+                                                     H->err);
+    } else {
+        launch_speeds(H, out, st);
+    }
     return cudaGetLastError();
 }
 
@@ -897,38 +925,65 @@ int hsgn_set_state(hsgn_handle_t H, const double* depth, const double* q, const 
     if (!H || !depth || !q || !heta || !hw) return HSGN_ERR_INVALID_ARG;
     cudaStream_t st = as_stream(stream);
     const double* src[4] = {depth, q, heta, hw};
-    // the windowed path holds double-float pairs: stage through the idle buffer
-    double* const* dst = H->windowed ? (H->cur ? H->U : H->V) : state(H);
-    for (int k = 0; k < 4; ++k)
-        if (cudaMemcpyAsync(dst[k], src[k], H->n * sizeof(double), cudaMemcpyDefault, st) !=
-            cudaSuccess)
-            return HSGN_ERR_CUDA;
-    if (H->windowed) {
+    if (!H->windowed) {
         for (int k = 0; k < 4; ++k)
-            k_df_from_f64<<<1216, 256, 0, st>>>(H->n, dst[k], reinterpret_cast<float2*>(state(H)[k]));
-        if (cudaGetLastError() != cudaSuccess) return HSGN_ERR_CUDA;
+            if (cudaMemcpyAsync(state(H)[k], src[k], H->n * sizeof(double), cudaMemcpyDefault,
+                                st) != cudaSuccess)
+                return HSGN_ERR_CUDA;
+        return refresh_speed(H, st) == cudaSuccess ? HSGN_OK : HSGN_ERR_CUDA;
     }
+    // the windowed path holds double-float pairs: converted straight from the
+    // caller's buffer when the device can address it (device memory of this
+    // device, page-locked host memory mapped into the device's address space),
+    // else copied to the idle buffer first
+    double* const* idle = H->cur ? H->U : H->V;
+    for (int k = 0; k < 4; ++k) {
+        const double* v = static_cast<const double*>(device_view(H, src[k]));
+        if (!v) {
+            if (cudaMemcpyAsync(idle[k], src[k], H->n * sizeof(double), cudaMemcpyDefault, st) !=
+                cudaSuccess)
+                return HSGN_ERR_CUDA;
+            v = idle[k];
+        }
+        k_df_from_f64<<<convert_blocks(H), 256, 0, st>>>(H->n, v,
+                                                         reinterpret_cast<float2*>(state(H)[k]));
+    }
+    if (cudaGetLastError() != cudaSuccess) return HSGN_ERR_CUDA;
     return refresh_speed(H, st) == cudaSuccess ? HSGN_OK : HSGN_ERR_CUDA;
 }
 
 int hsgn_get_state(hsgn_handle_t H, double* depth, double* q, double* heta, double* hw,
                    void* stream) {
+    const int rc = hsgn_copy_state_out(H, depth, q, heta, hw, stream);
+    if (rc != HSGN_OK) return rc;
+    return read_error(H, as_stream(stream));
+}
+
+int hsgn_copy_state_out(hsgn_handle_t H, double* depth, double* q, double* heta, double* hw,
+                        void* stream) {
     if (!H || !depth || !q || !heta || !hw) return HSGN_ERR_INVALID_ARG;
     cudaStream_t st = as_stream(stream);
     double* dst[4] = {depth, q, heta, hw};
     double* const* src = state(H);
-    if (H->windowed) {  // pairs to doubles in the idle buffer
+    if (H->windowed) {
+        // pairs to doubles: straight into the caller's buffer when the device
+        // can address it, else through the idle buffer and a copy
         double* const* tmp = H->cur ? H->U : H->V;
-        for (int k = 0; k < 4; ++k)
-            k_f64_from_df<<<1216, 256, 0, st>>>(H->n, reinterpret_cast<const float2*>(src[k]), tmp[k]);
-        if (cudaGetLastError() != cudaSuccess) return HSGN_ERR_CUDA;
-        src = tmp;
+        for (int k = 0; k < 4; ++k) {
+            double* v = static_cast<double*>(const_cast<void*>(device_view(H, dst[k])));
+            k_f64_from_df<<<convert_blocks(H), 256, 0, st>>>(
+                H->n, reinterpret_cast<const float2*>(src[k]), v ? v : tmp[k]);
+            if (!v && cudaMemcpyAsync(dst[k], tmp[k], H->n * sizeof(double), cudaMemcpyDefault,
+                                      st) != cudaSuccess)
+                return HSGN_ERR_CUDA;
+        }
+        return cudaGetLastError() == cudaSuccess ? HSGN_OK : HSGN_ERR_CUDA;
     }
     for (int k = 0; k < 4; ++k)
         if (cudaMemcpyAsync(dst[k], src[k], H->n * sizeof(double), cudaMemcpyDefault, st) !=
             cudaSuccess)
             return HSGN_ERR_CUDA;
-    return read_error(H, st);
+    return HSGN_OK;
 }
 
 // dt of a step: positive and finite for one instance, 0 for a batch (which

@@ -65,6 +65,7 @@ def load():
         "hsgn_create": [ctypes.POINTER(Grid), _D, _D, _P, ctypes.c_int32, ctypes.POINTER(_P)],
         "hsgn_set_state": [_P, _P, _P, _P, _P, _P],
         "hsgn_get_state": [_P, _P, _P, _P, _P, _P],
+        "hsgn_copy_state_out": [_P, _P, _P, _P, _P, _P],
         "hsgn_step": [_P, _D, _P],
         "hsgn_run": [_P, _D, _I64, _P],
         "hsgn_enqueue": [_P, _D, _I64, _P],
@@ -167,6 +168,14 @@ class Solver:
             out = [torch.empty(self.n, dtype=torch.float64, device=device) for _ in range(4)]
         _check(_lib.hsgn_get_state(self._h, *(_ptr(t) for t in out), _stream(stream)),
                "hsgn_get_state")
+        return tuple(out)
+
+    def copy_state_out(self, out, stream=None):
+        """Enqueue the copy of the state into `out` (four float64 tensors,
+        device or pinned host) without waiting; errors surface at the next
+        synchronising call (check, run, get_state)."""
+        _check(_lib.hsgn_copy_state_out(self._h, *(_ptr(t) for t in out), _stream(stream)),
+               "hsgn_copy_state_out")
         return tuple(out)
 
     def step(self, dt: float, stream=None):

@@ -546,3 +546,66 @@ def test_batched_set_tiles_rejects_bad_input():
         with pytest.raises(S().HsgnError) as e:
             B.set_tiles([0, 0, 0])
         assert e.value.code == 6
+
+
+# --------------------------------------------------------------------------
+# state exchange with host buffers: page-locked host memory is converted in
+# place by the device, pageable memory goes through a copy; every route gives
+# the same bits
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("flags", ["mixed", "fp64"])
+def test_state_exchange_routes_agree(flags):
+    n, dx = 70001, 0.1
+    U = inputs.random_state(99, n, dx)
+    fl = S().FLAG_MIXED if flags == "mixed" else S().FLAG_FP64
+    outs = {}
+    for route in ("device", "pinned", "pageable"):
+        with S().Solver(n, 0.0, n * dx, 0, lam=300.0, flags=fl) as s:
+            if route == "device":
+                src = [dev(u) for u in U]
+                dst = [torch.empty(n, dtype=torch.float64, device="cuda") for _ in range(4)]
+            elif route == "pinned":
+                src = [torch.tensor(u).pin_memory() for u in U]
+                dst = [torch.empty(n, dtype=torch.float64).pin_memory() for _ in range(4)]
+            else:
+                src = [torch.tensor(u) for u in U]
+                dst = [torch.empty(n, dtype=torch.float64) for _ in range(4)]
+            s.set_state(*src)
+            back = [t.cpu().numpy().copy() for t in s.get_state(out=dst)]
+            for k in range(4):  # the round trip is exact (pairs hold 48 bits)
+                np.testing.assert_array_equal(back[k], np.float64(np.float32(U[k])) + (
+                    U[k] - np.float64(np.float32(U[k]))).astype(np.float32).astype(np.float64)
+                    if flags == "mixed" else U[k])
+            s.set_state(*src)
+            s.run(0.01, 3)
+            outs[route] = [t.cpu().numpy().copy() for t in s.get_state(out=dst)]
+    for route in ("pinned", "pageable"):
+        for k in range(4):
+            np.testing.assert_array_equal(outs[route][k], outs["device"][k])
+
+
+@pytest.mark.parametrize("flags", ["mixed", "fp64"])
+def test_copy_state_out_is_stream_ordered(flags):
+    # the enqueued copy holds the state at its point in the stream, although
+    # the windowed form stages it through the buffer the next step overwrites
+    n, dx = 5001, 0.1
+    U = inputs.random_state(98, n, dx)
+    fl = S().FLAG_MIXED if flags == "mixed" else S().FLAG_FP64
+    st = torch.cuda.Stream()
+    with S().Solver(n, 0.0, n * dx, 0, lam=300.0, flags=fl) as s:
+        s.set_state(*(dev(u) for u in U), stream=st)
+        s.step(0.01, stream=st)
+        out1 = [torch.empty(n, dtype=torch.float64).pin_memory() for _ in range(4)]
+        out2 = [torch.empty(n, dtype=torch.float64, device="cuda") for _ in range(4)]
+        s.copy_state_out(out1, stream=st)
+        s.step(0.01, stream=st)
+        s.copy_state_out(out2, stream=st)
+        st.synchronize()
+        s.check()
+        a = [t.numpy().copy() for t in out1]
+        b = [t.cpu().numpy() for t in out2]
+    ref1 = gpu_run(n, 0.0, n * dx, 0, 300.0, U, 0.01, 1, flags=fl)
+    ref2 = gpu_run(n, 0.0, n * dx, 0, 300.0, U, 0.01, 2, flags=fl)
+    for k in range(4):
+        np.testing.assert_array_equal(a[k], ref1[k])
+        np.testing.assert_array_equal(b[k], ref2[k])
