@@ -44,6 +44,13 @@ constexpr size_t kAlign = 256;
 // resident CTAs ends in full waves.
 constexpr size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 
+// Rows per block of a single grid's FP64 / exact mixed stage for `slots`
+// co-resident CTAs: as many rows as one wave needs, within [64, AS].
+int64_t stage_block_rows(int64_t n, int64_t slots) {
+    const int64_t r = (n + slots - 1) / slots;
+    return r < 64 ? 64 : (r > AS ? AS : r);
+}
+
 BlockSplit make_split(int64_t n, int64_t rows_per_block) {
     BlockSplit s;
     s.n = n;
@@ -772,7 +779,31 @@ int hsgn_create(const hsgn_grid_t* grid, double g, double lambda, const double* 
     H->g = g;
     H->lam = lambda;
     cudaGetDevice(&H->device);
-    H->split = make_split(H->n, AS);
+    {
+        // rows per block of the FP64 stage: AS when the grid
+        // fills a wave of co-resident CTAs; for smaller grids shorter blocks
+        // (down to 64 rows, one per thread), which shortens the serial chunk
+        // elimination of each CTA (a division per row on the FP64 pipe)
+        int sms = 0, per_sm = 0;
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, H->device);
+        // the occupancy query needs the opt-in shared-memory size set first
+        set_smem(k_stage_assemble<AT, AM, BC_PERIODIC, false>, sizeof(AssembleShared<AT, AM>));
+        set_smem(k_stage_assemble<AT, AM, BC_PERIODIC, true>, sizeof(AssembleShared<AT, AM, true>));
+        if (H->wb)
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                &per_sm, k_stage_assemble<AT, AM, BC_PERIODIC, true>, AT,
+                sizeof(AssembleShared<AT, AM, true>));
+        else
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                &per_sm, k_stage_assemble<AT, AM, BC_PERIODIC, false>, AT,
+                sizeof(AssembleShared<AT, AM>));
+        cudaGetLastError();
+        // (the exact mixed form keeps AS rows, as its batches do, so that an
+        // instance evolves bitwise alike alone and in a batch)
+        H->split = make_split(H->n, (flags & HSGN_MIXED) ? (int64_t)AS
+                                    : stage_block_rows(H->n, (int64_t)(sms > 0 ? sms : 1) *
+                                                                 (per_sm > 0 ? per_sm : 1)));
+    }
     const int64_t n = H->n, P = H->split.P;
 
     H->mixed = (flags & HSGN_MIXED) != 0;
