@@ -287,3 +287,20 @@ def test_wb_mixed_shelf_2_24_steps():
     assert rel_l2(got[0], ref[0]) < 1e-7 and rel_l2(got[2], ref[2]) < 1e-7
     assert np.linalg.norm(got[1] - ref[1]) / np.linalg.norm(Sq) < 1e-6
     assert np.linalg.norm(got[3] - ref[3]) / np.linalg.norm(Sr) < 1e-6
+
+
+@pytest.mark.parametrize("bc", [0, 1])
+@pytest.mark.parametrize("n", [3, 4, 7])
+def test_wb_mixed_tiny_grids(n, bc):
+    dx, lam = 0.1, 300.0
+    x, _ = inputs.cell_centres(n, 0.0, n * dx)
+    b = inputs.gaussian_bathymetry(90 + n, x, amp_max=0.1)
+    U = inputs.random_state(5000 + n + 10 * bc, n, dx)
+    p = oracle.Params(n, dx, bc, lam=lam, form=1, bathy=b)
+    dt, _, _ = oracle.suggest_dt(p, U, 2.0, 0.5)
+    got = wb_mixed_run(n, dx, bc, lam, b, U, dt, 2)
+    ref = oracle.run(p, U, dt, 2)
+    Sq, Sr = wb_scales(p, U, dt)
+    assert rel_l2(got[0], ref[0]) < 1e-7 and rel_l2(got[2], ref[2]) < 1e-7
+    assert np.linalg.norm(got[1] - ref[1]) / np.linalg.norm(Sq) < 1e-6
+    assert np.linalg.norm(got[3] - ref[3]) / np.linalg.norm(Sr) < 1e-6

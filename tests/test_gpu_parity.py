@@ -609,3 +609,60 @@ def test_copy_state_out_is_stream_ordered(flags):
     for k in range(4):
         np.testing.assert_array_equal(a[k], ref1[k])
         np.testing.assert_array_equal(b[k], ref2[k])
+
+
+# --------------------------------------------------------------------------
+# edge cases of the windowed kernel and the batched workload at full size
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("lam", [0.0, 500.0])
+@pytest.mark.parametrize("bc", [0, 1])
+@pytest.mark.parametrize("n", [3, 4])
+def test_windowed_tiny_grids_and_shallow_water_limit(n, bc, lam):
+    # three and four cells: the periodic window is the ring unrolled many
+    # times, the transmissive one is the whole grid with both Neumann ends;
+    # lambda = 0 is the shallow-water limit (no relaxation terms). The step
+    # amplifies a perturbation of these random states by 1.3-2 per step (the
+    # oracle run on a perturbed state shows it), so the single-precision
+    # rounding each step adds (up to about 5e-8) reaches about 1.5e-7 after 3
+    # steps: the bound is 3e-7
+    dx = 0.1
+    U = inputs.random_state(4000 + n + 10 * bc, n, dx)
+    p = oracle.Params(n, dx, bc, lam=lam)
+    dt, _, _ = oracle.suggest_dt(p, U, 2.0, 0.5)
+    got = mixed_run(n, 0.0, n * dx, bc, lam, U, dt, 3)
+    ref = oracle.run(p, U, dt, 3)
+    sc = summand_scales(n, dx, bc, lam, U, dt)
+    assert rel_l2(got[0], ref[0]) < 3e-7 and rel_l2(got[2], ref[2]) < 3e-7
+    for k in (1, 3):
+        assert scaled_err(got[k], ref[k], sc[k]) < 1e-6, (k, scaled_err(got[k], ref[k], sc[k]))
+    if bc == 0:
+        assert abs(math.fsum(got[0]) - math.fsum(U[0])) <= 1e-13 * math.fsum(U[0])
+
+
+def test_batched_workload_full_size_sampled():
+    # the benchmark's batch as the benchmark runs it: 4096 periodic solitary
+    # waves of 256 .. 8192 cells, per-instance dt at CFL_IMEX 2, tiles picked by
+    # the autotuner; 10 steps; sampled instances against the oracle, mass of
+    # every instance
+    insts = inputs.batched_instances(inputs.SEED_BASE + 3, 4096)
+    ns = [it.n for it in insts]
+    xl = [-0.5 * it.n * it.dx for it in insts]
+    xr = [0.5 * it.n * it.dx for it in insts]
+    with S().BatchedSolver(ns, xl, xr, [it.lam for it in insts]) as B:
+        B.set_state(*(dev(a) for a in packed_state(insts)))
+        dts = B.suggest_dt(2.0, 0.5)
+        B.set_dt(dts)
+        B.autotune(2)
+        B.run(0.0, 10)
+        got = [t.cpu().numpy() for t in B.get_state()]
+    off = B.offsets
+    for k_inst in (0, 1, 777, 2048, 3333, 4095):
+        it = insts[k_inst]
+        ref = oracle.run(oracle.Params(it.n, it.dx, 0, lam=it.lam), it.state, dts[k_inst], 10)
+        o0, o1 = int(off[k_inst]), int(off[k_inst + 1])
+        assert rel_l2(got[0][o0:o1], ref[0]) < 5e-6, (k_inst, rel_l2(got[0][o0:o1], ref[0]))
+        assert rel_l2(got[2][o0:o1], ref[2]) < 5e-6
+    for k_inst, it in enumerate(insts):
+        o0, o1 = int(off[k_inst]), int(off[k_inst + 1])
+        m0 = math.fsum(it.state[0])
+        assert abs(math.fsum(got[0][o0:o1]) - m0) <= 1e-13 * m0, k_inst
