@@ -136,8 +136,10 @@ typedef struct hsgn_s* hsgn_handle_t;
  * during the call; the caller keeps ownership), which requires
  * HSGN_WELL_BALANCED (INVALID_ARG otherwise). HSGN_WELL_BALANCED with NULL
  * runs the well-balanced form over a flat bottom. Allocates the state and
- * workspace on the current device (about 17 doubles per cell in FP64, 19 with
- * a bottom, 4 doubles and 17 floats per cell with HSGN_MIXED).
+ * workspace on the current device: about 17 doubles per cell in FP64 (19 with
+ * a bottom); 80 bytes per cell with HSGN_MIXED (two state buffers of
+ * double-float pairs and four single-precision increments; 88 with a bottom);
+ * 4 doubles and 16 floats per cell with HSGN_MIXED | HSGN_EXACT_SOLVE.
  * On success *out owns them until hsgn_destroy. */
 int hsgn_create(const hsgn_grid_t* grid, double g, double lambda, const double* bathymetry,
                 int32_t flags, hsgn_handle_t* out);
