@@ -1179,7 +1179,12 @@ struct AdjWork {
     double* J = nullptr;
     int64_t* cells = nullptr;
     double* data = nullptr;
+    double* dseg = nullptr;     // gauge data of the current segment, K x n_gauges
     size_t work_bytes = 0;      // cellw + facew, zeroed per stage adjoint
+    // a full segment of K steps is the same launch sequence for every segment
+    // once its checkpoint is in seg[0] and its gauge data in dseg: captured
+    // once per kind (forward with the misfit, forward, reverse) and replayed
+    cudaGraphExec_t g_fwd_misfit = nullptr, g_fwd = nullptr, g_rev = nullptr;
 };
 
 Ptr4 cp4(const double* b, int64_t n) {
@@ -1357,8 +1362,10 @@ int hsgn_adjoint(hsgn_handle_t H, double dt, int64_t n_steps, int64_t n_gauges,
     const size_t gcb = align_up((size_t)(n_gauges > 0 ? n_gauges : 1) * sizeof(int64_t));
     const size_t gdb = align_up((size_t)(n_gauges > 0 ? n_gauges : 1) * (size_t)n_steps *
                                 sizeof(double));
-    const size_t total = (size_t)W.nck * s4 + (size_t)(W.K + 1) * s4 + 10 * s4 + cellb + faceb +
-                         swsb + align_up(4 * sizeof(unsigned long long)) + gcb + gdb;
+    const size_t dsb = align_up((size_t)(n_gauges > 0 ? n_gauges : 1) * (size_t)W.K *
+                                sizeof(double));
+    const size_t total = (size_t)W.nck * s4 + (size_t)(W.K + 1) * s4 + 8 * s4 + cellb + faceb +
+                         swsb + align_up(4 * sizeof(unsigned long long)) + gcb + gdb + dsb;
     if (cudaMalloc(&W.mem, total) != cudaSuccess) {
         cudaGetLastError();
         return HSGN_ERR_OUT_OF_MEMORY;
@@ -1376,8 +1383,6 @@ int hsgn_adjoint(hsgn_handle_t H, double dt, int64_t n_steps, int64_t n_gauges,
     // Ab and Al are contiguous (one memset clears both)
     W.Ab = reinterpret_cast<double*>(take(2 * s4));
     W.Al = W.Ab + 4 * n;
-    double* cur = reinterpret_cast<double*>(take(s4));
-    double* nxt = reinterpret_cast<double*>(take(s4));
     W.cellw = reinterpret_cast<double*>(take(cellb));
     W.facew = reinterpret_cast<double*>(take(faceb));
     W.work_bytes = cellb + faceb;  // contiguous
@@ -1387,6 +1392,7 @@ int hsgn_adjoint(hsgn_handle_t H, double dt, int64_t n_steps, int64_t n_gauges,
     W.J = reinterpret_cast<double*>(W.sbits + 3);
     W.cells = reinterpret_cast<int64_t*>(take(gcb));
     W.data = reinterpret_cast<double*>(take(gdb));
+    W.dseg = reinterpret_cast<double*>(take(dsb));
     // Ab/Al: 2*s4 holds 8n doubles only when s4 has no padding between the halves
     int rc = HSGN_OK;
     cudaError_t e = cudaSuccess;
@@ -1398,38 +1404,93 @@ int hsgn_adjoint(hsgn_handle_t H, double dt, int64_t n_steps, int64_t n_gauges,
                             cudaMemcpyDefault, st));
     }
     chk(cudaMemsetAsync(W.J, 0, sizeof(double), st));
+    const size_t sd = s4 / sizeof(double);
+    const unsigned gg = (unsigned)((n_gauges + 255) / 256);
+    double* const seg = W.seg;
+    // L steps from seg[0] into seg[1..L], with the misfit of each new state
+    auto fwd_segment = [&](int64_t L, bool misfit, cudaStream_t s) -> cudaError_t {
+        for (int64_t j = 0; j < L; ++j) {
+            cudaError_t x = adj_forward_step(H, W, seg + (size_t)j * sd, seg + (size_t)(j + 1) * sd,
+                                             dt, s);
+            if (x != cudaSuccess) return x;
+            if (misfit && n_gauges > 0)
+                k_adj_gauges<<<gg, 256, 0, s>>>(n_gauges, W.cells, W.dseg + j * n_gauges,
+                                                seg + (size_t)(j + 1) * sd, dt, W.J, nullptr);
+        }
+        return cudaGetLastError();
+    };
+    // the adjoints of steps L-1 .. 0 of the segment, seg[0..L] holding its states
+    auto rev_segment = [&](int64_t L, cudaStream_t s) -> cudaError_t {
+        for (int64_t j = L - 1; j >= 0; --j) {
+            if (n_gauges > 0)
+                k_adj_gauges<<<gg, 256, 0, s>>>(n_gauges, W.cells, W.dseg + j * n_gauges,
+                                                seg + (size_t)(j + 1) * sd, dt, nullptr, W.Ua);
+            cudaError_t x = adj_step(H, W, seg + (size_t)j * sd, dt, grad_bathymetry, s);
+            if (x != cudaSuccess) return x;
+        }
+        return cudaGetLastError();
+    };
+    // run a full segment through its graph (captured on first use)
+    auto replay = [&](cudaGraphExec_t& g, auto body) -> cudaError_t {
+        if (!g) {
+            const bool prof = H->prof;
+            H->prof = false;  // events are not captured into graphs
+            cudaGraph_t graph = nullptr;
+            cudaError_t x = cudaStreamBeginCapture(H->cap, cudaStreamCaptureModeThreadLocal);
+            if (x == cudaSuccess) {
+                const cudaError_t xb = body(H->cap);
+                x = cudaStreamEndCapture(H->cap, &graph);
+                if (x == cudaSuccess) x = xb;
+            }
+            H->prof = prof;
+            if (x == cudaSuccess) x = cudaGraphInstantiate(&g, graph, 0);
+            if (graph) cudaGraphDestroy(graph);
+            if (x != cudaSuccess) {
+                g = nullptr;
+                return x;
+            }
+        }
+        return cudaGraphLaunch(g, st);
+    };
+    auto stage_data = [&](int64_t s0, int64_t L) {
+        if (n_gauges > 0)
+            chk(cudaMemcpyAsync(W.dseg, W.data + s0 * n_gauges,
+                                (size_t)L * n_gauges * sizeof(double), cudaMemcpyDeviceToDevice,
+                                st));
+    };
     // forward: checkpoints every K steps, the misfit after every step
     for (int k = 0; k < 4; ++k)
-        chk(cudaMemcpyAsync(cur + k * n, H->U[k], n * sizeof(double), cudaMemcpyDeviceToDevice, st));
-    const unsigned gg = (unsigned)((n_gauges + 255) / 256);
-    for (int64_t s = 0; s < n_steps && e == cudaSuccess; ++s) {
-        if (s % W.K == 0)
-            chk(cudaMemcpyAsync(W.ck + (size_t)(s / W.K) * (s4 / sizeof(double)), cur,
-                                4 * n * sizeof(double), cudaMemcpyDeviceToDevice, st));
-        chk(adj_forward_step(H, W, cur, nxt, dt, st));
-        if (n_gauges > 0)
-            k_adj_gauges<<<gg, 256, 0, st>>>(n_gauges, W.cells, W.data + s * n_gauges, nxt, dt,
-                                             W.J, nullptr);
-        std::swap(cur, nxt);
+        chk(cudaMemcpyAsync(seg + k * n, H->U[k], n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    for (int64_t cix = 0; cix < W.nck && e == cudaSuccess; ++cix) {
+        const int64_t s0 = cix * W.K, L = std::min(W.K, n_steps - s0);
+        chk(cudaMemcpyAsync(W.ck + (size_t)cix * sd, seg, 4 * n * sizeof(double),
+                            cudaMemcpyDeviceToDevice, st));
+        stage_data(s0, L);
+        if (e != cudaSuccess) break;
+        if (L == W.K)
+            chk(replay(W.g_fwd_misfit, [&](cudaStream_t s) { return fwd_segment(L, true, s); }));
+        else
+            chk(fwd_segment(L, true, st));
+        chk(cudaMemcpyAsync(seg, seg + (size_t)L * sd, 4 * n * sizeof(double),
+                            cudaMemcpyDeviceToDevice, st));
     }
     for (int k = 0; k < 4 && e == cudaSuccess; ++k)
-        chk(cudaMemcpyAsync(H->U[k], cur + k * n, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
-    // reverse, one segment at a time
+        chk(cudaMemcpyAsync(H->U[k], seg + k * n, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    // reverse, one segment at a time: its states recomputed from the checkpoint
     chk(cudaMemsetAsync(W.Ua, 0, 4 * n * sizeof(double), st));
     if (grad_bathymetry) chk(cudaMemsetAsync(grad_bathymetry, 0, n * sizeof(double), st));
-    const size_t sd = s4 / sizeof(double);
     for (int64_t cix = W.nck - 1; cix >= 0 && e == cudaSuccess; --cix) {
-        const int64_t s0 = cix * W.K, s1 = std::min(n_steps, s0 + W.K);
-        chk(cudaMemcpyAsync(W.seg, W.ck + (size_t)cix * sd, 4 * n * sizeof(double),
+        const int64_t s0 = cix * W.K, L = std::min(W.K, n_steps - s0);
+        chk(cudaMemcpyAsync(seg, W.ck + (size_t)cix * sd, 4 * n * sizeof(double),
                             cudaMemcpyDeviceToDevice, st));
-        for (int64_t j = 0; j < s1 - s0 && e == cudaSuccess; ++j)
-            chk(adj_forward_step(H, W, W.seg + (size_t)j * sd, W.seg + (size_t)(j + 1) * sd, dt, st));
-        for (int64_t s = s1 - 1; s >= s0 && e == cudaSuccess; --s) {
-            const double* Uafter = W.seg + (size_t)(s - s0 + 1) * sd;
-            if (n_gauges > 0)
-                k_adj_gauges<<<gg, 256, 0, st>>>(n_gauges, W.cells, W.data + s * n_gauges, Uafter,
-                                                 dt, nullptr, W.Ua);
-            chk(adj_step(H, W, W.seg + (size_t)(s - s0) * sd, dt, grad_bathymetry, st));
+        stage_data(s0, L);
+        if (e != cudaSuccess) break;
+        if (L == W.K) {
+            chk(replay(W.g_fwd, [&](cudaStream_t s) { return fwd_segment(L, false, s); }));
+            chk(replay(W.g_rev, [&](cudaStream_t s) { return rev_segment(L, s); }));
+        } else {
+            chk(fwd_segment(L, false, st));
+            chk(rev_segment(L, st));
         }
     }
     if (grad_state)
@@ -1443,6 +1504,8 @@ int hsgn_adjoint(hsgn_handle_t H, double dt, int64_t n_steps, int64_t n_gauges,
     if (e == cudaSuccess) rc = read_error(H, st);  // synchronises
     else rc = HSGN_ERR_CUDA;
     cudaStreamSynchronize(st);
+    for (cudaGraphExec_t g : {W.g_fwd_misfit, W.g_fwd, W.g_rev})
+        if (g) cudaGraphExecDestroy(g);
     cudaFree(W.mem);
     return rc;
 }
