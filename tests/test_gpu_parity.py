@@ -666,3 +666,27 @@ def test_batched_workload_full_size_sampled():
         o0, o1 = int(off[k_inst]), int(off[k_inst + 1])
         m0 = math.fsum(it.state[0])
         assert abs(math.fsum(got[0][o0:o1]) - m0) <= 1e-13 * m0, k_inst
+
+
+@pytest.mark.parametrize("lam", [10.0, 1000.0])
+def test_dam_break_full_length(lam):
+    # the dam-break workload over its full 2000 steps at CFL_IMEX 4, on 2^16
+    # cells of the same spacing (the oracle's length limit; the waves stay
+    # clear of the ends): FP64 within 1e-10 of the oracle (rounding order
+    # only), mixed within the 1e-6 target of the mixed form; mass unchanged
+    n, dx, steps = 1 << 16, 0.05, 2000
+    x, U = inputs.dam_break(n, dx, 1.2, 1.0, 5.0 / dx)
+    p = oracle.Params(n, dx, 1, lam=lam)
+    dt, _, _ = oracle.suggest_dt(p, U, 4.0, 0.5)
+    ref = oracle.run(p, U, dt, steps)
+    xl, xr = -0.5 * n * dx, 0.5 * n * dx
+    f64 = gpu_run(n, xl, xr, 1, lam, U, dt, steps)
+    mix = mixed_run(n, xl, xr, 1, lam, U, dt, steps)
+    sc = summand_scales(n, dx, 1, lam, U, dt)
+    m0 = math.fsum(U[0])
+    assert rel_l2(f64[0], ref[0]) < 1e-10 and rel_l2(f64[2], ref[2]) < 1e-10
+    assert scaled_err(f64[1], ref[1], sc[1]) < 1e-9 and scaled_err(f64[3], ref[3], sc[3]) < 1e-9
+    assert rel_l2(mix[0], ref[0]) < 1e-6 and rel_l2(mix[2], ref[2]) < 1e-6
+    assert scaled_err(mix[1], ref[1], sc[1]) < 1e-5 and scaled_err(mix[3], ref[3], sc[3]) < 1e-5
+    assert abs(math.fsum(f64[0]) - m0) <= 1e-11 * m0
+    assert abs(math.fsum(mix[0]) - m0) <= 1e-12 * m0
