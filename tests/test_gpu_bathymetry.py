@@ -304,3 +304,27 @@ def test_wb_mixed_tiny_grids(n, bc):
     assert rel_l2(got[0], ref[0]) < 1e-7 and rel_l2(got[2], ref[2]) < 1e-7
     assert np.linalg.norm(got[1] - ref[1]) / np.linalg.norm(Sq) < 1e-6
     assert np.linalg.norm(got[3] - ref[3]) / np.linalg.norm(Sr) < 1e-6
+
+
+def test_wb_mixed_shelf_full_length_and_against_fp64():
+    # the large workload over its full 5000 steps in mixed precision (mass
+    # kept, no device error, finite), and its first 200 steps against the FP64
+    # bottom form, which matches the oracle to 1e-12 per step. A step changes h
+    # by under 1e-3 of itself, rounded in single precision to 2^-24: under 1e-10
+    # per step, so 200 steps stay below 2e-8
+    n, lam = 1 << 24, 1000.0
+    x, dx, b, U = inputs.shelf_wave(n)
+    p = oracle.Params(n, dx, 1, lam=lam, form=1, bathy=b)
+    dt, _, _ = oracle.suggest_dt(p, U, 4.0, 0.5)
+    m0 = math.fsum(U[0])
+    with wb_solver(n, dx, 1, lam, b, S().FLAG_MIXED) as s:
+        s.set_state(*(dev(u) for u in U))
+        s.run(dt, 200)
+        mixed200 = [t.cpu().numpy() for t in s.get_state()]
+        s.run(dt, 4800)
+        end = [t.cpu().numpy() for t in s.get_state()]
+    assert all(np.all(np.isfinite(a)) for a in end)
+    assert abs(math.fsum(end[0]) - m0) <= 1e-12 * m0
+    assert abs(math.fsum(mixed200[0]) - m0) <= 1e-12 * m0
+    f64 = gpu_run(n, dx, 1, lam, b, U, dt, 200)
+    assert rel_l2(mixed200[0], f64[0]) < 1e-7 and rel_l2(mixed200[2], f64[2]) < 1e-7

@@ -690,3 +690,32 @@ def test_dam_break_full_length(lam):
     assert scaled_err(mix[1], ref[1], sc[1]) < 1e-5 and scaled_err(mix[3], ref[3], sc[3]) < 1e-5
     assert abs(math.fsum(f64[0]) - m0) <= 1e-11 * m0
     assert abs(math.fsum(mix[0]) - m0) <= 1e-12 * m0
+
+
+def test_batched_workload_full_length_sampled():
+    # the batch over its full 1000 steps (CFL_IMEX 2). A step changes the
+    # largest waves (a = 0.4, lambda = 1000) by under 1 % of h, whose
+    # single-precision increments are rounded to 2^-24: at most about 5e-10
+    # per step, 5e-7 after 1000 steps even if every step's error added up
+    insts = inputs.batched_instances(inputs.SEED_BASE + 3, 4096)
+    ns = [it.n for it in insts]
+    xl = [-0.5 * it.n * it.dx for it in insts]
+    xr = [0.5 * it.n * it.dx for it in insts]
+    with S().BatchedSolver(ns, xl, xr, [it.lam for it in insts]) as B:
+        B.set_state(*(dev(a) for a in packed_state(insts)))
+        dts = B.suggest_dt(2.0, 0.5)
+        B.set_dt(dts)
+        B.run(0.0, 1000)
+        got = [t.cpu().numpy() for t in B.get_state()]
+    off = B.offsets
+    big = max(range(len(insts)), key=lambda k: insts[k].amp * (insts[k].lam == 1000.0))
+    for k_inst in (0, 2048, 4095, big):
+        it = insts[k_inst]
+        ref = oracle.run(oracle.Params(it.n, it.dx, 0, lam=it.lam), it.state, dts[k_inst], 1000)
+        o0, o1 = int(off[k_inst]), int(off[k_inst + 1])
+        assert rel_l2(got[0][o0:o1], ref[0]) < 1e-6, (k_inst, rel_l2(got[0][o0:o1], ref[0]))
+        assert rel_l2(got[2][o0:o1], ref[2]) < 1e-6
+    for k_inst, it in enumerate(insts):
+        o0, o1 = int(off[k_inst]), int(off[k_inst + 1])
+        m0 = math.fsum(it.state[0])
+        assert abs(math.fsum(got[0][o0:o1]) - m0) <= 1e-12 * m0, k_inst
