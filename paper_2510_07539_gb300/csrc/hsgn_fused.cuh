@@ -172,9 +172,11 @@ __host__ __device__ __forceinline__ int64_t cell_at(int64_t x, int64_t n) {
 
 // Cells read by the load phase for window cell index j (window cell j - 3):
 // the cell itself (gi) and its right neighbour (gn), j = 0 .. W + 5. A window
-// whose cells -3 .. W + 3 all lie in [0, n) (`inner`) indexes them directly.
+// whose cells -3 .. W + 3 all lie in [1, n) (`inner`) indexes them directly,
+// as offsets j and j + 1 from cell wl - 3 (cell 0 is left out: the face left
+// of it is read as the periodic face n - 1/2).
 __host__ __device__ inline bool inner_window(int64_t wl, int W, int64_t n) {
-    return wl - 3 >= 0 && wl + W + 3 < n;
+    return wl - 3 >= 1 && wl + W + 3 < n;
 }
 
 template <int BC>
@@ -302,9 +304,8 @@ __global__ void __launch_bounds__(T, (WB ? 768 : 1024) / T) k_mixed_fused(const 
     float* const dq1p = p.dq1 + cell0;
     float* const dm1p = p.dm1 + cell0;
     float* const dr1p = p.dr1 + cell0;
-    // G1 index of the face left of cell i: periodic face -1/2 is face n-1/2,
-    // which only the last tile writes
-    auto lf = [&](int64_t i) { return (BC == BC_PERIODIC && i == 0) ? n : i; };
+    // (G1: the face left of cell i at i, right of it at i + 1; the periodic
+    // face -1/2 is read as face n-1/2, which only the last tile writes)
     if (tid == 0) {
         sm.kmax = 0u;
         sm.kmin = 0x7F7FFFFFu;
@@ -315,68 +316,112 @@ __global__ void __launch_bounds__(T, (WB ? 768 : 1024) / T) k_mixed_fused(const 
     constexpr int NL = (Gm::R + 6 + T - 1) / T;
     // windows away from the domain ends read cells wl-3 .. wl+W+3 directly
     const bool inner = inner_window(wl, W, n);
-#pragma unroll
-    for (int it = 0; it < NL; ++it) {
-        const int j = tid + it * T;
-        if (j < W + 6) {
-            int64_t gi, gn;
-            load_cells<BC>(inner, wl, j, n, gi, gn);
-            const float2 h0 = __ldg(U0 + gi), q0 = __ldg(U1 + gi);
-            const float2 m0 = __ldg(U2 + gi), rr0 = __ldg(U3 + gi);
-            const float2 h1 = __ldg(U0 + gn), q1 = __ldg(U1 + gn), m1 = __ldg(U2 + gn);
-            float dh1 = 0.f, dq1 = 0.f, dm1 = 0.f, dr1 = 0.f, dh1n = 0.f, dq1n = 0.f, dm1n = 0.f;
-            if (two) {
-                const float g0 = __ldg(G1 + lf(gi)), g1 = __ldg(G1 + gi + 1);
-                const float g2 = __ldg(G1 + lf(gn)), g3 = __ldg(G1 + gn + 1);
-                dq1 = __ldg(dq1p + gi);
-                dm1 = __ldg(dm1p + gi);
-                dr1 = __ldg(dr1p + gi);
-                dq1n = __ldg(dq1p + gn);
-                dm1n = __ldg(dm1p + gn);
-                dh1 = g0 - g1;
-                dh1n = g2 - g3;
+    // one window cell: its loads come from `at` (cell itself, offset 0, or its
+    // right neighbour, offset 1, of U^n and the stage-1 increments; faces
+    // left / right of either); the direct path indexes from cell wl - 3 with
+    // 32-bit offsets, the general one maps every cell through cell_at
+    auto load_cell = [&](const int j, const auto& at) {
+        const float2 h0 = at.u(U0, 0), q0 = at.u(U1, 0);
+        const float2 m0 = at.u(U2, 0), rr0 = at.u(U3, 0);
+        const float2 h1 = at.u(U0, 1), q1 = at.u(U1, 1), m1 = at.u(U2, 1);
+        float dh1 = 0.f, dq1 = 0.f, dm1 = 0.f, dr1 = 0.f, dh1n = 0.f, dq1n = 0.f, dm1n = 0.f;
+        if (two) {
+            const float g0 = at.face_left(G1, 0), g1 = at.face_right(G1, 0);
+            const float g2 = at.face_left(G1, 1), g3 = at.face_right(G1, 1);
+            dq1 = at.f(dq1p, 0);
+            dm1 = at.f(dm1p, 0);
+            dr1 = at.f(dr1p, 0);
+            dq1n = at.f(dq1p, 1);
+            dm1n = at.f(dm1p, 1);
+            dh1 = g0 - g1;
+            dh1n = g2 - g3;
+        }
+        const float hf = h0.x, qf = q0.x, mf = m0.x, rf = rr0.x;
+        sm.hl[j] = fmaf(wl1, dh1, hf);
+        sm.ql[j] = fmaf(wl1, dq1, qf);
+        sm.ml[j] = fmaf(wl1, dm1, mf);
+        sm.rl[j] = fmaf(wl1, dr1, rf);
+        sm.qb[j] = fmaf(wb1, dq1, qf);
+        sm.mb[j] = fmaf(wb1, dm1, mf);
+        sm.rb[j] = fmaf(wb1, dr1, rf);
+        // differences of U^n at the face to the right: (hi1 - hi0) + (lo1 - lo0)
+        const float Dhn = __fadd_rn(__fsub_rn(h1.x, h0.x), __fsub_rn(h1.y, h0.y));
+        const float Dqn = __fadd_rn(__fsub_rn(q1.x, q0.x), __fsub_rn(q1.y, q0.y));
+        sm.Dq[j] = fmaf(wb1, dq1n - dq1, Dqn);
+        if constexpr (!WB) {
+            const float Dmn = __fadd_rn(__fsub_rn(m1.x, m0.x), __fsub_rn(m1.y, m0.y));
+            sm.Dh[j] = fmaf(wb1, dh1n - dh1, Dhn);
+            sm.Dm[j] = fmaf(wb1, dm1n - dm1, Dmn);
+        } else {
+            const float2 b0 = at.u(p.bathy + cell0, 0), b1 = at.u(p.bathy + cell0, 1);
+            // free-surface jump (h_l + b) at the face right of the cell:
+            // hi1 - hi0 of h is exact, that of b is taken exactly by TwoSum
+            float sb, eb;
+            two_sum(b1.x, -b0.x, sb, eb);
+            const float lo = __fadd_rn(__fadd_rn(__fsub_rn(h1.y, h0.y), __fsub_rn(b1.y, b0.y)), eb);
+            const float hz = __fadd_rn(__fsub_rn(h1.x, h0.x), sb);
+            sm.wb.Z[j] = fmaf(wl1, dh1n - dh1, __fadd_rn(hz, lo));
+            sm.wb.Db[j] = __fadd_rn(sb, __fadd_rn(__fsub_rn(b1.y, b0.y), eb));
+            sm.Dh[j] = (wl1 - wb1) * (dh1n - dh1);  // (h_l - h_b) jump
+            // P_l = h_l^2 - m_l: hi^2 = pp + pe exactly, pp - m.hi exact for m close to h^2
+            const float pp = __fmul_rn(hf, hf);
+            const float pe = fmaf(hf, hf, -pp);
+            const float P0 = __fadd_rn(__fsub_rn(pp, m0.x), fmaf(2.f * hf, h0.y, __fsub_rn(pe, m0.y)));
+            sm.Dm[j] = fmaf(wl1, fmaf(dh1, fmaf(wl1, dh1, 2.f * hf), -dm1), P0);
+            // (3/2) q_l (b_{c+1} - b_{c-1}) of the cells c = -1 .. W whose m^dag is formed
+            float src = 0.f;
+            if (j >= 2 && j <= W + 3)
+                src = 1.5f * fmaf(wl1, dq1, qf) * (b1.x - at.u(p.bathy + cell0, -1).x);
+            sm.wb.Sb[j] = src;
+            sm.wb.Mbl[j] = (wb1 - wl1) * dm1;
+        }
+    };
+    if (inner) {
+        // cells wl - 3 + j + d for d = -1, 0, 1: all in [0, n) for j in [2, W + 3]
+        // (d = -1) and j <= W + 5 (d = 0, 1), by the window test above
+        const int64_t b = wl - 3;
+        // (a + b) is the same for every cell of the CTA; only the 32-bit
+        // offset j + d varies
+        struct Direct {
+            int64_t b;
+            int j;
+            __device__ float2 u(const float2* a, int d) const { return __ldg((a + b) + (j + d)); }
+            __device__ float f(const float* a, int d) const { return __ldg((a + b) + (j + d)); }
+            __device__ float face_left(const float* a, int d) const {
+                return __ldg((a + b) + (j + d));
             }
-            const float hf = h0.x, qf = q0.x, mf = m0.x, rf = rr0.x;
-            sm.hl[j] = fmaf(wl1, dh1, hf);
-            sm.ql[j] = fmaf(wl1, dq1, qf);
-            sm.ml[j] = fmaf(wl1, dm1, mf);
-            sm.rl[j] = fmaf(wl1, dr1, rf);
-            sm.qb[j] = fmaf(wb1, dq1, qf);
-            sm.mb[j] = fmaf(wb1, dm1, mf);
-            sm.rb[j] = fmaf(wb1, dr1, rf);
-            // differences of U^n at the face to the right: (hi1 - hi0) + (lo1 - lo0)
-            const float Dhn = __fadd_rn(__fsub_rn(h1.x, h0.x), __fsub_rn(h1.y, h0.y));
-            const float Dqn = __fadd_rn(__fsub_rn(q1.x, q0.x), __fsub_rn(q1.y, q0.y));
-            sm.Dq[j] = fmaf(wb1, dq1n - dq1, Dqn);
-            if constexpr (!WB) {
-                const float Dmn = __fadd_rn(__fsub_rn(m1.x, m0.x), __fsub_rn(m1.y, m0.y));
-                sm.Dh[j] = fmaf(wb1, dh1n - dh1, Dhn);
-                sm.Dm[j] = fmaf(wb1, dm1n - dm1, Dmn);
-            } else {
-                const float2* __restrict__ Bp = p.bathy + cell0;
-                const float2 b0 = __ldg(Bp + gi), b1 = __ldg(Bp + gn);
-                // free-surface jump (h_l + b) at the face right of the cell:
-                // hi1 - hi0 of h is exact, that of b is taken exactly by TwoSum
-                float sb, eb;
-                two_sum(b1.x, -b0.x, sb, eb);
-                const float lo = __fadd_rn(__fadd_rn(__fsub_rn(h1.y, h0.y), __fsub_rn(b1.y, b0.y)), eb);
-                const float hz = __fadd_rn(__fsub_rn(h1.x, h0.x), sb);
-                sm.wb.Z[j] = fmaf(wl1, dh1n - dh1, __fadd_rn(hz, lo));
-                sm.wb.Db[j] = __fadd_rn(sb, __fadd_rn(__fsub_rn(b1.y, b0.y), eb));
-                sm.Dh[j] = (wl1 - wb1) * (dh1n - dh1);  // (h_l - h_b) jump
-                // P_l = h_l^2 - m_l: hi^2 = pp + pe exactly, pp - m.hi exact for m close to h^2
-                const float pp = __fmul_rn(hf, hf);
-                const float pe = fmaf(hf, hf, -pp);
-                const float P0 = __fadd_rn(__fsub_rn(pp, m0.x), fmaf(2.f * hf, h0.y, __fsub_rn(pe, m0.y)));
-                sm.Dm[j] = fmaf(wl1, fmaf(dh1, fmaf(wl1, dh1, 2.f * hf), -dm1), P0);
-                // (3/2) q_l (b_{c+1} - b_{c-1}) of the cells c = -1 .. W whose m^dag is formed
-                float src = 0.f;
-                if (j >= 2 && j <= W + 3) {
-                    const int64_t gp = inner ? gi - 1 : cell_at<BC>(wl - 4 + j, n);
-                    src = 1.5f * fmaf(wl1, dq1, qf) * (b1.x - __ldg(Bp + gp).x);
-                }
-                sm.wb.Sb[j] = src;
-                sm.wb.Mbl[j] = (wb1 - wl1) * dm1;
+            __device__ float face_right(const float* a, int d) const {
+                return __ldg((a + b) + (j + d + 1));
+            }
+        };
+#pragma unroll
+        for (int it = 0; it < NL; ++it) {
+            const int j = tid + it * T;
+            if (j < W + 6) load_cell(j, Direct{b, j});
+        }
+    } else {
+        struct General {
+            int64_t gi, gn, gp, n;
+            __device__ int64_t cell(int d) const { return d == 0 ? gi : (d > 0 ? gn : gp); }
+            __device__ float2 u(const float2* a, int d) const { return __ldg(a + cell(d)); }
+            __device__ float f(const float* a, int d) const { return __ldg(a + cell(d)); }
+            // G1 index of the face left of cell i: periodic face -1/2 is face n-1/2
+            __device__ float face_left(const float* a, int d) const {
+                const int64_t c = cell(d);
+                return __ldg(a + ((BC == BC_PERIODIC && c == 0) ? n : c));
+            }
+            __device__ float face_right(const float* a, int d) const {
+                return __ldg(a + cell(d) + 1);
+            }
+        };
+#pragma unroll
+        for (int it = 0; it < NL; ++it) {
+            const int j = tid + it * T;
+            if (j < W + 6) {
+                int64_t gi, gn;
+                load_cells<BC>(false, wl, j, n, gi, gn);
+                const int64_t gp = cell_at<BC>(wl - 4 + j, n);
+                load_cell(j, General{gi, gn, gp, n});
             }
         }
     }
@@ -688,9 +733,24 @@ __global__ void __launch_bounds__(T, (WB ? 768 : 1024) / T) k_mixed_fused(const 
     // ---- 4b. back-substitution of the tile rows
     const float lamv = lam;
     float umax = 0.f;
+    // the tile's cells and faces from its first cell: 32-bit offsets t
+    const int64_t t0 = win.t0;
+    const float2* const U0t = U0 + t0;
+    const float2* const U1t = U1 + t0;
+    const float2* const U2t = U2 + t0;
+    const float2* const U3t = U3 + t0;
+    const float* const G1t = G1 + t0;  // face left of cell t at t, right of it at t + 1
+    float* const dq1t = dq1p + t0;
+    float* const dm1t = dm1p + t0;
+    float* const dr1t = dr1p + t0;
+    float2* const o0t = two ? p.out[0] + cell0 + t0 : nullptr;
+    float2* const o1t = two ? p.out[1] + cell0 + t0 : nullptr;
+    float2* const o2t = two ? p.out[2] + cell0 + t0 : nullptr;
+    float2* const o3t = two ? p.out[3] + cell0 + t0 : nullptr;
+    // periodic face -1/2 is face n-1/2 (for the first cell of the first tile)
+    const bool wrap0 = BC == BC_PERIODIC && t0 == 0;
     for (int t = tid; t < sp; t += T) {
         const int r = lo + t;            // window row
-        const int64_t i = win.t0 + t;    // global row (in range)
         const float dhL = dha[pd(r)], dhC = dha[pd(r + 1)], dhR = dha[pd(r + 2)];
         const float dqC = dqa[r + 1], dmC = dma[r + 1];
         float dQ;
@@ -710,7 +770,7 @@ __global__ void __launch_bounds__(T, (WB ? 768 : 1024) / T) k_mixed_fused(const 
             dQ = dqC - fq * beC * dhc - lamv * fq * deC * dmc;
         }
         // base depth (rounded) and P0 = h_b^2 - m_b of this cell
-        const float2 h0 = U0[i], m0 = U2[i];
+        const float2 h0 = U0t[t], m0 = U2t[t];
         const float hf = h0.x;
         // (h^2 - m)^n: hi^2 = p + e exactly; p - m.hi is exact for m close to h^2
         const float pp = __fmul_rn(hf, hf);
@@ -719,9 +779,9 @@ __global__ void __launch_bounds__(T, (WB ? 768 : 1024) / T) k_mixed_fused(const 
         float P0 = __fadd_rn(__fsub_rn(pp, m0.x), fmaf(2.f * hf, h0.y, __fsub_rn(pe, m0.y)));
         float g1l = 0.f, g1r = 0.f;
         if (two) {
-            g1l = G1[lf(i)];
-            g1r = G1[i + 1];
-            const float dh1 = g1l - g1r, dm1 = dm1p[i];
+            g1l = (wrap0 && t == 0) ? G1[n] : G1t[t];
+            g1r = G1t[t + 1];
+            const float dh1 = g1l - g1r, dm1 = dm1t[t];
             hbf = fmaf(wb1, dh1, hf);
             P0 = fmaf(wb1, fmaf(dh1, fmaf(wb1, dh1, 2.f * hf), -dm1), P0);
         }
@@ -737,18 +797,18 @@ __global__ void __launch_bounds__(T, (WB ? 768 : 1024) / T) k_mixed_fused(const 
         if (!isfinite(dQ) || !isfinite(dM) || !isfinite(dR)) b2 |= HSGN_DEV_ERR_NONFINITE;
         bad |= b2;
         if (!two) {
-            dq1p[i] = dQ;
-            dm1p[i] = dM;
-            dr1p[i] = dR;
+            dq1t[t] = dQ;
+            dm1t[t] = dM;
+            dr1t[t] = dR;
         } else {
             const float Tp = fmaf(wb1, g1r, Gt[t + 1]);
             const float Tm = fmaf(wb1, g1l, Gt[t]);
             float d, de;
             two_sum(Tm, -Tp, d, de);  // exact Tm - Tp
-            p.out[0][cell0 + i] = df_add(h0, d, de);
-            p.out[1][cell0 + i] = df_add(U1[i], fmaf(wb1, dq1p[i], dQ), 0.f);
-            p.out[2][cell0 + i] = df_add(m0, fmaf(wb1, dm1p[i], dM), 0.f);
-            p.out[3][cell0 + i] = df_add(U3[i], fmaf(wb1, dr1p[i], dR), 0.f);
+            o0t[t] = df_add(h0, d, de);
+            o1t[t] = df_add(U1t[t], fmaf(wb1, dq1t[t], dQ), 0.f);
+            o2t[t] = df_add(m0, fmaf(wb1, dm1t[t], dM), 0.f);
+            o3t[t] = df_add(U3t[t], fmaf(wb1, dr1t[t], dR), 0.f);
             if (p.track_speed && !b2) umax = fmaxf(umax, fabsf((sm.qb[r + 3] + dQ) / hbar));
         }
     }

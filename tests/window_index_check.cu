@@ -51,6 +51,15 @@ void check(int64_t n, int S) {
             CHECK(gi >= 0 && gi < n && gn >= 0 && gn < n);
             CHECK(gi == ci && gn == cn);  // the direct path reads the cells the general one does
             if (BC == BC_PERIODIC) CHECK(((w.wl - 3 + j) % n + n) % n == gi);
+            if (inner) {
+                // the direct path: cells b + j - 1 (j in [2, W + 3]) .. b + j + 1 and
+                // faces b + j .. b + j + 2 from b = wl - 3; the face left of cell
+                // b + j is read at b + j, so cell 0 (periodic face n - 1/2) is excluded
+                const int64_t b = w.wl - 3;
+                CHECK(b + j >= 1 && b + j + 1 < n);
+                if (j >= 2 && j <= w.W + 3) CHECK(b + j - 1 >= 0 && cell_at<BC>(w.wl - 4 + j, n) == b + j - 1);
+                CHECK(b + j + 2 <= n);  // G1 has n + 1 faces
+            }
         }
         // padded stores: face couplings pd(j), j <= W; dh at pd(r + 1), r <= W
         CHECK(pd(w.W + 1) < G::NC);
