@@ -20,7 +20,6 @@ the host cores instead (the reference arm of this comparison).
 from __future__ import annotations
 
 import argparse
-import glob
 import hashlib
 import json
 import math
@@ -120,26 +119,36 @@ def config_dict(n, lams, dts, extra=None):
     return d
 
 
-def source_sha() -> str:
+def source_sha(files=None) -> str:
+    """Hash of kernel sources: the named files of the library's csrc folder
+    (a kernel's own header and those it includes), or all of them."""
     h = hashlib.sha256()
-    for f in sorted(glob.glob(os.path.join(ROOT, "paper_2510_07539_gb300", "csrc", "*"))):
-        with open(f, "rb") as fh:
+    csrc = os.path.join(ROOT, "paper_2510_07539_gb300", "csrc")
+    names = sorted(files) if files else sorted(os.listdir(csrc))
+    for name in names:
+        with open(os.path.join(csrc, name), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
 
 
 def profiled_traffic_per_cell(summary: str):
     """DRAM bytes per cell of a kernel from its committed ncu summary, or None
-    when the kernel sources changed since that capture."""
+    when the kernel's sources (the summary's `source_files`, else all of csrc)
+    changed since that capture."""
     path = os.path.join(ROOT, "profiles", summary)
     if not os.path.exists(path):
         return None
     txt = open(path).read()
     sha = re.search(r"source_sha:\s*([0-9a-f]+)", txt)
+    files = re.search(r"source_files:\s*([^\n]+)", txt)
     val = re.search(r"dram_bytes_per_cell_per_launch:\s*([0-9.eE+-]+)", txt)
-    if not sha or not val or sha.group(1) != source_sha():
+    if not sha or not val:
         return None
-    return float(val.group(1))
+    try:
+        cur = source_sha(files.group(1).split() if files else None)
+    except OSError:
+        return None
+    return float(val.group(1)) if sha.group(1) == cur else None
 
 
 # ---------------------------------------------------------------------------
