@@ -719,3 +719,23 @@ def test_batched_workload_full_length_sampled():
         o0, o1 = int(off[k_inst]), int(off[k_inst + 1])
         m0 = math.fsum(it.state[0])
         assert abs(math.fsum(got[0][o0:o1]) - m0) <= 1e-12 * m0, k_inst
+
+
+@pytest.mark.parametrize("bc", [0, 1])
+@pytest.mark.parametrize("n", [894, 895, 896, 1789, 1790, 1791, 2684, 2686, 8191, 65537])
+def test_windowed_sizes_around_tile_multiples(n, bc):
+    # grids of one tile, one tile plus a cell, two tiles minus a cell ...: the
+    # tile faces, ragged last tiles and the periodic seam at every position
+    # the tiling of 895-row tiles produces
+    dx, lam = 0.1, 300.0
+    U = inputs.random_state(6000 + n + bc, n, dx)
+    p = oracle.Params(n, dx, bc, lam=lam)
+    dt, _, _ = oracle.suggest_dt(p, U, 2.0, 0.5)
+    got = mixed_run(n, 0.0, n * dx, bc, lam, U, dt, 2)
+    ref = oracle.run(p, U, dt, 2)
+    sc = summand_scales(n, dx, bc, lam, U, dt)
+    assert rel_l2(got[0], ref[0]) < 1e-7 and rel_l2(got[2], ref[2]) < 1e-7
+    for k in (1, 3):
+        assert scaled_err(got[k], ref[k], sc[k]) < 1e-6, (k, scaled_err(got[k], ref[k], sc[k]))
+    if bc == 0:
+        assert abs(math.fsum(got[0]) - math.fsum(U[0])) <= 1e-13 * math.fsum(U[0])
