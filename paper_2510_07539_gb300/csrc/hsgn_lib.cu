@@ -1180,6 +1180,7 @@ struct AdjWork {
     int64_t* cells = nullptr;
     double* data = nullptr;
     double* dseg = nullptr;     // gauge data of the current segment, K x n_gauges
+    double* fw1 = nullptr;      // q^dag, m^dag, r^dag, beta of the step's stage 1, 4 x n
     size_t work_bytes = 0;      // cellw + facew, zeroed per stage adjoint
     // a full segment of K steps is the same launch sequence for every segment
     // once its checkpoint is in seg[0] and its gauge data in dseg: captured
@@ -1227,9 +1228,11 @@ cudaError_t adj_forward_step(hsgn_s* H, AdjWork& W, const double* in, double* ou
 
 // adjoint of one stage whose forward was just run by launch_stage (the work
 // arrays of the handle hold its q^dag, m^dag, r^dag, beta)
+// fw: q^dag, m^dag, r^dag and beta of that stage's forward (the handle's work
+// arrays right after it, or a copy of them)
 cudaError_t adj_stage(hsgn_s* H, AdjWork& W, const double* Ub, const double* Ul, double tau,
                       const double* out, const double* Ao, double* Ab, double* Al,
-                      double* Abathy, cudaStream_t st) {
+                      double* Abathy, const double* const fw[4], cudaStream_t st) {
     const int64_t n = W.n;
     AdjParams p;
     p.n = n;
@@ -1247,10 +1250,10 @@ cudaError_t adj_stage(hsgn_s* H, AdjWork& W, const double* Ub, const double* Ul,
         p.Al[v] = Al + v * n;
     }
     p.bathy = H->bathy;
-    p.qs = H->qs;
-    p.ms = H->ms;
-    p.rs = H->rs;
-    p.be = H->be;
+    p.qs = fw[0];
+    p.ms = fw[1];
+    p.rs = fw[2];
+    p.be = fw[3];
     p.hbar = out;
     p.mbar = out + 2 * n;
     p.Abathy = Abathy;
@@ -1300,8 +1303,14 @@ cudaError_t adj_step(hsgn_s* H, AdjWork& W, const double* U, double dt, double* 
     const double* speed = reinterpret_cast<const double*>(W.sbits);
     const double* A[4] = {U, U + n, U + 2 * n, U + 3 * n};
     double* U1m[4] = {W.U1, W.U1 + n, W.U1 + 2 * n, W.U1 + 3 * n};
-    // stage-1 forward, the stage-2 states, stage-2 forward
+    // stage-1 forward (its q^dag, m^dag, r^dag, beta kept for its adjoint),
+    // the stage-2 states, stage-2 forward
     e = launch_stage(H, A, nullptr, 1.0, 0.0, 1.0, 0.0, tau, speed, U1m, false, st);
+    if (e != cudaSuccess) return e;
+    const double* const hw[4] = {H->qs, H->ms, H->rs, H->be};
+    const double* const fw1[4] = {W.fw1, W.fw1 + n, W.fw1 + 2 * n, W.fw1 + 3 * n};
+    for (int v = 0; v < 4 && e == cudaSuccess; ++v)
+        e = cudaMemcpyAsync(W.fw1 + v * n, hw[v], n * sizeof(double), cudaMemcpyDeviceToDevice, st);
     if (e != cudaSuccess) return e;
     k_adj_axpby<<<gc, 256, 0, st>>>(n, wl0, cp4(U, n), wl1, cp4(W.U1, n), 0.0, none, mp4(W.Ue, n));
     k_adj_axpby<<<gc, 256, 0, st>>>(n, wb0, cp4(U, n), wb1, cp4(W.U1, n), 0.0, none, mp4(W.Ubs, n));
@@ -1314,18 +1323,16 @@ cudaError_t adj_step(hsgn_s* H, AdjWork& W, const double* U, double dt, double* 
     e = cudaMemsetAsync(W.Ab, 0, 8 * (size_t)n * sizeof(double), st);  // Ab and Al
     if (e == cudaSuccess) e = cudaMemsetAsync(W.Aspeed, 0, sizeof(double), st);
     if (e != cudaSuccess) return e;
-    e = adj_stage(H, W, W.Ubs, W.Ue, tau, W.O2, W.Ua, W.Ab, W.Al, Abathy, st);
+    e = adj_stage(H, W, W.Ubs, W.Ue, tau, W.O2, W.Ua, W.Ab, W.Al, Abathy, hw, st);
     if (e != cudaSuccess) return e;
     k_adj_axpby<<<gc, 256, 0, st>>>(n, wl1, cp4(W.Al, n), wb1, cp4(W.Ab, n), 0.0, none,
                                     mp4(W.Ua1, n));
     k_adj_axpby<<<gc, 256, 0, st>>>(n, wl0, cp4(W.Al, n), wb0, cp4(W.Ab, n), 0.0, none,
                                     mp4(W.Ua, n));
-    // stage-1 forward again (its work arrays), then its adjoint
-    e = launch_stage(H, A, nullptr, 1.0, 0.0, 1.0, 0.0, tau, speed, U1m, false, st);
-    if (e != cudaSuccess) return e;
+    // stage-1 adjoint
     e = cudaMemsetAsync(W.Ab, 0, 8 * (size_t)n * sizeof(double), st);
     if (e != cudaSuccess) return e;
-    e = adj_stage(H, W, U, U, tau, W.U1, W.Ua1, W.Ab, W.Al, Abathy, st);
+    e = adj_stage(H, W, U, U, tau, W.U1, W.Ua1, W.Ab, W.Al, Abathy, fw1, st);
     if (e != cudaSuccess) return e;
     k_adj_axpby<<<gc, 256, 0, st>>>(n, 1.0, cp4(W.Ua, n), 1.0, cp4(W.Ab, n), 1.0, cp4(W.Al, n),
                                     mp4(W.Ua, n));
@@ -1364,7 +1371,7 @@ int hsgn_adjoint(hsgn_handle_t H, double dt, int64_t n_steps, int64_t n_gauges,
                                 sizeof(double));
     const size_t dsb = align_up((size_t)(n_gauges > 0 ? n_gauges : 1) * (size_t)W.K *
                                 sizeof(double));
-    const size_t total = (size_t)W.nck * s4 + (size_t)(W.K + 1) * s4 + 8 * s4 + cellb + faceb +
+    const size_t total = (size_t)W.nck * s4 + (size_t)(W.K + 1) * s4 + 9 * s4 + cellb + faceb +
                          swsb + align_up(4 * sizeof(unsigned long long)) + gcb + gdb + dsb;
     if (cudaMalloc(&W.mem, total) != cudaSuccess) {
         cudaGetLastError();
@@ -1380,6 +1387,7 @@ int hsgn_adjoint(hsgn_handle_t H, double dt, int64_t n_steps, int64_t n_gauges,
     W.O2 = reinterpret_cast<double*>(take(s4));
     W.Ua = reinterpret_cast<double*>(take(s4));
     W.Ua1 = reinterpret_cast<double*>(take(s4));
+    W.fw1 = reinterpret_cast<double*>(take(s4));
     // Ab and Al are contiguous (one memset clears both)
     W.Ab = reinterpret_cast<double*>(take(2 * s4));
     W.Al = W.Ab + 4 * n;
