@@ -739,3 +739,36 @@ def test_windowed_sizes_around_tile_multiples(n, bc):
         assert scaled_err(got[k], ref[k], sc[k]) < 1e-6, (k, scaled_err(got[k], ref[k], sc[k]))
     if bc == 0:
         assert abs(math.fsum(got[0]) - math.fsum(U[0])) <= 1e-13 * math.fsum(U[0])
+
+
+@pytest.mark.parametrize("form", ["mixed", "mixed_bottom", "batched"])
+def test_device_errors_are_reported_by_every_form(form):
+    # a negative depth in the state: the next synchronising call reports
+    # HSGN_ERR_NONPOSITIVE_DEPTH (3) and clears the error word, after which a
+    # good state steps again
+    n, dx = 2000, 0.1
+    U = list(inputs.random_state(7, n, dx))
+    U[0] = U[0].copy()
+    U[0][1234] = -0.5
+    good = inputs.random_state(8, n, dx)
+    if form == "batched":
+        s = S().BatchedSolver([n, n], [0.0, 0.0], [n * dx] * 2, [100.0, 300.0])
+        bad = [np.concatenate([good[k], U[k]]) for k in range(4)]
+        ok = [np.concatenate([good[k], good[k]]) for k in range(4)]
+        s.set_state(*(dev(a) for a in ok))
+        s.set_dt([0.01, 0.01])
+        s.set_state(*(dev(a) for a in bad))
+        run = lambda k: s.run(0.0, k)
+    else:
+        flags = S().FLAG_MIXED | (S().FLAG_WELL_BALANCED if form == "mixed_bottom" else 0)
+        s = S().Solver(n, 0.0, n * dx, 0, lam=100.0, flags=flags)
+        ok = good
+        s.set_state(*(dev(u) for u in U))
+        run = lambda k: s.run(0.01, k)
+    with s:
+        with pytest.raises(S().HsgnError) as e:
+            run(1)
+        assert e.value.code == 3
+        s.set_state(*(dev(u) for u in ok))
+        run(2)
+        assert all(np.all(np.isfinite(t.cpu().numpy())) for t in s.get_state())
