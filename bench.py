@@ -76,6 +76,8 @@ def parse_args():
                     help="skip the scheme comparison (time to solution)")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint workload")
     ap.add_argument("--no-shelf", action="store_true", help="skip the 2^24-cell shelf workload")
+    ap.add_argument("--no-paper-runs", action="store_true",
+                    help="skip the runs of the paper's CPU-time tables")
     ap.add_argument("--shelf-log2n", type=int, default=24, help="cells of the shelf workload (log2)")
     ap.add_argument("--shelf-steps", type=int, default=50, help="timed steps of the shelf workload")
     ap.add_argument("--sequential", action="store_true",
@@ -409,6 +411,92 @@ def time_to_solution(S, torch, n, xl, xr, Ud, stream):
     }
 
 
+def run_to_time(S, torch, stream, n, xl, xr, bc, lam, flags, U, cfl, mcfl, T):
+    """GPU time of one run to the final time T with the fixed step of the
+    initial state (dt = T / ceil(T / dt0), dt0 from the Sec. 5 rule); returns
+    the record and the final depth (None when the run broke down)."""
+    with S.Solver(n, xl, xr, bc, lam=lam, flags=flags) as s:
+        Ud = [torch.tensor(u, device="cuda") for u in U]
+        s.set_state(*Ud)
+        dt0 = s.suggest_dt(cfl, mcfl)
+        steps = max(1, int(math.ceil(T / dt0 - 1e-9)))
+        dt = T / steps
+        s.run(dt, 2)  # the graphs of both buffers (windowed form) / the step graph
+        s.set_state(*Ud)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        s.enqueue(dt, steps, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        try:
+            s.check()
+        except S.HsgnError as err:
+            return {"steps": steps, "dt": dt, "failed": str(err)}, None
+        return {"steps": steps, "dt": dt, "ms": e0.elapsed_time(e1)}, s.get_state()[0].cpu().numpy()
+
+
+def time_paper_runs(S, torch, stream):
+    """The runs of the paper's CPU-time tables, timed on the GPU (the paper's
+    seconds are for an unstated CPU and implementation: context only).
+    Sec. 6.1: the Gaussian bell h = 1 + exp(-x^2/20) on [-200, 200], N = 5000,
+    T = 35, the paper's scheme at CFL_IMEX 2 against explicit Heun at CFL 0.4,
+    for lambda = 100, 500, 1000, 5000 (boundaries not printed: transmissive).
+    Sec. 6.3: the solitary wave of amplitude 1 over depth 1, N = 2000, T = 1,
+    lambda = 1000, first- and second-order semi-implicit schemes at CFL_IMEX
+    2.5 and explicit ones at CFL 0.4 (domain not printed: [-50, 50],
+    periodic), with the relative L1 error of the depth against the closed form.
+    Steps are fixed from the initial state. Under these readings the scheme has
+    a growing mode on the bell from lambda 1000 at CFL_IMEX 2 (and explicit
+    Heun from lambda 500 at CFL 0.4): the FP64 runs break down, in the oracle
+    alike; a mixed-precision run is timed only where its FP64 run reached T,
+    and its distance to it is reported. Even where the runs reach T, the bell
+    amplifies rounding differences by about 6 % per step from step ~200 until
+    they saturate: the FP64 path and the oracle end 0.7 % apart at lambda 100,
+    so the mixed-vs-FP64 distance measures that sensitivity, not the accuracy
+    of the mixed form."""
+    import numpy as np
+    from paper_2510_07539_gb300 import inputs as inp
+    bell = {}
+    paper_bell = {100.0: (7.68, 19.51), 500.0: (16.18, 39.938), 1000.0: (25.59, 75.86),
+                  5000.0: (63.34, 169.73)}
+    x, dx, U = inp.gaussian_bell()
+    for lam, (p_si, p_ex) in paper_bell.items():
+        row = {}
+        row["si_fp64"], h64 = run_to_time(S, torch, stream, 5000, -200.0, 200.0,
+                                          S.BC_TRANSMISSIVE, lam, S.FLAG_FP64, U, 2.0, 0.0, 35.0)
+        if h64 is not None:
+            row["si_mixed"], hm = run_to_time(S, torch, stream, 5000, -200.0, 200.0,
+                                              S.BC_TRANSMISSIVE, lam, S.FLAG_MIXED, U, 2.0, 0.0,
+                                              35.0)
+            if hm is not None:
+                row["si_mixed"]["depth_rel_l2_vs_fp64"] = float(np.linalg.norm(hm - h64) /
+                                                               np.linalg.norm(h64))
+        row["ex_heun_fp64"], _ = run_to_time(S, torch, stream, 5000, -200.0, 200.0,
+                                             S.BC_TRANSMISSIVE, lam, S.SCHEME_EX_HEUN, U, 0.4,
+                                             0.0, 35.0)
+        row["paper_cpu_s"] = {"si": p_si, "ex_heun": p_ex}
+        bell[f"lambda_{lam:g}"] = row
+    x, _ = inp.cell_centres(2000, -50.0, 50.0)
+    U = inp.solitary(x, 1.0, 1.0, 0.0, period=100.0)
+    h_exact = inp.solitary(x, 1.0, 1.0, 0.0, t=1.0, period=100.0)[0]
+    sol = {}
+    for name, flags, cfl, paper in (("si_order1", S.SCHEME_SI1, 2.5, 1.2502),
+                                    ("si_order2", S.FLAG_FP64, 2.5, 4.0350),
+                                    ("ex_order1", S.SCHEME_EX_EULER, 0.4, 3.2105),
+                                    ("ex_order2", S.SCHEME_EX_HEUN, 0.4, 16.9138)):
+        rec, h = run_to_time(S, torch, stream, 2000, -50.0, 50.0, S.BC_PERIODIC, 1000.0, flags,
+                             U, cfl, 0.0, 1.0)
+        if h is not None:
+            rec["depth_rel_l1_vs_closed_form"] = float(np.sum(np.abs(h - h_exact)) /
+                                                       np.sum(np.abs(h)))
+        rec["paper_cpu_s"] = paper
+        sol[name] = rec
+    return {"gaussian_bell": bell, "solitary_lambda_1000": sol,
+            "note": "paper CPU seconds: unstated hardware and implementation; context only"}
+
+
 def time_adjoint(S, torch, stream):
     """The adjoint workload: N = 4096, dx = 0.1, periodic, lambda = 100, a wave
     a = 0.1 over 8 Gaussian bumps (bottom form), 2000 steps at CFL_IMEX 2, the
@@ -624,6 +712,9 @@ def run_ours(args):
     adjoint = None
     if not args.no_adjoint and rank == 0:
         adjoint = time_adjoint(S, torch, stream)
+    paper_runs = None
+    if not args.no_paper_runs and rank == 0:
+        paper_runs = time_paper_runs(S, torch, stream)
     shelf = None
     if not args.no_shelf and rank == 0:
         shelf = time_shelf(S, torch, stream, hbm_peak, args.shelf_log2n, args.shelf_steps)
@@ -779,6 +870,7 @@ def run_ours(args):
             "batched_vs_fp64_single": (batched["value"] / fp64["value"])
             if (batched and fp64) else None,
             "comparators": comparators, "adjoint": adjoint, "shelf": shelf,
+            "paper_runs": paper_runs,
             "cpu_baseline": cpu, "e2e": e2e,
             "clocks": clocks, "gpu_launches": launches,
         }

@@ -95,7 +95,10 @@ enum {
  *   EX_HEUN  explicit hSGN (Sec. 4.4, eq. (GN_hyp_eq_explicit)), Heun's method,
  *            centred linear reconstruction; needs dt <= CFL dx / nu_max with
  *            CFL about 0.4 (hsgn_suggest_dt with that CFL)
- *   EX_EULER explicit hSGN, forward Euler, no reconstruction */
+ *   EX_EULER explicit hSGN, forward Euler, no reconstruction
+ * The explicit schemes treat every wave explicitly: their global Rusanov
+ * speed is the spectral radius max(|u| + c), c^2 = g h + (lambda/3) eta^2/h^2,
+ * of the step's state, where the semi-implicit schemes use max |u|. */
 #define HSGN_SCHEME_PRINTED 0x000
 #define HSGN_SCHEME_ARS222 0x100
 #define HSGN_SCHEME_SI1 0x200

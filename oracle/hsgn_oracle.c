@@ -664,11 +664,21 @@ int oracle_run(const oracle_params* p, double* h, double* q, double* m, double* 
     oracle_params ps = *p;
     for (int64_t s = 0; s < n_steps && rc == ORACLE_OK; ++s) {
         if (ps.rusanov) {
-            /* global Rusanov speed of this step: max over cells of |u^n| */
+            /* global Rusanov speed of this step: max over cells of |u^n| (R5).
+             * The fully explicit schemes treat every wave explicitly, so their
+             * Rusanov speed is the spectral radius of the system, max of
+             * |u| + c with c^2 = g h + (lambda/3) eta^2/h^2 (Sec. 2.2, eq.
+             * (eq:hSGN_eigenvalues); reading R12) */
+            const int spectral = ps.scheme == ORACLE_SCHEME_EX_HEUN ||
+                                 ps.scheme == ORACLE_SCHEME_EX_EULER;
             double umax = 0.0;
             for (int64_t i = 0; i < n; ++i) {
                 if (!(U[i] > 0.0)) return free(U), free(work), ORACLE_ERR_DEPTH;
-                const double u = fabs(U[n + i] / U[i]);
+                double u = fabs(U[n + i] / U[i]);
+                if (spectral) {
+                    const double e = U[2 * n + i] / (U[i] * U[i]);
+                    u += sqrt(ps.g * U[i] + (ps.lambda / 3.0) * e * e);
+                }
                 if (u > umax) umax = u;
             }
             ps.speed = umax;

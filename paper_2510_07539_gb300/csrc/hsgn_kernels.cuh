@@ -650,6 +650,7 @@ struct ExplicitParams {
     int32_t recon;        // 1: centred linear reconstruction; 0: none
     int32_t local_speed;  // 1: Rusanov speed max(|u^L|,|u^R|); 0: global *speed
     int32_t track_speed;  // 1: fold max |u| of out1 into *speed_next
+    int32_t spectral;     // with track_speed: fold max(|u| + c) instead (explicit schemes)
     double dx, g, lam;
     double idx, i2dx;     // 1/dx, 1/(2 dx)
     const double* Us[4];
@@ -749,7 +750,16 @@ __global__ void __launch_bounds__(ET) k_explicit(const ExplicitParams p) {
         if (!finite_bits(o1[0]) || !finite_bits(o1[1]) || !finite_bits(o1[2]) ||
             !finite_bits(o1[3]))
             bad |= HSGN_DEV_ERR_NONFINITE;
-        if (p.track_speed && !bad) umax = fabs(o1[1] / o1[0]);
+        if (p.track_speed && !bad) {
+            // |u|, or the spectral radius |u| + c, c^2 = g h + (lambda/3) eta^2/h^2
+            // (Sec. 2.2, eq. (eq:hSGN_eigenvalues)) of the new state
+            const double ihn = rcp(o1[0]);
+            umax = fabs(o1[1] * ihn);
+            if (p.spectral) {
+                const double en = o1[2] * ihn * ihn;
+                umax += sqrt(fma(p.g, o1[0], (p.lam * (1.0 / 3.0)) * en * en));
+            }
+        }
     }
     if (bad) flag_error(p.err, bad);
     if (p.track_speed) {

@@ -195,6 +195,10 @@ struct hsgn_s {
 namespace {
 
 bool local_speed(const hsgn_s* H) { return (H->flags & HSGN_RUSANOV_LOCAL) != 0; }
+// Explicit Heun / Euler: every wave explicit, Rusanov speed max(|u| + c)
+bool explicit_scheme(const hsgn_s* H) {
+    return H->scheme == HSGN_SCHEME_EX_HEUN || H->scheme == HSGN_SCHEME_EX_EULER;
+}
 
 // The buffer holding the current state, and the global Rusanov speed of the
 // state in buffer `which` (0: U, 1: V).
@@ -499,6 +503,7 @@ cudaError_t launch_explicit(hsgn_s* H, const double* const Us[4], const double* 
     p.recon = H->scheme == HSGN_SCHEME_EX_EULER ? 0 : 1;
     p.local_speed = local_speed(H) ? 1 : 0;
     p.track_speed = track && !local_speed(H) ? 1 : 0;
+    p.spectral = explicit_scheme(H) ? 1 : 0;
     p.dx = H->dx;
     p.g = H->g;
     p.lam = H->lam;
@@ -670,6 +675,14 @@ cudaError_t refresh_speed(hsgn_s* H, cudaStream_t st) {
     double* out = speed_of(H, H->cur);
     cudaError_t e = cudaMemsetAsync(out, 0, 2 * sizeof(double), st);
     if (e != cudaSuccess) return e;
+    if (explicit_scheme(H) && !local_speed(H)) {
+        // the fully explicit schemes step with the spectral radius max(|u| + c)
+        launch_speeds(H, out, st);
+        e = cudaGetLastError();
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(out, out + 1, sizeof(double), cudaMemcpyDeviceToDevice, st);
+        return e;
+    }
     if (H->windowed) {
         double* const* U = state(H);
         k_umax_df<<<convert_blocks(H), 256, 0, st>>>(H->n, reinterpret_cast<const float2*>(U[0]),

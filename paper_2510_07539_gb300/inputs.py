@@ -56,6 +56,16 @@ def solitary(x, h0: float, amp: float, x0: float = 0.0, t: float = 0.0, g: float
     return h, h * u, h * h, -h * h * ux
 
 
+def gaussian_bell(n: int = 5000, x_left: float = -200.0, x_right: float = 200.0,
+                  h_inf: float = 1.0, amp: float = 1.0):
+    """The breakdown of a Gaussian bell (Sec. 6.1): h = h_inf + amp exp(-x^2/20),
+    u = 0, eta = h, w = 0 on [x_left, x_right]: x, dx, (h, q, m, r)."""
+    x, dx = cell_centres(n, x_left, x_right)
+    h = h_inf + amp * np.exp(-x * x / 20.0)
+    z = np.zeros(n)
+    return x, dx, (h, z.copy(), h * h, z.copy())
+
+
 # --------------------------------------------------------------------------
 # Smoothed dam break: h = (hl + hr)/2 - (hl - hr)/2 tanh(x / (w dx)), u = 0,
 # eta = h, w = 0 (the tanh smoothing of the Favre-wave set-up, Sec. 6.4).

@@ -224,3 +224,62 @@ def test_solitary_wave_convergence(scheme, cfl, order):
         E = inputs.solitary(x, 1.0, 0.2, 0.0, t=1.0, period=100.0)
         errs.append(np.sum(np.abs(V[0] - E[0])) / np.sum(np.abs(V[0])))
     assert errs[0] / errs[1] > 3.0 and errs[1] / errs[2] > 1.8, errs
+
+
+def spectral_radius(U, g, lam):
+    """max over cells of |u| + c, c^2 = g h + (lambda/3) eta^2/h^2 (Sec. 2.2,
+    the eigenvalues of the hSGN system), from its definition."""
+    h, q, m, _ = U
+    eta = m / h
+    return float(np.max(np.abs(q / h) + np.sqrt(g * h + (lam / 3.0) * eta * eta / (h * h))))
+
+
+def test_explicit_steps_use_the_spectral_radius_as_rusanov_speed():
+    # every wave of the explicit schemes is explicit: their Rusanov speed is
+    # the spectral radius of the state (reading R12). One Euler step is
+    # U + dt L(U); one Heun step is (U + U* + dt L(U*))/2 with U* the Euler
+    # step, each L with the spectral radius of its own state
+    n, dx, lam, g = 400, 0.1, 300.0, 9.81
+    U = inputs.random_state(31, n, dx)
+    dt = 0.004
+
+    def L(V):
+        p = oracle.Params(n, dx, oracle.BC_PERIODIC, lam=lam,
+                          speed=spectral_radius(V, g, lam))
+        return oracle.explicit_rhs(p, V)
+
+    def L0(V):  # forward Euler runs without reconstruction (first order)
+        p = oracle.Params(n, dx, oracle.BC_PERIODIC, lam=lam, recon=0,
+                          speed=spectral_radius(V, g, lam))
+        return oracle.explicit_rhs(p, V)
+
+    LU0 = L0(U)
+    euler = [U[k] + dt * LU0[k] for k in range(4)]
+    got = oracle.run(oracle.Params(n, dx, oracle.BC_PERIODIC, lam=lam, recon=0,
+                                   scheme=oracle.SCHEME_EX_EULER), U, dt, 1)
+    for k in range(4):
+        np.testing.assert_allclose(got[k], euler[k], rtol=1e-13, atol=1e-13)
+    p_heun = oracle.Params(n, dx, oracle.BC_PERIODIC, lam=lam, scheme=oracle.SCHEME_EX_HEUN)
+    got = oracle.run(p_heun, U, dt, 1)
+    # Heun's two evaluations share the step's speed, that of U^n
+    LU = L(U)
+    sp = spectral_radius(U, g, lam)
+    p = oracle.Params(n, dx, oracle.BC_PERIODIC, lam=lam, speed=sp)
+    Us = [U[k] + dt * LU[k] for k in range(4)]
+    LUs = oracle.explicit_rhs(p, Us)
+    heun = [0.5 * (U[k] + Us[k] + dt * LUs[k]) for k in range(4)]
+    for k in range(4):
+        np.testing.assert_allclose(got[k], heun[k], rtol=1e-13, atol=1e-13)
+
+
+def test_explicit_heun_gaussian_bell_stays_bounded():
+    # the breakdown of the Gaussian bell (Sec. 6.1, lambda = 100) to t = 35 with
+    # Heun at CFL 0.4, on 1000 cells of [-200, 200]: with a Rusanov speed of
+    # |u| only, the centred acoustic terms of the explicit scheme are undamped
+    # and the depth goes negative long before t = 35
+    x, dx, U = inputs.gaussian_bell(n=1000)
+    p = oracle.Params(1000, dx, oracle.BC_TRANSMISSIVE, lam=100.0, scheme=oracle.SCHEME_EX_HEUN)
+    dt0, _, _ = oracle.suggest_dt(p, U, 0.4, 0.0)
+    steps = int(np.ceil(35.0 / dt0))
+    got = oracle.run(p, U, 35.0 / steps, steps)
+    assert np.all(got[0] > 0.5) and np.all(got[0] < 2.0)
