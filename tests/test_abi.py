@@ -86,3 +86,40 @@ def test_null_handle_calls_are_rejected(lib):
     assert lib.hsgn_step(None, 0.1, None) == 1
     assert lib.hsgn_run(None, 0.1, 1, None) == 1
     assert lib.hsgn_check(None, None) == 1
+    buf = (ctypes.c_double * 4)()
+    ptr = ctypes.cast(buf, ctypes.c_void_p)
+    assert lib.hsgn_set_state(None, ptr, ptr, ptr, ptr, None) == 1
+    assert lib.hsgn_get_state(None, ptr, ptr, ptr, ptr, None) == 1
+    assert lib.hsgn_copy_state_out(None, ptr, ptr, ptr, ptr, None) == 1
+    assert lib.hsgn_enqueue(None, 0.1, 1, None) == 1
+    dt = ctypes.c_double()
+    assert lib.hsgn_suggest_dt(None, 2.0, 0.5, ctypes.byref(dt), None) == 1
+    v = (ctypes.c_int32 * 2)()
+    assert lib.hsgn_batched_set_tiles(None, ctypes.cast(v, ctypes.c_void_p)) == 1
+    ms = (ctypes.c_double * 3)()
+    ch = ctypes.c_int32()
+    assert lib.hsgn_batched_autotune(None, 2, ctypes.cast(ms, ctypes.c_void_p), ctypes.byref(ch),
+                                     None) == 1
+    assert lib.hsgn_batched_set_dt(None, ctypes.cast(ms, ctypes.c_void_p)) == 1
+    assert lib.hsgn_profile(None, 1) == 1
+    lib.hsgn_destroy(None)
+
+
+def test_batched_create_rejects_bad_arguments(lib):
+    h = ctypes.c_void_p()
+    ns = (ctypes.c_int64 * 2)(100, 2)  # 2 cells: below the minimum of 3
+    xl = (ctypes.c_double * 2)(0.0, 0.0)
+    xr = (ctypes.c_double * 2)(10.0, 10.0)
+    lm = (ctypes.c_double * 2)(100.0, 100.0)
+    args = [ctypes.cast(a, ctypes.c_void_p) for a in (ns, xl, xr, lm)]
+    assert lib.hsgn_create_batched(2, *args, 9.81, 0, 1, ctypes.byref(h)) == 1
+    ns[1] = 100
+    xr[1] = -1.0  # empty interval
+    assert lib.hsgn_create_batched(2, *args, 9.81, 0, 1, ctypes.byref(h)) == 1
+    xr[1] = 10.0
+    lm[0] = -1.0  # negative lambda
+    assert lib.hsgn_create_batched(2, *args, 9.81, 0, 1, ctypes.byref(h)) == 1
+    lm[0] = 100.0
+    assert lib.hsgn_create_batched(0, *args, 9.81, 0, 1, ctypes.byref(h)) == 1
+    assert lib.hsgn_create_batched(2, *args, 9.81, 7, 1, ctypes.byref(h)) == 1  # unknown BC
+    assert not h.value
