@@ -78,6 +78,9 @@ def parse_args():
     ap.add_argument("--no-shelf", action="store_true", help="skip the 2^24-cell shelf workload")
     ap.add_argument("--no-paper-runs", action="store_true",
                     help="skip the runs of the paper's CPU-time tables")
+    ap.add_argument("--no-tridiag", action="store_true",
+                    help="skip the standalone tridiagonal solve")
+    ap.add_argument("--tridiag-log2n", type=int, default=24, help="rows of that solve (log2)")
     ap.add_argument("--shelf-log2n", type=int, default=24, help="cells of the shelf workload (log2)")
     ap.add_argument("--shelf-steps", type=int, default=50, help="timed steps of the shelf workload")
     ap.add_argument("--sequential", action="store_true",
@@ -497,6 +500,38 @@ def time_paper_runs(S, torch, stream):
             "note": "paper CPU seconds: unstated hardware and implementation; context only"}
 
 
+def time_tridiag(S, torch, stream, hbm_peak, log2n=24, reps=10):
+    """The library's tridiagonal component (hsgn_tridiag_solve, FP64) on 2^24
+    rows of an hSGN-like SPD system, cyclic and not. Each call synchronises
+    (it reports the device error word), so the per-call time includes that
+    round trip. Algorithmic bytes 40 per row (a, b, c, d in, x out)."""
+    from paper_2510_07539_gb300 import inputs as inp
+    n = 1 << log2n
+    out = {}
+    for periodic in (False, True):
+        rows = [torch.tensor(v, device="cuda") for v in inp.random_tridiag(77, n, periodic)]
+        x = torch.empty(n, dtype=torch.float64, device="cuda")
+        ws = torch.empty(S.tridiag_workspace_bytes(n) + 512, dtype=torch.uint8, device="cuda")
+        for _ in range(3):
+            S.tridiag_solve(*rows, periodic, out=x, workspace=ws)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            S.tridiag_solve(*rows, periodic, stream=stream, out=x, workspace=ws)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        gbs = 40.0 * n / (ms / 1e3) / 1e9
+        out["cyclic" if periodic else "open"] = {
+            "rows": n, "ms_per_solve": ms, "rows_per_s": n / (ms / 1e3), "achieved_gbs": gbs,
+            "frac_of_hbm": gbs / hbm_peak}
+    out["note"] = ("block reduction (one warp per 128 rows, three right-hand sides), recursive "
+                   "separator levels, back-substitution; FP64, each call synchronises")
+    return out
+
+
 def time_adjoint(S, torch, stream):
     """The adjoint workload: N = 4096, dx = 0.1, periodic, lambda = 100, a wave
     a = 0.1 over 8 Gaussian bumps (bottom form), 2000 steps at CFL_IMEX 2, the
@@ -712,6 +747,9 @@ def run_ours(args):
     adjoint = None
     if not args.no_adjoint and rank == 0:
         adjoint = time_adjoint(S, torch, stream)
+    tridiag = None
+    if not args.no_tridiag and rank == 0:
+        tridiag = time_tridiag(S, torch, stream, hbm_peak, args.tridiag_log2n)
     paper_runs = None
     if not args.no_paper_runs and rank == 0:
         paper_runs = time_paper_runs(S, torch, stream)
@@ -870,7 +908,7 @@ def run_ours(args):
             "batched_vs_fp64_single": (batched["value"] / fp64["value"])
             if (batched and fp64) else None,
             "comparators": comparators, "adjoint": adjoint, "shelf": shelf,
-            "paper_runs": paper_runs,
+            "paper_runs": paper_runs, "tridiag": tridiag,
             "cpu_baseline": cpu, "e2e": e2e,
             "clocks": clocks, "gpu_launches": launches,
         }

@@ -275,13 +275,17 @@ def tridiag_workspace_bytes(n: int) -> int:
     return nb.value
 
 
-def tridiag_solve(a, b, c, d, periodic: bool, stream=None):
-    """Solve the (cyclic) tridiagonal system on the GPU; returns x as a new tensor."""
+def tridiag_solve(a, b, c, d, periodic: bool, stream=None, out=None, workspace=None):
+    """Solve the (cyclic) tridiagonal system on the GPU; returns x (a new
+    tensor, or `out`). `workspace`: a uint8 device tensor of at least
+    tridiag_workspace_bytes(n) + 256 bytes, allocated here when None."""
     load()
     n = b.numel()
-    x = torch.empty_like(d)
+    x = torch.empty_like(d) if out is None else out
     nbytes = tridiag_workspace_bytes(n)
-    ws = torch.empty(max(nbytes, 256) + 256, dtype=torch.uint8, device=d.device)
+    ws = workspace
+    if ws is None or ws.numel() < max(nbytes, 256) + 256:
+        ws = torch.empty(max(nbytes, 256) + 256, dtype=torch.uint8, device=d.device)
     base = ws.data_ptr()
     aligned = (base + 255) // 256 * 256
     _check(_lib.hsgn_tridiag_solve(int(n), int(bool(periodic)), _ptr(a), _ptr(b), _ptr(c), _ptr(d),
