@@ -81,6 +81,11 @@ def parse_args():
     ap.add_argument("--no-tridiag", action="store_true",
                     help="skip the standalone tridiagonal solve")
     ap.add_argument("--tridiag-log2n", type=int, default=24, help="rows of that solve (log2)")
+    ap.add_argument("--accuracy", action="store_true",
+                    help="instead of the benchmark: both forms against the FP64 oracle / form "
+                         "over the configurations' full lengths (minutes)")
+    ap.add_argument("--accuracy-steps", type=int, default=2000)
+    ap.add_argument("--shelf-accuracy-steps", type=int, default=5000)
     ap.add_argument("--shelf-log2n", type=int, default=24, help="cells of the shelf workload (log2)")
     ap.add_argument("--shelf-steps", type=int, default=50, help="timed steps of the shelf workload")
     ap.add_argument("--sequential", action="store_true",
@@ -918,10 +923,91 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def _oracle_dam_break(args):
+    """Oracle run of one dam-break instance (a process of the accuracy mode)."""
+    lam, steps, log2n = args
+    import numpy as np
+    import oracle
+    n, dx, xl, xr, U, _ = workload(log2n, [lam])
+    p = oracle.Params(n, dx, oracle.BC_TRANSMISSIVE, lam=lam)
+    dt, _, _ = oracle.suggest_dt(p, U, 4.0, 0.5)
+    t0 = time.perf_counter()
+    r = oracle.run(p, U, dt, steps)
+    return lam, dt, [np.asarray(v) for v in r], time.perf_counter() - t0
+
+
+def run_accuracy(args):
+    """The error of both forms at the configurations' full lengths, one JSON
+    line: the dam break (2^20 cells, lambda 10 / 100 / 1000, 2000 steps at
+    CFL_IMEX 4) against the FP64 oracle, whose three runs go to a process pool
+    on the host cores (started with spawn, before the first GPU call) while the
+    GPU runs; and the shelf (2^24 cells, 5000 steps) in mixed precision against
+    the FP64 form. Minutes of host and GPU time; not part of the default run."""
+    import multiprocessing as mp
+    import numpy as np
+    lams = [float(x) for x in args.lams.split(",")]
+    steps = args.accuracy_steps
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(len(lams)) as pool:
+        fut = pool.map_async(_oracle_dam_break, [(l, steps, args.log2n) for l in lams])
+        import torch
+        from paper_2510_07539_gb300 import inputs as inp, solver as S
+        n, dx, xl, xr, U, _ = workload(args.log2n, lams)
+        Ud = [torch.tensor(u, device="cuda") for u in U]
+        gpu = {}
+        for lam in lams:
+            for name, flags in (("fp64", S.FLAG_FP64), ("mixed", S.FLAG_MIXED)):
+                with S.Solver(n, xl, xr, S.BC_TRANSMISSIVE, lam=lam, flags=flags) as s:
+                    s.set_state(*Ud)
+                    s.run(s.suggest_dt(4.0, 0.5), steps)
+                    gpu[(lam, name)] = [v.cpu().numpy() for v in s.get_state()]
+        # the shelf: FP64 against mixed over the configuration's 5000 steps
+        sn = 1 << args.shelf_log2n
+        x, sdx, b, SU = inp.shelf_wave(sn, dx=0.005 * (1 << 24) / sn)
+        SUd = [torch.tensor(u, device="cuda") for u in SU]
+        shelf, sdt, sms = {}, None, {}
+        for name, flags in (("fp64", S.FLAG_WELL_BALANCED),
+                            ("mixed", S.FLAG_WELL_BALANCED | S.FLAG_MIXED)):
+            with S.Solver(sn, 0.0, sn * sdx, S.BC_TRANSMISSIVE, lam=1000.0, flags=flags,
+                          bathymetry=b) as s:
+                s.set_state(*SUd)
+                if sdt is None:
+                    sdt = s.suggest_dt(4.0, 0.5)
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                s.run(sdt, args.shelf_accuracy_steps)
+                sms[name] = time.perf_counter() - t0
+                shelf[name] = [v.cpu().numpy() for v in s.get_state()]
+        refs = fut.get()
+    names = ("h", "q", "heta", "hw")
+    dam = []
+    for lam, dt, ref, el in refs:
+        for form in ("fp64", "mixed"):
+            got = gpu[(lam, form)]
+            dam.append({"lambda": lam, "form": form, "oracle_s": el,
+                        "rel_l2": {nm: float(np.linalg.norm(got[k] - ref[k]) / np.linalg.norm(ref[k]))
+                                   for k, nm in enumerate(names)},
+                        "depth_rel_l1": float(np.sum(np.abs(got[0] - ref[0])) /
+                                              np.sum(np.abs(ref[0])))})
+    ref, got = shelf["fp64"], shelf["mixed"]
+    m0 = float(np.sum(SU[0]))
+    line = {"mode": "accuracy",
+            "dam_break": {"cells": n, "steps": steps, "vs": "FP64 oracle", "runs": dam},
+            "shelf": {"cells": sn, "steps": args.shelf_accuracy_steps, "vs": "FP64 form",
+                      "seconds": sms,
+                      "rel_l2": {nm: float(np.linalg.norm(got[k] - ref[k]) / np.linalg.norm(ref[k]))
+                                 for k, nm in enumerate(names)},
+                      "mass_drift": {f: abs(float(np.sum(shelf[f][0])) - m0) / m0
+                                     for f in ("fp64", "mixed")}}}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse_args()
     if args.impl == "reference":
         run_reference(args)
+    elif args.accuracy:
+        run_accuracy(args)
     else:
         run_ours(args)
 
