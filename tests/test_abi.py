@@ -123,3 +123,15 @@ def test_batched_create_rejects_bad_arguments(lib):
     assert lib.hsgn_create_batched(0, *args, 9.81, 0, 1, ctypes.byref(h)) == 1
     assert lib.hsgn_create_batched(2, *args, 9.81, 7, 1, ctypes.byref(h)) == 1  # unknown BC
     assert not h.value
+
+
+def test_degenerate_grids_are_rejected(lib):
+    # fewer than 3 cells (the stencil of a stage spans 5) is an invalid grid;
+    # nothing is allocated
+    from paper_2510_07539_gb300.solver import Grid
+    h = ctypes.c_void_p()
+    for n in (0, 1, 2, -5):
+        g = Grid(n, 0.0, 1.0, 0, 0)
+        for flags in (0, 0x1):
+            assert lib.hsgn_create(ctypes.byref(g), 9.81, 1.0, None, flags, ctypes.byref(h)) == 1
+    assert not h.value

@@ -772,3 +772,35 @@ def test_device_errors_are_reported_by_every_form(form):
         s.set_state(*(dev(u) for u in ok))
         run(2)
         assert all(np.all(np.isfinite(t.cpu().numpy())) for t in s.get_state())
+
+
+def test_windowed_at_2_27_cells_properties():
+    # 134 million cells (10.7 GB of state and increments), far beyond what
+    # the oracle can follow: properties that hold at any size. The dam break
+    # over 3 steps keeps its mass, stays finite, leaves the far field at rest,
+    # and around the front equals the same dam break on 2^20 cells of the same
+    # spacing (only the tiling differs; the dropped window coupling is below
+    # 2^-30 of the increments)
+    dx, lam, steps = 0.05, 1000.0, 3
+    big, small = 1 << 27, 1 << 20
+    xb, Ub = inputs.dam_break(big, dx, 1.2, 1.0, 5.0 / dx)
+    p = oracle.Params(small, dx, 1, lam=lam)
+    xs, Us = inputs.dam_break(small, dx, 1.2, 1.0, 5.0 / dx)
+    dt, _, _ = oracle.suggest_dt(p, Us, 4.0, 0.5)
+    got = mixed_run(big, -0.5 * big * dx, 0.5 * big * dx, 1, lam, Ub, dt, steps)
+    ref = mixed_run(small, -0.5 * small * dx, 0.5 * small * dx, 1, lam, Us, dt, steps)
+    assert all(np.all(np.isfinite(g)) for g in got)
+    m0 = np.sum(Ub[0])
+    assert abs(np.sum(got[0]) - m0) <= 1e-12 * m0
+    far = np.abs(xb) > 2000.0
+    assert np.max(np.abs(got[0][far] - Ub[0][far])) <= 1e-12
+    assert np.max(np.abs(got[1][far])) <= 1e-12
+    # the central 2^16 cells of both grids hold the same cells; q and h w
+    # against the scale of their back-substitution summands, as elsewhere
+    cb, cs, w = big // 2, small // 2, 1 << 15
+    sc = summand_scales(small, dx, 1, lam, Us, dt)
+    for k in range(4):
+        a, b = got[k][cb - w:cb + w], ref[k][cs - w:cs + w]
+        scale = np.linalg.norm(b if k in (0, 2) else sc[k][cs - w:cs + w])
+        bound = 1e-7 if k in (0, 2) else 1e-6
+        assert np.linalg.norm(a - b) <= bound * scale, (k, np.linalg.norm(a - b) / scale)
