@@ -96,7 +96,9 @@ __device__ __forceinline__ void chunk_of(int nrows, int t, int& cs, int& m, int&
         m = 0;
         return;
     }
-    const int base = nrows / teff, extra = nrows % teff;
+    // teff = T (a power of two: shift and mask) or teff = nrows (one row each)
+    static_assert((T & (T - 1)) == 0, "T must be a power of two");
+    const int base = nrows >= T ? nrows / T : 1, extra = nrows >= T ? nrows % T : 0;
     m = base + (t < extra ? 1 : 0);
     cs = t * base + (t < extra ? t : extra);
 }
