@@ -806,7 +806,7 @@ def run_ours(args):
             "ms_per_step": bms / args.steps,
             "gpu_launches_per_step": 4 if tune["choice"] == 2 else 2,
             "autotune": {"ms_per_step_all_large_all_small_mixed": tune["ms_per_step"],
-                         "kept": ("all large tiles (895 rows)", "all small tiles (383 rows)",
+                         "kept": ("all large tiles (894 rows)", "all small tiles (382 rows)",
                                   "per-instance cost model")[tune["choice"]]},
         }
         if rank == 0 and world == 1 and not args.no_cpu:

@@ -276,8 +276,8 @@ int hsgn_batched_suggest_dt(hsgn_handle_t h, double cfl, double mcfl, double* dt
 
 /* Tiles of a batch (the windowed kernel; HSGN_ERR_UNIMPLEMENTED for a batch
  * created with HSGN_EXACT_SOLVE). variant[k] (host array of `count`) selects
- * for instance k the large windowed kernel (0: 256 threads, tiles of up to 895
- * rows, the default) or the small one (1: 128 threads, tiles of up to 383
+ * for instance k the large windowed kernel (0: 256 threads, tiles of up to 894
+ * rows, the default) or the small one (1: 128 threads, tiles of up to 382
  * rows, less padding for short instances); each kernel then runs as one launch
  * per stage over its instances' tiles. Values other than 0 and 1 give
  * INVALID_ARG. Synchronises the device; the results of both variants agree to

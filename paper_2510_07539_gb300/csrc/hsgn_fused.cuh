@@ -197,16 +197,31 @@ __host__ inline int64_t fused_tile_rows(int64_t n, int64_t smax, int64_t slots) 
     return (n + pmin - 1) / pmin;
 }
 
-// Capacity of the fused kernel: T threads, M rows per thread, overlap HW.
+// Capacity of the fused kernel: T threads, M = 4 rows per thread, overlap HW.
+// Thread t owns the window cells and rows 4t .. 4t + 3 in the flux,
+// coefficient, row and solve phases; the W + 2 cells c = -1 .. W whose
+// coefficients are formed must fit, hence R = T M - 2 window rows (the
+// elimination adds one identity row). The cell arrays have a multiple of 4
+// entries so that every array starts on a 16-byte boundary.
 template <int T, int M, int HW>
 struct FusedGeom {
-    static constexpr int R = T * M - 1;      // window rows (+1 identity row in the elimination)
+    static constexpr int R = T * M - 2;      // window rows
     static constexpr int S = R - 2 * HW;     // largest tile
     static constexpr int HB = HW - 1;        // half-width of a tile-boundary mini-window
-    static constexpr int NC = pd_size(R + 6);
+    static constexpr int NC = (pd_size(R + 6) + 3) & ~3;
     static constexpr int MB = (2 * HB + 1 + 31) / 32;  // rows per lane of the mini solve
+    static_assert(M == 4, "the cell phases move four cells per thread as one float4");
     static_assert(S > 0, "overlap too wide for the window");
 };
+
+// Shared-memory vectors of four consecutive cells (16-byte aligned).
+__device__ __forceinline__ void lds4(const float* a, float* v) {
+    const float4 x = *reinterpret_cast<const float4*>(a);
+    v[0] = x.x; v[1] = x.y; v[2] = x.z; v[3] = x.w;
+}
+__device__ __forceinline__ void sts4(float* a, const float* v) {
+    *reinterpret_cast<float4*>(a) = make_float4(v[0], v[1], v[2], v[3]);
+}
 
 // Single-precision reciprocal: the hardware approximation (hsgn_tridiag.cuh).
 __device__ __forceinline__ float rcpa(float x) { return rcp(x); }
@@ -215,10 +230,11 @@ __device__ __forceinline__ float rcpa(float x) { return rcp(x); }
 // window at index c+3 in the U arrays, c+1 in the per-cell arrays):
 //   phase 0: hl, ql, ml, rl (U_l), qb, mb, rb (U_b), Dh, Dq, Dm (differences
 //            of U_b at the face to the right of a cell);
-//   phase 1: fluxes Fq -> ql, Fm -> X0, Fr -> rl (face f at f+2);
-//   phase 2: dq -> ql, dm -> X0, dr -> rl, beta -> hl, delta -> ml;
-//   phase 3: rows: face couplings tau^2 beta_{f+1/2}/dx^2 -> rb, right-hand
-//            sides -> mb (both padded, read in the chunk mapping);
+//   phases 1+2 (fluxes in registers): dq -> ql, dm -> X0, dr -> rl,
+//            beta -> hl, delta -> ml;
+//   phase 3 (rows in registers): for the stage-2 mini solves the face couplings
+//            tau^2 beta_{f+1/2}/dx^2 -> rb and the right-hand sides -> mb
+//            (both padded: a lane of the mini solve reads rows at a stride);
 //   phase 4: dh -> Dq (padded); face mass fluxes of the tile -> rb.
 // The bottom form (WB) reuses Dh for the jump of h_l - h_b at the face, Dm for
 // P_l = h_l^2 - m_l and then beta (hl keeps h_l), ml for the non-gravity part
@@ -431,100 +447,100 @@ __global__ void __launch_bounds__(T, (WB ? 768 : 1024) / T) k_mixed_fused(const 
     const float gspeed = p.local_speed ? 0.f : (float)(*spd_in);
     unsigned bad = 0;
 
-    // ---- 1. Rusanov fluxes of U_l at faces f = -2 .. W (index f + 2), Sec. 4.1.
-    //         All reads of phase 0's ql / rl happen before the barrier, the
-    //         flux stores (which reuse ql, rl) after it.
-    constexpr int NF = (Gm::R + 3 + T - 1) / T;
-    float fq_[NF], fm_[NF], fr_[NF];
+    // ---- 1+2. Thread t owns the cells j = 4t .. 4t + 3 (window cell c = j - 1;
+    //           c = -1 .. W are formed). In registers it evaluates the Rusanov
+    //           fluxes of U_l (Sec. 4.1) at the five faces jf = 4t .. 4t + 4 around
+    //           them (face jf lies between cells jf - 2 and jf - 1) from the
+    //           cells 4t - 3 .. 4t + 4 (array index 4t .. 4t + 7, two float4 per
+    //           variable), then the increments and coefficients of its cells:
+    //           r^dag = r_b + dr' + lambda tau, m^dag = m_b + dm' + lambda tau^2,
+    //           q^dag = q_b + dq. The results are stored after the barrier
+    //           (they reuse the arrays the other threads still read).
+    const float lt2 = c_lt2, tdx = c_tdx, Cc = c_Cc;
+    const int j0 = 4 * tid;
+    float dq_[4], dm_[4], dr_[4], be_[4], de_[4];
+    float pt_[WB ? 4 : 1];
+    float kloc = 0.f, kmin = 3.0e38f;
+    {
+        float H[8], Q[8], Mv[8], Rv[8];
+        lds4(sm.hl + j0, H); lds4(sm.hl + j0 + 4, H + 4);
+        lds4(sm.ql + j0, Q); lds4(sm.ql + j0 + 4, Q + 4);
+        lds4(sm.ml + j0, Mv); lds4(sm.ml + j0 + 4, Mv + 4);
+        lds4(sm.rl + j0, Rv); lds4(sm.rl + j0 + 4, Rv + 4);
+        float FQ[5], FM[5], FR[5];
 #pragma unroll
-    for (int it = 0; it < NF; ++it) {
-        const int j = tid + it * T;
-        fq_[it] = fm_[it] = fr_[it] = 0.f;
-        if (j < W + 3) {
-            const float hm = sm.hl[j], h0 = sm.hl[j + 1], h1 = sm.hl[j + 2], h2 = sm.hl[j + 3];
-            const float qm = sm.ql[j], q0 = sm.ql[j + 1], q1 = sm.ql[j + 2], q2 = sm.ql[j + 3];
-            const float mm = sm.ml[j], m0 = sm.ml[j + 1], m1 = sm.ml[j + 2], m2 = sm.ml[j + 3];
-            const float rm = sm.rl[j], r0_ = sm.rl[j + 1], r1 = sm.rl[j + 2], r2 = sm.rl[j + 3];
+        for (int e = 0; e < 5; ++e) {
+            const float hm = H[e], h0 = H[e + 1], h1 = H[e + 2], h2 = H[e + 3];
+            const float qm = Q[e], q0 = Q[e + 1], q1 = Q[e + 2], q2 = Q[e + 3];
+            const float mm = Mv[e], m0 = Mv[e + 1], m1 = Mv[e + 2], m2 = Mv[e + 3];
+            const float rm = Rv[e], r0_ = Rv[e + 1], r1 = Rv[e + 2], r2 = Rv[e + 3];
             const float hL = fmaf(0.25f, h1 - hm, h0), hR = fmaf(-0.25f, h2 - h0, h1);
             const float qL = fmaf(0.25f, q1 - qm, q0), qR = fmaf(-0.25f, q2 - q0, q1);
             const float mL = fmaf(0.25f, m1 - mm, m0), mR = fmaf(-0.25f, m2 - m0, m1);
             const float rL = fmaf(0.25f, r1 - rm, r0_), rR = fmaf(-0.25f, r2 - r0_, r1);
-            if (!pos_finite(fminf(hL, hR))) bad |= HSGN_DEV_ERR_DEPTH;
+            if (j0 + e < W + 3 && !pos_finite(fminf(hL, hR))) bad |= HSGN_DEV_ERR_DEPTH;
             const float ip = rcpa(hL * hR);
             const float uL = qL * hR * ip, uR = qR * hL * ip;
             const float s = p.local_speed ? fmaxf(fabsf(uL), fabsf(uR)) : gspeed;
-            fq_[it] = 0.5f * (fmaf(uL, qL, uR * qR) - s * (qR - qL));
-            fm_[it] = 0.5f * (fmaf(uL, mL, uR * mR) - s * (mR - mL));
-            fr_[it] = 0.5f * (fmaf(uL, rL, uR * rR) - s * (rR - rL));
+            FQ[e] = 0.5f * (fmaf(uL, qL, uR * qR) - s * (qR - qL));
+            FM[e] = 0.5f * (fmaf(uL, mL, uR * mR) - s * (mR - mL));
+            FR[e] = 0.5f * (fmaf(uL, rL, uR * rR) - s * (rR - rL));
         }
-    }
-    __syncthreads();
-    float* const Fq = sm.ql;
-    float* const Fm = sm.X0;
-    float* const Fr = sm.rl;
-#pragma unroll
-    for (int it = 0; it < NF; ++it) {
-        const int j = tid + it * T;
-        if (j < W + 3) {
-            Fq[j] = fq_[it];
-            Fm[j] = fm_[it];
-            Fr[j] = fr_[it];
+        // cells j at array index j + 2: rb, mb (and the bottom-form arrays) of
+        // 4t + 2 .. 4t + 5 from two float4 each; hl, ml from the registers above
+        float RB[8], MB[8];
+        lds4(sm.rb + j0, RB); lds4(sm.rb + j0 + 4, RB + 4);
+        lds4(sm.mb + j0, MB); lds4(sm.mb + j0 + 4, MB + 4);
+        float SB[WB ? 8 : 1], PL[WB ? 8 : 1], MBL[WB ? 8 : 1];
+        if constexpr (WB) {
+            lds4(sm.wb.Sb + j0, SB); lds4(sm.wb.Sb + j0 + 4, SB + 4);
+            lds4(sm.Dm + j0, PL); lds4(sm.Dm + j0 + 4, PL + 4);
+            lds4(sm.wb.Mbl + j0, MBL); lds4(sm.wb.Mbl + j0 + 4, MBL + 4);
         }
-    }
-    __syncthreads();
-
-    // ---- 2. increments and coefficients at cells c = -1 .. W (index c + 1):
-    //         r^dag = r_b + dr' + lambda tau, m^dag = m_b + dm' + lambda tau^2, q^dag = q_b + dq
-    constexpr int NCL = (Gm::R + 2 + T - 1) / T;
-    const float lt2 = c_lt2, tdx = c_tdx, Cc = c_Cc;
-    float dq_[NCL], dm_[NCL], dr_[NCL], be_[NCL], de_[NCL];
-    float pt_[WB ? NCL : 1];
-    float kloc = 0.f, kmin = 3.0e38f;
 #pragma unroll
-    for (int it = 0; it < NCL; ++it) {
-        const int j = tid + it * T;
-        dq_[it] = dm_[it] = dr_[it] = be_[it] = de_[it] = 0.f;
-        if constexpr (WB) pt_[it] = 0.f;
-        if (j < W + 2) {
-            const int c3 = j + 2;
-            const float drv = -tdx * (Fr[j + 1] - Fr[j]);
-            float dmv = fmaf(tau, sm.rb[c3] + drv, -tdx * (Fm[j + 1] - Fm[j]));
-            // bottom source of the (h eta) equation, -(3/2) h u b_x (Sec. 2.3, eq. (hSGNb_eq)), from U_l
-            if constexpr (WB) dmv = fmaf(-c_fq, sm.wb.Sb[c3], dmv);
-            const float dqv = -tdx * (Fq[j + 1] - Fq[j]);
-            const float msv = sm.mb[c3] + dmv + lt2;
-            const float h = sm.hl[c3];
-            if (!pos_finite(h)) bad |= HSGN_DEV_ERR_DEPTH;
-            const float Dh_ = fmaf(h, h, lt2);
-            const float Rr = rcpa(h * Dh_);
-            const float ih = Dh_ * Rr;
-            const float iD = h * Rr;
-            const float eta = sm.ml[c3] * ih;
-            const float e = eta * ih;
-            const float alpha = fmaf(2.f, e, -1.f) * ih * (-1.f / 3.f);
-            const float c2 = fmaf(g, h, (lam * (1.f / 3.f)) * e * e);
-            const float a2 = fmaf(-lam * eta, alpha, c2);
-            const float ib1 = h * h * iD;
-            const float beta2 = (2.f * lt2) * h * iD * iD;
-            const float beta = fmaf(lam * alpha * beta2, msv, a2);
-            if (!pos_finite(beta)) bad |= HSGN_DEV_ERR_COERCIVE;
-            dq_[it] = dqv;
-            dm_[it] = dmv;
-            dr_[it] = drv;
-            be_[it] = beta;
-            if constexpr (!WB) {
-                de_[it] = alpha * ib1;
-            } else {
-                // p~ = (lambda/3)(1 - m_l/h_l^2) = (lambda/3) P_l / h_l^2;
-                // m^dag b_1 - m_l = (h^2 (m_b - m_l + dm) + lambda tau^2 P_l) / (h^2 + lambda tau^2)
-                const float Pl = sm.Dm[c3];
-                const float ptil = (lam * (1.f / 3.f)) * Pl * ih * ih;
-                const float X = fmaf(h * h, sm.wb.Mbl[c3] + dmv, lt2 * Pl) * iD;
-                de_[it] = fmaf(eta, ptil, lam * alpha * X);  // pi = eta p~ + lambda alpha X
-                pt_[it] = ptil;
+        for (int k = 0; k < 4; ++k) {
+            dq_[k] = dm_[k] = dr_[k] = be_[k] = de_[k] = 0.f;
+            if constexpr (WB) pt_[k] = 0.f;
+            if (j0 + k < W + 2) {
+                const float drv = -tdx * (FR[k + 1] - FR[k]);
+                float dmv = fmaf(tau, RB[k + 2] + drv, -tdx * (FM[k + 1] - FM[k]));
+                // bottom source of the (h eta) equation, -(3/2) h u b_x (Sec. 2.3, eq. (hSGNb_eq)), from U_l
+                if constexpr (WB) dmv = fmaf(-c_fq, SB[k + 2], dmv);
+                const float dqv = -tdx * (FQ[k + 1] - FQ[k]);
+                const float msv = MB[k + 2] + dmv + lt2;
+                const float h = H[k + 2];
+                if (!pos_finite(h)) bad |= HSGN_DEV_ERR_DEPTH;
+                const float Dh_ = fmaf(h, h, lt2);
+                const float Rr = rcpa(h * Dh_);
+                const float ih = Dh_ * Rr;
+                const float iD = h * Rr;
+                const float eta = Mv[k + 2] * ih;
+                const float e = eta * ih;
+                const float alpha = fmaf(2.f, e, -1.f) * ih * (-1.f / 3.f);
+                const float c2 = fmaf(g, h, (lam * (1.f / 3.f)) * e * e);
+                const float a2 = fmaf(-lam * eta, alpha, c2);
+                const float ib1 = h * h * iD;
+                const float beta2 = (2.f * lt2) * h * iD * iD;
+                const float beta = fmaf(lam * alpha * beta2, msv, a2);
+                if (!pos_finite(beta)) bad |= HSGN_DEV_ERR_COERCIVE;
+                dq_[k] = dqv;
+                dm_[k] = dmv;
+                dr_[k] = drv;
+                be_[k] = beta;
+                if constexpr (!WB) {
+                    de_[k] = alpha * ib1;
+                } else {
+                    // p~ = (lambda/3)(1 - m_l/h_l^2) = (lambda/3) P_l / h_l^2;
+                    // m^dag b_1 - m_l = (h^2 (m_b - m_l + dm) + lambda tau^2 P_l) / (h^2 + lambda tau^2)
+                    const float Pl = PL[k + 2];
+                    const float ptil = (lam * (1.f / 3.f)) * Pl * ih * ih;
+                    const float X = fmaf(h * h, MBL[k + 2] + dmv, lt2 * Pl) * iD;
+                    de_[k] = fmaf(eta, ptil, lam * alpha * X);  // pi = eta p~ + lambda alpha X
+                    pt_[k] = ptil;
+                }
+                kloc = fmaxf(kloc, Cc * beta);
+                kmin = fminf(kmin, Cc * beta);
             }
-            kloc = fmaxf(kloc, Cc * beta);
-            kmin = fminf(kmin, Cc * beta);
         }
     }
     __syncthreads();
@@ -534,18 +550,12 @@ __global__ void __launch_bounds__(T, (WB ? 768 : 1024) / T) k_mixed_fused(const 
     float* const bea = WB ? sm.Dm : sm.hl;
     float* const dea = sm.ml;  // delta (flat) or pi (bottom form)
     float* const pta = sm.mb;  // p~ (bottom form)
-#pragma unroll
-    for (int it = 0; it < NCL; ++it) {
-        const int j = tid + it * T;
-        if (j < W + 2) {
-            dqa[j] = dq_[it];
-            dma[j] = dm_[it];
-            dra[j] = dr_[it];
-            bea[j] = be_[it];
-            dea[j] = de_[it];
-            if constexpr (WB) pta[j] = pt_[it];
-        }
-    }
+    sts4(dqa + j0, dq_);
+    sts4(dma + j0, dm_);
+    sts4(dra + j0, dr_);
+    sts4(bea + j0, be_);
+    sts4(dea + j0, de_);
+    if constexpr (WB) sts4(pta + j0, pt_);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         kloc = fmaxf(kloc, __shfl_xor_sync(0xffffffffu, kloc, o));
@@ -570,73 +580,111 @@ __global__ void __launch_bounds__(T, (WB ? 768 : 1024) / T) k_mixed_fused(const 
     }
     __syncthreads();
 
-    // ---- 3. rows of A dh = d - A h_b: face couplings k_f = tau^2/dx^2 beta_{f+1/2}
-    //         (f = -1 .. W-1, at pd(f+1); zero across a transmissive domain end,
-    //         which makes the end rows the Neumann rows) and right-hand sides d_i
-    //         (i = 0 .. W-1, at pd(i)); cell c of the per-cell arrays at c+1,
-    //         the face right of cell c of the difference arrays at c+3
+    // ---- 3. rows i = 4t .. 4t + 3 of A dh = d - A h_b, in the registers of
+    //         thread t: face couplings k_j = tau^2/dx^2 beta at the faces j = 4t ..
+    //         4t + 4 (face j between rows j - 1 and j; zero across a transmissive
+    //         domain end, which makes the end rows the Neumann rows) and the
+    //         right-hand sides d_i (cell c of the per-cell arrays at c + 1, the face
+    //         right of cell c of the difference arrays at c + 3). The couplings and
+    //         right-hand sides also go to shared memory for the tile-face mini
+    //         solves of stage 2 (face j at pd(j), row i at pd(i)), the bottom
+    //         form's face forces Psi for the face fluxes (face j at j + 2).
     const float fq = c_fq, fd = c_fd;
     float* const BF = sm.rb;
     float* const RD = sm.mb;
-    float* Psi = nullptr;  // face forces of the bottom form, face f at f + 3
+    float* Psi = nullptr;  // face forces of the bottom form, face j at j + 2
     if constexpr (WB) Psi = sm.wb.Z;
-    if constexpr (WB) {
-        // face couplings and forces Psi_f, f = -1 .. W-1; zero across a transmissive domain end
-        for (int j = tid; j < W + 1; j += T) {
-            const int f = j - 1;
-            const float bf = 0.5f * (bea[f + 1] + bea[f + 2]);
-            const float hbar = 0.5f * (sm.hl[f + 3] + sm.hl[f + 4]);
-            const float ptf = 0.5f * (pta[f + 1] + pta[f + 2]);
-            float psi = fmaf(g * hbar, sm.wb.Z[f + 3], dea[f + 2] - dea[f + 1]);
-            psi = fmaf(1.5f * ptf, sm.wb.Db[f + 3], psi);
-            psi = fmaf(-bf, sm.Dh[f + 3], psi);
-            float kf = Cc * bf;
-            if (BC == BC_TRANSMISSIVE && ((f < 0 && win.lend) || (f == W - 1 && win.rend))) {
-                kf = 0.f;
-                psi = 0.f;
+    float KF[5], rd[4];
+    float PS[WB ? 5 : 1];
+    {
+        float B[8], DQ[8], QA[8], DH[8];
+        lds4(bea + j0, B); lds4(bea + j0 + 4, B + 4);
+        lds4(sm.Dq + j0, DQ); lds4(sm.Dq + j0 + 4, DQ + 4);
+        lds4(dqa + j0, QA); lds4(dqa + j0 + 4, QA + 4);
+        lds4(sm.Dh + j0, DH); lds4(sm.Dh + j0 + 4, DH + 4);
+        if constexpr (WB) {
+            float H[8], PT[8], DE[8], Z[8], DB[8];
+            lds4(sm.hl + j0, H); lds4(sm.hl + j0 + 4, H + 4);
+            lds4(pta + j0, PT); lds4(pta + j0 + 4, PT + 4);
+            lds4(dea + j0, DE); lds4(dea + j0 + 4, DE + 4);
+            lds4(sm.wb.Z + j0, Z); lds4(sm.wb.Z + j0 + 4, Z + 4);
+            lds4(sm.wb.Db + j0, DB); lds4(sm.wb.Db + j0 + 4, DB + 4);
+#pragma unroll
+            for (int e = 0; e < 5; ++e) {
+                const int j = j0 + e;
+                const float bf = 0.5f * (B[e] + B[e + 1]);
+                const float hbar = 0.5f * (H[e + 2] + H[e + 3]);
+                const float ptf = 0.5f * (PT[e] + PT[e + 1]);
+                float psi = fmaf(g * hbar, Z[e + 2], DE[e + 1] - DE[e]);
+                psi = fmaf(1.5f * ptf, DB[e + 2], psi);
+                psi = fmaf(-bf, DH[e + 2], psi);
+                float kf = __fmul_rn(Cc, bf);
+                if (BC == BC_TRANSMISSIVE && ((j == 0 && win.lend) || (j == W && win.rend))) {
+                    kf = 0.f;
+                    psi = 0.f;
+                }
+                KF[e] = kf;
+                PS[e] = psi;
             }
-            BF[pd(j)] = kf;
-            Psi[f + 3] = psi;
-        }
-        __syncthreads();
-        // d_i - (A h_b)_i = -tau/(2dx) (q^dag_{i+1} - q^dag_{i-1}) + tau^2/dx^2 (Psi_{i+1/2} - Psi_{i-1/2})
-        for (int i = tid; i < W; i += T) {
-            const float dqc = sm.Dq[i + 2] + sm.Dq[i + 3] + (dqa[i + 2] - dqa[i]);
-            RD[pd(i)] = fmaf(-fq, dqc, Cc * (Psi[i + 3] - Psi[i + 2]));
-        }
-    } else for (int j = tid; j < W + 1; j += T) {
-        const int f = j - 1;  // face between window rows f and f+1
-        float kf = Cc * (0.5f * (bea[f + 1] + bea[f + 2]));
-        if (BC == BC_TRANSMISSIVE && ((f < 0 && win.lend) || (f == W - 1 && win.rend))) kf = 0.f;
-        BF[pd(j)] = kf;
-        if (j < W) {
-            const int i = j;
-            const float bm = 0.5f * (bea[i] + bea[i + 1]);
-            const float bp = 0.5f * (bea[i + 1] + bea[i + 2]);
-            const float dmn = 0.5f * (dea[i] + dea[i + 1]);
-            const float dpl = 0.5f * (dea[i + 1] + dea[i + 2]);
-            const float dqc = sm.Dq[i + 2] + sm.Dq[i + 3] + (dqa[i + 2] - dqa[i]);
-            const float dmp = sm.Dm[i + 3] + (dma[i + 2] - dma[i + 1]);
-            const float dmm = sm.Dm[i + 2] + (dma[i + 1] - dma[i]);
-            RD[pd(i)] = -fq * dqc + fd * (dpl * dmp - dmn * dmm) -
-                        Cc * (bm * sm.Dh[i + 2] - bp * sm.Dh[i + 3]);
+            // d_i - (A h_b)_i = -tau/(2dx) (q^dag_{i+1} - q^dag_{i-1}) + tau^2/dx^2 (Psi_{i+1/2} - Psi_{i-1/2})
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const float dqc = DQ[k + 2] + DQ[k + 3] + (QA[k + 2] - QA[k]);
+                rd[k] = fmaf(-fq, dqc, Cc * (PS[k + 1] - PS[k]));
+            }
+        } else {
+            float DE[8], MA[8], DM[8];
+            lds4(dea + j0, DE); lds4(dea + j0 + 4, DE + 4);
+            lds4(dma + j0, MA); lds4(dma + j0 + 4, MA + 4);
+            lds4(sm.Dm + j0, DM); lds4(sm.Dm + j0 + 4, DM + 4);
+#pragma unroll
+            for (int e = 0; e < 5; ++e) {
+                const int j = j0 + e;
+                float kf = __fmul_rn(Cc, 0.5f * (B[e] + B[e + 1]));
+                if (BC == BC_TRANSMISSIVE && ((j == 0 && win.lend) || (j == W && win.rend))) kf = 0.f;
+                KF[e] = kf;
+            }
+            // Every product is rounded explicitly (fmaf / __fmul_rn): neighbouring
+            // rows share products (bp DH of row k is bm DH of row k + 1), and a
+            // shared product left to the compiler is not fused where a single-use
+            // one is, so a row's bits would depend on its position in the
+            // thread's four rows. The rows of a tile-face mini window must come
+            // out bitwise equal in the two windows that hold them.
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const float bm = 0.5f * (B[k] + B[k + 1]);
+                const float bp = 0.5f * (B[k + 1] + B[k + 2]);
+                const float dmn = 0.5f * (DE[k] + DE[k + 1]);
+                const float dpl = 0.5f * (DE[k + 1] + DE[k + 2]);
+                const float dqc = DQ[k + 2] + DQ[k + 3] + (QA[k + 2] - QA[k]);
+                const float dmp = DM[k + 3] + (MA[k + 2] - MA[k + 1]);
+                const float dmm = DM[k + 2] + (MA[k + 1] - MA[k]);
+                const float dd = fmaf(dpl, dmp, -__fmul_rn(dmn, dmm));
+                const float hd = fmaf(bm, DH[k + 2], -__fmul_rn(bp, DH[k + 3]));
+                rd[k] = fmaf(-fq, dqc, fmaf(fd, dd, -__fmul_rn(Cc, hd)));
+            }
         }
     }
     __syncthreads();
-    // row i of a window whose first / last row drops its outer coupling
-    auto row_at = [&](int i, bool cutL, bool cutR, float& a, float& bb, float& c, float& d) {
-        const float kl = BF[pd(i)], kr = BF[pd(i + 1)];
-        a = cutL ? 0.f : -kl;
-        c = cutR ? 0.f : -kr;
-        bb = 1.f + kl + kr;
-        d = RD[pd(i)];
-    };
+    // (the stores below overwrite arrays read above by the neighbouring threads)
+    if constexpr (WB) {
+#pragma unroll
+        for (int e = 0; e < 4; e += 2)
+            *reinterpret_cast<float2*>(Psi + j0 + e + 2) = make_float2(PS[e], PS[e + 1]);
+    }
     // tile-boundary mini solves (warps 1 and 2, while warp 0 solves the
     // separator system of the window)
     // (stage 2 only: stage 1 writes every face of G1 once, from the tile on
     // its left, and updates no depth)
     const bool lface = two && !(BC == BC_TRANSMISSIVE && win.t0 == 0);
     const bool rface = two && !(BC == BC_TRANSMISSIVE && win.t0 + win.sp == n);
+    if (two) {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            BF[pd(j0 + k)] = KF[k];
+            RD[pd(j0 + k)] = rd[k];
+        }
+    }
     auto mini = [&](int wid) {
         const int side = wid - 1;
         if (side < 0 || side > 1 || !(side == 0 ? lface : rface)) return;
@@ -644,12 +692,18 @@ __global__ void __launch_bounds__(T, (WB ? 768 : 1024) / T) k_mixed_fused(const 
         const MiniWindow mwn = mini_of<BC>(tf, n, Gm::HB);
         const int ms = (int)(mwn.ml - wl);                         // first mini row in the window
         const int mw = mwn.mw;
+        // mini row k (window row ms + k); its first / last row drops its outer coupling
         auto rowm = [&](int k, float& a, float& bb, float& c, float& d) {
             if (k >= mw) {
                 a = 0.f; bb = 1.f; c = 0.f; d = 0.f;
                 return;
             }
-            row_at(ms + k, k == 0 && !mwn.lend, k == mw - 1 && !mwn.rend, a, bb, c, d);
+            const int i = ms + k;
+            const float kl = BF[pd(i)], kr = BF[pd(i + 1)];
+            a = (k == 0 && !mwn.lend) ? 0.f : -kl;
+            c = (k == mw - 1 && !mwn.rend) ? 0.f : -kr;
+            bb = 1.f + kl + kr;
+            d = RD[pd(i)];
         };
         float y[Gm::MB], v[Gm::MB], w[Gm::MB], last[4];
         int cs, m;
@@ -665,16 +719,22 @@ __global__ void __launch_bounds__(T, (WB ? 768 : 1024) / T) k_mixed_fused(const 
     };
     float* const dha = sm.Dq;  // dh of window row r at pd(r + 1), r = -1 .. W
     {
-        auto roww = [&](int i, float& a, float& bb, float& c, float& d) {
-            if (i >= W) {  // identity row closing the window
+        // row 4t + k of the window; the first / last window row drops its outer
+        // coupling; the rows from W on close the window (identity)
+        auto roww = [&](int k, int i, float& a, float& bb, float& c, float& d) {
+            if (i >= W) {
                 a = 0.f; bb = 1.f; c = 0.f; d = 0.f;
                 return;
             }
-            row_at(i, i == 0 && !win.lend, i == W - 1 && !win.rend, a, bb, c, d);
+            const float kl = KF[k], kr = KF[k + 1];
+            a = (i == 0 && !win.lend) ? 0.f : -kl;
+            c = (i == W - 1 && !win.rend) ? 0.f : -kr;
+            bb = 1.f + kl + kr;
+            d = rd[k];
         };
         float y[M], v[M], w[M], last[4];
         int cs, m;
-        cta_block_solve<T, M>(W + 1, roww, sm.sep, y, v, w, cs, m, last, p.err, mini);
+        cta_block_solve_fixed<T, M>(W + 1, roww, sm.sep, y, v, w, cs, m, last, p.err, mini);
         // dh = y: the values outside the window (and the closing row) are taken as 0
 #pragma unroll
         for (int k = 0; k < M; ++k)
@@ -698,34 +758,55 @@ __global__ void __launch_bounds__(T, (WB ? 768 : 1024) / T) k_mixed_fused(const 
     }
     __syncthreads();
 
-    // ---- 4a. face mass fluxes (divided by dx) of the tile's faces f = lo-1 .. lo+sp-1,
-    //          each evaluated once; at a tile face both rows come from the shared
-    //          mini solve
+    // ---- 4a. face mass fluxes (divided by dx) of the tile's faces, each evaluated
+    //          once: thread t takes the window faces jf = 4t .. 4t + 3 (face jf
+    //          between rows jf - 1 and jf) that belong to the tile, jf = lo .. lo + sp;
+    //          at a tile face both rows come from the shared mini solve
     //   G = tau/(2dx) (q^dag_L + q^dag_R) - lambda tau^2/dx^2 delta_face (m^dag_R - m^dag_L)
     //       - tau^2/dx^2 beta_face (hbar_R - hbar_L)
     const int lo = win.lo, sp = win.sp;
-    float* const Gt = sm.rb;  // face f at f - lo + 1
-    for (int j = tid; j < sp + 1; j += T) {
-        const int f = lo - 1 + j;  // face between window cells f and f+1
-        float dL = dha[pd(f + 1)], dR = dha[pd(f + 2)];
-        if (j == 0 && lface) { dL = sm.bnd[0][0]; dR = sm.bnd[0][1]; }
-        if (j == sp && rface) { dL = sm.bnd[1][0]; dR = sm.bnd[1][1]; }
-        const float qsum = (sm.qb[f + 3] + sm.qb[f + 4]) + (dqa[f + 1] + dqa[f + 2]);
-        float G;
+    float* const Gt = sm.rb;  // face jf at jf - lo
+    if (j0 + 3 >= lo && j0 <= lo + sp) {
+        float QB[8], QA[8], B[8], DW[5];
+        lds4(sm.qb + j0, QB); lds4(sm.qb + j0 + 4, QB + 4);
+        lds4(dqa + j0, QA); lds4(dqa + j0 + 4, QA + 4);
+        lds4(bea + j0, B); lds4(bea + j0 + 4, B + 4);
+#pragma unroll
+        for (int e = 0; e < 5; ++e) DW[e] = dha[pd(j0 + e)];  // dh of row j0 + e - 1
+        float DE[WB ? 1 : 8], MA[WB ? 1 : 8], DM[WB ? 1 : 8], DH[WB ? 1 : 8], PV[WB ? 8 : 1];
         if constexpr (WB) {
-            // G = tau/(2dx) (q^dag_L + q^dag_R) - tau^2/dx^2 (Psi_f + beta_face (dh_R - dh_L))
-            G = fq * qsum - Cc * fmaf(0.5f * (bea[f + 1] + bea[f + 2]), dR - dL, Psi[f + 3]);
+            lds4(Psi + j0, PV); lds4(Psi + j0 + 4, PV + 4);
         } else {
-            const float dmf = sm.Dm[f + 3] + (dma[f + 2] - dma[f + 1]);
-            const float dhf = sm.Dh[f + 3] + (dR - dL);
-            G = fq * qsum - fd * (0.5f * (dea[f + 1] + dea[f + 2])) * dmf -
-                Cc * (0.5f * (bea[f + 1] + bea[f + 2])) * dhf;
+            lds4(dea + j0, DE); lds4(dea + j0 + 4, DE + 4);
+            lds4(dma + j0, MA); lds4(dma + j0 + 4, MA + 4);
+            lds4(sm.Dm + j0, DM); lds4(sm.Dm + j0 + 4, DM + 4);
+            lds4(sm.Dh + j0, DH); lds4(sm.Dh + j0 + 4, DH + 4);
         }
-        if (!isfinite(G)) bad |= HSGN_DEV_ERR_NONFINITE;
-        Gt[j] = G;
-        if (!two) {
-            const int64_t gf = win.t0 + j;  // G1 index of this face (face i+1/2 at i+1)
-            if (j > 0 || (BC == BC_TRANSMISSIVE && win.t0 == 0)) G1w[gf] = G;
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const int j = j0 + e - lo;  // tile face j = 0 .. sp
+            if (j >= 0 && j <= sp) {
+                float dL = DW[e], dR = DW[e + 1];
+                if (j == 0 && lface) { dL = sm.bnd[0][0]; dR = sm.bnd[0][1]; }
+                if (j == sp && rface) { dL = sm.bnd[1][0]; dR = sm.bnd[1][1]; }
+                const float qsum = (QB[e + 2] + QB[e + 3]) + (QA[e] + QA[e + 1]);
+                // (rounded explicitly: a tile face's flux is evaluated by both
+                // tiles beside it, at different positions among the four faces)
+                float G;
+                if constexpr (WB) {
+                    // G = tau/(2dx) (q^dag_L + q^dag_R) - tau^2/dx^2 (Psi_f + beta_face (dh_R - dh_L))
+                    G = fmaf(-Cc, fmaf(0.5f * (B[e] + B[e + 1]), dR - dL, PV[e + 2]),
+                             __fmul_rn(fq, qsum));
+                } else {
+                    const float dmf = DM[e + 2] + (MA[e + 1] - MA[e]);
+                    const float dhf = DH[e + 2] + (dR - dL);
+                    G = fmaf(-__fmul_rn(Cc, 0.5f * (B[e] + B[e + 1])), dhf,
+                             fmaf(-__fmul_rn(fd, 0.5f * (DE[e] + DE[e + 1])), dmf,
+                                  __fmul_rn(fq, qsum)));
+                }
+                if (!isfinite(G)) bad |= HSGN_DEV_ERR_NONFINITE;
+                Gt[j] = G;
+            }
         }
     }
     __syncthreads();
@@ -743,6 +824,11 @@ __global__ void __launch_bounds__(T, (WB ? 768 : 1024) / T) k_mixed_fused(const 
     float* const dq1t = dq1p + t0;
     float* const dm1t = dm1p + t0;
     float* const dr1t = dr1p + t0;
+    // stage 1 writes the tile's faces 1 .. sp of G1 here and face 0 only at a
+    // transmissive left domain end (face i+1/2 of cell i at i + 1; every other
+    // face 0 is the previous tile's face sp)
+    float* const G1wt = G1w + t0;
+    if (!two && BC == BC_TRANSMISSIVE && t0 == 0 && tid == 0) G1wt[0] = Gt[0];
     float2* const o0t = two ? p.out[0] + cell0 + t0 : nullptr;
     float2* const o1t = two ? p.out[1] + cell0 + t0 : nullptr;
     float2* const o2t = two ? p.out[2] + cell0 + t0 : nullptr;
@@ -800,6 +886,7 @@ __global__ void __launch_bounds__(T, (WB ? 768 : 1024) / T) k_mixed_fused(const 
             dq1t[t] = dQ;
             dm1t[t] = dM;
             dr1t[t] = dR;
+            G1wt[t + 1] = Gt[t + 1];
         } else {
             const float Tp = fmaf(wb1, g1r, Gt[t + 1]);
             const float Tm = fmaf(wb1, g1l, Gt[t]);

@@ -31,8 +31,8 @@ static_assert(XT * XM == AS, "both precision forms use the same block split");
 constexpr int OT = 256, OM = 16;
 // Windowed mixed stage: FT threads, FM rows per thread, FHW overlap rows.
 constexpr int FT = 256, FM = 4, FHW = 64;
-// Small variant of the windowed stage for batches (tiles of 383 rows instead of
-// 895), chosen per instance by hsgn_batched_set_tiles / hsgn_batched_autotune.
+// Small variant of the windowed stage for batches (tiles of 382 rows instead of
+// 894), chosen per instance by hsgn_batched_set_tiles / hsgn_batched_autotune.
 constexpr int FTS = 128;
 // Separator levels: one warp per block of GS rows; one warp solves up to RMAX rows.
 constexpr int GS = SEP_ROWS, RMAX = SEP_ROWS;

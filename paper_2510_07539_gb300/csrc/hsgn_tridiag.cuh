@@ -283,19 +283,29 @@ __device__ __forceinline__ void warp_block_solve(int nrows, RowFn row, Real (&y)
 
 
 // Eliminate a block of `nrows` rows (1 <= nrows <= T*M). All T threads of the
-// CTA must call it. `row(i, a, b, c, d)` returns local row i (0 <= i < nrows).
+// CTA must call it. `row(k, i, a, b, c, d)` returns local row i = cs + k
+// (0 <= i < nrows) of the calling thread's chunk. FIXED: thread t owns the
+// rows [M t, M t + M) (the rows in its registers; the last chunk may be
+// shorter, the threads past it none), k is a compile-time index; otherwise
+// the rows are split as evenly as possible (chunk_of).
 // On return thread t holds, for k < m, the triple (y, v, w) of row cs + k; the
 // block separator (row nrows - 1) gets (0, 0, -1). The thread that owns the
 // last row also returns its coefficients in last[0..3].
 // While warp 0 solves the separator system, every other warp w calls side(w).
-template <int T, int M, class RowFn, class Real, class Side = NoSide>
-__device__ __forceinline__ void cta_block_solve(int nrows, RowFn row, SepShared<T, Real>& sh,
-                                                Real (&y)[M], Real (&v)[M], Real (&w)[M],
-                                                int& cs, int& m, Real (&last)[4],
-                                                unsigned* err, Side side = Side()) {
+template <int T, int M, bool FIXED, class RowK, class Real, class Side>
+__device__ __forceinline__ void cta_block_solve_impl(int nrows, RowK row, SepShared<T, Real>& sh,
+                                                     Real (&y)[M], Real (&v)[M], Real (&w)[M],
+                                                     int& cs, int& m, Real (&last)[4],
+                                                     unsigned* err, Side side) {
     const int t = threadIdx.x;
     int teff;
-    chunk_of<T>(nrows, t, cs, m, teff);
+    if constexpr (FIXED) {
+        teff = (nrows + M - 1) / M;
+        cs = t < teff ? M * t : nrows;
+        m = t < teff ? min(M, nrows - M * t) : 0;
+    } else {
+        chunk_of<T>(nrows, t, cs, m, teff);
+    }
     const int nint = m - 1;  // interior rows of the chunk (the last row is its separator)
 
     // ---- 1. Thomas sweep of the chunk interior with three right-hand sides:
@@ -307,7 +317,7 @@ __device__ __forceinline__ void cta_block_solve(int nrows, RowFn row, SepShared<
     for (int k = 0; k < M; ++k) {
         if (k < nint) {
             Real a, b, c, d;
-            row(cs + k, a, b, c, d);
+            row(k, cs + k, a, b, c, d);
             Real p, ip;
             if (k == 0) {
                 p = b;
@@ -324,7 +334,13 @@ __device__ __forceinline__ void cta_block_solve(int nrows, RowFn row, SepShared<
             w[k] = c * ip;
         }
     }
-    if (m > 0) row(cs + m - 1, sa, sb, sc, sd);
+    if constexpr (FIXED) {
+#pragma unroll
+        for (int k = 0; k < M; ++k)
+            if (k == m - 1) row(k, cs + k, sa, sb, sc, sd);
+    } else if (m > 0) {
+        row(m - 1, cs + m - 1, sa, sb, sc, sd);
+    }
     // backward substitution: Y_k = g_k - c'_k Y_{k+1}, V likewise, W_k = -c'_k W_{k+1}.
     // The last interior values (YL, VL, WL) are kept in scalars; an empty
     // interior means the row before the separator is the previous separator.
@@ -450,5 +466,26 @@ __device__ __forceinline__ void cta_block_solve(int nrows, RowFn row, SepShared<
     }
 }
 
+
+// cta_block_solve_impl with rows split evenly; row(i, a, b, c, d) returns row i.
+template <int T, int M, class RowFn, class Real, class Side = NoSide>
+__device__ __forceinline__ void cta_block_solve(int nrows, RowFn row, SepShared<T, Real>& sh,
+                                                Real (&y)[M], Real (&v)[M], Real (&w)[M],
+                                                int& cs, int& m, Real (&last)[4],
+                                                unsigned* err, Side side = Side()) {
+    cta_block_solve_impl<T, M, false>(
+        nrows, [&](int, int i, Real& a, Real& b, Real& c, Real& d) { row(i, a, b, c, d); }, sh, y,
+        v, w, cs, m, last, err, side);
+}
+
+// cta_block_solve_impl with M rows per thread held in its registers:
+// row(k, i, a, b, c, d) returns the k-th row of the thread (row i = M t + k).
+template <int T, int M, class RowK, class Real, class Side = NoSide>
+__device__ __forceinline__ void cta_block_solve_fixed(int nrows, RowK row, SepShared<T, Real>& sh,
+                                                      Real (&y)[M], Real (&v)[M], Real (&w)[M],
+                                                      int& cs, int& m, Real (&last)[4],
+                                                      unsigned* err, Side side = Side()) {
+    cta_block_solve_impl<T, M, true>(nrows, row, sh, y, v, w, cs, m, last, err, side);
+}
 
 }  // namespace hsgn

@@ -722,11 +722,11 @@ def test_batched_workload_full_length_sampled():
 
 
 @pytest.mark.parametrize("bc", [0, 1])
-@pytest.mark.parametrize("n", [894, 895, 896, 1789, 1790, 1791, 2684, 2686, 8191, 65537])
+@pytest.mark.parametrize("n", [893, 894, 895, 1787, 1788, 1789, 2682, 2684, 8191, 65537])
 def test_windowed_sizes_around_tile_multiples(n, bc):
     # grids of one tile, one tile plus a cell, two tiles minus a cell ...: the
     # tile faces, ragged last tiles and the periodic seam at every position
-    # the tiling of 895-row tiles produces
+    # the tiling of 894-row tiles produces
     dx, lam = 0.1, 300.0
     U = inputs.random_state(6000 + n + bc, n, dx)
     p = oracle.Params(n, dx, bc, lam=lam)

@@ -7,7 +7,9 @@
 // cell index lies in [0, n), every shared-memory index within the arrays, that
 // tiles cover the grid once, that the rows kept from a window lie HW - 1 rows
 // or more inside it, and that the two tiles beside a face build the same
-// mini-window. Exit status 0 when every check passes.
+// mini-window, and that the four cells per thread of the cell, row and solve
+// phases cover the window within the arrays. Exit status 0 when every check
+// passes.
 #include <cstdio>
 #include <cstdlib>
 #include "../paper_2510_07539_gb300/csrc/hsgn_fused.cuh"
@@ -31,6 +33,9 @@ void check(int64_t n, int S) {
     using G = FusedGeom<T, M, HW>;
     int64_t p = -1;
     CHECK(S >= 1 && S <= G::S);
+    // cell, row and solve phases: thread t reads the cell arrays at 4t .. 4t + 7
+    // as two float4 (arrays 16-byte aligned) and writes the padded rows pd(4t + k)
+    CHECK(G::NC % 4 == 0 && 4 * T + 4 <= G::NC && pd(4 * T - 1) < G::NC);
     const int64_t P = (n + S - 1) / S;
     int64_t covered = 0;
     for (p = 0; p < P; ++p) {
@@ -40,6 +45,7 @@ void check(int64_t n, int S) {
         CHECK(w.t0 == covered);
         covered += w.sp;
         CHECK(w.W >= 1 && w.W + 1 <= T * M);  // rows of the block solve, closing row included
+        CHECK(w.W + 2 <= 4 * T);  // the cells c = -1 .. W, four per thread
         CHECK(w.lo >= 0 && w.lo + w.sp <= w.W);
         // load phase: j < W + 6, both cells in range on either path
         CHECK(w.W + 6 <= G::NC);
@@ -67,6 +73,8 @@ void check(int64_t n, int S) {
         if (!(BC == BC_TRANSMISSIVE && w.lend)) CHECK(w.lo >= HW);
         if (!(BC == BC_TRANSMISSIVE && w.rend)) CHECK(w.W - (w.lo + w.sp) >= HW);
         CHECK(pd(w.lo + w.sp + 1) < G::NC && w.lo + w.sp + 3 < G::NC);
+        // face fluxes: the threads with a tile face (4t <= lo + sp) read dh at pd(4t + 4)
+        CHECK(pd(w.lo + w.sp + 4) < G::NC);
         CHECK(w.t0 + w.sp <= n);
         // mini-windows of the tile faces
         const bool lface = !(BC == BC_TRANSMISSIVE && w.t0 == 0);
