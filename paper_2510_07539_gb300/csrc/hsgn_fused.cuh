@@ -235,7 +235,7 @@ __device__ __forceinline__ float rcpa(float x) { return rcp(x); }
 //   phase 3 (rows in registers): for the stage-2 mini solves the face couplings
 //            tau^2 beta_{f+1/2}/dx^2 -> rb and the right-hand sides -> mb
 //            (both padded: a lane of the mini solve reads rows at a stride);
-//   phase 4: dh -> Dq (padded); face mass fluxes of the tile -> rb.
+//   phase 4: dh -> Dq (window row r at r + 4); face mass fluxes of the tile -> rb.
 // The bottom form (WB) reuses Dh for the jump of h_l - h_b at the face, Dm for
 // P_l = h_l^2 - m_l and then beta (hl keeps h_l), ml for the non-gravity part
 // of the pressure, mb for p~, and adds the free-surface jump Z (which becomes
@@ -358,8 +358,10 @@ __global__ void __launch_bounds__(T, (WB ? 768 : 1024) / T) k_mixed_fused(const 
         sm.ml[j] = fmaf(wl1, dm1, mf);
         sm.rl[j] = fmaf(wl1, dr1, rf);
         sm.qb[j] = fmaf(wb1, dq1, qf);
-        sm.mb[j] = fmaf(wb1, dm1, mf);
-        sm.rb[j] = fmaf(wb1, dr1, rf);
+        if (two) {  // stage 1: U_b = U_l = U^n, read from ml, rl in the cell phase
+            sm.mb[j] = fmaf(wb1, dm1, mf);
+            sm.rb[j] = fmaf(wb1, dr1, rf);
+        }
         // differences of U^n at the face to the right: (hi1 - hi0) + (lo1 - lo0)
         const float Dhn = __fadd_rn(__fsub_rn(h1.x, h0.x), __fsub_rn(h1.y, h0.y));
         const float Dqn = __fadd_rn(__fsub_rn(q1.x, q0.x), __fsub_rn(q1.y, q0.y));
@@ -489,8 +491,16 @@ __global__ void __launch_bounds__(T, (WB ? 768 : 1024) / T) k_mixed_fused(const 
         // cells j at array index j + 2: rb, mb (and the bottom-form arrays) of
         // 4t + 2 .. 4t + 5 from two float4 each; hl, ml from the registers above
         float RB[8], MB[8];
-        lds4(sm.rb + j0, RB); lds4(sm.rb + j0 + 4, RB + 4);
-        lds4(sm.mb + j0, MB); lds4(sm.mb + j0 + 4, MB + 4);
+        if (two) {
+            lds4(sm.rb + j0, RB); lds4(sm.rb + j0 + 4, RB + 4);
+            lds4(sm.mb + j0, MB); lds4(sm.mb + j0 + 4, MB + 4);
+        } else {
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                RB[i] = Rv[i];
+                MB[i] = Mv[i];
+            }
+        }
         float SB[WB ? 8 : 1], PL[WB ? 8 : 1], MBL[WB ? 8 : 1];
         if constexpr (WB) {
             lds4(sm.wb.Sb + j0, SB); lds4(sm.wb.Sb + j0 + 4, SB + 4);
@@ -717,7 +727,7 @@ __global__ void __launch_bounds__(T, (WB ? 768 : 1024) / T) k_mixed_fused(const 
             }
         }
     };
-    float* const dha = sm.Dq;  // dh of window row r at pd(r + 1), r = -1 .. W
+    float* const dha = sm.Dq;  // dh of window row r at r + 4, r = -1 .. W (rows 4t.. as a float4)
     {
         // row 4t + k of the window; the first / last window row drops its outer
         // coupling; the rows from W on close the window (identity)
@@ -738,12 +748,13 @@ __global__ void __launch_bounds__(T, (WB ? 768 : 1024) / T) k_mixed_fused(const 
         // dh = y: the values outside the window (and the closing row) are taken as 0
 #pragma unroll
         for (int k = 0; k < M; ++k)
-            if (k < m && cs + k < W) dha[pd(cs + k + 1)] = y[k];
+            if (!(k < m && cs + k < W)) y[k] = 0.f;
+        sts4(dha + j0 + 4, y);
     }
     __syncthreads();
     if (BC == BC_TRANSMISSIVE && tid == 0) {
-        if (win.lend) dha[pd(0)] = dha[pd(1)];
-        if (win.rend) dha[pd(W + 1)] = dha[pd(W)];
+        if (win.lend) dha[3] = dha[4];
+        if (win.rend) dha[W + 4] = dha[W + 3];
     }
 
     // truncation bound of this window: rho*^HB <= 2^-30
@@ -765,14 +776,17 @@ __global__ void __launch_bounds__(T, (WB ? 768 : 1024) / T) k_mixed_fused(const 
     //   G = tau/(2dx) (q^dag_L + q^dag_R) - lambda tau^2/dx^2 delta_face (m^dag_R - m^dag_L)
     //       - tau^2/dx^2 beta_face (hbar_R - hbar_L)
     const int lo = win.lo, sp = win.sp;
-    float* const Gt = sm.rb;  // face jf at jf - lo
+    float* const Gt = sm.rb;   // face jf at jf - lo
+    float* const dQa = sm.mb;  // momentum increment of window row r at r
     if (j0 + 3 >= lo && j0 <= lo + sp) {
-        float QB[8], QA[8], B[8], DW[5];
+        float QB[8], QA[8], B[8];
         lds4(sm.qb + j0, QB); lds4(sm.qb + j0 + 4, QB + 4);
         lds4(dqa + j0, QA); lds4(dqa + j0 + 4, QA + 4);
         lds4(bea + j0, B); lds4(bea + j0 + 4, B + 4);
-#pragma unroll
-        for (int e = 0; e < 5; ++e) DW[e] = dha[pd(j0 + e)];  // dh of row j0 + e - 1
+        float DW[6];  // dh of the rows j0 - 1 .. j0 + 4
+        DW[0] = dha[j0 + 3];
+        lds4(dha + j0 + 4, DW + 1);
+        DW[5] = dha[j0 + 8];
         float DE[WB ? 1 : 8], MA[WB ? 1 : 8], DM[WB ? 1 : 8], DH[WB ? 1 : 8], PV[WB ? 8 : 1];
         if constexpr (WB) {
             lds4(Psi + j0, PV); lds4(Psi + j0 + 4, PV + 4);
@@ -808,11 +822,28 @@ __global__ void __launch_bounds__(T, (WB ? 768 : 1024) / T) k_mixed_fused(const 
                 Gt[j] = G;
             }
         }
+        // momentum increment of the rows 4t .. 4t + 3 (those of the tile are used)
+        float dq4[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const float dhL = DW[k], dhC = DW[k + 1], dhR = DW[k + 2];
+            if constexpr (WB) {
+                // q = q^dag - tau/(2dx) (F_{i+1/2} + F_{i-1/2}), F = Psi + beta_face (dh jump)
+                const float Fp = fmaf(0.5f * (B[k + 1] + B[k + 2]), dhR - dhC, PV[k + 3]);
+                const float Fl = fmaf(0.5f * (B[k] + B[k + 1]), dhC - dhL, PV[k + 2]);
+                dq4[k] = QA[k + 1] - fq * (Fp + Fl);
+            } else {
+                // q: tau/(2dx) beta (hbar_{i+1} - hbar_{i-1}), lambda tau/(2dx) delta (m^dag_{i+1} - m^dag_{i-1})
+                const float dhc = (DH[k + 2] + DH[k + 3]) + (dhR - dhL);  // faces r-1/2, r+1/2
+                const float dmc = (DM[k + 2] + DM[k + 3]) + (MA[k + 2] - MA[k]);
+                dq4[k] = QA[k + 1] - fq * B[k + 1] * dhc - lam * fq * DE[k + 1] * dmc;
+            }
+        }
+        sts4(dQa + j0, dq4);
     }
     __syncthreads();
 
     // ---- 4b. back-substitution of the tile rows
-    const float lamv = lam;
     float umax = 0.f;
     // the tile's cells and faces from its first cell: 32-bit offsets t
     const int64_t t0 = win.t0;
@@ -837,24 +868,7 @@ __global__ void __launch_bounds__(T, (WB ? 768 : 1024) / T) k_mixed_fused(const 
     const bool wrap0 = BC == BC_PERIODIC && t0 == 0;
     for (int t = tid; t < sp; t += T) {
         const int r = lo + t;            // window row
-        const float dhL = dha[pd(r)], dhC = dha[pd(r + 1)], dhR = dha[pd(r + 2)];
-        const float dqC = dqa[r + 1], dmC = dma[r + 1];
-        float dQ;
-        if constexpr (WB) {
-            // q = q^dag - tau/(2dx) (F_{i+1/2} + F_{i-1/2}), F = Psi + beta_face (dh jump)
-            const float Fp = fmaf(0.5f * (bea[r + 1] + bea[r + 2]), dhR - dhC, Psi[r + 3]);
-            const float Fl = fmaf(0.5f * (bea[r] + bea[r + 1]), dhC - dhL, Psi[r + 2]);
-            dQ = dqC - fq * (Fp + Fl);
-        } else {
-            const float dmL = dma[r], dmR = dma[r + 2];
-            const float beC = bea[r + 1], deC = dea[r + 1];
-            const float DhL = sm.Dh[r + 2], DhC = sm.Dh[r + 3];  // faces r-1/2, r+1/2
-            const float DmL = sm.Dm[r + 2], DmC = sm.Dm[r + 3];
-            // q: tau/(2dx) beta (hbar_{i+1} - hbar_{i-1}), lambda tau/(2dx) delta (m^dag_{i+1} - m^dag_{i-1})
-            const float dhc = (DhL + DhC) + (dhR - dhL);
-            const float dmc = (DmL + DmC) + (dmR - dmL);
-            dQ = dqC - fq * beC * dhc - lamv * fq * deC * dmc;
-        }
+        const float dhC = dha[r + 4], dmC = dma[r + 1], dQ = dQa[r];
         // base depth (rounded) and P0 = h_b^2 - m_b of this cell
         const float2 h0 = U0t[t], m0 = U2t[t];
         const float hf = h0.x;
@@ -896,7 +910,7 @@ __global__ void __launch_bounds__(T, (WB ? 768 : 1024) / T) k_mixed_fused(const 
             o1t[t] = df_add(U1t[t], fmaf(wb1, dq1t[t], dQ), 0.f);
             o2t[t] = df_add(m0, fmaf(wb1, dm1t[t], dM), 0.f);
             o3t[t] = df_add(U3t[t], fmaf(wb1, dr1t[t], dR), 0.f);
-            if (p.track_speed && !b2) umax = fmaxf(umax, fabsf((sm.qb[r + 3] + dQ) / hbar));
+            if (p.track_speed && !b2) umax = fmaxf(umax, fabsf(sm.qb[r + 3] + dQ) * rcpa(hbar));
         }
     }
     if (bad) flag_error(p.err, bad);

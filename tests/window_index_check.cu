@@ -34,8 +34,9 @@ void check(int64_t n, int S) {
     int64_t p = -1;
     CHECK(S >= 1 && S <= G::S);
     // cell, row and solve phases: thread t reads the cell arrays at 4t .. 4t + 7
-    // as two float4 (arrays 16-byte aligned) and writes the padded rows pd(4t + k)
-    CHECK(G::NC % 4 == 0 && 4 * T + 4 <= G::NC && pd(4 * T - 1) < G::NC);
+    // as two float4 (arrays 16-byte aligned), dh at 4t + 8, and writes the
+    // padded rows pd(4t + k)
+    CHECK(G::NC % 4 == 0 && 4 * T + 5 <= G::NC && pd(4 * T - 1) < G::NC);
     const int64_t P = (n + S - 1) / S;
     int64_t covered = 0;
     for (p = 0; p < P; ++p) {
@@ -73,8 +74,8 @@ void check(int64_t n, int S) {
         if (!(BC == BC_TRANSMISSIVE && w.lend)) CHECK(w.lo >= HW);
         if (!(BC == BC_TRANSMISSIVE && w.rend)) CHECK(w.W - (w.lo + w.sp) >= HW);
         CHECK(pd(w.lo + w.sp + 1) < G::NC && w.lo + w.sp + 3 < G::NC);
-        // face fluxes: the threads with a tile face (4t <= lo + sp) read dh at pd(4t + 4)
-        CHECK(pd(w.lo + w.sp + 4) < G::NC);
+        // dh of window row r at r + 4 (r = -1 .. W; thread t stores rows 4t .. 4t + 3)
+        CHECK(w.W + 4 < G::NC);
         CHECK(w.t0 + w.sp <= n);
         // mini-windows of the tile faces
         const bool lface = !(BC == BC_TRANSMISSIVE && w.t0 == 0);
