@@ -71,6 +71,15 @@ __device__ __forceinline__ float2 df_add(float2 a, float x, float y) {
     return make_float2(h, __fsub_rn(e, __fsub_rn(h, s)));
 }
 
+// (hi, lo) + x for one float x (df_add with y = 0).
+__device__ __forceinline__ float2 df_add1(float2 a, float x) {
+    float s, e;
+    two_sum(a.x, x, s, e);
+    e = __fadd_rn(e, a.y);
+    const float h = __fadd_rn(s, e);
+    return make_float2(h, __fsub_rn(e, __fsub_rn(h, s)));
+}
+
 // Pair of a double (state conversion, off the stepping path).
 __device__ __forceinline__ float2 df_of(double x) {
     const float hi = __double2float_rn(x);
@@ -458,7 +467,7 @@ __global__ void __launch_bounds__(T, (WB ? 768 : 1024) / T) k_mixed_fused(const 
     //           r^dag = r_b + dr' + lambda tau, m^dag = m_b + dm' + lambda tau^2,
     //           q^dag = q_b + dq. The results are stored after the barrier
     //           (they reuse the arrays the other threads still read).
-    const float lt2 = c_lt2, tdx = c_tdx, Cc = c_Cc;
+    const float lt2 = c_lt2, Cc = c_Cc, htdx = 0.5f * c_tdx;
     const int j0 = 4 * tid;
     float dq_[4], dm_[4], dr_[4], be_[4], de_[4];
     float pt_[WB ? 4 : 1];
@@ -484,9 +493,10 @@ __global__ void __launch_bounds__(T, (WB ? 768 : 1024) / T) k_mixed_fused(const 
             const float ip = rcpa(hL * hR);
             const float uL = qL * hR * ip, uR = qR * hL * ip;
             const float s = p.local_speed ? fmaxf(fabsf(uL), fabsf(uR)) : gspeed;
-            FQ[e] = 0.5f * (fmaf(uL, qL, uR * qR) - s * (qR - qL));
-            FM[e] = 0.5f * (fmaf(uL, mL, uR * mR) - s * (mR - mL));
-            FR[e] = 0.5f * (fmaf(uL, rL, uR * rR) - s * (rR - rL));
+            // twice the flux: the 1/2 is folded into htdx below (halving is exact)
+            FQ[e] = fmaf(uL, qL, uR * qR) - s * (qR - qL);
+            FM[e] = fmaf(uL, mL, uR * mR) - s * (mR - mL);
+            FR[e] = fmaf(uL, rL, uR * rR) - s * (rR - rL);
         }
         // cells j at array index j + 2: rb, mb (and the bottom-form arrays) of
         // 4t + 2 .. 4t + 5 from two float4 each; hl, ml from the registers above
@@ -512,11 +522,11 @@ __global__ void __launch_bounds__(T, (WB ? 768 : 1024) / T) k_mixed_fused(const 
             dq_[k] = dm_[k] = dr_[k] = be_[k] = de_[k] = 0.f;
             if constexpr (WB) pt_[k] = 0.f;
             if (j0 + k < W + 2) {
-                const float drv = -tdx * (FR[k + 1] - FR[k]);
-                float dmv = fmaf(tau, RB[k + 2] + drv, -tdx * (FM[k + 1] - FM[k]));
+                const float drv = -htdx * (FR[k + 1] - FR[k]);
+                float dmv = fmaf(tau, RB[k + 2] + drv, -htdx * (FM[k + 1] - FM[k]));
                 // bottom source of the (h eta) equation, -(3/2) h u b_x (Sec. 2.3, eq. (hSGNb_eq)), from U_l
                 if constexpr (WB) dmv = fmaf(-c_fq, SB[k + 2], dmv);
-                const float dqv = -tdx * (FQ[k + 1] - FQ[k]);
+                const float dqv = -htdx * (FQ[k + 1] - FQ[k]);
                 const float msv = MB[k + 2] + dmv + lt2;
                 const float h = H[k + 2];
                 if (!pos_finite(h)) bad |= HSGN_DEV_ERR_DEPTH;
@@ -576,19 +586,19 @@ __global__ void __launch_bounds__(T, (WB ? 768 : 1024) / T) k_mixed_fused(const 
         if (pos_finite(kmin)) atomicMin(&sm.kmin, __float_as_uint(kmin));
     }
     __syncthreads();
-    if (BC == BC_TRANSMISSIVE && tid == 0) {
+    if (BC == BC_TRANSMISSIVE && (win.lend || win.rend)) {  // (uniform over the CTA)
         // zero-order ghost copies at the domain ends
-        if (win.lend) {
+        if (tid == 0 && win.lend) {
             dqa[0] = dqa[1]; dma[0] = dma[1]; dra[0] = dra[1]; bea[0] = bea[1]; dea[0] = dea[1];
             if constexpr (WB) pta[0] = pta[1];
         }
-        if (win.rend) {
+        if (tid == 0 && win.rend) {
             const int a = W + 1, c = W;
             dqa[a] = dqa[c]; dma[a] = dma[c]; dra[a] = dra[c]; bea[a] = bea[c]; dea[a] = dea[c];
             if constexpr (WB) pta[a] = pta[c];
         }
+        __syncthreads();
     }
-    __syncthreads();
 
     // ---- 3. rows i = 4t .. 4t + 3 of A dh = d - A h_b, in the registers of
     //         thread t: face couplings k_j = tau^2/dx^2 beta at the faces j = 4t ..
@@ -599,7 +609,7 @@ __global__ void __launch_bounds__(T, (WB ? 768 : 1024) / T) k_mixed_fused(const 
     //         right-hand sides also go to shared memory for the tile-face mini
     //         solves of stage 2 (face j at pd(j), row i at pd(i)), the bottom
     //         form's face forces Psi for the face fluxes (face j at j + 2).
-    const float fq = c_fq, fd = c_fd;
+    const float fq = c_fq, hfd = 0.5f * c_fd, hCc = 0.5f * Cc;
     float* const BF = sm.rb;
     float* const RD = sm.mb;
     float* Psi = nullptr;  // face forces of the bottom form, face j at j + 2
@@ -650,28 +660,27 @@ __global__ void __launch_bounds__(T, (WB ? 768 : 1024) / T) k_mixed_fused(const 
 #pragma unroll
             for (int e = 0; e < 5; ++e) {
                 const int j = j0 + e;
-                float kf = __fmul_rn(Cc, 0.5f * (B[e] + B[e + 1]));
+                float kf = __fmul_rn(hCc, B[e] + B[e + 1]);
                 if (BC == BC_TRANSMISSIVE && ((j == 0 && win.lend) || (j == W && win.rend))) kf = 0.f;
                 KF[e] = kf;
             }
             // Every product is rounded explicitly (fmaf / __fmul_rn): neighbouring
-            // rows share products (bp DH of row k is bm DH of row k + 1), and a
-            // shared product left to the compiler is not fused where a single-use
-            // one is, so a row's bits would depend on its position in the
-            // thread's four rows. The rows of a tile-face mini window must come
-            // out bitwise equal in the two windows that hold them.
+            // rows share products (the right face of row k is the left face of
+            // row k + 1), and a shared product left to the compiler is not fused
+            // where a single-use one is, so a row's bits would depend on its
+            // position in the thread's four rows. The rows of a tile-face mini
+            // window must come out bitwise equal in the two windows that hold
+            // them. The face averages' 1/2 is folded into hfd and hCc.
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
-                const float bm = 0.5f * (B[k] + B[k + 1]);
-                const float bp = 0.5f * (B[k + 1] + B[k + 2]);
-                const float dmn = 0.5f * (DE[k] + DE[k + 1]);
-                const float dpl = 0.5f * (DE[k + 1] + DE[k + 2]);
+                const float bm = B[k] + B[k + 1], bp = B[k + 1] + B[k + 2];      // 2 beta_face
+                const float dmn = DE[k] + DE[k + 1], dpl = DE[k + 1] + DE[k + 2];  // 2 delta_face
                 const float dqc = DQ[k + 2] + DQ[k + 3] + (QA[k + 2] - QA[k]);
                 const float dmp = DM[k + 3] + (MA[k + 2] - MA[k + 1]);
                 const float dmm = DM[k + 2] + (MA[k + 1] - MA[k]);
                 const float dd = fmaf(dpl, dmp, -__fmul_rn(dmn, dmm));
                 const float hd = fmaf(bm, DH[k + 2], -__fmul_rn(bp, DH[k + 3]));
-                rd[k] = fmaf(-fq, dqc, fmaf(fd, dd, -__fmul_rn(Cc, hd)));
+                rd[k] = fmaf(-fq, dqc, fmaf(hfd, dd, -__fmul_rn(hCc, hd)));
             }
         }
     }
@@ -752,9 +761,10 @@ __global__ void __launch_bounds__(T, (WB ? 768 : 1024) / T) k_mixed_fused(const 
         sts4(dha + j0 + 4, y);
     }
     __syncthreads();
-    if (BC == BC_TRANSMISSIVE && tid == 0) {
-        if (win.lend) dha[3] = dha[4];
-        if (win.rend) dha[W + 4] = dha[W + 3];
+    if (BC == BC_TRANSMISSIVE && (win.lend || win.rend)) {  // (uniform over the CTA)
+        if (tid == 0 && win.lend) dha[3] = dha[4];
+        if (tid == 0 && win.rend) dha[W + 4] = dha[W + 3];
+        __syncthreads();
     }
 
     // truncation bound of this window: rho*^HB <= 2^-30
@@ -814,8 +824,8 @@ __global__ void __launch_bounds__(T, (WB ? 768 : 1024) / T) k_mixed_fused(const 
                 } else {
                     const float dmf = DM[e + 2] + (MA[e + 1] - MA[e]);
                     const float dhf = DH[e + 2] + (dR - dL);
-                    G = fmaf(-__fmul_rn(Cc, 0.5f * (B[e] + B[e + 1])), dhf,
-                             fmaf(-__fmul_rn(fd, 0.5f * (DE[e] + DE[e + 1])), dmf,
+                    G = fmaf(-__fmul_rn(hCc, B[e] + B[e + 1]), dhf,
+                             fmaf(-__fmul_rn(hfd, DE[e] + DE[e + 1]), dmf,
                                   __fmul_rn(fq, qsum)));
                 }
                 if (!isfinite(G)) bad |= HSGN_DEV_ERR_NONFINITE;
@@ -907,9 +917,9 @@ __global__ void __launch_bounds__(T, (WB ? 768 : 1024) / T) k_mixed_fused(const 
             float d, de;
             two_sum(Tm, -Tp, d, de);  // exact Tm - Tp
             o0t[t] = df_add(h0, d, de);
-            o1t[t] = df_add(U1t[t], fmaf(wb1, dq1t[t], dQ), 0.f);
-            o2t[t] = df_add(m0, fmaf(wb1, dm1t[t], dM), 0.f);
-            o3t[t] = df_add(U3t[t], fmaf(wb1, dr1t[t], dR), 0.f);
+            o1t[t] = df_add1(U1t[t], fmaf(wb1, dq1t[t], dQ));
+            o2t[t] = df_add1(m0, fmaf(wb1, dm1t[t], dM));
+            o3t[t] = df_add1(U3t[t], fmaf(wb1, dr1t[t], dR));
             if (p.track_speed && !b2) umax = fmaxf(umax, fabsf(sm.qb[r + 3] + dQ) * rcpa(hbar));
         }
     }
