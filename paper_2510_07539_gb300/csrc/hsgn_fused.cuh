@@ -281,8 +281,10 @@ struct FusedShared {
 // The free-surface jump comes from the double-float h and b, and p~ and
 // m^dag b_1 - m_l from P_l = h_l^2 - m_l of the pairs, so that a lake at rest
 // stays at rest to the pairs' precision rather than to single precision.
-template <int T, int M, int HW, int BC, bool WB = false>
+// STAGE (1 or 2, equal to p.stage) specialises the kernel for its stage.
+template <int T, int M, int HW, int BC, bool WB, int STAGE>
 __global__ void __launch_bounds__(T, (WB ? 768 : 1024) / T) k_mixed_fused(const FusedParams p) {
+    static_assert(STAGE == 1 || STAGE == 2, "two stages");
     using Gm = FusedGeom<T, M, HW>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     auto& sm = *reinterpret_cast<FusedShared<T, M, HW, WB>*>(smem_raw);
@@ -318,7 +320,7 @@ __global__ void __launch_bounds__(T, (WB ? 768 : 1024) / T) k_mixed_fused(const 
     const Window win = window_of<BC>(tile, n, S, HW);
     const int W = win.W;
     const int64_t wl = win.wl;
-    const bool two = p.stage == 2;
+    constexpr bool two = STAGE == 2;
     const float wl1 = p.wl1, wb1 = p.wb1;
     const float2* __restrict__ U0 = p.U[0] + cell0;
     const float2* __restrict__ U1 = p.U[1] + cell0;
@@ -335,7 +337,7 @@ __global__ void __launch_bounds__(T, (WB ? 768 : 1024) / T) k_mixed_fused(const 
         sm.kmax = 0u;
         sm.kmin = 0x7F7FFFFFu;
     }
-    if (p.track_speed && p.stage == 1 && tile == 0 && tid == 0) *spd_out = 0.0;
+    if (p.track_speed && !two && tile == 0 && tid == 0) *spd_out = 0.0;
 
     // ---- 0. window cells -3 .. W+2 (index c + 3)
     constexpr int NL = (Gm::R + 6 + T - 1) / T;
@@ -350,7 +352,7 @@ __global__ void __launch_bounds__(T, (WB ? 768 : 1024) / T) k_mixed_fused(const 
         const float2 m0 = at.u(U2, 0), rr0 = at.u(U3, 0);
         const float2 h1 = at.u(U0, 1), q1 = at.u(U1, 1), m1 = at.u(U2, 1);
         float dh1 = 0.f, dq1 = 0.f, dm1 = 0.f, dr1 = 0.f, dh1n = 0.f, dq1n = 0.f, dm1n = 0.f;
-        if (two) {
+        if constexpr (two) {
             const float g0 = at.face_left(G1, 0), g1 = at.face_right(G1, 0);
             const float g2 = at.face_left(G1, 1), g3 = at.face_right(G1, 1);
             dq1 = at.f(dq1p, 0);
@@ -367,7 +369,7 @@ __global__ void __launch_bounds__(T, (WB ? 768 : 1024) / T) k_mixed_fused(const 
         sm.ml[j] = fmaf(wl1, dm1, mf);
         sm.rl[j] = fmaf(wl1, dr1, rf);
         sm.qb[j] = fmaf(wb1, dq1, qf);
-        if (two) {  // stage 1: U_b = U_l = U^n, read from ml, rl in the cell phase
+        if constexpr (two) {  // stage 1: U_b = U_l = U^n, read from ml, rl in the cell phase
             sm.mb[j] = fmaf(wb1, dm1, mf);
             sm.rb[j] = fmaf(wb1, dr1, rf);
         }
@@ -501,7 +503,7 @@ __global__ void __launch_bounds__(T, (WB ? 768 : 1024) / T) k_mixed_fused(const 
         // cells j at array index j + 2: rb, mb (and the bottom-form arrays) of
         // 4t + 2 .. 4t + 5 from two float4 each; hl, ml from the registers above
         float RB[8], MB[8];
-        if (two) {
+        if constexpr (two) {
             lds4(sm.rb + j0, RB); lds4(sm.rb + j0 + 4, RB + 4);
             lds4(sm.mb + j0, MB); lds4(sm.mb + j0 + 4, MB + 4);
         } else {
@@ -888,7 +890,7 @@ __global__ void __launch_bounds__(T, (WB ? 768 : 1024) / T) k_mixed_fused(const 
         float hbf = hf;
         float P0 = __fadd_rn(__fsub_rn(pp, m0.x), fmaf(2.f * hf, h0.y, __fsub_rn(pe, m0.y)));
         float g1l = 0.f, g1r = 0.f;
-        if (two) {
+        if constexpr (two) {
             g1l = (wrap0 && t == 0) ? G1[n] : G1t[t];
             g1r = G1t[t + 1];
             const float dh1 = g1l - g1r, dm1 = dm1t[t];

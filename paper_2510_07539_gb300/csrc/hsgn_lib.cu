@@ -419,6 +419,25 @@ cudaError_t launch_stage_mixed(hsgn_s* H, int stage, double tau, cudaStream_t st
     return cudaGetLastError();
 }
 
+// One launch of the windowed stage kernel specialised for p.stage.
+template <int T, int BC, bool WB>
+void launch_fused(unsigned P, const FusedParams& p, cudaStream_t st) {
+    const size_t smem = sizeof(FusedShared<T, FM, FHW, WB>);
+    if (p.stage == 2)
+        k_mixed_fused<T, FM, FHW, BC, WB, 2><<<P, T, smem, st>>>(p);
+    else
+        k_mixed_fused<T, FM, FHW, BC, WB, 1><<<P, T, smem, st>>>(p);
+}
+
+// Dynamic shared-memory limit of both stage kernels of one variant.
+template <int T, int BC, bool WB>
+cudaError_t set_smem_fused() {
+    const size_t smem = sizeof(FusedShared<T, FM, FHW, WB>);
+    cudaError_t e = set_smem(k_mixed_fused<T, FM, FHW, BC, WB, 1>, smem);
+    if (e == cudaSuccess) e = set_smem(k_mixed_fused<T, FM, FHW, BC, WB, 2>, smem);
+    return e;
+}
+
 // One stage of the windowed mixed path (hsgn_fused.cuh): one launch. Stage 1
 // writes the FP32 increments, stage 2 writes U^{n+1} into the other buffer.
 cudaError_t launch_stage_fused(hsgn_s* H, int stage, double tau, cudaStream_t st) {
@@ -467,27 +486,24 @@ cudaError_t launch_stage_fused(hsgn_s* H, int stage, double tau, cudaStream_t st
             // instances on the small variant: a launch of their own over their tiles
             FusedParams ps_ = p;
             ps_.tile_inst = H->tile_inst_small;
-            const size_t smem = sizeof(FusedShared<FTS, FM, FHW>);
             const unsigned Ps = (unsigned)H->tiles_small;
             if (H->bc == BC_PERIODIC)
-                k_mixed_fused<FTS, FM, FHW, BC_PERIODIC><<<Ps, FTS, smem, st>>>(ps_);
+                launch_fused<FTS, BC_PERIODIC, false>(Ps, ps_, st);
             else
-                k_mixed_fused<FTS, FM, FHW, BC_TRANSMISSIVE><<<Ps, FTS, smem, st>>>(ps_);
+                launch_fused<FTS, BC_TRANSMISSIVE, false>(Ps, ps_, st);
         }
         if (P == 0) {
             // every instance of the batch runs on the small variant
         } else if (H->wb) {
-            const size_t smem = sizeof(FusedShared<FT, FM, FHW, true>);
             if (H->bc == BC_PERIODIC)
-                k_mixed_fused<FT, FM, FHW, BC_PERIODIC, true><<<P, FT, smem, st>>>(p);
+                launch_fused<FT, BC_PERIODIC, true>(P, p, st);
             else
-                k_mixed_fused<FT, FM, FHW, BC_TRANSMISSIVE, true><<<P, FT, smem, st>>>(p);
+                launch_fused<FT, BC_TRANSMISSIVE, true>(P, p, st);
         } else {
-            const size_t smem = sizeof(FusedShared<FT, FM, FHW>);
             if (H->bc == BC_PERIODIC)
-                k_mixed_fused<FT, FM, FHW, BC_PERIODIC><<<P, FT, smem, st>>>(p);
+                launch_fused<FT, BC_PERIODIC, false>(P, p, st);
             else
-                k_mixed_fused<FT, FM, FHW, BC_TRANSMISSIVE><<<P, FT, smem, st>>>(p);
+                launch_fused<FT, BC_TRANSMISSIVE, false>(P, p, st);
         }
     }
     return cudaGetLastError();
@@ -889,25 +905,19 @@ int hsgn_create(const hsgn_grid_t* grid, double g, double lambda, const double* 
 
     cudaError_t e = cudaMemset(H->mem, 0, total);
     if (e == cudaSuccess && H->windowed) {
-        e = set_smem(k_mixed_fused<FT, FM, FHW, BC_PERIODIC>, sizeof(FusedShared<FT, FM, FHW>));
-        if (e == cudaSuccess)
-            e = set_smem(k_mixed_fused<FT, FM, FHW, BC_TRANSMISSIVE>,
-                         sizeof(FusedShared<FT, FM, FHW>));
-        if (e == cudaSuccess)
-            e = set_smem(k_mixed_fused<FT, FM, FHW, BC_PERIODIC, true>,
-                         sizeof(FusedShared<FT, FM, FHW, true>));
-        if (e == cudaSuccess)
-            e = set_smem(k_mixed_fused<FT, FM, FHW, BC_TRANSMISSIVE, true>,
-                         sizeof(FusedShared<FT, FM, FHW, true>));
+        e = set_smem_fused<FT, BC_PERIODIC, false>();
+        if (e == cudaSuccess) e = set_smem_fused<FT, BC_TRANSMISSIVE, false>();
+        if (e == cudaSuccess) e = set_smem_fused<FT, BC_PERIODIC, true>();
+        if (e == cudaSuccess) e = set_smem_fused<FT, BC_TRANSMISSIVE, true>();
         int sms = 0, per_sm = 0;
         if (e == cudaSuccess)
             e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, H->device);
         if (e == cudaSuccess)
             e = H->wb ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-                            &per_sm, k_mixed_fused<FT, FM, FHW, BC_PERIODIC, true>, FT,
+                            &per_sm, k_mixed_fused<FT, FM, FHW, BC_PERIODIC, true, 2>, FT,
                             sizeof(FusedShared<FT, FM, FHW, true>))
                       : cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-                            &per_sm, k_mixed_fused<FT, FM, FHW, BC_PERIODIC>, FT,
+                            &per_sm, k_mixed_fused<FT, FM, FHW, BC_PERIODIC, false, 2>, FT,
                             sizeof(FusedShared<FT, FM, FHW>));
         const int64_t slots = (int64_t)(sms > 0 ? sms : 1) * (per_sm > 0 ? per_sm : 1);
         H->tileS = (int32_t)fused_tile_rows(n, FusedGeom<FT, FM, FHW>::S, slots);
@@ -1648,13 +1658,10 @@ int hsgn_create_batched(int32_t count, const int64_t* n, const double* x_left,
     if (e == cudaSuccess)
         e = set_smem(k_mixed_assemble<XT, XM, BC_TRANSMISSIVE>, sizeof(MixedShared<XT, XM>));
     if (e == cudaSuccess)
-        e = set_smem(k_mixed_fused<FT, FM, FHW, BC_PERIODIC>, sizeof(FusedShared<FT, FM, FHW>));
-    if (e == cudaSuccess)
-        e = set_smem(k_mixed_fused<FT, FM, FHW, BC_TRANSMISSIVE>, sizeof(FusedShared<FT, FM, FHW>));
-    if (e == cudaSuccess)
-        e = set_smem(k_mixed_fused<FTS, FM, FHW, BC_PERIODIC>, sizeof(FusedShared<FTS, FM, FHW>));
-    if (e == cudaSuccess)
-        e = set_smem(k_mixed_fused<FTS, FM, FHW, BC_TRANSMISSIVE>, sizeof(FusedShared<FTS, FM, FHW>));
+        e = set_smem_fused<FT, BC_PERIODIC, false>();
+    if (e == cudaSuccess) e = set_smem_fused<FT, BC_TRANSMISSIVE, false>();
+    if (e == cudaSuccess) e = set_smem_fused<FTS, BC_PERIODIC, false>();
+    if (e == cudaSuccess) e = set_smem_fused<FTS, BC_TRANSMISSIVE, false>();
     if (e == cudaSuccess && windowed) e = assign_tiles(H, std::vector<int8_t>((size_t)count, 0));
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&H->cap, cudaStreamNonBlocking);
     if (e != cudaSuccess) {
