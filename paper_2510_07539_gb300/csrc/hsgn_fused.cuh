@@ -80,6 +80,11 @@ __device__ __forceinline__ float2 df_add1(float2 a, float x) {
     return make_float2(h, __fsub_rn(e, __fsub_rn(h, s)));
 }
 
+// Hint: bring the 128-byte line holding *a into L2 (a must point into an allocation).
+__device__ __forceinline__ void prefetch_l2(const void* a) {
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(a));
+}
+
 // Pair of a double (state conversion, off the stepping path).
 __device__ __forceinline__ float2 df_of(double x) {
     const float hi = __double2float_rn(x);
@@ -92,6 +97,7 @@ struct FusedParams {
     int32_t local_speed;
     int32_t track_speed;  // stage 1 clears *speed_next, stage 2 folds max |u| into it
     int32_t S;            // tile rows (<= the kernel's capacity)
+    int32_t slots;        // co-resident CTAs (single instance; 0: no prefetch of the next wave)
     float g, lam, tau, tdx, fq, Cc, fd, lt2, ltau, wl1, wb1;
     const float2* U[4];             // U^n (double-float pairs)
     float *G1, *dq1, *dm1, *dr1;    // stage-1 increments; G1 has n+1 faces (face i+1/2 at i+1)
@@ -451,6 +457,35 @@ __global__ void __launch_bounds__(T, (WB ? 768 : 1024) / T) k_mixed_fused(const 
                 load_cells<BC>(false, wl, j, n, gi, gn);
                 const int64_t gp = cell_at<BC>(wl - 4 + j, n);
                 load_cell(j, General{gi, gn, gp, n});
+            }
+        }
+    }
+    // L2 prefetch of the tile that the next wave of CTAs starts on this slot
+    // (tile blockIdx.x + slots: CTAs are dispatched in index order as slots
+    // free up): one 128-byte line per thread and array over the cells of its
+    // window that lie in [0, n)
+    if (p.slots > 0) {
+        const int64_t ts = (int64_t)blockIdx.x + p.slots;
+        if (ts * (int64_t)S < n) {
+            const Window ws = window_of<BC>(ts, n, S, HW);
+            const int64_t c0 = ws.wl - 3 < 0 ? 0 : ws.wl - 3;
+            const int64_t c1 = ws.wl + ws.W + 3 > n ? n : ws.wl + ws.W + 3;
+            const int64_t c = c0 + 16 * (int64_t)tid;  // 16 pairs per line
+            if (c < c1) {
+                prefetch_l2(U0 + c);
+                prefetch_l2(U1 + c);
+                prefetch_l2(U2 + c);
+                prefetch_l2(U3 + c);
+                if constexpr (WB) prefetch_l2(p.bathy + cell0 + c);
+            }
+            if constexpr (two) {
+                const int64_t f = c0 + 32 * (int64_t)tid;  // 32 floats per line
+                if (f < c1) {
+                    prefetch_l2(G1 + f);
+                    prefetch_l2(dq1p + f);
+                    prefetch_l2(dm1p + f);
+                    prefetch_l2(dr1p + f);
+                }
             }
         }
     }

@@ -157,6 +157,7 @@ struct hsgn_s {
     // stage; U^{n+1} goes to the other of the two state buffers U, V
     bool windowed = false;
     int32_t tileS = 0;               // tile rows per CTA
+    int32_t tileSlots = 0;           // co-resident CTAs of the windowed kernel
     double* V[4] = {};
     int cur = 0;                     // 1: the state is in V
     // mixed precision (HSGN_MIXED): FP32 stage-1 increments and per-row results
@@ -449,6 +450,7 @@ cudaError_t launch_stage_fused(hsgn_s* H, int stage, double tau, cudaStream_t st
     p.local_speed = local_speed(H) ? 1 : 0;
     p.track_speed = local_speed(H) ? 0 : 1;
     p.S = H->tileS;
+    p.slots = H->batched ? 0 : H->tileSlots;
     const double dx = H->dx, lam = H->lam;
     p.g = (float)H->g;
     p.lam = (float)lam;
@@ -921,6 +923,7 @@ int hsgn_create(const hsgn_grid_t* grid, double g, double lambda, const double* 
                             sizeof(FusedShared<FT, FM, FHW>));
         const int64_t slots = (int64_t)(sms > 0 ? sms : 1) * (per_sm > 0 ? per_sm : 1);
         H->tileS = (int32_t)fused_tile_rows(n, FusedGeom<FT, FM, FHW>::S, slots);
+        H->tileSlots = (int32_t)slots;
     }
     // the bottom: host or device memory, copied once (cudaMemcpyDefault infers which);
     // the windowed form keeps it as double-float pairs, converted through V[0]
