@@ -369,12 +369,17 @@ __global__ void __launch_bounds__(T, (WB ? 768 : 1024) / T) k_mixed_fused(const 
             dh1 = g0 - g1;
             dh1n = g2 - g3;
         }
+        // x + w d with the stage-1 increments (stage 1 has none: x itself)
+        auto inc = [](float w, float d, float x) {
+            if constexpr (two) return fmaf(w, d, x);
+            else return x;
+        };
         const float hf = h0.x, qf = q0.x, mf = m0.x, rf = rr0.x;
-        sm.hl[j] = fmaf(wl1, dh1, hf);
-        sm.ql[j] = fmaf(wl1, dq1, qf);
-        sm.ml[j] = fmaf(wl1, dm1, mf);
-        sm.rl[j] = fmaf(wl1, dr1, rf);
-        sm.qb[j] = fmaf(wb1, dq1, qf);
+        sm.hl[j] = inc(wl1, dh1, hf);
+        sm.ql[j] = inc(wl1, dq1, qf);
+        sm.ml[j] = inc(wl1, dm1, mf);
+        sm.rl[j] = inc(wl1, dr1, rf);
+        sm.qb[j] = inc(wb1, dq1, qf);
         if constexpr (two) {  // stage 1: U_b = U_l = U^n, read from ml, rl in the cell phase
             sm.mb[j] = fmaf(wb1, dm1, mf);
             sm.rb[j] = fmaf(wb1, dr1, rf);
@@ -382,11 +387,11 @@ __global__ void __launch_bounds__(T, (WB ? 768 : 1024) / T) k_mixed_fused(const 
         // differences of U^n at the face to the right: (hi1 - hi0) + (lo1 - lo0)
         const float Dhn = __fadd_rn(__fsub_rn(h1.x, h0.x), __fsub_rn(h1.y, h0.y));
         const float Dqn = __fadd_rn(__fsub_rn(q1.x, q0.x), __fsub_rn(q1.y, q0.y));
-        sm.Dq[j] = fmaf(wb1, dq1n - dq1, Dqn);
+        sm.Dq[j] = inc(wb1, dq1n - dq1, Dqn);
         if constexpr (!WB) {
             const float Dmn = __fadd_rn(__fsub_rn(m1.x, m0.x), __fsub_rn(m1.y, m0.y));
-            sm.Dh[j] = fmaf(wb1, dh1n - dh1, Dhn);
-            sm.Dm[j] = fmaf(wb1, dm1n - dm1, Dmn);
+            sm.Dh[j] = inc(wb1, dh1n - dh1, Dhn);
+            sm.Dm[j] = inc(wb1, dm1n - dm1, Dmn);
         } else {
             const float2 b0 = at.u(p.bathy + cell0, 0), b1 = at.u(p.bathy + cell0, 1);
             // free-surface jump (h_l + b) at the face right of the cell:
@@ -395,20 +400,20 @@ __global__ void __launch_bounds__(T, (WB ? 768 : 1024) / T) k_mixed_fused(const 
             two_sum(b1.x, -b0.x, sb, eb);
             const float lo = __fadd_rn(__fadd_rn(__fsub_rn(h1.y, h0.y), __fsub_rn(b1.y, b0.y)), eb);
             const float hz = __fadd_rn(__fsub_rn(h1.x, h0.x), sb);
-            sm.wb.Z[j] = fmaf(wl1, dh1n - dh1, __fadd_rn(hz, lo));
+            sm.wb.Z[j] = inc(wl1, dh1n - dh1, __fadd_rn(hz, lo));
             sm.wb.Db[j] = __fadd_rn(sb, __fadd_rn(__fsub_rn(b1.y, b0.y), eb));
-            sm.Dh[j] = (wl1 - wb1) * (dh1n - dh1);  // (h_l - h_b) jump
+            sm.Dh[j] = two ? (wl1 - wb1) * (dh1n - dh1) : 0.f;  // (h_l - h_b) jump
             // P_l = h_l^2 - m_l: hi^2 = pp + pe exactly, pp - m.hi exact for m close to h^2
             const float pp = __fmul_rn(hf, hf);
             const float pe = fmaf(hf, hf, -pp);
             const float P0 = __fadd_rn(__fsub_rn(pp, m0.x), fmaf(2.f * hf, h0.y, __fsub_rn(pe, m0.y)));
-            sm.Dm[j] = fmaf(wl1, fmaf(dh1, fmaf(wl1, dh1, 2.f * hf), -dm1), P0);
+            sm.Dm[j] = inc(wl1, fmaf(dh1, fmaf(wl1, dh1, 2.f * hf), -dm1), P0);
             // (3/2) q_l (b_{c+1} - b_{c-1}) of the cells c = -1 .. W whose m^dag is formed
             float src = 0.f;
             if (j >= 2 && j <= W + 3)
-                src = 1.5f * fmaf(wl1, dq1, qf) * (b1.x - at.u(p.bathy + cell0, -1).x);
+                src = 1.5f * inc(wl1, dq1, qf) * (b1.x - at.u(p.bathy + cell0, -1).x);
             sm.wb.Sb[j] = src;
-            sm.wb.Mbl[j] = (wb1 - wl1) * dm1;
+            sm.wb.Mbl[j] = two ? (wb1 - wl1) * dm1 : 0.f;
         }
     };
     if (inner) {
@@ -463,8 +468,9 @@ __global__ void __launch_bounds__(T, (WB ? 768 : 1024) / T) k_mixed_fused(const 
     // L2 prefetch of the tile that the next wave of CTAs starts on this slot
     // (tile blockIdx.x + slots: CTAs are dispatched in index order as slots
     // free up): one 128-byte line per thread and array over the cells of its
-    // window that lie in [0, n)
-    if (p.slots > 0) {
+    // window that lie in [0, n); PF threads cover the widest window
+    constexpr int PF = (Gm::R + 6 + 15) / 16;
+    if (p.slots > 0 && tid < PF) {
         const int64_t ts = (int64_t)blockIdx.x + p.slots;
         if (ts * (int64_t)S < n) {
             const Window ws = window_of<BC>(ts, n, S, HW);
