@@ -97,7 +97,7 @@ struct FusedParams {
     int32_t local_speed;
     int32_t track_speed;  // stage 1 clears *speed_next, stage 2 folds max |u| into it
     int32_t S;            // tile rows (<= the kernel's capacity)
-    int32_t slots;        // co-resident CTAs (single instance; 0: no prefetch of the next wave)
+    int32_t slots;        // co-resident CTAs of this launch (0: no prefetch of the next wave)
     float g, lam, tau, tdx, fq, Cc, fd, lt2, ltau, wl1, wb1;
     const float2* U[4];             // U^n (double-float pairs)
     float *G1, *dq1, *dm1, *dr1;    // stage-1 increments; G1 has n+1 faces (face i+1/2 at i+1)
@@ -466,31 +466,41 @@ __global__ void __launch_bounds__(T, (WB ? 768 : 1024) / T) k_mixed_fused(const 
         }
     }
     // L2 prefetch of the tile that the next wave of CTAs starts on this slot
-    // (tile blockIdx.x + slots: CTAs are dispatched in index order as slots
-    // free up): one 128-byte line per thread and array over the cells of its
-    // window that lie in [0, n); PF threads cover the widest window
+    // (tile blockIdx.x + slots of this launch: CTAs are dispatched in index
+    // order as slots free up; in a batch it may belong to another instance):
+    // one 128-byte line per thread and array over the cells of its window that
+    // lie in [0, n) of its instance; PF threads cover the widest window
     constexpr int PF = (Gm::R + 6 + 15) / 16;
     if (p.slots > 0 && tid < PF) {
         const int64_t ts = (int64_t)blockIdx.x + p.slots;
-        if (ts * (int64_t)S < n) {
-            const Window ws = window_of<BC>(ts, n, S, HW);
+        if (ts < (int64_t)gridDim.x) {
+            int64_t sn = p.n, sc = 0, sf = 0, st = ts;
+            int sS = p.S;
+            if (p.batched) {
+                const int k = p.tile_inst[ts];
+                const InstInfo& I = p.inst[k];
+                sn = I.n;
+                sS = (int)I.base;
+                st = ts - I.blk0;
+                sc = I.cell0;
+                sf = I.cell0 + k;
+            }
+            const Window ws = window_of<BC>(st, sn, sS, HW);
             const int64_t c0 = ws.wl - 3 < 0 ? 0 : ws.wl - 3;
-            const int64_t c1 = ws.wl + ws.W + 3 > n ? n : ws.wl + ws.W + 3;
+            const int64_t c1 = ws.wl + ws.W + 3 > sn ? sn : ws.wl + ws.W + 3;
             const int64_t c = c0 + 16 * (int64_t)tid;  // 16 pairs per line
             if (c < c1) {
-                prefetch_l2(U0 + c);
-                prefetch_l2(U1 + c);
-                prefetch_l2(U2 + c);
-                prefetch_l2(U3 + c);
-                if constexpr (WB) prefetch_l2(p.bathy + cell0 + c);
+#pragma unroll
+                for (int v = 0; v < 4; ++v) prefetch_l2(p.U[v] + sc + c);
+                if constexpr (WB) prefetch_l2(p.bathy + sc + c);
             }
             if constexpr (two) {
                 const int64_t f = c0 + 32 * (int64_t)tid;  // 32 floats per line
                 if (f < c1) {
-                    prefetch_l2(G1 + f);
-                    prefetch_l2(dq1p + f);
-                    prefetch_l2(dm1p + f);
-                    prefetch_l2(dr1p + f);
+                    prefetch_l2(p.G1 + sf + f);
+                    prefetch_l2(p.dq1 + sc + f);
+                    prefetch_l2(p.dm1 + sc + f);
+                    prefetch_l2(p.dr1 + sc + f);
                 }
             }
         }

@@ -158,6 +158,7 @@ struct hsgn_s {
     bool windowed = false;
     int32_t tileS = 0;               // tile rows per CTA
     int32_t tileSlots = 0;           // co-resident CTAs of the windowed kernel
+    int32_t tileSlotsSmall = 0;      // the same for the small variant (batches)
     double* V[4] = {};
     int cur = 0;                     // 1: the state is in V
     // mixed precision (HSGN_MIXED): FP32 stage-1 increments and per-row results
@@ -450,7 +451,7 @@ cudaError_t launch_stage_fused(hsgn_s* H, int stage, double tau, cudaStream_t st
     p.local_speed = local_speed(H) ? 1 : 0;
     p.track_speed = local_speed(H) ? 0 : 1;
     p.S = H->tileS;
-    p.slots = H->batched ? 0 : H->tileSlots;
+    p.slots = H->tileSlots;
     const double dx = H->dx, lam = H->lam;
     p.g = (float)H->g;
     p.lam = (float)lam;
@@ -488,6 +489,7 @@ cudaError_t launch_stage_fused(hsgn_s* H, int stage, double tau, cudaStream_t st
             // instances on the small variant: a launch of their own over their tiles
             FusedParams ps_ = p;
             ps_.tile_inst = H->tile_inst_small;
+            ps_.slots = H->tileSlotsSmall;
             const unsigned Ps = (unsigned)H->tiles_small;
             if (H->bc == BC_PERIODIC)
                 launch_fused<FTS, BC_PERIODIC, false>(Ps, ps_, st);
@@ -1665,6 +1667,21 @@ int hsgn_create_batched(int32_t count, const int64_t* n, const double* x_left,
     if (e == cudaSuccess) e = set_smem_fused<FT, BC_TRANSMISSIVE, false>();
     if (e == cudaSuccess) e = set_smem_fused<FTS, BC_PERIODIC, false>();
     if (e == cudaSuccess) e = set_smem_fused<FTS, BC_TRANSMISSIVE, false>();
+    if (e == cudaSuccess && windowed) {
+        // co-resident CTAs of each variant (the next-wave L2 prefetch)
+        int sms = 0, large = 0, small = 0;
+        e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, H->device);
+        if (e == cudaSuccess)
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                &large, k_mixed_fused<FT, FM, FHW, BC_PERIODIC, false, 2>, FT,
+                sizeof(FusedShared<FT, FM, FHW>));
+        if (e == cudaSuccess)
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                &small, k_mixed_fused<FTS, FM, FHW, BC_PERIODIC, false, 2>, FTS,
+                sizeof(FusedShared<FTS, FM, FHW>));
+        H->tileSlots = sms * large;
+        H->tileSlotsSmall = sms * small;
+    }
     if (e == cudaSuccess && windowed) e = assign_tiles(H, std::vector<int8_t>((size_t)count, 0));
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&H->cap, cudaStreamNonBlocking);
     if (e != cudaSuccess) {
