@@ -994,19 +994,23 @@ int hsgn_set_state(hsgn_handle_t H, const double* depth, const double* q, const 
     // the windowed path holds double-float pairs: converted straight from the
     // caller's buffer when the device can address it (device memory of this
     // device, page-locked host memory mapped into the device's address space),
-    // else copied to the idle buffer first
+    // else copied to the idle buffer first. The copies are issued back to back
+    // and the conversions after them, so that the copy engine does not wait
+    // for a conversion between two arrays.
     double* const* idle = H->cur ? H->U : H->V;
+    const double* v[4];
     for (int k = 0; k < 4; ++k) {
-        const double* v = static_cast<const double*>(device_view(H, src[k]));
-        if (!v) {
+        v[k] = static_cast<const double*>(device_view(H, src[k]));
+        if (!v[k]) {
             if (cudaMemcpyAsync(idle[k], src[k], H->n * sizeof(double), cudaMemcpyDefault, st) !=
                 cudaSuccess)
                 return HSGN_ERR_CUDA;
-            v = idle[k];
+            v[k] = idle[k];
         }
-        k_df_from_f64<<<convert_blocks(H), 256, 0, st>>>(H->n, v,
-                                                         reinterpret_cast<float2*>(state(H)[k]));
     }
+    for (int k = 0; k < 4; ++k)
+        k_df_from_f64<<<convert_blocks(H), 256, 0, st>>>(H->n, v[k],
+                                                         reinterpret_cast<float2*>(state(H)[k]));
     if (cudaGetLastError() != cudaSuccess) return HSGN_ERR_CUDA;
     return refresh_speed(H, st) == cudaSuccess ? HSGN_OK : HSGN_ERR_CUDA;
 }
@@ -1026,17 +1030,21 @@ int hsgn_copy_state_out(hsgn_handle_t H, double* depth, double* q, double* heta,
     double* const* src = state(H);
     if (H->windowed) {
         // pairs to doubles: straight into the caller's buffer when the device
-        // can address it, else through the idle buffer and a copy
+        // can address it, else through the idle buffer and a copy (the four
+        // conversions first, then the copies back to back)
         double* const* tmp = H->cur ? H->U : H->V;
+        double* v[4];
         for (int k = 0; k < 4; ++k) {
-            double* v = static_cast<double*>(const_cast<void*>(device_view(H, dst[k])));
+            v[k] = static_cast<double*>(const_cast<void*>(device_view(H, dst[k])));
             k_f64_from_df<<<convert_blocks(H), 256, 0, st>>>(
-                H->n, reinterpret_cast<const float2*>(src[k]), v ? v : tmp[k]);
-            if (!v && cudaMemcpyAsync(dst[k], tmp[k], H->n * sizeof(double), cudaMemcpyDefault,
-                                      st) != cudaSuccess)
-                return HSGN_ERR_CUDA;
+                H->n, reinterpret_cast<const float2*>(src[k]), v[k] ? v[k] : tmp[k]);
         }
-        return cudaGetLastError() == cudaSuccess ? HSGN_OK : HSGN_ERR_CUDA;
+        if (cudaGetLastError() != cudaSuccess) return HSGN_ERR_CUDA;
+        for (int k = 0; k < 4; ++k)
+            if (!v[k] && cudaMemcpyAsync(dst[k], tmp[k], H->n * sizeof(double), cudaMemcpyDefault,
+                                         st) != cudaSuccess)
+                return HSGN_ERR_CUDA;
+        return HSGN_OK;
     }
     for (int k = 0; k < 4; ++k)
         if (cudaMemcpyAsync(dst[k], src[k], H->n * sizeof(double), cudaMemcpyDefault, st) !=
