@@ -393,6 +393,7 @@ __global__ void __launch_bounds__(T, (WB ? 768 : 1024) / T) k_mixed_fused(const 
             sm.Dh[j] = inc(wb1, dh1n - dh1, Dhn);
             sm.Dm[j] = inc(wb1, dm1n - dm1, Dmn);
         } else {
+            (void)dm1n;  // the bottom form carries P_l instead of the m difference
             const float2 b0 = at.u(p.bathy + cell0, 0), b1 = at.u(p.bathy + cell0, 1);
             // free-surface jump (h_l + b) at the face right of the cell:
             // hi1 - hi0 of h is exact, that of b is taken exactly by TwoSum
