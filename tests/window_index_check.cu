@@ -76,6 +76,14 @@ void check(int64_t n, int S) {
         CHECK(pd(w.lo + w.sp + 1) < G::NC && w.lo + w.sp + 3 < G::NC);
         // dh of window row r at r + 4 (r = -1 .. W; thread t stores rows 4t .. 4t + 3)
         CHECK(w.W + 4 < G::NC);
+        // next-wave L2 prefetch of this tile's window (clamped to [0, n)): the
+        // first (R + 21) / 16 threads, one line of 16 pairs each, cover it
+        {
+            const int64_t c0 = w.wl - 3 < 0 ? 0 : w.wl - 3;
+            const int64_t c1 = w.wl + w.W + 3 > n ? n : w.wl + w.W + 3;
+            CHECK(c0 >= 0 && c1 <= n && c0 < c1);
+            CHECK(c1 - c0 <= 16 * ((G::R + 6 + 15) / 16));
+        }
         CHECK(w.t0 + w.sp <= n);
         // mini-windows of the tile faces
         const bool lface = !(BC == BC_TRANSMISSIVE && w.t0 == 0);
