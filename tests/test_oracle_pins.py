@@ -462,3 +462,72 @@ def test_wb_form_mass_and_mirror_over_bathymetry():
     Vm = oracle.run(pm, (U[0][::-1], -U[1][::-1], U[2][::-1], U[3][::-1]), 0.02, 100)
     for k, s in enumerate((1, -1, 1, 1)):
         np.testing.assert_allclose(Vm[k], s * V[k][::-1], rtol=0, atol=1e-11)
+
+
+def _spectral_dx(f, length):
+    k = 2 * math.pi * np.fft.rfftfreq(len(f), d=length / len(f))
+    return np.fft.irfft(1j * k * np.fft.rfft(f), n=len(f))
+
+
+def _smooth_bottom(x, length):
+    # a band-limited periodic bottom with slopes up to about 0.06
+    k = 2 * math.pi / length
+    return (0.12 * np.sin(k * x + 0.4) + 0.08 * np.cos(2 * k * x - 1.1)
+            + 0.04 * np.sin(3 * k * x + 2.0))
+
+
+def bottom_model_rhs(U, b, length, lam):
+    """Right-hand side of the hSGN model with a bottom (Sec. 2.3, eq. (hSGNb_eq))
+    for b_t = 0, written from the equation itself and differentiated spectrally:
+      h_t    = -(hu)_x
+      (hu)_t = -(hu^2 + g h^2/2 + eta p~)_x - (g h + (3/2) p~) b_x
+      (h eta)_t = -(hu eta)_x + hw - (3/2) hu b_x   [(h eta~)_t + (hu eta~)_x = hw,
+                                                      eta~ = eta + 3b/2, minus 3/2 b times
+                                                      the mass equation]
+      (hw)_t = -(hu w)_x + 3 p~,      p~ = (lambda/3)(1 - eta/h).
+    Also returns the two non-hydrostatic bottom terms (3/2) p~ b_x and (3/2) hu b_x."""
+    h, q, m, r = U
+    u, eta = q / h, m / h
+    pt = (lam / 3.0) * (1.0 - eta / h)
+    d = lambda f: _spectral_dx(f, length)
+    bx = d(b)
+    rhs = (-d(q),
+           -d(q * u + 0.5 * G * h * h + eta * pt) - (G * h + 1.5 * pt) * bx,
+           -d(m * u) + r - 1.5 * q * bx,
+           -d(r * u) + 3.0 * pt)
+    return rhs, (1.5 * pt * bx, 1.5 * q * bx)
+
+
+def test_wb_form_stage_converges_to_the_bottom_model():
+    # One stage from U_b = U_l = U of length tau over a moving state (u, w != 0,
+    # eta != h) and a non-flat periodic bottom: (S(tau) - U)/tau tends to the
+    # right-hand side of eq. (hSGNb_eq) as tau, dx -> 0. Richardson in tau
+    # (2 D(tau/2) - D(tau)) removes the O(tau) part of the semi-implicit stage,
+    # so what is left is the spatial error, second order for every component.
+    # The two non-hydrostatic bottom terms, (3/2) p~ b_x in the momentum and
+    # -(3/2) hu b_x in the h eta equation, are O(0.1) and O(0.01) here: a wrong
+    # factor (1 or 3 for 3/2) or sign in either leaves an O(1) part of that term
+    # in the limit, which stalls the convergence far above the bounds below.
+    length, lam, tau = 40.0, 100.0, 1e-5
+    errs, terms = [], None
+    for n in (128, 256, 512):
+        dx = length / n
+        U = inputs.random_state(31, n, dx, h_var=0.1, u_amp=0.3, eta_rel=0.08, w_amp=0.1)
+        x = (np.arange(n) + 0.5) * dx
+        b = _smooth_bottom(x, length)
+        umax = float(np.max(np.abs(U[1] / U[0])))
+        p = oracle.Params(n, dx, oracle.BC_PERIODIC, lam=lam, form=1, bathy=b, speed=umax)
+        D = []
+        for t in (tau, 0.5 * tau):
+            V = oracle.stage(p, U, U, t)
+            D.append([(V[k] - U[k]) / t for k in range(4)])
+        R = [2.0 * D[1][k] - D[0][k] for k in range(4)]
+        E, terms = bottom_model_rhs(U, b, length, lam)
+        errs.append([float(np.max(np.abs(R[k] - E[k]))) for k in range(4)])
+    for k in range(4):
+        rates = [math.log2(errs[i][k] / errs[i + 1][k]) for i in range(2)]
+        assert all(1.7 < r < 2.5 for r in rates), (k, errs, rates)
+    t_q, t_m = (float(np.max(np.abs(t))) for t in terms)
+    assert t_q > 0.1 and t_m > 0.01  # the terms under test are not negligible
+    assert errs[-1][1] < 0.01 * t_q, (errs[-1], t_q)
+    assert errs[-1][2] < 0.01 * t_m, (errs[-1], t_m)
