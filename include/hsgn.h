@@ -337,7 +337,11 @@ int hsgn_tridiag_solve(int64_t n, int32_t periodic, const double* a, const doubl
  * larger n returns HSGN_ERR_INVALID_ARG before any device work.
  * Set-up: the first call on each device, with that device current, looks up
  * the device address of the array (cudaGetSymbolAddress); make that first call
- * before any stream capture. All calls share the one array, which keeps the
+ * before any stream capture. The address is kept for the life of the process:
+ * cudaDeviceReset, or anything else that destroys the device's primary
+ * context, reloads the library's device code at a possibly different address,
+ * so do not call this entry point on that device again in the same process
+ * after such a reset. All calls share the one array, which keeps the
  * contents of the previous call; the call clears its error word itself, and
  * every other scratch value is written before it is read. Calls that overlap
  * on the GPU (other streams or threads) race on the array and must not be
@@ -345,6 +349,7 @@ int hsgn_tridiag_solve(int64_t n, int32_t periodic, const double* a, const doubl
  * Synchronises `stream` and reports device errors like hsgn_tridiag_solve.
  * --------------------------------------------------------------------------- */
 #define HSGN_TRIDIAG_NOALLOC_MAX_N 262144
+#define HSGN_TRIDIAG_NOALLOC_SCRATCH_BYTES 6522624 /* 6.2 MiB */
 int hsgn_tridiag_solve_noalloc(int64_t n, int32_t periodic, const double* a, const double* b,
                                const double* c, const double* d, double* x, void* stream);
 

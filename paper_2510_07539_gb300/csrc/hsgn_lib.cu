@@ -1893,6 +1893,8 @@ constexpr int64_t kNoAllocMaxN = HSGN_TRIDIAG_NOALLOC_MAX_N;
 // error word + the workspace of the recursive solve of the largest size
 constexpr size_t kNoAllocBytes = kAlign + rows_ws_bytes(kNoAllocMaxN);
 static_assert(kNoAllocBytes < (size_t)8 << 20, "fixed scratch must stay modest");
+static_assert(kNoAllocBytes == HSGN_TRIDIAG_NOALLOC_SCRATCH_BYTES,
+              "the size stated in hsgn.h must match the array");
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
 

@@ -275,15 +275,32 @@ def tridiag_workspace_bytes(n: int) -> int:
     return nb.value
 
 
+def _check_rows(a, b, c, d, out):
+    """Every array of a tridiagonal call has b's length and lives on the current
+    CUDA device (the kernels index all of them up to n - 1)."""
+    n = b.numel()
+    arrays = (a, b, c, d) + (() if out is None else (out,))
+    for t in arrays:
+        if t.numel() != n:
+            raise ValueError(f"tridiagonal arrays must all have {n} entries, got {t.numel()}")
+    for t in arrays:
+        if t.device.type != "cuda" or t.device.index != torch.cuda.current_device():
+            raise ValueError("tridiagonal arrays must be CUDA tensors on the current device")
+    return n
+
+
 def tridiag_solve(a, b, c, d, periodic: bool, stream=None, out=None, workspace=None):
     """Solve the (cyclic) tridiagonal system on the GPU; returns x (a new
     tensor, or `out`). `workspace`: a uint8 device tensor of at least
     tridiag_workspace_bytes(n) + 256 bytes, allocated here when None."""
+    n = _check_rows(a, b, c, d, out)
     load()
-    n = b.numel()
     x = torch.empty_like(d) if out is None else out
     nbytes = tridiag_workspace_bytes(n)
     ws = workspace
+    if ws is not None and (ws.device.type != "cuda"
+                           or ws.device.index != torch.cuda.current_device()):
+        raise ValueError("the workspace must be a CUDA tensor on the current device")
     if ws is None or ws.numel() < max(nbytes, 256) + 256:
         ws = torch.empty(max(nbytes, 256) + 256, dtype=torch.uint8, device=d.device)
     base = ws.data_ptr()
@@ -300,6 +317,7 @@ NOALLOC_MAX_N = 262144
 def tridiag_solve_noalloc(a, b, c, d, periodic: bool, out=None, stream=None):
     """Same solve as tridiag_solve through the entry point that allocates
     nothing (fixed device scratch inside the library, n <= NOALLOC_MAX_N)."""
+    _check_rows(a, b, c, d, out)
     lib = load()
     f = lib.hsgn_tridiag_solve_noalloc
     f.argtypes = [_I64, ctypes.c_int32, _P, _P, _P, _P, _P, _P]

@@ -135,3 +135,24 @@ def test_degenerate_grids_are_rejected(lib):
         for flags in (0, 0x1):
             assert lib.hsgn_create(ctypes.byref(g), 9.81, 1.0, None, flags, ctypes.byref(h)) == 1
     assert not h.value
+
+
+@pytest.mark.parametrize("noalloc", [False, True])
+def test_tridiag_wrappers_reject_bad_arrays_before_any_launch(noalloc):
+    # A short array, or one that is not on the current CUDA device, would hand
+    # the kernels a pointer they index past its end; the binding refuses both
+    # before it touches the library or the device (this runs without a GPU).
+    torch = pytest.importorskip("torch")
+    from paper_2510_07539_gb300 import solver
+    f = solver.tridiag_solve_noalloc if noalloc else solver.tridiag_solve
+    n = 16
+    ok = [torch.ones(n, dtype=torch.float64) for _ in range(4)]
+    for k in range(4):
+        bad = list(ok)
+        bad[k] = torch.ones(n - 1, dtype=torch.float64)
+        with pytest.raises(ValueError, match="entries"):
+            f(*bad, periodic=False)
+    with pytest.raises(ValueError, match="entries"):
+        f(*ok, periodic=True, out=torch.empty(n + 1, dtype=torch.float64))
+    with pytest.raises(ValueError, match="CUDA"):
+        f(*ok, periodic=False)
