@@ -1,16 +1,20 @@
 #!/usr/bin/env python3
 """Throughput benchmark of the semi-implicit IMEX hSGN step on GB300.
 
-Workload (the dam-break / undular-bore configuration): N = 2^20 cells,
-dx = 0.05, transmissive ends, flat bottom, h = 1.2 on the left and 1.0 on the
-right joined by a tanh transition of width 5 h0 (h0 = 1), u = 0, eta = h,
-w = 0; one instance per relaxation parameter lambda in {10, 100, 1000}, each
-with its own dt = min(4 dx / nu_max, 0.5 dx / u_max) computed at t = 0
-(CFL_IMEX = 4, material CFL 0.5). One benchmark step advances all three
-instances by one IMEX step (two implicit stages each). Inputs are synthetic
-(seed-free closed forms). The headline is the mixed-precision form (FP32
-increments, FP64 state and accumulation) with its error against the FP64
-oracle; the all-FP64 form is timed on the same workload and reported beside it.
+Workload (the dam-break / undular-bore configuration, run at 2^24 cells per
+instance so that every state is far larger than L2): dx = 0.05, transmissive
+ends, flat bottom, h = 1.2 on the left and 1.0 on the right joined by a tanh
+transition of width 5 h0 (h0 = 1), u = 0, eta = h, w = 0; one instance per
+relaxation parameter lambda in {10, 100, 1000}, each with its own
+dt = min(4 dx / nu_max, 0.5 dx / u_max) computed at t = 0 (CFL_IMEX = 4,
+material CFL 0.5). One benchmark step advances all three instances by one IMEX
+step (two implicit stages each). Inputs are synthetic (seed-free closed forms).
+
+The headline is the FP64-class double-float form (every value a pair of
+single-precision numbers, one launch per stage; within 1e-12 per step of the
+FP64 oracle). The FP64 form and the mixed-precision form (FP32 increments) are
+timed on the same workload and reported beside it, each with its error against
+the oracle.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -41,8 +45,10 @@ FLUSH_BYTES = 512 * 1024 * 1024
 
 # Algorithmic traffic of one cell-stage in FP64 (flat bottom): stage 1 reads U^n
 # (32 B) and writes U_I^(1) (32 B); stage 2 reads U^n and U_I^(1) (64 B) and
-# writes U^{n+1} (32 B): 160 B per cell and step = 80 B per cell-stage.
+# writes U^{n+1} (32 B): 160 B per cell and step = 80 B per cell-stage; the
+# bottom adds 8 B per cell-stage (read once per stage).
 BYTES_PER_CELL_STAGE = 80.0
+BYTES_PER_CELL_STAGE_BOTTOM = 88.0
 # What the windowed mixed path itself moves per cell-stage: stage 1 reads U^n
 # (32 B) and writes the FP32 increments (16 B); stage 2 reads U^n and the
 # increments (48 B) and writes U^{n+1} (32 B): 64 B.
@@ -54,8 +60,19 @@ BYTES_MOVED_MIXED = 64.0
 # chunk Thomas sweep with three right-hand sides and recombination 25
 # (a fused multiply-add counts 2, a division 1).
 FLOPS_PER_CELL_ASSEMBLE = 149.0
-# FP64 peak of a GB300 (nominal, dense): 1.25 TFLOP/s.
-FP64_PEAK_TFLOPS = 1.25
+# Single-precision operations the double-float stage kernel executes per cell
+# and launch (average of its two stages, window overlap included): ncu's
+# per-launch counts of FADD + FMUL + 2 FFMA (sm__sass_thread_inst_executed_op_
+# {fadd,fmul,ffma}_pred_on.sum) divided by the cells of the launch, on the
+# 2^22-cell dam break (the capture summarised in profiles/ncu_df_stage.md).
+# Valid for the kernel sources whose hash is DF_FLOPS_SOURCE_SHA; None when the
+# kernel has changed since (the roofline then reports no achieved flop rate).
+DF_FLOPS_PER_CELL = 2058.4      # stage 1 / 2: 1943.8 / 2172.9
+DF_FP32_INST_PER_CELL = 1793.0  # FADD + FMUL + FFMA instructions, stage 1 / 2: 1695.4 / 1890.6
+DF_TRAFFIC_PER_CELL = 71.0      # dram__bytes_read + write per cell and launch, stage 1 / 2: 53.5 / 88.6
+DF_FLOPS_SOURCE_SHA = "2fcec70606e589df"
+DF_SOURCES = ("hsgn_dfstage.cuh", "hsgn_dfloat.cuh", "hsgn_fused.cuh", "hsgn_mixed.cuh",
+              "hsgn_tridiag.cuh")
 
 
 def parse_args():
@@ -64,14 +81,15 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
-    ap.add_argument("--log2n", type=int, default=20)
+    ap.add_argument("--log2n", type=int, default=24)
     ap.add_argument("--lams", default="10,100,1000")
-    ap.add_argument("--cpu-steps", type=int, default=40,
+    ap.add_argument("--cpu-steps", type=int, default=3,
                     help="oracle steps per instance for the CPU baseline and the L2 check")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-fp64", action="store_true", help="skip the all-FP64 path")
+    ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision path")
     ap.add_argument("--no-comparators", action="store_true",
                     help="skip the scheme comparison (time to solution)")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint workload")
@@ -139,26 +157,6 @@ def source_sha(files=None) -> str:
         with open(os.path.join(csrc, name), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
-
-
-def profiled_traffic_per_cell(summary: str):
-    """DRAM bytes per cell of a kernel from its committed ncu summary, or None
-    when the kernel's sources (the summary's `source_files`, else all of csrc)
-    changed since that capture."""
-    path = os.path.join(ROOT, "profiles", summary)
-    if not os.path.exists(path):
-        return None
-    txt = open(path).read()
-    sha = re.search(r"source_sha:\s*([0-9a-f]+)", txt)
-    files = re.search(r"source_files:\s*([^\n]+)", txt)
-    val = re.search(r"dram_bytes_per_cell_per_launch:\s*([0-9.eE+-]+)", txt)
-    if not sha or not val:
-        return None
-    try:
-        cur = source_sha(files.group(1).split() if files else None)
-    except OSError:
-        return None
-    return float(val.group(1)) if sha.group(1) == cur else None
 
 
 # ---------------------------------------------------------------------------
@@ -618,15 +616,15 @@ def time_shelf(S, torch, stream, hbm_peak, log2n=24, steps=50, warmup=3):
                          "state": [t.cpu().numpy() for t in s.get_state()]}
     ref, got = out["fp64"].pop("state"), out["mixed"].pop("state")
     rel = [float(np.linalg.norm(got[k] - ref[k]) / np.linalg.norm(ref[k])) for k in range(4)]
-    # the mixed bottom form must move 72 B per cell and stage (state and bottom
-    # pairs read, increments written and read back, new state written)
-    gbs = 72.0 * 2.0 * n * steps / (out["mixed"]["ms_per_step"] * steps / 1e3) / 1e9
-    tpc = profiled_traffic_per_cell("ncu_mixed_fused_bottom.md")
+    # algorithmic bytes of the bottom form: 88 per cell-stage (the FP64 state
+    # traffic of the scheme, 80 B, plus the bottom read once per stage)
+    gbs = (BYTES_PER_CELL_STAGE_BOTTOM * 2.0 * n * steps
+           / (out["mixed"]["ms_per_step"] * steps / 1e3) / 1e9)
     out["mixed"]["roofline"] = {"bound": "hbm", "kernel": "k_mixed_fused (bottom form)",
                                 "achieved": gbs, "peak": hbm_peak, "unit": "GB/s",
                                 "frac": gbs / hbm_peak,
-                                "algorithmic_bytes_per_cell_stage": 72,
-                                "traffic_per_launch": tpc * n if tpc is not None else None}
+                                "algorithmic_bytes_per_cell_stage": BYTES_PER_CELL_STAGE_BOTTOM,
+                                "timing": "whole steps (both stages), one stream"}
     return {"workload": f"wave a = 0.1 towards a 1:20 shelf, N = 2^{log2n}, dx = {dx:g}, "
                         f"transmissive, lambda = 1000, bottom form, dt = {dt:.6g} "
                         f"(CFL_IMEX 4), {steps} timed steps (of the 5000-step run)",
@@ -636,29 +634,42 @@ def time_shelf(S, torch, stream, hbm_peak, log2n=24, steps=50, warmup=3):
                                                  "h_w": rel[3]}}
 
 
-def time_fp64(S, torch, n, xl, xr, lams, Ud, args, flush, stream, dist, units_rank, world,
-              hbm_peak):
-    """The all-FP64 path (exact separator solve) on the same workload."""
-    fsols, fdts, fms, ftot, _ = time_path(S, torch, S.FLAG_FP64, n, xl, xr, lams, Ud,
-                                          args.steps, args.warmup, flush, stream, dist, None,
-                                          False)
-    favg = ftot["assemble"][0] / max(ftot["assemble"][1], 1)
-    ftf = FLOPS_PER_CELL_ASSEMBLE * n / (favg / 1e3) / 1e12
-    fshare_den = sum(v[0] for v in ftot.values())
-    fp64 = {
-        "value": units_rank * world / (fms / 1e3), "unit": UNIT, "ms_per_step": fms / args.steps,
-        "dtype": "f64",
-        "roofline": {"bound": "alu", "kernel": "k_stage_assemble", "achieved": ftf,
-                     "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": ftf / FP64_PEAK_TFLOPS,
-                     "peak_source": "nominal dense FP64 of GB300 (1.25 TFLOP/s)",
-                     "traffic": (lambda t: t * n if t is not None else None)(
-                         profiled_traffic_per_cell("ncu_stage_assemble.md")),
-                     "kernel_avg_ms": favg,
-                     "kernel_share": {k: v[0] / fshare_den for k, v in ftot.items()},
-                     "hbm_frac_of_measured": BYTES_PER_CELL_STAGE * units_rank / (fms / 1e3)
-                     / 1e9 / hbm_peak},
-    }
-    return fp64, fsols, fdts
+def kernel_roofline_alu(name, flops_per_cell, n, avg_ms, peak, peak_source):
+    """Arithmetic roofline of one stage kernel from its average launch time."""
+    if flops_per_cell is None or not (avg_ms > 0):
+        return {"bound": "alu", "kernel": name, "achieved": None, "peak": peak,
+                "unit": "TFLOP/s", "frac": None, "peak_source": peak_source,
+                "kernel_avg_ms": avg_ms}
+    tf = flops_per_cell * n / (avg_ms / 1e3) / 1e12
+    return {"bound": "alu", "kernel": name, "achieved": tf, "peak": peak, "unit": "TFLOP/s",
+            "frac": tf / peak, "peak_source": peak_source, "kernel_avg_ms": avg_ms,
+            "flops_per_cell_launch": flops_per_cell}
+
+
+def hbm_view(n, avg_ms, hbm_peak, bytes_per_cell=BYTES_PER_CELL_STAGE):
+    gbs = bytes_per_cell * n / (avg_ms / 1e3) / 1e9
+    return {"achieved_gbs": gbs, "frac_of_measured_hbm": gbs / hbm_peak,
+            "algorithmic_bytes_per_cell_stage": bytes_per_cell}
+
+
+def time_form(S, torch, flags, n, xl, xr, lams, Ud, args, flush, stream, dist, clocks,
+              concurrent):
+    """A form timed twice on the workload: the instances of a step on one stream
+    each (the throughput), then back to back on one stream, where the event
+    pair of every launch times that launch alone (the kernel's duration)."""
+    sols, dts, ms, tot, clk = time_path(S, torch, flags, n, xl, xr, lams, Ud, args.steps,
+                                        args.warmup, flush, stream, dist, clocks, concurrent)
+    if concurrent:
+        qsols, _, qms, qtot, _ = time_path(S, torch, flags, n, xl, xr, lams, Ud, args.steps,
+                                           args.warmup, flush, stream, dist, None, False)
+        for s_ in qsols:
+            s_.close()
+    else:
+        qms, qtot = ms, tot
+    avg = qtot["assemble"][0] / max(qtot["assemble"][1], 1)
+    share_den = sum(v[0] for v in qtot.values())
+    share = {k: v[0] / share_den for k, v in qtot.items() if v[1] > 0} if share_den > 0 else {}
+    return sols, dts, ms, qms, avg, share, clk
 
 
 def run_ours(args):
@@ -698,57 +709,79 @@ def run_ours(args):
     except Exception:
         pass
     hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
+    hbm_src = ("measured copy bandwidth (MEASURED_PEAKS.json hbm_gbs), burst"
+               if "hbm_gbs" in peaks else "fallback 6.8 TB/s of the profiling recipe")
+    # arithmetic peaks measured here: fused multiply-add chains on every SM
+    # (hsgn_fma_peak), best of three
+    fp32_peak = max(S.fma_peak(32) for _ in range(3))
+    fp64_peak = max(S.fma_peak(64) for _ in range(3))
     units_rank = 2.0 * n * len(lams) * args.steps
 
-    # ---- headline: mixed precision, windowed stage (one launch per stage);
+    # ---- headline: the double-float form (FP64 class), one launch per stage;
     #      the instances of a step on one stream each (whole-job throughput)
-    msols, mdts, mms, mtot, clocks = time_path(S, torch, S.FLAG_MIXED, n, xl, xr, lams, Ud,
-                                              args.steps, args.warmup, flush, stream, dist,
-                                              gpu_id, not args.sequential)
-    value = units_rank * world / (mms / 1e3)
-    stage_ms = mms / (2 * len(lams) * args.steps)
-    # the kernel's own duration: a second timed pass with the instances back to
-    # back on one stream, where each launch's event pair times that launch alone
-    if args.sequential:
-        qms, qtot = mms, mtot
-    else:
-        qsols, _, qms, qtot, _ = time_path(S, torch, S.FLAG_MIXED, n, xl, xr, lams, Ud,
-                                           args.steps, args.warmup, flush, stream, dist, None,
-                                           False)
-        for s in qsols:
-            s.close()
-    avg_k = qtot["assemble"][0] / max(qtot["assemble"][1], 1)
-    kernel_gbs = BYTES_PER_CELL_STAGE * n / (avg_k / 1e3) / 1e9
-    tpc = profiled_traffic_per_cell("ncu_mixed_fused.md")
-    roofline = {
-        "bound": "hbm",
-        "kernel": "k_mixed_fused (windowed stage: fluxes, rows, depth solve and "
-                  "back-substitution in one launch)",
-        "achieved": kernel_gbs, "peak": hbm_peak, "unit": "GB/s",
-        "frac": kernel_gbs / hbm_peak,
-        "peak_source": "measured copy bandwidth (MEASURED_PEAKS.json hbm_gbs), burst",
-        "traffic": tpc * n if tpc is not None else None,
-        "algorithmic_bytes_per_cell_stage": BYTES_PER_CELL_STAGE,
-        "bytes_moved_per_cell_stage": BYTES_MOVED_MIXED,
-        "kernel_avg_ms": avg_k,
-        "kernel_timing": f"one stream, {len(lams)} instances back to back, {args.steps} steps",
-        "stage_avg_ms": stage_ms,
-        "stage_achieved_gbs": BYTES_PER_CELL_STAGE * n / (stage_ms / 1e3) / 1e9,
-        "stage_frac": BYTES_PER_CELL_STAGE * n / (stage_ms / 1e3) / 1e9 / hbm_peak,
-        "sequential_value": units_rank * world / (qms / 1e3),
-    }
+    dsols, ddts, dms, dqms, davg, dshare, clocks = time_form(
+        S, torch, S.FLAG_DOUBLE_FLOAT, n, xl, xr, lams, Ud, args, flush, stream, dist, gpu_id,
+        not args.sequential)
+    value = units_rank * world / (dms / 1e3)
+    counted = DF_FLOPS_SOURCE_SHA is not None and source_sha(DF_SOURCES) == DF_FLOPS_SOURCE_SHA
+    dflops = DF_FLOPS_PER_CELL if counted else None
+    roofline = kernel_roofline_alu(
+        "k_df_stage (double-float stage: fluxes, rows, depth solve and back-substitution in one "
+        "launch)", dflops, n, davg, fp32_peak,
+        "measured here: FP32 fused multiply-add chains on every SM (hsgn_fma_peak), best of 3")
+    roofline.update({
+        # DRAM bytes per launch: the ncu count per cell of the 2^22-cell capture
+        # times the cells of one launch (traffic grows with the cells)
+        "traffic": DF_TRAFFIC_PER_CELL * n if counted else None,
+        # the FP32 pipe's issue share: FP32 instructions per second against half
+        # the measured multiply-add flop rate (one instruction per lane and clock)
+        "fp32_pipe_frac": (DF_FP32_INST_PER_CELL * n / (davg / 1e3) / 1e12 / (fp32_peak / 2.0))
+        if counted and davg > 0 else None,
+        "kernel_timing": f"one stream, {len(lams)} instances back to back, {args.steps} steps "
+                         "(the sequential pass)",
+        "kernel_share": dshare,
+        "hbm": hbm_view(n, davg, hbm_peak),
+        "sequential_value": units_rank * world / (dqms / 1e3),
+    })
     launches = len(lams) * args.steps * 2
 
-    # ---- the all-FP64 path on the same workload
+    # ---- the FP64 form (exact separator solve) on the same workload
     fp64, fsols, fdts = None, [], []
     if not args.no_fp64:
-        fp64, fsols, fdts = time_fp64(S, torch, n, xl, xr, lams, Ud, args, flush, stream, dist,
-                                      units_rank, world, hbm_peak)
+        fsols, fdts, fms, fqms, favg, fshare, _ = time_form(
+            S, torch, S.FLAG_FP64, n, xl, xr, lams, Ud, args, flush, stream, dist, None, False)
+        fp64 = {"value": units_rank * world / (fms / 1e3), "unit": UNIT,
+                "ms_per_step": fms / args.steps, "dtype": "f64",
+                "roofline": kernel_roofline_alu(
+                    "k_stage_assemble", FLOPS_PER_CELL_ASSEMBLE, n, favg, fp64_peak,
+                    "measured here: FP64 fused multiply-add chains on every SM (hsgn_fma_peak)"),
+                "kernel_share": fshare,
+                "hbm": {"frac_of_measured_hbm_whole_step": BYTES_PER_CELL_STAGE * units_rank
+                        / (fms / 1e3) / 1e9 / hbm_peak}}
+
+    # ---- the mixed-precision form (FP32 increments, windowed solve)
+    mixed, msols, mdts = None, [], []
+    if not args.no_mixed:
+        msols, mdts, mms, mqms, mavg, mshare, _ = time_form(
+            S, torch, S.FLAG_MIXED, n, xl, xr, lams, Ud, args, flush, stream, dist, None,
+            not args.sequential)
+        mgbs = BYTES_PER_CELL_STAGE * n / (mavg / 1e3) / 1e9
+        mixed = {"value": units_rank * world / (mms / 1e3), "unit": UNIT,
+                 "ms_per_step": mms / args.steps, "dtype": "f32 increments + double-float state",
+                 "roofline": {"bound": "hbm", "kernel": "k_mixed_fused", "achieved": mgbs,
+                              "peak": hbm_peak, "unit": "GB/s", "frac": mgbs / hbm_peak,
+                              "peak_source": hbm_src, "kernel_avg_ms": mavg,
+                              "algorithmic_bytes_per_cell_stage": BYTES_PER_CELL_STAGE,
+                              "bytes_moved_per_cell_stage": BYTES_MOVED_MIXED},
+                 "sequential_value": units_rank * world / (mqms / 1e3)}
 
     # ---- the paper's comparison: the same physical time with each scheme
     comparators = None
     if not args.no_comparators:
-        comparators = time_to_solution(S, torch, n, xl, xr, Ud, stream)
+        comparators = time_to_solution(S, torch, 1 << 20, -0.5 * (1 << 20) * dx,
+                                       0.5 * (1 << 20) * dx,
+                                       [torch.tensor(u, device="cuda")
+                                        for u in workload(20, lams)[4]], stream)
     adjoint = None
     if not args.no_adjoint and rank == 0:
         adjoint = time_adjoint(S, torch, stream)
@@ -763,7 +796,8 @@ def run_ours(args):
         shelf = time_shelf(S, torch, stream, hbm_peak, args.shelf_log2n, args.shelf_steps)
 
     # ---- batched workload: 4096 independent periodic solitary waves of uneven
-    #      length, the windowed mixed stage over all of them: one launch per stage
+    #      length, the windowed mixed stage over all of them, each step one
+    #      replay of the captured step graph
     batched = None
     if not args.no_batched:
         from paper_2510_07539_gb300 import inputs as inp
@@ -781,21 +815,20 @@ def run_ours(args):
         # tiles picked by the library's autotuner (outside the timed region;
         # the state is kept)
         tune = B.autotune(4)
-        for _ in range(args.warmup):
-            B.step()
-        B.check()
+        B.run(0.0, args.warmup)  # also captures the step graphs of both state buffers
         bev0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
         bev1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
         torch.cuda.synchronize()
         for k in range(args.steps):
             flush.fill_(float(k))
             bev0[k].record(stream)
-            B.step()
+            B.enqueue(0.0, 1, stream=stream)
             bev1[k].record(stream)
         torch.cuda.synchronize()
         B.check()
         bms = sum(a.elapsed_time(c) for a, c in zip(bev0, bev1))
         bcells = int(sum(ns))
+        bgbs = BYTES_PER_CELL_STAGE * 2.0 * bcells / (bms / args.steps / 1e3) / 1e9
         batched = {
             "workload": f"{len(ns)} periodic hSGN solitary waves, N ~ U[256, 8192], "
                         "a ~ U[0.05, 0.4], lambda in {10, 100, 1000}, per-instance dt "
@@ -804,6 +837,11 @@ def run_ours(args):
             "instances": len(ns), "cells": bcells,
             "value": 2.0 * bcells * args.steps * world / (bms / 1e3), "unit": UNIT,
             "ms_per_step": bms / args.steps,
+            "timing": "each step one replay of the captured step graph (hsgn_enqueue)",
+            "roofline": {"bound": "hbm", "achieved": bgbs, "peak": hbm_peak, "unit": "GB/s",
+                         "frac": bgbs / hbm_peak,
+                         "algorithmic_bytes_per_cell_stage": BYTES_PER_CELL_STAGE,
+                         "timing": "whole steps"},
             "gpu_launches_per_step": 4 if tune["choice"] == 2 else 2,
             "autotune": {"ms_per_step_all_large_all_small_mixed": tune["ms_per_step"],
                          "kept": ("all large tiles (894 rows)", "all small tiles (382 rows)",
@@ -825,7 +863,7 @@ def run_ours(args):
             batched["depth_rel_l2_vs_oracle"] = {"value": worst, "instances": 8, "steps": 10}
         B.close()
 
-    # ---- end to end through the C ABI with host buffers (mixed path)
+    # ---- end to end through the C ABI with host buffers (the headline form)
     e2e = None
     if not args.no_e2e:
         host_in = [[torch.tensor(u).pin_memory() for u in U] for _ in lams]
@@ -837,12 +875,12 @@ def run_ours(args):
         # own stream, so that one step's copies in overlap the previous step's
         # copies out on the two copy engines; errors are checked after the
         # timed region
-        sets = [msols, [S.Solver(n, xl, xr, S.BC_TRANSMISSIVE, lam=l, flags=S.FLAG_MIXED)
+        sets = [dsols, [S.Solver(n, xl, xr, S.BC_TRANSMISSIVE, lam=l, flags=S.FLAG_DOUBLE_FLOAT)
                         for l in lams]]
         host_out = [[[torch.empty(n, dtype=torch.float64).pin_memory() for _ in range(4)]
                      for _ in lams] for _ in sets]
         side = [[torch.cuda.Stream() for _ in lams] for _ in sets]
-        for s, dt, hi, ho in zip(sets[1], mdts, host_in, host_out[1]):
+        for s, dt, hi, ho in zip(sets[1], ddts, host_in, host_out[1]):
             s.set_state(*hi)
             s.step(dt)  # the step graph of the new handle, outside the timed region
             s.copy_state_out(ho)
@@ -857,7 +895,7 @@ def run_ours(args):
                 st.wait_event(fork)
         for it in range(k_e2e):
             c = it % 2
-            for s, dt, hi, ho, st in zip(sets[c], mdts, host_in, host_out[c], side[c]):
+            for s, dt, hi, ho, st in zip(sets[c], ddts, host_in, host_out[c], side[c]):
                 s.set_state(*hi, stream=st)
                 s.step(dt, stream=st)
                 s.copy_state_out(ho, stream=st)
@@ -878,38 +916,44 @@ def run_ours(args):
         e2e = {"value": units / (ems / 1e3), "unit": UNIT,
                "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes, "steps": k_e2e}
 
-    # ---- CPU oracle baseline and the error of both paths against it
+    # ---- CPU oracle baseline and the error of every form against it
     cpu = None
     l2err = None
     if rank == 0 and world == 1 and not args.no_cpu:
         ks = max(1, args.cpu_steps)
-        refs, el = oracle_steps(n, dx, U, lams, mdts, ks)
+        refs, el = oracle_steps(n, dx, U, lams, ddts, ks)
         cpu = {"value": 2.0 * n * len(lams) * ks / el, "unit": UNIT, "cores": 1, "kind": "oracle",
                "sample": f"{ks} IMEX steps of each of the {len(lams)} instances ({n} cells), "
                          f"single-threaded C oracle, {el:.1f} s"}
-        l2err = l2_vs_oracle(msols, mdts, Ud, refs, ks, np)
+        l2err = l2_vs_oracle(dsols, ddts, Ud, refs, ks, np)
         if fp64 is not None:
             fp64["l2_rel_err_vs_oracle"] = l2_vs_oracle(fsols, fdts, Ud, refs, ks, np)
-    for s in msols + fsols:
+        if mixed is not None:
+            mixed["l2_rel_err_vs_oracle"] = l2_vs_oracle(msols, mdts, Ud, refs, ks, np)
+    for s in dsols + fsols + msols:
         s.close()
 
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": mms / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32+df64",
+            "warmup": args.warmup, "ms_per_step": dms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "df64",
             "data": "synthetic",
-            "config": config_dict(n, lams, mdts, {
+            "config": config_dict(n, lams, ddts, {
                 "parallelism": f"{world} independent replicas",
                 "streams": ("one stream, instances back to back" if args.sequential else
                             "one CUDA stream per instance, joined every step"),
-                "precision": "FP32 fluxes, coefficients and depth solve on increments; "
-                             "state as double-float pairs (48-bit significand), exact "
-                             "base differences, TwoSum accumulation",
-                "depth_solve": "windows of the tile +- 64 rows, truncation bounded "
-                               "in-kernel by rho*^63 <= 2^-30"}),
+                "precision": "double-float: every value a pair of FP32 numbers (48-bit "
+                             "significand, about 2^-47 per operation); parity bar of the FP64 "
+                             "form (1e-12 relative per step against the FP64 oracle)",
+                "depth_solve": "windows of the tile +- 96 rows, truncation bounded in-kernel "
+                               "by rho*^95 <= 2^-50"}),
             "l2_rel_err_vs_oracle": l2err,
-            "roofline": roofline, "fp64_path": fp64, "batched": batched,
+            "roofline": roofline, "peaks": {"hbm_gbs": hbm_peak, "hbm_source": hbm_src,
+                                            "fp32_tflops": fp32_peak, "fp64_tflops": fp64_peak,
+                                            "fp32_fp64_source": "measured in this run "
+                                                                "(hsgn_fma_peak)"},
+            "fp64_path": fp64, "mixed_path": mixed, "batched": batched,
             "batched_vs_fp64_single": (batched["value"] / fp64["value"])
             if (batched and fp64) else None,
             "comparators": comparators, "adjoint": adjoint, "shelf": shelf,

@@ -80,6 +80,26 @@ enum {
                                 * set/get_state convert from and to doubles), so the
                                 * stage runs without double-precision instructions.
                                 * hsgn_stage is not available in this form. */
+#define HSGN_DOUBLE_FLOAT 0x8  /* FP64-class arithmetic on the single-precision
+                                * pipe: every value of the stage (state, fluxes,
+                                * coefficients, the depth solve and the
+                                * back-substitution) is a double-float pair
+                                * (hi + lo, 48-bit significand; about 2^-47
+                                * relative error per operation), so that one step
+                                * stays within 1e-12 of the FP64 scheme while no
+                                * double-precision instruction runs. One launch
+                                * per stage on overlapping windows as described
+                                * under HSGN_MIXED, here 96 rows wide, with the
+                                * truncation bound checked against 2^-50
+                                * (HSGN_ERR_TRUNCATION above about CFL_IMEX 7 for
+                                * smooth states); increment form, the state
+                                * alternating between two device buffers of pairs
+                                * (set/get_state convert). Flat bottom, single
+                                * instances, the paper's scheme; not combinable
+                                * with HSGN_MIXED, HSGN_EXACT_SOLVE or
+                                * HSGN_WELL_BALANCED (HSGN_ERR_UNIMPLEMENTED).
+                                * hsgn_stage works in this form and leaves the
+                                * state untouched. */
 #define HSGN_EXACT_SOLVE 0x4   /* with HSGN_MIXED: solve the depth system exactly
                                 * through the global separator system (three
                                 * launches per stage, state updated in place) */
@@ -302,6 +322,14 @@ void hsgn_destroy(hsgn_handle_t h);
 
 /* Static, NUL-terminated description of an error code. */
 const char* hsgn_error_string(int code);
+
+/* Measured arithmetic peak of the current device, the denominator of the
+ * roofline of the arithmetic-bound stage kernels (the paper has no
+ * counterpart): independent fused multiply-add chains in single (bits = 32)
+ * or double (bits = 64) precision on every SM, timed with CUDA events; a
+ * multiply-add counts two operations. *tflops receives TFLOP/s. Allocates a
+ * small output buffer on `stream` (stream-ordered) and synchronises. */
+int hsgn_fma_peak(int32_t bits, double* tflops, void* stream);
 
 /* ---------------------------------------------------------------------------
  * Tridiagonal component (the depth solve of Sec. 4.2, Delta[hbar] = h^dagger)

@@ -1,0 +1,487 @@
+// hsgn_dfstage.cuh -- the FP64-class stage in one launch: double-float
+// arithmetic on the single-precision pipe (sm_103a).
+//
+// One stage of Sec. 4.2, eq. (GN_hyp_eq_semi_fully_discrete), inside the
+// two-stage tableau of Sec. 3.2 (efficient form), computed with every value a
+// double-float pair (hsgn_dfloat.cuh: 48-bit significand, each operation a
+// few single-precision instructions; sm_103a issues 58 single-precision
+// operations per double-precision one). Same tiling as the windowed mixed
+// stage (hsgn_fused.cuh): CTA p owns the tile [t0, t0 + sp) of rows and solves
+// the depth system on the window [t0 - HW, t0 + sp + HW), dropping the
+// coupling beyond it; the decay bound of that truncation is checked per CTA
+// against 2^-50 (the pairs carry about 2^-47), else HSGN_ERR_TRUNCATION.
+//
+// Increment form, as in the mixed stage but with the increments kept as pairs:
+//  * stage 1 (U_b = U_l = U^n) writes dU1 = U_I^(1) - U^n;
+//  * stage 2 forms U_l = U^n + (c/gamma) dU1 and U_b = U^n + ((1-gamma)/gamma) dU1
+//    on load and writes U^{n+1} = U_b + dU2 into the other state buffer;
+//  * the depth system A dh = d - A h_b is solved for the increment dh, so its
+//    rounding scales with the increment rather than with the depth.
+// Accuracy choices (each measured against the FP64 oracle: without them the
+// h w error per stage was 4e-13, with them under 1e-13):
+//  * differences of neighbouring values (flux differences, q^dag, m^dag, h_b and
+//    dh differences) use the cancellation-accurate sum add_acc;
+//  * hbar^2 - m_b = (h_b^2 - m_b) + dh (2 h_b + dh), with h_b^2 - m_b formed
+//    exactly (sq_minus), so that the relaxation update
+//    (hw)bar = r_b + dr + lambda tau (hbar^2 - m^)/(hbar^2 + lambda tau^2),
+//    which amplifies errors in hbar^2 - m by lambda tau, sees no rounding of hbar.
+// Mass: hbar = h_b + dh with dh from the window solve (no flux form): the
+// pairs' rounding of dh is 2^-47 of the increment, far below the 1e-13
+// conservation bound.
+#pragma once
+
+#include "hsgn_fused.cuh"
+#include "hsgn_dfloat.cuh"
+
+namespace hsgn {
+
+// The block elimination of hsgn_tridiag.cuh instantiated for pairs needs these.
+__device__ __forceinline__ bool pos_finite(dfl x) { return pos_finite(x.hi); }
+__device__ __forceinline__ dfl shfl_up_d(dfl x, int s) {
+    return dfl(__shfl_up_sync(0xffffffffu, x.hi, s), __shfl_up_sync(0xffffffffu, x.lo, s));
+}
+__device__ __forceinline__ dfl shfl_down_d(dfl x, int s) {
+    return dfl(__shfl_down_sync(0xffffffffu, x.hi, s), __shfl_down_sync(0xffffffffu, x.lo, s));
+}
+__device__ __forceinline__ dfl shfl_xor_d(dfl x, int s) {
+    return dfl(__shfl_xor_sync(0xffffffffu, x.hi, s), __shfl_xor_sync(0xffffffffu, x.lo, s));
+}
+
+// A shared-memory array of pairs, high and low parts in separate planes so
+// that four consecutive entries are two 128-bit loads (lanes 16 bytes apart:
+// no bank conflicts).
+template <int NC>
+struct DArr {
+    float hi[NC], lo[NC];
+    __device__ __forceinline__ dfl get(int i) const { return dfl(hi[i], lo[i]); }
+    __device__ __forceinline__ void set(int i, dfl v) {
+        hi[i] = v.hi;
+        lo[i] = v.lo;
+    }
+    // entries i .. i+3 (i a multiple of 4)
+    __device__ __forceinline__ void get4(int i, dfl* v) const {
+        const float4 h = *reinterpret_cast<const float4*>(hi + i);
+        const float4 l = *reinterpret_cast<const float4*>(lo + i);
+        v[0] = dfl(h.x, l.x);
+        v[1] = dfl(h.y, l.y);
+        v[2] = dfl(h.z, l.z);
+        v[3] = dfl(h.w, l.w);
+    }
+    __device__ __forceinline__ void set4(int i, const dfl* v) {
+        *reinterpret_cast<float4*>(hi + i) = make_float4(v[0].hi, v[1].hi, v[2].hi, v[3].hi);
+        *reinterpret_cast<float4*>(lo + i) = make_float4(v[0].lo, v[1].lo, v[2].lo, v[3].lo);
+    }
+};
+
+// Geometry: T threads, M = 4 rows per thread, overlap HW (as FusedGeom).
+template <int T, int M, int HW>
+struct DfGeom {
+    static constexpr int R = T * M - 2;          // window rows (one identity row closes it)
+    static constexpr int S = R - 2 * HW;         // largest tile
+    static constexpr int HB = HW - 1;            // rows between a kept row and the window edge
+    static constexpr int NC = (R + 6 + 3) & ~3;  // cells -3 .. W+2 at c + 3
+    static_assert(M == 4, "four cells per thread");
+    static_assert(S > 0, "overlap too wide for the window");
+};
+
+// Shared memory. Cell c of the window at c + 3 in the state arrays, at c + 1
+// in the per-cell arrays; face jf (between window cells jf - 2 and jf - 1) at
+// jf. After the cell phase the U_l arrays and two flux arrays are reused:
+// dq -> hl, dm^ -> ql, dr -> ml, beta -> rl, delta -> fq; dh of row r -> fm at r + 4.
+template <int T, int M, int HW>
+struct DfShared {
+    static constexpr int NC = DfGeom<T, M, HW>::NC;
+    DArr<NC> hl, ql, ml, rl;  // U_l
+    DArr<NC> hb, qb, mb, rb;  // U_b
+    DArr<NC> fq, fm, fr;      // twice the Rusanov fluxes of q, h eta, h w
+    SepShared<T, dfl> sep;
+    unsigned kmax, kmin;      // bits of max / min tau^2 beta / dx^2 (positive floats order as integers)
+};
+
+struct DfParams {
+    int64_t n;
+    int32_t stage;        // 1: writes dU1; 2: writes U^{n+1} to out
+    int32_t local_speed;  // Rusanov speed max(|u^L|, |u^R|) per face instead of *speed
+    int32_t track_speed;  // stage 1 clears *speed_next, stage 2 folds max |u^{n+1}| into it
+    int32_t S;            // tile rows
+    // constants of the stage as pairs (tau = gamma dt): tau, lambda tau^2,
+    // lambda tau, tau/(2 dx), lambda tau/(2 dx), tau^2/dx^2, lambda tau^2/dx^2,
+    // g, lambda, lambda/3, 1/3, and the stage-2 weights c/gamma, (1-gamma)/gamma
+    dfl tau, lt2, ltau, fq, lfq, Cc, fd, g, lam, lam3, third, wl1, wb1;
+    const float2* U[4];   // U^n (pairs)
+    float2* D1[4];        // stage-1 increments dU1 (written by stage 1, read by stage 2)
+    float2* out[4];       // U^{n+1} (stage 2; not aliased with U)
+    const double* speed;  // global Rusanov speed of the step
+    double* speed_next;   // max |u^{n+1}|
+    unsigned* err;
+};
+
+template <int T, int M, int HW, int BC, int STAGE>
+__global__ void __launch_bounds__(T, 2) k_df_stage(const DfParams p) {
+    static_assert(STAGE == 1 || STAGE == 2, "two stages");
+    using Gm = DfGeom<T, M, HW>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    auto& sm = *reinterpret_cast<DfShared<T, M, HW>*>(smem_raw);
+    constexpr bool two = STAGE == 2;
+    const int tid = threadIdx.x;
+    const int64_t n = p.n;
+    const Window win = window_of<BC>(blockIdx.x, n, p.S, HW);
+    const int W = win.W;
+    const int64_t wl = win.wl;
+    if (tid == 0) {
+        sm.kmax = 0u;
+        sm.kmin = 0x7F7FFFFFu;
+    }
+    if (p.track_speed && !two && blockIdx.x == 0 && tid == 0) *p.speed_next = 0.0;
+
+    // ---- 0. window cells -3 .. W+2 (index c + 3): U_l and U_b (stage 2:
+    //         formed from U^n and dU1 with the efficient-form weights)
+    {
+        const bool inner = inner_window(wl, W, n);
+        constexpr int NL = (Gm::R + 6 + T - 1) / T;
+#pragma unroll
+        for (int it = 0; it < NL; ++it) {
+            const int j = tid + it * T;
+            if (j < W + 6) {
+                const int64_t gi = inner ? wl - 3 + j : cell_at<BC>(wl - 3 + j, n);
+                DArr<Gm::NC>* const L[4] = {&sm.hl, &sm.ql, &sm.ml, &sm.rl};
+                DArr<Gm::NC>* const B[4] = {&sm.hb, &sm.qb, &sm.mb, &sm.rb};
+#pragma unroll
+                for (int v = 0; v < 4; ++v) {
+                    const float2 a = __ldg(p.U[v] + gi);
+                    const dfl u(a.x, a.y);
+                    if constexpr (two) {
+                        const float2 d = __ldg(p.D1[v] + gi);
+                        const dfl dv(d.x, d.y);
+                        L[v]->set(j, fma(p.wl1, dv, u));
+                        B[v]->set(j, fma(p.wb1, dv, u));
+                    } else {
+                        L[v]->set(j, u);
+                        B[v]->set(j, u);
+                    }
+                }
+            }
+        }
+    }
+    __syncthreads();
+
+    unsigned bad = 0;
+    const int j0 = 4 * tid;
+    const dfl spd = p.local_speed ? dfl(0.f) : dfl_of(*p.speed);
+
+    // ---- A. twice the Rusanov fluxes of U_l (Sec. 4.1) at the faces
+    //         jf = 4t .. 4t+3 (face jf between window cells jf - 2 and jf - 1,
+    //         reconstructed from the cells at index jf .. jf + 3): centred
+    //         unlimited linear reconstruction of (h, q, h eta, h w),
+    //         u = q/h on either side, 2F = u^L X^L + u^R X^R - s (X^R - X^L)
+    {
+        dfl uL[4], uR[4], s[4];
+        {
+            dfl H[8], Q[8];
+            sm.hl.get4(j0, H);
+            sm.hl.get4(j0 + 4, H + 4);
+            sm.ql.get4(j0, Q);
+            sm.ql.get4(j0 + 4, Q + 4);
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const dfl hL = H[e + 1] + scale(H[e + 2] - H[e], 0.25f);
+                const dfl hR = H[e + 2] - scale(H[e + 3] - H[e + 1], 0.25f);
+                const dfl qL = Q[e + 1] + scale(Q[e + 2] - Q[e], 0.25f);
+                const dfl qR = Q[e + 2] - scale(Q[e + 3] - Q[e + 1], 0.25f);
+                if (j0 + e < W + 3 && !(pos_finite(hL) && pos_finite(hR))) bad |= HSGN_DEV_ERR_DEPTH;
+                uL[e] = qL / hL;
+                uR[e] = qR / hR;
+                s[e] = p.local_speed ? dmax(dabs(uL[e]), dabs(uR[e])) : spd;
+            }
+        }
+        DArr<Gm::NC>* const X[3] = {&sm.ql, &sm.ml, &sm.rl};
+        DArr<Gm::NC>* const F[3] = {&sm.fq, &sm.fm, &sm.fr};
+#pragma unroll
+        for (int v = 0; v < 3; ++v) {
+            dfl Xv[8];
+            X[v]->get4(j0, Xv);
+            X[v]->get4(j0 + 4, Xv + 4);
+            dfl Fv[4];
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const dfl xL = Xv[e + 1] + scale(Xv[e + 2] - Xv[e], 0.25f);
+                const dfl xR = Xv[e + 2] - scale(Xv[e + 3] - Xv[e + 1], 0.25f);
+                Fv[e] = fma(uL[e], xL, uR[e] * xR) - s[e] * (xR - xL);
+            }
+            F[v]->set4(j0, Fv);
+        }
+    }
+    __syncthreads();
+
+    // ---- B. per cell c = j - 1, j = 4t .. 4t+3 (c = -1 .. W are formed):
+    //         increments of the starred values (lines 1-3 of the scheme, the
+    //         lambda tau and lambda tau^2 terms kept apart),
+    //           dr = -tau/dx (F^r_{c+1/2} - F^r_{c-1/2}),        r^dag = r_b + dr + lambda tau
+    //           dm^ = tau (r_b + dr) - tau/dx (F^m ...),         m^dag = m_b + dm^ + lambda tau^2
+    //           dq = -tau/dx (F^q ...),                          q^dag = q_b + dq
+    //         and the coefficients of U_l (eq. (eq:hSGN_alpha) and the scheme):
+    //           eta = m/h, alpha = -(2 eta/h - 1)/(3h), c^2 = g h + (lambda/3) eta^2/h^2,
+    //           a^2 = c^2 - lambda eta alpha, beta_1 = 1 + lambda tau^2/h^2,
+    //           beta_2 = 2 lambda tau^2/(beta_1^2 h^3), beta = a^2 + lambda alpha beta_2 m^dag,
+    //           delta = alpha/beta_1
+    dfl dq_[4], dm_[4], dr_[4], be_[4], de_[4];
+    float kloc = 0.f, kmin = 3.0e38f;
+    {
+        dfl FQ[8], FM[8], FR[8];
+        sm.fq.get4(j0, FQ);
+        sm.fq.get4(j0 + 4, FQ + 4);
+        sm.fm.get4(j0, FM);
+        sm.fm.get4(j0 + 4, FM + 4);
+        sm.fr.get4(j0, FR);
+        sm.fr.get4(j0 + 4, FR + 4);
+        dfl HL[8], ML[8], MB[8], RB[8];
+        sm.hl.get4(j0, HL);
+        sm.hl.get4(j0 + 4, HL + 4);
+        sm.ml.get4(j0, ML);
+        sm.ml.get4(j0 + 4, ML + 4);
+        sm.mb.get4(j0, MB);
+        sm.mb.get4(j0 + 4, MB + 4);
+        sm.rb.get4(j0, RB);
+        sm.rb.get4(j0 + 4, RB + 4);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            dq_[k] = dm_[k] = dr_[k] = be_[k] = de_[k] = dfl(0.f);
+            if (j0 + k < W + 2) {
+                const dfl dr = -(p.fq * sub_acc(FR[k + 1], FR[k]));
+                const dfl dm = fma(p.tau, RB[k + 2] + dr, -(p.fq * sub_acc(FM[k + 1], FM[k])));
+                const dfl dq = -(p.fq * sub_acc(FQ[k + 1], FQ[k]));
+                const dfl ms = (MB[k + 2] + dm) + p.lt2;
+                const dfl h = HL[k + 2];
+                if (!pos_finite(h)) bad |= HSGN_DEV_ERR_DEPTH;
+                const dfl ih = rcp(h);
+                const dfl eta = ML[k + 2] * ih;
+                const dfl e = eta * ih;
+                const dfl alpha = -(add_f(scale(e, 2.f), -1.f) * ih * p.third);
+                const dfl c2 = fma(p.g, h, p.lam3 * (e * e));
+                const dfl a2 = c2 - p.lam * (eta * alpha);
+                const dfl h2 = h * h;
+                const dfl iD = rcp(h2 + p.lt2);       // 1/(beta_1 h^2)
+                const dfl ib1 = h2 * iD;              // 1/beta_1
+                const dfl beta2 = scale(p.lt2, 2.f) * (h * (iD * iD));
+                const dfl beta = fma(p.lam * alpha, beta2 * ms, a2);
+                if (!pos_finite(beta)) bad |= HSGN_DEV_ERR_COERCIVE;
+                dq_[k] = dq;
+                dm_[k] = dm;
+                dr_[k] = dr;
+                be_[k] = beta;
+                de_[k] = alpha * ib1;
+                const float kb = f_mul(p.Cc.hi, beta.hi);
+                kloc = fmaxf(kloc, kb);
+                kmin = fminf(kmin, kb);
+            }
+        }
+    }
+    __syncthreads();
+    DArr<Gm::NC>& DQ = sm.hl;
+    DArr<Gm::NC>& DM = sm.ql;
+    DArr<Gm::NC>& DR = sm.ml;
+    DArr<Gm::NC>& BE = sm.rl;
+    DArr<Gm::NC>& DE = sm.fq;
+    DArr<Gm::NC>& DH = sm.fm;
+    DQ.set4(j0, dq_);
+    DM.set4(j0, dm_);
+    DR.set4(j0, dr_);
+    BE.set4(j0, be_);
+    DE.set4(j0, de_);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        kloc = fmaxf(kloc, __shfl_xor_sync(0xffffffffu, kloc, o));
+        kmin = fminf(kmin, __shfl_xor_sync(0xffffffffu, kmin, o));
+    }
+    if ((tid & 31) == 0) {
+        if (pos_finite(kloc)) atomicMax(&sm.kmax, __float_as_uint(kloc));
+        if (pos_finite(kmin)) atomicMin(&sm.kmin, __float_as_uint(kmin));
+    }
+    __syncthreads();
+    if (BC == BC_TRANSMISSIVE && (win.lend || win.rend)) {  // (uniform over the CTA)
+        // zero-order ghost copies of the per-cell values at the domain ends
+        if (tid == 0 && win.lend) {
+            DQ.set(0, DQ.get(1)); DM.set(0, DM.get(1)); DR.set(0, DR.get(1));
+            BE.set(0, BE.get(1)); DE.set(0, DE.get(1));
+        }
+        if (tid == 0 && win.rend) {
+            const int a = W + 1, c = W;
+            DQ.set(a, DQ.get(c)); DM.set(a, DM.get(c)); DR.set(a, DR.get(c));
+            BE.set(a, BE.get(c)); DE.set(a, DE.get(c));
+        }
+        __syncthreads();
+    }
+
+    // ---- C. rows i = 4t .. 4t+3 of A dh = d - A h_b (lines 8-10 of the
+    //         scheme in increment form; interface values are means, reading
+    //         R2, and the delta term carries factor 1 with means, reading R3):
+    //           coupling of face f (rows f-1, f): K_f = tau^2/dx^2 beta_f
+    //             (zero across a transmissive domain end: Neumann rows);
+    //           Phi_f = lambda tau^2/dx^2 delta_f (m^dag_f - m^dag_{f-1}) + K_f (h_b,f - h_b,f-1);
+    //           d_i - (A h_b)_i = -tau/(2 dx) (q^dag_{i+1} - q^dag_{i-1}) + Phi_{i+1} - Phi_i.
+    dfl KF[5], rd[4];
+    {
+        dfl Phi[5];
+        {
+            dfl B8[8], E8[8];
+            BE.get4(j0, B8);
+            BE.get4(j0 + 4, B8 + 4);
+            DE.get4(j0, E8);
+            DE.get4(j0 + 4, E8 + 4);
+            dfl M8[8], MU[8], H8[8];
+            DM.get4(j0, M8);
+            DM.get4(j0 + 4, M8 + 4);
+            sm.mb.get4(j0, MU);
+            sm.mb.get4(j0 + 4, MU + 4);
+            sm.hb.get4(j0, H8);
+            sm.hb.get4(j0 + 4, H8 + 4);
+#pragma unroll
+            for (int e = 0; e < 5; ++e) {
+                const int f = j0 + e;  // rows f - 1 | f: per-cell index f, f + 1; state f + 2, f + 3
+                const dfl bf = scale(B8[e] + B8[e + 1], 0.5f);
+                const dfl df = scale(E8[e] + E8[e + 1], 0.5f);
+                dfl kf = p.Cc * bf;
+                if (BC == BC_TRANSMISSIVE && ((f == 0 && win.lend) || (f == W && win.rend)))
+                    kf = dfl(0.f);
+                const dfl dmf = sub_acc(MU[e + 3], MU[e + 2]) + sub_acc(M8[e + 1], M8[e]);
+                const dfl dhf = sub_acc(H8[e + 3], H8[e + 2]);
+                KF[e] = kf;
+                Phi[e] = fma(p.fd * df, dmf, kf * dhf);
+            }
+        }
+        dfl Q8[8], QU[8];
+        DQ.get4(j0, Q8);
+        DQ.get4(j0 + 4, Q8 + 4);
+        sm.qb.get4(j0, QU);
+        sm.qb.get4(j0 + 4, QU + 4);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            // q^dag of cells i+1 and i-1: state index i + 4, i + 2; per-cell index i + 2, i
+            const dfl dqc = sub_acc(QU[k + 4], QU[k + 2]) + sub_acc(Q8[k + 2], Q8[k]);
+            rd[k] = sub_acc(Phi[k + 1], Phi[k]) - p.fq * dqc;
+        }
+    }
+    {
+        // row 4t + k of the window; the first / last window row drops its outer
+        // coupling; the rows from W on close the window (identity)
+        auto roww = [&](int k, int i, dfl& a, dfl& bb, dfl& c, dfl& d) {
+            if (i >= W) {
+                a = dfl(0.f); bb = dfl(1.f); c = dfl(0.f); d = dfl(0.f);
+                return;
+            }
+            const dfl kl = KF[k], kr = KF[k + 1];
+            a = (i == 0 && !win.lend) ? dfl(0.f) : -kl;
+            c = (i == W - 1 && !win.rend) ? dfl(0.f) : -kr;
+            bb = add_f(kl + kr, 1.f);
+            d = rd[k];
+        };
+        dfl y[M], v[M], w[M], last[4];
+        int cs, m;
+        cta_block_solve_fixed<T, M>(W + 1, roww, sm.sep, y, v, w, cs, m, last, p.err);
+        // dh = y: the values outside the window (and the closing row) are taken as 0
+#pragma unroll
+        for (int k = 0; k < M; ++k)
+            if (!(k < m && cs + k < W)) y[k] = dfl(0.f);
+        DH.set4(j0 + 4, y);
+    }
+    __syncthreads();
+    if (BC == BC_TRANSMISSIVE && (win.lend || win.rend)) {  // (uniform over the CTA)
+        if (tid == 0 && win.lend) DH.set(3, DH.get(4));
+        if (tid == 0 && win.rend) DH.set(W + 4, DH.get(W + 3));
+        __syncthreads();
+    }
+    // truncation bound of this window: rho*^HB <= 2^-50
+    if (tid == 0) {
+        const bool cut = BC == BC_PERIODIC || !(win.lend && win.rend);
+        const float K = __uint_as_float(sm.kmax), kap = fminf(__uint_as_float(sm.kmin), K);
+        if (cut && K > 0.f) {
+            const float Bq = 1.f + K + kap;
+            const float rho = 2.f * K / (Bq + sqrtf(fmaxf(Bq * Bq - 4.f * kap * K, 0.f)));
+            if ((float)Gm::HB * __log2f(rho) > -50.f) bad |= HSGN_DEV_ERR_TRUNCATION;
+        }
+    }
+
+    // ---- E. back-substitution of the tile rows (lines 11-13 of the scheme;
+    //         h w with h^2 implicit, Sec. 6.3.1), in increment form:
+    //           dQ = dq - tau/(2dx) beta (hbar_{i+1} - hbar_{i-1})
+    //                   - lambda tau/(2dx) delta (m^dag_{i+1} - m^dag_{i-1}),
+    //           P = hbar^2 - m_b, E = hbar^2 - m^ = P - dm^, D = hbar^2 + lambda tau^2,
+    //           (h eta)bar - m_b = P - E hbar^2/D,  (h w)bar - r_b = dr + lambda tau E/D
+    //         (m^dag hbar^2/D and r^dag - lambda tau (h eta)bar/hbar^2 without the
+    //         cancellation of their lambda tau terms)
+    const int lo = win.lo, sp = win.sp;
+    const int64_t t0 = win.t0;
+    dfl umax(0.f);
+    for (int t = tid; t < sp; t += T) {
+        const int r = lo + t;  // window row; state index r + 3, per-cell index r + 1, dh index r + 4
+        const dfl dh = DH.get(r + 4);
+        const dfl hb = sm.hb.get(r + 3), mb = sm.mb.get(r + 3);
+        const dfl dhc = sub_acc(sm.hb.get(r + 4), sm.hb.get(r + 2)) +
+                        sub_acc(DH.get(r + 5), DH.get(r + 3));
+        const dfl dmv = DM.get(r + 1);
+        const dfl dmc = sub_acc(sm.mb.get(r + 4), sm.mb.get(r + 2)) +
+                        sub_acc(DM.get(r + 2), DM.get(r));
+        const dfl dQ = DQ.get(r + 1) - (p.fq * (BE.get(r + 1) * dhc) + p.lfq * (DE.get(r + 1) * dmc));
+        const dfl P = sq_minus(hb, mb) + dh * (scale(hb, 2.f) + dh);
+        const dfl E = P - dmv;
+        const dfl hbar = hb + dh;
+        const dfl h2 = hbar * hbar;
+        const dfl iDen = rcp(h2 + p.lt2);
+        const dfl Ei = E * iDen;
+        const dfl dR = fma(p.ltau, Ei, DR.get(r + 1));
+        const dfl dM = P - Ei * h2;
+        unsigned b2 = 0;
+        if (!pos_finite(hbar)) b2 |= HSGN_DEV_ERR_DEPTH;
+        if (!isfinite(dQ.hi) || !isfinite(dM.hi) || !isfinite(dR.hi)) b2 |= HSGN_DEV_ERR_NONFINITE;
+        bad |= b2;
+        const int64_t gc = t0 + t;
+        if constexpr (!two) {
+            p.D1[0][gc] = make_float2(dh.hi, dh.lo);
+            p.D1[1][gc] = make_float2(dQ.hi, dQ.lo);
+            p.D1[2][gc] = make_float2(dM.hi, dM.lo);
+            p.D1[3][gc] = make_float2(dR.hi, dR.lo);
+        } else {
+            const dfl qn = sm.qb.get(r + 3) + dQ;
+            const dfl mn = mb + dM;
+            const dfl rn = sm.rb.get(r + 3) + dR;
+            p.out[0][gc] = make_float2(hbar.hi, hbar.lo);
+            p.out[1][gc] = make_float2(qn.hi, qn.lo);
+            p.out[2][gc] = make_float2(mn.hi, mn.lo);
+            p.out[3][gc] = make_float2(rn.hi, rn.lo);
+            if (p.track_speed && !b2) umax = dmax(umax, dabs(qn) / hbar);
+        }
+    }
+    if (bad) flag_error(p.err, bad);
+    if (p.track_speed && two) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) umax = dmax(umax, shfl_xor_d(umax, o));
+        if ((tid & 31) == 0 && umax.hi > 0.f)
+            atomicMax(reinterpret_cast<unsigned long long*>(p.speed_next),
+                      (unsigned long long)__double_as_longlong(dfl_to_double(umax)));
+    }
+}
+
+// Pairs of base and lin - base (hsgn_stage on the double-float form): the
+// stage-2 kernel with weights 1 and 0 then runs the stage from U_b = base,
+// U_l = lin.
+__global__ void k_df_stage_inputs(int64_t n, const double* __restrict__ base,
+                                  const double* __restrict__ lin, float2* __restrict__ ub,
+                                  float2* __restrict__ dl) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const double b = base[i];
+        ub[i] = df_of(b);
+        dl[i] = df_of(lin[i] - b);
+    }
+}
+
+// Pairs to doubles in place (the pair and the double of entry i share its 8 bytes).
+__global__ void k_f64_from_df_inplace(int64_t n, void* buf) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const float2 v = reinterpret_cast<const float2*>(buf)[i];
+        reinterpret_cast<double*>(buf)[i] = (double)v.x + (double)v.y;
+    }
+}
+
+}  // namespace hsgn

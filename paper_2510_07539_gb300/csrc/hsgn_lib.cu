@@ -17,6 +17,7 @@
 #include "hsgn_kernels.cuh"
 #include "hsgn_fused.cuh"
 #include "hsgn_adjoint.cuh"
+#include "hsgn_dfstage.cuh"
 
 using namespace hsgn;
 
@@ -31,6 +32,10 @@ static_assert(XT * XM == AS, "both precision forms use the same block split");
 constexpr int OT = 256, OM = 16;
 // Windowed mixed stage: FT threads, FM rows per thread, FHW overlap rows.
 constexpr int FT = 256, FM = 4, FHW = 64;
+// Double-float windowed stage: DT threads, FM rows per thread, DHW overlap rows
+// (wider than the mixed stage's: the truncation bound is 2^-50, not 2^-30, and
+// 95 rows keep it up to CFL_IMEX of about 7 for smooth states).
+constexpr int DT = 256, DHW = 96;
 // Small variant of the windowed stage for batches (tiles of 382 rows instead of
 // 894), chosen per instance by hsgn_batched_set_tiles / hsgn_batched_autotune.
 constexpr int FTS = 128;
@@ -165,6 +170,9 @@ struct hsgn_s {
     bool mixed = false;
     float *G1 = nullptr, *dq1 = nullptr, *dm1 = nullptr, *dr1 = nullptr;
     float4* mrec = nullptr;          // three float4 records per row
+    // double-float windowed stage (HSGN_DOUBLE_FLOAT): stage-1 increments as pairs
+    bool dfloat = false;
+    float2* D1[4] = {};
     // batch (hsgn_create_batched)
     int32_t count = 1;
     bool batched = false;
@@ -513,6 +521,85 @@ cudaError_t launch_stage_fused(hsgn_s* H, int stage, double tau, cudaStream_t st
     return cudaGetLastError();
 }
 
+// One launch of the double-float stage kernel specialised for p.stage.
+template <int BC>
+void launch_df(unsigned P, const DfParams& p, cudaStream_t st) {
+    const size_t smem = sizeof(DfShared<DT, FM, DHW>);
+    if (p.stage == 2)
+        k_df_stage<DT, FM, DHW, BC, 2><<<P, DT, smem, st>>>(p);
+    else
+        k_df_stage<DT, FM, DHW, BC, 1><<<P, DT, smem, st>>>(p);
+}
+
+template <int BC>
+cudaError_t set_smem_df() {
+    const size_t smem = sizeof(DfShared<DT, FM, DHW>);
+    cudaError_t e = set_smem(k_df_stage<DT, FM, DHW, BC, 1>, smem);
+    if (e == cudaSuccess) e = set_smem(k_df_stage<DT, FM, DHW, BC, 2>, smem);
+    return e;
+}
+
+// Constants of a double-float stage of step tau; stage 2 gets the efficient-form
+// weights (wl1, wb1) unless given.
+DfParams df_params(const hsgn_s* H, int stage, double tau, double wl1, double wb1) {
+    DfParams p;
+    p.n = H->n;
+    p.stage = stage;
+    p.local_speed = local_speed(H) ? 1 : 0;
+    p.track_speed = local_speed(H) ? 0 : 1;
+    p.S = H->tileS;
+    const double dx = H->dx, lam = H->lam;
+    p.tau = dfl_of(tau);
+    p.lt2 = dfl_of(lam * tau * tau);
+    p.ltau = dfl_of(lam * tau);
+    p.fq = dfl_of(tau / (2.0 * dx));
+    p.lfq = dfl_of(lam * tau / (2.0 * dx));
+    p.Cc = dfl_of(tau * tau / (dx * dx));
+    p.fd = dfl_of(lam * tau * tau / (dx * dx));
+    p.g = dfl_of(H->g);
+    p.lam = dfl_of(lam);
+    p.lam3 = dfl_of(lam / 3.0);
+    p.third = dfl_of(1.0 / 3.0);
+    p.wl1 = dfl_of(wl1);
+    p.wb1 = dfl_of(wb1);
+    for (int k = 0; k < 4; ++k) {
+        p.U[k] = nullptr;
+        p.D1[k] = H->D1[k];
+        p.out[k] = nullptr;
+    }
+    p.speed = nullptr;
+    p.speed_next = nullptr;
+    p.err = H->err;
+    return p;
+}
+
+unsigned df_tiles(const hsgn_s* H) { return (unsigned)((H->n + H->tileS - 1) / H->tileS); }
+
+// One stage of the double-float path (hsgn_dfstage.cuh): one launch. Stage 1
+// writes the increments dU1, stage 2 writes U^{n+1} into the other buffer.
+cudaError_t launch_stage_df(hsgn_s* H, int stage, double tau, cudaStream_t st) {
+    const double gam = 1.0 - 1.0 / std::sqrt(2.0);
+    const double c = 1.0 / (2.0 * gam);
+    DfParams p = df_params(H, stage, tau, stage == 2 ? c / gam : 0.0,
+                           stage == 2 ? (1.0 - gam) / gam : 0.0);
+    double* const* Uc = state(H);
+    double* const* Un = H->cur ? H->U : H->V;
+    for (int k = 0; k < 4; ++k) {
+        p.U[k] = reinterpret_cast<const float2*>(Uc[k]);
+        p.out[k] = stage == 2 ? reinterpret_cast<float2*>(Un[k]) : nullptr;
+    }
+    p.speed = speed_of(H, H->cur);
+    p.speed_next = speed_of(H, 1 - H->cur);
+    {
+        ProfScope ps(H, HSGN_PROF_ASSEMBLE, st);
+        if (H->bc == BC_PERIODIC)
+            launch_df<BC_PERIODIC>(df_tiles(H), p, st);
+        else
+            launch_df<BC_TRANSMISSIVE>(df_tiles(H), p, st);
+    }
+    return cudaGetLastError();
+}
+
 // Explicit operator (k_explicit): out1 = a1 U0 + b1 Us + c1 L(Us), optional out2.
 cudaError_t launch_explicit(hsgn_s* H, const double* const Us[4], const double* const U0[4],
                             double a1, double b1, double c1, double* const out1[4],
@@ -612,6 +699,12 @@ cudaError_t enqueue_step(hsgn_s* H, double dt, cudaStream_t st) {
     const double gam = 1.0 - 1.0 / std::sqrt(2.0);
     const double c = 1.0 / (2.0 * gam);
     const double tau = gam * dt;
+    if (H->dfloat) {
+        cudaError_t e = launch_stage_df(H, 1, tau, st);
+        if (e == cudaSuccess) e = launch_stage_df(H, 2, tau, st);
+        if (e == cudaSuccess) H->cur ^= 1;
+        return e;
+    }
     if (H->windowed) {
         cudaError_t e = launch_stage_fused(H, 1, tau, st);
         if (e == cudaSuccess) e = launch_stage_fused(H, 2, tau, st);
@@ -703,7 +796,8 @@ cudaError_t refresh_speed(hsgn_s* H, cudaStream_t st) {
             e = cudaMemcpyAsync(out, out + 1, sizeof(double), cudaMemcpyDeviceToDevice, st);
         return e;
     }
-    if (H->windowed) {
+    if (H->windowed && !H->dfloat) {
+        // (the double-float form takes max |u| in double precision below)
         double* const* U = state(H);
         k_umax_df<<<convert_blocks(H), 256, 0, st>>>(H->n, reinterpret_cast<const float2*>(U[0]),
                                                      reinterpret_cast<const float2*>(U[1]), out,
@@ -790,7 +884,11 @@ int hsgn_create(const hsgn_grid_t* grid, double g, double lambda, const double* 
     if (!(g > 0.0) || !std::isfinite(g) || !(lambda >= 0.0) || !std::isfinite(lambda))
         return HSGN_ERR_INVALID_ARG;
     if (flags & ~(int32_t)(HSGN_RUSANOV_LOCAL | HSGN_MIXED | HSGN_WELL_BALANCED | HSGN_EXACT_SOLVE |
-                           HSGN_SCHEME_MASK))
+                           HSGN_DOUBLE_FLOAT | HSGN_SCHEME_MASK))
+        return HSGN_ERR_UNIMPLEMENTED;
+    // the double-float form: the paper's scheme, flat bottom, on its own
+    if ((flags & HSGN_DOUBLE_FLOAT) &&
+        (flags & (HSGN_MIXED | HSGN_EXACT_SOLVE | HSGN_WELL_BALANCED | HSGN_SCHEME_MASK)))
         return HSGN_ERR_UNIMPLEMENTED;
     const int32_t scheme = flags & HSGN_SCHEME_MASK;
     if (scheme > HSGN_SCHEME_EX_EULER) return HSGN_ERR_INVALID_ARG;
@@ -840,13 +938,15 @@ int hsgn_create(const hsgn_grid_t* grid, double g, double lambda, const double* 
     const int64_t n = H->n, P = H->split.P;
 
     H->mixed = (flags & HSGN_MIXED) != 0;
-    H->windowed = H->mixed && !(flags & HSGN_EXACT_SOLVE);
+    H->dfloat = (flags & HSGN_DOUBLE_FLOAT) != 0;
+    H->windowed = (H->mixed && !(flags & HSGN_EXACT_SOLVE)) || H->dfloat;
     H->wb = (flags & HSGN_WELL_BALANCED) != 0;
     H->scheme = scheme;
     const size_t vec = align_up(n * sizeof(double));
     const size_t fvec = align_up((n + 1) * sizeof(float));
     const size_t recb = align_up(3 * n * sizeof(float4));
-    size_t total = H->windowed ? 8 * vec + 4 * fvec            // U, V; G1 dq1 dm1 dr1
+    size_t total = H->dfloat   ? 12 * vec                      // U, V; dU1 (pairs)
+                   : H->windowed ? 8 * vec + 4 * fvec            // U, V; G1 dq1 dm1 dr1
                    : H->mixed  ? 4 * vec + 4 * fvec + recb     // U; G1 dq1 dm1 dr1; row records
                                : 16 * vec;                     // U, U1, y v w, 5 back-sub arrays
     if (H->wb) total += H->windowed ? vec : (bathymetry ? 2 : 1) * vec;  // pairs; Phi, bottom
@@ -866,7 +966,10 @@ int hsgn_create(const hsgn_grid_t* grid, double g, double lambda, const double* 
         return r;
     };
     for (int k = 0; k < 4; ++k) H->U[k] = reinterpret_cast<double*>(take(vec));
-    if (H->windowed) {
+    if (H->dfloat) {
+        for (int k = 0; k < 4; ++k) H->V[k] = reinterpret_cast<double*>(take(vec));
+        for (int k = 0; k < 4; ++k) H->D1[k] = reinterpret_cast<float2*>(take(vec));
+    } else if (H->windowed) {
         for (int k = 0; k < 4; ++k) H->V[k] = reinterpret_cast<double*>(take(vec));
         H->G1 = reinterpret_cast<float*>(take(fvec));
         H->dq1 = reinterpret_cast<float*>(take(fvec));
@@ -908,7 +1011,19 @@ int hsgn_create(const hsgn_grid_t* grid, double g, double lambda, const double* 
     H->err = reinterpret_cast<unsigned*>(take(align_up(sizeof(unsigned))));
 
     cudaError_t e = cudaMemset(H->mem, 0, total);
-    if (e == cudaSuccess && H->windowed) {
+    if (e == cudaSuccess && H->dfloat) {
+        e = set_smem_df<BC_PERIODIC>();
+        if (e == cudaSuccess) e = set_smem_df<BC_TRANSMISSIVE>();
+        int sms = 0, per_sm = 0;
+        if (e == cudaSuccess)
+            e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, H->device);
+        if (e == cudaSuccess)
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                &per_sm, k_df_stage<DT, FM, DHW, BC_PERIODIC, 2>, DT, sizeof(DfShared<DT, FM, DHW>));
+        const int64_t slots = (int64_t)(sms > 0 ? sms : 1) * (per_sm > 0 ? per_sm : 1);
+        H->tileS = (int32_t)fused_tile_rows(n, DfGeom<DT, FM, DHW>::S, slots);
+        H->tileSlots = (int32_t)slots;
+    } else if (e == cudaSuccess && H->windowed) {
         e = set_smem_fused<FT, BC_PERIODIC, false>();
         if (e == cudaSuccess) e = set_smem_fused<FT, BC_TRANSMISSIVE, false>();
         if (e == cudaSuccess) e = set_smem_fused<FT, BC_PERIODIC, true>();
@@ -1177,6 +1292,31 @@ int hsgn_stage(hsgn_handle_t H, const double* const base[4], const double* const
     for (int k = 0; k < 4; ++k)
         if (!base[k] || !lin[k] || !out[k]) return HSGN_ERR_INVALID_ARG;
     cudaStream_t st = as_stream(stream);
+    if (H->dfloat) {
+        // the stage-2 kernel with weights 1 and 0 from U_b = base (pairs, in the
+        // idle state buffer) and U_l - U_b (pairs, in the increment buffers);
+        // the pairs are written into `out` and converted to doubles in place
+        double* const* idle = H->cur ? H->U : H->V;
+        for (int k = 0; k < 4; ++k)
+            k_df_stage_inputs<<<convert_blocks(H), 256, 0, st>>>(
+                H->n, base[k], lin[k], reinterpret_cast<float2*>(idle[k]), H->D1[k]);
+        double* spd = H->spd + 1;
+        k_set_scalar<<<1, 1, 0, st>>>(spd, speed);
+        DfParams p = df_params(H, 2, tau, 1.0, 0.0);
+        p.track_speed = 0;
+        for (int k = 0; k < 4; ++k) {
+            p.U[k] = reinterpret_cast<const float2*>(idle[k]);
+            p.out[k] = reinterpret_cast<float2*>(out[k]);
+        }
+        p.speed = spd;
+        if (H->bc == BC_PERIODIC)
+            launch_df<BC_PERIODIC>(df_tiles(H), p, st);
+        else
+            launch_df<BC_TRANSMISSIVE>(df_tiles(H), p, st);
+        for (int k = 0; k < 4; ++k)
+            k_f64_from_df_inplace<<<convert_blocks(H), 256, 0, st>>>(H->n, out[k]);
+        return cudaGetLastError() == cudaSuccess ? HSGN_OK : HSGN_ERR_CUDA;
+    }
     k_set_scalar<<<1, 1, 0, st>>>(H->spd + 1, speed);
     if (cudaGetLastError() != cudaSuccess) return HSGN_ERR_CUDA;
     // A = base, B = lin: U_l = lin, U_b = base
@@ -1881,6 +2021,77 @@ int hsgn_tridiag_solve(int64_t n, int32_t periodic, const double* a, const doubl
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Arithmetic peaks of the device (hsgn_fma_peak): independent fused
+// multiply-add chains, eight per thread, over every SM.
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr int kPeakChains = 8;
+
+template <class R>
+__global__ void __launch_bounds__(256) k_fma_peak(int iters, R b, R c, R* out) {
+    R a[kPeakChains];
+#pragma unroll
+    for (int k = 0; k < kPeakChains; ++k) a[k] = (R)(threadIdx.x + k) * (R)1e-3;
+    for (int i = 0; i < iters; ++i) {
+#pragma unroll
+        for (int k = 0; k < kPeakChains; ++k) a[k] = fma(a[k], b, c);
+    }
+    R s = 0;
+#pragma unroll
+    for (int k = 0; k < kPeakChains; ++k) s += a[k];
+    out[(size_t)blockIdx.x * blockDim.x + threadIdx.x] = s;  // keeps the chains live
+}
+
+template <class R>
+int fma_peak(double* tflops, cudaStream_t st) {
+    int dev = 0, sms = 0, per_sm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fma_peak<R>, 256, 0) !=
+            cudaSuccess) {
+        cudaGetLastError();
+        return HSGN_ERR_CUDA;
+    }
+    const unsigned blocks = (unsigned)(sms * (per_sm > 0 ? per_sm : 1));
+    // FP32 runs about 58 times as many operations per clock as FP64 on sm_103a:
+    // each timed run takes some tens of milliseconds (launch ramps negligible)
+    const int iters = sizeof(R) == 4 ? 1 << 18 : 1 << 14;
+    R* out = nullptr;
+    cudaEvent_t a = nullptr, b = nullptr;
+    int rc = HSGN_OK;
+    if (cudaMallocAsync(&out, (size_t)blocks * 256 * sizeof(R), st) != cudaSuccess ||
+        cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess) {
+        rc = HSGN_ERR_CUDA;
+    } else {
+        k_fma_peak<R><<<blocks, 256, 0, st>>>(iters / 8, (R)0.999, (R)1e-3, out);  // warm-up
+        cudaEventRecord(a, st);
+        k_fma_peak<R><<<blocks, 256, 0, st>>>(iters, (R)0.999, (R)1e-3, out);
+        cudaEventRecord(b, st);
+        float ms = 0.f;
+        if (cudaEventSynchronize(b) != cudaSuccess || cudaEventElapsedTime(&ms, a, b) != cudaSuccess ||
+            !(ms > 0.f))
+            rc = HSGN_ERR_CUDA;
+        else
+            *tflops = 2.0 * kPeakChains * (double)iters * blocks * 256 / (ms * 1e-3) / 1e12;
+    }
+    if (out) cudaFreeAsync(out, st);
+    if (a) cudaEventDestroy(a);
+    if (b) cudaEventDestroy(b);
+    if (cudaStreamSynchronize(st) != cudaSuccess) rc = HSGN_ERR_CUDA;
+    cudaGetLastError();
+    return rc;
+}
+
+}  // namespace
+
+extern "C" int hsgn_fma_peak(int32_t bits, double* tflops, void* stream) {
+    if (!tflops || (bits != 32 && bits != 64)) return HSGN_ERR_INVALID_ARG;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    return bits == 32 ? fma_peak<float>(tflops, st) : fma_peak<double>(tflops, st);
+}
 
 // ---------------------------------------------------------------------------
 // No-allocation variant of the tridiagonal solve (declared in include/hsgn.h).

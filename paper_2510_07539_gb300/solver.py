@@ -23,6 +23,7 @@ FLAG_MIXED = 0x1
 FLAG_RUSANOV_LOCAL = 0x10
 FLAG_WELL_BALANCED = 0x2
 FLAG_EXACT_SOLVE = 0x4
+FLAG_DOUBLE_FLOAT = 0x8
 # time-stepping schemes (flags & SCHEME_MASK)
 SCHEME_PRINTED, SCHEME_ARS222, SCHEME_SI1, SCHEME_EX_HEUN, SCHEME_EX_EULER = (
     0x000, 0x100, 0x200, 0x300, 0x400)
@@ -266,6 +267,18 @@ class GaugeMisfit(torch.autograd.Function):
     def backward(ctx, gJ):
         gh, gq, gm, gr, gb = ctx.saved_tensors
         return (gJ * gh, gJ * gq, gJ * gm, gJ * gr, gJ * gb) + (None,) * 9
+
+
+def fma_peak(bits: int, stream=None) -> float:
+    """Measured fused multiply-add throughput of the current device in
+    TFLOP/s, single (32) or double (64) precision (hsgn_fma_peak)."""
+    lib = load()
+    f = lib.hsgn_fma_peak
+    f.argtypes = [ctypes.c_int32, ctypes.POINTER(_D), _P]
+    f.restype = ctypes.c_int
+    out = _D()
+    _check(f(int(bits), ctypes.byref(out), _stream(stream)), "hsgn_fma_peak")
+    return out.value
 
 
 def tridiag_workspace_bytes(n: int) -> int:

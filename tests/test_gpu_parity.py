@@ -1,6 +1,8 @@
 """GPU parity: the CUDA library (through its C ABI) against the FP64 CPU oracle.
 
-Element-by-element comparison on identical seeded inputs. Tolerances:
+Element-by-element comparison on identical seeded inputs. The FP64-class
+tests run both forms that carry the FP64 bar: the FP64 form and the
+double-float form (HSGN_DOUBLE_FLOAT), with the same tolerances. Tolerances:
   * tridiagonal solve: 1e-13 relative to max |x| (different elimination order,
     condition number of the hSGN depth matrix is below about 100);
   * one stage / one step: 1e-12 relative L2 per variable;
@@ -34,6 +36,11 @@ def _cuda():
 def S():
     from paper_2510_07539_gb300 import solver
     return solver
+
+
+# the forms held to the FP64 bar: FP64 arithmetic, and double-float pairs
+# (flags 0x0 and HSGN_DOUBLE_FLOAT)
+FP64_FORMS = [pytest.param(0x0, id="fp64"), pytest.param(0x8, id="dfloat")]
 
 
 def dev(a):
@@ -88,14 +95,15 @@ def test_tridiag_strong_coupling():
 # --------------------------------------------------------------------------
 # one stage (hsgn_stage) with U_b != U_l
 # --------------------------------------------------------------------------
+@pytest.mark.parametrize("form", FP64_FORMS)
 @pytest.mark.parametrize("bc", [0, 1])
 @pytest.mark.parametrize("n", [3, 4, 7, 64, 511, 512, 513, 1000, 5000, 70001])
-def test_stage_matches_oracle(n, bc):
+def test_stage_matches_oracle(n, bc, form):
     dx, lam, tau, speed = 0.1, 300.0, 0.01, 0.37
     Ub = inputs.random_state(1000 + n, n, dx)
     Ul = inputs.random_state(2000 + n, n, dx, h_var=0.1)
     for local in (0, 1):
-        flags = S().FLAG_RUSANOV_LOCAL if local else 0
+        flags = form | (S().FLAG_RUSANOV_LOCAL if local else 0)
         with S().Solver(n, 0.0, n * dx, bc, lam=lam, flags=flags) as s:
             out = s.stage([dev(u) for u in Ub], [dev(u) for u in Ul], tau, speed)
             got = [t.cpu().numpy() for t in out]
@@ -121,20 +129,22 @@ def gpu_run(n, x_left, x_right, bc, lam, U, dt, steps, flags=0, use_graph=True):
         return [t.cpu().numpy() for t in s.get_state()]
 
 
+@pytest.mark.parametrize("form", FP64_FORMS)
 @pytest.mark.parametrize("bc", [0, 1])
 @pytest.mark.parametrize("n", [5, 100, 1000, 1537])
-def test_one_step_matches_oracle(n, bc):
+def test_one_step_matches_oracle(n, bc, form):
     dx, lam = 0.1, 500.0
     U = inputs.random_state(3000 + n, n, dx)
     p = oracle.Params(n, dx, bc, lam=lam)
     dt, _, _ = oracle.suggest_dt(p, U, 2.0, 0.5)
-    got = gpu_run(n, 0.0, n * dx, bc, lam, U, dt, 1)
+    got = gpu_run(n, 0.0, n * dx, bc, lam, U, dt, 1, flags=form)
     ref = oracle.step(p, U, dt)
     for k in range(4):
         assert rel_l2(got[k], ref[k]) < 1e-12, (k, rel_l2(got[k], ref[k]))
 
 
-def test_solitary_trajectory_500_steps():
+@pytest.mark.parametrize("form", FP64_FORMS)
+def test_solitary_trajectory_500_steps(form):
     # workload 1: solitary wave, N = 1000 on [-50, 50], lambda = 100,
     # dt from the material CFL 0.5 only, 500 steps
     n, lam = 1000, 100.0
@@ -142,26 +152,28 @@ def test_solitary_trajectory_500_steps():
     U = inputs.solitary(x, 1.0, 0.2, 0.0, period=100.0)
     p = oracle.Params(n, dx, 0, lam=lam)
     dt, _, _ = oracle.suggest_dt(p, U, 1e9, 0.5)
-    got = gpu_run(n, -50.0, 50.0, 0, lam, U, dt, 500)
+    got = gpu_run(n, -50.0, 50.0, 0, lam, U, dt, 500, flags=form)
     ref = oracle.run(p, U, dt, 500)
     for k in range(4):
         assert rel_l2(got[k], ref[k]) < 1e-9, (k, rel_l2(got[k], ref[k]))
     assert abs(math.fsum(got[0]) - math.fsum(U[0])) <= 1e-13 * math.fsum(U[0])
 
 
-def test_graph_replay_equals_step_loop():
+@pytest.mark.parametrize("form", FP64_FORMS)
+def test_graph_replay_equals_step_loop(form):
     n, lam = 3000, 1000.0
     x, dx = inputs.cell_centres(n, -150.0, 150.0)
     U = inputs.solitary(x, 1.0, 0.3, 0.0, period=300.0)
     dt = 0.01
-    a = gpu_run(n, -150.0, 150.0, 0, lam, U, dt, 7, use_graph=True)
-    b = gpu_run(n, -150.0, 150.0, 0, lam, U, dt, 7, use_graph=False)
+    a = gpu_run(n, -150.0, 150.0, 0, lam, U, dt, 7, use_graph=True, flags=form)
+    b = gpu_run(n, -150.0, 150.0, 0, lam, U, dt, 7, use_graph=False, flags=form)
     for k in range(4):
         np.testing.assert_array_equal(a[k], b[k])
 
 
+@pytest.mark.parametrize("form", FP64_FORMS)
 @pytest.mark.parametrize("lam", [10.0, 100.0, 1000.0])
-def test_dam_break_full_size(lam):
+def test_dam_break_full_size(lam, form):
     # workload 2 at full size: N = 2^20, dx = 0.05, transmissive, tanh
     # transition of width 5 h0 (h0 = 1), CFL_IMEX = 4; every cell compared
     # after 10 steps. Most of the domain is at rest, where q and h w are
@@ -170,7 +182,7 @@ def test_dam_break_full_size(lam):
     x, U = inputs.dam_break(n, dx, 1.2, 1.0, 5.0 / dx)
     p = oracle.Params(n, dx, 1, lam=lam)
     dt, _, _ = oracle.suggest_dt(p, U, 4.0, 0.5)
-    got = gpu_run(n, -0.5 * n * dx, 0.5 * n * dx, 1, lam, U, dt, steps)
+    got = gpu_run(n, -0.5 * n * dx, 0.5 * n * dx, 1, lam, U, dt, steps, flags=form)
     ref = oracle.run(p, U, dt, steps)
     sc = summand_scales(n, dx, 1, lam, U, dt)
     for k in range(4):
@@ -179,7 +191,8 @@ def test_dam_break_full_size(lam):
     assert rel_l2(got[0], ref[0]) < 1e-12
 
 
-def test_large_instance_2_24_one_step():
+@pytest.mark.parametrize("form", FP64_FORMS)
+def test_large_instance_2_24_one_step(form):
     # workload 5 shape: N = 2^24 cells, lambda = 1000, transmissive, solitary
     # wave towards the shallow end (flat bottom), one step compared everywhere
     n, dx, lam = 1 << 24, 0.005, 1000.0
@@ -187,7 +200,7 @@ def test_large_instance_2_24_one_step():
     U = inputs.solitary(x, 1.0, 0.1, 0.5 * n * dx - 80.0)
     p = oracle.Params(n, dx, 1, lam=lam)
     dt, _, _ = oracle.suggest_dt(p, U, 4.0, 0.5)
-    got = gpu_run(n, 0.0, n * dx, 1, lam, U, dt, 1)
+    got = gpu_run(n, 0.0, n * dx, 1, lam, U, dt, 1, flags=form)
     ref = oracle.step(p, U, dt)
     sc = summand_scales(n, dx, 1, lam, U, dt)
     for k in range(4):
@@ -195,31 +208,34 @@ def test_large_instance_2_24_one_step():
     assert rel_l2(got[0], ref[0]) < 1e-12 and rel_l2(got[2], ref[2]) < 1e-12
 
 
-def test_mass_conservation_on_gpu():
+@pytest.mark.parametrize("form", FP64_FORMS)
+def test_mass_conservation_on_gpu(form):
     n, dx = 4099, 0.1
     U = inputs.random_state(42, n, dx)
-    got = gpu_run(n, 0.0, n * dx, 0, 500.0, U, 0.01, 300)
+    got = gpu_run(n, 0.0, n * dx, 0, 500.0, U, 0.01, 300, flags=form)
     assert abs(math.fsum(got[0]) - math.fsum(U[0])) <= 1e-13 * math.fsum(U[0])
 
 
-def test_suggest_dt_matches_oracle():
+@pytest.mark.parametrize("form", FP64_FORMS)
+def test_suggest_dt_matches_oracle(form):
     n = 5000
     x, dx = inputs.cell_centres(n, -50.0, 50.0)
     U = inputs.solitary(x, 1.0, 0.2, 0.0, period=100.0)
     for cfl, mcfl in ((2.0, 0.5), (1e9, 0.5), (4.0, 0.0)):
-        with S().Solver(n, -50.0, 50.0, 0, lam=700.0) as s:
+        with S().Solver(n, -50.0, 50.0, 0, lam=700.0, flags=form) as s:
             s.set_state(*(dev(u) for u in U))
             dt = s.suggest_dt(cfl, mcfl)
         ref, _, _ = oracle.suggest_dt(oracle.Params(n, dx, 0, lam=700.0), U, cfl, mcfl)
         assert abs(dt - ref) <= 1e-14 * ref
 
 
-def test_device_errors_are_reported():
+@pytest.mark.parametrize("form", FP64_FORMS)
+def test_device_errors_are_reported(form):
     n, dx = 600, 0.1
     U = list(inputs.random_state(5, n, dx))
     U[0] = U[0].copy()
     U[0][100] = -0.5
-    with S().Solver(n, 0.0, n * dx, 0, lam=100.0) as s:
+    with S().Solver(n, 0.0, n * dx, 0, lam=100.0, flags=form) as s:
         s.set_state(*(dev(u) for u in U))
         with pytest.raises(S().HsgnError) as e:
             s.run(0.01, 1)
@@ -227,11 +243,38 @@ def test_device_errors_are_reported():
         # the error word is cleared; a good state runs again
         s.set_state(*(dev(u) for u in inputs.random_state(6, n, dx)))
         s.run(0.01, 2)
-    with S().Solver(n, 0.0, n * dx, 0, lam=100.0) as s:
+    with S().Solver(n, 0.0, n * dx, 0, lam=100.0, flags=form) as s:
         with pytest.raises(S().HsgnError):
             s.step(-1.0)
         with pytest.raises(S().HsgnError):
             s.step(float("nan"))
+
+
+def test_dfloat_reports_truncation_beyond_its_window():
+    # the double-float windows bound the dropped coupling by 2^-50: CFL_IMEX 16
+    # (coupling decaying by about 0.95 per row) is reported, CFL_IMEX 4 is not
+    n, dx, lam = 20000, 0.1, 100.0
+    x, _ = inputs.cell_centres(n, 0.0, n * dx)
+    U = inputs.solitary(x, 1.0, 0.05, 0.5 * n * dx, period=n * dx)
+    p = oracle.Params(n, dx, 0, lam=lam)
+    for cfl, code in ((16.0, 8), (4.0, 0)):
+        dt, _, _ = oracle.suggest_dt(p, U, cfl, 1e9)
+        with S().Solver(n, 0.0, n * dx, 0, lam=lam, flags=S().FLAG_DOUBLE_FLOAT) as s:
+            s.set_state(*(dev(u) for u in U))
+            s.step(dt)
+            if code:
+                with pytest.raises(S().HsgnError) as e:
+                    s.check()
+                assert e.value.code == code
+            else:
+                s.check()
+
+
+def test_dfloat_rejects_other_forms():
+    for extra in (0x1, 0x2, 0x4, 0x100):
+        with pytest.raises(S().HsgnError) as e:
+            S().Solver(16, 0.0, 1.6, 0, lam=1.0, flags=S().FLAG_DOUBLE_FLOAT | extra)
+        assert e.value.code == 6
 
 
 def test_adjoint_needs_the_well_balanced_form():
