@@ -96,10 +96,14 @@ enum {
                                 * alternating between two device buffers of pairs
                                 * (set/get_state convert). Flat bottom, single
                                 * instances, the paper's scheme; not combinable
-                                * with HSGN_MIXED, HSGN_EXACT_SOLVE or
-                                * HSGN_WELL_BALANCED (HSGN_ERR_UNIMPLEMENTED).
-                                * hsgn_stage works in this form and leaves the
-                                * state untouched. */
+                                * with HSGN_EXACT_SOLVE or HSGN_WELL_BALANCED
+                                * (HSGN_ERR_UNIMPLEMENTED). hsgn_stage works in
+                                * this form and leaves the state untouched.
+                                * HSGN_DOUBLE_FLOAT | HSGN_MIXED is the precision
+                                * split with an FP64-class solve: reconstruction,
+                                * fluxes, starred increments and coefficients in
+                                * FP32; rows, depth solve, back-substitution and
+                                * the state accumulation in pairs. */
 #define HSGN_EXACT_SOLVE 0x4   /* with HSGN_MIXED: solve the depth system exactly
                                 * through the global separator system (three
                                 * launches per stage, state updated in place) */

@@ -14,9 +14,9 @@
 //    (e = fma(a, b, -p)).
 // Sum: TwoSum of the high parts plus the low parts, renormalised (error about
 // 2^-47 of |a| + |b|). Product: the exact product of the high parts plus the
-// two cross terms (about 2^-46 relative). Reciprocal and quotient: one
-// correction of the single-precision quotient by its exact residual, i.e. one
-// Newton step from a 23-bit start (about 2^-46 relative).
+// two cross terms (about 2^-46 relative), not renormalised. Reciprocal and
+// quotient: one correction of the single-precision quotient by its exact
+// residual, i.e. one Newton step from a 23-bit start (about 2^-46 relative).
 //
 // The helpers compile for the host too (plain C++, no contraction of a*b + c
 // into a fused multiply-add: the operations are spelled with explicit
@@ -146,12 +146,17 @@ HSGN_HD dfl add_f(dfl a, float x) {
     return renorm(s, f_add(e, a.lo));
 }
 
+// Products, reciprocals and quotients return the pair unrenormalised: the low
+// part is the rounding error of the high part plus terms of relative size
+// 2^-24 (|lo| <= about 2^-22 |hi|), which every operation here accepts as an
+// input (they use hi for the leading products and lo only in correction
+// terms); sums renormalise.
 HSGN_HD dfl operator*(dfl a, dfl b) {
     const float p = f_mul(a.hi, b.hi);
     float e = f_fma(a.hi, b.hi, -p);
     e = f_fma(a.hi, b.lo, e);
     e = f_fma(a.lo, b.hi, e);
-    return renorm(p, e);
+    return dfl_make(p, e);
 }
 
 // a * x for a single float x (exact constants such as small integers).
@@ -159,7 +164,7 @@ HSGN_HD dfl mul_f(dfl a, float x) {
     const float p = f_mul(a.hi, x);
     float e = f_fma(a.hi, x, -p);
     e = f_fma(a.lo, x, e);
-    return renorm(p, e);
+    return dfl_make(p, e);
 }
 
 // a * 2^k: exact.
@@ -182,7 +187,7 @@ HSGN_HD dfl rcp(dfl a) {
     const float r = f_rcp(a.hi);
     float e = f_fma(-a.hi, r, 1.f);
     e = f_fma(-a.lo, r, e);
-    return renorm(r, f_mul(e, r));
+    return dfl_make(r, f_mul(e, r));
 }
 
 // a / b: q0 = a.hi / b.hi to one ulp, corrected by the residual a - b q0.
@@ -193,7 +198,7 @@ HSGN_HD dfl operator/(dfl a, dfl b) {
     const float pe = f_fma(b.hi, q0, -p);
     float res = f_add(f_sub(f_sub(a.hi, p), pe), a.lo);
     res = f_fma(-b.lo, q0, res);
-    return renorm(q0, f_mul(res, r));
+    return dfl_make(q0, f_mul(res, r));
 }
 
 // h^2 - m for h close to sqrt(m) (m/h^2 within a factor 2 of 1), with an

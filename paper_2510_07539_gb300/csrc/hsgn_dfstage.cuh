@@ -37,6 +37,7 @@ namespace hsgn {
 
 // The block elimination of hsgn_tridiag.cuh instantiated for pairs needs these.
 __device__ __forceinline__ bool pos_finite(dfl x) { return pos_finite(x.hi); }
+__device__ __forceinline__ float hi_of(dfl x) { return x.hi; }
 __device__ __forceinline__ dfl shfl_up_d(dfl x, int s) {
     return dfl(__shfl_up_sync(0xffffffffu, x.hi, s), __shfl_up_sync(0xffffffffu, x.lo, s));
 }
@@ -46,6 +47,29 @@ __device__ __forceinline__ dfl shfl_down_d(dfl x, int s) {
 __device__ __forceinline__ dfl shfl_xor_d(dfl x, int s) {
     return dfl(__shfl_xor_sync(0xffffffffu, x.hi, s), __shfl_xor_sync(0xffffffffu, x.lo, s));
 }
+
+// Single-precision versions of the pair helpers (the FP32-flux split runs the
+// flux and coefficient phases on floats).
+__device__ __forceinline__ float scale(float a, float pow2) { return a * pow2; }
+__device__ __forceinline__ float sub_acc(float a, float b) { return a - b; }
+__device__ __forceinline__ float add_f(float a, float x) { return a + x; }
+__device__ __forceinline__ float dabs(float a) { return fabsf(a); }
+__device__ __forceinline__ float dmax(float a, float b) { return fmaxf(a, b); }
+__device__ __forceinline__ float fma(float a, float b, float c) { return fmaf(a, b, c); }
+__device__ __forceinline__ dfl to_dfl(dfl x) { return x; }
+__device__ __forceinline__ dfl to_dfl(float x) { return dfl(x); }
+__device__ __forceinline__ dfl as_R(dfl x, dfl) { return x; }
+__device__ __forceinline__ float as_R(dfl x, float) { return f_add(x.hi, x.lo); }
+
+// Number type of the flux and coefficient phases of k_df_stage.
+template <bool F32>
+struct FluxReal {
+    using type = dfl;
+};
+template <>
+struct FluxReal<true> {
+    using type = float;
+};
 
 // A shared-memory array of pairs, high and low parts in separate planes so
 // that four consecutive entries are two 128-bit loads (lanes 16 bytes apart:
@@ -72,6 +96,22 @@ struct DArr {
         *reinterpret_cast<float4*>(lo + i) = make_float4(v[0].lo, v[1].lo, v[2].lo, v[3].lo);
     }
 };
+
+// Four consecutive entries (i a multiple of 4) as pairs or as their high parts.
+template <int NC>
+__device__ __forceinline__ void ld4(const DArr<NC>& a, int i, dfl* v) { a.get4(i, v); }
+template <int NC>
+__device__ __forceinline__ void ld4(const DArr<NC>& a, int i, float* v) {
+    const float4 h = *reinterpret_cast<const float4*>(a.hi + i);
+    v[0] = h.x; v[1] = h.y; v[2] = h.z; v[3] = h.w;
+}
+template <int NC>
+__device__ __forceinline__ void st4(DArr<NC>& a, int i, const dfl* v) { a.set4(i, v); }
+template <int NC>
+__device__ __forceinline__ void st4(DArr<NC>& a, int i, const float* v) {
+    const dfl d[4] = {dfl(v[0]), dfl(v[1]), dfl(v[2]), dfl(v[3])};
+    a.set4(i, d);
+}
 
 // Geometry: T threads, M = 4 rows per thread, overlap HW (as FusedGeom).
 template <int T, int M, int HW>
@@ -116,7 +156,11 @@ struct DfParams {
     unsigned* err;
 };
 
-template <int T, int M, int HW, int BC, int STAGE>
+// F32 selects the precision split of the mixed FP64-solve form
+// (HSGN_MIXED | HSGN_DOUBLE_FLOAT): fluxes, starred increments and coefficients
+// in single precision, rows, depth solve, back-substitution and the
+// accumulation of the state in pairs.
+template <int T, int M, int HW, int BC, int STAGE, bool F32 = false>
 __global__ void __launch_bounds__(T, 2) k_df_stage(const DfParams p) {
     static_assert(STAGE == 1 || STAGE == 2, "two stages");
     using Gm = DfGeom<T, M, HW>;
@@ -167,48 +211,61 @@ __global__ void __launch_bounds__(T, 2) k_df_stage(const DfParams p) {
 
     unsigned bad = 0;
     const int j0 = 4 * tid;
-    const dfl spd = p.local_speed ? dfl(0.f) : dfl_of(*p.speed);
 
     // ---- A. twice the Rusanov fluxes of U_l (Sec. 4.1) at the faces
     //         jf = 4t .. 4t+3 (face jf between window cells jf - 2 and jf - 1,
     //         reconstructed from the cells at index jf .. jf + 3): centred
     //         unlimited linear reconstruction of (h, q, h eta, h w),
     //         u = q/h on either side, 2F = u^L X^L + u^R X^R - s (X^R - X^L)
+    //         (a cell's quarter centred difference serves the faces on both of
+    //         its sides; the flux is taken as (u^L + s) X^L + (u^R - s) X^R, the
+    //         two speed sums shared by the three variables).
+    //         R is the number type of phases A and B: pairs, or single
+    //         precision for the FP32-flux split (F32).
+    using R = typename FluxReal<F32>::type;
+    const R spd = p.local_speed ? R(0.f) : as_R(dfl_of(*p.speed), R());
     {
-        dfl uL[4], uR[4], s[4];
+        // the quarter centred difference of cell c = 1 .. 5 of the 8 loaded
+        auto quarter = [](const R* X, R* D) {
+#pragma unroll
+            for (int c = 1; c <= 5; ++c) D[c - 1] = scale(X[c + 1] - X[c - 1], 0.25f);
+        };
+        R wL[4], wR[4];  // u^L + s, u^R - s
         {
-            dfl H[8], Q[8];
-            sm.hl.get4(j0, H);
-            sm.hl.get4(j0 + 4, H + 4);
-            sm.ql.get4(j0, Q);
-            sm.ql.get4(j0 + 4, Q + 4);
+            R H[8], Q[8], DH[5], DQ[5];
+            ld4(sm.hl, j0, H);
+            ld4(sm.hl, j0 + 4, H + 4);
+            ld4(sm.ql, j0, Q);
+            ld4(sm.ql, j0 + 4, Q + 4);
+            quarter(H, DH);
+            quarter(Q, DQ);
 #pragma unroll
             for (int e = 0; e < 4; ++e) {
-                const dfl hL = H[e + 1] + scale(H[e + 2] - H[e], 0.25f);
-                const dfl hR = H[e + 2] - scale(H[e + 3] - H[e + 1], 0.25f);
-                const dfl qL = Q[e + 1] + scale(Q[e + 2] - Q[e], 0.25f);
-                const dfl qR = Q[e + 2] - scale(Q[e + 3] - Q[e + 1], 0.25f);
+                const R hL = H[e + 1] + DH[e], hR = H[e + 2] - DH[e + 1];
+                const R qL = Q[e + 1] + DQ[e], qR = Q[e + 2] - DQ[e + 1];
                 if (j0 + e < W + 3 && !(pos_finite(hL) && pos_finite(hR))) bad |= HSGN_DEV_ERR_DEPTH;
-                uL[e] = qL / hL;
-                uR[e] = qR / hR;
-                s[e] = p.local_speed ? dmax(dabs(uL[e]), dabs(uR[e])) : spd;
+                const R uL = qL / hL, uR = qR / hR;
+                const R s = p.local_speed ? dmax(dabs(uL), dabs(uR)) : spd;
+                wL[e] = uL + s;
+                wR[e] = uR - s;
             }
         }
         DArr<Gm::NC>* const X[3] = {&sm.ql, &sm.ml, &sm.rl};
         DArr<Gm::NC>* const F[3] = {&sm.fq, &sm.fm, &sm.fr};
 #pragma unroll
         for (int v = 0; v < 3; ++v) {
-            dfl Xv[8];
-            X[v]->get4(j0, Xv);
-            X[v]->get4(j0 + 4, Xv + 4);
-            dfl Fv[4];
+            R Xv[8], Dv[5];
+            ld4(*X[v], j0, Xv);
+            ld4(*X[v], j0 + 4, Xv + 4);
+            quarter(Xv, Dv);
+            R Fv[4];
 #pragma unroll
             for (int e = 0; e < 4; ++e) {
-                const dfl xL = Xv[e + 1] + scale(Xv[e + 2] - Xv[e], 0.25f);
-                const dfl xR = Xv[e + 2] - scale(Xv[e + 3] - Xv[e + 1], 0.25f);
-                Fv[e] = fma(uL[e], xL, uR[e] * xR) - s[e] * (xR - xL);
+                const R xL = Xv[e + 1] + Dv[e];
+                const R xR = Xv[e + 2] - Dv[e + 1];
+                Fv[e] = fma(wL[e], xL, wR[e] * xR);
             }
-            F[v]->set4(j0, Fv);
+            st4(*F[v], j0, Fv);
         }
     }
     __syncthreads();
@@ -227,50 +284,53 @@ __global__ void __launch_bounds__(T, 2) k_df_stage(const DfParams p) {
     dfl dq_[4], dm_[4], dr_[4], be_[4], de_[4];
     float kloc = 0.f, kmin = 3.0e38f;
     {
-        dfl FQ[8], FM[8], FR[8];
-        sm.fq.get4(j0, FQ);
-        sm.fq.get4(j0 + 4, FQ + 4);
-        sm.fm.get4(j0, FM);
-        sm.fm.get4(j0 + 4, FM + 4);
-        sm.fr.get4(j0, FR);
-        sm.fr.get4(j0 + 4, FR + 4);
-        dfl HL[8], ML[8], MB[8], RB[8];
-        sm.hl.get4(j0, HL);
-        sm.hl.get4(j0 + 4, HL + 4);
-        sm.ml.get4(j0, ML);
-        sm.ml.get4(j0 + 4, ML + 4);
-        sm.mb.get4(j0, MB);
-        sm.mb.get4(j0 + 4, MB + 4);
-        sm.rb.get4(j0, RB);
-        sm.rb.get4(j0 + 4, RB + 4);
+        const R c_fq = as_R(p.fq, R()), c_tau = as_R(p.tau, R()), c_lt2 = as_R(p.lt2, R());
+        const R c_third = as_R(p.third, R()), c_g = as_R(p.g, R()), c_lam3 = as_R(p.lam3, R());
+        const R c_lam = as_R(p.lam, R());
+        R FQ[8], FM[8], FR[8];
+        ld4(sm.fq, j0, FQ);
+        ld4(sm.fq, j0 + 4, FQ + 4);
+        ld4(sm.fm, j0, FM);
+        ld4(sm.fm, j0 + 4, FM + 4);
+        ld4(sm.fr, j0, FR);
+        ld4(sm.fr, j0 + 4, FR + 4);
+        R HL[8], ML[8], MB[8], RB[8];
+        ld4(sm.hl, j0, HL);
+        ld4(sm.hl, j0 + 4, HL + 4);
+        ld4(sm.ml, j0, ML);
+        ld4(sm.ml, j0 + 4, ML + 4);
+        ld4(sm.mb, j0, MB);
+        ld4(sm.mb, j0 + 4, MB + 4);
+        ld4(sm.rb, j0, RB);
+        ld4(sm.rb, j0 + 4, RB + 4);
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
             dq_[k] = dm_[k] = dr_[k] = be_[k] = de_[k] = dfl(0.f);
             if (j0 + k < W + 2) {
-                const dfl dr = -(p.fq * sub_acc(FR[k + 1], FR[k]));
-                const dfl dm = fma(p.tau, RB[k + 2] + dr, -(p.fq * sub_acc(FM[k + 1], FM[k])));
-                const dfl dq = -(p.fq * sub_acc(FQ[k + 1], FQ[k]));
-                const dfl ms = (MB[k + 2] + dm) + p.lt2;
-                const dfl h = HL[k + 2];
+                const R dr = -(c_fq * sub_acc(FR[k + 1], FR[k]));
+                const R dm = fma(c_tau, RB[k + 2] + dr, -(c_fq * sub_acc(FM[k + 1], FM[k])));
+                const R dq = -(c_fq * sub_acc(FQ[k + 1], FQ[k]));
+                const R ms = (MB[k + 2] + dm) + c_lt2;
+                const R h = HL[k + 2];
                 if (!pos_finite(h)) bad |= HSGN_DEV_ERR_DEPTH;
-                const dfl ih = rcp(h);
-                const dfl eta = ML[k + 2] * ih;
-                const dfl e = eta * ih;
-                const dfl alpha = -(add_f(scale(e, 2.f), -1.f) * ih * p.third);
-                const dfl c2 = fma(p.g, h, p.lam3 * (e * e));
-                const dfl a2 = c2 - p.lam * (eta * alpha);
-                const dfl h2 = h * h;
-                const dfl iD = rcp(h2 + p.lt2);       // 1/(beta_1 h^2)
-                const dfl ib1 = h2 * iD;              // 1/beta_1
-                const dfl beta2 = scale(p.lt2, 2.f) * (h * (iD * iD));
-                const dfl beta = fma(p.lam * alpha, beta2 * ms, a2);
+                const R ih = rcp(h);
+                const R eta = ML[k + 2] * ih;
+                const R e = eta * ih;
+                const R alpha = -(add_f(scale(e, 2.f), -1.f) * ih * c_third);
+                const R c2 = fma(c_g, h, c_lam3 * (e * e));
+                const R a2 = c2 - c_lam * (eta * alpha);
+                const R h2 = h * h;
+                const R iD = rcp(h2 + c_lt2);       // 1/(beta_1 h^2)
+                const R ib1 = h2 * iD;              // 1/beta_1
+                const R beta2 = scale(c_lt2, 2.f) * (h * (iD * iD));
+                const R beta = fma(c_lam * alpha, beta2 * ms, a2);
                 if (!pos_finite(beta)) bad |= HSGN_DEV_ERR_COERCIVE;
-                dq_[k] = dq;
-                dm_[k] = dm;
-                dr_[k] = dr;
-                be_[k] = beta;
-                de_[k] = alpha * ib1;
-                const float kb = f_mul(p.Cc.hi, beta.hi);
+                dq_[k] = to_dfl(dq);
+                dm_[k] = to_dfl(dm);
+                dr_[k] = to_dfl(dr);
+                be_[k] = to_dfl(beta);
+                de_[k] = to_dfl(alpha * ib1);
+                const float kb = f_mul(p.Cc.hi, hi_of(beta));
                 kloc = fmaxf(kloc, kb);
                 kmin = fminf(kmin, kb);
             }
@@ -375,13 +435,12 @@ __global__ void __launch_bounds__(T, 2) k_df_stage(const DfParams p) {
             bb = add_f(kl + kr, 1.f);
             d = rd[k];
         };
-        dfl y[M], v[M], w[M], last[4];
-        int cs, m;
-        cta_block_solve_fixed<T, M>(W + 1, roww, sm.sep, y, v, w, cs, m, last, p.err);
+        dfl y[M];
+        cta_window_solve<T, M>(W + 1, roww, sm.sep, y, p.err);
         // dh = y: the values outside the window (and the closing row) are taken as 0
 #pragma unroll
         for (int k = 0; k < M; ++k)
-            if (!(k < m && cs + k < W)) y[k] = dfl(0.f);
+            if (!(j0 + k < W)) y[k] = dfl(0.f);
         DH.set4(j0 + 4, y);
     }
     __syncthreads();

@@ -805,13 +805,24 @@ __global__ void __launch_bounds__(T, (WB ? 768 : 1024) / T) k_mixed_fused(const 
             bb = 1.f + kl + kr;
             d = rd[k];
         };
-        float y[M], v[M], w[M], last[4];
-        int cs, m;
-        cta_block_solve_fixed<T, M>(W + 1, roww, sm.sep, y, v, w, cs, m, last, p.err, mini);
-        // dh = y: the values outside the window (and the closing row) are taken as 0
+        float y[M];
+        if constexpr (two) {
+            // warp 0 solves the separator system while warps 1 and 2 solve the
+            // tile-face mini windows
+            float v[M], w[M], last[4];
+            int cs, m;
+            cta_block_solve_fixed<T, M>(W + 1, roww, sm.sep, y, v, w, cs, m, last, p.err, mini);
 #pragma unroll
-        for (int k = 0; k < M; ++k)
-            if (!(k < m && cs + k < W)) y[k] = 0.f;
+            for (int k = 0; k < M; ++k)
+                if (!(k < m && cs + k < W)) y[k] = 0.f;
+        } else {
+            // no mini windows in stage 1: the separators by cyclic reduction over all threads
+            cta_window_solve<T, M>(W + 1, roww, sm.sep, y, p.err);
+#pragma unroll
+            for (int k = 0; k < M; ++k)
+                if (!(j0 + k < W)) y[k] = 0.f;
+        }
+        // dh = y: the values outside the window (and the closing row) are taken as 0
         sts4(dha + j0 + 4, y);
     }
     __syncthreads();

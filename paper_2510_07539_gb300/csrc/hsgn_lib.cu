@@ -172,6 +172,7 @@ struct hsgn_s {
     float4* mrec = nullptr;          // three float4 records per row
     // double-float windowed stage (HSGN_DOUBLE_FLOAT): stage-1 increments as pairs
     bool dfloat = false;
+    bool df_f32 = false;             // with HSGN_MIXED: fluxes and coefficients in FP32
     float2* D1[4] = {};
     // batch (hsgn_create_batched)
     int32_t count = 1;
@@ -522,20 +523,33 @@ cudaError_t launch_stage_fused(hsgn_s* H, int stage, double tau, cudaStream_t st
 }
 
 // One launch of the double-float stage kernel specialised for p.stage.
-template <int BC>
+template <int BC, bool F32>
 void launch_df(unsigned P, const DfParams& p, cudaStream_t st) {
     const size_t smem = sizeof(DfShared<DT, FM, DHW>);
     if (p.stage == 2)
-        k_df_stage<DT, FM, DHW, BC, 2><<<P, DT, smem, st>>>(p);
+        k_df_stage<DT, FM, DHW, BC, 2, F32><<<P, DT, smem, st>>>(p);
     else
-        k_df_stage<DT, FM, DHW, BC, 1><<<P, DT, smem, st>>>(p);
+        k_df_stage<DT, FM, DHW, BC, 1, F32><<<P, DT, smem, st>>>(p);
+}
+
+// the kernel of the handle's boundary condition and precision split
+void launch_df(const hsgn_s* H, unsigned P, const DfParams& p, cudaStream_t st) {
+    if (H->bc == BC_PERIODIC) {
+        if (H->df_f32) launch_df<BC_PERIODIC, true>(P, p, st);
+        else launch_df<BC_PERIODIC, false>(P, p, st);
+    } else {
+        if (H->df_f32) launch_df<BC_TRANSMISSIVE, true>(P, p, st);
+        else launch_df<BC_TRANSMISSIVE, false>(P, p, st);
+    }
 }
 
 template <int BC>
 cudaError_t set_smem_df() {
     const size_t smem = sizeof(DfShared<DT, FM, DHW>);
-    cudaError_t e = set_smem(k_df_stage<DT, FM, DHW, BC, 1>, smem);
-    if (e == cudaSuccess) e = set_smem(k_df_stage<DT, FM, DHW, BC, 2>, smem);
+    cudaError_t e = set_smem(k_df_stage<DT, FM, DHW, BC, 1, false>, smem);
+    if (e == cudaSuccess) e = set_smem(k_df_stage<DT, FM, DHW, BC, 2, false>, smem);
+    if (e == cudaSuccess) e = set_smem(k_df_stage<DT, FM, DHW, BC, 1, true>, smem);
+    if (e == cudaSuccess) e = set_smem(k_df_stage<DT, FM, DHW, BC, 2, true>, smem);
     return e;
 }
 
@@ -592,10 +606,7 @@ cudaError_t launch_stage_df(hsgn_s* H, int stage, double tau, cudaStream_t st) {
     p.speed_next = speed_of(H, 1 - H->cur);
     {
         ProfScope ps(H, HSGN_PROF_ASSEMBLE, st);
-        if (H->bc == BC_PERIODIC)
-            launch_df<BC_PERIODIC>(df_tiles(H), p, st);
-        else
-            launch_df<BC_TRANSMISSIVE>(df_tiles(H), p, st);
+        launch_df(H, df_tiles(H), p, st);
     }
     return cudaGetLastError();
 }
@@ -886,9 +897,10 @@ int hsgn_create(const hsgn_grid_t* grid, double g, double lambda, const double* 
     if (flags & ~(int32_t)(HSGN_RUSANOV_LOCAL | HSGN_MIXED | HSGN_WELL_BALANCED | HSGN_EXACT_SOLVE |
                            HSGN_DOUBLE_FLOAT | HSGN_SCHEME_MASK))
         return HSGN_ERR_UNIMPLEMENTED;
-    // the double-float form: the paper's scheme, flat bottom, on its own
+    // the double-float form (alone, or with HSGN_MIXED for the FP32-flux split):
+    // the paper's scheme, flat bottom
     if ((flags & HSGN_DOUBLE_FLOAT) &&
-        (flags & (HSGN_MIXED | HSGN_EXACT_SOLVE | HSGN_WELL_BALANCED | HSGN_SCHEME_MASK)))
+        (flags & (HSGN_EXACT_SOLVE | HSGN_WELL_BALANCED | HSGN_SCHEME_MASK)))
         return HSGN_ERR_UNIMPLEMENTED;
     const int32_t scheme = flags & HSGN_SCHEME_MASK;
     if (scheme > HSGN_SCHEME_EX_EULER) return HSGN_ERR_INVALID_ARG;
@@ -937,8 +949,9 @@ int hsgn_create(const hsgn_grid_t* grid, double g, double lambda, const double* 
     }
     const int64_t n = H->n, P = H->split.P;
 
-    H->mixed = (flags & HSGN_MIXED) != 0;
     H->dfloat = (flags & HSGN_DOUBLE_FLOAT) != 0;
+    H->df_f32 = H->dfloat && (flags & HSGN_MIXED) != 0;
+    H->mixed = (flags & HSGN_MIXED) != 0 && !H->dfloat;
     H->windowed = (H->mixed && !(flags & HSGN_EXACT_SOLVE)) || H->dfloat;
     H->wb = (flags & HSGN_WELL_BALANCED) != 0;
     H->scheme = scheme;
@@ -1019,7 +1032,8 @@ int hsgn_create(const hsgn_grid_t* grid, double g, double lambda, const double* 
             e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, H->device);
         if (e == cudaSuccess)
             e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-                &per_sm, k_df_stage<DT, FM, DHW, BC_PERIODIC, 2>, DT, sizeof(DfShared<DT, FM, DHW>));
+                &per_sm, k_df_stage<DT, FM, DHW, BC_PERIODIC, 2, false>, DT,
+                sizeof(DfShared<DT, FM, DHW>));
         const int64_t slots = (int64_t)(sms > 0 ? sms : 1) * (per_sm > 0 ? per_sm : 1);
         H->tileS = (int32_t)fused_tile_rows(n, DfGeom<DT, FM, DHW>::S, slots);
         H->tileSlots = (int32_t)slots;
@@ -1309,10 +1323,7 @@ int hsgn_stage(hsgn_handle_t H, const double* const base[4], const double* const
             p.out[k] = reinterpret_cast<float2*>(out[k]);
         }
         p.speed = spd;
-        if (H->bc == BC_PERIODIC)
-            launch_df<BC_PERIODIC>(df_tiles(H), p, st);
-        else
-            launch_df<BC_TRANSMISSIVE>(df_tiles(H), p, st);
+        launch_df(H, df_tiles(H), p, st);
         for (int k = 0; k < 4; ++k)
             k_f64_from_df_inplace<<<convert_blocks(H), 256, 0, st>>>(H->n, out[k]);
         return cudaGetLastError() == cudaSuccess ? HSGN_OK : HSGN_ERR_CUDA;
@@ -2030,6 +2041,9 @@ namespace {
 
 constexpr int kPeakChains = 8;
 
+__device__ __forceinline__ float peak_fma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double peak_fma(double a, double b, double c) { return __fma_rn(a, b, c); }
+
 template <class R>
 __global__ void __launch_bounds__(256) k_fma_peak(int iters, R b, R c, R* out) {
     R a[kPeakChains];
@@ -2037,7 +2051,7 @@ __global__ void __launch_bounds__(256) k_fma_peak(int iters, R b, R c, R* out) {
     for (int k = 0; k < kPeakChains; ++k) a[k] = (R)(threadIdx.x + k) * (R)1e-3;
     for (int i = 0; i < iters; ++i) {
 #pragma unroll
-        for (int k = 0; k < kPeakChains; ++k) a[k] = fma(a[k], b, c);
+        for (int k = 0; k < kPeakChains; ++k) a[k] = peak_fma(a[k], b, c);
     }
     R s = 0;
 #pragma unroll

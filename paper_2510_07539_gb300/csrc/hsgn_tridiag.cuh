@@ -77,6 +77,10 @@ __device__ __forceinline__ float rcp(float x) {
     return fmaf(r, fmaf(-x, r, 1.f), r);
 }
 
+// Leading single-precision value of a number (magnitude tests).
+__device__ __forceinline__ float hi_of(float x) { return x; }
+__device__ __forceinline__ float hi_of(double x) { return (float)x; }
+
 // Shared memory of the separator system of a CTA with T threads.
 // Indexed with pd(): warp 0 reads the rows at a stride of T/32.
 template <int T, class Real = double>
@@ -466,6 +470,159 @@ __device__ __forceinline__ void cta_block_solve_impl(int nrows, RowK row, SepSha
     }
 }
 
+
+// ---------------------------------------------------------------------------
+// Depth solve of one window: nrows rows (the last one closes the window) with
+// the couplings beyond the window dropped, i.e. x_L = x_R = 0 in the notation
+// of hsgn_tridiag.cuh. Thread t holds the rows M t .. M t + M - 1 in its
+// registers (row(k, i, a, b, c, d) gives row i = M t + k); its last row is a
+// thread separator sigma_t. As in cta_block_solve_impl each thread first
+// eliminates its interior rows with three right-hand sides, so that
+// x_i = y_i - sigma_{t-1} v_i - sigma_t w_i. The separators then satisfy a
+// tridiagonal system of teff - 1 rows (the last thread's separator is the
+// closing row), which here is solved by parallel cyclic reduction over all
+// threads in shared memory, one row per thread and one right-hand side (the
+// window has no external couplings), instead of by one warp: log2 of the
+// row count levels, each a constant number of operations per thread, so no
+// warp idles while one works. On return x[k] holds the solution of row
+// M t + k (zero for the closing row and for rows past nrows).
+// ---------------------------------------------------------------------------
+template <int T, int M, class RowK, class Real>
+__device__ __forceinline__ void cta_window_solve(int nrows, RowK row, SepShared<T, Real>& sh,
+                                                 Real (&x)[M], unsigned* err) {
+    const int t = threadIdx.x;
+    const int teff = (nrows + M - 1) / M;
+    const int cs = t < teff ? M * t : nrows;
+    const int m = t < teff ? min(M, nrows - M * t) : 0;
+    const int nint = m - 1;
+    Real y[M], v[M], w[M];
+    // ---- 1. Thomas sweep of the chunk interior (three right-hand sides)
+    Real sa = Real(0), sb = Real(1), sc = Real(0), sd = Real(0);
+    bool bad = false;
+#pragma unroll
+    for (int k = 0; k < M; ++k) {
+        if (k < nint) {
+            Real a, b, c, d;
+            row(k, cs + k, a, b, c, d);
+            Real p, ip;
+            if (k == 0) {
+                p = b;
+                ip = rcp(p);
+                y[k] = d * ip;
+                v[k] = a * ip;
+            } else {
+                p = fma(-a, w[k - 1], b);
+                ip = rcp(p);
+                y[k] = fma(-a, y[k - 1], d) * ip;
+                v[k] = -a * v[k - 1] * ip;
+            }
+            bad |= !pos_finite(p);
+            w[k] = c * ip;
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < M; ++k)
+        if (k == m - 1) row(k, cs + k, sa, sb, sc, sd);
+    Real YL = Real(0), VL = -Real(1), WL = Real(0);
+    {
+        Real Yn = Real(0), Vn = Real(0), Wn = -Real(1);
+#pragma unroll
+        for (int k = M - 1; k >= 0; --k) {
+            if (k < nint) {
+                const Real Y = fma(-w[k], Yn, y[k]);
+                const Real V = fma(-w[k], Vn, v[k]);
+                const Real W = -w[k] * Wn;
+                if (k == nint - 1) {
+                    YL = Y;
+                    VL = V;
+                    WL = W;
+                }
+                y[k] = Y;
+                v[k] = V;
+                w[k] = W;
+                Yn = Y;
+                Vn = V;
+                Wn = W;
+            }
+        }
+    }
+    if (t < teff) {
+        sh.YF[pd(t)] = nint > 0 ? y[0] : Real(0);
+        sh.VF[pd(t)] = nint > 0 ? v[0] : Real(0);
+        sh.WF[pd(t)] = nint > 0 ? w[0] : -Real(1);
+    }
+    __syncthreads();
+
+    // ---- 2. separator rows sigma_t, t < ns = teff - 1 (sigma_{-1} = x_L and
+    //         sigma_{ns} = x_R are zero, so their couplings drop)
+    const int ns = teff - 1;
+    Real A = Real(0), B = Real(1), C = Real(0), D = Real(0);
+    if (t < ns) {
+        A = t == 0 ? Real(0) : -sa * VL;
+        B = sb - sa * WL - sc * sh.VF[pd(t + 1)];
+        C = t == ns - 1 ? Real(0) : -sc * sh.WF[pd(t + 1)];
+        D = sd - sa * YL - sc * sh.YF[pd(t + 1)];
+    }
+    __syncthreads();  // (the first-interior values are read above)
+    // ---- 3. parallel cyclic reduction: after the level of stride s, row t
+    //         couples sigma_t to sigma_{t-2s} and sigma_{t+2s} only; rows
+    //         outside [0, ns) are identity rows. The couplings of a diagonally
+    //         dominant system shrink geometrically with the stride: once every
+    //         row's remaining couplings are below `drop` of its diagonal (they
+    //         multiply separators no larger than the solution), the levels left
+    //         would change no separator beyond that and are skipped.
+    const float drop = sizeof(Real) == sizeof(float) ? 0x1p-26f : 0x1p-52f;
+    for (int s = 1; s < ns; s <<= 1) {
+        const bool coupled = t < ns && fabsf(hi_of(A)) + fabsf(hi_of(C)) > drop * fabsf(hi_of(B));
+        if (!__syncthreads_or(coupled)) break;
+        if (t < ns) {
+            sh.A[pd(t)] = A;
+            sh.B[pd(t)] = B;
+            sh.C[pd(t)] = C;
+            sh.D1[pd(t)] = D;
+        }
+        __syncthreads();
+        if (t < ns) {
+            Real nA = Real(0), nC = Real(0), nB = B, nD = D;
+            if (t - s >= 0) {
+                const Real k1 = A * rcp(sh.B[pd(t - s)]);
+                nA = -k1 * sh.A[pd(t - s)];
+                nB = fma(-k1, sh.C[pd(t - s)], nB);
+                nD = fma(-k1, sh.D1[pd(t - s)], nD);
+            }
+            if (t + s < ns) {
+                const Real k2 = C * rcp(sh.B[pd(t + s)]);
+                nC = -k2 * sh.C[pd(t + s)];
+                nB = fma(-k2, sh.A[pd(t + s)], nB);
+                nD = fma(-k2, sh.D1[pd(t + s)], nD);
+            }
+            A = nA;
+            B = nB;
+            C = nC;
+            D = nD;
+        }
+        __syncthreads();
+    }
+    if (t < ns) {
+        if (!pos_finite(B)) bad = true;
+        sh.YF[pd(t)] = D * rcp(B);
+    }
+    if (bad) flag_error(err, HSGN_DEV_ERR_COERCIVE);
+    __syncthreads();
+
+    // ---- 4. recombination: x_i = y_i - sigma_{t-1} v_i - sigma_t w_i
+    const Real sL = (t > 0 && t - 1 < ns) ? sh.YF[pd(t - 1)] : Real(0);
+    const Real sR = t < ns ? sh.YF[pd(t)] : Real(0);
+#pragma unroll
+    for (int k = 0; k < M; ++k) {
+        if (k < nint)
+            x[k] = y[k] - sL * v[k] - sR * w[k];
+        else if (k == nint)
+            x[k] = sR;
+        else
+            x[k] = Real(0);
+    }
+}
 
 // cta_block_solve_impl with rows split evenly; row(i, a, b, c, d) returns row i.
 template <int T, int M, class RowFn, class Real, class Side = NoSide>
