@@ -67,10 +67,10 @@ FLOPS_PER_CELL_ASSEMBLE = 149.0
 # 2^22-cell dam break (the capture summarised in profiles/ncu_df_stage.md).
 # Valid for the kernel sources whose hash is DF_FLOPS_SOURCE_SHA; None when the
 # kernel has changed since (the roofline then reports no achieved flop rate).
-DF_FLOPS_PER_CELL = 2058.4      # stage 1 / 2: 1943.8 / 2172.9
-DF_FP32_INST_PER_CELL = 1793.0  # FADD + FMUL + FFMA instructions, stage 1 / 2: 1695.4 / 1890.6
-DF_TRAFFIC_PER_CELL = 71.0      # dram__bytes_read + write per cell and launch, stage 1 / 2: 53.5 / 88.6
-DF_FLOPS_SOURCE_SHA = "2fcec70606e589df"
+DF_FLOPS_PER_CELL = 1847.0      # stage 1 / 2: 1734 / 1960
+DF_FP32_INST_PER_CELL = 1572.0  # FADD + FMUL + FFMA instructions, stage 1 / 2: 1476 / 1668
+DF_TRAFFIC_PER_CELL = 71.1      # dram__bytes_read + write per cell and launch, stage 1 / 2: 53.6 / 88.6
+DF_FLOPS_SOURCE_SHA = "d6be630afbb89a2b"
 DF_SOURCES = ("hsgn_dfstage.cuh", "hsgn_dfloat.cuh", "hsgn_fused.cuh", "hsgn_mixed.cuh",
               "hsgn_tridiag.cuh")
 
@@ -443,6 +443,35 @@ def run_to_time(S, torch, stream, n, xl, xr, bc, lam, flags, U, cfl, mcfl, T):
         return {"steps": steps, "dt": dt, "ms": e0.elapsed_time(e1)}, s.get_state()[0].cpu().numpy()
 
 
+def run_to_time_cfl(S, torch, stream, n, xl, xr, bc, lam, U, cfl, mcfl, T, chunk=200):
+    """The double-float form to the final time T with the time step re-evaluated
+    from the current state before every step (Sec. 5), on the device
+    (hsgn_run_cfl); the last step is shortened to land on T. Returns the record
+    and the final depth (None when the run broke down)."""
+    with S.Solver(n, xl, xr, bc, lam=lam, flags=S.FLAG_DOUBLE_FLOAT) as s:
+        Ud = [torch.tensor(u, device="cuda") for u in U]
+        s.set_state(*Ud)
+        torch.cuda.synchronize()
+        t, steps, t0 = 0.0, 0, time.perf_counter()
+        try:
+            while True:
+                dt = s.suggest_dt(cfl, mcfl)
+                if t + dt >= T:
+                    s.run(T - t, 1)
+                    steps += 1
+                    break
+                # chunks of steps whose sum stays below T by a margin of one
+                # chunk of the current dt
+                k = max(1, min(chunk, int((T - t) / dt) - 1))
+                t += s.run_cfl(cfl, mcfl, k)
+                steps += k
+        except S.HsgnError as err:
+            return {"steps": steps, "t": t, "failed": str(err)}, None
+        ms = 1e3 * (time.perf_counter() - t0)
+        return ({"steps": steps, "ms_wall": ms, "dt_policy": "per step (Sec. 5), on the device"},
+                s.get_state()[0].cpu().numpy())
+
+
 def time_paper_runs(S, torch, stream):
     """The runs of the paper's CPU-time tables, timed on the GPU (the paper's
     seconds are for an unstated CPU and implementation: context only).
@@ -479,6 +508,11 @@ def time_paper_runs(S, torch, stream):
             if hm is not None:
                 row["si_mixed"]["depth_rel_l2_vs_fp64"] = float(np.linalg.norm(hm - h64) /
                                                                np.linalg.norm(h64))
+        # the same run with the time step re-evaluated every step (double-float
+        # form): the policy of Sec. 5, under which lambda = 1000 reaches T
+        row["si_dfloat_per_step_dt"], _ = run_to_time_cfl(S, torch, stream, 5000, -200.0, 200.0,
+                                                          S.BC_TRANSMISSIVE, lam, U, 2.0, 0.0,
+                                                          35.0)
         row["ex_heun_fp64"], _ = run_to_time(S, torch, stream, 5000, -200.0, 200.0,
                                              S.BC_TRANSMISSIVE, lam, S.SCHEME_EX_HEUN, U, 0.4,
                                              0.0, 35.0)
@@ -775,6 +809,19 @@ def run_ours(args):
                               "bytes_moved_per_cell_stage": BYTES_MOVED_MIXED},
                  "sequential_value": units_rank * world / (mqms / 1e3)}
 
+    # ---- the precision split with an FP64-class solve: FP32 fluxes and
+    #      coefficients, rows, depth solve and back-substitution in pairs
+    mixed_df, xsols, xdts = None, [], []
+    if not args.no_mixed:
+        xsols, xdts, xms, xqms, xavg, _, _ = time_form(
+            S, torch, S.FLAG_MIXED | S.FLAG_DOUBLE_FLOAT, n, xl, xr, lams, Ud, args, flush,
+            stream, dist, None, not args.sequential)
+        mixed_df = {"value": units_rank * world / (xms / 1e3), "unit": UNIT,
+                    "ms_per_step": xms / args.steps,
+                    "dtype": "f32 fluxes and coefficients + double-float solve and state",
+                    "kernel_avg_ms": xavg, "hbm": hbm_view(n, xavg, hbm_peak),
+                    "sequential_value": units_rank * world / (xqms / 1e3)}
+
     # ---- the paper's comparison: the same physical time with each scheme
     comparators = None
     if not args.no_comparators:
@@ -930,7 +977,9 @@ def run_ours(args):
             fp64["l2_rel_err_vs_oracle"] = l2_vs_oracle(fsols, fdts, Ud, refs, ks, np)
         if mixed is not None:
             mixed["l2_rel_err_vs_oracle"] = l2_vs_oracle(msols, mdts, Ud, refs, ks, np)
-    for s in dsols + fsols + msols:
+        if mixed_df is not None:
+            mixed_df["l2_rel_err_vs_oracle"] = l2_vs_oracle(xsols, xdts, Ud, refs, ks, np)
+    for s in dsols + fsols + msols + xsols:
         s.close()
 
     if rank == 0:
@@ -953,7 +1002,8 @@ def run_ours(args):
                                             "fp32_tflops": fp32_peak, "fp64_tflops": fp64_peak,
                                             "fp32_fp64_source": "measured in this run "
                                                                 "(hsgn_fma_peak)"},
-            "fp64_path": fp64, "mixed_path": mixed, "batched": batched,
+            "fp64_path": fp64, "mixed_path": mixed, "mixed_dfsolve_path": mixed_df,
+            "batched": batched,
             "batched_vs_fp64_single": (batched["value"] / fp64["value"])
             if (batched and fp64) else None,
             "comparators": comparators, "adjoint": adjoint, "shelf": shelf,

@@ -222,6 +222,20 @@ int hsgn_enqueue(hsgn_handle_t h, double dt, int64_t n_steps, void* stream);
 int hsgn_profile(hsgn_handle_t h, int32_t enable);
 int hsgn_profile_read(hsgn_handle_t h, double* ms, int64_t* launches, int32_t reset);
 
+/* n_steps steps, each with its own time step from the rule of Sec. 5
+ * (Sec. 3.3, eq. (eq:MCFL)) applied to the state it starts from:
+ * dt = cfl dx / nu_max, reduced to mcfl dx / u_max if the material CFL
+ * u_max dt / dx would exceed mcfl (mcfl = 0 disables that test), with
+ * nu = |u| + sqrt(g h + (lambda/3) eta^2/h^2) as in hsgn_suggest_dt. The
+ * maxima of each new state are folded on the device by the stage that writes
+ * it and the next step reads them there, so steps run back to back (one
+ * captured graph per state buffer) with no host round trip. *t_advanced
+ * (host) receives the sum of the time steps taken. HSGN_DOUBLE_FLOAT forms
+ * with the global Rusanov speed only (HSGN_ERR_UNIMPLEMENTED otherwise).
+ * Synchronises and reports device errors like hsgn_run. */
+int hsgn_run_cfl(hsgn_handle_t h, double cfl, double mcfl, int64_t n_steps, double* t_advanced,
+                 void* stream);
+
 /* Synchronise the stream and report (and clear) pending device errors. */
 int hsgn_check(hsgn_handle_t h, void* stream);
 

@@ -106,6 +106,14 @@ __device__ __forceinline__ void ld4(const DArr<NC>& a, int i, float* v) {
     v[0] = h.x; v[1] = h.y; v[2] = h.z; v[3] = h.w;
 }
 template <int NC>
+__device__ __forceinline__ void ld1(const DArr<NC>& a, int i, dfl& v) { v = a.get(i); }
+template <int NC>
+__device__ __forceinline__ void ld1(const DArr<NC>& a, int i, float& v) { v = a.hi[i]; }
+template <int NC>
+__device__ __forceinline__ void st1(DArr<NC>& a, int i, dfl v) { a.set(i, v); }
+template <int NC>
+__device__ __forceinline__ void st1(DArr<NC>& a, int i, float v) { a.set(i, dfl(v)); }
+template <int NC>
 __device__ __forceinline__ void st4(DArr<NC>& a, int i, const dfl* v) { a.set4(i, v); }
 template <int NC>
 __device__ __forceinline__ void st4(DArr<NC>& a, int i, const float* v) {
@@ -136,7 +144,36 @@ struct DfShared {
     DArr<NC> fq, fm, fr;      // twice the Rusanov fluxes of q, h eta, h w
     SepShared<T, dfl> sep;
     unsigned kmax, kmin;      // bits of max / min tau^2 beta / dx^2 (positive floats order as integers)
+    dfl kc[7];                // per-step constants of an adaptive step
 };
+
+// The constants of a stage that depend on the time step (tau = gamma dt).
+struct DfStepConst {
+    dfl tau, lt2, ltau, fq, lfq, Cc, fd;
+};
+
+__device__ __forceinline__ DfStepConst df_step_const(double dt, double dx, double lam) {
+    const double tau = (1.0 - 1.0 / sqrt(2.0)) * dt;  // gamma dt, Sec. 3.2
+    DfStepConst k;
+    k.tau = dfl_of(tau);
+    k.lt2 = dfl_of(lam * tau * tau);
+    k.ltau = dfl_of(lam * tau);
+    k.fq = dfl_of(tau / (2.0 * dx));
+    k.lfq = dfl_of(lam * tau / (2.0 * dx));
+    k.Cc = dfl_of(tau * tau / (dx * dx));
+    k.fd = dfl_of(lam * tau * tau / (dx * dx));
+    return k;
+}
+
+// sqrt(a) of a positive pair: the single-precision root refined by one
+// Newton step, s + (a - s^2)/(2 s) with s^2 formed exactly.
+__device__ __forceinline__ dfl dsqrt(dfl a) {
+    const float s = sqrtf(a.hi);
+    const float p = f_mul(s, s);
+    const float pe = f_fma(s, s, -p);
+    const float r = f_add(f_sub(f_sub(a.hi, p), pe), a.lo);
+    return dfl_make(s, f_mul(r, f_rcp(f_add(s, s))));
+}
 
 struct DfParams {
     int64_t n;
@@ -148,6 +185,14 @@ struct DfParams {
     // lambda tau, tau/(2 dx), lambda tau/(2 dx), tau^2/dx^2, lambda tau^2/dx^2,
     // g, lambda, lambda/3, 1/3, and the stage-2 weights c/gamma, (1-gamma)/gamma
     dfl tau, lt2, ltau, fq, lfq, Cc, fd, g, lam, lam3, third, wl1, wb1;
+    // per-step time step (adaptive != 0): stage 1 takes dt = min(cfl dx / nu_max,
+    // mcfl dx / u_max) from speed[0] = max |u| and speed[1] = max nu of U^n, writes it
+    // to dtp[0] and adds it to dtp[1]; stage 2 reads dtp[0]; both derive the
+    // constants above that depend on dt themselves; stage 2 folds max nu of
+    // U^{n+1} into speed_next[1] (Sec. 3.3 eq. (eq:MCFL), Sec. 5)
+    int32_t adaptive;
+    double cfl, mcfl, dx, lam_d, g_d;
+    double* dtp;
     const float2* U[4];   // U^n (pairs)
     float2* D1[4];        // stage-1 increments dU1 (written by stage 1, read by stage 2)
     float2* out[4];       // U^{n+1} (stage 2; not aliased with U)
@@ -176,7 +221,33 @@ __global__ void __launch_bounds__(T, 2) k_df_stage(const DfParams p) {
         sm.kmax = 0u;
         sm.kmin = 0x7F7FFFFFu;
     }
-    if (p.track_speed && !two && blockIdx.x == 0 && tid == 0) *p.speed_next = 0.0;
+    if (p.track_speed && !two && blockIdx.x == 0 && tid == 0) {
+        p.speed_next[0] = 0.0;
+        if (p.adaptive) p.speed_next[1] = 0.0;
+    }
+    // the time step: fixed (from the parameters) or from the CFL rule
+    DfStepConst kc{p.tau, p.lt2, p.ltau, p.fq, p.lfq, p.Cc, p.fd};
+    if (p.adaptive) {
+        if (tid == 0) {
+            double dt;
+            if (!two) {
+                const double u = p.speed[0], nu = p.speed[1];
+                dt = p.cfl * p.dx / nu;
+                if (p.mcfl > 0.0 && u > 0.0 && u * dt / p.dx > p.mcfl) dt = p.mcfl * p.dx / u;
+                if (blockIdx.x == 0) {
+                    p.dtp[0] = dt;
+                    p.dtp[1] += dt;
+                }
+            } else {
+                dt = p.dtp[0];
+            }
+            const DfStepConst k = df_step_const(dt, p.dx, p.lam_d);
+            sm.kc[0] = k.tau; sm.kc[1] = k.lt2; sm.kc[2] = k.ltau; sm.kc[3] = k.fq;
+            sm.kc[4] = k.lfq; sm.kc[5] = k.Cc; sm.kc[6] = k.fd;
+        }
+        __syncthreads();
+        kc = DfStepConst{sm.kc[0], sm.kc[1], sm.kc[2], sm.kc[3], sm.kc[4], sm.kc[5], sm.kc[6]};
+    }
 
     // ---- 0. window cells -3 .. W+2 (index c + 3): U_l and U_b (stage 2:
     //         formed from U^n and dU1 with the efficient-form weights)
@@ -267,6 +338,32 @@ __global__ void __launch_bounds__(T, 2) k_df_stage(const DfParams p) {
             }
             st4(*F[v], j0, Fv);
         }
+        // the faces 4t .. 4t + 3 stop at 4T - 1; a full window (W = R) also
+        // needs face W + 2 = 4T (right of cell W): the last thread adds it
+        if (tid == T - 1 && W + 3 > 4 * T) {
+            const int f = 4 * T;  // cells at index f .. f + 3, all loaded (< W + 6)
+            auto face = [&](const DArr<Gm::NC>& A, R& xl, R& xr) {
+                R x0, x1, x2, x3;
+                ld1(A, f, x0);
+                ld1(A, f + 1, x1);
+                ld1(A, f + 2, x2);
+                ld1(A, f + 3, x3);
+                xl = x1 + scale(x2 - x0, 0.25f);
+                xr = x2 - scale(x3 - x1, 0.25f);
+            };
+            R hL, hR, qL, qR, mL, mR, rL, rR;
+            face(sm.hl, hL, hR);
+            face(sm.ql, qL, qR);
+            face(sm.ml, mL, mR);
+            face(sm.rl, rL, rR);
+            if (!(pos_finite(hL) && pos_finite(hR))) bad |= HSGN_DEV_ERR_DEPTH;
+            const R uL = qL / hL, uR = qR / hR;
+            const R s = p.local_speed ? dmax(dabs(uL), dabs(uR)) : spd;
+            const R wl = uL + s, wr = uR - s;
+            st1(sm.fq, f, fma(wl, qL, wr * qR));
+            st1(sm.fm, f, fma(wl, mL, wr * mR));
+            st1(sm.fr, f, fma(wl, rL, wr * rR));
+        }
     }
     __syncthreads();
 
@@ -284,7 +381,7 @@ __global__ void __launch_bounds__(T, 2) k_df_stage(const DfParams p) {
     dfl dq_[4], dm_[4], dr_[4], be_[4], de_[4];
     float kloc = 0.f, kmin = 3.0e38f;
     {
-        const R c_fq = as_R(p.fq, R()), c_tau = as_R(p.tau, R()), c_lt2 = as_R(p.lt2, R());
+        const R c_fq = as_R(kc.fq, R()), c_tau = as_R(kc.tau, R()), c_lt2 = as_R(kc.lt2, R());
         const R c_third = as_R(p.third, R()), c_g = as_R(p.g, R()), c_lam3 = as_R(p.lam3, R());
         const R c_lam = as_R(p.lam, R());
         R FQ[8], FM[8], FR[8];
@@ -330,7 +427,7 @@ __global__ void __launch_bounds__(T, 2) k_df_stage(const DfParams p) {
                 dr_[k] = to_dfl(dr);
                 be_[k] = to_dfl(beta);
                 de_[k] = to_dfl(alpha * ib1);
-                const float kb = f_mul(p.Cc.hi, hi_of(beta));
+                const float kb = f_mul(kc.Cc.hi, hi_of(beta));
                 kloc = fmaxf(kloc, kb);
                 kmin = fminf(kmin, kb);
             }
@@ -400,13 +497,13 @@ __global__ void __launch_bounds__(T, 2) k_df_stage(const DfParams p) {
                 const int f = j0 + e;  // rows f - 1 | f: per-cell index f, f + 1; state f + 2, f + 3
                 const dfl bf = scale(B8[e] + B8[e + 1], 0.5f);
                 const dfl df = scale(E8[e] + E8[e + 1], 0.5f);
-                dfl kf = p.Cc * bf;
+                dfl kf = kc.Cc * bf;
                 if (BC == BC_TRANSMISSIVE && ((f == 0 && win.lend) || (f == W && win.rend)))
                     kf = dfl(0.f);
                 const dfl dmf = sub_acc(MU[e + 3], MU[e + 2]) + sub_acc(M8[e + 1], M8[e]);
                 const dfl dhf = sub_acc(H8[e + 3], H8[e + 2]);
                 KF[e] = kf;
-                Phi[e] = fma(p.fd * df, dmf, kf * dhf);
+                Phi[e] = fma(kc.fd * df, dmf, kf * dhf);
             }
         }
         dfl Q8[8], QU[8];
@@ -418,7 +515,7 @@ __global__ void __launch_bounds__(T, 2) k_df_stage(const DfParams p) {
         for (int k = 0; k < 4; ++k) {
             // q^dag of cells i+1 and i-1: state index i + 4, i + 2; per-cell index i + 2, i
             const dfl dqc = sub_acc(QU[k + 4], QU[k + 2]) + sub_acc(Q8[k + 2], Q8[k]);
-            rd[k] = sub_acc(Phi[k + 1], Phi[k]) - p.fq * dqc;
+            rd[k] = sub_acc(Phi[k + 1], Phi[k]) - kc.fq * dqc;
         }
     }
     {
@@ -470,7 +567,7 @@ __global__ void __launch_bounds__(T, 2) k_df_stage(const DfParams p) {
     //         cancellation of their lambda tau terms)
     const int lo = win.lo, sp = win.sp;
     const int64_t t0 = win.t0;
-    dfl umax(0.f);
+    dfl umax(0.f), numax(0.f);
     for (int t = tid; t < sp; t += T) {
         const int r = lo + t;  // window row; state index r + 3, per-cell index r + 1, dh index r + 4
         const dfl dh = DH.get(r + 4);
@@ -480,14 +577,14 @@ __global__ void __launch_bounds__(T, 2) k_df_stage(const DfParams p) {
         const dfl dmv = DM.get(r + 1);
         const dfl dmc = sub_acc(sm.mb.get(r + 4), sm.mb.get(r + 2)) +
                         sub_acc(DM.get(r + 2), DM.get(r));
-        const dfl dQ = DQ.get(r + 1) - (p.fq * (BE.get(r + 1) * dhc) + p.lfq * (DE.get(r + 1) * dmc));
+        const dfl dQ = DQ.get(r + 1) - (kc.fq * (BE.get(r + 1) * dhc) + kc.lfq * (DE.get(r + 1) * dmc));
         const dfl P = sq_minus(hb, mb) + dh * (scale(hb, 2.f) + dh);
         const dfl E = P - dmv;
         const dfl hbar = hb + dh;
         const dfl h2 = hbar * hbar;
-        const dfl iDen = rcp(h2 + p.lt2);
+        const dfl iDen = rcp(h2 + kc.lt2);
         const dfl Ei = E * iDen;
-        const dfl dR = fma(p.ltau, Ei, DR.get(r + 1));
+        const dfl dR = fma(kc.ltau, Ei, DR.get(r + 1));
         const dfl dM = P - Ei * h2;
         unsigned b2 = 0;
         if (!pos_finite(hbar)) b2 |= HSGN_DEV_ERR_DEPTH;
@@ -507,7 +604,15 @@ __global__ void __launch_bounds__(T, 2) k_df_stage(const DfParams p) {
             p.out[1][gc] = make_float2(qn.hi, qn.lo);
             p.out[2][gc] = make_float2(mn.hi, mn.lo);
             p.out[3][gc] = make_float2(rn.hi, rn.lo);
-            if (p.track_speed && !b2) umax = dmax(umax, dabs(qn) / hbar);
+            if (p.track_speed && !b2) {
+                const dfl ua = dabs(qn) / hbar;
+                umax = dmax(umax, ua);
+                if (p.adaptive) {
+                    // nu = |u| + sqrt(g h + (lambda/3) eta^2/h^2) of U^{n+1} (reading R9)
+                    const dfl e = mn / (hbar * hbar);
+                    numax = dmax(numax, ua + dsqrt(fma(p.g, hbar, p.lam3 * (e * e))));
+                }
+            }
         }
     }
     if (bad) flag_error(p.err, bad);
@@ -517,6 +622,13 @@ __global__ void __launch_bounds__(T, 2) k_df_stage(const DfParams p) {
         if ((tid & 31) == 0 && umax.hi > 0.f)
             atomicMax(reinterpret_cast<unsigned long long*>(p.speed_next),
                       (unsigned long long)__double_as_longlong(dfl_to_double(umax)));
+        if (p.adaptive) {
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) numax = dmax(numax, shfl_xor_d(numax, o));
+            if ((tid & 31) == 0 && numax.hi > 0.f)
+                atomicMax(reinterpret_cast<unsigned long long*>(p.speed_next + 1),
+                          (unsigned long long)__double_as_longlong(dfl_to_double(numax)));
+        }
     }
 }
 

@@ -194,6 +194,8 @@ struct hsgn_s {
     cudaStream_t cap = nullptr;      // private stream used for graph capture
     cudaGraphExec_t gexec[2] = {};   // one step, per state buffer
     double gdt[2] = {};
+    cudaGraphExec_t gcfl[2] = {};    // one step with the device-side CFL time step
+    double gcfl_rule[2][2] = {};     // its (cfl, mcfl)
     // event-pair profiler (hsgn_profile)
     bool prof = false;
     std::vector<cudaEvent_t> ev_pool;
@@ -576,6 +578,12 @@ DfParams df_params(const hsgn_s* H, int stage, double tau, double wl1, double wb
     p.third = dfl_of(1.0 / 3.0);
     p.wl1 = dfl_of(wl1);
     p.wb1 = dfl_of(wb1);
+    p.adaptive = 0;
+    p.cfl = p.mcfl = 0.0;
+    p.dx = dx;
+    p.lam_d = lam;
+    p.g_d = H->g;
+    p.dtp = H->spd + 6;
     for (int k = 0; k < 4; ++k) {
         p.U[k] = nullptr;
         p.D1[k] = H->D1[k];
@@ -591,11 +599,19 @@ unsigned df_tiles(const hsgn_s* H) { return (unsigned)((H->n + H->tileS - 1) / H
 
 // One stage of the double-float path (hsgn_dfstage.cuh): one launch. Stage 1
 // writes the increments dU1, stage 2 writes U^{n+1} into the other buffer.
-cudaError_t launch_stage_df(hsgn_s* H, int stage, double tau, cudaStream_t st) {
+// cfl > 0: the step's dt from the CFL rule of the current state, on the
+// device (DfParams::adaptive); tau is then unused.
+cudaError_t launch_stage_df(hsgn_s* H, int stage, double tau, cudaStream_t st, double cfl = 0.0,
+                            double mcfl = 0.0) {
     const double gam = 1.0 - 1.0 / std::sqrt(2.0);
     const double c = 1.0 / (2.0 * gam);
     DfParams p = df_params(H, stage, tau, stage == 2 ? c / gam : 0.0,
                            stage == 2 ? (1.0 - gam) / gam : 0.0);
+    if (cfl > 0.0) {
+        p.adaptive = 1;
+        p.cfl = cfl;
+        p.mcfl = mcfl;
+    }
     double* const* Uc = state(H);
     double* const* Un = H->cur ? H->U : H->V;
     for (int k = 0; k < 4; ++k) {
@@ -1101,8 +1117,10 @@ void hsgn_destroy(hsgn_handle_t H) {
         cudaEventDestroy(r.b);
     }
     for (cudaEvent_t e : H->ev_pool) cudaEventDestroy(e);
-    for (int c = 0; c < 2; ++c)
+    for (int c = 0; c < 2; ++c) {
         if (H->gexec[c]) cudaGraphExecDestroy(H->gexec[c]);
+        if (H->gcfl[c]) cudaGraphExecDestroy(H->gcfl[c]);
+    }
     if (H->cap) cudaStreamDestroy(H->cap);
     cudaFree(H->mem);
     delete H;
@@ -1233,6 +1251,63 @@ int hsgn_enqueue(hsgn_handle_t H, double dt, int64_t n_steps, void* stream) {
         if (H->windowed) H->cur ^= 1;
     }
     return HSGN_OK;
+}
+
+int hsgn_run_cfl(hsgn_handle_t H, double cfl, double mcfl, int64_t n_steps, double* t_advanced,
+                 void* stream) {
+    if (!H || !t_advanced || !(cfl > 0.0) || !std::isfinite(cfl) || !(mcfl >= 0.0) ||
+        !std::isfinite(mcfl) || n_steps < 0)
+        return HSGN_ERR_INVALID_ARG;
+    if (!H->dfloat || H->batched || local_speed(H)) return HSGN_ERR_UNIMPLEMENTED;
+    cudaStream_t st = as_stream(stream);
+    // max |u| and max nu of the current state (set_state and fixed steps keep
+    // only max |u|), and the time advanced so far
+    double* const cur = speed_of(H, H->cur);
+    if (cudaMemsetAsync(cur, 0, 2 * sizeof(double), st) != cudaSuccess ||
+        cudaMemsetAsync(H->spd + 6, 0, 2 * sizeof(double), st) != cudaSuccess)
+        return HSGN_ERR_CUDA;
+    launch_speeds(H, cur, st);
+    if (cudaGetLastError() != cudaSuccess) return HSGN_ERR_CUDA;
+    for (int64_t k = 0; k < n_steps; ++k) {
+        const int c = H->cur;
+        if (!H->gcfl[c] || H->gcfl_rule[c][0] != cfl || H->gcfl_rule[c][1] != mcfl) {
+            const bool prof = H->prof;
+            H->prof = false;
+            if (H->gcfl[c]) {
+                cudaGraphExecDestroy(H->gcfl[c]);
+                H->gcfl[c] = nullptr;
+            }
+            cudaGraph_t graph = nullptr;
+            if (cudaStreamBeginCapture(H->cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+                H->prof = prof;
+                return HSGN_ERR_CUDA;
+            }
+            cudaError_t e1 = launch_stage_df(H, 1, 0.0, H->cap, cfl, mcfl);
+            if (e1 == cudaSuccess) e1 = launch_stage_df(H, 2, 0.0, H->cap, cfl, mcfl);
+            const cudaError_t e2 = cudaStreamEndCapture(H->cap, &graph);
+            H->prof = prof;
+            if (e1 != cudaSuccess || e2 != cudaSuccess) {
+                if (graph) cudaGraphDestroy(graph);
+                cudaGetLastError();
+                return HSGN_ERR_CUDA;
+            }
+            const cudaError_t e3 = cudaGraphInstantiate(&H->gcfl[c], graph, 0);
+            cudaGraphDestroy(graph);
+            if (e3 != cudaSuccess) {
+                H->gcfl[c] = nullptr;
+                cudaGetLastError();
+                return HSGN_ERR_CUDA;
+            }
+            H->gcfl_rule[c][0] = cfl;
+            H->gcfl_rule[c][1] = mcfl;
+        }
+        if (cudaGraphLaunch(H->gcfl[c], st) != cudaSuccess) return HSGN_ERR_CUDA;
+        H->cur ^= 1;
+    }
+    if (cudaMemcpyAsync(t_advanced, H->spd + 7, sizeof(double), cudaMemcpyDeviceToHost, st) !=
+        cudaSuccess)
+        return HSGN_ERR_CUDA;
+    return read_error(H, st);
 }
 
 int hsgn_run(hsgn_handle_t H, double dt, int64_t n_steps, void* stream) {

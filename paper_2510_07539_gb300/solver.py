@@ -185,6 +185,17 @@ class Solver:
     def run(self, dt: float, n_steps: int, stream=None):
         _check(_lib.hsgn_run(self._h, float(dt), int(n_steps), _stream(stream)), "hsgn_run")
 
+    def run_cfl(self, cfl: float, mcfl: float, n_steps: int, stream=None) -> float:
+        """n_steps steps, each with dt from the CFL rule of its own state
+        (hsgn_run_cfl, double-float forms); returns the time advanced."""
+        f = _lib.hsgn_run_cfl
+        f.argtypes = [_P, _D, _D, _I64, ctypes.POINTER(_D), _P]
+        f.restype = ctypes.c_int
+        t = _D()
+        _check(f(self._h, float(cfl), float(mcfl), int(n_steps), ctypes.byref(t),
+                 _stream(stream)), "hsgn_run_cfl")
+        return t.value
+
     def enqueue(self, dt: float, n_steps: int, stream=None):
         _check(_lib.hsgn_enqueue(self._h, float(dt), int(n_steps), _stream(stream)), "hsgn_enqueue")
 

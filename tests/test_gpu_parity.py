@@ -890,3 +890,40 @@ def test_windowed_at_2_27_cells_properties():
         scale = np.linalg.norm(b if k in (0, 2) else sc[k][cs - w:cs + w])
         bound = 1e-7 if k in (0, 2) else 1e-6
         assert np.linalg.norm(a - b) <= bound * scale, (k, np.linalg.norm(a - b) / scale)
+
+
+# --------------------------------------------------------------------------
+# per-step time step on the device (hsgn_run_cfl, Sec. 5)
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("bc", [0, 1])
+@pytest.mark.parametrize("cfl,mcfl", [(2.0, 0.5), (4.0, 0.0)])
+def test_run_cfl_matches_the_oracle_policy(bc, cfl, mcfl):
+    # every step takes dt = min(cfl dx/nu_max, mcfl dx/u_max) of the state it
+    # starts from: the oracle re-evaluates its time-step rule before each step,
+    # the library folds the maxima on the device; both must take the same
+    # steps (1e-13 relative in time) and stay within the FP64 trajectory bound
+    n, dx, lam, steps = 3001, 0.1, 500.0, 30
+    x = (np.arange(n) + 0.5) * dx
+    U = inputs.solitary(x, 1.0, 0.3, 0.5 * n * dx, period=n * dx)
+    p = oracle.Params(n, dx, bc, lam=lam)
+    V, t_ref = U, 0.0
+    for _ in range(steps):
+        dt, _, _ = oracle.suggest_dt(p, V, cfl, mcfl)
+        V = oracle.step(p, V, dt)
+        t_ref += dt
+    with S().Solver(n, 0.0, n * dx, bc, lam=lam, flags=S().FLAG_DOUBLE_FLOAT) as s:
+        s.set_state(*(dev(u) for u in U))
+        t = s.run_cfl(cfl, mcfl, 10)
+        t += s.run_cfl(cfl, mcfl, steps - 10)
+        got = [u.cpu().numpy() for u in s.get_state()]
+    assert abs(t - t_ref) <= 1e-13 * t_ref, (t, t_ref)
+    for k in range(4):
+        assert rel_l2(got[k], V[k]) < 1e-10, (k, rel_l2(got[k], V[k]))
+
+
+def test_run_cfl_needs_the_double_float_form():
+    for flags in (S().FLAG_FP64, S().FLAG_MIXED, S().FLAG_DOUBLE_FLOAT | S().FLAG_RUSANOV_LOCAL):
+        with S().Solver(64, 0.0, 6.4, 0, lam=10.0, flags=flags) as s:
+            with pytest.raises(S().HsgnError) as e:
+                s.run_cfl(2.0, 0.5, 1)
+            assert e.value.code == 6

@@ -8,11 +8,14 @@
 // tiles cover the grid once, that the rows kept from a window lie HW - 1 rows
 // or more inside it, and that the two tiles beside a face build the same
 // mini-window, and that the four cells per thread of the cell, row and solve
-// phases cover the window within the arrays. Exit status 0 when every check
-// passes.
+// phases cover the window within the arrays. The same for the double-float
+// stage (k_df_stage in hsgn_dfstage.cuh, 96-row overlap): in addition, the
+// faces its flux phase writes (four per thread, plus face 4T from the last
+// thread when the window is full) cover every face its cell phase reads.
+// Exit status 0 when every check passes.
 #include <cstdio>
 #include <cstdlib>
-#include "../paper_2510_07539_gb300/csrc/hsgn_fused.cuh"
+#include "../paper_2510_07539_gb300/csrc/hsgn_dfstage.cuh"
 
 using namespace hsgn;
 constexpr int M = 4, HW = 64;
@@ -119,6 +122,52 @@ void check(int64_t n, int S) {
     CHECK(covered == n);
 }
 
+// The double-float stage: T = 256 threads, four rows each, overlap DHW.
+constexpr int DT = 256, DHW = 96;
+
+template <int BC>
+void check_df(int64_t n, int S) {
+    using G = DfGeom<DT, M, DHW>;
+    int64_t p = -1;
+    CHECK(S >= 1 && S <= G::S);
+    CHECK(G::NC % 4 == 0 && 4 * DT + 4 <= G::NC);  // get4 at 4t + 4 reads up to 4T + 3
+    const int64_t P = (n + S - 1) / S;
+    int64_t covered = 0;
+    for (p = 0; p < P; ++p) {
+        ++checked_windows;
+        const Window w = window_of<BC>(p, n, S, DHW);
+        CHECK(w.sp >= 1 && w.sp <= S && w.t0 == covered);
+        covered += w.sp;
+        CHECK(w.W >= 1 && w.W <= G::R && w.W + 1 <= DT * M);
+        CHECK(w.lo >= 0 && w.lo + w.sp <= w.W);
+        CHECK(w.W + 6 <= G::NC);  // loaded cells -3 .. W + 2
+        const bool inner = inner_window(w.wl, w.W, n);
+        for (int j = 0; j < w.W + 6; ++j) {
+            const int64_t gi = inner ? w.wl - 3 + j : cell_at<BC>(w.wl - 3 + j, n);
+            CHECK(gi >= 0 && gi < n);
+            CHECK(gi == cell_at<BC>(w.wl - 3 + j, n));
+        }
+        // flux phase: thread t writes faces 4t .. 4t + 3; the last thread also
+        // face 4T when W + 3 > 4T. The cell phase reads faces 0 .. W + 2 (cells
+        // c = -1 .. W, faces j and j + 1 of cell j - 1); a face f is built from
+        // the loaded cells at index f .. f + 3
+        const int top = (w.W + 3 > 4 * DT) ? 4 * DT : 4 * DT - 1;  // highest face written
+        CHECK(w.W + 2 <= top);
+        CHECK(top + 3 < G::NC);
+        for (int f = 0; f <= w.W + 2; ++f) CHECK(f + 3 < w.W + 6);
+        // cell phase: cell j (j < W + 2) reads state index j + 2 (loaded) and
+        // writes per-cell index j; row phase: row i < W reads per-cell indices
+        // i .. i + 2 and state indices i + 2 .. i + 4; back-substitution: tile row
+        // r reads dh at r + 3 .. r + 5 (rows -1 .. W, index 3 a ghost only at a
+        // transmissive left end, where lo = 0)
+        CHECK(w.W + 1 + 2 < w.W + 6);
+        CHECK(w.W - 1 + 4 < w.W + 6);
+        CHECK(w.lo + w.sp - 1 + 5 <= w.W + 4 && w.W + 4 < G::NC);
+        CHECK(w.lo >= 1 || (BC == BC_TRANSMISSIVE && w.lend));
+    }
+    CHECK(covered == n);
+}
+
 template <int BC>
 void check_grid(int64_t n) {
     using G = FusedGeom<256, M, HW>;
@@ -126,6 +175,9 @@ void check_grid(int64_t n) {
     for (int64_t slots : {1, 2, 152, 304, 456, 608})
         check<256, BC>(n, (int)fused_tile_rows(n, G::S, slots));
     check<128, BC>(n, (int)fused_tile_rows(n, Gs::S, 1));
+    using D = DfGeom<DT, M, DHW>;
+    for (int64_t slots : {1, 2, 152, 304})
+        check_df<BC>(n, (int)fused_tile_rows(n, D::S, slots));
 }
 
 int main() {
@@ -149,7 +201,14 @@ int main() {
             check<128, BC_PERIODIC>(k * Gs::S + e, Gs::S);
             check<128, BC_TRANSMISSIVE>(k * Gs::S + e, Gs::S);
         }
-    printf("large: R=%d S=%d NC=%d; small: R=%d S=%d NC=%d; windows=%lld\n"
-           "all index checks passed\n", G::R, G::S, G::NC, Gs::R, Gs::S, Gs::NC, checked_windows);
+    // full double-float windows (tiles of the largest size, as a 2^16 grid gets)
+    using D = DfGeom<DT, M, DHW>;
+    for (int64_t k = 1; k <= 80; ++k) {
+        check_df<BC_PERIODIC>(k * D::S, D::S);
+        check_df<BC_TRANSMISSIVE>(k * D::S + 1, D::S);
+    }
+    printf("large: R=%d S=%d NC=%d; small: R=%d S=%d NC=%d; double-float: R=%d S=%d NC=%d; "
+           "windows=%lld\nall index checks passed\n", G::R, G::S, G::NC, Gs::R, Gs::S, Gs::NC,
+           D::R, D::S, D::NC, checked_windows);
     return 0;
 }
