@@ -314,24 +314,39 @@ int hsgn_batched_suggest_dt(hsgn_handle_t h, double cfl, double mcfl, double* dt
 
 /* Tiles of a batch (the windowed kernel; HSGN_ERR_UNIMPLEMENTED for a batch
  * created with HSGN_EXACT_SOLVE). variant[k] (host array of `count`) selects
- * for instance k the large windowed kernel (0: 256 threads, tiles of up to 894
- * rows, the default) or the small one (1: 128 threads, tiles of up to 382
- * rows, less padding for short instances); each kernel then runs as one launch
- * per stage over its instances' tiles. Values other than 0 and 1 give
- * INVALID_ARG. Synchronises the device; the results of both variants agree to
- * the rounding of the single-precision increments. */
+ * the windowed kernel of instance k:
+ *   0: 256 threads, 64-row window overlap, tiles of up to 894 rows (default);
+ *   1: 128 threads, 64-row overlap, tiles of up to 382 rows (less padding for
+ *      short instances);
+ *   2: 256 threads, 32-row overlap, tiles of up to 958 rows;
+ *   3: 128 threads, 32-row overlap, tiles of up to 446 rows.
+ * The narrow overlap (2, 3) needs the depth coupling to decay fast (small
+ * CFL numbers); each CTA checks its truncation bound (2^-30) and the next
+ * synchronising call reports HSGN_ERR_TRUNCATION when it does not hold. Each
+ * variant in use runs as one launch per stage over its instances' tiles.
+ * Values outside 0 .. 3 give INVALID_ARG. Synchronises the device; the
+ * results of the variants agree to the rounding of the single-precision
+ * increments. */
 int hsgn_batched_set_tiles(hsgn_handle_t h, const int32_t* variant);
 
+/* The tile variant of every instance (0 .. 3, as hsgn_batched_set_tiles;
+ * variant_out: host array of `count`), e.g. after hsgn_batched_autotune.
+ * HSGN_ERR_UNIMPLEMENTED for a batch created with HSGN_EXACT_SOLVE. */
+int hsgn_batched_get_tiles(hsgn_handle_t h, int32_t* variant_out);
+
 /* Autotuner of the tiles: from the current state (restored exactly after every
- * trial), times `steps` >= 1 steps with every instance on the large variant,
- * then on the small one; from these a cost per tile of each variant gives
- * each instance the variant of smaller predicted cost, and that assignment is
- * timed when it mixes the two. The fastest timed assignment is kept.
- * ms_out (host, 3 doubles, may be NULL): ms per step of all-large, all-small
- * and the mixed assignment (NaN when not timed); choice_out (may be NULL): 0,
- * 1 or 2 for the assignment kept. Needs hsgn_batched_set_dt first
- * (INVALID_ARG otherwise); allocates 32 bytes per cell for the duration of the
- * call; synchronises. */
+ * trial), times `steps` >= 1 steps with every instance on each of the four
+ * variants of hsgn_batched_set_tiles in turn (a variant that reports
+ * HSGN_ERR_TRUNCATION for this batch and time step is ruled out); from these
+ * a cost per tile of each variant gives each instance the variant of smallest
+ * predicted cost, and that assignment is timed when it mixes variants. The
+ * fastest timed assignment is kept. ms_out (host, 5 doubles, may be NULL): ms
+ * per step with every instance on variant 0, 1, 2, 3, then of the per-instance
+ * assignment (NaN when not timed or ruled out); choice_out (may be NULL): the
+ * variant kept for every instance (0 .. 3), or 4 for the per-instance
+ * assignment. HSGN_ERR_TRUNCATION when every variant is ruled out. Needs
+ * hsgn_batched_set_dt first (INVALID_ARG otherwise); allocates 32 bytes per
+ * cell for the duration of the call; synchronises. */
 int hsgn_batched_autotune(hsgn_handle_t h, int32_t steps, double* ms_out, int32_t* choice_out,
                           void* stream);
 

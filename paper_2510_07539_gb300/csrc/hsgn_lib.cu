@@ -36,9 +36,14 @@ constexpr int FT = 256, FM = 4, FHW = 64;
 // (wider than the mixed stage's: the truncation bound is 2^-50, not 2^-30, and
 // 95 rows keep it up to CFL_IMEX of about 7 for smooth states).
 constexpr int DT = 256, DHW = 96;
-// Small variant of the windowed stage for batches (tiles of 382 rows instead of
-// 894), chosen per instance by hsgn_batched_set_tiles / hsgn_batched_autotune.
-constexpr int FTS = 128;
+// Variants of the windowed stage for batches, chosen per instance by
+// hsgn_batched_set_tiles / hsgn_batched_autotune: v = 0 and 1 take FT = 256 and
+// FTS = 128 threads (tiles of up to 894 / 382 rows) with the FHW-row overlap,
+// v = 2 and 3 the same thread counts with a narrow FHWN-row overlap (tiles of
+// up to 958 / 446 rows), which meets the 2^-30 truncation bound where the
+// depth coupling decays fast (small CFL numbers) and reports
+// HSGN_ERR_TRUNCATION elsewhere.
+constexpr int FTS = 128, FHWN = 32, kBV = 4;
 // Separator levels: one warp per block of GS rows; one warp solves up to RMAX rows.
 constexpr int GS = SEP_ROWS, RMAX = SEP_ROWS;
 
@@ -163,7 +168,7 @@ struct hsgn_s {
     bool windowed = false;
     int32_t tileS = 0;               // tile rows per CTA
     int32_t tileSlots = 0;           // co-resident CTAs of the windowed kernel
-    int32_t tileSlotsSmall = 0;      // the same for the small variant (batches)
+    int32_t vslots[4] = {};          // co-resident CTAs of each batch variant
     double* V[4] = {};
     int cur = 0;                     // 1: the state is in V
     // mixed precision (HSGN_MIXED): FP32 stage-1 increments and per-row results
@@ -185,9 +190,9 @@ struct hsgn_s {
     double* speeds_next = nullptr;   // windowed batch: per-instance speed while the state is in V
     int32_t* tile_inst = nullptr;    // windowed batch: instance of every large tile (device)
     int64_t total_tiles = 0;
-    int32_t* tile_inst_small = nullptr;  // ... of every tile of the small variant
-    int64_t tiles_small = 0;
-    std::vector<int8_t> variant;     // per instance: 0 large, 1 small windowed variant
+    int32_t* vtile[4] = {};          // windowed batch: instance of every tile of each
+    int64_t vtiles[4] = {};          //   batch variant (vtile[0] is tile_inst), tile counts
+    std::vector<int8_t> variant;     // per instance: its batch variant, 0 .. 3
     std::vector<InstInfo> inst_h;    // host copy
     float *mblk = nullptr, *ms_ = nullptr;
     unsigned* err = nullptr;
@@ -433,21 +438,50 @@ cudaError_t launch_stage_mixed(hsgn_s* H, int stage, double tau, cudaStream_t st
 }
 
 // One launch of the windowed stage kernel specialised for p.stage.
-template <int T, int BC, bool WB>
+template <int T, int BC, bool WB, int HW = FHW>
 void launch_fused(unsigned P, const FusedParams& p, cudaStream_t st) {
-    const size_t smem = sizeof(FusedShared<T, FM, FHW, WB>);
+    const size_t smem = sizeof(FusedShared<T, FM, HW, WB>);
     if (p.stage == 2)
-        k_mixed_fused<T, FM, FHW, BC, WB, 2><<<P, T, smem, st>>>(p);
+        k_mixed_fused<T, FM, HW, BC, WB, 2><<<P, T, smem, st>>>(p);
     else
-        k_mixed_fused<T, FM, FHW, BC, WB, 1><<<P, T, smem, st>>>(p);
+        k_mixed_fused<T, FM, HW, BC, WB, 1><<<P, T, smem, st>>>(p);
 }
 
 // Dynamic shared-memory limit of both stage kernels of one variant.
-template <int T, int BC, bool WB>
+template <int T, int BC, bool WB, int HW = FHW>
 cudaError_t set_smem_fused() {
-    const size_t smem = sizeof(FusedShared<T, FM, FHW, WB>);
-    cudaError_t e = set_smem(k_mixed_fused<T, FM, FHW, BC, WB, 1>, smem);
-    if (e == cudaSuccess) e = set_smem(k_mixed_fused<T, FM, FHW, BC, WB, 2>, smem);
+    const size_t smem = sizeof(FusedShared<T, FM, HW, WB>);
+    cudaError_t e = set_smem(k_mixed_fused<T, FM, HW, BC, WB, 1>, smem);
+    if (e == cudaSuccess) e = set_smem(k_mixed_fused<T, FM, HW, BC, WB, 2>, smem);
+    return e;
+}
+
+// Batch variant v (flat bottom): launch, largest tile, co-resident CTAs per SM.
+template <int BC>
+void launch_batch_variant(int v, unsigned P, const FusedParams& p, cudaStream_t st) {
+    switch (v) {
+        case 0: launch_fused<FT, BC, false, FHW>(P, p, st); break;
+        case 1: launch_fused<FTS, BC, false, FHW>(P, p, st); break;
+        case 2: launch_fused<FT, BC, false, FHWN>(P, p, st); break;
+        default: launch_fused<FTS, BC, false, FHWN>(P, p, st); break;
+    }
+}
+
+int64_t batch_variant_smax(int v) {
+    switch (v) {
+        case 0: return FusedGeom<FT, FM, FHW>::S;
+        case 1: return FusedGeom<FTS, FM, FHW>::S;
+        case 2: return FusedGeom<FT, FM, FHWN>::S;
+        default: return FusedGeom<FTS, FM, FHWN>::S;
+    }
+}
+
+template <int T, int HW>
+cudaError_t batch_variant_slots(int sms, int32_t& slots) {
+    int per_sm = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+        &per_sm, k_mixed_fused<T, FM, HW, BC_PERIODIC, false, 2>, T, sizeof(FusedShared<T, FM, HW>));
+    slots = sms * (per_sm > 0 ? per_sm : 1);
     return e;
 }
 
@@ -492,23 +526,21 @@ cudaError_t launch_stage_fused(hsgn_s* H, int stage, double tau, cudaStream_t st
     p.inst = H->inst;
     p.tile_inst = H->tile_inst;
     p.bathy = H->bathy_df;
-    const unsigned P = H->batched ? (unsigned)H->total_tiles
-                                  : (unsigned)((H->n + H->tileS - 1) / H->tileS);
+    const unsigned P = (unsigned)((H->n + H->tileS - 1) / H->tileS);
     {
         ProfScope ps(H, HSGN_PROF_ASSEMBLE, st);
-        if (H->batched && H->tiles_small > 0) {
-            // instances on the small variant: a launch of their own over their tiles
-            FusedParams ps_ = p;
-            ps_.tile_inst = H->tile_inst_small;
-            ps_.slots = H->tileSlotsSmall;
-            const unsigned Ps = (unsigned)H->tiles_small;
-            if (H->bc == BC_PERIODIC)
-                launch_fused<FTS, BC_PERIODIC, false>(Ps, ps_, st);
-            else
-                launch_fused<FTS, BC_TRANSMISSIVE, false>(Ps, ps_, st);
-        }
-        if (P == 0) {
-            // every instance of the batch runs on the small variant
+        if (H->batched) {
+            // one launch per variant in use, each over its own tile table
+            for (int v = 0; v < kBV; ++v) {
+                if (H->vtiles[v] == 0) continue;
+                FusedParams pv = p;
+                pv.tile_inst = H->vtile[v];
+                pv.slots = H->vslots[v];
+                if (H->bc == BC_PERIODIC)
+                    launch_batch_variant<BC_PERIODIC>(v, (unsigned)H->vtiles[v], pv, st);
+                else
+                    launch_batch_variant<BC_TRANSMISSIVE>(v, (unsigned)H->vtiles[v], pv, st);
+            }
         } else if (H->wb) {
             if (H->bc == BC_PERIODIC)
                 launch_fused<FT, BC_PERIODIC, true>(P, p, st);
@@ -838,38 +870,35 @@ cudaError_t refresh_speed(hsgn_s* H, cudaStream_t st) {
 inline cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
 
 
-// Tiles of a windowed batch: instance k runs on the large (var[k] = 0) or the
-// small (var[k] = 1) windowed kernel with equal tiles of at most that kernel's
-// rows; instance info and both tile tables are rewritten (the device must be
-// idle) and the captured step graphs dropped, since the launches change.
-template <int T>
-int64_t tiles_of(int64_t n) {
-    const int64_t s = fused_tile_rows(n, FusedGeom<T, FM, FHW>::S, 1);
+// Tiles of a windowed batch: instance k runs on batch variant var[k] with
+// equal tiles of at most that variant's rows; instance info and the tile
+// tables are rewritten (the device must be idle) and the captured step graphs
+// dropped, since the launches change.
+int64_t batch_variant_tiles(int v, int64_t n) {
+    const int64_t s = fused_tile_rows(n, batch_variant_smax(v), 1);
     return (n + s - 1) / s;
 }
 
 cudaError_t assign_tiles(hsgn_s* H, const std::vector<int8_t>& var) {
-    std::vector<int32_t> t0, t1;
+    std::vector<int32_t> t[kBV];
     for (int32_t k = 0; k < H->count; ++k) {
         InstInfo& I = H->inst_h[(size_t)k];
-        const int64_t smax = var[(size_t)k] ? FusedGeom<FTS, FM, FHW>::S : FusedGeom<FT, FM, FHW>::S;
-        std::vector<int32_t>& t = var[(size_t)k] ? t1 : t0;
-        I.base = fused_tile_rows(I.n, smax, 1);
+        const int v = var[(size_t)k];
+        I.base = fused_tile_rows(I.n, batch_variant_smax(v), 1);
         I.P = (int32_t)((I.n + I.base - 1) / I.base);
-        I.blk0 = (int32_t)t.size();
-        for (int32_t b = 0; b < I.P; ++b) t.push_back(k);
+        I.blk0 = (int32_t)t[v].size();
+        for (int32_t b = 0; b < I.P; ++b) t[v].push_back(k);
     }
     cudaError_t e = cudaMemcpy(H->inst, H->inst_h.data(), H->count * sizeof(InstInfo),
                                cudaMemcpyHostToDevice);
-    if (e == cudaSuccess && !t0.empty())
-        e = cudaMemcpy(H->tile_inst, t0.data(), t0.size() * sizeof(int32_t), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess && !t1.empty())
-        e = cudaMemcpy(H->tile_inst_small, t1.data(), t1.size() * sizeof(int32_t),
-                       cudaMemcpyHostToDevice);
+    for (int v = 0; v < kBV && e == cudaSuccess; ++v)
+        if (!t[v].empty())
+            e = cudaMemcpy(H->vtile[v], t[v].data(), t[v].size() * sizeof(int32_t),
+                           cudaMemcpyHostToDevice);
     if (e != cudaSuccess) return e;
     H->variant = var;
-    H->total_tiles = (int64_t)t0.size();
-    H->tiles_small = (int64_t)t1.size();
+    for (int v = 0; v < kBV; ++v) H->vtiles[v] = (int64_t)t[v].size();
+    H->total_tiles = H->vtiles[0];
     for (int c = 0; c < 2; ++c)
         if (H->gexec[c]) {
             cudaGraphExecDestroy(H->gexec[c]);
@@ -1794,7 +1823,7 @@ int hsgn_create_batched(int32_t count, const int64_t* n, const double* x_left,
     std::vector<InstInfo> info((size_t)count);
     std::vector<int32_t> binst;
     int64_t cells = 0;
-    int64_t blocks = 0, small_cap = 0;
+    int64_t blocks = 0, vcap[kBV] = {0, 0, 0, 0};
     for (int32_t k = 0; k < count; ++k) {
         const int64_t nk = n[k];
         if (nk < 3 || (!windowed && nk > (int64_t)SEP_ROWS * AS) || nk > ((int64_t)1 << 31))
@@ -1816,7 +1845,7 @@ int hsgn_create_batched(int32_t count, const int64_t* n, const double* x_left,
             I.base = fused_tile_rows(nk, FusedGeom<FT, FM, FHW>::S, 1);
             I.P = (int32_t)((nk + I.base - 1) / I.base);
             I.rem = 0;
-            small_cap += tiles_of<FTS>(nk);
+            for (int v = 1; v < kBV; ++v) vcap[v] += batch_variant_tiles(v, nk);
         } else {
             const BlockSplit s = make_split(nk, AS);
             I.base = s.base;
@@ -1850,7 +1879,8 @@ int hsgn_create_batched(int32_t count, const int64_t* n, const double* x_left,
     if (!windowed)
         total += align_up(BLK_STRIDE * blocks * sizeof(float)) + align_up(blocks * sizeof(float));
     total += align_up(count * sizeof(InstInfo)) + align_up(blocks * sizeof(int32_t));
-    if (windowed) total += align_up(small_cap * sizeof(int32_t));
+    if (windowed)
+        for (int v = 1; v < kBV; ++v) total += align_up(vcap[v] * sizeof(int32_t));
     total += 4 * align_up(count * sizeof(double));
     total += align_up(8 * sizeof(double)) + align_up(sizeof(unsigned));
     if (cudaMalloc(&H->mem, total) != cudaSuccess) {
@@ -1880,7 +1910,9 @@ int hsgn_create_batched(int32_t count, const int64_t* n, const double* x_left,
     H->blk_inst = reinterpret_cast<int32_t*>(take(align_up(blocks * sizeof(int32_t))));
     if (windowed) {
         H->tile_inst = H->blk_inst;
-        H->tile_inst_small = reinterpret_cast<int32_t*>(take(align_up(small_cap * sizeof(int32_t))));
+        H->vtile[0] = H->blk_inst;
+        for (int v = 1; v < kBV; ++v)
+            H->vtile[v] = reinterpret_cast<int32_t*>(take(align_up(vcap[v] * sizeof(int32_t))));
     }
     H->speeds = reinterpret_cast<double*>(take(align_up(count * sizeof(double))));
     H->speeds_tmp = reinterpret_cast<double*>(take(2 * align_up(count * sizeof(double))));
@@ -1901,20 +1933,19 @@ int hsgn_create_batched(int32_t count, const int64_t* n, const double* x_left,
     if (e == cudaSuccess) e = set_smem_fused<FT, BC_TRANSMISSIVE, false>();
     if (e == cudaSuccess) e = set_smem_fused<FTS, BC_PERIODIC, false>();
     if (e == cudaSuccess) e = set_smem_fused<FTS, BC_TRANSMISSIVE, false>();
+    if (e == cudaSuccess) e = set_smem_fused<FT, BC_PERIODIC, false, FHWN>();
+    if (e == cudaSuccess) e = set_smem_fused<FT, BC_TRANSMISSIVE, false, FHWN>();
+    if (e == cudaSuccess) e = set_smem_fused<FTS, BC_PERIODIC, false, FHWN>();
+    if (e == cudaSuccess) e = set_smem_fused<FTS, BC_TRANSMISSIVE, false, FHWN>();
     if (e == cudaSuccess && windowed) {
         // co-resident CTAs of each variant (the next-wave L2 prefetch)
-        int sms = 0, large = 0, small = 0;
+        int sms = 0;
         e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, H->device);
-        if (e == cudaSuccess)
-            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-                &large, k_mixed_fused<FT, FM, FHW, BC_PERIODIC, false, 2>, FT,
-                sizeof(FusedShared<FT, FM, FHW>));
-        if (e == cudaSuccess)
-            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-                &small, k_mixed_fused<FTS, FM, FHW, BC_PERIODIC, false, 2>, FTS,
-                sizeof(FusedShared<FTS, FM, FHW>));
-        H->tileSlots = sms * large;
-        H->tileSlotsSmall = sms * small;
+        if (e == cudaSuccess) e = batch_variant_slots<FT, FHW>(sms, H->vslots[0]);
+        if (e == cudaSuccess) e = batch_variant_slots<FTS, FHW>(sms, H->vslots[1]);
+        if (e == cudaSuccess) e = batch_variant_slots<FT, FHWN>(sms, H->vslots[2]);
+        if (e == cudaSuccess) e = batch_variant_slots<FTS, FHWN>(sms, H->vslots[3]);
+        H->tileSlots = H->vslots[0];
     }
     if (e == cudaSuccess && windowed) e = assign_tiles(H, std::vector<int8_t>((size_t)count, 0));
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&H->cap, cudaStreamNonBlocking);
@@ -1980,19 +2011,27 @@ int hsgn_batched_set_tiles(hsgn_handle_t H, const int32_t* variant) {
     if (!H->windowed) return HSGN_ERR_UNIMPLEMENTED;
     std::vector<int8_t> var((size_t)H->count);
     for (int32_t k = 0; k < H->count; ++k) {
-        if (variant[k] != 0 && variant[k] != 1) return HSGN_ERR_INVALID_ARG;
+        if (variant[k] < 0 || variant[k] >= kBV) return HSGN_ERR_INVALID_ARG;
         var[(size_t)k] = (int8_t)variant[k];
     }
     if (cudaDeviceSynchronize() != cudaSuccess) return HSGN_ERR_CUDA;
     return assign_tiles(H, var) == cudaSuccess ? HSGN_OK : HSGN_ERR_CUDA;
 }
 
+int hsgn_batched_get_tiles(hsgn_handle_t H, int32_t* variant_out) {
+    if (!H || !H->batched || !variant_out) return HSGN_ERR_INVALID_ARG;
+    if (!H->windowed) return HSGN_ERR_UNIMPLEMENTED;
+    for (int32_t k = 0; k < H->count; ++k) variant_out[k] = H->variant[(size_t)k];
+    return HSGN_OK;
+}
+
 // Autotuner of the batch's tiles: times `steps` steps from the current state
-// (restored after every trial) with every instance on the large variant, then
-// on the small one; from the two times a cost per tile of each variant
-// (ms / tiles launched), which assigns each instance the variant with the
-// smaller predicted cost (tiles x cost per tile); that assignment is timed as
-// well when it mixes the variants. The fastest of the timed assignments stays.
+// (restored after every trial) with every instance on each batch variant in
+// turn; a variant whose windows report HSGN_ERR_TRUNCATION for this batch (its
+// overlap too narrow for the coupling) is ruled out. From the times a cost per
+// tile of each variant (ms / tiles launched) assigns each instance the variant
+// with the smallest predicted cost (tiles x cost per tile); that assignment is
+// timed as well when it mixes variants. The fastest timed assignment stays.
 int hsgn_batched_autotune(hsgn_handle_t H, int32_t steps, double* ms_out, int32_t* choice_out,
                           void* stream) {
     if (!H || !H->batched || steps < 1) return HSGN_ERR_INVALID_ARG;
@@ -2013,65 +2052,74 @@ int hsgn_batched_autotune(hsgn_handle_t H, int32_t steps, double* ms_out, int32_
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) rc = HSGN_ERR_CUDA;
     if (rc == HSGN_OK) rc = hsgn_get_state(H, kp[0], kp[1], kp[2], kp[3], stream);
     const std::vector<int8_t> start = H->variant;
+    const double nan = std::nan("");
+    // one timed assignment; a truncation report rules it out (ms stays NaN)
     auto trial = [&](const std::vector<int8_t>& var, double& ms) -> int {
+        ms = nan;
         if (cudaDeviceSynchronize() != cudaSuccess || assign_tiles(H, var) != cudaSuccess)
             return HSGN_ERR_CUDA;
         // two warm-up steps capture the graphs of both state buffers
         int r = hsgn_run(H, 0.0, 2, stream);
         if (r == HSGN_OK) r = hsgn_set_state(H, kp[0], kp[1], kp[2], kp[3], stream);
-        if (r != HSGN_OK) return r;
-        if (cudaEventRecord(e0, st) != cudaSuccess) return HSGN_ERR_CUDA;
-        r = hsgn_enqueue(H, 0.0, steps, stream);
-        if (r != HSGN_OK) return r;
-        float t = 0.f;
-        if (cudaEventRecord(e1, st) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
-            cudaEventElapsedTime(&t, e0, e1) != cudaSuccess)
-            return HSGN_ERR_CUDA;
-        ms = (double)t / steps;
-        r = read_error(H, st);
-        if (r == HSGN_OK) r = hsgn_set_state(H, kp[0], kp[1], kp[2], kp[3], stream);
-        return r;
+        if (r == HSGN_OK) {
+            if (cudaEventRecord(e0, st) != cudaSuccess) return HSGN_ERR_CUDA;
+            r = hsgn_enqueue(H, 0.0, steps, stream);
+            if (r != HSGN_OK) return r;
+            float t = 0.f;
+            if (cudaEventRecord(e1, st) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+                cudaEventElapsedTime(&t, e0, e1) != cudaSuccess)
+                return HSGN_ERR_CUDA;
+            r = read_error(H, st);
+            if (r == HSGN_OK) ms = (double)t / steps;
+        }
+        if (r != HSGN_OK && r != HSGN_ERR_TRUNCATION) return r;
+        return hsgn_set_state(H, kp[0], kp[1], kp[2], kp[3], stream);
     };
     const size_t c = (size_t)H->count;
-    std::vector<int8_t> v0(c, 0), v1(c, 1), vm(c, 0);
-    double t0 = 0.0, t1 = 0.0, tm = std::nan("");
-    if (rc == HSGN_OK) rc = trial(v0, t0);
-    if (rc == HSGN_OK) rc = trial(v1, t1);
-    int32_t choice = t1 < t0 ? 1 : 0;
+    double tv[kBV + 1] = {nan, nan, nan, nan, nan};
+    std::vector<int8_t> vm(c, 0);
+    int32_t choice = -1;
+    for (int v = 0; v < kBV && rc == HSGN_OK; ++v) {
+        rc = trial(std::vector<int8_t>(c, (int8_t)v), tv[v]);
+        if (rc == HSGN_OK && !std::isnan(tv[v]) && (choice < 0 || tv[v] < tv[choice])) choice = v;
+    }
+    if (rc == HSGN_OK && choice < 0) rc = HSGN_ERR_TRUNCATION;  // no variant fits this batch
     if (rc == HSGN_OK) {
-        int64_t n0 = 0, n1 = 0;
-        for (size_t k = 0; k < c; ++k) {
-            n0 += tiles_of<FT>(H->inst_h[k].n);
-            n1 += tiles_of<FTS>(H->inst_h[k].n);
+        double cost[kBV];
+        for (int v = 0; v < kBV; ++v) {
+            int64_t tiles = 0;
+            for (size_t k = 0; k < c; ++k) tiles += batch_variant_tiles(v, H->inst_h[k].n);
+            cost[v] = tv[v] / (double)tiles;
         }
-        const double c0 = t0 / (double)n0, c1 = t1 / (double)n1;
-        bool mixed = false, any0 = false;
+        bool mixed = false;
         for (size_t k = 0; k < c; ++k) {
             const int64_t nk = H->inst_h[k].n;
-            vm[k] = (double)tiles_of<FTS>(nk) * c1 < (double)tiles_of<FT>(nk) * c0 ? 1 : 0;
-            any0 |= vm[k] == 0;
-            mixed |= vm[k] == 1;
+            int best = choice;
+            for (int v = 0; v < kBV; ++v)
+                if (!std::isnan(cost[v]) &&
+                    (double)batch_variant_tiles(v, nk) * cost[v] <
+                        (double)batch_variant_tiles(best, nk) * cost[best])
+                    best = v;
+            vm[k] = (int8_t)best;
+            mixed |= vm[k] != vm[0];
         }
-        mixed = mixed && any0;
         if (mixed) {
-            rc = trial(vm, tm);
-            if (rc == HSGN_OK && tm < (choice ? t1 : t0)) choice = 2;
+            rc = trial(vm, tv[kBV]);
+            if (rc == HSGN_OK && !std::isnan(tv[kBV]) && tv[kBV] < tv[choice]) choice = kBV;
         }
     }
     if (rc == HSGN_OK) {
         if (cudaDeviceSynchronize() != cudaSuccess ||
-            assign_tiles(H, choice == 2 ? vm : (choice == 1 ? v1 : v0)) != cudaSuccess)
+            assign_tiles(H, choice == kBV ? vm : std::vector<int8_t>(c, (int8_t)choice)) !=
+                cudaSuccess)
             rc = HSGN_ERR_CUDA;
     } else {
         cudaDeviceSynchronize();
         cudaGetLastError();
         assign_tiles(H, start);
     }
-    if (ms_out) {
-        ms_out[0] = t0;
-        ms_out[1] = t1;
-        ms_out[2] = tm;
-    }
+    if (ms_out)
+        for (int v = 0; v <= kBV; ++v) ms_out[v] = tv[v];
     if (choice_out) *choice_out = choice;
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);

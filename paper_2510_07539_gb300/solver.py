@@ -82,6 +82,7 @@ def load():
         "hsgn_batched_set_dt": [_P, _P],
         "hsgn_batched_suggest_dt": [_P, _D, _D, _P, _P],
         "hsgn_batched_set_tiles": [_P, _P],
+        "hsgn_batched_get_tiles": [_P, _P],
         "hsgn_batched_autotune": [_P, ctypes.c_int32, _P, _P, _P],
         "hsgn_tridiag_solve": [_I64, ctypes.c_int32, _P, _P, _P, _P, _P, _P, ctypes.c_size_t, _P],
     }
@@ -393,19 +394,27 @@ class BatchedSolver(Solver):
         return out
 
     def set_tiles(self, variant):
-        """Per instance 0 (large windowed kernel) or 1 (small one)."""
+        """Per instance the batch variant 0 .. 3 (hsgn_batched_set_tiles)."""
         import numpy as np
         v = np.ascontiguousarray(variant, dtype=np.int32)
         if v.shape != (self.count,):
             raise ValueError(f"expected {self.count} variants")
         _check(_lib.hsgn_batched_set_tiles(self._h, v.ctypes.data), "hsgn_batched_set_tiles")
 
+    def get_tiles(self):
+        """Per instance the batch variant in use (hsgn_batched_get_tiles)."""
+        import numpy as np
+        v = np.empty(self.count, dtype=np.int32)
+        _check(_lib.hsgn_batched_get_tiles(self._h, v.ctypes.data), "hsgn_batched_get_tiles")
+        return v
+
     def autotune(self, steps: int = 4, stream=None):
         """Pick the tiles of the batch by timing (the state is kept); returns
-        the ms per step of all-large, all-small and the cost-model assignment
-        (NaN if not timed) and the choice kept (0, 1, 2)."""
+        the ms per step with every instance on variant 0, 1, 2, 3 and of the
+        cost-model assignment (NaN if not timed or ruled out) and the choice
+        kept (0 .. 3 for one variant everywhere, 4 for the assignment)."""
         import numpy as np
-        ms = np.empty(3)
+        ms = np.empty(5)
         ch = ctypes.c_int32(-1)
         _check(_lib.hsgn_batched_autotune(self._h, int(steps), ms.ctypes.data, ctypes.byref(ch),
                                           _stream(stream)), "hsgn_batched_autotune")

@@ -96,6 +96,7 @@ def test_null_handle_calls_are_rejected(lib):
     assert lib.hsgn_suggest_dt(None, 2.0, 0.5, ctypes.byref(dt), None) == 1
     v = (ctypes.c_int32 * 2)()
     assert lib.hsgn_batched_set_tiles(None, ctypes.cast(v, ctypes.c_void_p)) == 1
+    assert lib.hsgn_batched_get_tiles(None, ctypes.cast(v, ctypes.c_void_p)) == 1
     ms = (ctypes.c_double * 3)()
     ch = ctypes.c_int32()
     assert lib.hsgn_batched_autotune(None, 2, ctypes.cast(ms, ctypes.c_void_p), ctypes.byref(ch),

@@ -509,18 +509,23 @@ def packed_state(insts):
     return [np.concatenate([it.state[k] for it in insts]) for k in range(4)]
 
 
-@pytest.mark.parametrize("assign", ["small", "alternate"])
+@pytest.mark.parametrize("assign", ["small", "alternate", "narrow", "all_four"])
 def test_batched_tile_variants_match_oracle(assign):
-    # every instance on the small kernel, or the two kernels alternating (two
-    # launches per stage over disjoint tile tables); instances of 64 .. 5000
-    # cells span 1 .. 14 small tiles
+    # every instance on the small kernel, the two wide-overlap kernels
+    # alternating (two launches per stage over disjoint tile tables), every
+    # instance on the narrow-overlap large kernel, or all four variants in
+    # turn (four launches per stage); instances of 64 .. 5000 cells span
+    # 1 .. 14 small tiles. The 32-row overlap meets the truncation bound at
+    # CFL_IMEX 2 (rho* about 0.4), not at 4 (rho* about 0.55).
     insts, ns, xl, xr, lams = batch_case(14, 9, n_min=64, n_max=5000)
-    var = [1] * len(ns) if assign == "small" else [k % 2 for k in range(len(ns))]
+    var = {"small": [1] * len(ns), "alternate": [k % 2 for k in range(len(ns))],
+           "narrow": [2] * len(ns), "all_four": [k % 4 for k in range(len(ns))]}[assign]
     with S().BatchedSolver(ns, xl, xr, lams) as B:
         B.set_state(*(dev(a) for a in packed_state(insts)))
-        dts = B.suggest_dt(4.0, 0.5)
+        dts = B.suggest_dt(4.0 if assign in ("small", "alternate") else 2.0, 0.5)
         B.set_dt(dts)
         B.set_tiles(var)
+        np.testing.assert_array_equal(B.get_tiles(), var)
         B.run(0.0, 30)
         got = [t.cpu().numpy() for t in B.get_state()]
         # a graph replay and a step loop of the same assignment agree bitwise
@@ -537,6 +542,26 @@ def test_batched_tile_variants_match_oracle(assign):
         assert rel_l2(got[0][o0:o1], ref[0]) < 5e-6, (k_inst, rel_l2(got[0][o0:o1], ref[0]))
         assert rel_l2(got[2][o0:o1], ref[2]) < 5e-6
         assert abs(math.fsum(got[0][o0:o1]) - math.fsum(it.state[0])) <= 1e-13 * math.fsum(it.state[0])
+
+
+@pytest.mark.parametrize("v", [2, 3])
+def test_batched_narrow_overlap_reports_truncation_at_large_cfl(v):
+    # at CFL_IMEX 4 the depth coupling decays by about 0.55 per row: 31 rows
+    # do not reach 2^-30, so the narrow variants report the truncation error
+    # and the wide ones run the same steps
+    insts, ns, xl, xr, lams = batch_case(18, 5, n_min=1024, n_max=5000)
+    with S().BatchedSolver(ns, xl, xr, lams) as B:
+        B.set_state(*(dev(a) for a in packed_state(insts)))
+        dts = B.suggest_dt(4.0, 0.5)
+        B.set_dt(dts)
+        B.set_tiles([v] * len(ns))
+        with pytest.raises(S().HsgnError) as e:
+            B.run(0.0, 2)
+        assert e.value.code == 8
+        B.set_state(*(dev(a) for a in packed_state(insts)))
+        B.set_tiles([v - 2] * len(ns))
+        B.run(0.0, 2)
+        B.check()
 
 
 def test_batched_small_and_large_variant_agree_on_short_instances():
@@ -566,11 +591,20 @@ def test_batched_autotune_keeps_the_state_and_a_valid_assignment():
         dts = B.suggest_dt(2.0, 0.5)
         B.set_dt(dts)
         r = B.autotune(3)
-        assert r["choice"] in (0, 1, 2)
+        assert r["choice"] in (0, 1, 2, 3, 4)
         t = r["ms_per_step"]
-        assert t[0] > 0 and t[1] > 0 and (math.isnan(t[2]) or t[2] > 0)
+        assert len(t) == 5
+        # the wide-overlap variants always fit; the narrow ones may be ruled
+        # out by the truncation bound (NaN); the assignment is timed only when
+        # it mixes variants
+        assert t[0] > 0 and t[1] > 0
+        assert all(math.isnan(x) or x > 0 for x in t[2:])
         kept = t[r["choice"]]
         assert kept == min(x for x in t if not math.isnan(x))
+        v = B.get_tiles()
+        assert v.shape == (40,) and v.min() >= 0 and v.max() <= 3
+        if r["choice"] < 4:
+            assert (v == r["choice"]).all()
         after = [t_.cpu().numpy() for t_ in B.get_state()]
         for k in range(4):
             np.testing.assert_array_equal(before[k], after[k])
@@ -587,7 +621,7 @@ def test_batched_set_tiles_rejects_bad_input():
     insts, ns, xl, xr, lams = batch_case(17, 3)
     with S().BatchedSolver(ns, xl, xr, lams) as B:
         with pytest.raises(S().HsgnError) as e:
-            B.set_tiles([0, 2, 1])
+            B.set_tiles([0, 4, 1])
         assert e.value.code == 1
         with pytest.raises(ValueError):
             B.set_tiles([0, 1])

@@ -18,7 +18,7 @@
 #include "../paper_2510_07539_gb300/csrc/hsgn_dfstage.cuh"
 
 using namespace hsgn;
-constexpr int M = 4, HW = 64;
+constexpr int M = 4;
 
 #define CHECK(c)                                                                               \
     do {                                                                                       \
@@ -31,7 +31,7 @@ constexpr int M = 4, HW = 64;
 
 static long long checked_windows = 0;
 
-template <int T, int BC>
+template <int T, int BC, int HW = 64>
 void check(int64_t n, int S) {
     using G = FusedGeom<T, M, HW>;
     int64_t p = -1;
@@ -170,11 +170,14 @@ void check_df(int64_t n, int S) {
 
 template <int BC>
 void check_grid(int64_t n) {
-    using G = FusedGeom<256, M, HW>;
-    using Gs = FusedGeom<128, M, HW>;
+    using G = FusedGeom<256, M, 64>;
+    using Gs = FusedGeom<128, M, 64>;
     for (int64_t slots : {1, 2, 152, 304, 456, 608})
         check<256, BC>(n, (int)fused_tile_rows(n, G::S, slots));
     check<128, BC>(n, (int)fused_tile_rows(n, Gs::S, 1));
+    // the narrow-overlap batch variants (32 rows)
+    check<256, BC, 32>(n, (int)fused_tile_rows(n, FusedGeom<256, M, 32>::S, 1));
+    check<128, BC, 32>(n, (int)fused_tile_rows(n, FusedGeom<128, M, 32>::S, 1));
     using D = DfGeom<DT, M, DHW>;
     for (int64_t slots : {1, 2, 152, 304})
         check_df<BC>(n, (int)fused_tile_rows(n, D::S, slots));
@@ -192,8 +195,8 @@ int main() {
         check_grid<BC_TRANSMISSIVE>(n);
     }
     // windows ending 3 or 4 cells before the domain end (the edge of the direct path)
-    using G = FusedGeom<256, M, HW>;
-    using Gs = FusedGeom<128, M, HW>;
+    using G = FusedGeom<256, M, 64>;
+    using Gs = FusedGeom<128, M, 64>;
     for (int64_t k = 1; k <= 40; ++k)
         for (int64_t e = 60; e <= 72; ++e) {
             check<256, BC_PERIODIC>(k * G::S + e, G::S);
