@@ -686,8 +686,18 @@ def hbm_view(n, avg_ms, hbm_peak, bytes_per_cell=BYTES_PER_CELL_STAGE):
             "algorithmic_bytes_per_cell_stage": bytes_per_cell}
 
 
+# the library's profile slots per form: the stage kernel, the separator levels
+# of the FP64 form's global solve and its back-substitution kernel
+SHARE_NAMES = {
+    "df": {"assemble": "k_df_stage"},
+    "mixed": {"assemble": "k_mixed_fused"},
+    "fp64": {"assemble": "k_stage_assemble", "reduced": "separator levels (k_block_reduce, "
+             "k_cyclic_onewarp, k_block_backout)", "backsub": "k_backsub"},
+}
+
+
 def time_form(S, torch, flags, n, xl, xr, lams, Ud, args, flush, stream, dist, clocks,
-              concurrent):
+              concurrent, names=None):
     """A form timed twice on the workload: the instances of a step on one stream
     each (the throughput), then back to back on one stream, where the event
     pair of every launch times that launch alone (the kernel's duration)."""
@@ -702,7 +712,8 @@ def time_form(S, torch, flags, n, xl, xr, lams, Ud, args, flush, stream, dist, c
         qms, qtot = ms, tot
     avg = qtot["assemble"][0] / max(qtot["assemble"][1], 1)
     share_den = sum(v[0] for v in qtot.values())
-    share = {k: v[0] / share_den for k, v in qtot.items() if v[1] > 0} if share_den > 0 else {}
+    share = {(names or {}).get(k, k): v[0] / share_den for k, v in qtot.items()
+             if v[1] > 0} if share_den > 0 else {}
     return sols, dts, ms, qms, avg, share, clk
 
 
@@ -755,7 +766,7 @@ def run_ours(args):
     #      the instances of a step on one stream each (whole-job throughput)
     dsols, ddts, dms, dqms, davg, dshare, clocks = time_form(
         S, torch, S.FLAG_DOUBLE_FLOAT, n, xl, xr, lams, Ud, args, flush, stream, dist, gpu_id,
-        not args.sequential)
+        not args.sequential, SHARE_NAMES["df"])
     value = units_rank * world / (dms / 1e3)
     counted = DF_FLOPS_SOURCE_SHA is not None and source_sha(DF_SOURCES) == DF_FLOPS_SOURCE_SHA
     dflops = DF_FLOPS_PER_CELL if counted else None
@@ -783,7 +794,8 @@ def run_ours(args):
     fp64, fsols, fdts = None, [], []
     if not args.no_fp64:
         fsols, fdts, fms, fqms, favg, fshare, _ = time_form(
-            S, torch, S.FLAG_FP64, n, xl, xr, lams, Ud, args, flush, stream, dist, None, False)
+            S, torch, S.FLAG_FP64, n, xl, xr, lams, Ud, args, flush, stream, dist, None, False,
+            SHARE_NAMES["fp64"])
         fp64 = {"value": units_rank * world / (fms / 1e3), "unit": UNIT,
                 "ms_per_step": fms / args.steps, "dtype": "f64",
                 "roofline": kernel_roofline_alu(
@@ -798,7 +810,7 @@ def run_ours(args):
     if not args.no_mixed:
         msols, mdts, mms, mqms, mavg, mshare, _ = time_form(
             S, torch, S.FLAG_MIXED, n, xl, xr, lams, Ud, args, flush, stream, dist, None,
-            not args.sequential)
+            not args.sequential, SHARE_NAMES["mixed"])
         mgbs = BYTES_PER_CELL_STAGE * n / (mavg / 1e3) / 1e9
         mixed = {"value": units_rank * world / (mms / 1e3), "unit": UNIT,
                  "ms_per_step": mms / args.steps, "dtype": "f32 increments + double-float state",
