@@ -127,6 +127,22 @@ HSGN_HD dfl operator+(dfl a, dfl b) {
 }
 HSGN_HD dfl operator-(dfl a, dfl b) { return a + (-b); }
 
+// a + b left unrenormalised: the exact sum of the high parts (TwoSum) with the
+// low parts added to its error term, three operations fewer than the sum
+// above. The value carries the same error (about 2^-48 of |a| + |b|); the low
+// part may reach a few ulps of the high part, or exceed it where the high
+// parts cancel, and every operation here takes such a pair as an input
+// (products, quotients, reciprocals and roots form the leading term from the
+// high part and fold the low part into a correction; sums take both parts
+// exactly). Values that are stored as a state, tested for sign or compared
+// are formed with the renormalised operations.
+HSGN_HD dfl add_u(dfl a, dfl b) {
+    float s, e;
+    two_sum_f(a.hi, b.hi, s, e);
+    return dfl_make(s, f_add(e, f_add(a.lo, b.lo)));
+}
+HSGN_HD dfl sub_u(dfl a, dfl b) { return add_u(a, -b); }
+
 // a + b with an error of about 2^-47 of |a + b| rather than of |a| + |b|:
 // TwoSum of both the high and the low parts (for differences of close values,
 // whose cancellation the plain sum would leave at the operands' rounding).
@@ -179,6 +195,17 @@ HSGN_HD dfl fma(dfl a, dfl b, dfl c) {
     float s, t;
     two_sum_f(p, c.hi, s, t);
     return renorm(s, f_add(t, f_add(e, c.lo)));
+}
+
+// a * b + c without the final renormalisation (as add_u).
+HSGN_HD dfl fma_u(dfl a, dfl b, dfl c) {
+    const float p = f_mul(a.hi, b.hi);
+    float e = f_fma(a.hi, b.hi, -p);
+    e = f_fma(a.hi, b.lo, e);
+    e = f_fma(a.lo, b.hi, e);
+    float s, t;
+    two_sum_f(p, c.hi, s, t);
+    return dfl_make(s, f_add(t, f_add(e, c.lo)));
 }
 
 // 1/a: r = 1/a.hi to one ulp, then r + r (1 - a r) with the residual formed

@@ -56,6 +56,8 @@ __device__ __forceinline__ float add_f(float a, float x) { return a + x; }
 __device__ __forceinline__ float dabs(float a) { return fabsf(a); }
 __device__ __forceinline__ float dmax(float a, float b) { return fmaxf(a, b); }
 __device__ __forceinline__ float fma(float a, float b, float c) { return fmaf(a, b, c); }
+__device__ __forceinline__ float add_u(float a, float b) { return a + b; }
+__device__ __forceinline__ float sub_u(float a, float b) { return a - b; }
 __device__ __forceinline__ dfl to_dfl(dfl x) { return x; }
 __device__ __forceinline__ dfl to_dfl(float x) { return dfl(x); }
 __device__ __forceinline__ dfl as_R(dfl x, dfl) { return x; }
@@ -268,8 +270,8 @@ __global__ void __launch_bounds__(T, 2) k_df_stage(const DfParams p) {
                     if constexpr (two) {
                         const float2 d = __ldg(p.D1[v] + gi);
                         const dfl dv(d.x, d.y);
-                        L[v]->set(j, fma(p.wl1, dv, u));
-                        B[v]->set(j, fma(p.wb1, dv, u));
+                        L[v]->set(j, fma_u(p.wl1, dv, u));
+                        B[v]->set(j, fma_u(p.wb1, dv, u));
                     } else {
                         L[v]->set(j, u);
                         B[v]->set(j, u);
@@ -299,7 +301,7 @@ __global__ void __launch_bounds__(T, 2) k_df_stage(const DfParams p) {
         // the quarter centred difference of cell c = 1 .. 5 of the 8 loaded
         auto quarter = [](const R* X, R* D) {
 #pragma unroll
-            for (int c = 1; c <= 5; ++c) D[c - 1] = scale(X[c + 1] - X[c - 1], 0.25f);
+            for (int c = 1; c <= 5; ++c) D[c - 1] = scale(sub_u(X[c + 1], X[c - 1]), 0.25f);
         };
         R wL[4], wR[4];  // u^L + s, u^R - s
         {
@@ -310,21 +312,25 @@ __global__ void __launch_bounds__(T, 2) k_df_stage(const DfParams p) {
             ld4(sm.ql, j0 + 4, Q + 4);
             quarter(H, DH);
             quarter(Q, DQ);
+            R Fq[4];
 #pragma unroll
             for (int e = 0; e < 4; ++e) {
-                const R hL = H[e + 1] + DH[e], hR = H[e + 2] - DH[e + 1];
-                const R qL = Q[e + 1] + DQ[e], qR = Q[e + 2] - DQ[e + 1];
+                const R hL = add_u(H[e + 1], DH[e]), hR = sub_u(H[e + 2], DH[e + 1]);
+                const R qL = add_u(Q[e + 1], DQ[e]), qR = sub_u(Q[e + 2], DQ[e + 1]);
                 if (j0 + e < W + 3 && !(pos_finite(hL) && pos_finite(hR))) bad |= HSGN_DEV_ERR_DEPTH;
                 const R uL = qL / hL, uR = qR / hR;
                 const R s = p.local_speed ? dmax(dabs(uL), dabs(uR)) : spd;
-                wL[e] = uL + s;
-                wR[e] = uR - s;
+                wL[e] = add_u(uL, s);
+                wR[e] = sub_u(uR, s);
+                // the momentum flux from the same reconstruction of q
+                Fq[e] = fma_u(wL[e], qL, wR[e] * qR);
             }
+            st4(sm.fq, j0, Fq);
         }
-        DArr<Gm::NC>* const X[3] = {&sm.ql, &sm.ml, &sm.rl};
-        DArr<Gm::NC>* const F[3] = {&sm.fq, &sm.fm, &sm.fr};
+        DArr<Gm::NC>* const X[2] = {&sm.ml, &sm.rl};
+        DArr<Gm::NC>* const F[2] = {&sm.fm, &sm.fr};
 #pragma unroll
-        for (int v = 0; v < 3; ++v) {
+        for (int v = 0; v < 2; ++v) {
             R Xv[8], Dv[5];
             ld4(*X[v], j0, Xv);
             ld4(*X[v], j0 + 4, Xv + 4);
@@ -332,9 +338,9 @@ __global__ void __launch_bounds__(T, 2) k_df_stage(const DfParams p) {
             R Fv[4];
 #pragma unroll
             for (int e = 0; e < 4; ++e) {
-                const R xL = Xv[e + 1] + Dv[e];
-                const R xR = Xv[e + 2] - Dv[e + 1];
-                Fv[e] = fma(wL[e], xL, wR[e] * xR);
+                const R xL = add_u(Xv[e + 1], Dv[e]);
+                const R xR = sub_u(Xv[e + 2], Dv[e + 1]);
+                Fv[e] = fma_u(wL[e], xL, wR[e] * xR);
             }
             st4(*F[v], j0, Fv);
         }
@@ -348,8 +354,8 @@ __global__ void __launch_bounds__(T, 2) k_df_stage(const DfParams p) {
                 ld1(A, f + 1, x1);
                 ld1(A, f + 2, x2);
                 ld1(A, f + 3, x3);
-                xl = x1 + scale(x2 - x0, 0.25f);
-                xr = x2 - scale(x3 - x1, 0.25f);
+                xl = add_u(x1, scale(sub_u(x2, x0), 0.25f));
+                xr = sub_u(x2, scale(sub_u(x3, x1), 0.25f));
             };
             R hL, hR, qL, qR, mL, mR, rL, rR;
             face(sm.hl, hL, hR);
@@ -359,10 +365,10 @@ __global__ void __launch_bounds__(T, 2) k_df_stage(const DfParams p) {
             if (!(pos_finite(hL) && pos_finite(hR))) bad |= HSGN_DEV_ERR_DEPTH;
             const R uL = qL / hL, uR = qR / hR;
             const R s = p.local_speed ? dmax(dabs(uL), dabs(uR)) : spd;
-            const R wl = uL + s, wr = uR - s;
-            st1(sm.fq, f, fma(wl, qL, wr * qR));
-            st1(sm.fm, f, fma(wl, mL, wr * mR));
-            st1(sm.fr, f, fma(wl, rL, wr * rR));
+            const R wl = add_u(uL, s), wr = sub_u(uR, s);
+            st1(sm.fq, f, fma_u(wl, qL, wr * qR));
+            st1(sm.fm, f, fma_u(wl, mL, wr * mR));
+            st1(sm.fr, f, fma_u(wl, rL, wr * rR));
         }
     }
     __syncthreads();
@@ -405,19 +411,19 @@ __global__ void __launch_bounds__(T, 2) k_df_stage(const DfParams p) {
             dq_[k] = dm_[k] = dr_[k] = be_[k] = de_[k] = dfl(0.f);
             if (j0 + k < W + 2) {
                 const R dr = -(c_fq * sub_acc(FR[k + 1], FR[k]));
-                const R dm = fma(c_tau, RB[k + 2] + dr, -(c_fq * sub_acc(FM[k + 1], FM[k])));
+                const R dm = fma_u(c_tau, add_u(RB[k + 2], dr), -(c_fq * sub_acc(FM[k + 1], FM[k])));
                 const R dq = -(c_fq * sub_acc(FQ[k + 1], FQ[k]));
-                const R ms = (MB[k + 2] + dm) + c_lt2;
+                const R ms = add_u(add_u(MB[k + 2], dm), c_lt2);
                 const R h = HL[k + 2];
                 if (!pos_finite(h)) bad |= HSGN_DEV_ERR_DEPTH;
                 const R ih = rcp(h);
                 const R eta = ML[k + 2] * ih;
                 const R e = eta * ih;
                 const R alpha = -(add_f(scale(e, 2.f), -1.f) * ih * c_third);
-                const R c2 = fma(c_g, h, c_lam3 * (e * e));
-                const R a2 = c2 - c_lam * (eta * alpha);
+                const R c2 = fma_u(c_g, h, c_lam3 * (e * e));
+                const R a2 = sub_u(c2, c_lam * (eta * alpha));
                 const R h2 = h * h;
-                const R iD = rcp(h2 + c_lt2);       // 1/(beta_1 h^2)
+                const R iD = rcp(add_u(h2, c_lt2));  // 1/(beta_1 h^2)
                 const R ib1 = h2 * iD;              // 1/beta_1
                 const R beta2 = scale(c_lt2, 2.f) * (h * (iD * iD));
                 const R beta = fma(c_lam * alpha, beta2 * ms, a2);
@@ -495,15 +501,15 @@ __global__ void __launch_bounds__(T, 2) k_df_stage(const DfParams p) {
 #pragma unroll
             for (int e = 0; e < 5; ++e) {
                 const int f = j0 + e;  // rows f - 1 | f: per-cell index f, f + 1; state f + 2, f + 3
-                const dfl bf = scale(B8[e] + B8[e + 1], 0.5f);
-                const dfl df = scale(E8[e] + E8[e + 1], 0.5f);
+                const dfl bf = scale(add_u(B8[e], B8[e + 1]), 0.5f);
+                const dfl df = scale(add_u(E8[e], E8[e + 1]), 0.5f);
                 dfl kf = kc.Cc * bf;
                 if (BC == BC_TRANSMISSIVE && ((f == 0 && win.lend) || (f == W && win.rend)))
                     kf = dfl(0.f);
-                const dfl dmf = sub_acc(MU[e + 3], MU[e + 2]) + sub_acc(M8[e + 1], M8[e]);
+                const dfl dmf = add_u(sub_acc(MU[e + 3], MU[e + 2]), sub_acc(M8[e + 1], M8[e]));
                 const dfl dhf = sub_acc(H8[e + 3], H8[e + 2]);
                 KF[e] = kf;
-                Phi[e] = fma(kc.fd * df, dmf, kf * dhf);
+                Phi[e] = fma_u(kc.fd * df, dmf, kf * dhf);
             }
         }
         dfl Q8[8], QU[8];
@@ -514,8 +520,8 @@ __global__ void __launch_bounds__(T, 2) k_df_stage(const DfParams p) {
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
             // q^dag of cells i+1 and i-1: state index i + 4, i + 2; per-cell index i + 2, i
-            const dfl dqc = sub_acc(QU[k + 4], QU[k + 2]) + sub_acc(Q8[k + 2], Q8[k]);
-            rd[k] = sub_acc(Phi[k + 1], Phi[k]) - kc.fq * dqc;
+            const dfl dqc = add_u(sub_acc(QU[k + 4], QU[k + 2]), sub_acc(Q8[k + 2], Q8[k]));
+            rd[k] = sub_u(sub_acc(Phi[k + 1], Phi[k]), kc.fq * dqc);
         }
     }
     {
@@ -529,7 +535,7 @@ __global__ void __launch_bounds__(T, 2) k_df_stage(const DfParams p) {
             const dfl kl = KF[k], kr = KF[k + 1];
             a = (i == 0 && !win.lend) ? dfl(0.f) : -kl;
             c = (i == W - 1 && !win.rend) ? dfl(0.f) : -kr;
-            bb = add_f(kl + kr, 1.f);
+            bb = add_f(add_u(kl, kr), 1.f);
             d = rd[k];
         };
         dfl y[M];
@@ -572,20 +578,21 @@ __global__ void __launch_bounds__(T, 2) k_df_stage(const DfParams p) {
         const int r = lo + t;  // window row; state index r + 3, per-cell index r + 1, dh index r + 4
         const dfl dh = DH.get(r + 4);
         const dfl hb = sm.hb.get(r + 3), mb = sm.mb.get(r + 3);
-        const dfl dhc = sub_acc(sm.hb.get(r + 4), sm.hb.get(r + 2)) +
-                        sub_acc(DH.get(r + 5), DH.get(r + 3));
+        const dfl dhc = add_u(sub_acc(sm.hb.get(r + 4), sm.hb.get(r + 2)),
+                              sub_acc(DH.get(r + 5), DH.get(r + 3)));
         const dfl dmv = DM.get(r + 1);
-        const dfl dmc = sub_acc(sm.mb.get(r + 4), sm.mb.get(r + 2)) +
-                        sub_acc(DM.get(r + 2), DM.get(r));
-        const dfl dQ = DQ.get(r + 1) - (kc.fq * (BE.get(r + 1) * dhc) + kc.lfq * (DE.get(r + 1) * dmc));
-        const dfl P = sq_minus(hb, mb) + dh * (scale(hb, 2.f) + dh);
-        const dfl E = P - dmv;
+        const dfl dmc = add_u(sub_acc(sm.mb.get(r + 4), sm.mb.get(r + 2)),
+                              sub_acc(DM.get(r + 2), DM.get(r)));
+        const dfl dQ = sub_u(DQ.get(r + 1),
+                             add_u(kc.fq * (BE.get(r + 1) * dhc), kc.lfq * (DE.get(r + 1) * dmc)));
+        const dfl P = add_u(sq_minus(hb, mb), dh * add_u(scale(hb, 2.f), dh));
+        const dfl E = sub_u(P, dmv);
         const dfl hbar = hb + dh;
         const dfl h2 = hbar * hbar;
-        const dfl iDen = rcp(h2 + kc.lt2);
+        const dfl iDen = rcp(add_u(h2, kc.lt2));
         const dfl Ei = E * iDen;
-        const dfl dR = fma(kc.ltau, Ei, DR.get(r + 1));
-        const dfl dM = P - Ei * h2;
+        const dfl dR = fma_u(kc.ltau, Ei, DR.get(r + 1));
+        const dfl dM = sub_u(P, Ei * h2);
         unsigned b2 = 0;
         if (!pos_finite(hbar)) b2 |= HSGN_DEV_ERR_DEPTH;
         if (!isfinite(dQ.hi) || !isfinite(dM.hi) || !isfinite(dR.hi)) b2 |= HSGN_DEV_ERR_NONFINITE;

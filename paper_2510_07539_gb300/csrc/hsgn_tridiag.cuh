@@ -77,6 +77,11 @@ __device__ __forceinline__ float rcp(float x) {
     return fmaf(r, fmaf(-x, r, 1.f), r);
 }
 
+// a * b + c in one rounding; the double-float pairs have an overload of the
+// same name that skips the final renormalisation.
+__device__ __forceinline__ float fma_u(float a, float b, float c) { return fmaf(a, b, c); }
+__device__ __forceinline__ double fma_u(double a, double b, double c) { return ::fma(a, b, c); }
+
 // Leading single-precision value of a number (magnitude tests).
 __device__ __forceinline__ float hi_of(float x) { return x; }
 __device__ __forceinline__ float hi_of(double x) { return (float)x; }
@@ -511,9 +516,9 @@ __device__ __forceinline__ void cta_window_solve(int nrows, RowK row, SepShared<
                 y[k] = d * ip;
                 v[k] = a * ip;
             } else {
-                p = fma(-a, w[k - 1], b);
+                p = fma_u(-a, w[k - 1], b);
                 ip = rcp(p);
-                y[k] = fma(-a, y[k - 1], d) * ip;
+                y[k] = fma_u(-a, y[k - 1], d) * ip;
                 v[k] = -a * v[k - 1] * ip;
             }
             bad |= !pos_finite(p);
@@ -529,8 +534,8 @@ __device__ __forceinline__ void cta_window_solve(int nrows, RowK row, SepShared<
 #pragma unroll
         for (int k = M - 1; k >= 0; --k) {
             if (k < nint) {
-                const Real Y = fma(-w[k], Yn, y[k]);
-                const Real V = fma(-w[k], Vn, v[k]);
+                const Real Y = fma_u(-w[k], Yn, y[k]);
+                const Real V = fma_u(-w[k], Vn, v[k]);
                 const Real W = -w[k] * Wn;
                 if (k == nint - 1) {
                     YL = Y;
@@ -587,14 +592,14 @@ __device__ __forceinline__ void cta_window_solve(int nrows, RowK row, SepShared<
             if (t - s >= 0) {
                 const Real k1 = A * rcp(sh.B[pd(t - s)]);
                 nA = -k1 * sh.A[pd(t - s)];
-                nB = fma(-k1, sh.C[pd(t - s)], nB);
-                nD = fma(-k1, sh.D1[pd(t - s)], nD);
+                nB = fma_u(-k1, sh.C[pd(t - s)], nB);
+                nD = fma_u(-k1, sh.D1[pd(t - s)], nD);
             }
             if (t + s < ns) {
                 const Real k2 = C * rcp(sh.B[pd(t + s)]);
                 nC = -k2 * sh.C[pd(t + s)];
-                nB = fma(-k2, sh.A[pd(t + s)], nB);
-                nD = fma(-k2, sh.D1[pd(t + s)], nD);
+                nB = fma_u(-k2, sh.A[pd(t + s)], nB);
+                nD = fma_u(-k2, sh.D1[pd(t + s)], nD);
             }
             A = nA;
             B = nB;
