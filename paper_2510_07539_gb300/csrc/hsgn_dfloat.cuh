@@ -146,20 +146,22 @@ HSGN_HD dfl sub_u(dfl a, dfl b) { return add_u(a, -b); }
 // a + b with an error of about 2^-47 of |a + b| rather than of |a| + |b|:
 // TwoSum of both the high and the low parts (for differences of close values,
 // whose cancellation the plain sum would leave at the operands' rounding).
+// The last low-part term is added without a final renormalisation (as add_u:
+// the value is the same, the pair may carry a low part of a few ulps).
 HSGN_HD dfl add_acc(dfl a, dfl b) {
     float s1, s2, t1, t2;
     two_sum_f(a.hi, b.hi, s1, s2);
     two_sum_f(a.lo, b.lo, t1, t2);
     const dfl u = renorm(s1, f_add(s2, t1));
-    return renorm(u.hi, f_add(u.lo, t2));
+    return dfl_make(u.hi, f_add(u.lo, t2));
 }
 HSGN_HD dfl sub_acc(dfl a, dfl b) { return add_acc(a, -b); }
 
-// a + x for a single float x.
+// a + x for a single float x, unrenormalised (as add_u).
 HSGN_HD dfl add_f(dfl a, float x) {
     float s, e;
     two_sum_f(a.hi, x, s, e);
-    return renorm(s, f_add(e, a.lo));
+    return dfl_make(s, f_add(e, a.lo));
 }
 
 // Products, reciprocals and quotients return the pair unrenormalised: the low

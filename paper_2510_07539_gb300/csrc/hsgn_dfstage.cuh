@@ -587,7 +587,8 @@ __global__ void __launch_bounds__(T, 2) k_df_stage(const DfParams p) {
                              add_u(kc.fq * (BE.get(r + 1) * dhc), kc.lfq * (DE.get(r + 1) * dmc)));
         const dfl P = add_u(sq_minus(hb, mb), dh * add_u(scale(hb, 2.f), dh));
         const dfl E = sub_u(P, dmv);
-        const dfl hbar = hb + dh;
+        // (renormalised where it is written as the new state)
+        const dfl hbar = two ? hb + dh : add_u(hb, dh);
         const dfl h2 = hbar * hbar;
         const dfl iDen = rcp(add_u(h2, kc.lt2));
         const dfl Ei = E * iDen;
