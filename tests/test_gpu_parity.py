@@ -208,6 +208,47 @@ def test_large_instance_2_24_one_step(form):
     assert rel_l2(got[0], ref[0]) < 1e-12 and rel_l2(got[2], ref[2]) < 1e-12
 
 
+def test_headline_configuration_on_concurrent_streams():
+    # the benchmark's headline run as it is timed: the dam break at 2^24 cells
+    # for lambda = 10, 100, 1000 in the double-float form, each instance on its
+    # own CUDA stream with its steps enqueued as replays of its step graph and
+    # the three streams running at once; two steps compared everywhere
+    n, dx, steps = 1 << 24, 0.05, 2
+    x, U = inputs.dam_break(n, dx, 1.2, 1.0, 5.0 / dx)
+    lams = (10.0, 100.0, 1000.0)
+    Ud = [dev(u) for u in U]
+    sols, dts, streams = [], [], []
+    try:
+        for lam in lams:
+            s = S().Solver(n, -0.5 * n * dx, 0.5 * n * dx, 1, lam=lam,
+                           flags=S().FLAG_DOUBLE_FLOAT)
+            sols.append(s)
+            s.set_state(*Ud)
+            dts.append(s.suggest_dt(4.0, 0.5))
+            streams.append(torch.cuda.Stream())
+        torch.cuda.synchronize()
+        for _ in range(steps):
+            for s, st, dt in zip(sols, streams, dts):
+                s.enqueue(dt, 1, stream=st)
+        torch.cuda.synchronize()
+        got = []
+        for s in sols:
+            s.check()
+            got.append([t.cpu().numpy() for t in s.get_state()])
+    finally:
+        for s in sols:
+            s.close()
+    del Ud
+    for lam, dt, g in zip(lams, dts, got):
+        p = oracle.Params(n, dx, 1, lam=lam)
+        ref = oracle.run(p, U, dt, steps)
+        sc = summand_scales(n, dx, 1, lam, U, dt)
+        for k in range(4):
+            e = scaled_err(g[k], ref[k], sc[k])
+            assert e < 1e-12, (lam, k, e)
+        assert rel_l2(g[0], ref[0]) < 1e-12 and rel_l2(g[2], ref[2]) < 1e-12
+
+
 @pytest.mark.parametrize("form", FP64_FORMS)
 def test_mass_conservation_on_gpu(form):
     n, dx = 4099, 0.1
