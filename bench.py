@@ -768,6 +768,8 @@ def run_ours(args):
         S, torch, S.FLAG_DOUBLE_FLOAT, n, xl, xr, lams, Ud, args, flush, stream, dist, gpu_id,
         not args.sequential, SHARE_NAMES["df"])
     value = units_rank * world / (dms / 1e3)
+    # the window overlap each instance stepped with (it follows the coupling)
+    dover = [s.df_overlap() for s in dsols]
     counted = DF_FLOPS_SOURCE_SHA is not None and source_sha(DF_SOURCES) == DF_FLOPS_SOURCE_SHA
     dflops = DF_FLOPS_PER_CELL if counted else None
     roofline = kernel_roofline_alu(
@@ -1015,8 +1017,13 @@ def run_ours(args):
                 "precision": "double-float: every value a pair of FP32 numbers (48-bit "
                              "significand, about 2^-47 per operation); parity bar of the FP64 "
                              "form (1e-12 relative per step against the FP64 oracle)",
-                "depth_solve": "windows of the tile +- 96 rows, truncation bounded in-kernel "
-                               "by rho*^95 <= 2^-50"}),
+                "depth_solve": "windows of the tile +- an overlap that follows the coupling "
+                               "(the rows the last synchronised step needed + 5, rounded up to "
+                               "a multiple of 8 within 48..96), truncation bounded in-kernel by "
+                               "rho*^(overlap - 1) <= 2^-50; a tile whose window misses it is "
+                               "redone with 96 rows",
+                "overlap_rows": [o for _, o in dover],
+                "rows_needed": [r for r, _ in dover]}),
             "l2_rel_err_vs_oracle": l2err,
             "roofline": roofline, "peaks": {"hbm_gbs": hbm_peak, "hbm_source": hbm_src,
                                             "fp32_tflops": fp32_peak, "fp64_tflops": fp64_peak,

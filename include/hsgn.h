@@ -89,9 +89,10 @@ enum {
                                 * stays within 1e-12 of the FP64 scheme while no
                                 * double-precision instruction runs. One launch
                                 * per stage on overlapping windows as described
-                                * under HSGN_MIXED, here 96 rows wide, with the
-                                * truncation bound checked against 2^-50
-                                * (HSGN_ERR_TRUNCATION above about CFL_IMEX 7 for
+                                * under HSGN_MIXED, with the truncation bound
+                                * checked against 2^-50 and an overlap of 48 to 96
+                                * rows that follows the coupling (hsgn_df_overlap;
+                                * HSGN_ERR_TRUNCATION above about CFL_IMEX 7 for
                                 * smooth states); increment form, the state
                                 * alternating between two device buffers of pairs
                                 * (set/get_state convert). Flat bottom, single
@@ -235,6 +236,23 @@ int hsgn_profile_read(hsgn_handle_t h, double* ms, int64_t* launches, int32_t re
  * Synchronises and reports device errors like hsgn_run. */
 int hsgn_run_cfl(hsgn_handle_t h, double cfl, double mcfl, int64_t n_steps, double* t_advanced,
                  void* stream);
+
+/* Window overlap of the HSGN_DOUBLE_FLOAT form (not part of the paper's
+ * method: how far the windowed depth solve of Sec. 4.2 must reach). Each
+ * window checks that the decay of the depth coupling over its overlap stays
+ * under 2^-50, and stage 2 of every step records on the device how many rows
+ * of overlap its windows needed. Every synchronising call (hsgn_run,
+ * hsgn_run_cfl, hsgn_check, this one) sets the overlap of the steps enqueued
+ * after it to that record plus 5 rows, rounded up to a multiple of 8 within
+ * [48, 96] (64 while nothing is recorded; longer tiles for a narrower
+ * overlap); captured step graphs are re-captured when it changes. A window
+ * whose overlap misses the bound all the same (the coupling grew since the
+ * record) redoes its tile in pieces with 96 rows, so the overlap changes only
+ * the speed; beyond 96 rows the step reports HSGN_ERR_TRUNCATION. A new state
+ * (hsgn_set_state) starts with nothing recorded. *rows_needed (host) receives
+ * the rows recorded by the last step (0 if none), *overlap the overlap of the
+ * next steps. Synchronises the stream. HSGN_ERR_UNIMPLEMENTED for other forms. */
+int hsgn_df_overlap(hsgn_handle_t h, int32_t* rows_needed, int32_t* overlap, void* stream);
 
 /* Synchronise the stream and report (and clear) pending device errors. */
 int hsgn_check(hsgn_handle_t h, void* stream);

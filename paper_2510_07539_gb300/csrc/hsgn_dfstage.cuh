@@ -123,6 +123,36 @@ __device__ __forceinline__ void st4(DArr<NC>& a, int i, const float* v) {
     a.set4(i, d);
 }
 
+// Window of the tile rows [t0, t0 + sp) with overlap HW (window_of for a run
+// of rows that need not start at a multiple of the tile size).
+template <int BC>
+__host__ __device__ inline Window window_at(int64_t t0, int sp, int64_t n, int HW) {
+    Window w;
+    w.t0 = t0;
+    w.sp = sp;
+    if (BC == BC_PERIODIC) {
+        w.wl = t0 - HW;
+        w.W = sp + 2 * HW;
+        w.lend = w.rend = false;
+    } else {
+        w.wl = t0 - HW < 0 ? 0 : t0 - HW;
+        const int64_t wr = t0 + sp + HW > n ? n : t0 + sp + HW;
+        w.W = (int)(wr - w.wl);
+        w.lend = w.wl == 0;
+        w.rend = wr == n;
+    }
+    w.lo = (int)(t0 - w.wl);
+    return w;
+}
+
+// Rows between a kept row and the window edge that bring the decay bound
+// rho*^rows under 2^-50, from log2 rho* (0xFFFF when the coupling does not decay).
+__host__ __device__ inline unsigned df_rows_needed(float lg) {
+    if (!(lg < 0.f)) return 0xFFFFu;
+    const float r = ceilf(-50.f / lg);
+    return r < 65535.f ? (unsigned)r : 0xFFFFu;
+}
+
 // Geometry: T threads, M = 4 rows per thread, overlap HW (as FusedGeom).
 template <int T, int M, int HW>
 struct DfGeom {
@@ -182,7 +212,12 @@ struct DfParams {
     int32_t stage;        // 1: writes dU1; 2: writes U^{n+1} to out
     int32_t local_speed;  // Rusanov speed max(|u^L|, |u^R|) per face instead of *speed
     int32_t track_speed;  // stage 1 clears *speed_next, stage 2 folds max |u^{n+1}| into it
-    int32_t S;            // tile rows
+    int32_t S;            // tile rows (one CTA per tile)
+    // overlap of a tile's window, HWt <= HW of the kernel; a tile whose window
+    // misses the decay bound with HWt < HW is redone in pieces with overlap HW
+    int32_t HWt;
+    unsigned* need_out;   // stage 1 clears it, stage 2 records the overlap rows its
+                          // windows needed (df_rows_needed; or nullptr)
     // constants of the stage as pairs (tau = gamma dt): tau, lambda tau^2,
     // lambda tau, tau/(2 dx), lambda tau/(2 dx), tau^2/dx^2, lambda tau^2/dx^2,
     // g, lambda, lambda/3, 1/3, and the stage-2 weights c/gamma, (1-gamma)/gamma
@@ -216,17 +251,15 @@ __global__ void __launch_bounds__(T, 2) k_df_stage(const DfParams p) {
     constexpr bool two = STAGE == 2;
     const int tid = threadIdx.x;
     const int64_t n = p.n;
-    const Window win = window_of<BC>(blockIdx.x, n, p.S, HW);
-    const int W = win.W;
-    const int64_t wl = win.wl;
-    if (tid == 0) {
-        sm.kmax = 0u;
-        sm.kmin = 0x7F7FFFFFu;
-    }
     if (p.track_speed && !two && blockIdx.x == 0 && tid == 0) {
         p.speed_next[0] = 0.0;
         if (p.adaptive) p.speed_next[1] = 0.0;
     }
+    if (!two && p.need_out && blockIdx.x == 0 && tid == 0) *p.need_out = 0u;
+    const int S0 = p.S;
+    const int HW0 = p.HWt < HW ? p.HWt : HW;
+    const int64_t tile0 = (int64_t)blockIdx.x * S0;
+    const int sp0 = (int)(n - tile0 < S0 ? n - tile0 : S0);
     // the time step: fixed (from the parameters) or from the CFL rule
     DfStepConst kc{p.tau, p.lt2, p.ltau, p.fq, p.lfq, p.Cc, p.fd};
     if (p.adaptive) {
@@ -249,6 +282,25 @@ __global__ void __launch_bounds__(T, 2) k_df_stage(const DfParams p) {
         }
         __syncthreads();
         kc = DfStepConst{sm.kc[0], sm.kc[1], sm.kc[2], sm.kc[3], sm.kc[4], sm.kc[5], sm.kc[6]};
+    }
+
+    unsigned bad = 0;
+    dfl umax(0.f), numax(0.f);
+    // pass -1: the tile with the overlap HW0; if its window misses the decay
+    // bound with HW0 < HW, passes 0 .. npieces-1 redo the tile in pieces of
+    // pr rows with the wide overlap HW
+    int npieces = 0, pr = 0;
+    for (int piece = -1;;) {
+    if (piece >= 0) __syncthreads();  // (the previous pass's shared reads are done)
+    const int HWc = piece < 0 ? HW0 : HW;
+    const Window win = piece < 0 ? window_at<BC>(tile0, sp0, n, HW0)
+                                 : window_at<BC>(tile0 + (int64_t)piece * pr,
+                                                 min(pr, sp0 - piece * pr), n, HW);
+    const int W = win.W;
+    const int64_t wl = win.wl;
+    if (tid == 0) {
+        sm.kmax = 0u;
+        sm.kmin = 0x7F7FFFFFu;
     }
 
     // ---- 0. window cells -3 .. W+2 (index c + 3): U_l and U_b (stage 2:
@@ -282,7 +334,6 @@ __global__ void __launch_bounds__(T, 2) k_df_stage(const DfParams p) {
     }
     __syncthreads();
 
-    unsigned bad = 0;
     const int j0 = 4 * tid;
 
     // ---- A. twice the Rusanov fluxes of U_l (Sec. 4.1) at the faces
@@ -461,6 +512,29 @@ __global__ void __launch_bounds__(T, 2) k_df_stage(const DfParams p) {
         if (pos_finite(kmin)) atomicMin(&sm.kmin, __float_as_uint(kmin));
     }
     __syncthreads();
+    // truncation bound of this window, rho*^(HWc - 1) <= 2^-50, from the
+    // coupling bounds of its rows (every thread evaluates the same words: the
+    // decision below is uniform over the CTA)
+    {
+        const bool cut = BC == BC_PERIODIC || !(win.lend && win.rend);
+        const float K = __uint_as_float(sm.kmax), kap = fminf(__uint_as_float(sm.kmin), K);
+        float lg = -INFINITY;
+        if (cut && K > 0.f) {
+            const float Bq = 1.f + K + kap;
+            const float rho = 2.f * K / (Bq + sqrtf(fmaxf(Bq * Bq - 4.f * kap * K, 0.f)));
+            lg = __log2f(rho);
+        }
+        if (two && piece < 0 && p.need_out && tid == 0 && lg > -INFINITY)
+            atomicMax(p.need_out, df_rows_needed(lg));
+        const bool misses = (float)(HWc - 1) * lg > -50.f;
+        if (misses && piece < 0 && HWc < HW) {
+            npieces = (sp0 + Gm::S - 1) / Gm::S;
+            pr = (sp0 + npieces - 1) / npieces;
+            piece = 0;
+            continue;
+        }
+        if (misses && tid == 0) bad |= HSGN_DEV_ERR_TRUNCATION;
+    }
     if (BC == BC_TRANSMISSIVE && (win.lend || win.rend)) {  // (uniform over the CTA)
         // zero-order ghost copies of the per-cell values at the domain ends
         if (tid == 0 && win.lend) {
@@ -552,16 +626,6 @@ __global__ void __launch_bounds__(T, 2) k_df_stage(const DfParams p) {
         if (tid == 0 && win.rend) DH.set(W + 4, DH.get(W + 3));
         __syncthreads();
     }
-    // truncation bound of this window: rho*^HB <= 2^-50
-    if (tid == 0) {
-        const bool cut = BC == BC_PERIODIC || !(win.lend && win.rend);
-        const float K = __uint_as_float(sm.kmax), kap = fminf(__uint_as_float(sm.kmin), K);
-        if (cut && K > 0.f) {
-            const float Bq = 1.f + K + kap;
-            const float rho = 2.f * K / (Bq + sqrtf(fmaxf(Bq * Bq - 4.f * kap * K, 0.f)));
-            if ((float)Gm::HB * __log2f(rho) > -50.f) bad |= HSGN_DEV_ERR_TRUNCATION;
-        }
-    }
 
     // ---- E. back-substitution of the tile rows (lines 11-13 of the scheme;
     //         h w with h^2 implicit, Sec. 6.3.1), in increment form:
@@ -573,7 +637,6 @@ __global__ void __launch_bounds__(T, 2) k_df_stage(const DfParams p) {
     //         cancellation of their lambda tau terms)
     const int lo = win.lo, sp = win.sp;
     const int64_t t0 = win.t0;
-    dfl umax(0.f), numax(0.f);
     for (int t = tid; t < sp; t += T) {
         const int r = lo + t;  // window row; state index r + 3, per-cell index r + 1, dh index r + 4
         const dfl dh = DH.get(r + 4);
@@ -623,6 +686,8 @@ __global__ void __launch_bounds__(T, 2) k_df_stage(const DfParams p) {
             }
         }
     }
+    if (piece < 0 || ++piece >= npieces) break;
+    }  // passes
     if (bad) flag_error(p.err, bad);
     if (p.track_speed && two) {
 #pragma unroll

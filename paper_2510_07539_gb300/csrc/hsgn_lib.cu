@@ -34,8 +34,21 @@ constexpr int OT = 256, OM = 16;
 constexpr int FT = 256, FM = 4, FHW = 64;
 // Double-float windowed stage: DT threads, FM rows per thread, DHW overlap rows
 // (wider than the mixed stage's: the truncation bound is 2^-50, not 2^-30, and
-// 95 rows keep it up to CFL_IMEX of about 7 for smooth states).
-constexpr int DT = 256, DHW = 96;
+// 95 rows keep it up to CFL_IMEX of about 7 for smooth states). The overlap a
+// step takes follows the coupling: stage 2 records the rows its windows
+// needed, and every synchronising call sets the overlap of the next steps to
+// that need plus DF_MARGIN rows, rounded up to a multiple of 8 within
+// [DHW_MIN, DHW] (DHW_START while nothing is recorded); a tile whose window
+// misses the bound all the same is redone with DHW rows (k_df_stage).
+constexpr int DT = 256, DHW = 96, DHW_MIN = 48, DHW_START = 64, DF_MARGIN = 4;
+
+// Overlap rows of the double-float windows for a recorded need (0: none).
+int df_overlap_for(unsigned need) {
+    if (need == 0) return DHW_START;
+    const unsigned want = need + DF_MARGIN + 1;
+    const int hw = (int)((want + 7) / 8 * 8);
+    return hw < DHW_MIN ? DHW_MIN : (hw > DHW ? DHW : hw);
+}
 // Variants of the windowed stage for batches, chosen per instance by
 // hsgn_batched_set_tiles / hsgn_batched_autotune: v = 0 and 1 take FT = 256 and
 // FTS = 128 threads (tiles of up to 894 / 382 rows) with the FHW-row overlap,
@@ -167,6 +180,9 @@ struct hsgn_s {
     // stage; U^{n+1} goes to the other of the two state buffers U, V
     bool windowed = false;
     int32_t tileS = 0;               // tile rows per CTA
+    int32_t dfhw = 0;                // double-float: window overlap of the next steps (tileS follows it)
+    int32_t ghw[2] = {};             // double-float: the overlap each captured step graph holds
+    unsigned* dfneed = nullptr;      // double-float: overlap rows the coupling needed, per state buffer
     int32_t tileSlots = 0;           // co-resident CTAs of the windowed kernel
     int32_t vslots[4] = {};          // co-resident CTAs of each batch variant
     double* V[4] = {};
@@ -201,6 +217,7 @@ struct hsgn_s {
     double gdt[2] = {};
     cudaGraphExec_t gcfl[2] = {};    // one step with the device-side CFL time step
     double gcfl_rule[2][2] = {};     // its (cfl, mcfl)
+    int32_t gcfl_hw[2] = {};         // its double-float window overlap
     // event-pair profiler (hsgn_profile)
     bool prof = false;
     std::vector<cudaEvent_t> ev_pool;
@@ -587,6 +604,13 @@ cudaError_t set_smem_df() {
     return e;
 }
 
+// The window overlap of the next double-float steps and its tile rows.
+void set_df_overlap(hsgn_s* H, int hw) {
+    H->dfhw = hw;
+    H->tileS = (int32_t)fused_tile_rows(H->n, DfGeom<DT, FM, DHW>::R - 2 * hw,
+                                        H->tileSlots > 0 ? H->tileSlots : 1);
+}
+
 // Constants of a double-float stage of step tau; stage 2 gets the efficient-form
 // weights (wl1, wb1) unless given.
 DfParams df_params(const hsgn_s* H, int stage, double tau, double wl1, double wb1) {
@@ -596,6 +620,8 @@ DfParams df_params(const hsgn_s* H, int stage, double tau, double wl1, double wb
     p.local_speed = local_speed(H) ? 1 : 0;
     p.track_speed = local_speed(H) ? 0 : 1;
     p.S = H->tileS;
+    p.HWt = H->dfhw;
+    p.need_out = nullptr;
     const double dx = H->dx, lam = H->lam;
     p.tau = dfl_of(tau);
     p.lt2 = dfl_of(lam * tau * tau);
@@ -652,6 +678,9 @@ cudaError_t launch_stage_df(hsgn_s* H, int stage, double tau, cudaStream_t st, d
     }
     p.speed = speed_of(H, H->cur);
     p.speed_next = speed_of(H, 1 - H->cur);
+    // stage 2 records the coupling of the state it writes (read at the next
+    // synchronising call, which sets the overlap of the steps after it)
+    p.need_out = H->dfneed + (1 - H->cur);
     {
         ProfScope ps(H, HSGN_PROF_ASSEMBLE, st);
         launch_df(H, df_tiles(H), p, st);
@@ -785,10 +814,16 @@ cudaError_t enqueue_step(hsgn_s* H, double dt, cudaStream_t st) {
 }
 
 int read_error(hsgn_s* H, cudaStream_t st) {
-    unsigned bits = 0;
+    unsigned bits = 0, need = 0;
     if (cudaMemcpyAsync(&bits, H->err, sizeof(unsigned), cudaMemcpyDeviceToHost, st) != cudaSuccess)
         return HSGN_ERR_CUDA;
+    // the double-float form: the coupling the last step recorded sets the
+    // window overlap of the steps enqueued from here on
+    if (H->dfneed && cudaMemcpyAsync(&need, H->dfneed + H->cur, sizeof(unsigned),
+                                     cudaMemcpyDeviceToHost, st) != cudaSuccess)
+        return HSGN_ERR_CUDA;
     if (cudaStreamSynchronize(st) != cudaSuccess) return HSGN_ERR_CUDA;
+    if (H->dfneed && need) set_df_overlap(H, df_overlap_for(need));
     if (bits) {
         if (cudaMemsetAsync(H->err, 0, sizeof(unsigned), st) != cudaSuccess) return HSGN_ERR_CUDA;
         if (cudaStreamSynchronize(st) != cudaSuccess) return HSGN_ERR_CUDA;
@@ -846,6 +881,12 @@ cudaError_t refresh_speed(hsgn_s* H, cudaStream_t st) {
     }
     double* out = speed_of(H, H->cur);
     cudaError_t e = cudaMemsetAsync(out, 0, 2 * sizeof(double), st);
+    if (e != cudaSuccess) return e;
+    // a new state: no coupling recorded yet
+    if (H->dfneed) {
+        e = cudaMemsetAsync(H->dfneed, 0, 2 * sizeof(unsigned), st);
+        set_df_overlap(H, DHW_START);
+    }
     if (e != cudaSuccess) return e;
     if (explicit_scheme(H) && !local_speed(H)) {
         // the fully explicit schemes step with the spectral radius max(|u| + c)
@@ -1012,6 +1053,7 @@ int hsgn_create(const hsgn_grid_t* grid, double g, double lambda, const double* 
     total += align_up(BLK_STRIDE * P * sizeof(double)) + align_up(P * sizeof(double));
     const size_t rws = rows_ws_bytes(P);
     total += rws + align_up(8 * sizeof(double)) + align_up(sizeof(unsigned));
+    if (H->dfloat) total += align_up(2 * sizeof(unsigned));
     if (cudaMalloc(&H->mem, total) != cudaSuccess) {
         cudaGetLastError();
         delete H;
@@ -1066,6 +1108,7 @@ int hsgn_create(const hsgn_grid_t* grid, double g, double lambda, const double* 
     }
     H->rws = rws ? take(rws) : nullptr;
     H->spd = reinterpret_cast<double*>(take(align_up(8 * sizeof(double))));
+    if (H->dfloat) H->dfneed = reinterpret_cast<unsigned*>(take(align_up(2 * sizeof(unsigned))));
     H->err = reinterpret_cast<unsigned*>(take(align_up(sizeof(unsigned))));
 
     cudaError_t e = cudaMemset(H->mem, 0, total);
@@ -1080,8 +1123,8 @@ int hsgn_create(const hsgn_grid_t* grid, double g, double lambda, const double* 
                 &per_sm, k_df_stage<DT, FM, DHW, BC_PERIODIC, 2, false>, DT,
                 sizeof(DfShared<DT, FM, DHW>));
         const int64_t slots = (int64_t)(sms > 0 ? sms : 1) * (per_sm > 0 ? per_sm : 1);
-        H->tileS = (int32_t)fused_tile_rows(n, DfGeom<DT, FM, DHW>::S, slots);
         H->tileSlots = (int32_t)slots;
+        set_df_overlap(H, DHW_START);
     } else if (e == cudaSuccess && H->windowed) {
         e = set_smem_fused<FT, BC_PERIODIC, false>();
         if (e == cudaSuccess) e = set_smem_fused<FT, BC_TRANSMISSIVE, false>();
@@ -1246,7 +1289,7 @@ int hsgn_enqueue(hsgn_handle_t H, double dt, int64_t n_steps, void* stream) {
     // one captured step per state buffer (the windowed path alternates them)
     for (int64_t k = 0; k < n_steps; ++k) {
         const int c = H->cur;
-        if (!H->gexec[c] || H->gdt[c] != dt) {
+        if (!H->gexec[c] || H->gdt[c] != dt || H->ghw[c] != H->dfhw) {
             const bool prof = H->prof;
             H->prof = false;  // events are not captured into the graph
             if (H->gexec[c]) {
@@ -1275,10 +1318,26 @@ int hsgn_enqueue(hsgn_handle_t H, double dt, int64_t n_steps, void* stream) {
                 return HSGN_ERR_CUDA;
             }
             H->gdt[c] = dt;
+            H->ghw[c] = H->dfhw;
         }
         if (cudaGraphLaunch(H->gexec[c], st) != cudaSuccess) return HSGN_ERR_CUDA;
         if (H->windowed) H->cur ^= 1;
     }
+    return HSGN_OK;
+}
+
+int hsgn_df_overlap(hsgn_handle_t H, int32_t* rows_needed, int32_t* overlap, void* stream) {
+    if (!H || !rows_needed || !overlap) return HSGN_ERR_INVALID_ARG;
+    if (!H->dfloat || !H->dfneed) return HSGN_ERR_UNIMPLEMENTED;
+    cudaStream_t st = as_stream(stream);
+    unsigned need = 0;
+    if (cudaMemcpyAsync(&need, H->dfneed + H->cur, sizeof(unsigned), cudaMemcpyDeviceToHost,
+                        st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+        return HSGN_ERR_CUDA;
+    set_df_overlap(H, df_overlap_for(need));
+    *rows_needed = (int32_t)need;
+    *overlap = H->dfhw;
     return HSGN_OK;
 }
 
@@ -1299,7 +1358,8 @@ int hsgn_run_cfl(hsgn_handle_t H, double cfl, double mcfl, int64_t n_steps, doub
     if (cudaGetLastError() != cudaSuccess) return HSGN_ERR_CUDA;
     for (int64_t k = 0; k < n_steps; ++k) {
         const int c = H->cur;
-        if (!H->gcfl[c] || H->gcfl_rule[c][0] != cfl || H->gcfl_rule[c][1] != mcfl) {
+        if (!H->gcfl[c] || H->gcfl_rule[c][0] != cfl || H->gcfl_rule[c][1] != mcfl ||
+            H->gcfl_hw[c] != H->dfhw) {
             const bool prof = H->prof;
             H->prof = false;
             if (H->gcfl[c]) {
@@ -1329,6 +1389,7 @@ int hsgn_run_cfl(hsgn_handle_t H, double cfl, double mcfl, int64_t n_steps, doub
             }
             H->gcfl_rule[c][0] = cfl;
             H->gcfl_rule[c][1] = mcfl;
+            H->gcfl_hw[c] = H->dfhw;
         }
         if (cudaGraphLaunch(H->gcfl[c], st) != cudaSuccess) return HSGN_ERR_CUDA;
         H->cur ^= 1;

@@ -73,6 +73,7 @@ def load():
         "hsgn_profile": [_P, ctypes.c_int32],
         "hsgn_profile_read": [_P, _P, _P, ctypes.c_int32],
         "hsgn_check": [_P, _P],
+        "hsgn_df_overlap": [_P, _P, _P, _P],
         "hsgn_suggest_dt": [_P, _D, _D, ctypes.POINTER(_D), _P],
         "hsgn_stage": [_P, ctypes.POINTER(_P), ctypes.POINTER(_P), _D, _D, ctypes.POINTER(_P), _P],
         "hsgn_adjoint": [_P, _D, _I64, _I64, _P, _P, _I64, _P, _P, _P, _P],
@@ -199,6 +200,14 @@ class Solver:
 
     def enqueue(self, dt: float, n_steps: int, stream=None):
         _check(_lib.hsgn_enqueue(self._h, float(dt), int(n_steps), _stream(stream)), "hsgn_enqueue")
+
+    def df_overlap(self, stream=None):
+        """(rows the last step's coupling needed, overlap rows of the next
+        step) of a double-float form (hsgn_df_overlap)."""
+        need, ov = ctypes.c_int32(0), ctypes.c_int32(0)
+        _check(_lib.hsgn_df_overlap(self._h, ctypes.byref(need), ctypes.byref(ov),
+                                    _stream(stream)), "hsgn_df_overlap")
+        return int(need.value), int(ov.value)
 
     def profile(self, enable: bool):
         _check(_lib.hsgn_profile(self._h, int(bool(enable))), "hsgn_profile")

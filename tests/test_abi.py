@@ -97,6 +97,8 @@ def test_null_handle_calls_are_rejected(lib):
     v = (ctypes.c_int32 * 2)()
     assert lib.hsgn_batched_set_tiles(None, ctypes.cast(v, ctypes.c_void_p)) == 1
     assert lib.hsgn_batched_get_tiles(None, ctypes.cast(v, ctypes.c_void_p)) == 1
+    i1, i2 = ctypes.c_int32(), ctypes.c_int32()
+    assert lib.hsgn_df_overlap(None, ctypes.byref(i1), ctypes.byref(i2), None) == 1
     ms = (ctypes.c_double * 3)()
     ch = ctypes.c_int32()
     assert lib.hsgn_batched_autotune(None, 2, ctypes.cast(ms, ctypes.c_void_p), ctypes.byref(ch),

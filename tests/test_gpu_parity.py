@@ -311,6 +311,55 @@ def test_dfloat_reports_truncation_beyond_its_window():
                 s.check()
 
 
+def df_overlap_for(need):
+    # the overlap the library takes after recording `need` rows (0: none yet):
+    # need + 4 + 1 rounded up to a multiple of 8, within [48, 96]; 64 unrecorded
+    if need == 0:
+        return 64
+    return min(96, max(48, (need + 5 + 7) // 8 * 8))
+
+
+def test_dfloat_overlap_follows_the_coupling():
+    # CFL_IMEX 4: the coupling decays by about 0.55 per row and the windows
+    # need under 64 rows of overlap. CFL_IMEX 5.5: about 0.65 per row; the
+    # first step's 64-row windows miss the 2^-50 bound and redo their tiles in
+    # pieces with 96 rows, and the rows recorded by that step set the overlap
+    # of the next ones. Both agree with the oracle to the FP64 bar.
+    n, dx, lam, steps = 20000, 0.1, 100.0, 3
+    x, _ = inputs.cell_centres(n, 0.0, n * dx)
+    U = inputs.solitary(x, 1.0, 0.05, 0.5 * n * dx, period=n * dx)
+    p = oracle.Params(n, dx, 0, lam=lam)
+    for cfl in (4.0, 5.5):
+        dt, _, _ = oracle.suggest_dt(p, U, cfl, 1e9)
+        with S().Solver(n, 0.0, n * dx, 0, lam=lam, flags=S().FLAG_DOUBLE_FLOAT) as s:
+            s.set_state(*(dev(u) for u in U))
+            assert s.df_overlap() == (0, 64)  # a new state: nothing recorded
+            s.step(dt)
+            s.check()
+            need, ov = s.df_overlap()
+            assert ov == df_overlap_for(need), (cfl, need, ov)
+            if cfl == 4.0:
+                assert 0 < need <= 63 and ov <= 64, (need, ov)
+            else:
+                assert 63 < need <= 95 and ov > 64, (need, ov)  # the first step fell back
+            s.run(dt, steps - 1)
+            need2, ov2 = s.df_overlap()
+            assert ov2 == df_overlap_for(need2) and abs(need2 - need) <= 2, (need, need2)
+            got = [t.cpu().numpy() for t in s.get_state()]
+            s.set_state(*(dev(u) for u in U))
+            assert s.df_overlap() == (0, 64)
+        ref = oracle.run(p, U, dt, steps)
+        sc = summand_scales(n, dx, 0, lam, U, dt)
+        for k in range(4):
+            e = scaled_err(got[k], ref[k], sc[k])
+            assert e < 1e-12, (cfl, k, e)
+        assert rel_l2(got[0], ref[0]) < 1e-12 and rel_l2(got[2], ref[2]) < 1e-12
+    with S().Solver(n, 0.0, n * dx, 0, lam=lam, flags=S().FLAG_MIXED) as s:
+        with pytest.raises(S().HsgnError) as e:
+            s.df_overlap()
+        assert e.value.code == 6
+
+
 def test_dfloat_rejects_other_forms():
     for extra in (0x2, 0x4, 0x100, 0x5):
         with pytest.raises(S().HsgnError) as e:

@@ -123,47 +123,88 @@ void check(int64_t n, int S) {
 }
 
 // The double-float stage: T = 256 threads, four rows each, overlap DHW.
-constexpr int DT = 256, DHW = 96;
+constexpr int DT = 256, DHW = 96, DHW_MIN = 48;
 
+// One window of the double-float stage (tile rows [w.t0, w.t0 + w.sp)).
 template <int BC>
-void check_df(int64_t n, int S) {
+void check_df_window(const Window& w, int64_t n) {
+    using G = DfGeom<DT, M, DHW>;
+    const int S = w.sp;          // (reported by CHECK)
+    const int64_t p = w.t0;
+    ++checked_windows;
+    CHECK(w.sp >= 1);
+    CHECK(w.W >= 1 && w.W <= G::R && w.W + 1 <= DT * M);
+    CHECK(w.lo >= 0 && w.lo + w.sp <= w.W);
+    CHECK(w.W + 6 <= G::NC);  // loaded cells -3 .. W + 2
+    const bool inner = inner_window(w.wl, w.W, n);
+    for (int j = 0; j < w.W + 6; ++j) {
+        const int64_t gi = inner ? w.wl - 3 + j : cell_at<BC>(w.wl - 3 + j, n);
+        CHECK(gi >= 0 && gi < n);
+        CHECK(gi == cell_at<BC>(w.wl - 3 + j, n));
+    }
+    // flux phase: thread t writes faces 4t .. 4t + 3; the last thread also
+    // face 4T when W + 3 > 4T. The cell phase reads faces 0 .. W + 2 (cells
+    // c = -1 .. W, faces j and j + 1 of cell j - 1); a face f is built from
+    // the loaded cells at index f .. f + 3
+    const int top = (w.W + 3 > 4 * DT) ? 4 * DT : 4 * DT - 1;  // highest face written
+    CHECK(w.W + 2 <= top);
+    CHECK(top + 3 < G::NC);
+    for (int f = 0; f <= w.W + 2; ++f) CHECK(f + 3 < w.W + 6);
+    // cell phase: cell j (j < W + 2) reads state index j + 2 (loaded) and
+    // writes per-cell index j; row phase: row i < W reads per-cell indices
+    // i .. i + 2 and state indices i + 2 .. i + 4; back-substitution: tile row
+    // r reads dh at r + 3 .. r + 5 (rows -1 .. W, index 3 a ghost only at a
+    // transmissive left end, where lo = 0)
+    CHECK(w.W + 1 + 2 < w.W + 6);
+    CHECK(w.W - 1 + 4 < w.W + 6);
+    CHECK(w.lo + w.sp - 1 + 5 <= w.W + 4 && w.W + 4 < G::NC);
+    CHECK(w.lo >= 1 || (BC == BC_TRANSMISSIVE && w.lend));
+}
+
+// The wide tiling (tiles of S rows, overlap DHW) and a narrower one (tiles of
+// Sn rows, overlap hwn: 48 .. 88 in steps of 8) of an n-cell grid: the windows
+// of every tile, and of the pieces (wide overlap) that a narrower tile is redone
+// in when its window misses the decay bound; both tilings cover the grid once.
+template <int BC>
+void check_df(int64_t n, int S, int Sn = 0, int hwn = 0) {
     using G = DfGeom<DT, M, DHW>;
     int64_t p = -1;
-    CHECK(S >= 1 && S <= G::S);
     CHECK(G::NC % 4 == 0 && 4 * DT + 4 <= G::NC);  // get4 at 4t + 4 reads up to 4T + 3
+    CHECK(S >= 1 && S <= G::S);
     const int64_t P = (n + S - 1) / S;
     int64_t covered = 0;
     for (p = 0; p < P; ++p) {
-        ++checked_windows;
         const Window w = window_of<BC>(p, n, S, DHW);
+        const Window wa = window_at<BC>(p * (int64_t)S, w.sp, n, DHW);
+        CHECK(w.t0 == wa.t0 && w.wl == wa.wl && w.W == wa.W && w.lo == wa.lo && w.sp == wa.sp);
         CHECK(w.sp >= 1 && w.sp <= S && w.t0 == covered);
         covered += w.sp;
-        CHECK(w.W >= 1 && w.W <= G::R && w.W + 1 <= DT * M);
-        CHECK(w.lo >= 0 && w.lo + w.sp <= w.W);
-        CHECK(w.W + 6 <= G::NC);  // loaded cells -3 .. W + 2
-        const bool inner = inner_window(w.wl, w.W, n);
-        for (int j = 0; j < w.W + 6; ++j) {
-            const int64_t gi = inner ? w.wl - 3 + j : cell_at<BC>(w.wl - 3 + j, n);
-            CHECK(gi >= 0 && gi < n);
-            CHECK(gi == cell_at<BC>(w.wl - 3 + j, n));
+        check_df_window<BC>(w, n);
+    }
+    CHECK(covered == n);
+    if (Sn == 0) return;
+    CHECK(hwn >= DHW_MIN && hwn < DHW && hwn % 8 == 0);
+    CHECK(Sn >= S && Sn <= G::R - 2 * hwn);
+    const int64_t Pn = (n + Sn - 1) / Sn;
+    covered = 0;
+    for (p = 0; p < Pn; ++p) {
+        const int64_t t0 = p * (int64_t)Sn;
+        const int sp = (int)(n - t0 < Sn ? n - t0 : Sn);
+        CHECK(sp >= 1 && t0 == covered);
+        covered += sp;
+        check_df_window<BC>(window_at<BC>(t0, sp, n, hwn), n);
+        const int np = (sp + G::S - 1) / G::S;
+        const int pr = (sp + np - 1) / np;
+        int64_t pc = t0;
+        for (int k = 0; k < np; ++k) {
+            const int psp = pr < sp - k * pr ? pr : sp - k * pr;
+            CHECK(psp >= 1 && psp <= G::S);
+            const Window w = window_at<BC>(t0 + (int64_t)k * pr, psp, n, DHW);
+            CHECK(w.t0 == pc);
+            pc += psp;
+            check_df_window<BC>(w, n);
         }
-        // flux phase: thread t writes faces 4t .. 4t + 3; the last thread also
-        // face 4T when W + 3 > 4T. The cell phase reads faces 0 .. W + 2 (cells
-        // c = -1 .. W, faces j and j + 1 of cell j - 1); a face f is built from
-        // the loaded cells at index f .. f + 3
-        const int top = (w.W + 3 > 4 * DT) ? 4 * DT : 4 * DT - 1;  // highest face written
-        CHECK(w.W + 2 <= top);
-        CHECK(top + 3 < G::NC);
-        for (int f = 0; f <= w.W + 2; ++f) CHECK(f + 3 < w.W + 6);
-        // cell phase: cell j (j < W + 2) reads state index j + 2 (loaded) and
-        // writes per-cell index j; row phase: row i < W reads per-cell indices
-        // i .. i + 2 and state indices i + 2 .. i + 4; back-substitution: tile row
-        // r reads dh at r + 3 .. r + 5 (rows -1 .. W, index 3 a ghost only at a
-        // transmissive left end, where lo = 0)
-        CHECK(w.W + 1 + 2 < w.W + 6);
-        CHECK(w.W - 1 + 4 < w.W + 6);
-        CHECK(w.lo + w.sp - 1 + 5 <= w.W + 4 && w.W + 4 < G::NC);
-        CHECK(w.lo >= 1 || (BC == BC_TRANSMISSIVE && w.lend));
+        CHECK(pc == t0 + sp);
     }
     CHECK(covered == n);
 }
@@ -180,7 +221,9 @@ void check_grid(int64_t n) {
     check<128, BC, 32>(n, (int)fused_tile_rows(n, FusedGeom<128, M, 32>::S, 1));
     using D = DfGeom<DT, M, DHW>;
     for (int64_t slots : {1, 2, 152, 304})
-        check_df<BC>(n, (int)fused_tile_rows(n, D::S, slots));
+        for (int hw = DHW_MIN; hw < DHW; hw += 8)
+            check_df<BC>(n, (int)fused_tile_rows(n, D::S, slots),
+                         (int)fused_tile_rows(n, D::R - 2 * hw, slots), hw);
 }
 
 int main() {
@@ -206,10 +249,14 @@ int main() {
         }
     // full double-float windows (tiles of the largest size, as a 2^16 grid gets)
     using D = DfGeom<DT, M, DHW>;
-    for (int64_t k = 1; k <= 80; ++k) {
-        check_df<BC_PERIODIC>(k * D::S, D::S);
-        check_df<BC_TRANSMISSIVE>(k * D::S + 1, D::S);
-    }
+    for (int64_t k = 1; k <= 80; ++k)
+        for (int hw = DHW_MIN; hw < DHW; hw += 8) {
+            const int sn = D::R - 2 * hw;
+            check_df<BC_PERIODIC>(k * D::S, D::S, sn, hw);
+            check_df<BC_TRANSMISSIVE>(k * D::S + 1, D::S, sn, hw);
+            check_df<BC_PERIODIC>(k * sn, D::S, sn, hw);
+            check_df<BC_TRANSMISSIVE>(k * sn + 1, D::S, sn, hw);
+        }
     printf("large: R=%d S=%d NC=%d; small: R=%d S=%d NC=%d; double-float: R=%d S=%d NC=%d; "
            "windows=%lld\nall index checks passed\n", G::R, G::S, G::NC, Gs::R, Gs::S, Gs::NC,
            D::R, D::S, D::NC, checked_windows);
