@@ -64,13 +64,14 @@ FLOPS_PER_CELL_ASSEMBLE = 149.0
 # and launch (average of its two stages, window overlap included): ncu's
 # per-launch counts of FADD + FMUL + 2 FFMA (sm__sass_thread_inst_executed_op_
 # {fadd,fmul,ffma}_pred_on.sum) divided by the cells of the launch, on the
-# 2^22-cell dam break (lambda = 1000; the capture of profiles/ncu_df_stage.md).
+# 2^22-cell dam break (lambda = 1000, 64-row window overlap; the capture of
+# profiles/ncu_df_stage.md).
 # Valid for the kernel sources whose hash is DF_FLOPS_SOURCE_SHA; None when the
 # kernel has changed since (the roofline then reports no achieved flop rate).
-DF_FLOPS_PER_CELL = 1596.0      # stage 1 / 2: 1496 / 1696
-DF_FP32_INST_PER_CELL = 1321.0  # FADD + FMUL + FFMA instructions, stage 1 / 2: 1238 / 1404
-DF_TRAFFIC_PER_CELL = 71.5      # dram__bytes_read + write per cell and launch, stage 1 / 2: 54.0 / 89.0
-DF_FLOPS_SOURCE_SHA = "398d7dd3540bf64e"
+DF_FLOPS_PER_CELL = 1519.5      # stage 1 / 2: 1425 / 1614
+DF_FP32_INST_PER_CELL = 1258.5  # FADD + FMUL + FFMA instructions, stage 1 / 2: 1180 / 1337
+DF_TRAFFIC_PER_CELL = 70.9      # dram__bytes_read + write per cell and launch, stage 1 / 2: 53.2 / 88.6
+DF_FLOPS_SOURCE_SHA = "83c006e0d51cad44"
 DF_SOURCES = ("hsgn_dfstage.cuh", "hsgn_dfloat.cuh", "hsgn_fused.cuh", "hsgn_mixed.cuh",
               "hsgn_tridiag.cuh")
 
