@@ -941,15 +941,19 @@ def run_ours(args):
         # every step copies each instance's state in from pinned host memory,
         # steps it and copies the result out to pinned host memory
         # (hsgn_copy_state_out: enqueued, no host wait). Consecutive steps
-        # alternate between two sets of handles, each instance of a set on its
-        # own stream, so that one step's copies in overlap the previous step's
-        # copies out on the two copy engines; errors are checked after the
+        # alternate between two sets of handles, each instance of a set with
+        # its own pair of streams: the copies and their conversions on a
+        # high-priority stream, so that they are not held behind the stage
+        # kernels of the other instances, the step on a normal one, joined by
+        # events; one step's copies in then overlap the other instances' steps
+        # and copies out on the copy engines. Errors are checked after the
         # timed region
         sets = [dsols, [S.Solver(n, xl, xr, S.BC_TRANSMISSIVE, lam=l, flags=S.FLAG_DOUBLE_FLOAT)
                         for l in lams]]
         host_out = [[[torch.empty(n, dtype=torch.float64).pin_memory() for _ in range(4)]
                      for _ in lams] for _ in sets]
         side = [[torch.cuda.Stream() for _ in lams] for _ in sets]
+        cside = [[torch.cuda.Stream(priority=-1) for _ in lams] for _ in sets]
         for s, dt, hi, ho in zip(sets[1], ddts, host_in, host_out[1]):
             s.set_state(*hi)
             s.step(dt)  # the step graph of the new handle, outside the timed region
@@ -960,16 +964,23 @@ def run_ours(args):
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         fork.record(stream)
-        for sts in side:
+        for sts in side + cside:
             for st in sts:
                 st.wait_event(fork)
         for it in range(k_e2e):
             c = it % 2
-            for s, dt, hi, ho, st in zip(sets[c], ddts, host_in, host_out[c], side[c]):
-                s.set_state(*hi, stream=st)
+            for s, dt, hi, ho, st, cs in zip(sets[c], ddts, host_in, host_out[c], side[c],
+                                             cside[c]):
+                s.set_state(*hi, stream=cs)
+                ready = torch.cuda.Event()
+                ready.record(cs)
+                st.wait_event(ready)
                 s.step(dt, stream=st)
-                s.copy_state_out(ho, stream=st)
-        for sts in side:
+                done = torch.cuda.Event()
+                done.record(st)
+                cs.wait_event(done)
+                s.copy_state_out(ho, stream=cs)
+        for sts in side + cside:
             for st in sts:
                 j = torch.cuda.Event()
                 j.record(st)
