@@ -745,8 +745,8 @@ __global__ void __launch_bounds__(T, (WB ? 768 : 1024) / T) k_mixed_fused(const 
         for (int e = 0; e < 4; e += 2)
             *reinterpret_cast<float2*>(Psi + j0 + e + 2) = make_float2(PS[e], PS[e + 1]);
     }
-    // tile-boundary mini solves (warps 1 and 2, while warp 0 solves the
-    // separator system of the window)
+    // tile-boundary mini solves (the last two warps, while the others solve
+    // the separator system of the window; wid = 1, 2 selects the face)
     // (stage 2 only: stage 1 writes every face of G1 once, from the tile on
     // its left, and updates no depth)
     const bool lface = two && !(BC == BC_TRANSMISSIVE && win.t0 == 0);
@@ -807,21 +807,16 @@ __global__ void __launch_bounds__(T, (WB ? 768 : 1024) / T) k_mixed_fused(const 
         };
         float y[M];
         if constexpr (two) {
-            // warp 0 solves the separator system while warps 1 and 2 solve the
-            // tile-face mini windows
-            float v[M], w[M], last[4];
-            int cs, m;
-            cta_block_solve_fixed<T, M>(W + 1, roww, sm.sep, y, v, w, cs, m, last, p.err, mini);
-#pragma unroll
-            for (int k = 0; k < M; ++k)
-                if (!(k < m && cs + k < W)) y[k] = 0.f;
+            // the separators by cyclic reduction over all warps but the last
+            // two, which solve the tile-face mini windows meanwhile
+            cta_window_solve<T, M, T - 64>(W + 1, roww, sm.sep, y, p.err, mini);
         } else {
             // no mini windows in stage 1: the separators by cyclic reduction over all threads
             cta_window_solve<T, M>(W + 1, roww, sm.sep, y, p.err);
-#pragma unroll
-            for (int k = 0; k < M; ++k)
-                if (!(j0 + k < W)) y[k] = 0.f;
         }
+#pragma unroll
+        for (int k = 0; k < M; ++k)
+            if (!(j0 + k < W)) y[k] = 0.f;
         // dh = y: the values outside the window (and the closing row) are taken as 0
         sts4(dha + j0 + 4, y);
     }

@@ -82,6 +82,23 @@ __device__ __forceinline__ float rcp(float x) {
 __device__ __forceinline__ float fma_u(float a, float b, float c) { return fmaf(a, b, c); }
 __device__ __forceinline__ double fma_u(double a, double b, double c) { return ::fma(a, b, c); }
 
+// Barrier of the first n threads of the CTA (n a multiple of 32) on hardware
+// barrier id (1 .. 15; __syncthreads uses 0), and the same barrier returning
+// whether any of them passed a true predicate.
+__device__ __forceinline__ void group_sync(int id, int n) {
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory");
+}
+__device__ __forceinline__ bool group_or(int id, int n, bool pred) {
+    int r;
+    asm volatile(
+        "{\n\t.reg .pred pi, po;\n\tsetp.ne.s32 pi, %1, 0;\n\t"
+        "bar.red.or.pred po, %2, %3, pi;\n\tselp.s32 %0, 1, 0, po;\n\t}"
+        : "=r"(r)
+        : "r"((int)pred), "r"(id), "r"(n)
+        : "memory");
+    return r != 0;
+}
+
 // Leading single-precision value of a number (magnitude tests).
 __device__ __forceinline__ float hi_of(float x) { return x; }
 __device__ __forceinline__ float hi_of(double x) { return (float)x; }
@@ -491,10 +508,14 @@ __device__ __forceinline__ void cta_block_solve_impl(int nrows, RowK row, SepSha
 // row count levels, each a constant number of operations per thread, so no
 // warp idles while one works. On return x[k] holds the solution of row
 // M t + k (zero for the closing row and for rows past nrows).
+// TP < T: only the first TP threads (TP = T - 64) reduce the separators, two
+// rows each, on their own barrier, while the last two warps run
+// side(1) and side(2) (other work of the CTA that needs no barrier).
 // ---------------------------------------------------------------------------
-template <int T, int M, class RowK, class Real>
+template <int T, int M, int TP = T, class RowK, class Real, class Side = NoSide>
 __device__ __forceinline__ void cta_window_solve(int nrows, RowK row, SepShared<T, Real>& sh,
-                                                 Real (&x)[M], unsigned* err) {
+                                                 Real (&x)[M], unsigned* err,
+                                                 Side side = Side()) {
     const int t = threadIdx.x;
     const int teff = (nrows + M - 1) / M;
     const int cs = t < teff ? M * t : nrows;
@@ -577,40 +598,85 @@ __device__ __forceinline__ void cta_window_solve(int nrows, RowK row, SepShared<
     //         multiply separators no larger than the solution), the levels left
     //         would change no separator beyond that and are skipped.
     const float drop = sizeof(Real) == sizeof(float) ? 0x1p-26f : 0x1p-52f;
-    for (int s = 1; s < ns; s <<= 1) {
-        const bool coupled = t < ns && fabsf(hi_of(A)) + fabsf(hi_of(C)) > drop * fabsf(hi_of(B));
-        if (!__syncthreads_or(coupled)) break;
-        if (t < ns) {
-            sh.A[pd(t)] = A;
-            sh.B[pd(t)] = B;
-            sh.C[pd(t)] = C;
-            sh.D1[pd(t)] = D;
+    auto coupled_row = [&](const Real& a, const Real& b, const Real& c) {
+        return fabsf(hi_of(a)) + fabsf(hi_of(c)) > drop * fabsf(hi_of(b));
+    };
+    // row r of the level of stride s from its neighbours' rows in shared memory
+    auto reduce_row = [&](int r, int s, Real& a, Real& b, Real& c, Real& d) {
+        Real nA = Real(0), nC = Real(0), nB = b, nD = d;
+        if (r - s >= 0) {
+            const Real k1 = a * rcp(sh.B[pd(r - s)]);
+            nA = -k1 * sh.A[pd(r - s)];
+            nB = fma_u(-k1, sh.C[pd(r - s)], nB);
+            nD = fma_u(-k1, sh.D1[pd(r - s)], nD);
         }
-        __syncthreads();
-        if (t < ns) {
-            Real nA = Real(0), nC = Real(0), nB = B, nD = D;
-            if (t - s >= 0) {
-                const Real k1 = A * rcp(sh.B[pd(t - s)]);
-                nA = -k1 * sh.A[pd(t - s)];
-                nB = fma_u(-k1, sh.C[pd(t - s)], nB);
-                nD = fma_u(-k1, sh.D1[pd(t - s)], nD);
-            }
-            if (t + s < ns) {
-                const Real k2 = C * rcp(sh.B[pd(t + s)]);
-                nC = -k2 * sh.C[pd(t + s)];
-                nB = fma_u(-k2, sh.A[pd(t + s)], nB);
-                nD = fma_u(-k2, sh.D1[pd(t + s)], nD);
-            }
-            A = nA;
-            B = nB;
-            C = nC;
-            D = nD;
+        if (r + s < ns) {
+            const Real k2 = c * rcp(sh.B[pd(r + s)]);
+            nC = -k2 * sh.C[pd(r + s)];
+            nB = fma_u(-k2, sh.A[pd(r + s)], nB);
+            nD = fma_u(-k2, sh.D1[pd(r + s)], nD);
         }
+        a = nA;
+        b = nB;
+        c = nC;
+        d = nD;
+    };
+    auto store_row = [&](int r, const Real& a, const Real& b, const Real& c, const Real& d) {
+        sh.A[pd(r)] = a;
+        sh.B[pd(r)] = b;
+        sh.C[pd(r)] = c;
+        sh.D1[pd(r)] = d;
+    };
+    if constexpr (TP == T) {
+        for (int s = 1; s < ns; s <<= 1) {
+            const bool coupled = t < ns && coupled_row(A, B, C);
+            if (!__syncthreads_or(coupled)) break;
+            if (t < ns) store_row(t, A, B, C, D);
+            __syncthreads();
+            if (t < ns) reduce_row(t, s, A, B, C, D);
+            __syncthreads();
+        }
+        if (t < ns) {
+            if (!pos_finite(B)) bad = true;
+            sh.YF[pd(t)] = D * rcp(B);
+        }
+    } else {
+        static_assert(TP == T - 64 && TP % 32 == 0 && 2 * TP >= T, "the group leaves two warps");
+        // the rows of the last two warps go to the group: thread t < TP takes
+        // rows t and t + TP
+        if (t >= TP && t < ns) store_row(t, A, B, C, D);
         __syncthreads();
-    }
-    if (t < ns) {
-        if (!pos_finite(B)) bad = true;
-        sh.YF[pd(t)] = D * rcp(B);
+        if (t < TP) {
+            const int t2 = t + TP;
+            Real A2 = Real(0), B2 = Real(1), C2 = Real(0), D2 = Real(0);
+            if (t2 < ns) {
+                A2 = sh.A[pd(t2)];
+                B2 = sh.B[pd(t2)];
+                C2 = sh.C[pd(t2)];
+                D2 = sh.D1[pd(t2)];
+            }
+            for (int s = 1; s < ns; s <<= 1) {
+                const bool coupled =
+                    (t < ns && coupled_row(A, B, C)) || (t2 < ns && coupled_row(A2, B2, C2));
+                if (!group_or(1, TP, coupled)) break;
+                if (t < ns) store_row(t, A, B, C, D);
+                if (t2 < ns) store_row(t2, A2, B2, C2, D2);
+                group_sync(1, TP);
+                if (t < ns) reduce_row(t, s, A, B, C, D);
+                if (t2 < ns) reduce_row(t2, s, A2, B2, C2, D2);
+                group_sync(1, TP);
+            }
+            if (t < ns) {
+                if (!pos_finite(B)) bad = true;
+                sh.YF[pd(t)] = D * rcp(B);
+            }
+            if (t2 < ns) {
+                if (!pos_finite(B2)) bad = true;
+                sh.YF[pd(t2)] = D2 * rcp(B2);
+            }
+        } else {
+            side(t / 32 - TP / 32 + 1);
+        }
     }
     if (bad) flag_error(err, HSGN_DEV_ERR_COERCIVE);
     __syncthreads();
