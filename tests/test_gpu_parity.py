@@ -360,6 +360,44 @@ def test_dfloat_overlap_follows_the_coupling():
         assert e.value.code == 6
 
 
+@pytest.mark.parametrize("bc", [0, 1])
+@pytest.mark.parametrize("n", [1000, 1799, 2689, 9001])
+def test_dfloat_fallback_tiles_match_oracle(n, bc):
+    # every tile of the first step misses the bound with its 64-row window and
+    # is redone in pieces with 96 rows (CFL_IMEX 5.5), over grids whose last
+    # tile is ragged and, periodic, across the seam; the next step takes the
+    # overlap recorded by the first, and a step at CFL_IMEX 2 brings it back
+    # down to the narrowest
+    dx, lam = 0.1, 100.0
+    L = n * dx
+    x, _ = inputs.cell_centres(n, 0.0, L)
+    U = inputs.solitary(x, 1.0, 0.05, 0.5 * L, period=L if bc == 0 else None)
+    p = oracle.Params(n, dx, bc, lam=lam)
+    dt, _, _ = oracle.suggest_dt(p, U, 5.5, 1e9)
+    with S().Solver(n, 0.0, L, bc, lam=lam, flags=S().FLAG_DOUBLE_FLOAT) as s:
+        s.set_state(*(dev(u) for u in U))
+        s.run(dt, 1)
+        need, ov = s.df_overlap()
+        assert 63 < need <= 95 and ov == df_overlap_for(need), (need, ov)
+        one = [t.cpu().numpy() for t in s.get_state()]
+        s.run(dt, 1)
+        two = [t.cpu().numpy() for t in s.get_state()]
+        dt2, _, _ = oracle.suggest_dt(p, two, 2.0, 1e9)
+        s.run(dt2, 1)
+        need3, ov3 = s.df_overlap()
+        assert need3 < need and ov3 == df_overlap_for(need3) and ov3 < ov, (need3, ov3)
+        three = [t.cpu().numpy() for t in s.get_state()]
+    r1 = oracle.step(p, U, dt)
+    r2 = oracle.step(p, r1, dt)
+    r3 = oracle.step(p, r2, dt2)
+    for got, ref, u0, d in ((one, r1, U, dt), (two, r2, r1, dt), (three, r3, r2, dt2)):
+        sc = summand_scales(n, dx, bc, lam, u0, d)
+        for k in range(4):
+            e = scaled_err(got[k], ref[k], sc[k])
+            assert e < 1e-12, (k, e)
+        assert rel_l2(got[0], ref[0]) < 1e-12
+
+
 def test_dfloat_rejects_other_forms():
     for extra in (0x2, 0x4, 0x100, 0x5):
         with pytest.raises(S().HsgnError) as e:
