@@ -95,16 +95,20 @@ enum {
                                 * HSGN_ERR_TRUNCATION above about CFL_IMEX 7 for
                                 * smooth states); increment form, the state
                                 * alternating between two device buffers of pairs
-                                * (set/get_state convert). Flat bottom, single
-                                * instances, the paper's scheme; not combinable
-                                * with HSGN_EXACT_SOLVE or HSGN_WELL_BALANCED
-                                * (HSGN_ERR_UNIMPLEMENTED). hsgn_stage works in
-                                * this form and leaves the state untouched.
+                                * (set/get_state convert). Single instances, the
+                                * paper's scheme, flat or with HSGN_WELL_BALANCED
+                                * (the bottom form in pairs throughout); not
+                                * combinable with HSGN_EXACT_SOLVE
+                                * (HSGN_ERR_UNIMPLEMENTED), and hsgn_adjoint stays
+                                * with the FP64 form. hsgn_stage works in this
+                                * form and leaves the state untouched.
                                 * HSGN_DOUBLE_FLOAT | HSGN_MIXED is the precision
                                 * split with an FP64-class solve: reconstruction,
                                 * fluxes, starred increments and coefficients in
                                 * FP32; rows, depth solve, back-substitution and
-                                * the state accumulation in pairs. */
+                                * the state accumulation in pairs (flat bottom
+                                * only: with HSGN_WELL_BALANCED as well,
+                                * HSGN_ERR_UNIMPLEMENTED). */
 #define HSGN_EXACT_SOLVE 0x4   /* with HSGN_MIXED: solve the depth system exactly
                                 * through the global separator system (three
                                 * launches per stage, state updated in place) */
@@ -142,9 +146,10 @@ enum {
                                  * depth rows and the momentum as face forces
                                  * linearised about U_l, so that a lake at rest
                                  * (u = 0, eta = h, w = 0, h + b constant) stays at
-                                 * rest. FP64, or HSGN_MIXED on the windowed
-                                 * kernel (the bottom held as double-float pairs,
-                                 * the free-surface jumps taken from the pairs;
+                                 * rest. FP64, HSGN_DOUBLE_FLOAT (every value a
+                                 * pair), or HSGN_MIXED on the windowed kernel
+                                 * (the bottom held as double-float pairs, the
+                                 * free-surface jumps taken from the pairs;
                                  * HSGN_ERR_UNIMPLEMENTED with HSGN_EXACT_SOLVE);
                                  * single instances only. */
 

@@ -164,16 +164,29 @@ struct DfGeom {
     static_assert(S > 0, "overlap too wide for the window");
 };
 
+// The bottom of the window (bottom form only).
+template <int NC, bool WB>
+struct DfWb {
+    DArr<NC> bb;
+};
+template <int NC>
+struct DfWb<NC, false> {};
+
 // Shared memory. Cell c of the window at c + 3 in the state arrays, at c + 1
 // in the per-cell arrays; face jf (between window cells jf - 2 and jf - 1) at
-// jf. After the cell phase the U_l arrays and two flux arrays are reused:
-// dq -> hl, dm^ -> ql, dr -> ml, beta -> rl, delta -> fq; dh of row r -> fm at r + 4.
-template <int T, int M, int HW>
+// jf. After the cell phase the U_l arrays and the flux arrays are reused:
+// flat: dq -> hl, dm^ -> ql, dr -> ml, beta -> rl, delta -> fq; dh of row r
+// -> fm at r + 4. Bottom form (h_l stays in hl for the face forces): dq -> ql,
+// dm^ -> ml, dr -> rl, beta -> fq, pi -> fm, p~ -> fr; after the solve the
+// face forces Psi -> fm (face jf at jf) and dh -> fr.
+
+template <int T, int M, int HW, bool WB = false>
 struct DfShared {
     static constexpr int NC = DfGeom<T, M, HW>::NC;
     DArr<NC> hl, ql, ml, rl;  // U_l
     DArr<NC> hb, qb, mb, rb;  // U_b
     DArr<NC> fq, fm, fr;      // twice the Rusanov fluxes of q, h eta, h w
+    DfWb<NC, WB> wb;          // the bottom b, cells -3 .. W+2 at c + 3
     SepShared<T, dfl> sep;
     unsigned kmax, kmin;      // bits of max / min tau^2 beta / dx^2 (positive floats order as integers)
     dfl kc[7];                // per-step constants of an adaptive step
@@ -218,6 +231,10 @@ struct DfParams {
     int32_t HWt;
     unsigned* need_out;   // stage 1 clears it, stage 2 records the overlap rows its
                           // windows needed (df_rows_needed; or nullptr)
+    // bottom form: the bottom b per cell (pairs), and wb1 - wl1, the weight of
+    // m_b - m_l = (wb1 - wl1) dm1 in stage 2
+    const float2* bathy;
+    dfl wmd;
     // constants of the stage as pairs (tau = gamma dt): tau, lambda tau^2,
     // lambda tau, tau/(2 dx), lambda tau/(2 dx), tau^2/dx^2, lambda tau^2/dx^2,
     // g, lambda, lambda/3, 1/3, and the stage-2 weights c/gamma, (1-gamma)/gamma
@@ -242,12 +259,24 @@ struct DfParams {
 // (HSGN_MIXED | HSGN_DOUBLE_FLOAT): fluxes, starred increments and coefficients
 // in single precision, rows, depth solve, back-substitution and the
 // accumulation of the state in pairs.
-template <int T, int M, int HW, int BC, int STAGE, bool F32 = false>
+// WB selects the well-balanced bottom form (reading R7 of the oracle): the
+// (h eta) equation's bottom source -(3/2) tau q_l b_x in m^dag, and in place of
+// the delta term the face forces
+//   Psi_f = Phi_f + beta_f (h_b jump) = g hbar_f (h_l + b jump) + (pi jump)
+//           + (3/2) p~_f (b jump) - beta_f (h_l - h_b jump),
+// p~ = (lambda/3)(1 - eta/h), pi = eta p~ + lambda alpha (m^dag b_1 - m_l)
+// (p^ of the scheme less g h^2/2, whose jump is g hbar_f (h_l jump)), with
+// m^dag b_1 - m_l = (h^2 (m_b - m_l + dm^) + lambda tau^2 (h^2 - m_l)) / (h^2 + lambda tau^2)
+// and m_b - m_l = (wb1 - wl1) dm1 taken from the stage-1 increment; the
+// momentum then takes q = q^dag - tau/(2dx) (F_{i+1/2} + F_{i-1/2}) with
+// F_f = Psi_f + beta_f (dh jump).
+template <int T, int M, int HW, int BC, int STAGE, bool F32 = false, bool WB = false>
 __global__ void __launch_bounds__(T, 2) k_df_stage(const DfParams p) {
     static_assert(STAGE == 1 || STAGE == 2, "two stages");
+    static_assert(!(F32 && WB), "the bottom form computes every phase in pairs");
     using Gm = DfGeom<T, M, HW>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    auto& sm = *reinterpret_cast<DfShared<T, M, HW>*>(smem_raw);
+    auto& sm = *reinterpret_cast<DfShared<T, M, HW, WB>*>(smem_raw);
     constexpr bool two = STAGE == 2;
     const int tid = threadIdx.x;
     const int64_t n = p.n;
@@ -328,6 +357,10 @@ __global__ void __launch_bounds__(T, 2) k_df_stage(const DfParams p) {
                         L[v]->set(j, u);
                         B[v]->set(j, u);
                     }
+                }
+                if constexpr (WB) {
+                    const float2 b = __ldg(p.bathy + gi);
+                    sm.wb.bb.set(j, dfl(b.x, b.y));
                 }
             }
         }
@@ -435,7 +468,11 @@ __global__ void __launch_bounds__(T, 2) k_df_stage(const DfParams p) {
     //           a^2 = c^2 - lambda eta alpha, beta_1 = 1 + lambda tau^2/h^2,
     //           beta_2 = 2 lambda tau^2/(beta_1^2 h^3), beta = a^2 + lambda alpha beta_2 m^dag,
     //           delta = alpha/beta_1
-    dfl dq_[4], dm_[4], dr_[4], be_[4], de_[4];
+    //         Bottom form: m^dag also takes -(3/2) tau q_l b_x, and per cell
+    //           p~ = (lambda/3) P_l/h^2, P_l = h^2 - m_l (h = h_l),
+    //           pi = eta p~ + lambda alpha (h^2 (m_b - m_l + dm^) + lambda tau^2 P_l)/(h^2 + lambda tau^2)
+    //         take the place of delta
+    dfl dq_[4], dm_[4], dr_[4], be_[4], de_[4], pt_[WB ? 4 : 1];
     float kloc = 0.f, kmin = 3.0e38f;
     {
         const R c_fq = as_R(kc.fq, R()), c_tau = as_R(kc.tau, R()), c_lt2 = as_R(kc.lt2, R());
@@ -457,12 +494,37 @@ __global__ void __launch_bounds__(T, 2) k_df_stage(const DfParams p) {
         ld4(sm.mb, j0 + 4, MB + 4);
         ld4(sm.rb, j0, RB);
         ld4(sm.rb, j0 + 4, RB + 4);
+        // bottom form: q_l and b of the cells, and m_b - m_l = (wb1 - wl1) dm1
+        // from the stage-1 increments (zero in stage 1)
+        dfl QL[WB ? 8 : 1], BB[WB ? 8 : 1], MBL[WB ? 4 : 1];
+        if constexpr (WB) {
+            ld4(sm.ql, j0, QL);
+            ld4(sm.ql, j0 + 4, QL + 4);
+            ld4(sm.wb.bb, j0, BB);
+            ld4(sm.wb.bb, j0 + 4, BB + 4);
+            const bool inner = inner_window(wl, W, n);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                MBL[k] = dfl(0.f);
+                if (two && j0 + k < W + 2) {
+                    // per-cell index j is window cell j - 1, global cell wl + j - 1
+                    const int64_t gi = inner ? wl + j0 + k - 1 : cell_at<BC>(wl + j0 + k - 1, n);
+                    const float2 d = __ldg(p.D1[2] + gi);
+                    MBL[k] = p.wmd * dfl(d.x, d.y);
+                }
+            }
+        }
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
             dq_[k] = dm_[k] = dr_[k] = be_[k] = de_[k] = dfl(0.f);
+            if constexpr (WB) pt_[k] = dfl(0.f);
             if (j0 + k < W + 2) {
                 const R dr = -(c_fq * sub_acc(FR[k + 1], FR[k]));
-                const R dm = fma_u(c_tau, add_u(RB[k + 2], dr), -(c_fq * sub_acc(FM[k + 1], FM[k])));
+                R dm = fma_u(c_tau, add_u(RB[k + 2], dr), -(c_fq * sub_acc(FM[k + 1], FM[k])));
+                // bottom source of the (h eta) equation, -(3/2) tau q_l (b_{c+1} - b_{c-1})/(2 dx)
+                // (Sec. 2.3, eq. (hSGNb_eq))
+                if constexpr (WB)
+                    dm = sub_u(dm, mul_f(c_fq * (QL[k + 2] * sub_acc(BB[k + 3], BB[k + 1])), 1.5f));
                 const R dq = -(c_fq * sub_acc(FQ[k + 1], FQ[k]));
                 const R ms = add_u(add_u(MB[k + 2], dm), c_lt2);
                 const R h = HL[k + 2];
@@ -483,7 +545,15 @@ __global__ void __launch_bounds__(T, 2) k_df_stage(const DfParams p) {
                 dm_[k] = to_dfl(dm);
                 dr_[k] = to_dfl(dr);
                 be_[k] = to_dfl(beta);
-                de_[k] = to_dfl(alpha * ib1);
+                if constexpr (!WB) {
+                    de_[k] = to_dfl(alpha * ib1);
+                } else {
+                    const dfl Pl = sq_minus(h, ML[k + 2]);
+                    const dfl ptil = c_lam3 * (Pl * (ih * ih));
+                    const dfl X = fma_u(h2, add_u(MBL[k], dm), c_lt2 * Pl) * iD;
+                    de_[k] = fma_u(eta, ptil, (c_lam * alpha) * X);  // pi
+                    pt_[k] = ptil;
+                }
                 const float kb = f_mul(kc.Cc.hi, hi_of(beta));
                 kloc = fmaxf(kloc, kb);
                 kmin = fminf(kmin, kb);
@@ -491,17 +561,20 @@ __global__ void __launch_bounds__(T, 2) k_df_stage(const DfParams p) {
         }
     }
     __syncthreads();
-    DArr<Gm::NC>& DQ = sm.hl;
-    DArr<Gm::NC>& DM = sm.ql;
-    DArr<Gm::NC>& DR = sm.ml;
-    DArr<Gm::NC>& BE = sm.rl;
-    DArr<Gm::NC>& DE = sm.fq;
-    DArr<Gm::NC>& DH = sm.fm;
+    DArr<Gm::NC>& DQ = WB ? sm.ql : sm.hl;
+    DArr<Gm::NC>& DM = WB ? sm.ml : sm.ql;
+    DArr<Gm::NC>& DR = WB ? sm.rl : sm.ml;
+    DArr<Gm::NC>& BE = WB ? sm.fq : sm.rl;
+    DArr<Gm::NC>& DE = WB ? sm.fm : sm.fq;  // delta, or pi of the bottom form
+    DArr<Gm::NC>& PT = sm.fr;               // p~ of the bottom form
+    DArr<Gm::NC>& DH = WB ? sm.fr : sm.fm;  // (after the solve)
+    DArr<Gm::NC>& PSI = sm.fm;              // face forces of the bottom form (after the solve)
     DQ.set4(j0, dq_);
     DM.set4(j0, dm_);
     DR.set4(j0, dr_);
     BE.set4(j0, be_);
     DE.set4(j0, de_);
+    if constexpr (WB) PT.set4(j0, pt_);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         kloc = fmaxf(kloc, __shfl_xor_sync(0xffffffffu, kloc, o));
@@ -540,11 +613,13 @@ __global__ void __launch_bounds__(T, 2) k_df_stage(const DfParams p) {
         if (tid == 0 && win.lend) {
             DQ.set(0, DQ.get(1)); DM.set(0, DM.get(1)); DR.set(0, DR.get(1));
             BE.set(0, BE.get(1)); DE.set(0, DE.get(1));
+            if constexpr (WB) PT.set(0, PT.get(1));
         }
         if (tid == 0 && win.rend) {
             const int a = W + 1, c = W;
             DQ.set(a, DQ.get(c)); DM.set(a, DM.get(c)); DR.set(a, DR.get(c));
             BE.set(a, BE.get(c)); DE.set(a, DE.get(c));
+            if constexpr (WB) PT.set(a, PT.get(c));
         }
         __syncthreads();
     }
@@ -556,8 +631,57 @@ __global__ void __launch_bounds__(T, 2) k_df_stage(const DfParams p) {
     //             (zero across a transmissive domain end: Neumann rows);
     //           Phi_f = lambda tau^2/dx^2 delta_f (m^dag_f - m^dag_{f-1}) + K_f (h_b,f - h_b,f-1);
     //           d_i - (A h_b)_i = -tau/(2 dx) (q^dag_{i+1} - q^dag_{i-1}) + Phi_{i+1} - Phi_i.
-    dfl KF[5], rd[4];
-    {
+    //         Bottom form: Phi_f = tau^2/dx^2 Psi_f with the face forces Psi_f above.
+    dfl KF[5], rd[4], PSv[WB ? 4 : 1];
+    if constexpr (WB) {
+        dfl Phi[5];
+        {
+            dfl B8[8], E8[8], H8[8], HL8[8], BB8[8], PT8[8];
+            BE.get4(j0, B8);
+            BE.get4(j0 + 4, B8 + 4);
+            DE.get4(j0, E8);
+            DE.get4(j0 + 4, E8 + 4);
+            sm.hb.get4(j0, H8);
+            sm.hb.get4(j0 + 4, H8 + 4);
+            sm.hl.get4(j0, HL8);
+            sm.hl.get4(j0 + 4, HL8 + 4);
+            sm.wb.bb.get4(j0, BB8);
+            sm.wb.bb.get4(j0 + 4, BB8 + 4);
+            PT.get4(j0, PT8);
+            PT.get4(j0 + 4, PT8 + 4);
+#pragma unroll
+            for (int e = 0; e < 5; ++e) {
+                const int f = j0 + e;  // rows f - 1 | f: per-cell index f, f + 1; state f + 2, f + 3
+                const dfl bf = scale(add_u(B8[e], B8[e + 1]), 0.5f);
+                dfl kf = kc.Cc * bf;
+                const dfl dhl = sub_acc(HL8[e + 3], HL8[e + 2]);
+                const dfl db = sub_acc(BB8[e + 3], BB8[e + 2]);
+                const dfl hbar = scale(add_u(HL8[e + 2], HL8[e + 3]), 0.5f);
+                const dfl ptf = scale(add_u(PT8[e], PT8[e + 1]), 0.5f);
+                // g hbar_f (h_l + b jump) + (pi jump) + (3/2) p~_f (b jump) - beta_f (h_l - h_b jump)
+                dfl psi = add_u(add_u(p.g * (hbar * add_u(dhl, db)), sub_acc(E8[e + 1], E8[e])),
+                                sub_u(mul_f(ptf * db, 1.5f),
+                                      bf * sub_u(dhl, sub_acc(H8[e + 3], H8[e + 2]))));
+                if (BC == BC_TRANSMISSIVE && ((f == 0 && win.lend) || (f == W && win.rend))) {
+                    kf = dfl(0.f);
+                    psi = dfl(0.f);
+                }
+                KF[e] = kf;
+                Phi[e] = kc.Cc * psi;
+                if (e < 4) PSv[e] = psi;
+            }
+        }
+        dfl Q8[8], QU[8];
+        DQ.get4(j0, Q8);
+        DQ.get4(j0 + 4, Q8 + 4);
+        sm.qb.get4(j0, QU);
+        sm.qb.get4(j0 + 4, QU + 4);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const dfl dqc = add_u(sub_acc(QU[k + 4], QU[k + 2]), sub_acc(Q8[k + 2], Q8[k]));
+            rd[k] = sub_u(sub_acc(Phi[k + 1], Phi[k]), kc.fq * dqc);
+        }
+    } else {
         dfl Phi[5];
         {
             dfl B8[8], E8[8];
@@ -619,6 +743,9 @@ __global__ void __launch_bounds__(T, 2) k_df_stage(const DfParams p) {
         for (int k = 0; k < M; ++k)
             if (!(j0 + k < W)) y[k] = dfl(0.f);
         DH.set4(j0 + 4, y);
+        // the face forces of the bottom form for the back-substitution (their
+        // array held pi, last read before the solve's first barrier)
+        if constexpr (WB) PSI.set4(j0, PSv);
     }
     __syncthreads();
     if (BC == BC_TRANSMISSIVE && (win.lend || win.rend)) {  // (uniform over the CTA)
@@ -644,10 +771,21 @@ __global__ void __launch_bounds__(T, 2) k_df_stage(const DfParams p) {
         const dfl dhc = add_u(sub_acc(sm.hb.get(r + 4), sm.hb.get(r + 2)),
                               sub_acc(DH.get(r + 5), DH.get(r + 3)));
         const dfl dmv = DM.get(r + 1);
-        const dfl dmc = add_u(sub_acc(sm.mb.get(r + 4), sm.mb.get(r + 2)),
-                              sub_acc(DM.get(r + 2), DM.get(r)));
-        const dfl dQ = sub_u(DQ.get(r + 1),
-                             add_u(kc.fq * (BE.get(r + 1) * dhc), kc.lfq * (DE.get(r + 1) * dmc)));
+        dfl dQ;
+        if constexpr (!WB) {
+            const dfl dmc = add_u(sub_acc(sm.mb.get(r + 4), sm.mb.get(r + 2)),
+                                  sub_acc(DM.get(r + 2), DM.get(r)));
+            dQ = sub_u(DQ.get(r + 1),
+                       add_u(kc.fq * (BE.get(r + 1) * dhc), kc.lfq * (DE.get(r + 1) * dmc)));
+        } else {
+            // q = q^dag - tau/(2dx) (F_{r+1/2} + F_{r-1/2}), F_f = Psi_f + beta_f (dh jump)
+            (void)dhc;
+            const dfl bp = scale(add_u(BE.get(r + 1), BE.get(r + 2)), 0.5f);
+            const dfl bm = scale(add_u(BE.get(r), BE.get(r + 1)), 0.5f);
+            const dfl Fp = fma_u(bp, sub_acc(DH.get(r + 5), dh), PSI.get(r + 1));
+            const dfl Fm = fma_u(bm, sub_acc(dh, DH.get(r + 3)), PSI.get(r));
+            dQ = sub_u(DQ.get(r + 1), kc.fq * add_u(Fp, Fm));
+        }
         const dfl P = add_u(sq_minus(hb, mb), dh * add_u(scale(hb, 2.f), dh));
         const dfl E = sub_u(P, dmv);
         // (renormalised where it is written as the new state)

@@ -574,33 +574,38 @@ cudaError_t launch_stage_fused(hsgn_s* H, int stage, double tau, cudaStream_t st
 }
 
 // One launch of the double-float stage kernel specialised for p.stage.
-template <int BC, bool F32>
+template <int BC, bool F32, bool WB>
 void launch_df(unsigned P, const DfParams& p, cudaStream_t st) {
-    const size_t smem = sizeof(DfShared<DT, FM, DHW>);
+    const size_t smem = sizeof(DfShared<DT, FM, DHW, WB>);
     if (p.stage == 2)
-        k_df_stage<DT, FM, DHW, BC, 2, F32><<<P, DT, smem, st>>>(p);
+        k_df_stage<DT, FM, DHW, BC, 2, F32, WB><<<P, DT, smem, st>>>(p);
     else
-        k_df_stage<DT, FM, DHW, BC, 1, F32><<<P, DT, smem, st>>>(p);
+        k_df_stage<DT, FM, DHW, BC, 1, F32, WB><<<P, DT, smem, st>>>(p);
 }
 
-// the kernel of the handle's boundary condition and precision split
+// the kernel of the handle's boundary condition, precision split and bottom form
 void launch_df(const hsgn_s* H, unsigned P, const DfParams& p, cudaStream_t st) {
     if (H->bc == BC_PERIODIC) {
-        if (H->df_f32) launch_df<BC_PERIODIC, true>(P, p, st);
-        else launch_df<BC_PERIODIC, false>(P, p, st);
+        if (H->wb) launch_df<BC_PERIODIC, false, true>(P, p, st);
+        else if (H->df_f32) launch_df<BC_PERIODIC, true, false>(P, p, st);
+        else launch_df<BC_PERIODIC, false, false>(P, p, st);
     } else {
-        if (H->df_f32) launch_df<BC_TRANSMISSIVE, true>(P, p, st);
-        else launch_df<BC_TRANSMISSIVE, false>(P, p, st);
+        if (H->wb) launch_df<BC_TRANSMISSIVE, false, true>(P, p, st);
+        else if (H->df_f32) launch_df<BC_TRANSMISSIVE, true, false>(P, p, st);
+        else launch_df<BC_TRANSMISSIVE, false, false>(P, p, st);
     }
 }
 
 template <int BC>
 cudaError_t set_smem_df() {
     const size_t smem = sizeof(DfShared<DT, FM, DHW>);
+    const size_t smem_wb = sizeof(DfShared<DT, FM, DHW, true>);
     cudaError_t e = set_smem(k_df_stage<DT, FM, DHW, BC, 1, false>, smem);
     if (e == cudaSuccess) e = set_smem(k_df_stage<DT, FM, DHW, BC, 2, false>, smem);
     if (e == cudaSuccess) e = set_smem(k_df_stage<DT, FM, DHW, BC, 1, true>, smem);
     if (e == cudaSuccess) e = set_smem(k_df_stage<DT, FM, DHW, BC, 2, true>, smem);
+    if (e == cudaSuccess) e = set_smem(k_df_stage<DT, FM, DHW, BC, 1, false, true>, smem_wb);
+    if (e == cudaSuccess) e = set_smem(k_df_stage<DT, FM, DHW, BC, 2, false, true>, smem_wb);
     return e;
 }
 
@@ -636,6 +641,8 @@ DfParams df_params(const hsgn_s* H, int stage, double tau, double wl1, double wb
     p.third = dfl_of(1.0 / 3.0);
     p.wl1 = dfl_of(wl1);
     p.wb1 = dfl_of(wb1);
+    p.bathy = H->bathy_df;
+    p.wmd = dfl_of(wb1 - wl1);
     p.adaptive = 0;
     p.cfl = p.mcfl = 0.0;
     p.dx = dx;
@@ -984,9 +991,10 @@ int hsgn_create(const hsgn_grid_t* grid, double g, double lambda, const double* 
                            HSGN_DOUBLE_FLOAT | HSGN_SCHEME_MASK))
         return HSGN_ERR_UNIMPLEMENTED;
     // the double-float form (alone, or with HSGN_MIXED for the FP32-flux split):
-    // the paper's scheme, flat bottom
-    if ((flags & HSGN_DOUBLE_FLOAT) &&
-        (flags & (HSGN_EXACT_SOLVE | HSGN_WELL_BALANCED | HSGN_SCHEME_MASK)))
+    // the paper's scheme; the bottom form in pairs throughout (not with the split)
+    if ((flags & HSGN_DOUBLE_FLOAT) && (flags & (HSGN_EXACT_SOLVE | HSGN_SCHEME_MASK)))
+        return HSGN_ERR_UNIMPLEMENTED;
+    if ((flags & HSGN_DOUBLE_FLOAT) && (flags & HSGN_WELL_BALANCED) && (flags & HSGN_MIXED))
         return HSGN_ERR_UNIMPLEMENTED;
     const int32_t scheme = flags & HSGN_SCHEME_MASK;
     if (scheme > HSGN_SCHEME_EX_EULER) return HSGN_ERR_INVALID_ARG;
@@ -1069,6 +1077,7 @@ int hsgn_create(const hsgn_grid_t* grid, double g, double lambda, const double* 
     if (H->dfloat) {
         for (int k = 0; k < 4; ++k) H->V[k] = reinterpret_cast<double*>(take(vec));
         for (int k = 0; k < 4; ++k) H->D1[k] = reinterpret_cast<float2*>(take(vec));
+        if (H->wb) H->bathy_df = reinterpret_cast<float2*>(take(vec));
     } else if (H->windowed) {
         for (int k = 0; k < 4; ++k) H->V[k] = reinterpret_cast<double*>(take(vec));
         H->G1 = reinterpret_cast<float*>(take(fvec));
@@ -1119,9 +1128,12 @@ int hsgn_create(const hsgn_grid_t* grid, double g, double lambda, const double* 
         if (e == cudaSuccess)
             e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, H->device);
         if (e == cudaSuccess)
-            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-                &per_sm, k_df_stage<DT, FM, DHW, BC_PERIODIC, 2, false>, DT,
-                sizeof(DfShared<DT, FM, DHW>));
+            e = H->wb ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                            &per_sm, k_df_stage<DT, FM, DHW, BC_PERIODIC, 2, false, true>, DT,
+                            sizeof(DfShared<DT, FM, DHW, true>))
+                      : cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                            &per_sm, k_df_stage<DT, FM, DHW, BC_PERIODIC, 2, false>, DT,
+                            sizeof(DfShared<DT, FM, DHW>));
         const int64_t slots = (int64_t)(sms > 0 ? sms : 1) * (per_sm > 0 ? per_sm : 1);
         H->tileSlots = (int32_t)slots;
         set_df_overlap(H, DHW_START);
@@ -1704,7 +1716,8 @@ int hsgn_adjoint(hsgn_handle_t H, double dt, int64_t n_steps, int64_t n_gauges,
     if (!H || !(dt > 0.0) || !std::isfinite(dt) || n_steps < 1 || n_gauges < 0 || !misfit ||
         checkpoint_every < 1 || (n_gauges > 0 && (!gauge_cells || !gauge_data)))
         return HSGN_ERR_INVALID_ARG;
-    if (H->batched || H->mixed || !H->wb || H->scheme != HSGN_SCHEME_PRINTED || local_speed(H))
+    if (H->batched || H->mixed || H->dfloat || !H->wb || H->scheme != HSGN_SCHEME_PRINTED ||
+        local_speed(H))
         return HSGN_ERR_UNIMPLEMENTED;
     const int64_t n = H->n;
     for (int64_t k = 0; k < n_gauges; ++k)

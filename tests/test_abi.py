@@ -69,6 +69,10 @@ def test_create_rejects_bad_arguments_before_touching_the_device(lib):
     assert lib.hsgn_create(ctypes.byref(g), 9.81, 1.0, None, 0x300 | 0x1, ctypes.byref(h)) == 6
     assert lib.hsgn_create(ctypes.byref(g), 9.81, 1.0, None, 0x100 | 0x2, ctypes.byref(h)) == 6
     assert lib.hsgn_create(ctypes.byref(g), 9.81, 1.0, None, 0x500, ctypes.byref(h)) == 1
+    # the double-float form: not with the exact solve, nor with both the FP32-flux
+    # split and the bottom form
+    assert lib.hsgn_create(ctypes.byref(g), 9.81, 1.0, None, 0x8 | 0x4, ctypes.byref(h)) == 6
+    assert lib.hsgn_create(ctypes.byref(g), 9.81, 1.0, None, 0x8 | 0x2 | 0x1, ctypes.byref(h)) == 6
     assert not h.value
     lib.hsgn_destroy(None)
 

@@ -42,6 +42,10 @@ def rel_l2(x, ref):
     return float(np.linalg.norm(x - ref) / max(np.linalg.norm(ref), 1e-300))
 
 
+# the forms held to the FP64 bar: FP64 arithmetic and double-float pairs
+FORMS = [pytest.param(0x0, id="fp64"), pytest.param(0x8, id="dfloat")]
+
+
 def wb_solver(n, dx, bc, lam, b, flags=0):
     return S().Solver(n, 0.0, n * dx, bc, lam=lam, flags=flags | S().FLAG_WELL_BALANCED,
                       bathymetry=b)
@@ -55,8 +59,8 @@ def hw_scale(U, lam, dt):
     return np.abs(U[3]) + lam * tau * (1.0 + np.abs(U[2]) / (U[0] * U[0]))
 
 
-def gpu_run(n, dx, bc, lam, b, U, dt, steps, use_graph=True):
-    with wb_solver(n, dx, bc, lam, b) as s:
+def gpu_run(n, dx, bc, lam, b, U, dt, steps, use_graph=True, form=0):
+    with wb_solver(n, dx, bc, lam, b, form) as s:
         s.set_state(*(dev(u) for u in U))
         if use_graph:
             s.run(dt, steps)
@@ -67,16 +71,17 @@ def gpu_run(n, dx, bc, lam, b, U, dt, steps, use_graph=True):
         return [t.cpu().numpy() for t in s.get_state()]
 
 
+@pytest.mark.parametrize("form", FORMS)
 @pytest.mark.parametrize("bc", [0, 1])
 @pytest.mark.parametrize("n", [3, 4, 7, 64, 511, 512, 513, 1000, 5000, 70001])
-def test_wb_stage_matches_oracle(n, bc):
+def test_wb_stage_matches_oracle(n, bc, form):
     dx, lam, tau, speed = 0.1, 300.0, 0.01, 0.37
     x, _ = inputs.cell_centres(n, 0.0, n * dx)
     b = inputs.gaussian_bathymetry(70 + n, x, amp_max=0.1)
     Ub = inputs.random_state(1000 + n, n, dx)
     Ul = inputs.random_state(2000 + n, n, dx, h_var=0.1)
     for local in (0, 1):
-        flags = S().FLAG_RUSANOV_LOCAL if local else 0
+        flags = (S().FLAG_RUSANOV_LOCAL if local else 0) | form
         with wb_solver(n, dx, bc, lam, b, flags) as s:
             out = s.stage([dev(u) for u in Ub], [dev(u) for u in Ul], tau, speed)
             got = [t.cpu().numpy() for t in out]
@@ -88,24 +93,26 @@ def test_wb_stage_matches_oracle(n, bc):
             assert rel_l2(got[k], ref[k]) < 1e-12, (k, local, rel_l2(got[k], ref[k]))
 
 
-def test_wb_flat_bottom_pointer_equals_null_bottom():
+@pytest.mark.parametrize("form", FORMS)
+def test_wb_flat_bottom_pointer_equals_null_bottom(form):
     # a zero bottom array and no bottom at all give bitwise the same steps
     n, dx, lam = 1537, 0.1, 500.0
     U = inputs.random_state(77, n, dx)
-    a = gpu_run(n, dx, 1, lam, np.zeros(n), U, 0.01, 3)
-    b = gpu_run(n, dx, 1, lam, None, U, 0.01, 3)
+    a = gpu_run(n, dx, 1, lam, np.zeros(n), U, 0.01, 3, form=form)
+    b = gpu_run(n, dx, 1, lam, None, U, 0.01, 3, form=form)
     for k in range(4):
         np.testing.assert_array_equal(a[k], b[k])
 
 
+@pytest.mark.parametrize("form", FORMS)
 @pytest.mark.parametrize("bc", [0, 1])
 @pytest.mark.parametrize("n", [5, 100, 1000, 1537])
-def test_wb_one_step_matches_oracle(n, bc):
+def test_wb_one_step_matches_oracle(n, bc, form):
     dx, lam = 0.1, 500.0
     x, _, b, U = inputs.gauss_bottom_wave(300 + n, n, dx)
     p = oracle.Params(n, dx, bc, lam=lam, form=1, bathy=b)
     dt, _, _ = oracle.suggest_dt(p, U, 2.0, 0.5)
-    got = gpu_run(n, dx, bc, lam, b, U, dt, 1)
+    got = gpu_run(n, dx, bc, lam, b, U, dt, 1, form=form)
     ref = oracle.step(p, U, dt)
     # q is compared against its own scale plus the size of the depth-driven
     # forces (q itself is small where the wave has not arrived); h w against
@@ -116,9 +123,10 @@ def test_wb_one_step_matches_oracle(n, bc):
     assert np.linalg.norm(got[3] - ref[3]) < 1e-12 * np.linalg.norm(hw_scale(U, lam, dt))
 
 
+@pytest.mark.parametrize("form", FORMS)
 @pytest.mark.parametrize("bc", [0, 1])
 @pytest.mark.parametrize("n", [400, 5000])
-def test_wb_lake_at_rest_on_gpu(n, bc):
+def test_wb_lake_at_rest_on_gpu(n, bc, form):
     # u = 0, eta = h, w = 0, h + b = const: the GPU keeps the state at rest to
     # rounding over 40 steps, like the oracle (Sec. 2.3 with b_t = 0)
     x, dx = inputs.cell_centres(n, 0.0, 0.2 * n)
@@ -126,21 +134,22 @@ def test_wb_lake_at_rest_on_gpu(n, bc):
     b = b - b.min()
     h = 1.0 - b
     U = (h, 0 * h, h * h, 0 * h)
-    got = gpu_run(n, dx, bc, 500.0, b, U, 0.05, 40)
+    got = gpu_run(n, dx, bc, 500.0, b, U, 0.05, 40, form=form)
     assert np.max(np.abs(got[0] - h)) < 1e-12
     assert np.max(np.abs(got[1])) < 1e-12
     assert np.max(np.abs(got[2] - h * h)) < 1e-12
     assert np.max(np.abs(got[3])) < 1e-11
 
 
-def test_wb_gauss_bottom_trajectory():
+@pytest.mark.parametrize("form", FORMS)
+def test_wb_gauss_bottom_trajectory(form):
     # the adjoint workload's forward problem: N = 4096, dx = 0.1, periodic,
     # lambda = 100, wave a = 0.1 over 8 Gaussian bumps; 200 steps at CFL 2
     n, lam, steps = 4096, 100.0, 200
     x, dx, b, U = inputs.gauss_bottom_wave(20251011, n)
     p = oracle.Params(n, dx, 0, lam=lam, form=1, bathy=b)
     dt, _, _ = oracle.suggest_dt(p, U, 2.0, 0.5)
-    got = gpu_run(n, dx, 0, lam, b, U, dt, steps)
+    got = gpu_run(n, dx, 0, lam, b, U, dt, steps, form=form)
     ref = oracle.run(p, U, dt, steps)
     for k in range(3):
         assert rel_l2(got[k], ref[k]) < 1e-9, (k, rel_l2(got[k], ref[k]))
@@ -148,23 +157,25 @@ def test_wb_gauss_bottom_trajectory():
     assert abs(math.fsum(got[0]) - math.fsum(U[0])) <= 1e-13 * math.fsum(U[0])
 
 
-def test_wb_graph_replay_equals_step_loop():
+@pytest.mark.parametrize("form", FORMS)
+def test_wb_graph_replay_equals_step_loop(form):
     n, lam = 3000, 1000.0
     x, dx, b, U = inputs.gauss_bottom_wave(8, n)
-    a = gpu_run(n, dx, 0, lam, b, U, 0.01, 7, use_graph=True)
-    c = gpu_run(n, dx, 0, lam, b, U, 0.01, 7, use_graph=False)
+    a = gpu_run(n, dx, 0, lam, b, U, 0.01, 7, use_graph=True, form=form)
+    c = gpu_run(n, dx, 0, lam, b, U, 0.01, 7, use_graph=False, form=form)
     for k in range(4):
         np.testing.assert_array_equal(a[k], c[k])
 
 
-def test_wb_shelf_2_24_one_step():
+@pytest.mark.parametrize("form", FORMS)
+def test_wb_shelf_2_24_one_step(form):
     # the large workload: N = 2^24, dx = 0.005, transmissive, lambda = 1000,
     # 1:20 shelf, wave a = 0.1; one step at CFL_IMEX 4, every cell compared
     n, lam = 1 << 24, 1000.0
     x, dx, b, U = inputs.shelf_wave(n)
     p = oracle.Params(n, dx, 1, lam=lam, form=1, bathy=b)
     dt, _, _ = oracle.suggest_dt(p, U, 4.0, 0.5)
-    got = gpu_run(n, dx, 1, lam, b, U, dt, 1)
+    got = gpu_run(n, dx, 1, lam, b, U, dt, 1, form=form)
     ref = oracle.step(p, U, dt)
     A = oracle.assemble(p, U, U, (1.0 - 1.0 / math.sqrt(2.0)) * dt)
     tau = (1.0 - 1.0 / math.sqrt(2.0)) * dt

@@ -399,7 +399,9 @@ def test_dfloat_fallback_tiles_match_oracle(n, bc):
 
 
 def test_dfloat_rejects_other_forms():
-    for extra in (0x2, 0x4, 0x100, 0x5):
+    # not with the exact solve, the comparison schemes, or the FP32-flux split
+    # together with the bottom form (0x1 | 0x2)
+    for extra in (0x4, 0x100, 0x5, 0x3):
         with pytest.raises(S().HsgnError) as e:
             S().Solver(16, 0.0, 1.6, 0, lam=1.0, flags=S().FLAG_DOUBLE_FLOAT | extra)
         assert e.value.code == 6
@@ -407,10 +409,11 @@ def test_dfloat_rejects_other_forms():
 
 def test_adjoint_needs_the_well_balanced_form():
     # the adjoint exists for the FP64 bottom form only
-    with S().Solver(16, 0.0, 1.6, 0, lam=1.0) as s:
-        with pytest.raises(S().HsgnError) as e:
-            s.adjoint(0.01, 2, [3], np.zeros(2))
-        assert e.value.code == 6
+    for flags in (0x0, S().FLAG_WELL_BALANCED | S().FLAG_DOUBLE_FLOAT):
+        with S().Solver(16, 0.0, 1.6, 0, lam=1.0, flags=flags) as s:
+            with pytest.raises(S().HsgnError) as e:
+                s.adjoint(0.01, 2, [3], np.zeros(2))
+            assert e.value.code == 6
 
 
 # --------------------------------------------------------------------------
