@@ -617,10 +617,10 @@ def time_adjoint(S, torch, stream):
 def time_shelf(S, torch, stream, hbm_peak, log2n=24, steps=50, warmup=3):
     """The large workload: N = 2^24, dx = 0.005, transmissive, lambda = 1000, a
     wave a = 0.1 running towards a 1:20 shelf (depth 1 -> 0.5), bottom form,
-    dt = min(4 dx/nu, 0.5 dx/u_max) at t = 0. FP64 and mixed precision
-    advance the same initial state by `steps` steps (each state is 537 MB,
-    far above L2); the mixed result is compared with the FP64 one, which
-    matches the FP64 oracle to 1e-12 per step."""
+    dt = min(4 dx/nu, 0.5 dx/u_max) at t = 0. FP64, double-float and mixed
+    precision advance the same initial state by `steps` steps (each state is
+    537 MB, far above L2); the double-float and mixed results are compared
+    with the FP64 one, which matches the FP64 oracle to 1e-12 per step."""
     import numpy as np
     from paper_2510_07539_gb300 import inputs as inp
     n, lam = 1 << log2n, 1000.0
@@ -629,6 +629,7 @@ def time_shelf(S, torch, stream, hbm_peak, log2n=24, steps=50, warmup=3):
     del U
     out, dt = {}, None
     for name, flags in (("fp64", S.FLAG_WELL_BALANCED),
+                        ("dfloat", S.FLAG_WELL_BALANCED | S.FLAG_DOUBLE_FLOAT),
                         ("mixed", S.FLAG_WELL_BALANCED | S.FLAG_MIXED)):
         with S.Solver(n, 0.0, n * dx, S.BC_TRANSMISSIVE, lam=lam, flags=flags,
                       bathymetry=b) as s:
@@ -650,7 +651,9 @@ def time_shelf(S, torch, stream, hbm_peak, log2n=24, steps=50, warmup=3):
                          "ms_per_step": ms / steps,
                          "state": [t.cpu().numpy() for t in s.get_state()]}
     ref, got = out["fp64"].pop("state"), out["mixed"].pop("state")
+    gdf = out["dfloat"].pop("state")
     rel = [float(np.linalg.norm(got[k] - ref[k]) / np.linalg.norm(ref[k])) for k in range(4)]
+    rel_df = [float(np.linalg.norm(gdf[k] - ref[k]) / np.linalg.norm(ref[k])) for k in range(4)]
     # algorithmic bytes of the bottom form: 88 per cell-stage (the FP64 state
     # traffic of the scheme, 80 B, plus the bottom read once per stage)
     gbs = (BYTES_PER_CELL_STAGE_BOTTOM * 2.0 * n * steps
@@ -663,7 +666,10 @@ def time_shelf(S, torch, stream, hbm_peak, log2n=24, steps=50, warmup=3):
     return {"workload": f"wave a = 0.1 towards a 1:20 shelf, N = 2^{log2n}, dx = {dx:g}, "
                         f"transmissive, lambda = 1000, bottom form, dt = {dt:.6g} "
                         f"(CFL_IMEX 4), {steps} timed steps (of the 5000-step run)",
-            "fp64": out["fp64"], "mixed": out["mixed"],
+            "fp64": out["fp64"], "dfloat": out["dfloat"], "mixed": out["mixed"],
+            "dfloat_over_fp64": out["dfloat"]["value"] / out["fp64"]["value"],
+            "dfloat_vs_fp64_rel_l2_after_steps": {"h": rel_df[0], "q": rel_df[1],
+                                                  "h_eta": rel_df[2], "h_w": rel_df[3]},
             "mixed_over_fp64": out["mixed"]["value"] / out["fp64"]["value"],
             "mixed_vs_fp64_rel_l2_after_steps": {"h": rel[0], "q": rel[1], "h_eta": rel[2],
                                                  "h_w": rel[3]}}
