@@ -70,8 +70,8 @@ FLOPS_PER_CELL_ASSEMBLE = 149.0
 # kernel has changed since (the roofline then reports no achieved flop rate).
 DF_FLOPS_PER_CELL = 1519.5      # stage 1 / 2: 1425 / 1614
 DF_FP32_INST_PER_CELL = 1258.5  # FADD + FMUL + FFMA instructions, stage 1 / 2: 1180 / 1337
-DF_TRAFFIC_PER_CELL = 71.0      # dram__bytes_read + write per cell and launch, stage 1 / 2: 53.2 / 88.7
-DF_FLOPS_SOURCE_SHA = "fb76546db288fdd6"
+DF_TRAFFIC_PER_CELL = 70.9      # dram__bytes_read + write per cell and launch, stage 1 / 2: 53.2 / 88.6
+DF_FLOPS_SOURCE_SHA = "c14a7a8cf4688bbf"
 DF_SOURCES = ("hsgn_dfstage.cuh", "hsgn_dfloat.cuh", "hsgn_fused.cuh", "hsgn_mixed.cuh",
               "hsgn_tridiag.cuh")
 

@@ -494,26 +494,9 @@ __global__ void __launch_bounds__(T, 2) k_df_stage(const DfParams p) {
         ld4(sm.mb, j0 + 4, MB + 4);
         ld4(sm.rb, j0, RB);
         ld4(sm.rb, j0 + 4, RB + 4);
-        // bottom form: q_l and b of the cells, and m_b - m_l = (wb1 - wl1) dm1
-        // from the stage-1 increments (zero in stage 1)
-        dfl QL[WB ? 8 : 1], BB[WB ? 8 : 1], MBL[WB ? 4 : 1];
-        if constexpr (WB) {
-            ld4(sm.ql, j0, QL);
-            ld4(sm.ql, j0 + 4, QL + 4);
-            ld4(sm.wb.bb, j0, BB);
-            ld4(sm.wb.bb, j0 + 4, BB + 4);
-            const bool inner = inner_window(wl, W, n);
-#pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                MBL[k] = dfl(0.f);
-                if (two && j0 + k < W + 2) {
-                    // per-cell index j is window cell j - 1, global cell wl + j - 1
-                    const int64_t gi = inner ? wl + j0 + k - 1 : cell_at<BC>(wl + j0 + k - 1, n);
-                    const float2 d = __ldg(p.D1[2] + gi);
-                    MBL[k] = p.wmd * dfl(d.x, d.y);
-                }
-            }
-        }
+        // bottom form: m_b - m_l = (wb1 - wl1) dm1 from the stage-1 increments
+        // (zero in stage 1), read per cell inside the loop with q_l and b
+        const bool inner = WB && two && inner_window(wl, W, n);
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
             dq_[k] = dm_[k] = dr_[k] = be_[k] = de_[k] = dfl(0.f);
@@ -524,7 +507,10 @@ __global__ void __launch_bounds__(T, 2) k_df_stage(const DfParams p) {
                 // bottom source of the (h eta) equation, -(3/2) tau q_l (b_{c+1} - b_{c-1})/(2 dx)
                 // (Sec. 2.3, eq. (hSGNb_eq))
                 if constexpr (WB)
-                    dm = sub_u(dm, mul_f(c_fq * (QL[k + 2] * sub_acc(BB[k + 3], BB[k + 1])), 1.5f));
+                    dm = sub_u(dm, mul_f(c_fq * (sm.ql.get(j0 + k + 2) *
+                                                 sub_acc(sm.wb.bb.get(j0 + k + 3),
+                                                         sm.wb.bb.get(j0 + k + 1))),
+                                         1.5f));
                 const R dq = -(c_fq * sub_acc(FQ[k + 1], FQ[k]));
                 const R ms = add_u(add_u(MB[k + 2], dm), c_lt2);
                 const R h = HL[k + 2];
@@ -548,9 +534,16 @@ __global__ void __launch_bounds__(T, 2) k_df_stage(const DfParams p) {
                 if constexpr (!WB) {
                     de_[k] = to_dfl(alpha * ib1);
                 } else {
+                    dfl mbl(0.f);
+                    if (two) {
+                        // per-cell index j is window cell j - 1, global cell wl + j - 1
+                        const int64_t gi = inner ? wl + j0 + k - 1 : cell_at<BC>(wl + j0 + k - 1, n);
+                        const float2 d = __ldg(p.D1[2] + gi);
+                        mbl = p.wmd * dfl(d.x, d.y);
+                    }
                     const dfl Pl = sq_minus(h, ML[k + 2]);
                     const dfl ptil = c_lam3 * (Pl * (ih * ih));
-                    const dfl X = fma_u(h2, add_u(MBL[k], dm), c_lt2 * Pl) * iD;
+                    const dfl X = fma_u(h2, add_u(mbl, dm), c_lt2 * Pl) * iD;
                     de_[k] = fma_u(eta, ptil, (c_lam * alpha) * X);  // pi
                     pt_[k] = ptil;
                 }
@@ -636,32 +629,25 @@ __global__ void __launch_bounds__(T, 2) k_df_stage(const DfParams p) {
     if constexpr (WB) {
         dfl Phi[5];
         {
-            dfl B8[8], E8[8], H8[8], HL8[8], BB8[8], PT8[8];
-            BE.get4(j0, B8);
-            BE.get4(j0 + 4, B8 + 4);
-            DE.get4(j0, E8);
-            DE.get4(j0 + 4, E8 + 4);
-            sm.hb.get4(j0, H8);
-            sm.hb.get4(j0 + 4, H8 + 4);
-            sm.hl.get4(j0, HL8);
-            sm.hl.get4(j0 + 4, HL8 + 4);
-            sm.wb.bb.get4(j0, BB8);
-            sm.wb.bb.get4(j0 + 4, BB8 + 4);
-            PT.get4(j0, PT8);
-            PT.get4(j0 + 4, PT8 + 4);
+            // face by face, each face's values read as it goes (left cell:
+            // per-cell index f, state f + 2; right cell: f + 1, f + 3), so that
+            // the six per-cell arrays are not all held in registers at once
+            dfl bL = BE.get(j0), eL = DE.get(j0), pL = PT.get(j0);
+            dfl hlL = sm.hl.get(j0 + 2), hbL = sm.hb.get(j0 + 2), bbL = sm.wb.bb.get(j0 + 2);
 #pragma unroll
             for (int e = 0; e < 5; ++e) {
                 const int f = j0 + e;  // rows f - 1 | f: per-cell index f, f + 1; state f + 2, f + 3
-                const dfl bf = scale(add_u(B8[e], B8[e + 1]), 0.5f);
+                const dfl bR = BE.get(f + 1), eR = DE.get(f + 1), pR = PT.get(f + 1);
+                const dfl hlR = sm.hl.get(f + 3), hbR = sm.hb.get(f + 3), bbR = sm.wb.bb.get(f + 3);
+                const dfl bf = scale(add_u(bL, bR), 0.5f);
                 dfl kf = kc.Cc * bf;
-                const dfl dhl = sub_acc(HL8[e + 3], HL8[e + 2]);
-                const dfl db = sub_acc(BB8[e + 3], BB8[e + 2]);
-                const dfl hbar = scale(add_u(HL8[e + 2], HL8[e + 3]), 0.5f);
-                const dfl ptf = scale(add_u(PT8[e], PT8[e + 1]), 0.5f);
+                const dfl dhl = sub_acc(hlR, hlL);
+                const dfl db = sub_acc(bbR, bbL);
+                const dfl hbar = scale(add_u(hlL, hlR), 0.5f);
+                const dfl ptf = scale(add_u(pL, pR), 0.5f);
                 // g hbar_f (h_l + b jump) + (pi jump) + (3/2) p~_f (b jump) - beta_f (h_l - h_b jump)
-                dfl psi = add_u(add_u(p.g * (hbar * add_u(dhl, db)), sub_acc(E8[e + 1], E8[e])),
-                                sub_u(mul_f(ptf * db, 1.5f),
-                                      bf * sub_u(dhl, sub_acc(H8[e + 3], H8[e + 2]))));
+                dfl psi = add_u(add_u(p.g * (hbar * add_u(dhl, db)), sub_acc(eR, eL)),
+                                sub_u(mul_f(ptf * db, 1.5f), bf * sub_u(dhl, sub_acc(hbR, hbL))));
                 if (BC == BC_TRANSMISSIVE && ((f == 0 && win.lend) || (f == W && win.rend))) {
                     kf = dfl(0.f);
                     psi = dfl(0.f);
@@ -669,6 +655,8 @@ __global__ void __launch_bounds__(T, 2) k_df_stage(const DfParams p) {
                 KF[e] = kf;
                 Phi[e] = kc.Cc * psi;
                 if (e < 4) PSv[e] = psi;
+                bL = bR; eL = eR; pL = pR;
+                hlL = hlR; hbL = hbR; bbL = bbR;
             }
         }
         dfl Q8[8], QU[8];
