@@ -318,9 +318,10 @@ def test_wb_mixed_tiny_grids(n, bc):
 
 
 def test_wb_mixed_shelf_full_length_and_against_fp64():
-    # the large workload over its full 5000 steps in mixed precision (mass
-    # kept, no device error, finite), and its first 200 steps against the FP64
-    # bottom form, which matches the oracle to 1e-12 per step. A step changes h
+    # the large workload over its full 5000 steps in mixed precision and in
+    # double-float pairs (mass kept, no device error, finite), and its first
+    # 200 steps against the FP64 bottom form, which matches the oracle to
+    # 1e-12 per step. A step changes h
     # by under 1e-3 of itself, rounded in single precision to 2^-24: under 1e-10
     # per step, so 200 steps stay below 2e-8
     n, lam = 1 << 24, 1000.0
@@ -339,3 +340,17 @@ def test_wb_mixed_shelf_full_length_and_against_fp64():
     assert abs(math.fsum(mixed200[0]) - m0) <= 1e-12 * m0
     f64 = gpu_run(n, dx, 1, lam, b, U, dt, 200)
     assert rel_l2(mixed200[0], f64[0]) < 1e-7 and rel_l2(mixed200[2], f64[2]) < 1e-7
+    # the double-float bottom form over the same run: within the FP64 bar of
+    # the FP64 form after 200 steps (1e-9 over a trajectory), and over the
+    # 5000 steps finite, free of device errors and with the mass kept
+    with wb_solver(n, dx, 1, lam, b, S().FLAG_DOUBLE_FLOAT) as s:
+        s.set_state(*(dev(u) for u in U))
+        s.run(dt, 200)
+        df200 = [t.cpu().numpy() for t in s.get_state()]
+        s.run(dt, 4800)
+        dfend = [t.cpu().numpy() for t in s.get_state()]
+    for k in (0, 2):
+        assert rel_l2(df200[k], f64[k]) < 1e-9, (k, rel_l2(df200[k], f64[k]))
+    assert np.linalg.norm(df200[1] - f64[1]) < 1e-9 * (np.linalg.norm(f64[1]) + np.linalg.norm(U[0]))
+    assert all(np.all(np.isfinite(a)) for a in dfend)
+    assert abs(math.fsum(dfend[0]) - m0) <= 1e-12 * m0
