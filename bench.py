@@ -1076,12 +1076,14 @@ def _oracle_dam_break(args):
 
 
 def run_accuracy(args):
-    """The error of both forms at the configurations' full lengths, one JSON
+    """The error of every form at the configurations' full lengths, one JSON
     line: the dam break (2^20 cells, lambda 10 / 100 / 1000, 2000 steps at
-    CFL_IMEX 4) against the FP64 oracle, whose three runs go to a process pool
-    on the host cores (started with spawn, before the first GPU call) while the
-    GPU runs; and the shelf (2^24 cells, 5000 steps) in mixed precision against
-    the FP64 form. Minutes of host and GPU time; not part of the default run."""
+    CFL_IMEX 4) in the FP64, double-float and mixed forms against the FP64
+    oracle, whose three runs go to a process pool on the host cores (started
+    with spawn, before the first GPU call) while the GPU runs; and the shelf
+    (2^24 cells, 5000 steps) in double-float and mixed precision against the
+    FP64 form. Minutes of host and GPU time (run it with --log2n 20: the
+    oracle takes minutes per 2^20-cell run); not part of the default run."""
     import multiprocessing as mp
     import numpy as np
     lams = [float(x) for x in args.lams.split(",")]
@@ -1095,17 +1097,19 @@ def run_accuracy(args):
         Ud = [torch.tensor(u, device="cuda") for u in U]
         gpu = {}
         for lam in lams:
-            for name, flags in (("fp64", S.FLAG_FP64), ("mixed", S.FLAG_MIXED)):
+            for name, flags in (("fp64", S.FLAG_FP64), ("dfloat", S.FLAG_DOUBLE_FLOAT),
+                                ("mixed", S.FLAG_MIXED)):
                 with S.Solver(n, xl, xr, S.BC_TRANSMISSIVE, lam=lam, flags=flags) as s:
                     s.set_state(*Ud)
                     s.run(s.suggest_dt(4.0, 0.5), steps)
                     gpu[(lam, name)] = [v.cpu().numpy() for v in s.get_state()]
-        # the shelf: FP64 against mixed over the configuration's 5000 steps
+        # the shelf: FP64 against double-float and mixed over the configuration's 5000 steps
         sn = 1 << args.shelf_log2n
         x, sdx, b, SU = inp.shelf_wave(sn, dx=0.005 * (1 << 24) / sn)
         SUd = [torch.tensor(u, device="cuda") for u in SU]
         shelf, sdt, sms = {}, None, {}
         for name, flags in (("fp64", S.FLAG_WELL_BALANCED),
+                            ("dfloat", S.FLAG_WELL_BALANCED | S.FLAG_DOUBLE_FLOAT),
                             ("mixed", S.FLAG_WELL_BALANCED | S.FLAG_MIXED)):
             with S.Solver(sn, 0.0, sn * sdx, S.BC_TRANSMISSIVE, lam=1000.0, flags=flags,
                           bathymetry=b) as s:
@@ -1121,23 +1125,25 @@ def run_accuracy(args):
     names = ("h", "q", "heta", "hw")
     dam = []
     for lam, dt, ref, el in refs:
-        for form in ("fp64", "mixed"):
+        for form in ("fp64", "dfloat", "mixed"):
             got = gpu[(lam, form)]
             dam.append({"lambda": lam, "form": form, "oracle_s": el,
                         "rel_l2": {nm: float(np.linalg.norm(got[k] - ref[k]) / np.linalg.norm(ref[k]))
                                    for k, nm in enumerate(names)},
                         "depth_rel_l1": float(np.sum(np.abs(got[0] - ref[0])) /
                                               np.sum(np.abs(ref[0])))})
-    ref, got = shelf["fp64"], shelf["mixed"]
+    ref = shelf["fp64"]
     m0 = float(np.sum(SU[0]))
     line = {"mode": "accuracy",
             "dam_break": {"cells": n, "steps": steps, "vs": "FP64 oracle", "runs": dam},
             "shelf": {"cells": sn, "steps": args.shelf_accuracy_steps, "vs": "FP64 form",
                       "seconds": sms,
-                      "rel_l2": {nm: float(np.linalg.norm(got[k] - ref[k]) / np.linalg.norm(ref[k]))
-                                 for k, nm in enumerate(names)},
+                      "rel_l2": {f: {nm: float(np.linalg.norm(shelf[f][k] - ref[k]) /
+                                               np.linalg.norm(ref[k]))
+                                     for k, nm in enumerate(names)}
+                                 for f in ("dfloat", "mixed")},
                       "mass_drift": {f: abs(float(np.sum(shelf[f][0])) - m0) / m0
-                                     for f in ("fp64", "mixed")}}}
+                                     for f in ("fp64", "dfloat", "mixed")}}}
     print(json.dumps(line), flush=True)
 
 
