@@ -157,6 +157,28 @@ def test_wb_gauss_bottom_trajectory(form):
     assert abs(math.fsum(got[0]) - math.fsum(U[0])) <= 1e-13 * math.fsum(U[0])
 
 
+def test_wb_dfloat_per_step_dt_matches_the_oracle_policy():
+    # the per-step time step (Sec. 5) on the double-float bottom form: every
+    # step takes dt = min(2 dx/nu_max, 0.5 dx/u_max) of the state it starts
+    # from, on the device, over a wave crossing Gaussian bumps; the oracle's
+    # bottom form re-evaluates the same rule before each step
+    n, lam, steps = 4096, 100.0, 25
+    x, dx, b, U = inputs.gauss_bottom_wave(20251011, n)
+    p = oracle.Params(n, dx, 0, lam=lam, form=1, bathy=b)
+    V, t_ref = U, 0.0
+    for _ in range(steps):
+        dt, _, _ = oracle.suggest_dt(p, V, 2.0, 0.5)
+        V = oracle.step(p, V, dt)
+        t_ref += dt
+    with wb_solver(n, dx, 0, lam, b, S().FLAG_DOUBLE_FLOAT) as s:
+        s.set_state(*(dev(u) for u in U))
+        t = s.run_cfl(2.0, 0.5, steps)
+        got = [u.cpu().numpy() for u in s.get_state()]
+    assert abs(t - t_ref) <= 1e-13 * t_ref, (t, t_ref)
+    for k in range(3):
+        assert rel_l2(got[k], V[k]) < 1e-10, (k, rel_l2(got[k], V[k]))
+
+
 @pytest.mark.parametrize("form", FORMS)
 def test_wb_graph_replay_equals_step_loop(form):
     n, lam = 3000, 1000.0
