@@ -229,6 +229,7 @@ struct DfParams {
     // overlap of a tile's window, HWt <= HW of the kernel; a tile whose window
     // misses the decay bound with HWt < HW is redone in pieces with overlap HW
     int32_t HWt;
+    int32_t slots;        // co-resident CTAs of the launch (next-wave L2 prefetch; 0: none)
     unsigned* need_out;   // stage 1 clears it, stage 2 records the overlap rows its
                           // windows needed (df_rows_needed; or nullptr)
     // bottom form: the bottom b per cell (pairs), and wb1 - wl1, the weight of
@@ -361,6 +362,30 @@ __global__ void __launch_bounds__(T, 2) k_df_stage(const DfParams p) {
                 if constexpr (WB) {
                     const float2 b = __ldg(p.bathy + gi);
                     sm.wb.bb.set(j, dfl(b.x, b.y));
+                }
+            }
+        }
+        // L2 prefetch of the window of the tile that the next wave of CTAs
+        // starts on this slot (tile blockIdx.x + slots: CTAs are dispatched in
+        // index order as slots free up), one 128-byte line (16 pairs) per
+        // thread and array over the cells of that window inside [0, n)
+        constexpr int PF = (Gm::R + 6 + 15) / 16;
+        if (piece < 0 && p.slots > 0 && tid < PF) {
+            const int64_t ts = (int64_t)blockIdx.x + p.slots;
+            if (ts < (int64_t)gridDim.x) {
+                const int64_t nt0 = ts * S0;
+                const Window ws = window_at<BC>(nt0, (int)(n - nt0 < S0 ? n - nt0 : S0), n, HW0);
+                const int64_t c0 = ws.wl - 3 < 0 ? 0 : ws.wl - 3;
+                const int64_t c1 = ws.wl + ws.W + 3 > n ? n : ws.wl + ws.W + 3;
+                const int64_t c = c0 + 16 * (int64_t)tid;
+                if (c < c1) {
+#pragma unroll
+                    for (int v = 0; v < 4; ++v) prefetch_l2(p.U[v] + c);
+                    if constexpr (two) {
+#pragma unroll
+                        for (int v = 0; v < 4; ++v) prefetch_l2(p.D1[v] + c);
+                    }
+                    if constexpr (WB) prefetch_l2(p.bathy + c);
                 }
             }
         }

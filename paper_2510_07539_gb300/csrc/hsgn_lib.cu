@@ -626,6 +626,7 @@ DfParams df_params(const hsgn_s* H, int stage, double tau, double wl1, double wb
     p.track_speed = local_speed(H) ? 0 : 1;
     p.S = H->tileS;
     p.HWt = H->dfhw;
+    p.slots = H->tileSlots;
     p.need_out = nullptr;
     const double dx = H->dx, lam = H->lam;
     p.tau = dfl_of(tau);
