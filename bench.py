@@ -68,10 +68,10 @@ FLOPS_PER_CELL_ASSEMBLE = 149.0
 # profiles/ncu_df_stage.md).
 # Valid for the kernel sources whose hash is DF_FLOPS_SOURCE_SHA; None when the
 # kernel has changed since (the roofline then reports no achieved flop rate).
-DF_FLOPS_PER_CELL = 1519.5      # stage 1 / 2: 1425 / 1614
-DF_FP32_INST_PER_CELL = 1258.5  # FADD + FMUL + FFMA instructions, stage 1 / 2: 1180 / 1337
-DF_TRAFFIC_PER_CELL = 70.9      # dram__bytes_read + write per cell and launch, stage 1 / 2: 53.2 / 88.6
-DF_FLOPS_SOURCE_SHA = "c14a7a8cf4688bbf"
+DF_FLOPS_PER_CELL = 1521.0      # stage 1 / 2: 1428 / 1614
+DF_FP32_INST_PER_CELL = 1259.5  # FADD + FMUL + FFMA instructions, stage 1 / 2: 1182 / 1337
+DF_TRAFFIC_PER_CELL = 70.8      # dram__bytes_read + write per cell and launch, stage 1 / 2: 53.1 / 88.5
+DF_FLOPS_SOURCE_SHA = "fb0c0bdae639874a"
 DF_SOURCES = ("hsgn_dfstage.cuh", "hsgn_dfloat.cuh", "hsgn_fused.cuh", "hsgn_mixed.cuh",
               "hsgn_tridiag.cuh")
 
