@@ -71,7 +71,7 @@ FLOPS_PER_CELL_ASSEMBLE = 149.0
 DF_FLOPS_PER_CELL = 1521.0      # stage 1 / 2: 1428 / 1614
 DF_FP32_INST_PER_CELL = 1259.5  # FADD + FMUL + FFMA instructions, stage 1 / 2: 1182 / 1337
 DF_TRAFFIC_PER_CELL = 70.8      # dram__bytes_read + write per cell and launch, stage 1 / 2: 53.1 / 88.5
-DF_FLOPS_SOURCE_SHA = "fb0c0bdae639874a"
+DF_FLOPS_SOURCE_SHA = "ee1f947fd30781ea"
 DF_SOURCES = ("hsgn_dfstage.cuh", "hsgn_dfloat.cuh", "hsgn_fused.cuh", "hsgn_mixed.cuh",
               "hsgn_tridiag.cuh")
 
@@ -148,15 +148,42 @@ def config_dict(n, lams, dts, extra=None):
     return d
 
 
+def code_of(text: str) -> str:
+    """C/C++/CUDA source without its comments, trailing blanks and empty lines
+    (a comment changes no instruction the counters were taken from). String
+    literals are kept as they are."""
+    out, i, n = [], 0, len(text)
+    while i < n:
+        c = text[i]
+        if c == '"' or c == "'":
+            j = i + 1
+            while j < n and text[j] != c:
+                j += 2 if text[j] == "\\" else 1
+            out.append(text[i:j + 1])
+            i = j + 1
+        elif text.startswith("//", i):
+            while i < n and text[i] != "\n":
+                i += 1
+        elif text.startswith("/*", i):
+            j = text.find("*/", i + 2)
+            i = n if j < 0 else j + 2
+        else:
+            out.append(c)
+            i += 1
+    lines = (ln.rstrip() for ln in "".join(out).split("\n"))
+    return "\n".join(ln for ln in lines if ln)
+
+
 def source_sha(files=None) -> str:
-    """Hash of kernel sources: the named files of the library's csrc folder
-    (a kernel's own header and those it includes), or all of them."""
+    """Hash of kernel sources without comments: the named files of the
+    library's csrc folder (a kernel's own header and those it includes), or
+    all of them."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2510_07539_gb300", "csrc")
     names = sorted(files) if files else sorted(os.listdir(csrc))
     for name in names:
-        with open(os.path.join(csrc, name), "rb") as fh:
-            h.update(fh.read())
+        with open(os.path.join(csrc, name), encoding="utf-8") as fh:
+            h.update(code_of(fh.read()).encode("utf-8"))
     return h.hexdigest()[:16]
 
 

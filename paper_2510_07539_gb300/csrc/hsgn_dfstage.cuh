@@ -7,9 +7,13 @@
 // few single-precision instructions; sm_103a issues 58 single-precision
 // operations per double-precision one). Same tiling as the windowed mixed
 // stage (hsgn_fused.cuh): CTA p owns the tile [t0, t0 + sp) of rows and solves
-// the depth system on the window [t0 - HW, t0 + sp + HW), dropping the
-// coupling beyond it; the decay bound of that truncation is checked per CTA
-// against 2^-50 (the pairs carry about 2^-47), else HSGN_ERR_TRUNCATION.
+// the depth system on the window [t0 - HWt, t0 + sp + HWt), dropping the
+// coupling beyond it. The overlap HWt (48 .. 96 rows) is a launch parameter
+// that the host sets from the coupling stage 2 recorded; the decay bound of
+// the truncation is checked per CTA against 2^-50 (the pairs carry about
+// 2^-47), a tile whose window misses it is redone in pieces with the widest
+// overlap HW, and beyond that the stage reports HSGN_ERR_TRUNCATION. The flat
+// bottom and the well-balanced bottom form (WB) share the kernel.
 //
 // Increment form, as in the mixed stage but with the increments kept as pairs:
 //  * stage 1 (U_b = U_l = U^n) writes dU1 = U_I^(1) - U^n;
