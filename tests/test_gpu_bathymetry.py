@@ -157,6 +157,33 @@ def test_wb_gauss_bottom_trajectory(form):
     assert abs(math.fsum(got[0]) - math.fsum(U[0])) <= 1e-13 * math.fsum(U[0])
 
 
+@pytest.mark.parametrize("bc", [0, 1])
+@pytest.mark.parametrize("n", [1000, 2689])
+def test_wb_dfloat_fallback_tiles_match_oracle(n, bc):
+    # CFL_IMEX 5.5 over Gaussian bumps: the first step's 64-row windows miss
+    # the decay bound and every tile is redone in pieces with 96 rows (the
+    # bottom reloaded per piece); the second step takes the recorded overlap
+    dx, lam = 0.1, 100.0
+    x, _, b, U = inputs.gauss_bottom_wave(400 + n, n, dx, amp=0.05)
+    p = oracle.Params(n, dx, bc, lam=lam, form=1, bathy=b)
+    dt, _, _ = oracle.suggest_dt(p, U, 5.5, 1e9)
+    with wb_solver(n, dx, bc, lam, b, S().FLAG_DOUBLE_FLOAT) as s:
+        s.set_state(*(dev(u) for u in U))
+        s.run(dt, 1)
+        need, ov = s.df_overlap()
+        assert 63 < need <= 95 and ov > 64, (need, ov)
+        one = [t.cpu().numpy() for t in s.get_state()]
+        s.run(dt, 1)
+        two = [t.cpu().numpy() for t in s.get_state()]
+    r1 = oracle.step(p, U, dt)
+    r2 = oracle.step(p, r1, dt)
+    for got, ref, u0 in ((one, r1, U), (two, r2, r1)):
+        for k in (0, 2):
+            assert rel_l2(got[k], ref[k]) < 1e-12, (k, rel_l2(got[k], ref[k]))
+        assert np.linalg.norm(got[1] - ref[1]) < 1e-12 * (np.linalg.norm(ref[1]) + np.linalg.norm(u0[0]))
+        assert np.linalg.norm(got[3] - ref[3]) < 1e-12 * np.linalg.norm(hw_scale(u0, lam, dt))
+
+
 def test_wb_dfloat_per_step_dt_matches_the_oracle_policy():
     # the per-step time step (Sec. 5) on the double-float bottom form: every
     # step takes dt = min(2 dx/nu_max, 0.5 dx/u_max) of the state it starts
