@@ -310,16 +310,15 @@ __global__ void __launch_bounds__(T, (WB ? 768 : 1024) / T) k_mixed_fused(const 
         tile = blockIdx.x - I.blk0;
         cell0 = I.cell0;
         face0 = I.cell0 + k;  // instance k's n+1 faces follow those of instances < k
-        // tau = gamma dt, gamma = 1 - 1/sqrt(2) (Sec. 3.2), rounded as for one instance
-        const double tau = (1.0 - 1.0 / sqrt(2.0)) * I.dt;
-        c_tau = (float)tau;
-        c_lam = (float)I.lam;
-        c_tdx = (float)(tau / I.dx);
-        c_fq = (float)(tau / (2.0 * I.dx));
-        c_Cc = (float)(tau * tau / (I.dx * I.dx));
-        c_fd = (float)(I.lam * tau * tau / (I.dx * I.dx));
-        c_lt2 = (float)(I.lam * tau * tau);
-        c_ltau = (float)(I.lam * tau);
+        // the instance's stage constants (set on the host with its time step)
+        c_tau = I.tau;
+        c_lam = I.lamf;
+        c_tdx = I.tdx;
+        c_fq = I.fq;
+        c_Cc = I.Cc;
+        c_fd = I.fd;
+        c_lt2 = I.lt2;
+        c_ltau = I.ltau;
         spd_in = p.speed + k;
         spd_out = p.speed_next + k;
     }

@@ -1884,6 +1884,22 @@ int hsgn_adjoint(hsgn_handle_t H, double dt, int64_t n_steps, int64_t n_gauges,
     return rc;
 }
 
+// The single-precision stage constants of an instance from its time step,
+// rounded exactly as the single-instance path rounds them (tau = gamma dt,
+// gamma = 1 - 1/sqrt(2), Sec. 3.2; each constant formed in double precision).
+void set_inst_constants(InstInfo& I) {
+    const double gam = 1.0 - 1.0 / std::sqrt(2.0);
+    const double tau = gam * I.dt, dx = I.dx, lam = I.lam;
+    I.tau = (float)tau;
+    I.tdx = (float)(tau / dx);
+    I.fq = (float)(tau / (2.0 * dx));
+    I.Cc = (float)(tau * tau / (dx * dx));
+    I.fd = (float)(lam * tau * tau / (dx * dx));
+    I.lt2 = (float)(lam * tau * tau);
+    I.ltau = (float)(lam * tau);
+    I.lamf = (float)lam;
+}
+
 int hsgn_create_batched(int32_t count, const int64_t* n, const double* x_left,
                         const double* x_right, const double* lambda, double g, int32_t bc,
                         int32_t flags, hsgn_handle_t* out) {
@@ -1914,6 +1930,7 @@ int hsgn_create_batched(int32_t count, const int64_t* n, const double* x_left,
         I.dx = (x_right[k] - x_left[k]) / (double)nk;
         I.lam = lambda[k];
         I.dt = 0.0;
+        set_inst_constants(I);
         if (windowed) {
             // tiles of the windowed stage (set by assign_tiles below); the tile
             // tables hold every instance on either variant
@@ -2039,7 +2056,10 @@ int hsgn_batched_set_dt(hsgn_handle_t H, const double* dt) {
     if (!H || !H->batched || !dt) return HSGN_ERR_INVALID_ARG;
     for (int32_t k = 0; k < H->count; ++k)
         if (!(dt[k] > 0.0) || !std::isfinite(dt[k])) return HSGN_ERR_INVALID_ARG;
-    for (int32_t k = 0; k < H->count; ++k) H->inst_h[(size_t)k].dt = dt[k];
+    for (int32_t k = 0; k < H->count; ++k) {
+        H->inst_h[(size_t)k].dt = dt[k];
+        set_inst_constants(H->inst_h[(size_t)k]);
+    }
     if (cudaDeviceSynchronize() != cudaSuccess) return HSGN_ERR_CUDA;
     if (cudaMemcpy(H->inst, H->inst_h.data(), H->count * sizeof(InstInfo), cudaMemcpyHostToDevice) !=
         cudaSuccess)

@@ -104,7 +104,11 @@ struct MixedParams {
 };
 
 // One instance of a batch: packed cell offset, size, block split, first global
-// block, grid spacing, relaxation parameter and time step.
+// block, grid spacing, relaxation parameter and time step, and the stage
+// constants in single precision that follow from them (tau = gamma dt: tau,
+// tau/dx, tau/(2dx), tau^2/dx^2, lambda tau^2/dx^2, lambda tau^2, lambda tau,
+// lambda), set on the host with the time step exactly as for one instance
+// (the FP64 pipe would otherwise spend every CTA's start on them).
 struct InstInfo {
     int64_t cell0;
     int64_t n;
@@ -112,6 +116,7 @@ struct InstInfo {
     int32_t P, rem;
     int32_t blk0, pad;
     double dx, lam, dt;
+    float tau, tdx, fq, Cc, fd, lt2, ltau, lamf;
 };
 
 // Geometry and constants of the instance that owns a block.
@@ -150,16 +155,8 @@ __device__ __forceinline__ BlockCtx make_ctx(const MixedParams& p, int64_t b) {
         c.split.rem = I.rem;
         c.lb = b - I.blk0;
         c.blk0 = I.blk0;
-        // tau = gamma dt with gamma = 1 - 1/sqrt(2) (Sec. 3.2)
-        const double tau = (1.0 - 1.0 / sqrt(2.0)) * I.dt;
-        c.tau = (float)tau;
-        c.tdx = (float)(tau / I.dx);
-        c.fq = (float)(tau / (2.0 * I.dx));
-        c.Cc = (float)(tau * tau / (I.dx * I.dx));
-        c.fd = (float)(I.lam * tau * tau / (I.dx * I.dx));
-        c.lt2 = (float)(I.lam * tau * tau);
-        c.ltau = (float)(I.lam * tau);
-        c.lam = (float)I.lam;
+        c.tau = I.tau; c.tdx = I.tdx; c.fq = I.fq; c.Cc = I.Cc; c.fd = I.fd;
+        c.lt2 = I.lt2; c.ltau = I.ltau; c.lam = I.lamf;
         c.speed = p.speeds + k;
     }
     c.r0 = c.split.start(c.lb);
