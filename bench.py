@@ -70,8 +70,8 @@ FLOPS_PER_CELL_ASSEMBLE = 149.0
 # kernel has changed since (the roofline then reports no achieved flop rate).
 DF_FLOPS_PER_CELL = 1521.0      # stage 1 / 2: 1428 / 1614
 DF_FP32_INST_PER_CELL = 1259.5  # FADD + FMUL + FFMA instructions, stage 1 / 2: 1182 / 1337
-DF_TRAFFIC_PER_CELL = 70.8      # dram__bytes_read + write per cell and launch, stage 1 / 2: 53.1 / 88.5
-DF_FLOPS_SOURCE_SHA = "ee1f947fd30781ea"
+DF_TRAFFIC_PER_CELL = 70.8      # dram__bytes_read + write per cell and launch, stage 1 / 2: 53.1 / 88.4
+DF_FLOPS_SOURCE_SHA = "42b93e9b3d93b8a3"
 DF_SOURCES = ("hsgn_dfstage.cuh", "hsgn_dfloat.cuh", "hsgn_fused.cuh", "hsgn_mixed.cuh",
               "hsgn_tridiag.cuh")
 
