@@ -1029,6 +1029,48 @@ def run_ours(args):
         nbytes = 4 * n * 8 * len(lams)
         e2e = {"value": units / (ems / 1e3), "unit": UNIT,
                "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes, "steps": k_e2e}
+        # the host link alone, after the timed region: the same arrays copied in,
+        # out and both ways at once (one stream per direction, best of three);
+        # a step cannot take less than its bytes at the two-way rate
+        dev_in = [torch.empty(n, dtype=torch.float64, device="cuda") for _ in range(4 * len(lams))]
+        dev_out = [torch.zeros(n, dtype=torch.float64, device="cuda") for _ in range(4 * len(lams))]
+        src_in = [u for hi in host_in for u in hi]
+        dst_out = [u for ho in host_out[0] for u in ho]
+        up, down = torch.cuda.Stream(), torch.cuda.Stream()
+
+        def link_ms(h2d, d2h):
+            best = float("inf")
+            for _ in range(3):
+                torch.cuda.synchronize()
+                a = torch.cuda.Event(enable_timing=True)
+                b = torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                for st, on, pairs in ((up, h2d, zip(dev_in, src_in)),
+                                      (down, d2h, zip(dst_out, dev_out))):
+                    if not on:
+                        continue
+                    st.wait_event(a)
+                    with torch.cuda.stream(st):
+                        for dst, src in pairs:
+                            dst.copy_(src, non_blocking=True)
+                    j = torch.cuda.Event()
+                    j.record(st)
+                    stream.wait_event(j)
+                b.record(stream)
+                b.synchronize()
+                best = min(best, a.elapsed_time(b))
+            return best
+
+        t_up, t_down, t_both = link_ms(True, False), link_ms(False, True), link_ms(True, True)
+        del dev_in, dev_out
+        both_gbs = nbytes / (t_both * 1e6)
+        ceiling = 2.0 * n * len(lams) / (t_both / 1e3)
+        e2e["host_link"] = {
+            "h2d_gbs": nbytes / (t_up * 1e6), "d2h_gbs": nbytes / (t_down * 1e6),
+            "both_ways_gbs_per_direction": both_gbs,
+            "e2e_ceiling": ceiling, "frac_of_ceiling": e2e["value"] / ceiling,
+            "note": "plain copies of the step's bytes, timed after the e2e region; the ceiling is "
+                    "the step's updates over the time both copies take at once"}
 
     # ---- CPU oracle baseline and the error of every form against it
     cpu = None
