@@ -23,8 +23,14 @@
 //    rounding scales with the increment rather than with the depth.
 // Accuracy choices (each measured against the FP64 oracle: without them the
 // h w error per stage was 4e-13, with them under 1e-13):
-//  * differences of neighbouring values (flux differences, q^dag, m^dag, h_b and
-//    dh differences) use the cancellation-accurate sum add_acc;
+//  * differences of neighbouring state values (the U_b parts of q^dag and
+//    m^dag, h_b, h_l, the bottom, pi) use the cancellation-accurate sum add_acc;
+//    so do the fluxes of h eta and h w, the face terms Phi and the dm^
+//    differences inside them, whose errors reach h w through the relaxation's
+//    lambda tau. The plain pair sum add_u (rounding about 2^-47 of its
+//    operands) takes the differences that reach the depth system only through
+//    tau/(2dx) twice (the flux of q; the dq increments of the rows) or reach
+//    only q (the dh and dm^ increments of the back-substitution);
 //  * hbar^2 - m_b = (h_b^2 - m_b) + dh (2 h_b + dh), with h_b^2 - m_b formed
 //    exactly (sq_minus), so that the relaxation update
 //    (hw)bar = r_b + dr + lambda tau (hbar^2 - m^)/(hbar^2 + lambda tau^2),
@@ -540,7 +546,9 @@ __global__ void __launch_bounds__(T, 2) k_df_stage(const DfParams p) {
                                                  sub_acc(sm.wb.bb.get(j0 + k + 3),
                                                          sm.wb.bb.get(j0 + k + 1))),
                                          1.5f));
-                const R dq = -(c_fq * sub_acc(FQ[k + 1], FQ[k]));
+                // (the q flux difference reaches the depth system only through
+                // tau/(2dx) twice: the plain pair sum)
+                const R dq = -(c_fq * sub_u(FQ[k + 1], FQ[k]));
                 const R ms = add_u(add_u(MB[k + 2], dm), c_lt2);
                 const R h = HL[k + 2];
                 if (!pos_finite(h)) bad |= HSGN_DEV_ERR_DEPTH;
@@ -695,7 +703,7 @@ __global__ void __launch_bounds__(T, 2) k_df_stage(const DfParams p) {
         sm.qb.get4(j0 + 4, QU + 4);
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
-            const dfl dqc = add_u(sub_acc(QU[k + 4], QU[k + 2]), sub_acc(Q8[k + 2], Q8[k]));
+            const dfl dqc = add_u(sub_acc(QU[k + 4], QU[k + 2]), sub_u(Q8[k + 2], Q8[k]));
             rd[k] = sub_u(sub_acc(Phi[k + 1], Phi[k]), kc.fq * dqc);
         }
     } else {
@@ -735,7 +743,7 @@ __global__ void __launch_bounds__(T, 2) k_df_stage(const DfParams p) {
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
             // q^dag of cells i+1 and i-1: state index i + 4, i + 2; per-cell index i + 2, i
-            const dfl dqc = add_u(sub_acc(QU[k + 4], QU[k + 2]), sub_acc(Q8[k + 2], Q8[k]));
+            const dfl dqc = add_u(sub_acc(QU[k + 4], QU[k + 2]), sub_u(Q8[k + 2], Q8[k]));
             rd[k] = sub_u(sub_acc(Phi[k + 1], Phi[k]), kc.fq * dqc);
         }
     }
@@ -786,12 +794,12 @@ __global__ void __launch_bounds__(T, 2) k_df_stage(const DfParams p) {
         const dfl dh = DH.get(r + 4);
         const dfl hb = sm.hb.get(r + 3), mb = sm.mb.get(r + 3);
         const dfl dhc = add_u(sub_acc(sm.hb.get(r + 4), sm.hb.get(r + 2)),
-                              sub_acc(DH.get(r + 5), DH.get(r + 3)));
+                              sub_u(DH.get(r + 5), DH.get(r + 3)));
         const dfl dmv = DM.get(r + 1);
         dfl dQ;
         if constexpr (!WB) {
             const dfl dmc = add_u(sub_acc(sm.mb.get(r + 4), sm.mb.get(r + 2)),
-                                  sub_acc(DM.get(r + 2), DM.get(r)));
+                                  sub_u(DM.get(r + 2), DM.get(r)));
             dQ = sub_u(DQ.get(r + 1),
                        add_u(kc.fq * (BE.get(r + 1) * dhc), kc.lfq * (DE.get(r + 1) * dmc)));
         } else {
@@ -799,8 +807,8 @@ __global__ void __launch_bounds__(T, 2) k_df_stage(const DfParams p) {
             (void)dhc;
             const dfl bp = scale(add_u(BE.get(r + 1), BE.get(r + 2)), 0.5f);
             const dfl bm = scale(add_u(BE.get(r), BE.get(r + 1)), 0.5f);
-            const dfl Fp = fma_u(bp, sub_acc(DH.get(r + 5), dh), PSI.get(r + 1));
-            const dfl Fm = fma_u(bm, sub_acc(dh, DH.get(r + 3)), PSI.get(r));
+            const dfl Fp = fma_u(bp, sub_u(DH.get(r + 5), dh), PSI.get(r + 1));
+            const dfl Fm = fma_u(bm, sub_u(dh, DH.get(r + 3)), PSI.get(r));
             dQ = sub_u(DQ.get(r + 1), kc.fq * add_u(Fp, Fm));
         }
         const dfl P = add_u(sq_minus(hb, mb), dh * add_u(scale(hb, 2.f), dh));
