@@ -71,9 +71,9 @@ FLOPS_PER_CELL_ASSEMBLE = 149.0
 DF_FLOPS_PER_CELL = 1481.5      # stage 1 / 2: 1389 / 1574
 DF_FP32_INST_PER_CELL = 1220.5  # FADD + FMUL + FFMA instructions, stage 1 / 2: 1143 / 1298
 DF_TRAFFIC_PER_CELL = 70.9      # dram__bytes_read + write per cell and launch, stage 1 / 2: 53.1 / 88.6
-DF_FLOPS_SOURCE_SHA = "31e2a8f6550f6dbd"
+DF_FLOPS_SOURCE_SHA = "c2cfbebac1571de6"
 DF_SOURCES = ("hsgn_dfstage.cuh", "hsgn_dfloat.cuh", "hsgn_fused.cuh", "hsgn_mixed.cuh",
-              "hsgn_tridiag.cuh")
+              "hsgn_kernels.cuh", "hsgn_tridiag.cuh")
 
 
 def parse_args():
